@@ -1,0 +1,125 @@
+"""Python front end of the CPU FP64 oracle (``bbc_oracle.c``).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use this module.  It never imports the CUDA
+package and the CUDA package never imports it.
+
+The oracle returns the raw correlator C_ch(r) of one time slice,
+``out[channel, r, s]`` complex128, spin ``s = a + 2(b + 2(a' + 2 b'))`` over
+the upper Dirac components; ``normalise`` multiplies by
+exp((m_B1 + m_B2) d) as in Sec. 2 Eq. 2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bbc_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libbbc_oracle.so")
+_lib = None
+
+BARYONS = ["p", "n", "Sigma+", "Sigma-", "Sigma0", "Lambda", "Xi0", "Xi-"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O3, OpenMP) into oracle/_build/."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_correlator.restype = ctypes.c_int
+        L.oracle_correlator.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_channel_count.restype = ctypes.c_int
+        L.oracle_channel_baryons.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        L.oracle_wick_count.argtypes = [ctypes.c_int]
+        L.oracle_term_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.oracle_cg5.argtypes = [ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def n_channels() -> int:
+    """52 printed channels followed by the 4 channels omitted in the isospin limit."""
+    return lib().oracle_channel_count()
+
+
+def channel_baryons(ch: int) -> tuple:
+    b = np.zeros(4, dtype=np.int32)
+    if lib().oracle_channel_baryons(ch, b.ctypes.data) != 0:
+        raise ValueError(f"bad channel {ch}")
+    return tuple(BARYONS[i] for i in b)
+
+
+def channel_name(ch: int) -> str:
+    b = channel_baryons(ch)
+    return f"{b[0]} {b[1]} <- {b[2]} {b[3]}"
+
+
+def wick_count(ch: int) -> int:
+    return lib().oracle_wick_count(ch)
+
+
+def term_count(ch: int, ap: int, bp: int) -> int:
+    return lib().oracle_term_count(ch, ap, bp)
+
+
+def cg5() -> np.ndarray:
+    out = np.zeros(16)
+    lib().oracle_cg5(out.ctypes.data)
+    return out.reshape(4, 4)
+
+
+def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
+               r_list=None) -> np.ndarray:
+    """Raw correlators of one time slice: [n_ch, n_r (or V), 16] complex128.
+
+    Su, Sd, Ss: [V, 12, 12] complex128 propagator slices (sink row 3a+c,
+    source column 3a'+c').
+    """
+    V = L ** 3
+    arrs = [np.ascontiguousarray(S, dtype=np.complex128).reshape(V, 12, 12) for S in (Su, Sd, Ss)]
+    ch = np.ascontiguousarray(np.atleast_1d(channels), dtype=np.int32)
+    if r_list is None:
+        rl, nr, n_out = None, 0, V
+    else:
+        rl = np.ascontiguousarray(np.atleast_1d(r_list), dtype=np.int32)
+        nr = n_out = len(rl)
+    out = np.zeros((len(ch), n_out, 16), dtype=np.complex128)
+    rc = lib().oracle_correlator(L, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                 len(ch), ch.ctypes.data, nr,
+                                 None if rl is None else rl.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_correlator failed ({rc})")
+    return out
+
+
+#: synthetic hadron masses for the normalisation: the sum of the quark decay
+#: masses of the generator (the paper divides by exp(-(m_B1 + m_B2)(t - t0))).
+def baryon_mass(name: str, m_ud: float, m_s: float) -> float:
+    n_s = {"p": 0, "n": 0, "Sigma+": 1, "Sigma-": 1, "Sigma0": 1, "Lambda": 1, "Xi0": 2, "Xi-": 2}[name]
+    return (3 - n_s) * m_ud + n_s * m_s
+
+
+def normalise(C: np.ndarray, channels, d: int, m_ud: float, m_s: float) -> np.ndarray:
+    """R = C * exp((m_B1 + m_B2) d) per channel (Sec. 2 Eq. 2)."""
+    out = np.array(C, copy=True)
+    for i, ch in enumerate(np.atleast_1d(channels)):
+        b = channel_baryons(int(ch))
+        out[i] *= np.exp((baryon_mass(b[0], m_ud, m_s) + baryon_mass(b[1], m_ud, m_s)) * d)
+    return out
