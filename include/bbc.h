@@ -1,0 +1,177 @@
+/*
+ * bbc.h -- C ABI of the GB300 effective-block-algorithm library (libbbc).
+ *
+ * The library computes the isospin-symmetric octet baryon-baryon four-point
+ * correlators (NBS wave functions) of Nemura, "Instructive discussion of an
+ * effective block algorithm for baryon-baryon correlators" (arXiv:1510.00903):
+ *
+ *   C_ch(r, t) = sum_X < B1_a(X + r, t) B2_b(X, t) Jbar_{B3_a' B4_b'}(t0) >
+ *
+ * (Sec. 2 Eq. 2 without the spin projection; Sec. 3 for the block/FFT method;
+ * Sec. 4 for the 52 channels) from wall-source quark propagators of a light
+ * (u = d) and a strange quark.  Per time slice the work is: baryon blocks per
+ * site (Sec. 3, diagrams (i)-(vi); Appendix A aggregation), a forward 3-D FFT
+ * of every block field, the q-space contraction of block pairs into channels
+ * (Sec. 3 Eq. LN.pLLp.FFT), an inverse 3-D FFT and the normalisation by
+ * exp((m_B1 + m_B2)(t - t0)) (Sec. 2 Eq. 2).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a bbc_status; no C++ exception crosses the ABI.  A
+ *    message describing the last failure of a context is kept per context
+ *    (bbc_last_error).
+ *  - Device pointers are only read or written on the context's CUDA stream,
+ *    asynchronously; the caller synchronises that stream before reading
+ *    results on the host.  The library never frees caller memory and never
+ *    allocates device memory: all device scratch lives in a workspace the
+ *    caller allocates (bbc_workspace_size / bbc_set_workspace).
+ *  - Propagator layout, one time slice of one flavour: S[site][12][12]
+ *    complex (interleaved re, im), site = x + L*(y + L*z), row = 3*alpha + c
+ *    (sink Dirac and colour index), column = 3*alpha' + c' (wall source).
+ *    Dirac representation, gamma4 = diag(1,1,-1,-1), C = gamma4 gamma2.
+ *  - Output layout: out[n_channels][L^3][16] complex128, spin index
+ *    s = a + 2*(b + 2*(a' + 2*b')) over the upper Dirac components
+ *    (a, b, a', b' in {0, 1}), r = x + L*(y + L*z) the relative distance of
+ *    B1 (at X + r) and B2 (at X) -- the xi ordering of Sec. 5.
+ *  - Channel ids 0..51 follow the printed order of Sec. 4 Eqs.
+ *    GeneralBB_NN .. GeneralBB_XX (row by row); ids 52..55 are the four
+ *    channels the paper omits because they vanish in the isospin limit
+ *    (Lambda Lambda <- Sigma0 Lambda, Sigma0 Sigma0 <- Sigma0 Lambda,
+ *    Sigma0 Lambda <- Lambda Lambda, Sigma0 Lambda <- Sigma0 Sigma0).
+ */
+#ifndef BBC_H
+#define BBC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bbc_ctx bbc_ctx;
+
+typedef enum {
+  BBC_OK = 0,
+  BBC_EINVAL = -1,   /* bad argument (size, id, null pointer, misaligned pointer) */
+  BBC_ENOMEM = -2,   /* workspace missing or too small, host allocation failure */
+  BBC_ECUDA = -3,    /* a CUDA runtime call failed; message in bbc_last_error */
+  BBC_ESTATE = -4,   /* call out of order (e.g. contract before build) */
+  BBC_ETIMEOUT = -5, /* reserved: a bounded device wait gave up */
+  BBC_ENUMERIC = -6  /* non-finite propagator scale detected */
+} bbc_status;
+
+typedef enum {
+  BBC_FP64 = 0,      /* blocks, FFTs, contraction and sums in FP64 */
+  BBC_MIXED_FP32 = 1 /* blocks, FFTs and block-pair products in FP32 after an exact
+                        per-slice power-of-two rescaling of each propagator; the signed
+                        sum over Wick diagrams and the normalisation in FP64 */
+} bbc_precision;
+
+typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
+
+typedef enum { BBC_LIGHT = 0, BBC_STRANGE = 1 } bbc_flavour;
+
+/* Lattice description.  L: spatial extent (4, 8, 16 or 32); T: number of time
+ * slices; t0: source time slice; m_ud, m_s: quark decay masses that fix the
+ * baryon masses used by the normalisation, m_B = (3 - n_s) m_ud + n_s m_s
+ * (a reading for synthetic data; the paper divides by the measured masses). */
+typedef struct {
+  int L;
+  int T;
+  int t0;
+  double m_ud;
+  double m_s;
+} bbc_lattice;
+
+/* Create a context for one lattice, one precision and one CUDA stream
+ * (cudaStream_t passed as void*; NULL = the legacy default stream).
+ * channels[n_channels]: channel ids (see above), any order, no duplicates.
+ * Builds the contraction plan on the host (Sec. 3 diagram classification,
+ * Appendix A block aggregation); its device tables are uploaded into the
+ * workspace by bbc_set_workspace.  Errors: EINVAL (bad L, T, t0, id,
+ * duplicate), ENOMEM. */
+bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
+                      const int* channels, int n_channels, void* cuda_stream);
+
+/* Bytes of device workspace needed to process up to `slices` time slices per
+ * bbc_run call (blocks of one slice, transforms, propagator copies). */
+bbc_status bbc_workspace_size(const bbc_ctx* ctx, int slices, size_t* bytes);
+
+/* Attach caller-owned device memory (256-byte aligned) of at least
+ * bbc_workspace_size(ctx, slices) bytes and upload the plan tables into it
+ * (asynchronously, on the context stream).  The library uses it until the
+ * next bbc_set_workspace or bbc_destroy; the caller frees it after that. */
+bbc_status bbc_set_workspace(bbc_ctx* ctx, void* dev_ptr, size_t bytes, int slices);
+
+/* Copy one time slice t of one flavour into the workspace slot `slot`
+ * (0 <= slot < slices): S[L^3][12][12] of dtype; on_device != 0 means `data`
+ * is a device pointer, else a host pointer (pinned memory gives an
+ * asynchronous copy).  The caller keeps ownership of `data`; it must stay
+ * valid until the stream has passed this call. */
+bbc_status bbc_load_propagator(bbc_ctx* ctx, int flavour, int slot, int t, const void* data,
+                               int dtype, int on_device);
+
+/* Step-1 of Sec. 5 for the slices in slots [0, n_slots): every aggregated
+ * baryon block at every site, then its forward 3-D FFT (Sec. 3 Eq.
+ * LN.pLLp.FFT, forward transform exp(-i q.x), unnormalised). */
+bbc_status bbc_build_blocks(bbc_ctx* ctx, int n_slots);
+
+/* Step-2 of Sec. 5 for slot `slot`: the q-space contraction of all channels
+ * (block-pair products summed over the open colour/spin indices, then the
+ * signed sum over Wick diagrams in FP64), the inverse 3-D FFT with 1/V, and
+ * (normalised != 0) the factor exp((m_B1 + m_B2) d), d = (t - t0) mod T.
+ * out_dev: device pointer, [n_channels][L^3][16] complex128, written fully. */
+bbc_status bbc_contract(bbc_ctx* ctx, int slot, void* out_dev, int normalised);
+
+/* Plan statistics of one channel (position in the context's channel list)
+ * and one pair of source operator terms (term3 of B3, term4 of B4; the
+ * X_u, X_d, X_s terms of Lambda / Sigma0 in that order, 0 otherwise):
+ * n_diagrams and, per diagram, the number of iterations of its open-index
+ * sum (1, 9, 36 or 144) times the parity of its Wick permutation (+1/-1)
+ * written to iters_signed[0 .. min(n, cap)).  Reproduces the paper's
+ * Tables of iteration counts (Sec. 4). */
+bbc_status bbc_plan_stats(const bbc_ctx* ctx, int channel_pos, int term3, int term4,
+                          int* n_diagrams, int* iters_signed, int cap);
+
+/* Aggregated plan sizes: unique blocks, block outputs per site, aligned
+ * block-pair products per (q, spin) and the total open-index iterations. */
+bbc_status bbc_plan_sizes(const bbc_ctx* ctx, int* n_blocks, int* n_block_outputs,
+                          int* n_pair_items, long long* pair_macs_per_site);
+
+/* Stages timed by bbc_stage_timing. */
+typedef enum {
+  BBC_STAGE_INGEST = 0,     /* propagator rescaling copy (per flavour and slice) */
+  BBC_STAGE_BUILD = 1,      /* baryon blocks of every site */
+  BBC_STAGE_FFT_FWD = 2,    /* forward 3-D FFT of every block field (3 passes) */
+  BBC_STAGE_CONTRACT = 3,   /* q-space block-pair products and Wick-sign sums */
+  BBC_STAGE_FFT_INV = 4,    /* inverse 3-D FFT of every output field (3 passes) */
+  BBC_STAGE_NORMALISE = 5,  /* 1/V, rescaling, exp((m_B1 + m_B2) d) */
+  BBC_N_STAGES = 6
+} bbc_stage;
+
+/* enable != 0: from now on bracket every stage launch with CUDA events on the
+ * context stream (events are created by the library; no device memory).
+ * enable == 0: stop.  Either way the accumulated record is cleared. */
+bbc_status bbc_enable_stage_timing(bbc_ctx* ctx, int enable);
+
+/* Synchronise the context stream, then write per stage the summed device
+ * time in milliseconds (ms[BBC_N_STAGES]) and the number of timed stage
+ * launches (launches[BBC_N_STAGES], one per API call that ran the stage) since
+ * timing was enabled or last read; clears the record. */
+bbc_status bbc_stage_timing(bbc_ctx* ctx, double* ms, long long* launches);
+
+/* Number of kernel launches one bbc_contract call issues, and one
+ * bbc_build_blocks call per slot-batch, and one bbc_load_propagator call. */
+bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, int* per_contract);
+
+/* Message of the last failed call on ctx (or of the last failed bbc_create
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* bbc_last_error(const bbc_ctx* ctx);
+
+/* Release the context and its plan tables (not the caller's workspace). */
+void bbc_destroy(bbc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBC_H */

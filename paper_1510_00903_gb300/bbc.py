@@ -1,0 +1,231 @@
+"""Thin Python binding of libbbc (include/bbc.h): argument marshalling only.
+
+Every function named ``bbc_*`` wraps the C entry point of the same name and
+raises :class:`BBCError` on a non-zero status.  :class:`Correlators` strings
+the calls together for whole time-slice ranges, using PyTorch only for
+device memory (the workspace and outputs) and the CUDA stream.
+
+There is no fallback: if ``libbbc.so`` has not been built the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libbbc.so")
+
+BBC_OK, BBC_EINVAL, BBC_ENOMEM, BBC_ECUDA, BBC_ESTATE, BBC_ETIMEOUT, BBC_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+BBC_FP64, BBC_MIXED_FP32 = 0, 1
+BBC_C128, BBC_C64 = 0, 1
+BBC_LIGHT, BBC_STRANGE = 0, 1
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "ETIMEOUT", -6: "ENUMERIC"}
+
+#: the 52 channels of Sec. 4 in printed order, then the 4 omitted ones
+CHANNELS_52 = list(range(52))
+
+
+class BBCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class bbc_lattice(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("t0", ctypes.c_int),
+                ("m_ud", ctypes.c_double), ("m_s", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbbc.so not built ({LIB_PATH}); run paper_1510_00903_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "bbc_create": ([ctypes.POINTER(P), ctypes.POINTER(bbc_lattice), I, ctypes.POINTER(I), I, P], I),
+        "bbc_workspace_size": ([P, I, ctypes.POINTER(ctypes.c_size_t)], I),
+        "bbc_set_workspace": ([P, P, ctypes.c_size_t, I], I),
+        "bbc_load_propagator": ([P, I, I, I, P, I, I], I),
+        "bbc_build_blocks": ([P, I], I),
+        "bbc_contract": ([P, I, P, I], I),
+        "bbc_plan_stats": ([P, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), I], I),
+        "bbc_plan_sizes": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(LL)], I),
+        "bbc_enable_stage_timing": ([P, I], I),
+        "bbc_stage_timing": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)], I),
+        "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bbc_last_error": ([P], ctypes.c_char_p),
+        "bbc_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != BBC_OK:
+        msg = _lib.bbc_last_error(ctx)
+        raise BBCError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------- C entry points
+def bbc_create(L: int, T: int, t0: int, m_ud: float, m_s: float, precision: int, channels,
+               cuda_stream: int = 0):
+    lat = bbc_lattice(L, T, t0, m_ud, m_s)
+    ch = (ctypes.c_int * len(channels))(*[int(c) for c in channels])
+    ctx = ctypes.c_void_p()
+    st = _lib.bbc_create(ctypes.byref(ctx), ctypes.byref(lat), int(precision), ch, len(channels),
+                         ctypes.c_void_p(cuda_stream or None))
+    _check(None, st)
+    return ctx
+
+
+def bbc_workspace_size(ctx, slices: int) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, _lib.bbc_workspace_size(ctx, slices, ctypes.byref(n)))
+    return n.value
+
+
+def bbc_set_workspace(ctx, dev_ptr: int, nbytes: int, slices: int):
+    _check(ctx, _lib.bbc_set_workspace(ctx, ctypes.c_void_p(dev_ptr), nbytes, slices))
+
+
+def bbc_load_propagator(ctx, flavour: int, slot: int, t: int, ptr: int, dtype: int, on_device: bool):
+    _check(ctx, _lib.bbc_load_propagator(ctx, flavour, slot, t, ctypes.c_void_p(ptr), dtype, int(on_device)))
+
+
+def bbc_build_blocks(ctx, n_slots: int):
+    _check(ctx, _lib.bbc_build_blocks(ctx, n_slots))
+
+
+def bbc_contract(ctx, slot: int, out_ptr: int, normalised: bool):
+    _check(ctx, _lib.bbc_contract(ctx, slot, ctypes.c_void_p(out_ptr), int(normalised)))
+
+
+def bbc_plan_stats(ctx, channel_pos: int, term3: int, term4: int, cap: int = 64):
+    n = ctypes.c_int()
+    buf = (ctypes.c_int * cap)()
+    _check(ctx, _lib.bbc_plan_stats(ctx, channel_pos, term3, term4, ctypes.byref(n), buf, cap))
+    return [buf[i] for i in range(min(n.value, cap))]
+
+
+def bbc_plan_sizes(ctx):
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(ctx, _lib.bbc_plan_sizes(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return {"blocks": a.value, "block_outputs": b.value, "pair_items": c.value, "pair_macs_per_site": d.value}
+
+
+STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise"]
+
+
+def bbc_enable_stage_timing(ctx, enable: bool):
+    _check(ctx, _lib.bbc_enable_stage_timing(ctx, int(enable)))
+
+
+def bbc_stage_timing(ctx):
+    """{stage: (summed ms, launches)} since timing was enabled or last read."""
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (ctypes.c_longlong * len(STAGES))()
+    _check(ctx, _lib.bbc_stage_timing(ctx, ms, n))
+    return {s: (ms[i], n[i]) for i, s in enumerate(STAGES)}
+
+
+def bbc_launch_counts(ctx):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, _lib.bbc_launch_counts(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"load": a.value, "build": b.value, "contract": c.value}
+
+
+def bbc_last_error(ctx) -> str:
+    m = _lib.bbc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def bbc_destroy(ctx):
+    _lib.bbc_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience
+class Correlators:
+    """All steps of the path for one lattice, on one CUDA stream.
+
+    ``run(S_light, S_strange, times)`` takes propagators ``[len(times), V, 12, 12]``
+    (torch tensors, complex128 or complex64, on the GPU or pinned on the host)
+    and returns ``[len(times), n_channels, V, 16]`` complex128 on the GPU.
+    """
+
+    def __init__(self, L: int, T: int, t0: int = 0, m_ud: float = 0.3, m_s: float = 0.4,
+                 channels=CHANNELS_52, precision: int = BBC_FP64, slices: int = 1, device=None,
+                 stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.L, self.T, self.t0, self.V = L, T, t0, L ** 3
+        self.channels = list(channels)
+        self.precision = precision
+        self.ctx = bbc_create(L, T, t0, m_ud, m_s, precision, self.channels, self.stream.cuda_stream)
+        self.slices = slices
+        nbytes = bbc_workspace_size(self.ctx, slices)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        with torch.cuda.stream(self.stream):
+            bbc_set_workspace(self.ctx, self._ws_ptr, nbytes, slices)
+
+    def sizes(self):
+        return bbc_plan_sizes(self.ctx)
+
+    def load(self, flavour: int, slot: int, t: int, S):
+        torch = self.torch
+        dtype = {torch.complex128: BBC_C128, torch.complex64: BBC_C64}[S.dtype]
+        if not S.is_contiguous() or S.numel() != self.V * 144:
+            raise ValueError(f"propagator slice must be contiguous [{self.V}, 12, 12]")
+        if S.is_cuda and S.device != self.device:
+            raise ValueError("propagator on another device")
+        bbc_load_propagator(self.ctx, flavour, slot, t, S.data_ptr(), dtype, S.is_cuda)
+
+    def build(self, n_slots: int):
+        bbc_build_blocks(self.ctx, n_slots)
+
+    def contract(self, slot: int, out, normalised: bool = True):
+        if out.dtype != self.torch.complex128 or not out.is_cuda or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex128 CUDA tensor")
+        bbc_contract(self.ctx, slot, out.data_ptr(), normalised)
+
+    def run(self, S_light, S_strange, times, out=None, normalised: bool = True):
+        torch = self.torch
+        times = list(times)
+        n_ch = len(self.channels)
+        if out is None:
+            out = torch.empty((len(times), n_ch, self.V, 16), dtype=torch.complex128, device=self.device)
+        with torch.cuda.stream(self.stream):
+            for i0 in range(0, len(times), self.slices):
+                chunk = times[i0:i0 + self.slices]
+                for j, t in enumerate(chunk):
+                    self.load(BBC_LIGHT, j, t, S_light[i0 + j])
+                    self.load(BBC_STRANGE, j, t, S_strange[i0 + j])
+                self.build(len(chunk))
+                for j in range(len(chunk)):
+                    self.contract(j, out[i0 + j], normalised)
+        return out
+
+    def close(self):
+        if self.ctx:
+            bbc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,419 @@
+// bbc_api.cpp -- C ABI of libbbc (declared in include/bbc.h).
+//
+// A context owns the host plan (planner.cpp) and a view of the caller's
+// device workspace: the plan tables, per-slot propagator copies and the
+// block fields of every slot.  Every device operation is issued on the
+// context stream; nothing here allocates device memory.
+#include "../../include/bbc.h"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "planner.hpp"
+
+struct bbc_ctx {
+  bbc_lattice lat{};
+  int prec = BBC_FP64;
+  cudaStream_t stream = nullptr;
+  int V = 0;
+  bbc::Plan plan;
+  std::string err;
+  // workspace view
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int slots = 0;
+  int* d_row_ptr = nullptr;
+  uint32_t* d_entries = nullptr;
+  bbc::DevPairItem* d_items = nullptr;
+  int* d_cptr = nullptr;
+  int* d_citem = nullptr;
+  double* d_ccoef = nullptr;
+  char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
+  char* d_prop = nullptr;                // [slots][2][V*144] compute precision
+  unsigned long long* d_amax = nullptr;  // [slots][2]
+  int* d_kexp = nullptr;                 // [slots][2]
+  char* d_blk = nullptr;                 // [slots][V][n_out]
+  std::vector<int> slot_t;               // time slice of each slot (-1: none)
+  std::vector<int> slot_loaded;          // bit 0: light, bit 1: strange
+  std::vector<int> slot_built;
+  bool twiddles = false;
+  // stage timing: event pairs per stage, recycled through a pool
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[BBC_N_STAGES];
+  std::vector<cudaEvent_t> pool;
+  ~bbc_ctx() {
+    for (auto& v : pending)
+      for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+std::string g_create_error;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
+
+struct Layout {
+  size_t row_ptr, entries, items, cptr, citem, ccoef, tables_end;
+  size_t stage, prop, amax, kexp, blk, total;
+};
+
+Layout layout(const bbc_ctx* c, int slots) {
+  const bbc::Plan& p = c->plan;
+  Layout L{};
+  size_t o = 0;
+  L.row_ptr = o; o = align256(o + sizeof(int) * p.row_ptr.size());
+  L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
+  L.items = o; o = align256(o + sizeof(bbc::DevPairItem) * p.items.size());
+  L.cptr = o; o = align256(o + sizeof(int) * p.contrib_ptr.size());
+  L.citem = o; o = align256(o + sizeof(int) * p.contrib_item.size());
+  L.ccoef = o; o = align256(o + sizeof(double) * p.contrib_coef.size());
+  L.tables_end = o;
+  const size_t V = c->V;
+  L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
+  L.prop = o; o = align256(o + (size_t)slots * 2 * V * 144 * cplx_bytes(c->prec));
+  L.amax = o; o = align256(o + (size_t)slots * 2 * sizeof(unsigned long long));
+  L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
+  L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
+  L.total = o;
+  return L;
+}
+
+bbc_status fail(bbc_ctx* c, bbc_status s, const std::string& m) {
+  if (c) c->err = m;
+  else g_create_error = m;
+  return s;
+}
+
+bbc_status cuda_fail(bbc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, BBC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool supported_L(int L) { return L == 2 || L == 4 || L == 8 || L == 16 || L == 32; }
+
+cudaEvent_t take_event(bbc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one stage launch with events when timing is enabled.
+struct StageScope {
+  bbc_ctx* c;
+  int stage;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(bbc_ctx* ctx, int s) : c(ctx), stage(s) {
+    if (!c->timing) return;
+    a = take_event(c);
+    b = take_event(c);
+    if (a) cudaEventRecord(a, c->stream);
+  }
+  ~StageScope() {
+    if (!a || !b) return;
+    cudaEventRecord(b, c->stream);
+    c->pending[stage].push_back({a, b});
+  }
+};
+
+bbc::DevGroups groups_of(const bbc::Plan& p) {
+  bbc::DevGroups g{};
+  g.n = (int)p.groups.size();
+  for (int i = 0; i < g.n; i++) {
+    g.first[i] = p.groups[i].first_row;
+    g.rows[i] = p.groups[i].n_rows;
+    g.fam0[i] = p.groups[i].fam[0];
+    g.fam1[i] = p.groups[i].fam[1];
+  }
+  return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec, const int* channels,
+                      int n_channels, void* cuda_stream) {
+  if (!ctx || !lat || !channels) return fail(nullptr, BBC_EINVAL, "null argument");
+  *ctx = nullptr;
+  if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 32)");
+  if (lat->T < 1 || lat->t0 < 0 || lat->t0 >= lat->T) return fail(nullptr, BBC_EINVAL, "bad T or t0");
+  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32) return fail(nullptr, BBC_EINVAL, "bad precision");
+  if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");
+  bbc_ctx* c = new (std::nothrow) bbc_ctx();
+  if (!c) return fail(nullptr, BBC_ENOMEM, "host allocation failed");
+  c->lat = *lat;
+  c->prec = prec;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->V = lat->L * lat->L * lat->L;
+  std::string err;
+  try {
+    if (!bbc::build_plan(channels, n_channels, &c->plan, &err)) {
+      delete c;
+      return fail(nullptr, BBC_EINVAL, err);
+    }
+  } catch (const std::bad_alloc&) {
+    delete c;
+    return fail(nullptr, BBC_ENOMEM, "host allocation failed while planning");
+  } catch (...) {
+    delete c;
+    return fail(nullptr, BBC_EINVAL, "planner failed");
+  }
+  *ctx = c;
+  return BBC_OK;
+}
+
+bbc_status bbc_workspace_size(const bbc_ctx* ctx, int slices, size_t* bytes) {
+  if (!ctx || !bytes || slices < 1) return BBC_EINVAL;
+  *bytes = layout(ctx, slices).total;
+  return BBC_OK;
+}
+
+bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices) {
+  if (!c) return BBC_EINVAL;
+  if (!dev_ptr || slices < 1) return fail(c, BBC_EINVAL, "null workspace or slices < 1");
+  if (((uintptr_t)dev_ptr) & 255) return fail(c, BBC_EINVAL, "workspace must be 256-byte aligned");
+  Layout L = layout(c, slices);
+  if (bytes < L.total) return fail(c, BBC_ENOMEM, "workspace too small: need " + std::to_string(L.total) + " bytes");
+  if (!c->twiddles) {
+    cudaError_t e = bbc::upload_twiddles();
+    if (e != cudaSuccess) return cuda_fail(c, e, "twiddle upload");
+    c->twiddles = true;
+  }
+  char* w = (char*)dev_ptr;
+  c->ws = w;
+  c->ws_bytes = bytes;
+  c->slots = slices;
+  c->d_row_ptr = (int*)(w + L.row_ptr);
+  c->d_entries = (uint32_t*)(w + L.entries);
+  c->d_items = (bbc::DevPairItem*)(w + L.items);
+  c->d_cptr = (int*)(w + L.cptr);
+  c->d_citem = (int*)(w + L.citem);
+  c->d_ccoef = (double*)(w + L.ccoef);
+  c->d_stage = w + L.stage;
+  c->d_prop = w + L.prop;
+  c->d_amax = (unsigned long long*)(w + L.amax);
+  c->d_kexp = (int*)(w + L.kexp);
+  c->d_blk = w + L.blk;
+  const bbc::Plan& p = c->plan;
+  std::vector<bbc::DevPairItem> items(p.items.size());
+  for (size_t i = 0; i < p.items.size(); i++) {
+    const bbc::PairItem& s = p.items[i];
+    items[i].offA = s.offA;
+    items[i].offB = s.offB;
+    items[i].n12 = s.n1 | (s.n2 << 16);
+    items[i].sA = s.sA1 | (s.sA2 << 16);
+    items[i].sB = s.sB1 | (s.sB2 << 16);
+    items[i].pad = 0;
+  }
+  struct Up { void* dst; const void* src; size_t n; } ups[] = {
+      {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
+      {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
+      {c->d_items, items.data(), sizeof(bbc::DevPairItem) * items.size()},
+      {c->d_cptr, p.contrib_ptr.data(), sizeof(int) * p.contrib_ptr.size()},
+      {c->d_citem, p.contrib_item.data(), sizeof(int) * p.contrib_item.size()},
+      {c->d_ccoef, p.contrib_coef.data(), sizeof(double) * p.contrib_coef.size()},
+  };
+  for (auto& u : ups) {
+    if (u.n == 0) continue;
+    // synchronous copy from pageable host memory: the tables are live only
+    // as long as this call
+    cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "table upload");
+  c->slot_t.assign(slices, -1);
+  c->slot_loaded.assign(slices, 0);
+  c->slot_built.assign(slices, 0);
+  return BBC_OK;
+}
+
+bbc_status bbc_load_propagator(bbc_ctx* c, int flavour, int slot, int t, const void* data, int dtype,
+                               int on_device) {
+  if (!c) return BBC_EINVAL;
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  if (flavour != BBC_LIGHT && flavour != BBC_STRANGE) return fail(c, BBC_EINVAL, "bad flavour");
+  if (slot < 0 || slot >= c->slots) return fail(c, BBC_EINVAL, "bad slot");
+  if (t < 0 || t >= c->lat.T) return fail(c, BBC_EINVAL, "bad time slice");
+  if (!data) return fail(c, BBC_EINVAL, "null propagator");
+  if (dtype != BBC_C128 && dtype != BBC_C64) return fail(c, BBC_EINVAL, "bad dtype");
+  const size_t nc = (size_t)c->V * 144;
+  const size_t in_bytes = nc * (dtype == BBC_C128 ? 16 : 8);
+  const void* src = data;
+  if (!on_device) {
+    char* stage = c->d_stage + ((size_t)slot * 2 + flavour) * nc * 16;
+    cudaError_t e = cudaMemcpyAsync(stage, data, in_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "propagator upload");
+    src = stage;
+  } else if (((uintptr_t)data) & 15) {
+    return fail(c, BBC_EINVAL, "device propagator must be 16-byte aligned");
+  }
+  unsigned long long* amax = c->d_amax + slot * 2 + flavour;
+  int* kexp = c->d_kexp + slot * 2 + flavour;
+  StageScope scope(c, BBC_STAGE_INGEST);
+  cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(*amax), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  e = bbc::launch_absmax(src, dtype, (long long)nc, amax, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "absmax kernel");
+  char* dst = c->d_prop + ((size_t)slot * 2 + flavour) * nc * cplx_bytes(c->prec);
+  e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, c->prec == BBC_FP64, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
+  if (c->slot_t[slot] != t) {
+    c->slot_loaded[slot] = 0;
+    c->slot_t[slot] = t;
+  }
+  c->slot_loaded[slot] |= 1 << flavour;
+  c->slot_built[slot] = 0;
+  return BBC_OK;
+}
+
+bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
+  if (!c) return BBC_EINVAL;
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  if (n_slots < 1 || n_slots > c->slots) return fail(c, BBC_EINVAL, "bad slot count");
+  for (int s = 0; s < n_slots; s++)
+    if (c->slot_loaded[s] != 3) return fail(c, BBC_ESTATE, "slot " + std::to_string(s) + " lacks a propagator");
+  const bool fp64 = c->prec == BBC_FP64;
+  const bbc::Plan& p = c->plan;
+  cudaError_t e;
+  {
+    StageScope scope(c, BBC_STAGE_BUILD);
+    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_row_ptr, c->d_entries, groups_of(p), c->d_blk,
+                                p.n_out, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "block build");
+  }
+  {
+    StageScope scope(c, BBC_STAGE_FFT_FWD);
+    for (int axis = 0; axis < 3; axis++) {
+      e = bbc::launch_fft_pass(c->d_blk, c->lat.L, n_slots, p.n_out, axis, false, fp64, fp64, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
+    }
+  }
+  for (int s = 0; s < n_slots; s++) c->slot_built[s] = 1;
+  return BBC_OK;
+}
+
+bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
+  if (!c) return BBC_EINVAL;
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  if (slot < 0 || slot >= c->slots) return fail(c, BBC_EINVAL, "bad slot");
+  if (!c->slot_built[slot]) return fail(c, BBC_ESTATE, "blocks of this slot are not built");
+  if (!out_dev || (((uintptr_t)out_dev) & 15)) return fail(c, BBC_EINVAL, "output must be a 16-byte aligned device pointer");
+  const bool fp64 = c->prec == BBC_FP64;
+  const bbc::Plan& p = c->plan;
+  const int n_ch = (int)p.channels.size();
+  const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+  cudaError_t e;
+  {
+    StageScope scope(c, BBC_STAGE_CONTRACT);
+    e = bbc::launch_contract(blk, c->lat.L, p.n_out, c->d_items, (int)p.items.size(), c->d_cptr, c->d_citem,
+                             c->d_ccoef, n_ch, out_dev, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "contract");
+  }
+  {
+    StageScope scope(c, BBC_STAGE_FFT_INV);
+    for (int axis = 0; axis < 3; axis++) {
+      e = bbc::launch_fft_pass(out_dev, c->lat.L, n_ch, 16, axis, true, true, fp64, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
+    }
+  }
+  bbc::NormParams np{};
+  np.n_ch = n_ch;
+  const int t = c->slot_t[slot];
+  const int d = ((t - c->lat.t0) % c->lat.T + c->lat.T) % c->lat.T;
+  for (int i = 0; i < n_ch; i++) {
+    const int ns = p.n_strange[i];
+    const double mass = (6 - ns) * c->lat.m_ud + ns * c->lat.m_s;  // m_B1 + m_B2
+    np.f[i] = (1.0 / c->V) * (normalised ? std::exp(mass * d) : 1.0);
+    np.nl[i] = 6 - ns;
+    np.ns[i] = ns;
+  }
+  StageScope scope(c, BBC_STAGE_NORMALISE);
+  e = bbc::launch_normalise(out_dev, c->V, np, c->d_kexp + slot * 2, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "normalise");
+  return BBC_OK;
+}
+
+bbc_status bbc_plan_stats(const bbc_ctx* c, int channel_pos, int term3, int term4, int* n_diagrams,
+                          int* iters_signed, int cap) {
+  if (!c || !n_diagrams) return BBC_EINVAL;
+  if (channel_pos < 0 || channel_pos >= (int)c->plan.channels.size()) return BBC_EINVAL;
+  int n = 0;
+  for (const auto& d : c->plan.diagrams)
+    if (d.ch_pos == channel_pos && d.term3 == term3 && d.term4 == term4) {
+      if (iters_signed && n < cap) iters_signed[n] = d.K * d.parity;
+      n++;
+    }
+  *n_diagrams = n;
+  return BBC_OK;
+}
+
+bbc_status bbc_plan_sizes(const bbc_ctx* c, int* n_blocks, int* n_block_outputs, int* n_pair_items,
+                          long long* pair_macs_per_site) {
+  if (!c) return BBC_EINVAL;
+  if (n_blocks) *n_blocks = c->plan.n_blocks;
+  if (n_block_outputs) *n_block_outputs = c->plan.n_out;
+  if (n_pair_items) *n_pair_items = (int)c->plan.items.size();
+  if (pair_macs_per_site) *pair_macs_per_site = c->plan.pair_macs;
+  return BBC_OK;
+}
+
+bbc_status bbc_enable_stage_timing(bbc_ctx* c, int enable) {
+  if (!c) return BBC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stage timing");
+  for (auto& v : c->pending) {
+    for (auto& p : v) { c->pool.push_back(p.first); c->pool.push_back(p.second); }
+    v.clear();
+  }
+  c->timing = enable != 0;
+  return BBC_OK;
+}
+
+bbc_status bbc_stage_timing(bbc_ctx* c, double* ms, long long* launches) {
+  if (!c || !ms || !launches) return BBC_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stage timing");
+  for (int s = 0; s < BBC_N_STAGES; s++) {
+    double sum = 0.0;
+    for (auto& p : c->pending[s]) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p.first, p.second);
+      if (e != cudaSuccess) return cuda_fail(c, e, "event time");
+      sum += t;
+      c->pool.push_back(p.first);
+      c->pool.push_back(p.second);
+    }
+    ms[s] = sum;
+    launches[s] = (long long)c->pending[s].size();
+    c->pending[s].clear();
+  }
+  return BBC_OK;
+}
+
+bbc_status bbc_launch_counts(const bbc_ctx* c, int* per_load, int* per_build, int* per_contract) {
+  if (!c) return BBC_EINVAL;
+  if (per_load) *per_load = 2;          // absmax, convert
+  if (per_build) *per_build = 1 + 3;    // block build, three FFT passes
+  if (per_contract) *per_contract = 1 + 3 + 1;  // contract, three inverse passes, normalise
+  return BBC_OK;
+}
+
+const char* bbc_last_error(const bbc_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void bbc_destroy(bbc_ctx* c) { delete c; }
+
+}  // extern "C"

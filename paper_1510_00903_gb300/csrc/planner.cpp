@@ -1,0 +1,537 @@
+// planner.cpp -- diagram classification, block aggregation and contraction
+// plan of the effective block algorithm (arXiv:1510.00903, Secs. 3-4 and
+// Appendix A).  Host C++, no CUDA.
+//
+// Per channel <B1 B2 | Bbar3 Bbar4> and per pair of source operator terms
+// (the X_u, X_d, X_s terms of Lambda and Sigma0 are taken one at a time, as in
+// the paper's Tables), the flavour-preserving Wick permutations are grouped
+// into diagrams by the set S1 of source quarks contracted into the sink baryon
+// B1 (identical quarks of one sink baryon are absorbed into its block, Sec. 3
+// factor 2^{B - N_Lambda - N_Sigma0}).  A source baryon whose quarks split 2+1
+// between the sink baryons puts its tensor into the block holding two of them;
+// the third (minority) quark becomes an open index of both blocks: colour only
+// when it is the quark carried by delta (its spin is then the external source
+// spin, which moves to the other block), colour and spin otherwise (Sec. 3,
+// diagrams (ii)-(vi)).  Each block is a sparse integer-weighted sum over the
+// entries of four per-site sink tensor families; identical blocks (up to the
+// order of their external and open axes and an overall sign) are stored once
+// (Appendix A), and so are identical aligned block-pair products.
+#include "planner.hpp"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <utility>
+
+namespace bbc {
+namespace {
+
+struct Term {
+  int coef, gi, gj, dk;  // coef * eps * Cg5(a_gi, a_gj) * delta(ext, a_dk)
+};
+struct Op {
+  const char* name;
+  char flav[4];  // quark string (u, d, s)
+  double scale;  // operator prefactor (sign, 1/sqrt6, 1/sqrt2)
+  int nterm;
+  Term t[3];
+  int n_s;  // strange quarks
+};
+
+// Sec. 2: p, n (Eq. FieldOperator_N); Sigma+-, Sigma0, Lambda, Xi0, Xi-
+// (Eq. FieldOperator_SLXi) with X_u = eps(d Cg5 s)u, X_d = eps(s Cg5 u)d,
+// X_s = eps(u Cg5 d)s (Eq. FieldOperator_xxx) written on the common string
+// (d, s, u) (cyclic reorderings of three quark fields are even).
+enum { OP_P, OP_N, OP_SP, OP_SM, OP_S0, OP_LA, OP_X0, OP_XM };
+const double kInvSqrt6 = 0.40824829046386301637;
+const double kInvSqrt2 = 0.70710678118654752440;
+const Op kOps[8] = {
+    {"p", "udu", 1.0, 1, {{1, 0, 1, 2}}, 0},
+    {"n", "udd", -1.0, 1, {{1, 0, 1, 2}}, 0},
+    {"Sigma+", "usu", -1.0, 1, {{1, 0, 1, 2}}, 1},
+    {"Sigma-", "dsd", -1.0, 1, {{1, 0, 1, 2}}, 1},
+    {"Sigma0", "dsu", kInvSqrt2, 2, {{1, 0, 1, 2}, {-1, 1, 2, 0}}, 1},
+    {"Lambda", "dsu", kInvSqrt6, 3, {{1, 0, 1, 2}, {1, 1, 2, 0}, {-2, 2, 0, 1}}, 1},
+    {"Xi0", "uss", 1.0, 1, {{1, 0, 1, 2}}, 2},
+    {"Xi-", "dss", -1.0, 1, {{1, 0, 1, 2}}, 2},
+};
+
+// Channels of Sec. 4 (Eqs. GeneralBB_NN .. GeneralBB_XX) in printed order,
+// then the four omitted ones.
+std::vector<std::array<int, 4>> make_channels() {
+  std::vector<std::array<int, 4>> c;
+  c.push_back({OP_P, OP_N, OP_P, OP_N});
+  const int nl[3][2] = {{OP_P, OP_LA}, {OP_SP, OP_N}, {OP_S0, OP_P}};
+  for (auto& a : nl)
+    for (auto& b : nl) c.push_back({a[0], a[1], b[0], b[1]});
+  const int s6[6][2] = {{OP_LA, OP_LA}, {OP_P, OP_XM}, {OP_N, OP_X0},
+                        {OP_SP, OP_SM}, {OP_S0, OP_S0}, {OP_S0, OP_LA}};
+  for (int b = 0; b < 5; b++) c.push_back({OP_LA, OP_LA, s6[b][0], s6[b][1]});
+  const int mid[3][2] = {{OP_P, OP_XM}, {OP_N, OP_X0}, {OP_SP, OP_SM}};
+  for (auto& a : mid)
+    for (int b = 0; b < 6; b++) c.push_back({a[0], a[1], s6[b][0], s6[b][1]});
+  for (int b = 0; b < 5; b++) c.push_back({OP_S0, OP_S0, s6[b][0], s6[b][1]});
+  for (int b = 1; b < 4; b++) c.push_back({OP_S0, OP_LA, s6[b][0], s6[b][1]});
+  c.push_back({OP_S0, OP_LA, OP_S0, OP_LA});
+  const int xl[3][2] = {{OP_XM, OP_LA}, {OP_SM, OP_X0}, {OP_S0, OP_XM}};
+  for (auto& a : xl)
+    for (auto& b : xl) c.push_back({a[0], a[1], b[0], b[1]});
+  c.push_back({OP_XM, OP_X0, OP_XM, OP_X0});
+  c.push_back({OP_LA, OP_LA, OP_S0, OP_LA});
+  c.push_back({OP_S0, OP_S0, OP_S0, OP_LA});
+  c.push_back({OP_S0, OP_LA, OP_LA, OP_LA});
+  c.push_back({OP_S0, OP_LA, OP_S0, OP_S0});
+  return c;
+}
+
+const std::vector<std::array<int, 4>>& channels_table() {
+  static const std::vector<std::array<int, 4>> t = make_channels();
+  return t;
+}
+
+// C gamma5 in the Dirac representation (gamma4 = diag(1,1,-1,-1),
+// C = gamma4 gamma2): non-zero entries (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1.
+const int kCg5[4][3] = {{0, 1, +1}, {1, 0, -1}, {2, 3, +1}, {3, 2, -1}};
+// Permutations of three colours and their signs (eps tensor).
+const int kEps[6][4] = {{0, 1, 2, +1}, {1, 2, 0, +1}, {2, 0, 1, +1},
+                        {0, 2, 1, -1}, {2, 1, 0, -1}, {1, 0, 2, -1}};
+
+bool is_strange(char f) { return f == 's'; }
+
+// Family of a sink term and the slot order (Gamma pair, delta) in it.
+// D_sl[x, y] = D_ls[y, x] (eps and Cg5 both antisymmetric), so an (s, l)
+// diquark is read as (l, s) with its two slots swapped.
+int family_of(const char* flav, const Term& t, int slots[3]) {
+  bool a = is_strange(flav[t.gi]), b = is_strange(flav[t.gj]), c = is_strange(flav[t.dk]);
+  slots[0] = t.gi; slots[1] = t.gj; slots[2] = t.dk;
+  if (a && !b) { std::swap(a, b); std::swap(slots[0], slots[1]); }
+  if (!a && !b) return c ? F_LLS : F_LLL;
+  if (!a && b) return c ? F_LSS : F_LSL;
+  return -1;  // (s, s) diquark: not in the octet operators
+}
+
+// Global tensor index; families with two light diquark quarks are symmetric
+// in their first two indices, which are then stored ordered.
+int zindex(int fam, int a, int e0, int e1, int e2) {
+  if ((fam == F_LLL || fam == F_LLS) && e1 < e0) std::swap(e0, e1);
+  return (fam * 2 + a) * 1728 + e0 * 144 + e1 * 12 + e2;
+}
+
+struct SrcEntry { int eta[3]; int val; };
+
+std::vector<SrcEntry> source_entries(const Term& t, int ext) {
+  std::vector<SrcEntry> out;
+  for (auto& e : kEps)
+    for (auto& g : kCg5) {
+      int sp[3];
+      sp[t.gi] = g[0]; sp[t.gj] = g[1]; sp[t.dk] = ext;
+      SrcEntry s;
+      for (int m = 0; m < 3; m++) s.eta[m] = 3 * sp[m] + e[m];
+      s.val = e[3] * g[2];
+      out.push_back(s);
+    }
+  return out;
+}
+
+int perm_parity(const int* p, int n) {
+  int inv = 0;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) inv += p[i] > p[j];
+  return (inv & 1) ? -1 : 1;
+}
+
+using Row = std::vector<std::pair<int, int>>;  // (tensor index, weight), sorted
+
+struct NatBlock {           // a block in the diagram's natural axis order
+  std::vector<int> ext;     // source baryons (0 = B3, 1 = B4) whose spin it carries
+  std::vector<int> osz;     // open axis sizes (diagram order)
+  std::vector<Row> rows;    // index ((a * 2^next + ev) * K + ov)
+};
+
+int flat_open(const std::vector<int>& osz, const std::vector<int>& ov) {
+  int f = 0;
+  for (size_t i = 0; i < osz.size(); i++) f = f * osz[i] + ov[i];
+  return f;
+}
+int flat_ext(const std::vector<int>& ev) {
+  int f = 0;
+  for (int v : ev) f = 2 * f + v;
+  return f;
+}
+
+struct Variant {
+  std::vector<int64_t> key;
+  std::vector<int> pe, po;  // canonical axis i = natural axis pe[i] / po[i]
+  int sgn;
+};
+
+Variant canonical(const NatBlock& b) {
+  const int ne = (int)b.ext.size(), no = (int)b.osz.size();
+  const int K = std::accumulate(b.osz.begin(), b.osz.end(), 1, std::multiplies<int>());
+  std::vector<int> pe(ne), po(no);
+  std::iota(pe.begin(), pe.end(), 0);
+  Variant best;
+  bool have = false;
+  do {
+    std::iota(po.begin(), po.end(), 0);
+    do {
+      for (int sgn : {1, -1}) {
+        std::vector<int> oszc(no);
+        for (int i = 0; i < no; i++) oszc[i] = b.osz[po[i]];
+        std::vector<const Row*> crow(b.rows.size());
+        // natural -> canonical
+        for (int a = 0; a < 2; a++)
+          for (int evf = 0; evf < (1 << ne); evf++)
+            for (int ovf = 0; ovf < K; ovf++) {
+              std::vector<int> ev(ne), ov(no);
+              for (int i = ne - 1, x = evf; i >= 0; i--, x >>= 1) ev[i] = x & 1;
+              for (int i = no - 1, x = ovf; i >= 0; i--) { ov[i] = x % b.osz[i]; x /= b.osz[i]; }
+              std::vector<int> evc(ne), ovc(no);
+              for (int i = 0; i < ne; i++) evc[i] = ev[pe[i]];
+              for (int i = 0; i < no; i++) ovc[i] = ov[po[i]];
+              int ci = (a * (1 << ne) + flat_ext(evc)) * K + flat_open(oszc, ovc);
+              crow[ci] = &b.rows[(a * (1 << ne) + evf) * K + ovf];
+            }
+        std::vector<int64_t> key;
+        key.push_back(ne);
+        key.push_back(no);
+        for (int v : oszc) key.push_back(v);
+        for (const Row* r : crow) {
+          key.push_back((int64_t)r->size());
+          for (auto& zw : *r) { key.push_back(zw.first); key.push_back(sgn * zw.second); }
+        }
+        if (!have || key < best.key) { best.key = key; best.pe = pe; best.po = po; best.sgn = sgn; have = true; }
+      }
+    } while (std::next_permutation(po.begin(), po.end()));
+  } while (std::next_permutation(pe.begin(), pe.end()));
+  return best;
+}
+
+struct UBlock {
+  int ne, no;
+  std::vector<int> osz;     // canonical open sizes
+  std::vector<Row> rows;    // canonical order
+  int fam_mask = 0;
+  int base = 0;
+};
+
+// Offset of a natural (a, ev, ov) entry of a block stored canonically.
+int canon_offset(const UBlock& u, const Variant& v, int a, const std::vector<int>& ev,
+                 const std::vector<int>& ov) {
+  const int K = std::accumulate(u.osz.begin(), u.osz.end(), 1, std::multiplies<int>());
+  std::vector<int> evc(u.ne), ovc(u.no);
+  for (int i = 0; i < u.ne; i++) evc[i] = ev[v.pe[i]];
+  for (int i = 0; i < u.no; i++) ovc[i] = ov[v.po[i]];
+  return u.base + (a * (1 << u.ne) + flat_ext(evc)) * K + flat_open(u.osz, ovc);
+}
+
+}  // namespace
+
+int channel_count() { return (int)channels_table().size(); }
+
+void channel_names(int id, const char* out[4]) {
+  const auto& c = channels_table()[id];
+  for (int i = 0; i < 4; i++) out[i] = kOps[c[i]].name;
+}
+
+bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
+  const auto& table = channels_table();
+  if (n <= 0) { *err = "empty channel list"; return false; }
+  for (int i = 0; i < n; i++) {
+    if (channels[i] < 0 || channels[i] >= (int)table.size()) { *err = "unknown channel id " + std::to_string(channels[i]); return false; }
+    for (int j = 0; j < i; j++)
+      if (channels[j] == channels[i]) { *err = "duplicate channel id " + std::to_string(channels[i]); return false; }
+  }
+  Plan P;
+  P.channels.assign(channels, channels + n);
+
+  std::map<std::vector<int64_t>, int> uniq;
+  std::vector<UBlock> ublocks;
+  struct Inst { int ch_pos; double coef; int uA, uB; Variant vA, vB; std::vector<int> extA, extB, osz; };
+  std::vector<Inst> insts;
+
+  for (int cp = 0; cp < n; cp++) {
+    const auto& ch = table[channels[cp]];
+    const Op* op[4] = {&kOps[ch[0]], &kOps[ch[1]], &kOps[ch[2]], &kOps[ch[3]]};
+    P.n_strange.push_back(op[0]->n_s + op[1]->n_s);
+    char sinkf[6], srcf[6];
+    for (int i = 0; i < 3; i++) {
+      sinkf[i] = op[0]->flav[i]; sinkf[3 + i] = op[1]->flav[i];
+      srcf[i] = op[2]->flav[i]; srcf[3 + i] = op[3]->flav[i];
+    }
+    for (int t3 = 0; t3 < op[2]->nterm; t3++)
+      for (int t4 = 0; t4 < op[3]->nterm; t4++) {
+        const Term src[2] = {op[2]->t[t3], op[3]->t[t4]};
+        const double c34 = src[0].coef * src[1].coef * op[2]->scale * op[3]->scale;
+        std::vector<int> seen;  // bitmask of S1 already classified
+        int perm[6] = {0, 1, 2, 3, 4, 5};
+        do {
+          bool ok = true;
+          for (int i = 0; i < 6 && ok; i++) ok = sinkf[i] == srcf[perm[i]];
+          if (!ok) continue;
+          int s1 = (1 << perm[0]) | (1 << perm[1]) | (1 << perm[2]);
+          if (std::find(seen.begin(), seen.end(), s1) != seen.end()) continue;
+          seen.push_back(s1);
+          const int parity = perm_parity(perm, 6);
+          // which block (0 = A at X+r, 1 = B at X) holds each source tensor
+          int att[2], minority[2];
+          for (int k = 0; k < 2; k++) {
+            int inA = 0;
+            for (int j = 3 * k; j < 3 * k + 3; j++) inA += (s1 >> j) & 1;
+            att[k] = inA >= 2 ? 0 : 1;
+            minority[k] = -1;
+            for (int j = 3 * k; j < 3 * k + 3; j++) {
+              bool in_att = (((s1 >> j) & 1) != 0) == (att[k] == 0);
+              if (!in_att) minority[k] = j;
+            }
+          }
+          std::vector<int> opens, osz;
+          for (int k = 0; k < 2; k++)
+            if (minority[k] >= 0) {
+              opens.push_back(k);
+              osz.push_back(minority[k] - 3 * k == src[k].dk ? 3 : 12);
+            }
+          const int K = std::accumulate(osz.begin(), osz.end(), 1, std::multiplies<int>());
+          NatBlock nb[2];
+          for (int blk = 0; blk < 2; blk++) {
+            NatBlock& b = nb[blk];
+            b.osz = osz;
+            for (int k = 0; k < 2; k++) {
+              int dpos = 3 * k + src[k].dk;
+              int carrier = (minority[k] != dpos) ? att[k] : 1 - att[k];
+              if (carrier == blk) b.ext.push_back(k);
+            }
+            const Op* sink = op[blk];
+            int pos[3];
+            for (int s = 0; s < 3; s++) pos[s] = perm[3 * blk + s];
+            // same-flavour permutations of the sink slots (with parity)
+            std::vector<std::array<int, 4>> pis;
+            int p3[3] = {0, 1, 2};
+            do {
+              if (sink->flav[p3[0]] == sink->flav[0] && sink->flav[p3[1]] == sink->flav[1] &&
+                  sink->flav[p3[2]] == sink->flav[2])
+                pis.push_back({p3[0], p3[1], p3[2], perm_parity(p3, 3)});
+            } while (std::next_permutation(p3, p3 + 3));
+            std::vector<int> attk;
+            for (int k = 0; k < 2; k++)
+              if (att[k] == blk) attk.push_back(k);
+            const int ne = (int)b.ext.size();
+            b.rows.assign(2 * (1 << ne) * K, Row());
+            for (int a = 0; a < 2; a++)
+              for (int evf = 0; evf < (1 << ne); evf++)
+                for (int ovf = 0; ovf < K; ovf++) {
+                  int evk[2] = {-1, -1}, ovk[2] = {-1, -1};
+                  for (int i = ne - 1, x = evf; i >= 0; i--, x >>= 1) evk[b.ext[i]] = x & 1;
+                  for (int i = (int)opens.size() - 1, x = ovf; i >= 0; i--) { ovk[opens[i]] = x % osz[i]; x /= osz[i]; }
+                  std::map<int, int> acc;
+                  // enumerate entries of the attached tensors (at most two)
+                  std::vector<std::vector<SrcEntry>> lists;
+                  for (int k : attk) {
+                    bool dmin = minority[k] >= 0 && minority[k] - 3 * k == src[k].dk;
+                    auto all = source_entries(src[k], dmin ? 0 : evk[k]);
+                    std::vector<SrcEntry> keep;
+                    for (auto& e : all)
+                      if (minority[k] < 0 || e.eta[minority[k] - 3 * k] == ovk[k]) keep.push_back(e);
+                    lists.push_back(keep);
+                  }
+                  size_t n0 = lists.size() > 0 ? lists[0].size() : 1;
+                  size_t n1 = lists.size() > 1 ? lists[1].size() : 1;
+                  for (size_t i0 = 0; i0 < n0; i0++)
+                    for (size_t i1 = 0; i1 < n1; i1++) {
+                      int eta[6] = {-1, -1, -1, -1, -1, -1};
+                      int w = 1;
+                      for (size_t li = 0; li < lists.size(); li++) {
+                        const SrcEntry& e = lists[li][li == 0 ? i0 : i1];
+                        int k = attk[li];
+                        for (int m = 0; m < 3; m++) eta[3 * k + m] = e.eta[m];
+                        w *= e.val;
+                      }
+                      for (int k = 0; k < 2; k++)
+                        if (att[k] != blk && minority[k] >= 0) {
+                          int m = minority[k];
+                          eta[m] = (m - 3 * k == src[k].dk) ? 3 * evk[k] + ovk[k] : ovk[k];
+                        }
+                      for (auto& pi : pis) {
+                        int ein[3];
+                        for (int s = 0; s < 3; s++) ein[s] = eta[pos[pi[s]]];
+                        for (int t = 0; t < sink->nterm; t++) {
+                          int sl[3];
+                          int fam = family_of(sink->flav, sink->t[t], sl);
+                          int z = zindex(fam, a, ein[sl[0]], ein[sl[1]], ein[sl[2]]);
+                          acc[z] += w * pi[3] * sink->t[t].coef;
+                        }
+                      }
+                    }
+                  Row& r = b.rows[(a * (1 << ne) + evf) * K + ovf];
+                  for (auto& kv : acc)
+                    if (kv.second != 0) r.push_back(kv);
+                }
+          }
+          Inst in;
+          in.ch_pos = cp;
+          in.coef = parity * c34 * op[0]->scale * op[1]->scale;
+          in.extA = nb[0].ext; in.extB = nb[1].ext; in.osz = osz;
+          for (int blk = 0; blk < 2; blk++) {
+            Variant v = canonical(nb[blk]);
+            auto it = uniq.find(v.key);
+            int id;
+            if (it == uniq.end()) {
+              id = (int)ublocks.size();
+              uniq.emplace(v.key, id);
+              UBlock u;
+              u.ne = (int)nb[blk].ext.size();
+              u.no = (int)osz.size();
+              u.osz.resize(u.no);
+              for (int i = 0; i < u.no; i++) u.osz[i] = osz[v.po[i]];
+              const int Kc = K;
+              u.rows.assign(nb[blk].rows.size(), Row());
+              for (int a = 0; a < 2; a++)
+                for (int evf = 0; evf < (1 << u.ne); evf++)
+                  for (int ovf = 0; ovf < Kc; ovf++) {
+                    std::vector<int> ev(u.ne), ov(u.no);
+                    for (int i = u.ne - 1, x = evf; i >= 0; i--, x >>= 1) ev[i] = x & 1;
+                    for (int i = u.no - 1, x = ovf; i >= 0; i--) { ov[i] = x % osz[i]; x /= osz[i]; }
+                    int ci = canon_offset(u, v, a, ev, ov);  // base 0 at this point
+                    Row r = nb[blk].rows[(a * (1 << u.ne) + evf) * Kc + ovf];
+                    for (auto& zw : r) { zw.second *= v.sgn; u.fam_mask |= 1 << (zw.first / kFamEntries); }
+                    u.rows[ci] = r;
+                  }
+              ublocks.push_back(u);
+            } else {
+              id = it->second;
+            }
+            if (blk == 0) { in.uA = id; in.vA = v; } else { in.uB = id; in.vB = v; }
+          }
+          insts.push_back(in);
+          DiagramInfo di{cp, t3, t4, K, parity, in.coef};
+          P.diagrams.push_back(di);
+        } while (std::next_permutation(perm, perm + 6));
+      }
+  }
+
+  // --- group blocks by the families they read, assign row offsets ---------
+  // group order: lll | lss | lsl | lsl+lls (the last two share slot 0)
+  const std::vector<std::array<int, 2>> gfam = {{F_LLL, -1}, {F_LSS, -1}, {F_LSL, -1}, {F_LSL, F_LLS}};
+  std::vector<std::vector<int>> members(gfam.size());
+  for (int u = 0; u < (int)ublocks.size(); u++) {
+    int m = ublocks[u].fam_mask, g = -1;
+    if (m == (1 << F_LLL)) g = 0;
+    else if (m == (1 << F_LSS)) g = 1;
+    else if (m == (1 << F_LSL)) g = 2;
+    else if ((m & ~((1 << F_LSL) | (1 << F_LLS))) == 0) g = 3;
+    if (g < 0) { *err = "internal: block reads an unexpected family set"; return false; }
+    members[g].push_back(u);
+  }
+  int row = 0;
+  P.row_ptr.push_back(0);
+  for (size_t g = 0; g < gfam.size(); g++) {
+    if (members[g].empty()) continue;
+    GroupInfo gi;
+    gi.first_row = row;
+    gi.fam[0] = gfam[g][0];
+    gi.fam[1] = gfam[g][1];
+    for (int u : members[g]) {
+      UBlock& ub = ublocks[u];
+      ub.base = row;
+      for (auto& r : ub.rows) {
+        for (auto& zw : r) {
+          int fam = zw.first / kFamEntries, local = zw.first % kFamEntries;
+          int slot = fam == gi.fam[0] ? 0 : 1;
+          if (fam != gi.fam[slot]) { *err = "internal: family slot"; return false; }
+          if (zw.second < -32768 || zw.second > 32767) { *err = "internal: weight range"; return false; }
+          P.entries.push_back((uint32_t)(slot * kFamEntries + local) |
+                              ((uint32_t)(uint16_t)(int16_t)zw.second << 16));
+        }
+        P.row_ptr.push_back((int)P.entries.size());
+        row++;
+      }
+    }
+    gi.n_rows = row - gi.first_row;
+    P.groups.push_back(gi);
+  }
+  P.n_out = row;
+  P.n_blocks = (int)ublocks.size();
+
+  // --- aligned pair products and their signed sums -------------------------
+  std::map<std::array<int, 8>, int> item_id;
+  std::vector<std::vector<std::pair<int, double>>> contrib(n * 16);
+  for (const Inst& in : insts) {
+    const UBlock& A = ublocks[in.uA];
+    const UBlock& B = ublocks[in.uB];
+    const int no = (int)in.osz.size();
+    const int n1 = no > 0 ? in.osz[0] : 1, n2 = no > 1 ? in.osz[1] : 1;
+    for (int s = 0; s < 16; s++) {
+      int a = s & 1, b = (s >> 1) & 1, e[2] = {(s >> 2) & 1, (s >> 3) & 1};
+      std::vector<int> evA, evB;
+      for (int k : in.extA) evA.push_back(e[k]);
+      for (int k : in.extB) evB.push_back(e[k]);
+      auto ovec = [&](int i, int j) {
+        std::vector<int> ov;
+        if (no > 0) ov.push_back(i);
+        if (no > 1) ov.push_back(j);
+        return ov;
+      };
+      int oA = canon_offset(A, in.vA, a, evA, ovec(0, 0));
+      int oB = canon_offset(B, in.vB, b, evB, ovec(0, 0));
+      int sA1 = n1 > 1 ? canon_offset(A, in.vA, a, evA, ovec(1, 0)) - oA : 0;
+      int sA2 = n2 > 1 ? canon_offset(A, in.vA, a, evA, ovec(0, 1)) - oA : 0;
+      int sB1 = n1 > 1 ? canon_offset(B, in.vB, b, evB, ovec(1, 0)) - oB : 0;
+      int sB2 = n2 > 1 ? canon_offset(B, in.vB, b, evB, ovec(0, 1)) - oB : 0;
+      std::array<int, 8> key = {oA, oB, n1, n2, sA1, sA2, sB1, sB2};
+      auto it = item_id.find(key);
+      int id;
+      if (it == item_id.end()) {
+        id = (int)P.items.size();
+        item_id.emplace(key, id);
+        P.items.push_back(PairItem{oA, oB, n1, n2, sA1, sA2, sB1, sB2});
+      } else {
+        id = it->second;
+      }
+      contrib[in.ch_pos * 16 + s].push_back({id, in.coef * in.vA.sgn * in.vB.sgn});
+    }
+  }
+  // order items by decreasing work (round-robin over threads stays balanced)
+  std::vector<int> order(P.items.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return P.items[x].n1 * P.items[x].n2 > P.items[y].n1 * P.items[y].n2;
+  });
+  std::vector<int> rank(order.size());
+  std::vector<PairItem> sorted;
+  for (size_t i = 0; i < order.size(); i++) { rank[order[i]] = (int)i; sorted.push_back(P.items[order[i]]); }
+  P.items = sorted;
+  P.pair_macs = 0;
+  for (auto& it : P.items) P.pair_macs += (long long)it.n1 * it.n2;
+  P.contrib_ptr.push_back(0);
+  for (auto& c : contrib) {
+    // merge repeated items of one output
+    std::map<int, double> m;
+    for (auto& p : c) m[rank[p.first]] += p.second;
+    for (auto& kv : m)
+      if (kv.second != 0.0) { P.contrib_item.push_back(kv.first); P.contrib_coef.push_back(kv.second); }
+    P.contrib_ptr.push_back((int)P.contrib_item.size());
+  }
+  // bounds of every device table index (checked once on the host so that no
+  // kernel can read outside a block row or the product buffer)
+  for (const PairItem& it : P.items) {
+    auto last = [](int off, int n1, int n2, int s1, int s2) { return off + (n1 - 1) * s1 + (n2 - 1) * s2; };
+    if (it.offA < 0 || it.offB < 0 || it.n1 < 1 || it.n2 < 1 || it.n1 > 0xffff || it.n2 > 0xffff ||
+        it.sA1 < 0 || it.sA2 < 0 || it.sB1 < 0 || it.sB2 < 0 || it.sA1 > 0xffff || it.sA2 > 0x7fff ||
+        it.sB1 > 0xffff || it.sB2 > 0x7fff ||
+        last(it.offA, it.n1, it.n2, it.sA1, it.sA2) >= P.n_out || last(it.offB, it.n1, it.n2, it.sB1, it.sB2) >= P.n_out) {
+      *err = "internal: pair item out of range";
+      return false;
+    }
+  }
+  for (int id : P.contrib_item)
+    if (id < 0 || id >= (int)P.items.size()) { *err = "internal: contribution index"; return false; }
+  for (uint32_t e : P.entries)
+    if ((e & 0xffffu) >= 2u * kFamEntries) { *err = "internal: tensor index"; return false; }
+  if ((int)P.row_ptr.size() != P.n_out + 1) { *err = "internal: row table"; return false; }
+  *plan = std::move(P);
+  return true;
+}
+
+}  // namespace bbc

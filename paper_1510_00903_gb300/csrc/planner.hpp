@@ -1,0 +1,67 @@
+// planner.hpp -- host-side contraction planner of the effective block algorithm.
+//
+// Turns a list of baryon-baryon channels into (a) the aggregated baryon
+// blocks, each a sparse linear functional of per-site sink tensors, and
+// (b) the q-space contraction as block-pair products and signed sums into
+// channels (Nemura, arXiv:1510.00903, Sec. 3 diagrams (i)-(vi) and Eq.
+// LN.pLLp.FFT; Sec. 4 for all channels; Appendix A for block sharing).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace bbc {
+
+// Sink-tensor families: the diquark (Gamma1 = C gamma5) pair and the third
+// (delta) quark of a baryon term, by numeric flavour (l = u = d, s).
+//   F[a][e0][e1][e2] = sum eps(c0,c1,c2) Cg5(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1] S_f2[(a,c2),e2]
+enum Family { F_LLL = 0, F_LLS = 1, F_LSL = 2, F_LSS = 3, N_FAMILY = 4 };
+constexpr int kFamEntries = 2 * 1728;  // sink spin a in {0,1} (upper) x 12^3
+
+struct GroupInfo {
+  int first_row, n_rows;  // block-output rows of this group
+  int fam[2];             // families held in the two tensor slots (-1 = unused)
+};
+
+struct PairItem {  // one product sum_{i<n1, j<n2} A[offA + i sA1 + j sA2] B[offB + i sB1 + j sB2]
+  int offA, offB;
+  int n1, n2, sA1, sA2, sB1, sB2;
+};
+
+struct DiagramInfo {
+  int ch_pos, term3, term4;  // channel position, source operator terms
+  int K;                     // open-index iterations
+  int parity;                // parity of the Wick permutation (+1 / -1)
+  double coef;               // parity x operator coefficients
+};
+
+struct Plan {
+  std::vector<int> channels;
+  // block build: rows (block outputs per site) grouped by the families they read
+  int n_out = 0;
+  int n_blocks = 0;
+  std::vector<GroupInfo> groups;
+  std::vector<int> row_ptr;          // n_out + 1
+  std::vector<uint32_t> entries;     // low 16 bits: tensor index (slot*3456 + a*1728 + e0*144 + e1*12 + e2),
+                                     // high 16 bits: signed integer weight
+  // contraction: unique aligned pair products and their signed sums into channels
+  std::vector<PairItem> items;       // sorted by decreasing work
+  std::vector<int> contrib_ptr;      // n_channels*16 + 1
+  std::vector<int> contrib_item;
+  std::vector<double> contrib_coef;
+  long long pair_macs = 0;           // sum over items of n1*n2
+  // normalisation data per channel position
+  std::vector<int> n_strange;        // strange quarks of the sink pair (light = 6 - n_strange)
+  // statistics for the paper's tables
+  std::vector<DiagramInfo> diagrams;
+};
+
+// Number of supported channel ids (52 printed + 4 omitted).
+int channel_count();
+// Names of the four baryons of a channel (B1, B2 | B3, B4).
+void channel_names(int id, const char* out[4]);
+// Build the plan; returns false and sets *err on a bad channel list.
+bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
+
+}  // namespace bbc

@@ -14,3 +14,11 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+def pytest_sessionstart(session):
+    # build the CUDA library (sm_103a) and the oracle before collection
+    from paper_1510_00903_gb300 import build as _b
+    _b.build()
+    import oracle.oracle as _o
+    _o.build()

@@ -1,0 +1,69 @@
+"""The C-ABI library loads, exports every entry point of include/bbc.h and
+rejects bad arguments with the documented status codes (CPU only: no call
+here touches a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1510_00903_gb300 import bbc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(bbc_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol():
+    lib = ctypes.CDLL(bbc.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+        assert hasattr(bbc, n), n  # the binding keeps the C names
+
+
+@pytest.mark.parametrize("L,T,t0,ch,prec", [
+    (5, 8, 0, [0], 0), (16, 0, 0, [0], 0), (16, 8, 8, [0], 0),
+    (16, 8, 0, [56], 0), (16, 8, 0, [-1], 0), (16, 8, 0, [3, 3], 0), (16, 8, 0, [0], 7)])
+def test_create_rejects_bad_arguments(L, T, t0, ch, prec):
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_create(L, T, t0, 0.3, 0.4, prec, ch)
+    assert e.value.status == bbc.BBC_EINVAL
+    assert bbc.bbc_last_error(None)
+
+
+def test_workspace_and_state_errors():
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
+    try:
+        one, two = bbc.bbc_workspace_size(c, 1), bbc.bbc_workspace_size(c, 2)
+        assert two > one > 0
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_build_blocks(c, 1)
+        assert e.value.status == bbc.BBC_ESTATE
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_set_workspace(c, 256, one - 1, 1)
+        assert e.value.status == bbc.BBC_ENOMEM
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_set_workspace(c, 255, one, 1)
+        assert e.value.status == bbc.BBC_EINVAL
+    finally:
+        bbc.bbc_destroy(c)
+
+
+def test_mixed_workspace_is_smaller():
+    a = bbc.bbc_create(16, 4, 0, 0.3, 0.4, bbc.BBC_FP64, list(range(52)))
+    b = bbc.bbc_create(16, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, list(range(52)))
+    try:
+        assert bbc.bbc_workspace_size(b, 1) < bbc.bbc_workspace_size(a, 1)
+    finally:
+        bbc.bbc_destroy(a)
+        bbc.bbc_destroy(b)
