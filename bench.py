@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--single-slice", choices=["fp64", "mixed"], default=None,
+                    help="run one time slice of the workload once and exit (small case for profilers)")
     return ap.parse_args()
 
 
@@ -173,6 +175,16 @@ def main():
 
     L, T = L_BENCH, T_BENCH
     V = L ** 3
+    if args.single_slice:
+        t = T // 2
+        F1 = synth.flavour_set(L, T, 0, M_UD, M_S, seed=1000, times=[t])
+        prec = bbc.BBC_FP64 if args.single_slice == "fp64" else bbc.BBC_MIXED_FP32
+        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
+        o = cor.run(torch.from_numpy(F1["u"]).to(dev), torch.from_numpy(F1["s"]).to(dev), [t])
+        torch.cuda.synchronize(dev)
+        print("single slice done", float(o.abs().max()))
+        cor.close()
+        return
     F = synth.flavour_set(L, T, 0, M_UD, M_S, seed=1000 + rank, source=rank)
     Sl_h = torch.from_numpy(F["u"]).pin_memory()
     Ss_h = torch.from_numpy(F["s"]).pin_memory()

@@ -168,7 +168,10 @@ class Correlators:
                  stream=None):
         import torch
         self.torch = torch
-        self.device = torch.device(device or "cuda")
+        dev = torch.device(device or "cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.L, self.T, self.t0, self.V = L, T, t0, L ** 3
         self.channels = list(channels)
