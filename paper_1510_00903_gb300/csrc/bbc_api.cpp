@@ -30,10 +30,16 @@ struct bbc_ctx {
   int slots = 0;
   int* d_row_ptr = nullptr;
   uint32_t* d_entries = nullptr;
-  bbc::DevPairItem* d_items = nullptr;
+  bbc::DevTask* d_tasks = nullptr;
+  int* d_sched_ptr = nullptr;
+  int2* d_units = nullptr;
   int* d_cptr = nullptr;
   int* d_citem = nullptr;
   double* d_ccoef = nullptr;
+  int* d_qlist = nullptr;
+  int n_q = 0;                           // pairs {q, -q}
+  std::vector<int> sched_ptr;            // contraction schedule (threads + 1)
+  std::vector<bbc::Unit> units;
   char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
   char* d_prop = nullptr;                // [slots][2][V*144] compute precision
   unsigned long long* d_amax = nullptr;  // [slots][2]
@@ -62,7 +68,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
-  size_t row_ptr, entries, items, cptr, citem, ccoef, tables_end;
+  size_t row_ptr, entries, tasks, sched_ptr, units, cptr, citem, ccoef, qlist, tables_end;
   size_t stage, prop, amax, kexp, blk, total;
 };
 
@@ -72,10 +78,13 @@ Layout layout(const bbc_ctx* c, int slots) {
   size_t o = 0;
   L.row_ptr = o; o = align256(o + sizeof(int) * p.row_ptr.size());
   L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
-  L.items = o; o = align256(o + sizeof(bbc::DevPairItem) * p.items.size());
-  L.cptr = o; o = align256(o + sizeof(int) * p.contrib_ptr.size());
-  L.citem = o; o = align256(o + sizeof(int) * p.contrib_item.size());
-  L.ccoef = o; o = align256(o + sizeof(double) * p.contrib_coef.size());
+  L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
+  L.sched_ptr = o; o = align256(o + sizeof(int) * c->sched_ptr.size());
+  L.units = o; o = align256(o + sizeof(int2) * c->units.size());
+  L.cptr = o; o = align256(o + sizeof(int) * p.tcontrib_ptr.size());
+  L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
+  L.ccoef = o; o = align256(o + sizeof(double) * p.tcontrib_coef.size());
+  L.qlist = o; o = align256(o + sizeof(int) * (size_t)c->V);
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -171,6 +180,8 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     delete c;
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
+  // contraction schedule for the thread count of this precision
+  bbc::make_schedule(c->plan, bbc::contract_threads(prec == BBC_FP64), 36, &c->sched_ptr, &c->units);
   *ctx = c;
   return BBC_OK;
 }
@@ -198,33 +209,53 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->slots = slices;
   c->d_row_ptr = (int*)(w + L.row_ptr);
   c->d_entries = (uint32_t*)(w + L.entries);
-  c->d_items = (bbc::DevPairItem*)(w + L.items);
+  c->d_tasks = (bbc::DevTask*)(w + L.tasks);
+  c->d_sched_ptr = (int*)(w + L.sched_ptr);
+  c->d_units = (int2*)(w + L.units);
   c->d_cptr = (int*)(w + L.cptr);
   c->d_citem = (int*)(w + L.citem);
   c->d_ccoef = (double*)(w + L.ccoef);
+  c->d_qlist = (int*)(w + L.qlist);
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
   c->d_amax = (unsigned long long*)(w + L.amax);
   c->d_kexp = (int*)(w + L.kexp);
   c->d_blk = w + L.blk;
   const bbc::Plan& p = c->plan;
-  std::vector<bbc::DevPairItem> items(p.items.size());
-  for (size_t i = 0; i < p.items.size(); i++) {
-    const bbc::PairItem& s = p.items[i];
-    items[i].offA = s.offA;
-    items[i].offB = s.offB;
-    items[i].n12 = s.n1 | (s.n2 << 16);
-    items[i].sA = s.sA1 | (s.sA2 << 16);
-    items[i].sB = s.sB1 | (s.sB2 << 16);
-    items[i].pad = 0;
+  std::vector<bbc::DevTask> tasks(p.tasks.size());
+  for (size_t i = 0; i < p.tasks.size(); i++) {
+    const bbc::PairTask& t = p.tasks[i];
+    bbc::DevTask& d = tasks[i];
+    for (int r = 0; r < 8; r++) {
+      d.offA[r] = r < t.nA ? t.offA[r] : 0;
+      d.offB[r] = r < t.nB ? t.offB[r] : 0;
+    }
+    d.nAnB = t.nA | (t.nB << 8);
+    d.n2 = t.n2;
+    d.sA = t.sA1 | (t.sA2 << 16);
+    d.sB = t.sB1 | (t.sB2 << 16);
   }
+  std::vector<int2> units(c->units.size());
+  for (size_t i = 0; i < c->units.size(); i++) units[i] = make_int2(c->units[i].task, c->units[i].k0 | (c->units[i].k1 << 16));
+  // one q of every pair {q, -q}
+  std::vector<int> qlist;
+  const int Ls = c->lat.L;
+  for (int q = 0; q < c->V; q++) {
+    int qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
+    int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
+    if (q <= nq) qlist.push_back(q);
+  }
+  c->n_q = (int)qlist.size();
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
-      {c->d_items, items.data(), sizeof(bbc::DevPairItem) * items.size()},
-      {c->d_cptr, p.contrib_ptr.data(), sizeof(int) * p.contrib_ptr.size()},
-      {c->d_citem, p.contrib_item.data(), sizeof(int) * p.contrib_item.size()},
-      {c->d_ccoef, p.contrib_coef.data(), sizeof(double) * p.contrib_coef.size()},
+      {c->d_tasks, tasks.data(), sizeof(bbc::DevTask) * tasks.size()},
+      {c->d_sched_ptr, c->sched_ptr.data(), sizeof(int) * c->sched_ptr.size()},
+      {c->d_units, units.data(), sizeof(int2) * units.size()},
+      {c->d_cptr, p.tcontrib_ptr.data(), sizeof(int) * p.tcontrib_ptr.size()},
+      {c->d_citem, p.tcontrib_item.data(), sizeof(int) * p.tcontrib_item.size()},
+      {c->d_ccoef, p.tcontrib_coef.data(), sizeof(double) * p.tcontrib_coef.size()},
+      {c->d_qlist, qlist.data(), sizeof(int) * qlist.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -319,8 +350,9 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_CONTRACT);
-    e = bbc::launch_contract(blk, c->lat.L, p.n_out, c->d_items, (int)p.items.size(), c->d_cptr, c->d_citem,
-                             c->d_ccoef, n_ch, out_dev, fp64, c->stream);
+    e = bbc::launch_contract(blk, c->lat.L, p.n_out, c->d_qlist, c->n_q, c->d_tasks, (int)p.tasks.size(),
+                             c->d_sched_ptr, c->d_units, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, out_dev, fp64,
+                             c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "contract");
   }
   {

@@ -318,61 +318,131 @@ cudaError_t launch_fft_pass(void* data, int L, long long n_outer, int n_inner, i
 }
 
 // --------------------------------------------------------------- contract
-constexpr int kContractThreads = 256;
-
-template <typename R>
-__global__ void __launch_bounds__(kContractThreads)
-k_contract(const cpx<R>* __restrict__ blk, int L, int n_out, const DevPairItem* __restrict__ items,
-           int n_items, const int* __restrict__ cptr, const int* __restrict__ citem,
-           const double* __restrict__ ccoef, int n_outputs, cpx<double>* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<double>* sP = reinterpret_cast<cpx<double>*>(smem_raw);
-  const int q = blockIdx.x, V = L * L * L;
-  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
-  const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
-  const cpx<R>* A = blk + (size_t)q * n_out;
-  const cpx<R>* B = blk + (size_t)nq * n_out;
-  for (int it = threadIdx.x; it < n_items; it += kContractThreads) {
-    const DevPairItem pi = items[it];
-    const int n1 = pi.n12 & 0xffff, n2 = pi.n12 >> 16;
-    const int sA1 = pi.sA & 0xffff, sA2 = pi.sA >> 16, sB1 = pi.sB & 0xffff, sB2 = pi.sB >> 16;
-    cpx<R> acc(0, 0);
-    for (int i1 = 0; i1 < n1; i1++) {
-      const cpx<R>* a = A + pi.offA + i1 * sA1;
-      const cpx<R>* b = B + pi.offB + i1 * sB1;
-      for (int i2 = 0; i2 < n2; i2++) cmac(acc, a[i2 * sA2], b[i2 * sB2]);
-    }
-    sP[it] = cpx<double>(acc);
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < n_outputs; o += kContractThreads) {
-    cpx<double> s(0, 0);
-    const int c1 = cptr[o + 1];
-    for (int c = cptr[o]; c < c1; c++) {
-      const double w = ccoef[c];
-      const cpx<double> p = sP[citem[c]];
-      s.re = fma(w, p.re, s.re);
-      s.im = fma(w, p.im, s.im);
-    }
-    out[((size_t)(o >> 4) * V + q) * 16 + (o & 15)] = s;
+// One schedule unit: the open-index range [k0, k1) of one task, all nA x nB
+// spin products accumulated in registers (each loaded block value is reused
+// nB or nA times).
+template <typename R, int NA, int NB>
+__device__ __forceinline__ void run_unit(const cpx<R>* __restrict__ A, const cpx<R>* __restrict__ B,
+                                         const DevTask& t, int k0, int k1, cpx<R> (&acc)[16]) {
+  const int n2 = t.n2;
+  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
+  int i1 = k0 / n2, i2 = k0 - i1 * n2;
+  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
+  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
+  for (int k = k0; k < k1; k++) {
+    cpx<R> a[NA], b[NB];
+#pragma unroll
+    for (int r = 0; r < NA; r++) a[r] = A[t.offA[r] + oA];
+#pragma unroll
+    for (int r = 0; r < NB; r++) b[r] = B[t.offB[r] + oB];
+#pragma unroll
+    for (int ra = 0; ra < NA; ra++)
+#pragma unroll
+      for (int rb = 0; rb < NB; rb++) cmac(acc[ra * NB + rb], a[ra], b[rb]);
+    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
+    else { oA += sA2; oB += sB2; }
   }
 }
 
-cudaError_t launch_contract(const void* blk, int L, int n_out, const DevPairItem* items, int n_items,
-                            const int* cptr, const int* citem, const double* ccoef, int n_ch, void* out,
-                            bool fp64, cudaStream_t st) {
+template <typename R>
+__device__ __forceinline__ void smem_add(cpx<R>* p, cpx<R> v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+
+// PAIR = false: one CTA per q, block rows read from global memory (FP64).
+// PAIR = true: one CTA per pair {q, -q}; both block rows staged in shared
+// memory once and used for the products at q (A(q) B(-q)) and at -q (FP32).
+template <typename R, bool PAIR, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_contract(const cpx<R>* __restrict__ blk, int L, int n_out, const int* __restrict__ qlist,
+           const DevTask* __restrict__ tasks, int n_tasks, const int* __restrict__ sched_ptr,
+           const int2* __restrict__ units, const int* __restrict__ cptr, const int* __restrict__ citem,
+           const double* __restrict__ ccoef, int n_outputs, cpx<double>* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, V = L * L * L;
+  const int q = PAIR ? qlist[blockIdx.x] : blockIdx.x;
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
+  const int sides = (PAIR && nq != q) ? 2 : 1;
+  cpx<R>* rows = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* P = PAIR ? rows + 2 * n_out : rows;
+  const cpx<R>* gq = blk + (size_t)q * n_out;
+  const cpx<R>* gn = blk + (size_t)nq * n_out;
+  if (PAIR) {
+    // n_out * sizeof(cpx<R>) is a multiple of 16 bytes (n_out even)
+    const int n16 = n_out * (int)sizeof(cpx<R>) / 16;
+    const float4* s0 = reinterpret_cast<const float4*>(gq);
+    const float4* s1 = reinterpret_cast<const float4*>(gn);
+    float4* d = reinterpret_cast<float4*>(rows);
+    for (int i = tid; i < n16; i += THREADS) {
+      d[i] = __ldg(s0 + i);
+      if (sides == 2) d[n16 + i] = __ldg(s1 + i);
+    }
+  }
+  for (int side = 0; side < sides; side++) {
+    const cpx<R>* A = PAIR ? rows + side * n_out : gq;
+    const cpx<R>* B = PAIR ? rows + (sides == 2 ? 1 - side : 0) * n_out : gn;
+    const int qq = side ? nq : q;
+    for (int i = tid; i < n_tasks * 16; i += THREADS) P[i] = cpx<R>(0, 0);
+    __syncthreads();
+    const int u1 = sched_ptr[tid + 1];
+    for (int u = sched_ptr[tid]; u < u1; u++) {
+      const int2 un = units[u];
+      const DevTask t = tasks[un.x];
+      const int k0 = un.y & 0xffff, k1 = un.y >> 16;
+      cpx<R> acc[16];
+#pragma unroll
+      for (int i = 0; i < 16; i++) acc[i] = cpx<R>(0, 0);
+      const int nA = t.nAnB & 0xff;
+      if (nA == 4) run_unit<R, 4, 4>(A, B, t, k0, k1, acc);
+      else if (nA == 2) run_unit<R, 2, 8>(A, B, t, k0, k1, acc);
+      else run_unit<R, 8, 2>(A, B, t, k0, k1, acc);
+      cpx<R>* p = P + un.x * 16;
+#pragma unroll
+      for (int i = 0; i < 16; i++) smem_add(p + i, acc[i]);
+    }
+    __syncthreads();
+    // signed FP64 sum over Wick diagrams into channels and spins
+    for (int o = tid; o < n_outputs; o += THREADS) {
+      cpx<double> s(0, 0);
+      const int c1 = cptr[o + 1];
+      for (int c = cptr[o]; c < c1; c++) {
+        const double w = ccoef[c];
+        const cpx<R> p = P[citem[c]];
+        s.re = fma(w, (double)p.re, s.re);
+        s.im = fma(w, (double)p.im, s.im);
+      }
+      out[((size_t)(o >> 4) * V + qq) * 16 + (o & 15)] = s;
+    }
+    __syncthreads();
+  }
+}
+
+int contract_threads(bool fp64) { return fp64 ? 256 : 512; }
+
+size_t contract_smem(bool fp64, int n_out, int n_tasks) {
+  return fp64 ? (size_t)n_tasks * 16 * sizeof(cpx<double>)
+              : (size_t)(2 * n_out + n_tasks * 16) * sizeof(cpx<float>);
+}
+
+cudaError_t launch_contract(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+                            int n_tasks, const int* sched_ptr, const int2* units, const int* cptr, const int* citem,
+                            const double* ccoef, int n_ch, void* out, bool fp64, cudaStream_t st) {
   const int V = L * L * L;
-  size_t sm = (size_t)n_items * sizeof(cpx<double>);
+  const size_t sm = contract_smem(fp64, n_out, n_tasks);
   if (fp64) {
-    cudaError_t e = cudaFuncSetAttribute(k_contract<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto k = k_contract<double, false, 256>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_contract<double><<<V, kContractThreads, sm, st>>>((const cpx<double>*)blk, L, n_out, items, n_items, cptr,
-                                                        citem, ccoef, n_ch * 16, (cpx<double>*)out);
+    k<<<V, 256, sm, st>>>((const cpx<double>*)blk, L, n_out, qlist, tasks, n_tasks, sched_ptr, units, cptr, citem,
+                          ccoef, n_ch * 16, (cpx<double>*)out);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_contract<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto k = k_contract<float, true, 512>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_contract<float><<<V, kContractThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, items, n_items, cptr,
-                                                       citem, ccoef, n_ch * 16, (cpx<double>*)out);
+    k<<<n_q, 512, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, sched_ptr, units, cptr, citem,
+                            ccoef, n_ch * 16, (cpx<double>*)out);
   }
   return cudaGetLastError();
 }

@@ -9,13 +9,13 @@
 
 namespace bbc {
 
-// Device copy of one aligned block-pair product (planner PairItem).
-struct DevPairItem {
-  int offA, offB;
-  int n12;   // n1 | n2 << 16
+// Device copy of one block-pair task (planner PairTask).
+struct DevTask {
+  int offA[8], offB[8];
+  int nAnB;  // nA | nB << 8
+  int n2;
   int sA;    // sA1 | sA2 << 16
   int sB;    // sB1 | sB2 << 16
-  int pad;
 };
 
 struct DevGroups {  // block-build groups (rows that read the same tensor families)
@@ -50,9 +50,15 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* 
 cudaError_t launch_fft_pass(void* data, int L, long long n_outer, int n_inner, int axis,
                             bool inverse, bool fp64_store, bool fp64_compute, cudaStream_t st);
 // q-space contraction of one slice: blk [V][n_out] -> out [n_ch][V][16] (c128).
-cudaError_t launch_contract(const void* blk, int L, int n_out, const DevPairItem* items,
-                            int n_items, const int* cptr, const int* citem, const double* ccoef,
-                            int n_ch, void* out, bool fp64, cudaStream_t st);
+// qlist[n_q]: one q of every pair {q, -q} (FP32 path); tasks, per-thread
+// schedule (sched_ptr[threads+1], units {task, k0 | k1 << 16}) and the signed
+// sums (cptr, citem, ccoef) over task products P[task*16 + rA*nB + rB].
+int contract_threads(bool fp64);
+size_t contract_smem(bool fp64, int n_out, int n_tasks);
+cudaError_t launch_contract(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+                            int n_tasks, const int* sched_ptr, const int2* units, const int* cptr,
+                            const int* citem, const double* ccoef, int n_ch, void* out, bool fp64,
+                            cudaStream_t st);
 // out[ch][r][s] *= f[ch] * 2^(nl[ch] k_l + ns[ch] k_s).
 cudaError_t launch_normalise(void* out, int V, const NormParams& p, const int* kexp,
                              cudaStream_t st);

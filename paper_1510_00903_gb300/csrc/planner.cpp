@@ -492,6 +492,80 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
       contrib[in.ch_pos * 16 + s].push_back({id, in.coef * in.vA.sgn * in.vB.sgn});
     }
   }
+  // task products: one per aligned block pair, all 16 spin combinations
+  {
+    std::map<std::vector<int>, int> task_id;
+    std::vector<std::vector<std::pair<int, double>>> tc(n * 16);
+    for (const Inst& in : insts) {
+      const UBlock& A = ublocks[in.uA];
+      const UBlock& B = ublocks[in.uB];
+      const int no = (int)in.osz.size();
+      const int n1 = no > 0 ? in.osz[0] : 1, n2 = no > 1 ? in.osz[1] : 1;
+      const int neA = (int)in.extA.size(), neB = (int)in.extB.size();
+      PairTask t{};
+      t.nA = 2 << neA;
+      t.nB = 2 << neB;
+      t.n1 = n1;
+      t.n2 = n2;
+      auto ovec = [&](int i, int j) {
+        std::vector<int> ov;
+        if (no > 0) ov.push_back(i);
+        if (no > 1) ov.push_back(j);
+        return ov;
+      };
+      auto evbits = [](int x, int ne) {
+        std::vector<int> ev(ne);
+        for (int i = ne - 1; i >= 0; i--, x >>= 1) ev[i] = x & 1;
+        return ev;
+      };
+      for (int rA = 0; rA < t.nA; rA++) {
+        int a = rA >> neA;
+        auto ev = evbits(rA & ((1 << neA) - 1), neA);
+        t.offA[rA] = canon_offset(A, in.vA, a, ev, ovec(0, 0));
+        if (rA == 0) {
+          t.sA1 = n1 > 1 ? canon_offset(A, in.vA, a, ev, ovec(1, 0)) - t.offA[0] : 0;
+          t.sA2 = n2 > 1 ? canon_offset(A, in.vA, a, ev, ovec(0, 1)) - t.offA[0] : 0;
+        }
+      }
+      for (int rB = 0; rB < t.nB; rB++) {
+        int b = rB >> neB;
+        auto ev = evbits(rB & ((1 << neB) - 1), neB);
+        t.offB[rB] = canon_offset(B, in.vB, b, ev, ovec(0, 0));
+        if (rB == 0) {
+          t.sB1 = n1 > 1 ? canon_offset(B, in.vB, b, ev, ovec(1, 0)) - t.offB[0] : 0;
+          t.sB2 = n2 > 1 ? canon_offset(B, in.vB, b, ev, ovec(0, 1)) - t.offB[0] : 0;
+        }
+      }
+      std::vector<int> key = {t.nA, t.nB, t.n1, t.n2, t.sA1, t.sA2, t.sB1, t.sB2};
+      for (int r = 0; r < t.nA; r++) key.push_back(t.offA[r]);
+      for (int r = 0; r < t.nB; r++) key.push_back(t.offB[r]);
+      auto it = task_id.find(key);
+      int id;
+      if (it == task_id.end()) {
+        id = (int)P.tasks.size();
+        task_id.emplace(key, id);
+        P.tasks.push_back(t);
+      } else {
+        id = it->second;
+      }
+      for (int s = 0; s < 16; s++) {
+        int a = s & 1, b = (s >> 1) & 1, e[2] = {(s >> 2) & 1, (s >> 3) & 1};
+        int rA = a, rB = b;
+        for (int k : in.extA) rA = 2 * rA + e[k];
+        for (int k : in.extB) rB = 2 * rB + e[k];
+        tc[in.ch_pos * 16 + s].push_back({id * 16 + rA * t.nB + rB, in.coef * in.vA.sgn * in.vB.sgn});
+      }
+    }
+    P.tcontrib_ptr.push_back(0);
+    for (auto& c : tc) {
+      std::map<int, double> m;
+      for (auto& p : c) m[p.first] += p.second;
+      for (auto& kv : m)
+        if (kv.second != 0.0) { P.tcontrib_item.push_back(kv.first); P.tcontrib_coef.push_back(kv.second); }
+      P.tcontrib_ptr.push_back((int)P.tcontrib_item.size());
+    }
+  }
+
   // order items by decreasing work (round-robin over threads stays balanced)
   std::vector<int> order(P.items.size());
   std::iota(order.begin(), order.end(), 0);
@@ -527,11 +601,51 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   }
   for (int id : P.contrib_item)
     if (id < 0 || id >= (int)P.items.size()) { *err = "internal: contribution index"; return false; }
+  for (const PairTask& t : P.tasks) {
+    if (!((t.nA == 2 && t.nB == 8) || (t.nA == 4 && t.nB == 4) || (t.nA == 8 && t.nB == 2)) || t.n1 < 1 ||
+        t.n2 < 1 || t.n1 * t.n2 > 0xffff) {
+      *err = "internal: task shape";
+      return false;
+    }
+    for (int r = 0; r < t.nA; r++)
+      if (t.offA[r] < 0 || t.offA[r] + (t.n1 - 1) * t.sA1 + (t.n2 - 1) * t.sA2 >= P.n_out) { *err = "internal: task A range"; return false; }
+    for (int r = 0; r < t.nB; r++)
+      if (t.offB[r] < 0 || t.offB[r] + (t.n1 - 1) * t.sB1 + (t.n2 - 1) * t.sB2 >= P.n_out) { *err = "internal: task B range"; return false; }
+    if (t.sA1 < 0 || t.sA2 < 0 || t.sB1 < 0 || t.sB2 < 0) { *err = "internal: task stride"; return false; }
+  }
+  for (int id : P.tcontrib_item)
+    if (id < 0 || id >= 16 * (int)P.tasks.size()) { *err = "internal: task contribution index"; return false; }
   for (uint32_t e : P.entries)
     if ((e & 0xffffu) >= 2u * kFamEntries) { *err = "internal: tensor index"; return false; }
   if ((int)P.row_ptr.size() != P.n_out + 1) { *err = "internal: row table"; return false; }
   *plan = std::move(P);
   return true;
+}
+
+void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* thread_ptr,
+                   std::vector<Unit>* units) {
+  std::vector<Unit> all;
+  for (int t = 0; t < (int)plan.tasks.size(); t++) {
+    const int K = plan.tasks[t].n1 * plan.tasks[t].n2;
+    const int step = K > chunk ? chunk : K;
+    for (int k = 0; k < K; k += step) all.push_back(Unit{t, k, std::min(K, k + step)});
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Unit& a, const Unit& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
+  std::vector<long long> load(threads, 0);
+  std::vector<std::vector<Unit>> per(threads);
+  for (const Unit& u : all) {
+    int best = 0;
+    for (int i = 1; i < threads; i++)
+      if (load[i] < load[best]) best = i;
+    load[best] += (u.k1 - u.k0) + 2;  // +2: fixed cost of a unit (task load, flush)
+    per[best].push_back(u);
+  }
+  thread_ptr->assign(1, 0);
+  units->clear();
+  for (auto& v : per) {
+    for (auto& u : v) units->push_back(u);
+    thread_ptr->push_back((int)units->size());
+  }
 }
 
 }  // namespace bbc

@@ -29,6 +29,21 @@ struct PairItem {  // one product sum_{i<n1, j<n2} A[offA + i sA1 + j sA2] B[off
   int n1, n2, sA1, sA2, sB1, sB2;
 };
 
+// One aligned block pair at one q: P[rA][rB] = sum_k A[offA[rA] + k] B[offB[rB] + k]
+// over the flattened open index k = (i1, i2) (offsets i1*s1 + i2*s2); rA runs
+// over (sink spin a, external spins carried by A), rB likewise for B, and
+// nA * nB = 16 spin combinations.
+struct PairTask {
+  int nA, nB;            // (2,8), (4,4) or (8,2)
+  int offA[8], offB[8];  // row offsets in the block row of one site
+  int n1, n2, sA1, sA2, sB1, sB2;
+};
+
+// A schedule unit: flattened open-index range [k0, k1) of one task.
+struct Unit {
+  int task, k0, k1;
+};
+
 struct DiagramInfo {
   int ch_pos, term3, term4;  // channel position, source operator terms
   int K;                     // open-index iterations
@@ -46,7 +61,11 @@ struct Plan {
   std::vector<uint32_t> entries;     // low 16 bits: tensor index (slot*3456 + a*1728 + e0*144 + e1*12 + e2),
                                      // high 16 bits: signed integer weight
   // contraction: unique aligned pair products and their signed sums into channels
-  std::vector<PairItem> items;       // sorted by decreasing work
+  std::vector<PairTask> tasks;       // products of block pairs; P index = task*16 + rA*nB + rB
+  std::vector<int> tcontrib_ptr;     // n_channels*16 + 1, contributions over task products
+  std::vector<int> tcontrib_item;
+  std::vector<double> tcontrib_coef;
+  std::vector<PairItem> items;       // per-spin products (reference layout), sorted by decreasing work
   std::vector<int> contrib_ptr;      // n_channels*16 + 1
   std::vector<int> contrib_item;
   std::vector<double> contrib_coef;
@@ -63,5 +82,13 @@ int channel_count();
 void channel_names(int id, const char* out[4]);
 // Build the plan; returns false and sets *err on a bad channel list.
 bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
+
+// Balanced static schedule of the task products over `threads` threads:
+// tasks with more than `chunk` open-index iterations are split into chunks
+// of `chunk`; chunks go longest-first to the least loaded thread.
+// Output: thread_ptr[threads + 1] and units[] (thread t owns
+// units[thread_ptr[t] .. thread_ptr[t+1])).
+void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* thread_ptr,
+                   std::vector<Unit>* units);
 
 }  // namespace bbc
