@@ -30,6 +30,7 @@ struct bbc_ctx {
   int slots = 0;
   int* d_row_ptr = nullptr;
   uint32_t* d_entries = nullptr;
+  uint16_t* d_zneed = nullptr;
   bbc::DevTask* d_tasks = nullptr;
   int* d_sched_ptr = nullptr;
   int2* d_units = nullptr;
@@ -68,7 +69,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
-  size_t row_ptr, entries, tasks, sched_ptr, units, cptr, citem, ccoef, qlist, tables_end;
+  size_t row_ptr, entries, zneed, tasks, sched_ptr, units, cptr, citem, ccoef, qlist, tables_end;
   size_t stage, prop, amax, kexp, blk, total;
 };
 
@@ -78,6 +79,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   size_t o = 0;
   L.row_ptr = o; o = align256(o + sizeof(int) * p.row_ptr.size());
   L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
+  L.zneed = o; o = align256(o + sizeof(uint16_t) * p.zneed.size());
   L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
   L.sched_ptr = o; o = align256(o + sizeof(int) * c->sched_ptr.size());
   L.units = o; o = align256(o + sizeof(int2) * c->units.size());
@@ -146,6 +148,7 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
     g.fam0[i] = p.groups[i].fam[0];
     g.fam1[i] = p.groups[i].fam[1];
   }
+  for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   return g;
 }
 
@@ -209,6 +212,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->slots = slices;
   c->d_row_ptr = (int*)(w + L.row_ptr);
   c->d_entries = (uint32_t*)(w + L.entries);
+  c->d_zneed = (uint16_t*)(w + L.zneed);
   c->d_tasks = (bbc::DevTask*)(w + L.tasks);
   c->d_sched_ptr = (int*)(w + L.sched_ptr);
   c->d_units = (int2*)(w + L.units);
@@ -249,6 +253,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
+      {c->d_zneed, p.zneed.data(), sizeof(uint16_t) * p.zneed.size()},
       {c->d_tasks, tasks.data(), sizeof(bbc::DevTask) * tasks.size()},
       {c->d_sched_ptr, c->sched_ptr.data(), sizeof(int) * c->sched_ptr.size()},
       {c->d_units, units.data(), sizeof(int2) * units.size()},
@@ -322,8 +327,8 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_BUILD);
-    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_row_ptr, c->d_entries, groups_of(p), c->d_blk,
-                                p.n_out, fp64, c->stream);
+    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_row_ptr, c->d_entries, c->d_zneed, groups_of(p),
+                                c->d_blk, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
   {

@@ -164,12 +164,15 @@ constexpr int kBuildThreads = 256;
 template <typename R>
 __global__ void __launch_bounds__(kBuildThreads)
 k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ row_ptr,
-              const uint32_t* __restrict__ entries, DevGroups g, cpx<R>* __restrict__ blk, int n_out) {
+              const uint32_t* __restrict__ entries, const uint16_t* __restrict__ zneed, DevGroups g,
+              cpx<R>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][144]  light, strange
   cpx<R>* sD = sS + 288;                              // [2][432]  diquarks (l,l), (l,s)
   cpx<R>* sZ = sD + 864;                              // [2][3456] sink-tensor families
+  R* sW = reinterpret_cast<R*>(sZ + 2 * 3456);        // weights -16..15 (no int->float conversion per term)
   const int site = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
+  if (tid < 32) sW[tid] = (R)(tid - 16);
   const cpx<R>* P = prop + (size_t)slot * 2 * V * 144;
   for (int i = tid; i < 288; i += kBuildThreads) sS[i] = P[(size_t)(i / 144) * V * 144 + (size_t)site * 144 + i % 144];
   __syncthreads();
@@ -194,26 +197,22 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
     sD[i] = acc;
   }
   __syncthreads();
-  int loaded0 = -1, loaded1 = -1;
   for (int gi = 0; gi < g.n; gi++) {
-    const int fams[2] = {g.fam0[gi], g.fam1[gi]};
-    for (int sl = 0; sl < 2; sl++) {
-      const int fam = fams[sl];
-      if (fam < 0 || fam == (sl == 0 ? loaded0 : loaded1)) continue;
+    // the tensor entries this group reads (and the previous group did not leave)
+    const int z1 = g.zneed_first[gi + 1];
+    for (int j = g.zneed_first[gi] + tid; j < z1; j += kBuildThreads) {
+      const int zi = zneed[j], sl = zi / 3456, i = zi % 3456;
+      const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
       // F[a][e0][e1][e2] = sum_c2 D[e0][e1][c2] S_f2[(a,c2),e2]
       const int dq = (fam == 2 || fam == 3) ? 1 : 0;  // LSL, LSS read the (l,s) diquark
       const int f2 = (fam == 1 || fam == 3) ? 1 : 0;  // LLS, LSS: strange third quark
       const cpx<R>* D = sD + 432 * dq;
       const cpx<R>* S2 = sS + 144 * f2;
-      cpx<R>* Z = sZ + 3456 * sl;
-      for (int i = tid; i < 3456; i += kBuildThreads) {
-        const int a = i / 1728, r = i % 1728, e01 = r / 12, e2 = r % 12;
-        cpx<R> acc(0, 0);
+      const int a = i / 1728, r = i % 1728, e01 = r / 12, e2 = r % 12;
+      cpx<R> acc(0, 0);
 #pragma unroll
-        for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);
-        Z[i] = acc;
-      }
-      if (sl == 0) loaded0 = fam; else loaded1 = fam;
+      for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);
+      sZ[zi] = acc;
     }
     __syncthreads();
     const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
@@ -223,7 +222,7 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
       const int k1 = row_ptr[r + 1];
       for (int k = row_ptr[r]; k < k1; k++) {
         const uint32_t e = __ldg(entries + k);
-        const R w = (R)(int16_t)(e >> 16);
+        const R w = sW[((int)(int16_t)(e >> 16)) + 16];
         const cpx<R> z = sZ[e & 0xffffu];
         acc.re = fma(w, z.re, acc.re);
         acc.im = fma(w, z.im, acc.im);
@@ -235,21 +234,21 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
 }
 
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const DevGroups& g, void* blk, int n_out,
-                               bool fp64, cudaStream_t st) {
+                               const uint32_t* entries, const uint16_t* zneed, const DevGroups& g, void* blk,
+                               int n_out, bool fp64, cudaStream_t st) {
   dim3 grid(V, n_slots);
   if (fp64) {
-    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<double>);
+    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<double>) + 32 * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_block_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, g,
-                                                           (cpx<double>*)blk, n_out);
+    k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, zneed,
+                                                           g, (cpx<double>*)blk, n_out);
   } else {
-    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<float>);
+    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<float>) + 32 * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_block_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, g,
-                                                          (cpx<float>*)blk, n_out);
+    k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, zneed,
+                                                          g, (cpx<float>*)blk, n_out);
   }
   return cudaGetLastError();
 }
@@ -344,6 +343,52 @@ __device__ __forceinline__ void run_unit(const cpx<R>* __restrict__ A, const cpx
   }
 }
 
+// FP64 variant with three real products per complex product (Gauss):
+// s1 += ar br, s2 += ai bi, s3 += (ar + ai)(br + bi); then re = s1 - s2,
+// im = s3 - s1 - s2.  The sums ar + ai, br + bi are formed once per loaded
+// value and reused across the register tile: 3 instead of 4 FP64 FMAs per
+// complex multiply-add on the FP64-bound path.
+template <int NA, int NB>
+__device__ __forceinline__ void run_unit_gauss(const cpx<double>* __restrict__ A, const cpx<double>* __restrict__ B,
+                                               const DevTask& t, int k0, int k1, cpx<double> (&acc)[16]) {
+  const int n2 = t.n2;
+  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
+  int i1 = k0 / n2, i2 = k0 - i1 * n2;
+  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
+  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
+  double s1[NA * NB], s2[NA * NB], s3[NA * NB];
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) { s1[i] = 0.0; s2[i] = 0.0; s3[i] = 0.0; }
+  for (int k = k0; k < k1; k++) {
+    cpx<double> a[NA], b[NB];
+    double as[NA], bs[NB];
+#pragma unroll
+    for (int r = 0; r < NA; r++) { a[r] = A[t.offA[r] + oA]; as[r] = a[r].re + a[r].im; }
+#pragma unroll
+    for (int r = 0; r < NB; r++) { b[r] = B[t.offB[r] + oB]; bs[r] = b[r].re + b[r].im; }
+#pragma unroll
+    for (int ra = 0; ra < NA; ra++)
+#pragma unroll
+      for (int rb = 0; rb < NB; rb++) {
+        const int i = ra * NB + rb;
+        s1[i] = fma(a[ra].re, b[rb].re, s1[i]);
+        s2[i] = fma(a[ra].im, b[rb].im, s2[i]);
+        s3[i] = fma(as[ra], bs[rb], s3[i]);
+      }
+    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
+    else { oA += sA2; oB += sB2; }
+  }
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) acc[i] = cpx<double>(s1[i] - s2[i], s3[i] - s1[i] - s2[i]);
+}
+
+template <typename R, int NA, int NB>
+__device__ __forceinline__ void run_unit_any(const cpx<R>* A, const cpx<R>* B, const DevTask& t, int k0, int k1,
+                                             cpx<R> (&acc)[16]) {
+  if constexpr (sizeof(R) == 8) run_unit_gauss<NA, NB>(A, B, t, k0, k1, acc);
+  else run_unit<R, NA, NB>(A, B, t, k0, k1, acc);
+}
+
 template <typename R>
 __device__ __forceinline__ void smem_add(cpx<R>* p, cpx<R> v) {
   atomicAdd(&p->re, v.re);
@@ -395,9 +440,9 @@ k_contract(const cpx<R>* __restrict__ blk, int L, int n_out, const int* __restri
 #pragma unroll
       for (int i = 0; i < 16; i++) acc[i] = cpx<R>(0, 0);
       const int nA = t.nAnB & 0xff;
-      if (nA == 4) run_unit<R, 4, 4>(A, B, t, k0, k1, acc);
-      else if (nA == 2) run_unit<R, 2, 8>(A, B, t, k0, k1, acc);
-      else run_unit<R, 8, 2>(A, B, t, k0, k1, acc);
+      if (nA == 4) run_unit_any<R, 4, 4>(A, B, t, k0, k1, acc);
+      else if (nA == 2) run_unit_any<R, 2, 8>(A, B, t, k0, k1, acc);
+      else run_unit_any<R, 8, 2>(A, B, t, k0, k1, acc);
       cpx<R>* p = P + un.x * 16;
 #pragma unroll
       for (int i = 0; i < 16; i++) smem_add(p + i, acc[i]);

@@ -21,6 +21,7 @@ struct DevTask {
 struct DevGroups {  // block-build groups (rows that read the same tensor families)
   int n;
   int first[8], rows[8], fam0[8], fam1[8];
+  int zneed_first[9];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
 };
 
 constexpr int kMaxChannels = 64;
@@ -43,8 +44,8 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
                            cudaStream_t st);
 // Baryon blocks of every site: prop [slots][2][V][144], blk [slots][V][n_out].
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const DevGroups& g, void* blk,
-                               int n_out, bool fp64, cudaStream_t st);
+                               const uint32_t* entries, const uint16_t* zneed, const DevGroups& g,
+                               void* blk, int n_out, bool fp64, cudaStream_t st);
 // In-place 1-D DFTs of length L along `axis` of data[n_outer][V][n_inner];
 // storage and compute precision: fp64_store / fp64_compute; inverse = e^{+i}.
 cudaError_t launch_fft_pass(void* data, int L, long long n_outer, int n_inner, int axis,

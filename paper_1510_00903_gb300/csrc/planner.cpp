@@ -453,6 +453,31 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   }
   P.n_out = row;
   P.n_blocks = (int)ublocks.size();
+  // entries each group computes: those its rows read, minus those the previous
+  // group left in the same slot for the same family
+  {
+    std::vector<char> prev(2 * kFamEntries, 0);
+    int prev_fam[2] = {-1, -1};
+    P.zneed_first.push_back(0);
+    for (const GroupInfo& gi : P.groups) {
+      std::vector<char> need(2 * kFamEntries, 0);
+      for (int r = gi.first_row; r < gi.first_row + gi.n_rows; r++)
+        for (int k = P.row_ptr[r]; k < P.row_ptr[r + 1]; k++) need[P.entries[k] & 0xffffu] = 1;
+      for (int z = 0; z < 2 * kFamEntries; z++) {
+        const int sl = z / kFamEntries;
+        const bool valid = prev[z] && prev_fam[sl] == gi.fam[sl];
+        if (need[z] && !valid) P.zneed.push_back((uint16_t)z);
+      }
+      for (int sl = 0; sl < 2; sl++) {
+        if (gi.fam[sl] != prev_fam[sl])
+          for (int z = sl * kFamEntries; z < (sl + 1) * kFamEntries; z++) prev[z] = 0;
+        prev_fam[sl] = gi.fam[sl];
+      }
+      for (int z = 0; z < 2 * kFamEntries; z++)
+        if (need[z]) prev[z] = 1;
+      P.zneed_first.push_back((int)P.zneed.size());
+    }
+  }
 
   // --- aligned pair products and their signed sums -------------------------
   std::map<std::array<int, 8>, int> item_id;

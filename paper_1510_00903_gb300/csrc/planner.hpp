@@ -60,6 +60,8 @@ struct Plan {
   std::vector<int> row_ptr;          // n_out + 1
   std::vector<uint32_t> entries;     // low 16 bits: tensor index (slot*3456 + a*1728 + e0*144 + e1*12 + e2),
                                      // high 16 bits: signed integer weight
+  std::vector<uint16_t> zneed;       // tensor entries each group computes (group-major)
+  std::vector<int> zneed_first;      // groups + 1 offsets into zneed
   // contraction: unique aligned pair products and their signed sums into channels
   std::vector<PairTask> tasks;       // products of block pairs; P index = task*16 + rA*nB + rB
   std::vector<int> tcontrib_ptr;     // n_channels*16 + 1, contributions over task products
