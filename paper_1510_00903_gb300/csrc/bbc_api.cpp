@@ -32,20 +32,22 @@ struct bbc_ctx {
   uint32_t* d_entries = nullptr;
   uint16_t* d_zneed = nullptr;
   bbc::DevTask* d_tasks = nullptr;
-  int* d_sched_ptr = nullptr;
-  int2* d_units = nullptr;
+  int* d_group_ptr = nullptr;
+  int* d_group_task = nullptr;
   int* d_cptr = nullptr;
   int* d_citem = nullptr;
   double* d_ccoef = nullptr;
-  int* d_qlist = nullptr;
-  int n_q = 0;                           // pairs {q, -q}
-  std::vector<int> sched_ptr;            // contraction schedule (threads + 1)
-  std::vector<bbc::Unit> units;
+  std::vector<int> group_ptr;            // warp task groups of the pair products
+  std::vector<int> group_task;
   char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
   char* d_prop = nullptr;                // [slots][2][V*144] compute precision
   unsigned long long* d_amax = nullptr;  // [slots][2]
   int* d_kexp = nullptr;                 // [slots][2]
-  char* d_blk = nullptr;                 // [slots][V][n_out]
+  char* d_blk = nullptr;                 // [slots][V][n_out] site-major build output
+  char* d_blkf = nullptr;                // [slots][n_out][V] field-major, Fourier space
+  char* d_P = nullptr;                   // [n_tasks*16][V] pair products of one slice
+  char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators
+  double* d_scale = nullptr;             // [kMaxChannels]
   std::vector<int> slot_t;               // time slice of each slot (-1: none)
   std::vector<int> slot_loaded;          // bit 0: light, bit 1: strange
   std::vector<int> slot_built;
@@ -69,8 +71,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
-  size_t row_ptr, entries, zneed, tasks, sched_ptr, units, cptr, citem, ccoef, qlist, tables_end;
-  size_t stage, prop, amax, kexp, blk, total;
+  size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, tables_end;
+  size_t stage, prop, amax, kexp, blk, blkf, P, ct, scale, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -81,12 +83,11 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
   L.zneed = o; o = align256(o + sizeof(uint16_t) * p.zneed.size());
   L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
-  L.sched_ptr = o; o = align256(o + sizeof(int) * c->sched_ptr.size());
-  L.units = o; o = align256(o + sizeof(int2) * c->units.size());
+  L.group_ptr = o; o = align256(o + sizeof(int) * c->group_ptr.size());
+  L.group_task = o; o = align256(o + sizeof(int) * c->group_task.size());
   L.cptr = o; o = align256(o + sizeof(int) * p.tcontrib_ptr.size());
   L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
   L.ccoef = o; o = align256(o + sizeof(double) * p.tcontrib_coef.size());
-  L.qlist = o; o = align256(o + sizeof(int) * (size_t)c->V);
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -94,6 +95,10 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.amax = o; o = align256(o + (size_t)slots * 2 * sizeof(unsigned long long));
   L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
   L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
+  L.blkf = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
+  L.P = o; o = align256(o + (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec));
+  L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
+  L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
   L.total = o;
   return L;
 }
@@ -183,8 +188,8 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     delete c;
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
-  // contraction schedule for the thread count of this precision
-  bbc::make_schedule(c->plan, bbc::contract_threads(prec == BBC_FP64), 36, &c->sched_ptr, &c->units);
+  // warp task groups of the pair products: enough warps per 32 q to fill the GPU
+  bbc::make_task_groups(c->plan, 16, &c->group_ptr, &c->group_task);
   *ctx = c;
   return BBC_OK;
 }
@@ -214,17 +219,20 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_entries = (uint32_t*)(w + L.entries);
   c->d_zneed = (uint16_t*)(w + L.zneed);
   c->d_tasks = (bbc::DevTask*)(w + L.tasks);
-  c->d_sched_ptr = (int*)(w + L.sched_ptr);
-  c->d_units = (int2*)(w + L.units);
+  c->d_group_ptr = (int*)(w + L.group_ptr);
+  c->d_group_task = (int*)(w + L.group_task);
   c->d_cptr = (int*)(w + L.cptr);
   c->d_citem = (int*)(w + L.citem);
   c->d_ccoef = (double*)(w + L.ccoef);
-  c->d_qlist = (int*)(w + L.qlist);
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
   c->d_amax = (unsigned long long*)(w + L.amax);
   c->d_kexp = (int*)(w + L.kexp);
   c->d_blk = w + L.blk;
+  c->d_blkf = w + L.blkf;
+  c->d_P = w + L.P;
+  c->d_ct = w + L.ct;
+  c->d_scale = (double*)(w + L.scale);
   const bbc::Plan& p = c->plan;
   std::vector<bbc::DevTask> tasks(p.tasks.size());
   for (size_t i = 0; i < p.tasks.size(); i++) {
@@ -235,32 +243,21 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       d.offB[r] = r < t.nB ? t.offB[r] : 0;
     }
     d.nAnB = t.nA | (t.nB << 8);
+    d.n1 = t.n1;
     d.n2 = t.n2;
     d.sA = t.sA1 | (t.sA2 << 16);
     d.sB = t.sB1 | (t.sB2 << 16);
   }
-  std::vector<int2> units(c->units.size());
-  for (size_t i = 0; i < c->units.size(); i++) units[i] = make_int2(c->units[i].task, c->units[i].k0 | (c->units[i].k1 << 16));
-  // one q of every pair {q, -q}
-  std::vector<int> qlist;
-  const int Ls = c->lat.L;
-  for (int q = 0; q < c->V; q++) {
-    int qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
-    int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
-    if (q <= nq) qlist.push_back(q);
-  }
-  c->n_q = (int)qlist.size();
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
       {c->d_zneed, p.zneed.data(), sizeof(uint16_t) * p.zneed.size()},
       {c->d_tasks, tasks.data(), sizeof(bbc::DevTask) * tasks.size()},
-      {c->d_sched_ptr, c->sched_ptr.data(), sizeof(int) * c->sched_ptr.size()},
-      {c->d_units, units.data(), sizeof(int2) * units.size()},
+      {c->d_group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size()},
+      {c->d_group_task, c->group_task.data(), sizeof(int) * c->group_task.size()},
       {c->d_cptr, p.tcontrib_ptr.data(), sizeof(int) * p.tcontrib_ptr.size()},
       {c->d_citem, p.tcontrib_item.data(), sizeof(int) * p.tcontrib_item.size()},
       {c->d_ccoef, p.tcontrib_coef.data(), sizeof(double) * p.tcontrib_coef.size()},
-      {c->d_qlist, qlist.data(), sizeof(int) * qlist.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -333,10 +330,8 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   }
   {
     StageScope scope(c, BBC_STAGE_FFT_FWD);
-    for (int axis = 0; axis < 3; axis++) {
-      e = bbc::launch_fft_pass(c->d_blk, c->lat.L, n_slots, p.n_out, axis, false, fp64, fp64, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
-    }
+    e = bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
   }
   for (int s = 0; s < n_slots; s++) c->slot_built[s] = 1;
   return BBC_OK;
@@ -351,36 +346,36 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   const bool fp64 = c->prec == BBC_FP64;
   const bbc::Plan& p = c->plan;
   const int n_ch = (int)p.channels.size();
-  const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+  const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_CONTRACT);
-    e = bbc::launch_contract(blk, c->lat.L, p.n_out, c->d_qlist, c->n_q, c->d_tasks, (int)p.tasks.size(),
-                             c->d_sched_ptr, c->d_units, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, out_dev, fp64,
-                             c->stream);
+    e = bbc::launch_contract(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                             (int)c->group_ptr.size() - 1, c->d_P, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct,
+                             fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "contract");
   }
-  {
-    StageScope scope(c, BBC_STAGE_FFT_INV);
-    for (int axis = 0; axis < 3; axis++) {
-      e = bbc::launch_fft_pass(out_dev, c->lat.L, n_ch, 16, axis, true, true, fp64, c->stream);
-      if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
-    }
-  }
-  bbc::NormParams np{};
-  np.n_ch = n_ch;
+  bbc::ScaleParams sp{};
+  sp.n_ch = n_ch;
   const int t = c->slot_t[slot];
   const int d = ((t - c->lat.t0) % c->lat.T + c->lat.T) % c->lat.T;
   for (int i = 0; i < n_ch; i++) {
     const int ns = p.n_strange[i];
     const double mass = (6 - ns) * c->lat.m_ud + ns * c->lat.m_s;  // m_B1 + m_B2
-    np.f[i] = (1.0 / c->V) * (normalised ? std::exp(mass * d) : 1.0);
-    np.nl[i] = 6 - ns;
-    np.ns[i] = ns;
+    sp.f[i] = (1.0 / c->V) * (normalised ? std::exp(mass * d) : 1.0);
+    sp.nl[i] = 6 - ns;
+    sp.ns[i] = ns;
   }
-  StageScope scope(c, BBC_STAGE_NORMALISE);
-  e = bbc::launch_normalise(out_dev, c->V, np, c->d_kexp + slot * 2, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "normalise");
+  {
+    StageScope scope(c, BBC_STAGE_NORMALISE);
+    e = bbc::launch_scales(sp, c->d_kexp + slot * 2, c->d_scale, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "normalisation");
+  }
+  {
+    StageScope scope(c, BBC_STAGE_FFT_INV);
+    e = bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
+  }
   return BBC_OK;
 }
 
@@ -445,7 +440,7 @@ bbc_status bbc_launch_counts(const bbc_ctx* c, int* per_load, int* per_build, in
   if (!c) return BBC_EINVAL;
   if (per_load) *per_load = 2;          // absmax, convert
   if (per_build) *per_build = 1 + 3;    // block build, three FFT passes
-  if (per_contract) *per_contract = 1 + 3 + 1;  // contract, three inverse passes, normalise
+  if (per_contract) *per_contract = 2 + 1 + 3;  // pair products, Wick sums, scales, three inverse passes
   return BBC_OK;
 }
 

@@ -261,41 +261,91 @@ __device__ __forceinline__ void load_bitrev(cpx<R> (&v)[N], const cpx<S>* p, lon
   ((v[bitrev(Ks, N)] = cpx<R>(p[Ks * step])), ...);
 }
 
-template <typename S, typename R, int N, bool INV>
-__global__ void __launch_bounds__(256)
-k_fft_pass(cpx<S>* __restrict__ data, long long n_outer, int n_inner, int axis) {
-  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long lines = (long long)N * N;
-  if (gid >= n_outer * lines * n_inner) return;
-  const int i = (int)(gid % n_inner);
-  const long long rest = gid / n_inner;
-  const int line = (int)(rest % lines);
-  const long long o = rest / lines;
+__device__ __forceinline__ void line_base(int N, int axis, int line, int& base, int& stride) {
   const int a = line % N, b = line / N;
-  int base, stride;
-  if (axis == 0) { base = N * (a + N * b); stride = 1; }
-  else if (axis == 1) { base = a + N * N * b; stride = N; }
-  else { base = a + N * b; stride = N * N; }
-  const long long V = (long long)N * N * N;
-  cpx<S>* p = data + (o * V + base) * (long long)n_inner + i;
-  const long long step = (long long)stride * n_inner;
-  cpx<R> v[N];
-  load_bitrev<S, R, N>(v, p, step, std::make_integer_sequence<int, N>{});
-  fft_pow2<R, N, INV>(v);
-#pragma unroll
-  for (int k = 0; k < N; k++) p[k * step] = cpx<S>(v[k]);
+  if (axis == 0) { base = N * (a + N * b); stride = 1; }           // x varies, (y, z) = (a, b)
+  else if (axis == 1) { base = a + N * N * b; stride = N; }        // y varies, (x, z) = (a, b)
+  else { base = a + N * b; stride = N * N; }                       // z varies, (x, y) = (a, b)
 }
 
-template <typename S, typename R>
-static cudaError_t fft_dispatch(void* data, int L, long long n_outer, int n_inner, int axis, bool inv,
-                                cudaStream_t st) {
-  long long total = n_outer * (long long)L * L * n_inner;
+// Mode SITE2FIELD (x axis): in[o][site][n_inner] -> out[o][inner][site] (the
+// transpose to field-major storage rides on the first pass; lanes run over
+// the contiguous inner index).
+// Mode FIELD (any axis, in place on in = out): data[n_fields][V]; lanes run
+// over the line index, which is contiguous for the y and z passes.
+// Mode FIELD2OUT (z axis): in[ch][s][V] -> out[ch][r][16] times scale[ch]
+// (the last inverse pass writes the output layout and normalises it).
+enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2 };
+
+template <typename S, typename R, int N, bool INV, int MODE>
+__global__ void __launch_bounds__(256)
+k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer, int n_inner, int axis,
+      const double* __restrict__ scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lines = N * N;
+  const long long V = (long long)N * N * N;
+  int line, inner;
+  long long o;
+  if (MODE == FFT_SITE2FIELD) {
+    if (gid >= n_outer * lines * n_inner) return;
+    inner = (int)(gid % n_inner);
+    const long long rest = gid / n_inner;
+    line = (int)(rest % lines);
+    o = rest / lines;
+  } else if (MODE == FFT_FIELD) {
+    if (gid >= n_outer * lines) return;
+    line = (int)(gid % lines);
+    o = gid / lines;
+    inner = 0;
+  } else {  // FIELD2OUT: spin fastest so that each site's 16 spins are written together
+    if (gid >= n_outer * lines * 16) return;
+    inner = (int)(gid % 16);
+    const long long rest = gid / 16;
+    line = (int)(rest % lines);
+    o = rest / lines;  // channel
+  }
+  int base, stride;
+  line_base(N, axis, line, base, stride);
+  cpx<R> v[N];
+  if (MODE == FFT_SITE2FIELD) {
+    load_bitrev<S, R, N>(v, in + (o * V + base) * n_inner + inner, (long long)stride * n_inner,
+                         std::make_integer_sequence<int, N>{});
+  } else if (MODE == FFT_FIELD) {
+    load_bitrev<S, R, N>(v, in + o * V + base, stride, std::make_integer_sequence<int, N>{});
+  } else {
+    load_bitrev<S, R, N>(v, in + (o * 16 + inner) * V + base, stride, std::make_integer_sequence<int, N>{});
+  }
+  fft_pow2<R, N, INV>(v);
+  if (MODE == FFT_SITE2FIELD) {
+    cpx<S>* p = out + (o * n_inner + inner) * V + base;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+  } else if (MODE == FFT_FIELD) {
+    cpx<S>* p = out + o * V + base;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+  } else {
+    const R f = (R)scale[o];
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+      cpx<S> w(v[k].re * f, v[k].im * f);
+      out[(o * V + base + (long long)k * stride) * 16 + inner] = w;
+    }
+  }
+}
+
+template <typename S, typename R, int MODE>
+static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
+                                const double* scale, cudaStream_t st) {
+  long long per = (MODE == FFT_SITE2FIELD) ? n_inner : (MODE == FFT_FIELD ? 1 : 16);
+  long long total = n_outer * (long long)L * L * per;
   unsigned blocks = (unsigned)((total + 255) / 256);
-  cpx<S>* d = (cpx<S>*)data;
-#define BBC_FFT_CASE(NN)                                                              \
-  case NN:                                                                            \
-    if (inv) k_fft_pass<S, R, NN, true><<<blocks, 256, 0, st>>>(d, n_outer, n_inner, axis); \
-    else k_fft_pass<S, R, NN, false><<<blocks, 256, 0, st>>>(d, n_outer, n_inner, axis);    \
+  const cpx<S>* i = (const cpx<S>*)in;
+  cpx<S>* o = (cpx<S>*)out;
+#define BBC_FFT_CASE(NN)                                                                                   \
+  case NN:                                                                                                 \
+    if (inv) k_fft<S, R, NN, true, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);    \
+    else k_fft<S, R, NN, false, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);        \
     break;
   switch (L) {
     BBC_FFT_CASE(2)
@@ -309,206 +359,180 @@ static cudaError_t fft_dispatch(void* data, int L, long long n_outer, int n_inne
   return cudaGetLastError();
 }
 
-cudaError_t launch_fft_pass(void* data, int L, long long n_outer, int n_inner, int axis, bool inverse,
-                            bool fp64_store, bool fp64_compute, cudaStream_t st) {
-  if (fp64_store && fp64_compute) return fft_dispatch<double, double>(data, L, n_outer, n_inner, axis, inverse, st);
-  if (fp64_store) return fft_dispatch<double, float>(data, L, n_outer, n_inner, axis, inverse, st);
-  return fft_dispatch<float, float>(data, L, n_outer, n_inner, axis, inverse, st);
+cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
+                               cudaStream_t st) {
+  cudaError_t e;
+  if (fp64) {
+    e = fft_dispatch<double, double, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+    for (int axis = 1; axis < 3; axis++) {
+      e = fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
+                                                  nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    e = fft_dispatch<float, float, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+    for (int axis = 1; axis < 3; axis++) {
+      e = fft_dispatch<float, float, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
+                                                nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                               cudaStream_t st) {
+  cudaError_t e;
+  for (int axis = 0; axis < 2; axis++) {
+    e = fp64_compute ? fft_dispatch<double, double, FFT_FIELD>(ct, ct, L, (long long)n_ch * 16, 1, axis, true, nullptr, st)
+                     : fft_dispatch<double, float, FFT_FIELD>(ct, ct, L, (long long)n_ch * 16, 1, axis, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return fp64_compute ? fft_dispatch<double, double, FFT_FIELD2OUT>(ct, out, L, n_ch, 16, 2, true, scale, st)
+                      : fft_dispatch<double, float, FFT_FIELD2OUT>(ct, out, L, n_ch, 16, 2, true, scale, st);
 }
 
 // --------------------------------------------------------------- contract
-// One schedule unit: the open-index range [k0, k1) of one task, all nA x nB
-// spin products accumulated in registers (each loaded block value is reused
-// nB or nA times).
+// Pair products with one q per lane: a warp runs a fixed list of tasks for 32
+// consecutive q (uniform control flow, coalesced loads from the field-major
+// block storage), every nA x nB spin product of a task accumulated in
+// registers over its open index; P[task*16 + rA*nB + rB][q] is stored for the
+// signed sums.
 template <typename R, int NA, int NB>
-__device__ __forceinline__ void run_unit(const cpx<R>* __restrict__ A, const cpx<R>* __restrict__ B,
-                                         const DevTask& t, int k0, int k1, cpx<R> (&acc)[16]) {
-  const int n2 = t.n2;
+__device__ __forceinline__ void task_products(const cpx<R>* __restrict__ F, long long V, int q, int nq,
+                                              const DevTask& t, cpx<R>* __restrict__ P) {
+  const int n2 = t.n2, K = t.n1 * n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
-  int i1 = k0 / n2, i2 = k0 - i1 * n2;
-  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
-  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
-  for (int k = k0; k < k1; k++) {
-    cpx<R> a[NA], b[NB];
+  cpx<R> acc[NA * NB];
 #pragma unroll
-    for (int r = 0; r < NA; r++) a[r] = A[t.offA[r] + oA];
+  for (int i = 0; i < NA * NB; i++) acc[i] = cpx<R>(0, 0);
+  if constexpr (sizeof(R) == 8) {
+    // FP64: three real products per complex product (Gauss), sums formed once
+    // per loaded value and reused across the register tile
+    double s1[NA * NB], s2[NA * NB], s3[NA * NB];
 #pragma unroll
-    for (int r = 0; r < NB; r++) b[r] = B[t.offB[r] + oB];
+    for (int i = 0; i < NA * NB; i++) { s1[i] = 0.0; s2[i] = 0.0; s3[i] = 0.0; }
+    int i1 = 0, i2 = 0, oA = 0, oB = 0;
+    for (int k = 0; k < K; k++) {
+      cpx<R> a[NA], b[NB];
+      double as[NA], bs[NB];
 #pragma unroll
-    for (int ra = 0; ra < NA; ra++)
+      for (int r = 0; r < NA; r++) { a[r] = F[(long long)(t.offA[r] + oA) * V + q]; as[r] = a[r].re + a[r].im; }
 #pragma unroll
-      for (int rb = 0; rb < NB; rb++) cmac(acc[ra * NB + rb], a[ra], b[rb]);
-    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
-    else { oA += sA2; oB += sB2; }
-  }
-}
-
-// FP64 variant with three real products per complex product (Gauss):
-// s1 += ar br, s2 += ai bi, s3 += (ar + ai)(br + bi); then re = s1 - s2,
-// im = s3 - s1 - s2.  The sums ar + ai, br + bi are formed once per loaded
-// value and reused across the register tile: 3 instead of 4 FP64 FMAs per
-// complex multiply-add on the FP64-bound path.
-template <int NA, int NB>
-__device__ __forceinline__ void run_unit_gauss(const cpx<double>* __restrict__ A, const cpx<double>* __restrict__ B,
-                                               const DevTask& t, int k0, int k1, cpx<double> (&acc)[16]) {
-  const int n2 = t.n2;
-  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
-  int i1 = k0 / n2, i2 = k0 - i1 * n2;
-  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
-  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
-  double s1[NA * NB], s2[NA * NB], s3[NA * NB];
+      for (int r = 0; r < NB; r++) { b[r] = F[(long long)(t.offB[r] + oB) * V + nq]; bs[r] = b[r].re + b[r].im; }
 #pragma unroll
-  for (int i = 0; i < NA * NB; i++) { s1[i] = 0.0; s2[i] = 0.0; s3[i] = 0.0; }
-  for (int k = k0; k < k1; k++) {
-    cpx<double> a[NA], b[NB];
-    double as[NA], bs[NB];
+      for (int ra = 0; ra < NA; ra++)
 #pragma unroll
-    for (int r = 0; r < NA; r++) { a[r] = A[t.offA[r] + oA]; as[r] = a[r].re + a[r].im; }
+        for (int rb = 0; rb < NB; rb++) {
+          const int i = ra * NB + rb;
+          s1[i] = fma(a[ra].re, b[rb].re, s1[i]);
+          s2[i] = fma(a[ra].im, b[rb].im, s2[i]);
+          s3[i] = fma(as[ra], bs[rb], s3[i]);
+        }
+      if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
+      else { oA += sA2; oB += sB2; }
+    }
 #pragma unroll
-    for (int r = 0; r < NB; r++) { b[r] = B[t.offB[r] + oB]; bs[r] = b[r].re + b[r].im; }
+    for (int i = 0; i < NA * NB; i++) acc[i] = cpx<R>(s1[i] - s2[i], s3[i] - s1[i] - s2[i]);
+  } else {
+    int i1 = 0, i2 = 0, oA = 0, oB = 0;
+    for (int k = 0; k < K; k++) {
+      cpx<R> a[NA], b[NB];
 #pragma unroll
-    for (int ra = 0; ra < NA; ra++)
+      for (int r = 0; r < NA; r++) a[r] = F[(long long)(t.offA[r] + oA) * V + q];
 #pragma unroll
-      for (int rb = 0; rb < NB; rb++) {
-        const int i = ra * NB + rb;
-        s1[i] = fma(a[ra].re, b[rb].re, s1[i]);
-        s2[i] = fma(a[ra].im, b[rb].im, s2[i]);
-        s3[i] = fma(as[ra], bs[rb], s3[i]);
-      }
-    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
-    else { oA += sA2; oB += sB2; }
+      for (int r = 0; r < NB; r++) b[r] = F[(long long)(t.offB[r] + oB) * V + nq];
+#pragma unroll
+      for (int ra = 0; ra < NA; ra++)
+#pragma unroll
+        for (int rb = 0; rb < NB; rb++) cmac(acc[ra * NB + rb], a[ra], b[rb]);
+      if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
+      else { oA += sA2; oB += sB2; }
+    }
   }
 #pragma unroll
-  for (int i = 0; i < NA * NB; i++) acc[i] = cpx<double>(s1[i] - s2[i], s3[i] - s1[i] - s2[i]);
+  for (int i = 0; i < NA * NB; i++) P[(long long)i * V] = acc[i];
 }
 
-template <typename R, int NA, int NB>
-__device__ __forceinline__ void run_unit_any(const cpx<R>* A, const cpx<R>* B, const DevTask& t, int k0, int k1,
-                                             cpx<R> (&acc)[16]) {
-  if constexpr (sizeof(R) == 8) run_unit_gauss<NA, NB>(A, B, t, k0, k1, acc);
-  else run_unit<R, NA, NB>(A, B, t, k0, k1, acc);
-}
+constexpr int kPairWarps = 4;
 
 template <typename R>
-__device__ __forceinline__ void smem_add(cpx<R>* p, cpx<R> v) {
-  atomicAdd(&p->re, v.re);
-  atomicAdd(&p->im, v.im);
-}
-
-// PAIR = false: one CTA per q, block rows read from global memory (FP64).
-// PAIR = true: one CTA per pair {q, -q}; both block rows staged in shared
-// memory once and used for the products at q (A(q) B(-q)) and at -q (FP32).
-template <typename R, bool PAIR, int THREADS>
-__global__ void __launch_bounds__(THREADS)
-k_contract(const cpx<R>* __restrict__ blk, int L, int n_out, const int* __restrict__ qlist,
-           const DevTask* __restrict__ tasks, int n_tasks, const int* __restrict__ sched_ptr,
-           const int2* __restrict__ units, const int* __restrict__ cptr, const int* __restrict__ citem,
-           const double* __restrict__ ccoef, int n_outputs, cpx<double>* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tid = threadIdx.x, V = L * L * L;
-  const int q = PAIR ? qlist[blockIdx.x] : blockIdx.x;
+__global__ void __launch_bounds__(32 * kPairWarps)
+k_pair_products(const cpx<R>* __restrict__ F, int L, const DevTask* __restrict__ tasks,
+                const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
+                cpx<R>* __restrict__ P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = blockIdx.y * kPairWarps + warp;
+  const int V = L * L * L;
+  const int q = blockIdx.x * 32 + lane;
+  if (g >= n_groups || q >= V) return;
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
-  const int sides = (PAIR && nq != q) ? 2 : 1;
-  cpx<R>* rows = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* P = PAIR ? rows + 2 * n_out : rows;
-  const cpx<R>* gq = blk + (size_t)q * n_out;
-  const cpx<R>* gn = blk + (size_t)nq * n_out;
-  if (PAIR) {
-    // n_out * sizeof(cpx<R>) is a multiple of 16 bytes (n_out even)
-    const int n16 = n_out * (int)sizeof(cpx<R>) / 16;
-    const float4* s0 = reinterpret_cast<const float4*>(gq);
-    const float4* s1 = reinterpret_cast<const float4*>(gn);
-    float4* d = reinterpret_cast<float4*>(rows);
-    for (int i = tid; i < n16; i += THREADS) {
-      d[i] = __ldg(s0 + i);
-      if (sides == 2) d[n16 + i] = __ldg(s1 + i);
-    }
-  }
-  for (int side = 0; side < sides; side++) {
-    const cpx<R>* A = PAIR ? rows + side * n_out : gq;
-    const cpx<R>* B = PAIR ? rows + (sides == 2 ? 1 - side : 0) * n_out : gn;
-    const int qq = side ? nq : q;
-    for (int i = tid; i < n_tasks * 16; i += THREADS) P[i] = cpx<R>(0, 0);
-    __syncthreads();
-    const int u1 = sched_ptr[tid + 1];
-    for (int u = sched_ptr[tid]; u < u1; u++) {
-      const int2 un = units[u];
-      const DevTask t = tasks[un.x];
-      const int k0 = un.y & 0xffff, k1 = un.y >> 16;
-      cpx<R> acc[16];
-#pragma unroll
-      for (int i = 0; i < 16; i++) acc[i] = cpx<R>(0, 0);
-      const int nA = t.nAnB & 0xff;
-      if (nA == 4) run_unit_any<R, 4, 4>(A, B, t, k0, k1, acc);
-      else if (nA == 2) run_unit_any<R, 2, 8>(A, B, t, k0, k1, acc);
-      else run_unit_any<R, 8, 2>(A, B, t, k0, k1, acc);
-      cpx<R>* p = P + un.x * 16;
-#pragma unroll
-      for (int i = 0; i < 16; i++) smem_add(p + i, acc[i]);
-    }
-    __syncthreads();
-    // signed FP64 sum over Wick diagrams into channels and spins
-    for (int o = tid; o < n_outputs; o += THREADS) {
-      cpx<double> s(0, 0);
-      const int c1 = cptr[o + 1];
-      for (int c = cptr[o]; c < c1; c++) {
-        const double w = ccoef[c];
-        const cpx<R> p = P[citem[c]];
-        s.re = fma(w, (double)p.re, s.re);
-        s.im = fma(w, (double)p.im, s.im);
-      }
-      out[((size_t)(o >> 4) * V + qq) * 16 + (o & 15)] = s;
-    }
-    __syncthreads();
+  const int j1 = group_ptr[g + 1];
+  for (int j = group_ptr[g]; j < j1; j++) {
+    const int ti = group_task[j];
+    const DevTask t = tasks[ti];
+    cpx<R>* p = P + (long long)ti * 16 * V + q;
+    const int nA = t.nAnB & 0xff;
+    if (nA == 4) task_products<R, 4, 4>(F, V, q, nq, t, p);
+    else if (nA == 2) task_products<R, 2, 8>(F, V, q, nq, t, p);
+    else task_products<R, 8, 2>(F, V, q, nq, t, p);
   }
 }
 
-int contract_threads(bool fp64) { return fp64 ? 256 : 512; }
-
-size_t contract_smem(bool fp64, int n_out, int n_tasks) {
-  return fp64 ? (size_t)n_tasks * 16 * sizeof(cpx<double>)
-              : (size_t)(2 * n_out + n_tasks * 16) * sizeof(cpx<float>);
+// Signed FP64 sums over Wick diagrams: Ct[o][q] = sum_c coef_c P[item_c][q],
+// o = channel*16 + spin.
+template <typename R>
+__global__ void __launch_bounds__(128)
+k_wick_sums(const cpx<R>* __restrict__ P, int V, const int* __restrict__ cptr, const int* __restrict__ citem,
+            const double* __restrict__ ccoef, cpx<double>* __restrict__ Ct) {
+  const int q = blockIdx.x * 128 + threadIdx.x, o = blockIdx.y;
+  if (q >= V) return;
+  cpx<double> s(0, 0);
+  const int c1 = cptr[o + 1];
+  for (int c = cptr[o]; c < c1; c++) {
+    const double w = ccoef[c];
+    const cpx<R> p = P[(long long)citem[c] * V + q];
+    s.re = fma(w, (double)p.re, s.re);
+    s.im = fma(w, (double)p.im, s.im);
+  }
+  Ct[(long long)o * V + q] = s;
 }
 
-cudaError_t launch_contract(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
-                            int n_tasks, const int* sched_ptr, const int2* units, const int* cptr, const int* citem,
-                            const double* ccoef, int n_ch, void* out, bool fp64, cudaStream_t st) {
+cudaError_t launch_contract(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
+                            const int* group_task, int n_groups, void* P, const int* cptr, const int* citem,
+                            const double* ccoef, int n_ch, void* ct, bool fp64, cudaStream_t st) {
   const int V = L * L * L;
-  const size_t sm = contract_smem(fp64, n_out, n_tasks);
+  dim3 g1((V + 31) / 32, (n_groups + kPairWarps - 1) / kPairWarps);
+  dim3 g2((V + 127) / 128, n_ch * 16);
   if (fp64) {
-    auto k = k_contract<double, false, 256>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pair_products<double><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, L, tasks, group_ptr,
+                                                            group_task, n_groups, (cpx<double>*)P);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k<<<V, 256, sm, st>>>((const cpx<double>*)blk, L, n_out, qlist, tasks, n_tasks, sched_ptr, units, cptr, citem,
-                          ccoef, n_ch * 16, (cpx<double>*)out);
+    k_wick_sums<double><<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
   } else {
-    auto k = k_contract<float, true, 512>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_pair_products<float><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<float>*)blk_field, L, tasks, group_ptr,
+                                                           group_task, n_groups, (cpx<float>*)P);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k<<<n_q, 512, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, sched_ptr, units, cptr, citem,
-                            ccoef, n_ch * 16, (cpx<double>*)out);
+    k_wick_sums<float><<<g2, 128, 0, st>>>((const cpx<float>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
   }
   return cudaGetLastError();
 }
 
-// -------------------------------------------------------------- normalise
-__global__ void k_normalise(cpx<double>* __restrict__ out, int V, NormParams p, const int* __restrict__ kexp) {
-  const long long n = (long long)p.n_ch * V * 16;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const int kl = kexp[0], ks = kexp[1];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int ch = (int)(i / ((long long)V * 16));
-    const double s = ldexp(p.f[ch], p.nl[ch] * kl + p.ns[ch] * ks);
-    cpx<double> v = out[i];
-    out[i] = cpx<double>(v.re * s, v.im * s);
-  }
+// ------------------------------------------------------------ normalisation
+// scale[ch] = f[ch] * 2^(nl[ch] k_l + ns[ch] k_s): 1/V, the mass factor and the
+// undoing of the power-of-two propagator rescaling of this slice.
+__global__ void k_scales(ScaleParams p, const int* __restrict__ kexp, double* __restrict__ scale) {
+  const int ch = threadIdx.x;
+  if (ch < p.n_ch) scale[ch] = ldexp(p.f[ch], p.nl[ch] * kexp[0] + p.ns[ch] * kexp[1]);
 }
 
-cudaError_t launch_normalise(void* out, int V, const NormParams& p, const int* kexp, cudaStream_t st) {
-  long long n = (long long)p.n_ch * V * 16;
-  int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-  k_normalise<<<blocks, 256, 0, st>>>((cpx<double>*)out, V, p, kexp);
+cudaError_t launch_scales(const ScaleParams& p, const int* kexp, double* scale, cudaStream_t st) {
+  k_scales<<<1, kMaxChannels, 0, st>>>(p, kexp, scale);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ namespace bbc {
 struct DevTask {
   int offA[8], offB[8];
   int nAnB;  // nA | nB << 8
-  int n2;
+  int n1, n2;
   int sA;    // sA1 | sA2 << 16
   int sB;    // sB1 | sB2 << 16
 };
@@ -25,11 +25,13 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
 };
 
 constexpr int kMaxChannels = 64;
-struct NormParams {  // per channel: host factor (1/V, mass normalisation) and quark counts
+struct ScaleParams {  // per channel: host factor (1/V, mass normalisation) and quark counts
   int n_ch;
   double f[kMaxChannels];
   int nl[kMaxChannels], ns[kMaxChannels];
 };
+// scale[ch] = f[ch] * 2^(nl[ch] kexp[0] + ns[ch] kexp[1]) on the device.
+cudaError_t launch_scales(const ScaleParams& p, const int* kexp, double* scale, cudaStream_t st);
 
 // Twiddle tables e^{-2 pi i k / 96} (double and float) into __constant__ memory.
 cudaError_t upload_twiddles();
@@ -46,22 +48,20 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
                                const uint32_t* entries, const uint16_t* zneed, const DevGroups& g,
                                void* blk, int n_out, bool fp64, cudaStream_t st);
-// In-place 1-D DFTs of length L along `axis` of data[n_outer][V][n_inner];
-// storage and compute precision: fp64_store / fp64_compute; inverse = e^{+i}.
-cudaError_t launch_fft_pass(void* data, int L, long long n_outer, int n_inner, int axis,
-                            bool inverse, bool fp64_store, bool fp64_compute, cudaStream_t st);
-// q-space contraction of one slice: blk [V][n_out] -> out [n_ch][V][16] (c128).
-// qlist[n_q]: one q of every pair {q, -q} (FP32 path); tasks, per-thread
-// schedule (sched_ptr[threads+1], units {task, k0 | k1 << 16}) and the signed
-// sums (cptr, citem, ccoef) over task products P[task*16 + rA*nB + rB].
-int contract_threads(bool fp64);
-size_t contract_smem(bool fp64, int n_out, int n_tasks);
-cudaError_t launch_contract(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
-                            int n_tasks, const int* sched_ptr, const int2* units, const int* cptr,
-                            const int* citem, const double* ccoef, int n_ch, void* out, bool fp64,
-                            cudaStream_t st);
-// out[ch][r][s] *= f[ch] * 2^(nl[ch] k_l + ns[ch] k_s).
-cudaError_t launch_normalise(void* out, int V, const NormParams& p, const int* kexp,
-                             cudaStream_t st);
+// Forward 3-D FFT of every block field: x pass from the site-major build
+// output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],
+// then the y and z passes in place (exp(-i q.x), unnormalised).
+cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
+                               cudaStream_t st);
+// Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z
+// pass writing out[n_ch][V][16] (complex128) multiplied by scale[ch].
+cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                               cudaStream_t st);
+// q-space contraction of one slice from field-major blocks blk_field[n_rows][V]:
+// pair products of every task (warp task groups group_ptr/group_task) into
+// P[n_tasks*16][V], then the signed FP64 sums into ct[n_ch*16][V] (complex128).
+cudaError_t launch_contract(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
+                            const int* group_task, int n_groups, void* P, const int* cptr, const int* citem,
+                            const double* ccoef, int n_ch, void* ct, bool fp64, cudaStream_t st);
 
 }  // namespace bbc

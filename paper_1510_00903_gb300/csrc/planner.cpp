@@ -673,4 +673,30 @@ void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* t
   }
 }
 
+void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task) {
+  std::vector<int> order(plan.tasks.size());
+  std::iota(order.begin(), order.end(), 0);
+  auto cost = [&](int t) {
+    const PairTask& k = plan.tasks[t];
+    return (long long)k.n1 * k.n2 * (4 * k.nA * k.nB + 2 * (k.nA + k.nB)) + 64;  // FMAs + loads + stores
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<long long> load(groups, 0);
+  std::vector<std::vector<int>> per(groups);
+  for (int t : order) {
+    int best = 0;
+    for (int g = 1; g < groups; g++)
+      if (load[g] < load[best]) best = g;
+    load[best] += cost(t);
+    per[best].push_back(t);
+  }
+  group_ptr->assign(1, 0);
+  group_task->clear();
+  for (auto& v : per) {
+    std::sort(v.begin(), v.end());
+    for (int t : v) group_task->push_back(t);
+    group_ptr->push_back((int)group_task->size());
+  }
+}
+
 }  // namespace bbc

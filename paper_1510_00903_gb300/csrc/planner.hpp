@@ -93,4 +93,8 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
 void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* thread_ptr,
                    std::vector<Unit>* units);
 
+// Partition of the tasks into `groups` lists of near-equal cost (longest task
+// first to the cheapest list); each list is run by one warp for 32 q at a time.
+void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task);
+
 }  // namespace bbc
