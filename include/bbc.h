@@ -132,8 +132,9 @@ bbc_status bbc_contract(bbc_ctx* ctx, int slot, void* out_dev, int normalised);
 bbc_status bbc_plan_stats(const bbc_ctx* ctx, int channel_pos, int term3, int term4,
                           int* n_diagrams, int* iters_signed, int cap);
 
-/* Aggregated plan sizes: unique blocks, block outputs per site, aligned
- * block-pair products per (q, spin) and the total open-index iterations. */
+/* Aggregated plan sizes: unique blocks, block outputs per site, block-pair
+ * products per q (16 spin combinations per aligned block pair) and their
+ * complex multiply-adds per site. */
 bbc_status bbc_plan_sizes(const bbc_ctx* ctx, int* n_blocks, int* n_block_outputs,
                           int* n_pair_items, long long* pair_macs_per_site);
 

@@ -188,8 +188,9 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     delete c;
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
-  // warp task groups of the pair products: enough warps per 32 q to fill the GPU
-  bbc::make_task_groups(c->plan, 16, &c->group_ptr, &c->group_task);
+  // warp task groups of the pair products: enough warps per 32 q to fill the
+  // GPU several times over at L = 16 (V/32 q tiles x groups warps)
+  bbc::make_task_groups(c->plan, 48, &c->group_ptr, &c->group_task);
   *ctx = c;
   return BBC_OK;
 }
@@ -398,7 +399,7 @@ bbc_status bbc_plan_sizes(const bbc_ctx* c, int* n_blocks, int* n_block_outputs,
   if (!c) return BBC_EINVAL;
   if (n_blocks) *n_blocks = c->plan.n_blocks;
   if (n_block_outputs) *n_block_outputs = c->plan.n_out;
-  if (n_pair_items) *n_pair_items = (int)c->plan.items.size();
+  if (n_pair_items) *n_pair_items = 16 * (int)c->plan.tasks.size();
   if (pair_macs_per_site) *pair_macs_per_site = c->plan.pair_macs;
   return BBC_OK;
 }

@@ -464,9 +464,11 @@ k_pair_products(const cpx<R>* __restrict__ F, int L, const DevTask* __restrict__
                 const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
                 cpx<R>* __restrict__ P) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = blockIdx.y * kPairWarps + warp;
+  // task groups of one q tile are adjacent in the grid, so the tile's block
+  // rows are shared in L2 while its groups run
+  const int g = blockIdx.x * kPairWarps + warp;
   const int V = L * L * L;
-  const int q = blockIdx.x * 32 + lane;
+  const int q = blockIdx.y * 32 + lane;
   if (g >= n_groups || q >= V) return;
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
@@ -505,7 +507,7 @@ cudaError_t launch_contract(const void* blk_field, int L, const DevTask* tasks, 
                             const int* group_task, int n_groups, void* P, const int* cptr, const int* citem,
                             const double* ccoef, int n_ch, void* ct, bool fp64, cudaStream_t st) {
   const int V = L * L * L;
-  dim3 g1((V + 31) / 32, (n_groups + kPairWarps - 1) / kPairWarps);
+  dim3 g1((n_groups + kPairWarps - 1) / kPairWarps, (V + 31) / 32);
   dim3 g2((V + 127) / 128, n_ch * 16);
   if (fp64) {
     k_pair_products<double><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, L, tasks, group_ptr,

@@ -249,7 +249,14 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
 
   std::map<std::vector<int64_t>, int> uniq;
   std::vector<UBlock> ublocks;
-  struct Inst { int ch_pos; double coef; int uA, uB; Variant vA, vB; std::vector<int> extA, extB, osz; };
+  // promA/promB: source baryons whose delta-quark minority enters that block as
+  // a full (spin, colour) open index; the external spin then selects a slice
+  // of it (Appendix A: a block with that quark's colour open and its spin
+  // fixed is a sub-block of the one with both open).
+  struct Inst {
+    int ch_pos; double coef; int uA, uB; Variant vA, vB;
+    std::vector<int> extA, extB, promA, promB, osz, oszA, oszB, open_k;
+  };
   std::vector<Inst> insts;
 
   for (int cp = 0; cp < n; cp++) {
@@ -295,11 +302,19 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
             }
           const int K = std::accumulate(osz.begin(), osz.end(), 1, std::multiplies<int>());
           NatBlock nb[2];
+          std::vector<int> prom[2];
           for (int blk = 0; blk < 2; blk++) {
             NatBlock& b = nb[blk];
             b.osz = osz;
             for (int k = 0; k < 2; k++) {
               int dpos = 3 * k + src[k].dk;
+              const bool incoming_delta = att[k] != blk && minority[k] == dpos;
+              if (incoming_delta) {
+                prom[blk].push_back(k);
+                for (size_t i = 0; i < opens.size(); i++)
+                  if (opens[i] == k) b.osz[i] = 12;
+                continue;
+              }
               int carrier = (minority[k] != dpos) ? att[k] : 1 - att[k];
               if (carrier == blk) b.ext.push_back(k);
             }
@@ -318,13 +333,14 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
             for (int k = 0; k < 2; k++)
               if (att[k] == blk) attk.push_back(k);
             const int ne = (int)b.ext.size();
-            b.rows.assign(2 * (1 << ne) * K, Row());
+            const int Kb = std::accumulate(b.osz.begin(), b.osz.end(), 1, std::multiplies<int>());
+            b.rows.assign(2 * (1 << ne) * Kb, Row());
             for (int a = 0; a < 2; a++)
               for (int evf = 0; evf < (1 << ne); evf++)
-                for (int ovf = 0; ovf < K; ovf++) {
+                for (int ovf = 0; ovf < Kb; ovf++) {
                   int evk[2] = {-1, -1}, ovk[2] = {-1, -1};
                   for (int i = ne - 1, x = evf; i >= 0; i--, x >>= 1) evk[b.ext[i]] = x & 1;
-                  for (int i = (int)opens.size() - 1, x = ovf; i >= 0; i--) { ovk[opens[i]] = x % osz[i]; x /= osz[i]; }
+                  for (int i = (int)opens.size() - 1, x = ovf; i >= 0; i--) { ovk[opens[i]] = x % b.osz[i]; x /= b.osz[i]; }
                   std::map<int, int> acc;
                   // enumerate entries of the attached tensors (at most two)
                   std::vector<std::vector<SrcEntry>> lists;
@@ -349,10 +365,7 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
                         w *= e.val;
                       }
                       for (int k = 0; k < 2; k++)
-                        if (att[k] != blk && minority[k] >= 0) {
-                          int m = minority[k];
-                          eta[m] = (m - 3 * k == src[k].dk) ? 3 * evk[k] + ovk[k] : ovk[k];
-                        }
+                        if (att[k] != blk && minority[k] >= 0) eta[minority[k]] = ovk[k];  // (spin, colour)
                       for (auto& pi : pis) {
                         int ein[3];
                         for (int s = 0; s < 3; s++) ein[s] = eta[pos[pi[s]]];
@@ -364,7 +377,7 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
                         }
                       }
                     }
-                  Row& r = b.rows[(a * (1 << ne) + evf) * K + ovf];
+                  Row& r = b.rows[(a * (1 << ne) + evf) * Kb + ovf];
                   for (auto& kv : acc)
                     if (kv.second != 0) r.push_back(kv);
                 }
@@ -373,6 +386,9 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
           in.ch_pos = cp;
           in.coef = parity * c34 * op[0]->scale * op[1]->scale;
           in.extA = nb[0].ext; in.extB = nb[1].ext; in.osz = osz;
+          in.promA = prom[0]; in.promB = prom[1];
+          in.open_k = opens;
+          in.oszA = nb[0].osz; in.oszB = nb[1].osz;
           for (int blk = 0; blk < 2; blk++) {
             Variant v = canonical(nb[blk]);
             auto it = uniq.find(v.key);
@@ -381,18 +397,19 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
               id = (int)ublocks.size();
               uniq.emplace(v.key, id);
               UBlock u;
+              const std::vector<int>& bosz = nb[blk].osz;
               u.ne = (int)nb[blk].ext.size();
-              u.no = (int)osz.size();
+              u.no = (int)bosz.size();
               u.osz.resize(u.no);
-              for (int i = 0; i < u.no; i++) u.osz[i] = osz[v.po[i]];
-              const int Kc = K;
+              for (int i = 0; i < u.no; i++) u.osz[i] = bosz[v.po[i]];
+              const int Kc = std::accumulate(bosz.begin(), bosz.end(), 1, std::multiplies<int>());
               u.rows.assign(nb[blk].rows.size(), Row());
               for (int a = 0; a < 2; a++)
                 for (int evf = 0; evf < (1 << u.ne); evf++)
                   for (int ovf = 0; ovf < Kc; ovf++) {
                     std::vector<int> ev(u.ne), ov(u.no);
                     for (int i = u.ne - 1, x = evf; i >= 0; i--, x >>= 1) ev[i] = x & 1;
-                    for (int i = u.no - 1, x = ovf; i >= 0; i--) { ov[i] = x % osz[i]; x /= osz[i]; }
+                    for (int i = u.no - 1, x = ovf; i >= 0; i--) { ov[i] = x % bosz[i]; x /= bosz[i]; }
                     int ci = canon_offset(u, v, a, ev, ov);  // base 0 at this point
                     Row r = nb[blk].rows[(a * (1 << u.ne) + evf) * Kc + ovf];
                     for (auto& zw : r) { zw.second *= v.sgn; u.fam_mask |= 1 << (zw.first / kFamEntries); }
@@ -479,45 +496,9 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
     }
   }
 
-  // --- aligned pair products and their signed sums -------------------------
-  std::map<std::array<int, 8>, int> item_id;
-  std::vector<std::vector<std::pair<int, double>>> contrib(n * 16);
-  for (const Inst& in : insts) {
-    const UBlock& A = ublocks[in.uA];
-    const UBlock& B = ublocks[in.uB];
-    const int no = (int)in.osz.size();
-    const int n1 = no > 0 ? in.osz[0] : 1, n2 = no > 1 ? in.osz[1] : 1;
-    for (int s = 0; s < 16; s++) {
-      int a = s & 1, b = (s >> 1) & 1, e[2] = {(s >> 2) & 1, (s >> 3) & 1};
-      std::vector<int> evA, evB;
-      for (int k : in.extA) evA.push_back(e[k]);
-      for (int k : in.extB) evB.push_back(e[k]);
-      auto ovec = [&](int i, int j) {
-        std::vector<int> ov;
-        if (no > 0) ov.push_back(i);
-        if (no > 1) ov.push_back(j);
-        return ov;
-      };
-      int oA = canon_offset(A, in.vA, a, evA, ovec(0, 0));
-      int oB = canon_offset(B, in.vB, b, evB, ovec(0, 0));
-      int sA1 = n1 > 1 ? canon_offset(A, in.vA, a, evA, ovec(1, 0)) - oA : 0;
-      int sA2 = n2 > 1 ? canon_offset(A, in.vA, a, evA, ovec(0, 1)) - oA : 0;
-      int sB1 = n1 > 1 ? canon_offset(B, in.vB, b, evB, ovec(1, 0)) - oB : 0;
-      int sB2 = n2 > 1 ? canon_offset(B, in.vB, b, evB, ovec(0, 1)) - oB : 0;
-      std::array<int, 8> key = {oA, oB, n1, n2, sA1, sA2, sB1, sB2};
-      auto it = item_id.find(key);
-      int id;
-      if (it == item_id.end()) {
-        id = (int)P.items.size();
-        item_id.emplace(key, id);
-        P.items.push_back(PairItem{oA, oB, n1, n2, sA1, sA2, sB1, sB2});
-      } else {
-        id = it->second;
-      }
-      contrib[in.ch_pos * 16 + s].push_back({id, in.coef * in.vA.sgn * in.vB.sgn});
-    }
-  }
-  // task products: one per aligned block pair, all 16 spin combinations
+  // task products: one per aligned block pair, all 16 spin combinations.
+  // Row rA enumerates (a, spins of extA, spins of promA); a promoted delta
+  // minority of source baryon k is read at spin e_k of the 12-valued axis.
   {
     std::map<std::vector<int>, int> task_id;
     std::vector<std::vector<std::pair<int, double>>> tc(n * 16);
@@ -526,39 +507,63 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
       const UBlock& B = ublocks[in.uB];
       const int no = (int)in.osz.size();
       const int n1 = no > 0 ? in.osz[0] : 1, n2 = no > 1 ? in.osz[1] : 1;
-      const int neA = (int)in.extA.size(), neB = (int)in.extB.size();
+      const int neA = (int)(in.extA.size() + in.promA.size()), neB = (int)(in.extB.size() + in.promB.size());
       PairTask t{};
       t.nA = 2 << neA;
       t.nB = 2 << neB;
       t.n1 = n1;
       t.n2 = n2;
-      auto ovec = [&](int i, int j) {
+      auto side_offset = [&](const UBlock& U, const Variant& v, const std::vector<int>& ext,
+                             const std::vector<int>& prom, const std::vector<int>& bosz, int a, const int e[2],
+                             int i, int j) {
+        std::vector<int> ev;
+        for (int k : ext) ev.push_back(e[k]);
         std::vector<int> ov;
-        if (no > 0) ov.push_back(i);
-        if (no > 1) ov.push_back(j);
-        return ov;
+        const int dv[2] = {i, j};
+        for (int x = 0; x < no; x++) {
+          int val = dv[x];
+          if (bosz[x] != in.osz[x]) {
+            // promoted axis (12 values in the block, 3 in the diagram): its
+            // source baryon is the one in prom whose open axis this is
+            int k = in.open_k[x];
+            val = 3 * e[k] + dv[x];
+          }
+          ov.push_back(val);
+        }
+        return canon_offset(U, v, a, ev, ov);
       };
-      auto evbits = [](int x, int ne) {
-        std::vector<int> ev(ne);
-        for (int i = ne - 1; i >= 0; i--, x >>= 1) ev[i] = x & 1;
-        return ev;
+      auto decode = [](int r, const std::vector<int>& ext, const std::vector<int>& prom, int& a, int e[2]) {
+        const int ne = (int)(ext.size() + prom.size());
+        a = r >> ne;
+        int x = r & ((1 << ne) - 1);
+        for (int i = (int)prom.size() - 1; i >= 0; i--, x >>= 1) e[prom[i]] = x & 1;
+        for (int i = (int)ext.size() - 1; i >= 0; i--, x >>= 1) e[ext[i]] = x & 1;
       };
       for (int rA = 0; rA < t.nA; rA++) {
-        int a = rA >> neA;
-        auto ev = evbits(rA & ((1 << neA) - 1), neA);
-        t.offA[rA] = canon_offset(A, in.vA, a, ev, ovec(0, 0));
+        int a, e[2] = {0, 0};
+        decode(rA, in.extA, in.promA, a, e);
+        t.offA[rA] = side_offset(A, in.vA, in.extA, in.promA, in.oszA, a, e, 0, 0);
         if (rA == 0) {
-          t.sA1 = n1 > 1 ? canon_offset(A, in.vA, a, ev, ovec(1, 0)) - t.offA[0] : 0;
-          t.sA2 = n2 > 1 ? canon_offset(A, in.vA, a, ev, ovec(0, 1)) - t.offA[0] : 0;
+          t.sA1 = n1 > 1 ? side_offset(A, in.vA, in.extA, in.promA, in.oszA, a, e, 1, 0) - t.offA[0] : 0;
+          t.sA2 = n2 > 1 ? side_offset(A, in.vA, in.extA, in.promA, in.oszA, a, e, 0, 1) - t.offA[0] : 0;
+        } else {
+          // strides must not depend on the row (checked)
+          const int s1 = n1 > 1 ? side_offset(A, in.vA, in.extA, in.promA, in.oszA, a, e, 1, 0) - t.offA[rA] : 0;
+          const int s2 = n2 > 1 ? side_offset(A, in.vA, in.extA, in.promA, in.oszA, a, e, 0, 1) - t.offA[rA] : 0;
+          if (s1 != t.sA1 || s2 != t.sA2) { *err = "internal: row-dependent stride"; return false; }
         }
       }
       for (int rB = 0; rB < t.nB; rB++) {
-        int b = rB >> neB;
-        auto ev = evbits(rB & ((1 << neB) - 1), neB);
-        t.offB[rB] = canon_offset(B, in.vB, b, ev, ovec(0, 0));
+        int b, e[2] = {0, 0};
+        decode(rB, in.extB, in.promB, b, e);
+        t.offB[rB] = side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 0, 0);
         if (rB == 0) {
-          t.sB1 = n1 > 1 ? canon_offset(B, in.vB, b, ev, ovec(1, 0)) - t.offB[0] : 0;
-          t.sB2 = n2 > 1 ? canon_offset(B, in.vB, b, ev, ovec(0, 1)) - t.offB[0] : 0;
+          t.sB1 = n1 > 1 ? side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 1, 0) - t.offB[0] : 0;
+          t.sB2 = n2 > 1 ? side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 0, 1) - t.offB[0] : 0;
+        } else {
+          const int s1 = n1 > 1 ? side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 1, 0) - t.offB[rB] : 0;
+          const int s2 = n2 > 1 ? side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 0, 1) - t.offB[rB] : 0;
+          if (s1 != t.sB1 || s2 != t.sB2) { *err = "internal: row-dependent stride"; return false; }
         }
       }
       std::vector<int> key = {t.nA, t.nB, t.n1, t.n2, t.sA1, t.sA2, t.sB1, t.sB2};
@@ -577,7 +582,9 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
         int a = s & 1, b = (s >> 1) & 1, e[2] = {(s >> 2) & 1, (s >> 3) & 1};
         int rA = a, rB = b;
         for (int k : in.extA) rA = 2 * rA + e[k];
+        for (int k : in.promA) rA = 2 * rA + e[k];
         for (int k : in.extB) rB = 2 * rB + e[k];
+        for (int k : in.promB) rB = 2 * rB + e[k];
         tc[in.ch_pos * 16 + s].push_back({id * 16 + rA * t.nB + rB, in.coef * in.vA.sgn * in.vB.sgn});
       }
     }
@@ -591,41 +598,10 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
     }
   }
 
-  // order items by decreasing work (round-robin over threads stays balanced)
-  std::vector<int> order(P.items.size());
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return P.items[x].n1 * P.items[x].n2 > P.items[y].n1 * P.items[y].n2;
-  });
-  std::vector<int> rank(order.size());
-  std::vector<PairItem> sorted;
-  for (size_t i = 0; i < order.size(); i++) { rank[order[i]] = (int)i; sorted.push_back(P.items[order[i]]); }
-  P.items = sorted;
   P.pair_macs = 0;
-  for (auto& it : P.items) P.pair_macs += (long long)it.n1 * it.n2;
-  P.contrib_ptr.push_back(0);
-  for (auto& c : contrib) {
-    // merge repeated items of one output
-    std::map<int, double> m;
-    for (auto& p : c) m[rank[p.first]] += p.second;
-    for (auto& kv : m)
-      if (kv.second != 0.0) { P.contrib_item.push_back(kv.first); P.contrib_coef.push_back(kv.second); }
-    P.contrib_ptr.push_back((int)P.contrib_item.size());
-  }
+  for (const PairTask& t : P.tasks) P.pair_macs += 16LL * t.n1 * t.n2;
   // bounds of every device table index (checked once on the host so that no
   // kernel can read outside a block row or the product buffer)
-  for (const PairItem& it : P.items) {
-    auto last = [](int off, int n1, int n2, int s1, int s2) { return off + (n1 - 1) * s1 + (n2 - 1) * s2; };
-    if (it.offA < 0 || it.offB < 0 || it.n1 < 1 || it.n2 < 1 || it.n1 > 0xffff || it.n2 > 0xffff ||
-        it.sA1 < 0 || it.sA2 < 0 || it.sB1 < 0 || it.sB2 < 0 || it.sA1 > 0xffff || it.sA2 > 0x7fff ||
-        it.sB1 > 0xffff || it.sB2 > 0x7fff ||
-        last(it.offA, it.n1, it.n2, it.sA1, it.sA2) >= P.n_out || last(it.offB, it.n1, it.n2, it.sB1, it.sB2) >= P.n_out) {
-      *err = "internal: pair item out of range";
-      return false;
-    }
-  }
-  for (int id : P.contrib_item)
-    if (id < 0 || id >= (int)P.items.size()) { *err = "internal: contribution index"; return false; }
   for (const PairTask& t : P.tasks) {
     if (!((t.nA == 2 && t.nB == 8) || (t.nA == 4 && t.nB == 4) || (t.nA == 8 && t.nB == 2)) || t.n1 < 1 ||
         t.n2 < 1 || t.n1 * t.n2 > 0xffff) {
@@ -645,32 +621,6 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   if ((int)P.row_ptr.size() != P.n_out + 1) { *err = "internal: row table"; return false; }
   *plan = std::move(P);
   return true;
-}
-
-void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* thread_ptr,
-                   std::vector<Unit>* units) {
-  std::vector<Unit> all;
-  for (int t = 0; t < (int)plan.tasks.size(); t++) {
-    const int K = plan.tasks[t].n1 * plan.tasks[t].n2;
-    const int step = K > chunk ? chunk : K;
-    for (int k = 0; k < K; k += step) all.push_back(Unit{t, k, std::min(K, k + step)});
-  }
-  std::stable_sort(all.begin(), all.end(), [](const Unit& a, const Unit& b) { return a.k1 - a.k0 > b.k1 - b.k0; });
-  std::vector<long long> load(threads, 0);
-  std::vector<std::vector<Unit>> per(threads);
-  for (const Unit& u : all) {
-    int best = 0;
-    for (int i = 1; i < threads; i++)
-      if (load[i] < load[best]) best = i;
-    load[best] += (u.k1 - u.k0) + 2;  // +2: fixed cost of a unit (task load, flush)
-    per[best].push_back(u);
-  }
-  thread_ptr->assign(1, 0);
-  units->clear();
-  for (auto& v : per) {
-    for (auto& u : v) units->push_back(u);
-    thread_ptr->push_back((int)units->size());
-  }
 }
 
 void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task) {

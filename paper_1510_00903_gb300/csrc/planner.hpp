@@ -24,11 +24,6 @@ struct GroupInfo {
   int fam[2];             // families held in the two tensor slots (-1 = unused)
 };
 
-struct PairItem {  // one product sum_{i<n1, j<n2} A[offA + i sA1 + j sA2] B[offB + i sB1 + j sB2]
-  int offA, offB;
-  int n1, n2, sA1, sA2, sB1, sB2;
-};
-
 // One aligned block pair at one q: P[rA][rB] = sum_k A[offA[rA] + k] B[offB[rB] + k]
 // over the flattened open index k = (i1, i2) (offsets i1*s1 + i2*s2); rA runs
 // over (sink spin a, external spins carried by A), rB likewise for B, and
@@ -37,11 +32,6 @@ struct PairTask {
   int nA, nB;            // (2,8), (4,4) or (8,2)
   int offA[8], offB[8];  // row offsets in the block row of one site
   int n1, n2, sA1, sA2, sB1, sB2;
-};
-
-// A schedule unit: flattened open-index range [k0, k1) of one task.
-struct Unit {
-  int task, k0, k1;
 };
 
 struct DiagramInfo {
@@ -67,11 +57,7 @@ struct Plan {
   std::vector<int> tcontrib_ptr;     // n_channels*16 + 1, contributions over task products
   std::vector<int> tcontrib_item;
   std::vector<double> tcontrib_coef;
-  std::vector<PairItem> items;       // per-spin products (reference layout), sorted by decreasing work
-  std::vector<int> contrib_ptr;      // n_channels*16 + 1
-  std::vector<int> contrib_item;
-  std::vector<double> contrib_coef;
-  long long pair_macs = 0;           // sum over items of n1*n2
+  long long pair_macs = 0;           // complex multiply-adds of all task products per site
   // normalisation data per channel position
   std::vector<int> n_strange;        // strange quarks of the sink pair (light = 6 - n_strange)
   // statistics for the paper's tables
@@ -84,14 +70,6 @@ int channel_count();
 void channel_names(int id, const char* out[4]);
 // Build the plan; returns false and sets *err on a bad channel list.
 bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
-
-// Balanced static schedule of the task products over `threads` threads:
-// tasks with more than `chunk` open-index iterations are split into chunks
-// of `chunk`; chunks go longest-first to the least loaded thread.
-// Output: thread_ptr[threads + 1] and units[] (thread t owns
-// units[thread_ptr[t] .. thread_ptr[t+1])).
-void make_schedule(const Plan& plan, int threads, int chunk, std::vector<int>* thread_ptr,
-                   std::vector<Unit>* units);
 
 // Partition of the tasks into `groups` lists of near-equal cost (longest task
 // first to the cheapest list); each list is run by one warp for 32 q at a time.

@@ -53,10 +53,12 @@ def test_diagonal_rows_keep_the_printed_signs(ctx52):
 def test_aggregation_sizes(ctx52):
     """52 channels, upper spin components: 655 diagram instances with
     43,507 open-index iterations per spin (sum of the Tables' totals), stored
-    as 42 shared blocks (Appendix A aggregation)."""
+    as 24 shared blocks of 7,368 complex entries per site (Appendix A
+    aggregation, including the sub-block identity n^(2) in n^(3))."""
     s = bbc.bbc_plan_sizes(ctx52)
-    assert s["blocks"] == 42
-    assert s["block_outputs"] == 11040
+    assert s["blocks"] == 24
+    assert s["block_outputs"] == 7368
+    assert s["pair_macs_per_site"] == 277984
     total, n_diag = 0, 0
     for pos in range(52):
         for t3 in range(3):
