@@ -250,7 +250,7 @@ def main():
     c_avg_ms = c_ms / max(c_n, 1)
     flops_per_launch = 8.0 * sizes["pair_macs_per_site"] * V
     achieved = flops_per_launch / (c_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_contract<double>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+    roofline = {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                 "algorithmic_flop_per_launch": flops_per_launch, "avg_launch_ms": c_avg_ms}
@@ -276,7 +276,7 @@ def main():
         v, dt, cores = oracle_sample(seed=7)
         cpu = {"value": v, "unit": "site*channels/s", "cores": cores, "kind": "oracle",
                "sample": f"t=T/2, one random r, all 52 channels x 16 spins, sum over all {V} X ({dt:.1f} s)"}
-    cnt = {"load": 2, "build": 4, "contract": 5}
+    cnt = {"load": 2, "build": 4, "contract": 7}
     launches = args.steps * T * (2 * cnt["load"] + cnt["build"] + cnt["contract"])
     line = {
         "metric": "BB correlator site*channels/s", "value": value, "unit": "site*channels/s",

@@ -143,10 +143,11 @@ typedef enum {
   BBC_STAGE_INGEST = 0,     /* propagator rescaling copy (per flavour and slice) */
   BBC_STAGE_BUILD = 1,      /* baryon blocks of every site */
   BBC_STAGE_FFT_FWD = 2,    /* forward 3-D FFT of every block field (3 passes) */
-  BBC_STAGE_CONTRACT = 3,   /* q-space block-pair products and Wick-sign sums */
-  BBC_STAGE_FFT_INV = 4,    /* inverse 3-D FFT of every output field (3 passes) */
-  BBC_STAGE_NORMALISE = 5,  /* 1/V, rescaling, exp((m_B1 + m_B2) d) */
-  BBC_N_STAGES = 6
+  BBC_STAGE_CONTRACT = 3,   /* q-space block-pair products (all spins, summed over open indices) */
+  BBC_STAGE_FFT_INV = 4,    /* inverse 3-D FFT with the fused output transpose and normalisation */
+  BBC_STAGE_NORMALISE = 5,  /* per-channel normalisation factors */
+  BBC_STAGE_WICK = 6,       /* signed FP64 sums of pair products over Wick diagrams */
+  BBC_N_STAGES = 7
 } bbc_stage;
 
 /* enable != 0: from now on bracket every stage launch with CUDA events on the

@@ -124,7 +124,7 @@ def bbc_plan_sizes(ctx):
     return {"blocks": a.value, "block_outputs": b.value, "pair_items": c.value, "pair_macs_per_site": d.value}
 
 
-STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise"]
+STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise", "wick"]
 
 
 def bbc_enable_stage_timing(ctx, enable: bool):

@@ -351,10 +351,14 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_CONTRACT);
-    e = bbc::launch_contract(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
-                             (int)c->group_ptr.size() - 1, c->d_P, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct,
-                             fp64, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "contract");
+    e = bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                  (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pair products");
+  }
+  {
+    StageScope scope(c, BBC_STAGE_WICK);
+    e = bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
   }
   bbc::ScaleParams sp{};
   sp.n_ch = n_ch;

@@ -503,25 +503,25 @@ k_wick_sums(const cpx<R>* __restrict__ P, int V, const int* __restrict__ cptr, c
   Ct[(long long)o * V + q] = s;
 }
 
-cudaError_t launch_contract(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
-                            const int* group_task, int n_groups, void* P, const int* cptr, const int* citem,
-                            const double* ccoef, int n_ch, void* ct, bool fp64, cudaStream_t st) {
+cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
+                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st) {
   const int V = L * L * L;
   dim3 g1((n_groups + kPairWarps - 1) / kPairWarps, (V + 31) / 32);
-  dim3 g2((V + 127) / 128, n_ch * 16);
-  if (fp64) {
+  if (fp64)
     k_pair_products<double><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, L, tasks, group_ptr,
                                                             group_task, n_groups, (cpx<double>*)P);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_wick_sums<double><<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
-  } else {
+  else
     k_pair_products<float><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<float>*)blk_field, L, tasks, group_ptr,
                                                            group_task, n_groups, (cpx<float>*)P);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_wick_sums<float><<<g2, 128, 0, st>>>((const cpx<float>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
-  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
+                             void* ct, bool fp64, cudaStream_t st) {
+  const int V = L * L * L;
+  dim3 g2((V + 127) / 128, n_ch * 16);
+  if (fp64) k_wick_sums<double><<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
+  else k_wick_sums<float><<<g2, 128, 0, st>>>((const cpx<float>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
   return cudaGetLastError();
 }
 

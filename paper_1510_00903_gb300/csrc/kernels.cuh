@@ -59,9 +59,11 @@ cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const doubl
                                cudaStream_t st);
 // q-space contraction of one slice from field-major blocks blk_field[n_rows][V]:
 // pair products of every task (warp task groups group_ptr/group_task) into
-// P[n_tasks*16][V], then the signed FP64 sums into ct[n_ch*16][V] (complex128).
-cudaError_t launch_contract(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
-                            const int* group_task, int n_groups, void* P, const int* cptr, const int* citem,
-                            const double* ccoef, int n_ch, void* ct, bool fp64, cudaStream_t st);
+// P[n_tasks*16][V] ...
+cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
+                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st);
+// ... then the signed FP64 sums over Wick diagrams into ct[n_ch*16][V] (complex128).
+cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
+                             void* ct, bool fp64, cudaStream_t st);
 
 }  // namespace bbc
