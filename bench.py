@@ -276,7 +276,7 @@ def main():
         v, dt, cores = oracle_sample(seed=7)
         cpu = {"value": v, "unit": "site*channels/s", "cores": cores, "kind": "oracle",
                "sample": f"t=T/2, one random r, all 52 channels x 16 spins, sum over all {V} X ({dt:.1f} s)"}
-    cnt = {"load": 2, "build": 4, "contract": 7}
+    cnt = {"load": 2, "build": 4, "contract": 6}
     launches = args.steps * T * (2 * cnt["load"] + cnt["build"] + cnt["contract"])
     line = {
         "metric": "BB correlator site*channels/s", "value": value, "unit": "site*channels/s",
