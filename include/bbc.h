@@ -165,6 +165,36 @@ bbc_status bbc_stage_timing(bbc_ctx* ctx, double* ms, long long* launches);
  * bbc_build_blocks call per slot-batch, and one bbc_load_propagator call. */
 bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, int* per_contract);
 
+/* Bytes of the static device array used by bbc_run_slice_static. */
+#define BBC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* One time slice of the whole path without any device allocation, for
+ * callers that cannot call cudaMalloc (a process whose device memory belongs
+ * to another runtime's pool allocator, a plugin inside such a process, or a
+ * loop that must not take an allocation's implicit synchronisation).  The
+ * paper has no counterpart: it is an interface for such callers.
+ *
+ * Computes what bbc_load_propagator (both flavours, one slot), bbc_build_blocks
+ * and bbc_contract compute for time slice t, with every byte of device scratch
+ * in one file-scope __device__ array of BBC_STATIC_SCRATCH_BYTES (32 MiB)
+ * that every GPU loading the library holds from module load until exit.  No
+ * workspace needs to be attached.  S_light, S_strange: device pointers,
+ * [L^3][12][12] of dtype (16-byte aligned); out_dev: device pointer,
+ * [n_channels][L^3][16] complex128, written fully.  Everything runs
+ * asynchronously on the context stream.
+ *
+ * Size limit: the plan tables and one slice of blocks, pair products and
+ * q-space correlators must fit in the array -- L <= 4 with all 52 channels;
+ * larger lattices or channel lists return BBC_EINVAL with a message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and leave their
+ * data in it: calls whose work overlaps on the GPU (other streams, other host
+ * threads without ordering) race on it.  Allocates no device memory; host
+ * memory only for the error message of a failed call. */
+bbc_status bbc_run_slice_static(bbc_ctx* ctx, int t, const void* S_light, const void* S_strange, int dtype,
+                                void* out_dev, int normalised);
+
 /* Message of the last failed call on ctx (or of the last failed bbc_create
  * when ctx is NULL).  Valid until the next call on the same context. */
 const char* bbc_last_error(const bbc_ctx* ctx);

@@ -54,6 +54,7 @@ def _load():
         "bbc_enable_stage_timing": ([P, I], I),
         "bbc_stage_timing": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)], I),
         "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bbc_run_slice_static": ([P, I, P, P, I, P, I], I),
         "bbc_last_error": ([P], ctypes.c_char_p),
         "bbc_destroy": ([P], None),
     }
@@ -143,6 +144,14 @@ def bbc_launch_counts(ctx):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(ctx, _lib.bbc_launch_counts(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return {"load": a.value, "build": b.value, "contract": c.value}
+
+
+def bbc_run_slice_static(ctx, t: int, light_ptr: int, strange_ptr: int, dtype: int, out_ptr: int,
+                         normalised: bool):
+    """One slice with all device scratch in the library's static array (no
+    device allocation); see include/bbc.h for the size limit and sharing."""
+    _check(ctx, _lib.bbc_run_slice_static(ctx, t, ctypes.c_void_p(light_ptr), ctypes.c_void_p(strange_ptr), dtype,
+                                          ctypes.c_void_p(out_ptr), int(normalised)))
 
 
 def bbc_last_error(ctx) -> str:

@@ -1,0 +1,59 @@
+// ctx_internal.hpp -- definition of the opaque bbc_ctx (internal to libbbc).
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bbc.h"
+#include "kernels.cuh"
+#include "planner.hpp"
+
+struct bbc_ctx {
+  bbc_lattice lat{};
+  int prec = BBC_FP64;
+  cudaStream_t stream = nullptr;
+  int V = 0;
+  bbc::Plan plan;
+  std::string err;
+  // workspace view
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int slots = 0;
+  int* d_row_ptr = nullptr;
+  uint32_t* d_entries = nullptr;
+  uint16_t* d_zneed = nullptr;
+  bbc::DevTask* d_tasks = nullptr;
+  int* d_group_ptr = nullptr;
+  int* d_group_task = nullptr;
+  int* d_cptr = nullptr;
+  int* d_citem = nullptr;
+  double* d_ccoef = nullptr;
+  std::vector<int> group_ptr;            // warp task groups of the pair products
+  std::vector<int> group_task;
+  char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
+  char* d_prop = nullptr;                // [slots][2][V*144] compute precision
+  unsigned long long* d_amax = nullptr;  // [slots][2]
+  int* d_kexp = nullptr;                 // [slots][2]
+  char* d_blk = nullptr;                 // [slots][V][n_out] site-major build output
+  char* d_blkf = nullptr;                // [slots][n_out][V] field-major, Fourier space
+  char* d_P = nullptr;                   // [n_tasks*16][V] pair products of one slice
+  char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators
+  double* d_scale = nullptr;             // [kMaxChannels]
+  std::vector<int> slot_t;               // time slice of each slot (-1: none)
+  std::vector<int> slot_loaded;          // bit 0: light, bit 1: strange
+  std::vector<int> slot_built;
+  bool twiddles = false;
+  // stage timing: event pairs per stage, recycled through a pool
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[BBC_N_STAGES];
+  std::vector<cudaEvent_t> pool;
+  ~bbc_ctx() {
+    for (auto& v : pending)
+      for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
