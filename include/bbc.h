@@ -70,7 +70,7 @@ typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
 
 typedef enum { BBC_LIGHT = 0, BBC_STRANGE = 1 } bbc_flavour;
 
-/* Lattice description.  L: spatial extent (4, 8, 16 or 32); T: number of time
+/* Lattice description.  L: spatial extent (2, 4, 8, 16, 24, 32 or 48); T: number of time
  * slices; t0: source time slice; m_ud, m_s: quark decay masses that fix the
  * baryon masses used by the normalisation, m_B = (3 - n_s) m_ud + n_s m_s
  * (a reading for synthetic data; the paper divides by the measured masses). */

@@ -68,7 +68,7 @@ bbc_status cuda_fail(bbc_ctx* c, cudaError_t e, const char* where) {
   return fail(c, BBC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-bool supported_L(int L) { return L == 2 || L == 4 || L == 8 || L == 16 || L == 32; }
+bool supported_L(int L) { return L == 2 || L == 4 || L == 8 || L == 16 || L == 24 || L == 32 || L == 48; }
 
 cudaEvent_t take_event(bbc_ctx* c) {
   if (!c->pool.empty()) {
@@ -120,7 +120,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
                       int n_channels, void* cuda_stream) {
   if (!ctx || !lat || !channels) return fail(nullptr, BBC_EINVAL, "null argument");
   *ctx = nullptr;
-  if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 32)");
+  if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 24, 32, 48)");
   if (lat->T < 1 || lat->t0 < 0 || lat->t0 >= lat->T) return fail(nullptr, BBC_EINVAL, "bad T or t0");
   if (prec != BBC_FP64 && prec != BBC_MIXED_FP32) return fail(nullptr, BBC_EINVAL, "bad precision");
   if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");

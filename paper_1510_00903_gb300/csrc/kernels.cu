@@ -111,6 +111,43 @@ __device__ __forceinline__ void fft_pow2(cpx<R> (&v)[N]) {
   if constexpr (N > 1) fft_stage<R, N, 2, INV>(v);
 }
 
+// N = 3 M (M a power of two): decimation in time into three size-M transforms
+// of x[3 n2 + n1], then per k2 the twiddles exp(-+2 pi i n1 k2 / N) and a
+// radix-3 butterfly giving X[k2 + M k1] (k1 = 0, 1, 2).  On entry u[n1][.]
+// holds x[3 n2 + n1] in bit-reversed n2 order; on exit v holds X (natural).
+template <typename R, int M, bool INV>
+__device__ __forceinline__ void fft_radix3(cpx<R> (&u)[3][M], cpx<R> (&v)[3 * M]) {
+  constexpr int N = 3 * M;
+  fft_pow2<R, M, INV>(u[0]);
+  fft_pow2<R, M, INV>(u[1]);
+  fft_pow2<R, M, INV>(u[2]);
+  // omega = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
+  const R hs = (R)0.86602540378443864676;  // sqrt(3)/2
+#pragma unroll
+  for (int k2 = 0; k2 < M; k2++) {
+    cpx<R> t1 = u[1][k2], t2 = u[2][k2];
+    const int i1 = k2 * (kTw / N), i2 = 2 * k2 * (kTw / N);
+    if (i1 != 0) {
+      cpx<R> w = twiddle<R>(i1 % kTw);
+      if (INV) w.im = -w.im;
+      t1 = w * t1;
+    }
+    if (i2 != 0) {
+      cpx<R> w = twiddle<R>(i2 % kTw);
+      if (INV) w.im = -w.im;
+      t2 = w * t2;
+    }
+    const cpx<R> t0 = u[0][k2];
+    const cpx<R> s = t1 + t2, d = t1 - t2;
+    // X[k2] = t0 + s; X[k2 + M] = t0 - s/2 -+ i hs d; X[k2 + 2M] = t0 - s/2 +- i hs d
+    const cpx<R> m(t0.re - (R)0.5 * s.re, t0.im - (R)0.5 * s.im);
+    const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);  // -+ i hs d
+    v[k2] = t0 + s;
+    v[k2 + M] = m + r;
+    v[k2 + 2 * M] = m - r;
+  }
+}
+
 // ------------------------------------------------------------------ ingest
 __global__ void k_absmax(const void* __restrict__ src, int dtype, long long n_real,
                          unsigned long long* amax) {
@@ -261,6 +298,27 @@ __device__ __forceinline__ void load_bitrev(cpx<R> (&v)[N], const cpx<S>* p, lon
   ((v[bitrev(Ks, N)] = cpx<R>(p[Ks * step])), ...);
 }
 
+// u[n1][bitrev(n2)] = p[(3 n2 + n1) * step], compile-time indices
+template <typename S, typename R, int M, int... Ks>
+__device__ __forceinline__ void load_radix3(cpx<R> (&u)[3][M], const cpx<S>* p, long long step,
+                                            std::integer_sequence<int, Ks...>) {
+  ((u[Ks % 3][bitrev(Ks / 3, M)] = cpx<R>(p[Ks * step])), ...);
+}
+
+// Length-N transform of one line (N = 2^k, or 3 * 2^k), natural order in and out.
+template <typename S, typename R, int N, bool INV>
+__device__ __forceinline__ void line_fft(const cpx<S>* p, long long step, cpx<R> (&v)[N]) {
+  if constexpr ((N & (N - 1)) == 0) {
+    load_bitrev<S, R, N>(v, p, step, std::make_integer_sequence<int, N>{});
+    fft_pow2<R, N, INV>(v);
+  } else {
+    constexpr int M = N / 3;
+    cpx<R> u[3][M];
+    load_radix3<S, R, M>(u, p, step, std::make_integer_sequence<int, N>{});
+    fft_radix3<R, M, INV>(u, v);
+  }
+}
+
 __device__ __forceinline__ void line_base(int N, int axis, int line, int& base, int& stride) {
   const int a = line % N, b = line / N;
   if (axis == 0) { base = N * (a + N * b); stride = 1; }           // x varies, (y, z) = (a, b)
@@ -308,14 +366,12 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
   line_base(N, axis, line, base, stride);
   cpx<R> v[N];
   if (MODE == FFT_SITE2FIELD) {
-    load_bitrev<S, R, N>(v, in + (o * V + base) * n_inner + inner, (long long)stride * n_inner,
-                         std::make_integer_sequence<int, N>{});
+    line_fft<S, R, N, INV>(in + (o * V + base) * n_inner + inner, (long long)stride * n_inner, v);
   } else if (MODE == FFT_FIELD) {
-    load_bitrev<S, R, N>(v, in + o * V + base, stride, std::make_integer_sequence<int, N>{});
+    line_fft<S, R, N, INV>(in + o * V + base, stride, v);
   } else {
-    load_bitrev<S, R, N>(v, in + (o * 16 + inner) * V + base, stride, std::make_integer_sequence<int, N>{});
+    line_fft<S, R, N, INV>(in + (o * 16 + inner) * V + base, stride, v);
   }
-  fft_pow2<R, N, INV>(v);
   if (MODE == FFT_SITE2FIELD) {
     cpx<S>* p = out + (o * n_inner + inner) * V + base;
 #pragma unroll
@@ -353,6 +409,8 @@ static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_ou
     BBC_FFT_CASE(8)
     BBC_FFT_CASE(16)
     BBC_FFT_CASE(32)
+    BBC_FFT_CASE(24)
+    BBC_FFT_CASE(48)
     default: return cudaErrorInvalidValue;
   }
 #undef BBC_FFT_CASE

@@ -122,7 +122,7 @@ def test_multi_slot_batch_equals_single():
 
 
 # ---------------------------------------------------- closed form, any size
-@pytest.mark.parametrize("L", [8, 16, 32])
+@pytest.mark.parametrize("L", [8, 16, 24, 32, 48])
 def test_plane_wave_closed_form_all_channels(L):
     """Colour-diagonal plane waves: C(r) = V delta(P1+P2) e^{i P1.r} K, with K
     the single-site value from the oracle (property of Sec. 3 Eq.
@@ -180,6 +180,24 @@ def test_config_L16_T32_all_channels_sampled_fp64():
     in the launch configuration the benchmark times; the oracle checks two
     slices at r = 0 and random r, all 52 channels."""
     sampled_parity(16, 32, [1, 16], list(range(52)), 1, bbc.BBC_FP64, FP64_TOL, seed=5)
+
+
+def test_L24_radix3_sampled_fp64():
+    """L = 24 (radix-3 transforms) against the oracle on sampled r."""
+    L, T, t = 24, 4, 2
+    chans = [0, 10, 51]
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=8, times=[t])
+    r_list = [0, 1, 24 * 24 * 5 + 24 * 13 + 7]
+    want = orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], chans, r_list)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=bbc.BBC_FP64)
+    dev = torch.device("cuda")
+    out = cor.run(torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev), [t], normalised=False)
+    torch.cuda.synchronize()
+    g = out[0].cpu().numpy()
+    cor.close()
+    scale = np.abs(g).reshape(len(chans), -1).max(axis=1)
+    e = np.abs(g[:, r_list] - want).reshape(len(chans), -1).max(axis=1) / scale
+    assert e.max() < FP64_TOL, e
 
 
 def test_config_L32_T64_sampled_fp64_and_mixed():
