@@ -26,7 +26,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
-  size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, tables_end;
+  size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
+  size_t batches, wptr, wunits, qlist, tables_end;
   size_t stage, prop, amax, kexp, blk, blkf, P, ct, scale, total;
 };
 
@@ -43,6 +44,10 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.cptr = o; o = align256(o + sizeof(int) * p.tcontrib_ptr.size());
   L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
   L.ccoef = o; o = align256(o + sizeof(double) * p.tcontrib_coef.size());
+  L.batches = o; o = align256(o + sizeof(bbc::WarpBatch) * c->batches.size());
+  L.wptr = o; o = align256(o + sizeof(int) * c->wptr.size());
+  L.wunits = o; o = align256(o + sizeof(int4) * c->wunits.size());
+  L.qlist = o; o = align256(o + sizeof(int) * c->qlist.size());
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -50,8 +55,9 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.amax = o; o = align256(o + (size_t)slots * 2 * sizeof(unsigned long long));
   L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
   L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
-  L.blkf = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
-  L.P = o; o = align256(o + (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec));
+  const bool fp64 = c->prec == BBC_FP64;  // the FP32 path keeps q-major blocks and no product buffer
+  L.blkf = o; o = align256(o + (fp64 ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
+  L.P = o; o = align256(o + (fp64 ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
   L.total = o;
@@ -146,6 +152,13 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   // warp task groups of the pair products: enough warps per 32 q to fill the
   // GPU several times over at L = 16 (V/32 q tiles x groups warps)
   bbc::make_task_groups(c->plan, 48, &c->group_ptr, &c->group_task);
+  // fused FP32 contraction: warp batches and one q of every pair {q, -q}
+  bbc::make_warp_batches(c->plan, bbc::kFusedWarps, 36, &c->batches, &c->wptr, &c->wunits);
+  for (int q = 0; q < c->V; q++) {
+    const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
+    const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
+    if (q <= nq) c->qlist.push_back(q);
+  }
   *ctx = c;
   return BBC_OK;
 }
@@ -180,6 +193,10 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_cptr = (int*)(w + L.cptr);
   c->d_citem = (int*)(w + L.citem);
   c->d_ccoef = (double*)(w + L.ccoef);
+  c->d_batches = (bbc::WarpBatch*)(w + L.batches);
+  c->d_wptr = (int*)(w + L.wptr);
+  c->d_wunits = (int4*)(w + L.wunits);
+  c->d_qlist = (int*)(w + L.qlist);
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
   c->d_amax = (unsigned long long*)(w + L.amax);
@@ -204,6 +221,15 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     d.sA = t.sA1 | (t.sA2 << 16);
     d.sB = t.sB1 | (t.sB2 << 16);
   }
+  std::vector<bbc::WarpBatch> wb(c->batches.size());
+  for (size_t i = 0; i < c->batches.size(); i++) {
+    wb[i].n = (int)c->batches[i].tasks.size();
+    wb[i].nA = c->batches[i].nA;
+    for (int j = 0; j < 32; j++) wb[i].task[j] = j < wb[i].n ? c->batches[i].tasks[j] : 0;
+  }
+  std::vector<int4> wu(c->wunits.size());
+  for (size_t i = 0; i < c->wunits.size(); i++)
+    wu[i] = make_int4(c->wunits[i].batch, c->wunits[i].side, c->wunits[i].k0, c->wunits[i].k1);
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
@@ -214,6 +240,10 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_cptr, p.tcontrib_ptr.data(), sizeof(int) * p.tcontrib_ptr.size()},
       {c->d_citem, p.tcontrib_item.data(), sizeof(int) * p.tcontrib_item.size()},
       {c->d_ccoef, p.tcontrib_coef.data(), sizeof(double) * p.tcontrib_coef.size()},
+      {c->d_batches, wb.data(), sizeof(bbc::WarpBatch) * wb.size()},
+      {c->d_wptr, c->wptr.data(), sizeof(int) * c->wptr.size()},
+      {c->d_wunits, wu.data(), sizeof(int4) * wu.size()},
+      {c->d_qlist, c->qlist.data(), sizeof(int) * c->qlist.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -286,7 +316,9 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   }
   {
     StageScope scope(c, BBC_STAGE_FFT_FWD);
-    e = bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream);
+    // FP64: field-major copy for the lanes-over-q products; FP32: in place, q-major
+    e = fp64 ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
+             : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
   }
   for (int s = 0; s < n_slots; s++) c->slot_built[s] = 1;
@@ -302,18 +334,27 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   const bool fp64 = c->prec == BBC_FP64;
   const bbc::Plan& p = c->plan;
   const int n_ch = (int)p.channels.size();
-  const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
   cudaError_t e;
-  {
+  if (fp64) {
+    const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+    {
+      StageScope scope(c, BBC_STAGE_CONTRACT);
+      e = bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                    (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "pair products");
+    }
+    {
+      StageScope scope(c, BBC_STAGE_WICK);
+      e = bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
+    }
+  } else {
+    const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
     StageScope scope(c, BBC_STAGE_CONTRACT);
-    e = bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
-                                  (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "pair products");
-  }
-  {
-    StageScope scope(c, BBC_STAGE_WICK);
-    e = bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
+    e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_qlist, (int)c->qlist.size(), c->d_tasks,
+                                   (int)p.tasks.size(), c->d_batches, c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem,
+                                   c->d_ccoef, n_ch, c->d_ct, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fused contraction");
   }
   bbc::ScaleParams sp{};
   sp.n_ch = n_ch;
@@ -333,7 +374,8 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   }
   {
     StageScope scope(c, BBC_STAGE_FFT_INV);
-    e = bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
+    e = fp64 ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
+             : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
   return BBC_OK;

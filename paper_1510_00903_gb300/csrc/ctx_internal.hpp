@@ -31,8 +31,17 @@ struct bbc_ctx {
   int* d_cptr = nullptr;
   int* d_citem = nullptr;
   double* d_ccoef = nullptr;
-  std::vector<int> group_ptr;            // warp task groups of the pair products
+  std::vector<int> group_ptr;            // warp task groups of the pair products (FP64)
   std::vector<int> group_task;
+  // fused FP32 contraction: warp batches, per-warp units, one q per pair {q, -q}
+  std::vector<bbc::Batch> batches;
+  std::vector<int> wptr;
+  std::vector<bbc::BatchUnit> wunits;
+  std::vector<int> qlist;
+  bbc::WarpBatch* d_batches = nullptr;
+  int* d_wptr = nullptr;
+  int4* d_wunits = nullptr;
+  int* d_qlist = nullptr;
   char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
   char* d_prop = nullptr;                // [slots][2][V*144] compute precision
   unsigned long long* d_amax = nullptr;  // [slots][2]

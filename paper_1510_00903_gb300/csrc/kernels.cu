@@ -333,7 +333,9 @@ __device__ __forceinline__ void line_base(int N, int axis, int line, int& base, 
 // over the line index, which is contiguous for the y and z passes.
 // Mode FIELD2OUT (z axis): in[ch][s][V] -> out[ch][r][16] times scale[ch]
 // (the last inverse pass writes the output layout and normalises it).
-enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2 };
+// Mode SITE (any axis, in place): data[o][site][n_inner], lanes over inner.
+// Mode SITE2OUT (z axis): in[site][n_ch*16] -> out[ch][r][16] times scale[ch].
+enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4 };
 
 template <typename S, typename R, int N, bool INV, int MODE>
 __global__ void __launch_bounds__(256)
@@ -344,7 +346,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
   const long long V = (long long)N * N * N;
   int line, inner;
   long long o;
-  if (MODE == FFT_SITE2FIELD) {
+  if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
     if (gid >= n_outer * lines * n_inner) return;
     inner = (int)(gid % n_inner);
     const long long rest = gid / n_inner;
@@ -365,7 +367,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
   int base, stride;
   line_base(N, axis, line, base, stride);
   cpx<R> v[N];
-  if (MODE == FFT_SITE2FIELD) {
+  if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
     line_fft<S, R, N, INV>(in + (o * V + base) * n_inner + inner, (long long)stride * n_inner, v);
   } else if (MODE == FFT_FIELD) {
     line_fft<S, R, N, INV>(in + o * V + base, stride, v);
@@ -380,6 +382,16 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
     cpx<S>* p = out + o * V + base;
 #pragma unroll
     for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+  } else if (MODE == FFT_SITE) {
+    cpx<S>* p = out + (o * V + base) * n_inner + inner;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[(long long)k * stride * n_inner] = cpx<S>(v[k]);
+  } else if (MODE == FFT_SITE2OUT) {
+    // inner = channel * 16 + spin; out[ch][r][16]
+    const R f = (R)scale[inner >> 4];
+    cpx<S>* p = out + ((long long)(inner >> 4) * V + base) * 16 + (inner & 15);
+#pragma unroll
+    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<S>(cpx<R>(v[k].re * f, v[k].im * f));
   } else {
     const R f = (R)scale[o];
 #pragma unroll
@@ -393,7 +405,8 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
 template <typename S, typename R, int MODE>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
                                 const double* scale, cudaStream_t st) {
-  long long per = (MODE == FFT_SITE2FIELD) ? n_inner : (MODE == FFT_FIELD ? 1 : 16);
+  long long per = (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) ? n_inner
+                  : (MODE == FFT_FIELD ? 1 : 16);
   long long total = n_outer * (long long)L * L * per;
   unsigned blocks = (unsigned)((total + 255) / 256);
   const cpx<S>* i = (const cpx<S>*)in;
@@ -438,6 +451,27 @@ cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int
     }
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st) {
+  for (int axis = 0; axis < 3; axis++) {
+    cudaError_t e = fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st)
+                         : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                                    cudaStream_t st) {
+  cudaError_t e;
+  for (int axis = 0; axis < 2; axis++) {
+    e = fp64_compute ? fft_dispatch<double, double, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st)
+                     : fft_dispatch<double, float, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return fp64_compute ? fft_dispatch<double, double, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st)
+                      : fft_dispatch<double, float, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
 }
 
 cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
@@ -580,6 +614,123 @@ cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* c
   dim3 g2((V + 127) / 128, n_ch * 16);
   if (fp64) k_wick_sums<double><<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
   else k_wick_sums<float><<<g2, 128, 0, st>>>((const cpx<float>*)P, V, cptr, citem, ccoef, (cpx<double>*)ct);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- fused contraction (FP32)
+// One CTA per pair {q, -q}: both q-rows of the q-major Fourier-space blocks
+// (blk[q][n_out]) are staged in shared memory once, every block element is
+// thus read from HBM exactly once.  Warps run units (batch of up to 32 tasks
+// of one shape and one open-index length, side, k range): lane l takes task
+// l of the batch, so control flow is uniform within the warp.  Side 0 forms
+// A(q) B(-q), side 1 A(-q) B(q).  Products accumulate in FP32 registers and
+// are added into P[side][task*16 + spin pair] in shared memory; the signed
+// FP64 sums over Wick diagrams then run in the same CTA and write ct[q][o].
+template <int NA, int NB>
+__device__ __forceinline__ void unit_products_smem(const cpx<float>* __restrict__ A, const cpx<float>* __restrict__ B,
+                                                   const DevTask& t, int k0, int k1, cpx<float>* P) {
+  const int n2 = t.n2;
+  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
+  int i1 = k0 / n2, i2 = k0 - i1 * n2;
+  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
+  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
+  cpx<float> acc[NA * NB];
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) acc[i] = cpx<float>(0.f, 0.f);
+  for (int k = k0; k < k1; k++) {
+    cpx<float> a[NA], b[NB];
+#pragma unroll
+    for (int r = 0; r < NA; r++) a[r] = A[t.offA[r] + oA];
+#pragma unroll
+    for (int r = 0; r < NB; r++) b[r] = B[t.offB[r] + oB];
+#pragma unroll
+    for (int ra = 0; ra < NA; ra++)
+#pragma unroll
+      for (int rb = 0; rb < NB; rb++) cmac(acc[ra * NB + rb], a[ra], b[rb]);
+    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
+    else { oA += sA2; oB += sB2; }
+  }
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) {
+    atomicAdd(&P[i].re, acc[i].re);
+    atomicAdd(&P[i].im, acc[i].im);
+  }
+}
+
+constexpr int kFusedThreads = 512;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ qlist,
+                 const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
+                 const int* __restrict__ wptr, const int4* __restrict__ wunits, const int* __restrict__ cptr,
+                 const int* __restrict__ citem, const double* __restrict__ ccoef, int n_outputs,
+                 cpx<double>* __restrict__ ct) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  cpx<float>* rows = reinterpret_cast<cpx<float>*>(smem_raw);  // [2][n_out]
+  cpx<float>* P = rows + 2 * n_out;                              // [2][n_tasks * 16]
+  const int q = qlist[blockIdx.x];
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
+  const bool self = nq == q;
+  {
+    const int n16 = n_out / 2;  // float4 = two complex values (n_out is even)
+    const float4* s0 = reinterpret_cast<const float4*>(blk + (size_t)q * n_out);
+    const float4* s1 = reinterpret_cast<const float4*>(blk + (size_t)nq * n_out);
+    float4* d = reinterpret_cast<float4*>(rows);
+    for (int i = tid; i < n16; i += kFusedThreads) {
+      d[i] = __ldg(s0 + i);
+      d[n16 + i] = self ? d[i] : __ldg(s1 + i);
+    }
+    float4* pz = reinterpret_cast<float4*>(P);
+    for (int i = tid; i < n_tasks * 16; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const int u1 = wptr[warp + 1];
+  for (int u = wptr[warp]; u < u1; u++) {
+    const int4 un = wunits[u];  // batch, side, k0, k1
+    if (self && un.y == 1) continue;
+    const WarpBatch& wb = batches[un.x];
+    if (lane >= wb.n) continue;
+    const int ti = wb.task[lane];
+    const DevTask t = tasks[ti];
+    const cpx<float>* A = rows + un.y * n_out;
+    const cpx<float>* B = rows + (1 - un.y) * n_out;
+    cpx<float>* p = P + (un.y * n_tasks + ti) * 16;
+    if (wb.nA == 4) unit_products_smem<4, 4>(A, B, t, un.z, un.w, p);
+    else if (wb.nA == 2) unit_products_smem<2, 8>(A, B, t, un.z, un.w, p);
+    else unit_products_smem<8, 2>(A, B, t, un.z, un.w, p);
+  }
+  __syncthreads();
+  const int sides = self ? 1 : 2;
+  for (int j = tid; j < sides * n_outputs; j += kFusedThreads) {
+    const int side = j / n_outputs, o = j - side * n_outputs;
+    const cpx<float>* Ps = P + side * n_tasks * 16;
+    cpx<double> acc(0, 0);
+    const int c1 = cptr[o + 1];
+    for (int c = cptr[o]; c < c1; c++) {
+      const double w = ccoef[c];
+      const cpx<float> v = Ps[citem[c]];
+      acc.re = fma(w, (double)v.re, acc.re);
+      acc.im = fma(w, (double)v.im, acc.im);
+    }
+    ct[(size_t)(side ? nq : q) * n_outputs + o] = acc;
+  }
+}
+
+size_t contract_fused_smem(int n_out, int n_tasks) {
+  return (size_t)(2 * n_out + 2 * n_tasks * 16) * sizeof(cpx<float>);
+}
+
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+                                  int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
+                                  const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
+                                  cudaStream_t st) {
+  const size_t sm = contract_fused_smem(n_out, n_tasks);
+  cudaError_t e = cudaFuncSetAttribute(k_contract_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, batches,
+                                                   wptr, wunits, cptr, citem, ccoef, n_ch * 16, (cpx<double>*)ct);
   return cudaGetLastError();
 }
 

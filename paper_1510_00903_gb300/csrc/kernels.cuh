@@ -18,6 +18,12 @@ struct DevTask {
   int sB;    // sB1 | sB2 << 16
 };
 
+// A warp batch: up to 32 tasks of one shape (nA) and one open-index length.
+struct WarpBatch {
+  int n, nA;
+  int task[32];
+};
+
 struct DevGroups {  // block-build groups (rows that read the same tensor families)
   int n;
   int first[8], rows[8], fam0[8], fam1[8];
@@ -53,6 +59,22 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* 
 // then the y and z passes in place (exp(-i q.x), unnormalised).
 cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
                                cudaStream_t st);
+// Forward 3-D FFT in place on site-major blocks blk[slots][V][n_rows] (lanes
+// over the contiguous row index); output is q-major.
+cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st);
+// Inverse 3-D FFT of q-major ct[V][n_ch*16] (complex128, x and y in place),
+// the z pass writing out[n_ch][V][16] multiplied by scale[ch].
+cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                                    cudaStream_t st);
+// Fused FP32 contraction of one slice from q-major blocks blk[V][n_out]: one
+// CTA per pair {q, -q} (qlist[n_q]), warp units wunits {batch, side, k0, k1}
+// (warp w owns wunits[wptr[w] .. wptr[w+1])), FP64 Wick sums into ct[V][n_ch*16].
+constexpr int kFusedWarps = 16;
+size_t contract_fused_smem(int n_out, int n_tasks);
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+                                  int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
+                                  const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
+                                  cudaStream_t st);
 // Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z
 // pass writing out[n_ch][V][16] (complex128) multiplied by scale[ch].
 cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,

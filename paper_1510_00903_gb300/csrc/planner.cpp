@@ -623,6 +623,51 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   return true;
 }
 
+void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch>* batches, std::vector<int>* warp_ptr,
+                       std::vector<BatchUnit>* units) {
+  std::map<std::array<int, 3>, std::vector<int>> cls;
+  for (int t = 0; t < (int)plan.tasks.size(); t++) {
+    const PairTask& k = plan.tasks[t];
+    cls[{k.nA, k.nB, k.n1 * k.n2}].push_back(t);
+  }
+  batches->clear();
+  std::vector<BatchUnit> all;
+  for (auto& kv : cls) {
+    const int K = kv.first[2];
+    for (size_t i = 0; i < kv.second.size(); i += 32) {
+      Batch b;
+      b.nA = kv.first[0];
+      for (size_t j = i; j < kv.second.size() && j < i + 32; j++) b.tasks.push_back(kv.second[j]);
+      const int id = (int)batches->size();
+      batches->push_back(b);
+      const int step = K > chunk ? chunk : K;
+      for (int side = 0; side < 2; side++)
+        for (int k = 0; k < K; k += step) all.push_back(BatchUnit{id, side, k, std::min(K, k + step)});
+    }
+  }
+  auto cost = [&](const BatchUnit& u) {
+    const Batch& b = (*batches)[u.batch];
+    const int nB = 16 / b.nA;
+    return (long long)(u.k1 - u.k0) * (64 + 2 * (b.nA + nB)) + 64;
+  };
+  std::stable_sort(all.begin(), all.end(), [&](const BatchUnit& a, const BatchUnit& b) { return cost(a) > cost(b); });
+  std::vector<long long> load(warps, 0);
+  std::vector<std::vector<BatchUnit>> per(warps);
+  for (const BatchUnit& u : all) {
+    int best = 0;
+    for (int w = 1; w < warps; w++)
+      if (load[w] < load[best]) best = w;
+    load[best] += cost(u);
+    per[best].push_back(u);
+  }
+  warp_ptr->assign(1, 0);
+  units->clear();
+  for (auto& v : per) {
+    for (auto& u : v) units->push_back(u);
+    warp_ptr->push_back((int)units->size());
+  }
+}
+
 void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task) {
   std::vector<int> order(plan.tasks.size());
   std::iota(order.begin(), order.end(), 0);

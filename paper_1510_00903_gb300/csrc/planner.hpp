@@ -71,6 +71,20 @@ void channel_names(int id, const char* out[4]);
 // Build the plan; returns false and sets *err on a bad channel list.
 bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
 
+// Warp batches for the fused contraction: tasks grouped by (nA, nB, n1*n2),
+// at most 32 per batch (one per lane); units (batch, side, k0, k1) split open
+// indices longer than `chunk`; units go longest first to the least loaded of
+// `warps` warps.  Output: batches (nA, task ids), warp_ptr[warps + 1], units.
+struct Batch {
+  int nA;
+  std::vector<int> tasks;
+};
+struct BatchUnit {
+  int batch, side, k0, k1;
+};
+void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch>* batches, std::vector<int>* warp_ptr,
+                       std::vector<BatchUnit>* units);
+
 // Partition of the tasks into `groups` lists of near-equal cost (longest task
 // first to the cheapest list); each list is run by one warp for 32 q at a time.
 void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task);
