@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--error-report", action="store_true",
+                    help="per-channel error of the mixed path against the FP64 path (L=32, T=64, t=32), "
+                         "the FP64 path checked against the oracle at sampled points")
     ap.add_argument("--single-slice", choices=["fp64", "mixed"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
     return ap.parse_args()
@@ -173,6 +176,8 @@ def main():
     _build.build()
     from paper_1510_00903_gb300 import bbc
 
+    if args.error_report:
+        return error_report(torch, dev, bbc, synth)
     L, T = L_BENCH, T_BENCH
     V = L ** 3
     if args.single_slice:
@@ -301,6 +306,31 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def error_report(torch, dev, bbc, synth):
+    """Per-channel max |mixed - fp64| / max |fp64| over r and spin on one slice
+    of the L=32, T=64 workload; the FP64 result against the oracle at r = 0
+    and two random r for four channels."""
+    import oracle.oracle as orc
+    L, T, t = 32, 64, 32
+    F = synth.flavour_set(L, T, 0, M_UD, M_S, seed=3, times=[t])
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    res = {}
+    for name, prec in (("fp64", bbc.BBC_FP64), ("mixed", bbc.BBC_MIXED_FP32)):
+        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
+        res[name] = cor.run(Sl, Ss, [t], normalised=True)[0].cpu().numpy()
+        cor.close()
+    a, b = res["mixed"], res["fp64"]
+    scale = np.abs(b).reshape(N_CH, -1).max(axis=1)
+    err = np.abs(a - b).reshape(N_CH, -1).max(axis=1) / scale
+    chans, r_list = [0, 10, 41, 51], [0, 12345, 30001]
+    want = orc.normalise(orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], chans, r_list), chans, t, M_UD, M_S)
+    o_err = float((np.abs(b[chans][:, r_list] - want).reshape(len(chans), -1).max(axis=1) / scale[chans]).max())
+    print(json.dumps({"report": "mixed precision error per channel", "L": L, "T": T, "t": t,
+                      "metric": "max_{r,s}|C_mixed - C_fp64| / max_{r,s}|C_fp64|",
+                      "per_channel": [float(x) for x in err], "max": float(err.max()), "median": float(np.median(err)),
+                      "fp64_vs_oracle_sampled": o_err}), flush=True)
 
 
 class _Null:

@@ -628,7 +628,7 @@ cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* c
 // FP64 sums over Wick diagrams then run in the same CTA and write ct[q][o].
 template <int NA, int NB>
 __device__ __forceinline__ void unit_products_smem(const cpx<float>* __restrict__ A, const cpx<float>* __restrict__ B,
-                                                   const DevTask& t, int k0, int k1, cpx<float>* P) {
+                                                   const DevTask& t, int k0, int k1, cpx<float>* P, int rot) {
   const int n2 = t.n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
   int i1 = k0 / n2, i2 = k0 - i1 * n2;
@@ -650,10 +650,13 @@ __device__ __forceinline__ void unit_products_smem(const cpx<float>* __restrict_
     if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
     else { oA += sA2; oB += sB2; }
   }
+  // P slot of product i of task ti: ti*16 + ((i + ti) & 15) -- the rotation
+  // spreads the 32 lanes' (distinct tasks') slots over the shared-memory banks
 #pragma unroll
   for (int i = 0; i < NA * NB; i++) {
-    atomicAdd(&P[i].re, acc[i].re);
-    atomicAdd(&P[i].im, acc[i].im);
+    cpx<float>* d = P + ((i + rot) & 15);
+    atomicAdd(&d->re, acc[i].re);
+    atomicAdd(&d->im, acc[i].im);
   }
 }
 
@@ -697,9 +700,9 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
     const cpx<float>* A = rows + un.y * n_out;
     const cpx<float>* B = rows + (1 - un.y) * n_out;
     cpx<float>* p = P + (un.y * n_tasks + ti) * 16;
-    if (wb.nA == 4) unit_products_smem<4, 4>(A, B, t, un.z, un.w, p);
-    else if (wb.nA == 2) unit_products_smem<2, 8>(A, B, t, un.z, un.w, p);
-    else unit_products_smem<8, 2>(A, B, t, un.z, un.w, p);
+    if (wb.nA == 4) unit_products_smem<4, 4>(A, B, t, un.z, un.w, p, ti);
+    else if (wb.nA == 2) unit_products_smem<2, 8>(A, B, t, un.z, un.w, p, ti);
+    else unit_products_smem<8, 2>(A, B, t, un.z, un.w, p, ti);
   }
   __syncthreads();
   const int sides = self ? 1 : 2;
@@ -710,7 +713,8 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
     const int c1 = cptr[o + 1];
     for (int c = cptr[o]; c < c1; c++) {
       const double w = ccoef[c];
-      const cpx<float> v = Ps[citem[c]];
+      const int it = citem[c], ti = it >> 4;
+      const cpx<float> v = Ps[(ti << 4) + ((it + ti) & 15)];
       acc.re = fma(w, (double)v.re, acc.re);
       acc.im = fma(w, (double)v.im, acc.im);
     }

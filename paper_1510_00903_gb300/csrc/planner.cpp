@@ -634,10 +634,21 @@ void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch
   std::vector<BatchUnit> all;
   for (auto& kv : cls) {
     const int K = kv.first[2];
-    for (size_t i = 0; i < kv.second.size(); i += 32) {
+    // order the class so that each run of 32 tasks cycles through the 16
+    // residues of offA[0] mod 16: the lanes' shared-memory rows then fall on
+    // distinct bank pairs (a complex FP32 value spans two banks)
+    std::vector<std::vector<int>> by_res(16);
+    for (int t : kv.second) by_res[plan.tasks[t].offA[0] & 15].push_back(t);
+    std::vector<int> order;
+    for (bool left = true; left;) {
+      left = false;
+      for (auto& v : by_res)
+        if (!v.empty()) { order.push_back(v.back()); v.pop_back(); left = true; }
+    }
+    for (size_t i = 0; i < order.size(); i += 32) {
       Batch b;
       b.nA = kv.first[0];
-      for (size_t j = i; j < kv.second.size() && j < i + 32; j++) b.tasks.push_back(kv.second[j]);
+      for (size_t j = i; j < order.size() && j < i + 32; j++) b.tasks.push_back(order[j]);
       const int id = (int)batches->size();
       batches->push_back(b);
       const int step = K > chunk ? chunk : K;
