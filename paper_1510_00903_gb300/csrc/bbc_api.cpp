@@ -37,7 +37,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   size_t o = 0;
   L.row_ptr = o; o = align256(o + sizeof(int) * p.row_ptr.size());
   L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
-  L.zneed = o; o = align256(o + sizeof(uint16_t) * p.zneed.size());
+  L.zneed = o; o = align256(o + sizeof(uint32_t) * p.zneed.size());
   L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
   L.group_ptr = o; o = align256(o + sizeof(int) * c->group_ptr.size());
   L.group_task = o; o = align256(o + sizeof(int) * c->group_task.size());
@@ -115,6 +115,7 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
     g.fam1[i] = p.groups[i].fam[1];
   }
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
+  g.z_slots = p.z_slots;
   return g;
 }
 
@@ -186,7 +187,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->slots = slices;
   c->d_row_ptr = (int*)(w + L.row_ptr);
   c->d_entries = (uint32_t*)(w + L.entries);
-  c->d_zneed = (uint16_t*)(w + L.zneed);
+  c->d_zneed = (uint32_t*)(w + L.zneed);
   c->d_tasks = (bbc::DevTask*)(w + L.tasks);
   c->d_group_ptr = (int*)(w + L.group_ptr);
   c->d_group_task = (int*)(w + L.group_task);
@@ -233,7 +234,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
-      {c->d_zneed, p.zneed.data(), sizeof(uint16_t) * p.zneed.size()},
+      {c->d_zneed, p.zneed.data(), sizeof(uint32_t) * p.zneed.size()},
       {c->d_tasks, tasks.data(), sizeof(bbc::DevTask) * tasks.size()},
       {c->d_group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size()},
       {c->d_group_task, c->group_task.data(), sizeof(int) * c->group_task.size()},

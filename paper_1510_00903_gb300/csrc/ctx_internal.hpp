@@ -24,7 +24,7 @@ struct bbc_ctx {
   int slots = 0;
   int* d_row_ptr = nullptr;
   uint32_t* d_entries = nullptr;
-  uint16_t* d_zneed = nullptr;
+  uint32_t* d_zneed = nullptr;
   bbc::DevTask* d_tasks = nullptr;
   int* d_group_ptr = nullptr;
   int* d_group_task = nullptr;

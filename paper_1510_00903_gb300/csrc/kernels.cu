@@ -201,13 +201,13 @@ constexpr int kBuildThreads = 256;
 template <typename R>
 __global__ void __launch_bounds__(kBuildThreads)
 k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ row_ptr,
-              const uint32_t* __restrict__ entries, const uint16_t* __restrict__ zneed, DevGroups g,
+              const uint32_t* __restrict__ entries, const uint32_t* __restrict__ zneed, DevGroups g,
               cpx<R>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][144]  light, strange
   cpx<R>* sD = sS + 288;                              // [2][432]  diquarks (l,l), (l,s)
-  cpx<R>* sZ = sD + 864;                              // [2][3456] sink-tensor families
-  R* sW = reinterpret_cast<R*>(sZ + 2 * 3456);        // weights -16..15 (no int->float conversion per term)
+  cpx<R>* sZ = sD + 864;                              // [g.z_slots] the tensor entries the rows read
+  R* sW = reinterpret_cast<R*>(sZ + g.z_slots);       // weights -16..15 (no int->float conversion per term)
   const int site = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
   if (tid < 32) sW[tid] = (R)(tid - 16);
   const cpx<R>* P = prop + (size_t)slot * 2 * V * 144;
@@ -238,7 +238,8 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
     // the tensor entries this group reads (and the previous group did not leave)
     const int z1 = g.zneed_first[gi + 1];
     for (int j = g.zneed_first[gi] + tid; j < z1; j += kBuildThreads) {
-      const int zi = zneed[j], sl = zi / 3456, i = zi % 3456;
+      const uint32_t zn = zneed[j];
+      const int pos = zn & 0x1fff, sl = (zn >> 13) & 1, i = zn >> 14;
       const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
       // F[a][e0][e1][e2] = sum_c2 D[e0][e1][c2] S_f2[(a,c2),e2]
       const int dq = (fam == 2 || fam == 3) ? 1 : 0;  // LSL, LSS read the (l,s) diquark
@@ -249,7 +250,7 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
       cpx<R> acc(0, 0);
 #pragma unroll
       for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);
-      sZ[zi] = acc;
+      sZ[pos] = acc;
     }
     __syncthreads();
     const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
@@ -271,17 +272,17 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
 }
 
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const uint16_t* zneed, const DevGroups& g, void* blk,
+                               const uint32_t* entries, const uint32_t* zneed, const DevGroups& g, void* blk,
                                int n_out, bool fp64, cudaStream_t st) {
   dim3 grid(V, n_slots);
   if (fp64) {
-    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<double>) + 32 * sizeof(double);
+    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<double>) + 32 * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_block_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, zneed,
                                                            g, (cpx<double>*)blk, n_out);
   } else {
-    size_t sm = (288 + 864 + 2 * 3456) * sizeof(cpx<float>) + 32 * sizeof(float);
+    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<float>) + 32 * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_block_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, zneed,

@@ -28,6 +28,7 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int n;
   int first[8], rows[8], fam0[8], fam1[8];
   int zneed_first[9];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
+  int z_slots;         // shared-memory positions for tensor entries
 };
 
 constexpr int kMaxChannels = 64;
@@ -52,7 +53,7 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
                            cudaStream_t st);
 // Baryon blocks of every site: prop [slots][2][V][144], blk [slots][V][n_out].
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const uint16_t* zneed, const DevGroups& g,
+                               const uint32_t* entries, const uint32_t* zneed, const DevGroups& g,
                                void* blk, int n_out, bool fp64, cudaStream_t st);
 // Forward 3-D FFT of every block field: x pass from the site-major build
 // output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],

@@ -470,28 +470,47 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   }
   P.n_out = row;
   P.n_blocks = (int)ublocks.size();
-  // entries each group computes: those its rows read, minus those the previous
-  // group left in the same slot for the same family
+  // Compact shared-memory storage of the tensor entries: each group gets
+  // positions for the entries its rows read; an entry the previous group left
+  // in place (same family in the same slot) keeps its position, so it is
+  // neither recomputed nor moved.  entries[] are rewritten to positions.
   {
-    std::vector<char> prev(2 * kFamEntries, 0);
+    std::map<int, int> live;  // (slot * kFamEntries + local) -> position, valid for the current families
     int prev_fam[2] = {-1, -1};
     P.zneed_first.push_back(0);
+    P.z_slots = 0;
     for (const GroupInfo& gi : P.groups) {
-      std::vector<char> need(2 * kFamEntries, 0);
-      for (int r = gi.first_row; r < gi.first_row + gi.n_rows; r++)
-        for (int k = P.row_ptr[r]; k < P.row_ptr[r + 1]; k++) need[P.entries[k] & 0xffffu] = 1;
-      for (int z = 0; z < 2 * kFamEntries; z++) {
-        const int sl = z / kFamEntries;
-        const bool valid = prev[z] && prev_fam[sl] == gi.fam[sl];
-        if (need[z] && !valid) P.zneed.push_back((uint16_t)z);
-      }
-      for (int sl = 0; sl < 2; sl++) {
+      // drop entries of a slot whose family changes
+      for (int sl = 0; sl < 2; sl++)
         if (gi.fam[sl] != prev_fam[sl])
-          for (int z = sl * kFamEntries; z < (sl + 1) * kFamEntries; z++) prev[z] = 0;
-        prev_fam[sl] = gi.fam[sl];
-      }
-      for (int z = 0; z < 2 * kFamEntries; z++)
-        if (need[z]) prev[z] = 1;
+          for (auto it = live.begin(); it != live.end();) {
+            if (it->first / kFamEntries == sl) it = live.erase(it);
+            else ++it;
+          }
+      std::vector<char> used(8192, 0);
+      for (auto& kv : live) used[kv.second] = 1;
+      int next = 0;
+      for (int r = gi.first_row; r < gi.first_row + gi.n_rows; r++)
+        for (int k = P.row_ptr[r]; k < P.row_ptr[r + 1]; k++) {
+          const int z = (int)(P.entries[k] & 0xffffu);
+          auto it = live.find(z);
+          int pos;
+          if (it == live.end()) {
+            while (next < 8192 && used[next]) next++;
+            if (next >= 8192) { *err = "internal: tensor positions"; return false; }
+            pos = next;
+            used[pos] = 1;
+            live.emplace(z, pos);
+            const int sl = z / kFamEntries, local = z % kFamEntries;
+            P.zneed.push_back((uint32_t)pos | ((uint32_t)sl << 13) | ((uint32_t)local << 14));
+          } else {
+            pos = it->second;
+          }
+          P.entries[k] = (P.entries[k] & 0xffff0000u) | (uint32_t)pos;
+          P.z_slots = std::max(P.z_slots, pos + 1);
+        }
+      prev_fam[0] = gi.fam[0];
+      prev_fam[1] = gi.fam[1];
       P.zneed_first.push_back((int)P.zneed.size());
     }
   }
@@ -617,7 +636,9 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   for (int id : P.tcontrib_item)
     if (id < 0 || id >= 16 * (int)P.tasks.size()) { *err = "internal: task contribution index"; return false; }
   for (uint32_t e : P.entries)
-    if ((e & 0xffffu) >= 2u * kFamEntries) { *err = "internal: tensor index"; return false; }
+    if ((int)(e & 0xffffu) >= P.z_slots) { *err = "internal: tensor position"; return false; }
+  for (uint32_t z : P.zneed)
+    if ((int)(z & 0x1fffu) >= P.z_slots || (z >> 14) >= (uint32_t)kFamEntries) { *err = "internal: tensor entry"; return false; }
   if ((int)P.row_ptr.size() != P.n_out + 1) { *err = "internal: row table"; return false; }
   *plan = std::move(P);
   return true;

@@ -48,10 +48,11 @@ struct Plan {
   int n_blocks = 0;
   std::vector<GroupInfo> groups;
   std::vector<int> row_ptr;          // n_out + 1
-  std::vector<uint32_t> entries;     // low 16 bits: tensor index (slot*3456 + a*1728 + e0*144 + e1*12 + e2),
+  std::vector<uint32_t> entries;     // low 16 bits: compact position of a tensor entry in shared memory,
                                      // high 16 bits: signed integer weight
-  std::vector<uint16_t> zneed;       // tensor entries each group computes (group-major)
+  std::vector<uint32_t> zneed;       // entries each group computes: pos | slot << 13 | (a*1728 + e0*144 + e1*12 + e2) << 14
   std::vector<int> zneed_first;      // groups + 1 offsets into zneed
+  int z_slots = 0;                   // shared-memory positions needed (max over groups)
   // contraction: unique aligned pair products and their signed sums into channels
   std::vector<PairTask> tasks;       // products of block pairs; P index = task*16 + rA*nB + rB
   std::vector<int> tcontrib_ptr;     // n_channels*16 + 1, contributions over task products

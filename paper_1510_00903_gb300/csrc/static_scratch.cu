@@ -44,7 +44,7 @@ StaticLayout static_layout(const bbc_ctx* c) {
   size_t o = 0;
   L.row_ptr = o; o = a256(o + sizeof(int) * p.row_ptr.size());
   L.entries = o; o = a256(o + sizeof(uint32_t) * p.entries.size());
-  L.zneed = o; o = a256(o + sizeof(uint16_t) * p.zneed.size());
+  L.zneed = o; o = a256(o + sizeof(uint32_t) * p.zneed.size());
   L.tasks = o; o = a256(o + sizeof(bbc::DevTask) * p.tasks.size());
   L.group_ptr = o; o = a256(o + sizeof(int) * c->group_ptr.size());
   L.group_task = o; o = a256(o + sizeof(int) * c->group_task.size());
@@ -115,7 +115,7 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
       {L.row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {L.entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
-      {L.zneed, p.zneed.data(), sizeof(uint16_t) * p.zneed.size()},
+      {L.zneed, p.zneed.data(), sizeof(uint32_t) * p.zneed.size()},
       {L.group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size()},
       {L.group_task, c->group_task.data(), sizeof(int) * c->group_task.size()},
       {L.cptr, p.tcontrib_ptr.data(), sizeof(int) * p.tcontrib_ptr.size()},
@@ -174,8 +174,9 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
     g.fam1[i] = p.groups[i].fam[1];
   }
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
+  g.z_slots = p.z_slots;
   e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int*)(w + L.row_ptr), (const uint32_t*)(w + L.entries),
-                              (const uint16_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st);
+                              (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   e = bbc::launch_fft_forward(w + L.blk, w + L.blkf, c->lat.L, 1, p.n_out, fp64, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
