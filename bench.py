@@ -41,6 +41,26 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def profiled_traffic(path, kernel_src):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, if the summary was taken on the current kernel source (its
+    SHA-256 is recorded beside the counters); else None."""
+    import hashlib
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith(("kernels_cu_sha256", "dram_bytes_per_launch")):
+            k, v = line.split(":", 1)
+            fields[k.strip().strip("`- ")] = v.strip().strip("`")
+    if fields.get("kernels_cu_sha256") != sha or "dram_bytes_per_launch" not in fields:
+        return None
+    return float(fields["dram_bytes_per_launch"])
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,8 +275,11 @@ def main():
     c_avg_ms = c_ms / max(c_n, 1)
     flops_per_launch = 8.0 * sizes["pair_macs_per_site"] * V
     achieved = flops_per_launch / (c_avg_ms * 1e-3) / 1e12
+    here = os.path.dirname(os.path.abspath(__file__))
+    traffic = profiled_traffic(os.path.join(here, "profiles", "k_pair_products_f64_L16_slice.md"),
+                               os.path.join(here, "paper_1510_00903_gb300", "csrc", "kernels.cu"))
     roofline = {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                 "algorithmic_flop_per_launch": flops_per_launch, "avg_launch_ms": c_avg_ms}
     stage_ms = {k: v[0] / args.steps for k, v in stages.items()}
