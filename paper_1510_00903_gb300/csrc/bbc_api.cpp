@@ -154,7 +154,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   // GPU several times over at L = 16 (V/32 q tiles x groups warps)
   bbc::make_task_groups(c->plan, 48, &c->group_ptr, &c->group_task);
   // fused FP32 contraction: warp batches and one q of every pair {q, -q}
-  bbc::make_warp_batches(c->plan, bbc::kFusedWarps, 36, &c->batches, &c->wptr, &c->wunits);
+  bbc::make_warp_batches(c->plan, bbc::kFusedWarps, 18, &c->batches, &c->wptr, &c->wunits);
   for (int q = 0; q < c->V; q++) {
     const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
     const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));

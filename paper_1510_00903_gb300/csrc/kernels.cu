@@ -15,6 +15,7 @@
 //   normalise   1/V, the rescaling, exp((m_B1 + m_B2) d) (Sec. 2 Eq. 2)
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <utility>
 
@@ -619,35 +620,40 @@ cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* c
 }
 
 // ------------------------------------------------- fused contraction (FP32)
-// One CTA per pair {q, -q}: both q-rows of the q-major Fourier-space blocks
-// (blk[q][n_out]) are staged in shared memory once, every block element is
-// thus read from HBM exactly once.  Warps run units (batch of up to 32 tasks
-// of one shape and one open-index length, side, k range): lane l takes task
-// l of the batch, so control flow is uniform within the warp.  Side 0 forms
-// A(q) B(-q), side 1 A(-q) B(q).  Products accumulate in FP32 registers and
-// are added into P[side][task*16 + spin pair] in shared memory; the signed
-// FP64 sums over Wick diagrams then run in the same CTA and write ct[q][o].
+// One CTA per pair {q, -q}.  The q-row and the -q row of the q-major
+// Fourier-space blocks (blk[q][n_out]) are staged in shared memory once,
+// interleaved as R[i] = (F_q[i], F_-q[i]), so one 16-byte load serves both
+// products A(q) B(-q) (side 0) and A(-q) B(q) (side 1); every block element is
+// read from HBM exactly once.  Warps run units (batch of up to 32 tasks of
+// one shape and one open-index length, k range): lane l takes task l, so
+// control flow is uniform within the warp.  Products accumulate in FP32
+// registers and are added into P[side][task*16 + spin pair] in shared memory.
+// The products are then converted once to FP64 and the signed FP64 sums over
+// Wick diagrams run in the same CTA, writing ct[q][o].
 template <int NA, int NB>
-__device__ __forceinline__ void unit_products_smem(const cpx<float>* __restrict__ A, const cpx<float>* __restrict__ B,
-                                                   const DevTask& t, int k0, int k1, cpx<float>* P, int rot) {
+__device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R, const DevTask& t, int k0, int k1,
+                                                   cpx<float>* P0, cpx<float>* P1, int rot, bool self) {
   const int n2 = t.n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
   int i1 = k0 / n2, i2 = k0 - i1 * n2;
   int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
   const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
-  cpx<float> acc[NA * NB];
+  cpx<float> acc0[NA * NB], acc1[NA * NB];
 #pragma unroll
-  for (int i = 0; i < NA * NB; i++) acc[i] = cpx<float>(0.f, 0.f);
+  for (int i = 0; i < NA * NB; i++) { acc0[i] = cpx<float>(0.f, 0.f); acc1[i] = cpx<float>(0.f, 0.f); }
   for (int k = k0; k < k1; k++) {
-    cpx<float> a[NA], b[NB];
+    float4 a[NA], b[NB];
 #pragma unroll
-    for (int r = 0; r < NA; r++) a[r] = A[t.offA[r] + oA];
+    for (int r = 0; r < NA; r++) a[r] = R[t.offA[r] + oA];
 #pragma unroll
-    for (int r = 0; r < NB; r++) b[r] = B[t.offB[r] + oB];
+    for (int r = 0; r < NB; r++) b[r] = R[t.offB[r] + oB];
 #pragma unroll
     for (int ra = 0; ra < NA; ra++)
 #pragma unroll
-      for (int rb = 0; rb < NB; rb++) cmac(acc[ra * NB + rb], a[ra], b[rb]);
+      for (int rb = 0; rb < NB; rb++) {
+        cmac(acc0[ra * NB + rb], cpx<float>(a[ra].x, a[ra].y), cpx<float>(b[rb].z, b[rb].w));
+        cmac(acc1[ra * NB + rb], cpx<float>(a[ra].z, a[ra].w), cpx<float>(b[rb].x, b[rb].y));
+      }
     if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
     else { oA += sA2; oB += sB2; }
   }
@@ -655,9 +661,14 @@ __device__ __forceinline__ void unit_products_smem(const cpx<float>* __restrict_
   // spreads the 32 lanes' (distinct tasks') slots over the shared-memory banks
 #pragma unroll
   for (int i = 0; i < NA * NB; i++) {
-    cpx<float>* d = P + ((i + rot) & 15);
-    atomicAdd(&d->re, acc[i].re);
-    atomicAdd(&d->im, acc[i].im);
+    cpx<float>* d0 = P0 + ((i + rot) & 15);
+    atomicAdd(&d0->re, acc0[i].re);
+    atomicAdd(&d0->im, acc0[i].im);
+    if (!self) {
+      cpx<float>* d1 = P1 + ((i + rot) & 15);
+      atomicAdd(&d1->re, acc1[i].re);
+      atomicAdd(&d1->im, acc1[i].im);
+    }
   }
 }
 
@@ -671,60 +682,66 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
                  cpx<double>* __restrict__ ct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  cpx<float>* rows = reinterpret_cast<cpx<float>*>(smem_raw);  // [2][n_out]
-  cpx<float>* P = rows + 2 * n_out;                              // [2][n_tasks * 16]
+  const int np = n_tasks * 16;                                        // products per side
+  const size_t region = max((size_t)n_out * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
+  float4* R = reinterpret_cast<float4*>(smem_raw);                     // [n_out] (F_q, F_-q)
+  cpx<double>* Pd = reinterpret_cast<cpx<double>*>(smem_raw);         // [2][np], after the products
+  cpx<float>* P = reinterpret_cast<cpx<float>*>(smem_raw + region);   // [2][np]
   const int q = qlist[blockIdx.x];
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
   const bool self = nq == q;
   {
-    const int n16 = n_out / 2;  // float4 = two complex values (n_out is even)
-    const float4* s0 = reinterpret_cast<const float4*>(blk + (size_t)q * n_out);
-    const float4* s1 = reinterpret_cast<const float4*>(blk + (size_t)nq * n_out);
-    float4* d = reinterpret_cast<float4*>(rows);
-    for (int i = tid; i < n16; i += kFusedThreads) {
-      d[i] = __ldg(s0 + i);
-      d[n16 + i] = self ? d[i] : __ldg(s1 + i);
+    const float2* s0 = reinterpret_cast<const float2*>(blk + (size_t)q * n_out);
+    const float2* s1 = reinterpret_cast<const float2*>(blk + (size_t)nq * n_out);
+    for (int i = tid; i < n_out; i += kFusedThreads) {
+      const float2 x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
+      R[i] = make_float4(x.x, x.y, y.x, y.y);
     }
     float4* pz = reinterpret_cast<float4*>(P);
-    for (int i = tid; i < n_tasks * 16; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < np; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   const int u1 = wptr[warp + 1];
   for (int u = wptr[warp]; u < u1; u++) {
-    const int4 un = wunits[u];  // batch, side, k0, k1
-    if (self && un.y == 1) continue;
+    const int4 un = wunits[u];  // batch, -, k0, k1
     const WarpBatch& wb = batches[un.x];
     if (lane >= wb.n) continue;
     const int ti = wb.task[lane];
     const DevTask t = tasks[ti];
-    const cpx<float>* A = rows + un.y * n_out;
-    const cpx<float>* B = rows + (1 - un.y) * n_out;
-    cpx<float>* p = P + (un.y * n_tasks + ti) * 16;
-    if (wb.nA == 4) unit_products_smem<4, 4>(A, B, t, un.z, un.w, p, ti);
-    else if (wb.nA == 2) unit_products_smem<2, 8>(A, B, t, un.z, un.w, p, ti);
-    else unit_products_smem<8, 2>(A, B, t, un.z, un.w, p, ti);
+    cpx<float>* p0 = P + ti * 16;
+    cpx<float>* p1 = P + np + ti * 16;
+    if (wb.nA == 4) unit_products_pair<4, 4>(R, t, un.z, un.w, p0, p1, ti, self);
+    else if (wb.nA == 2) unit_products_pair<2, 8>(R, t, un.z, un.w, p0, p1, ti, self);
+    else unit_products_pair<8, 2>(R, t, un.z, un.w, p0, p1, ti, self);
   }
   __syncthreads();
+  // products to FP64 once (undoing the slot rotation), over the rows' space
   const int sides = self ? 1 : 2;
+  for (int j = tid; j < sides * np; j += kFusedThreads) {
+    const int side = j / np, it = j - side * np, ti = it >> 4;
+    const cpx<float> v = P[side * np + (ti << 4) + ((it + ti) & 15)];
+    Pd[j] = cpx<double>((double)v.re, (double)v.im);
+  }
+  __syncthreads();
   for (int j = tid; j < sides * n_outputs; j += kFusedThreads) {
     const int side = j / n_outputs, o = j - side * n_outputs;
-    const cpx<float>* Ps = P + side * n_tasks * 16;
+    const cpx<double>* Ps = Pd + side * np;
     cpx<double> acc(0, 0);
     const int c1 = cptr[o + 1];
     for (int c = cptr[o]; c < c1; c++) {
       const double w = ccoef[c];
-      const int it = citem[c], ti = it >> 4;
-      const cpx<float> v = Ps[(ti << 4) + ((it + ti) & 15)];
-      acc.re = fma(w, (double)v.re, acc.re);
-      acc.im = fma(w, (double)v.im, acc.im);
+      const cpx<double> v = Ps[citem[c]];
+      acc.re = fma(w, v.re, acc.re);
+      acc.im = fma(w, v.im, acc.im);
     }
     ct[(size_t)(side ? nq : q) * n_outputs + o] = acc;
   }
 }
 
 size_t contract_fused_smem(int n_out, int n_tasks) {
-  return (size_t)(2 * n_out + 2 * n_tasks * 16) * sizeof(cpx<float>);
+  const size_t np = (size_t)n_tasks * 16;
+  return std::max((size_t)n_out * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
 }
 
 cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,

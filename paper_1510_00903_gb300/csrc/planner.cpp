@@ -673,14 +673,13 @@ void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch
       const int id = (int)batches->size();
       batches->push_back(b);
       const int step = K > chunk ? chunk : K;
-      for (int side = 0; side < 2; side++)
-        for (int k = 0; k < K; k += step) all.push_back(BatchUnit{id, side, k, std::min(K, k + step)});
+      for (int k = 0; k < K; k += step) all.push_back(BatchUnit{id, 0, k, std::min(K, k + step)});
     }
   }
   auto cost = [&](const BatchUnit& u) {
     const Batch& b = (*batches)[u.batch];
     const int nB = 16 / b.nA;
-    return (long long)(u.k1 - u.k0) * (64 + 2 * (b.nA + nB)) + 64;
+    return (long long)(u.k1 - u.k0) * (128 + 4 * (b.nA + nB)) + 128;
   };
   std::stable_sort(all.begin(), all.end(), [&](const BatchUnit& a, const BatchUnit& b) { return cost(a) > cost(b); });
   std::vector<long long> load(warps, 0);

@@ -73,8 +73,8 @@ void channel_names(int id, const char* out[4]);
 bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
 
 // Warp batches for the fused contraction: tasks grouped by (nA, nB, n1*n2),
-// at most 32 per batch (one per lane); units (batch, side, k0, k1) split open
-// indices longer than `chunk`; units go longest first to the least loaded of
+// at most 32 per batch (one per lane); units (batch, k0, k1) cover both sides
+// {q, -q} and split open indices longer than `chunk`; units go longest first to the least loaded of
 // `warps` warps.  Output: batches (nA, task ids), warp_ptr[warps + 1], units.
 struct Batch {
   int nA;
