@@ -277,7 +277,7 @@ def main():
     achieved = flops_per_launch / (c_avg_ms * 1e-3) / 1e12
     here = os.path.dirname(os.path.abspath(__file__))
     traffic = profiled_traffic(os.path.join(here, "profiles", "k_pair_products_f64_L16_slice.md"),
-                               os.path.join(here, "paper_1510_00903_gb300", "csrc", "kernels.cu"))
+                               os.path.join(here, "paper_1510_00903_gb300", "csrc", "pair_products.cu"))
     roofline = {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz",

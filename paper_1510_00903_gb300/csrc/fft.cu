@@ -1,0 +1,309 @@
+// fft.cu -- batched in-register 3-D FFT passes (radix 2 and 3) of the block fields and of the q-space correlators (Sec. 3 Eq. LN.pLLp.FFT)
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "device_common.cuh"
+
+namespace bbc {
+
+// --------------------------------------------------------------- twiddles
+constexpr int kTw = 96;  // common multiple of every supported transform length
+__constant__ double c_tw64[kTw][2];
+__constant__ float c_tw32[kTw][2];
+
+cudaError_t upload_twiddles() {
+  double h64[kTw][2];
+  float h32[kTw][2];
+  for (int k = 0; k < kTw; k++) {
+    long double a = 2.0L * 3.14159265358979323846264338327950288L * k / kTw;
+    h64[k][0] = (double)cosl(a);
+    h64[k][1] = (double)-sinl(a);
+    h32[k][0] = (float)cosl(a);
+    h32[k][1] = (float)-sinl(a);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_tw64, h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_tw32, h32, sizeof(h32));
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> twiddle(int k);
+template <>
+__device__ __forceinline__ cpx<double> twiddle<double>(int k) { return cpx<double>(c_tw64[k][0], c_tw64[k][1]); }
+template <>
+__device__ __forceinline__ cpx<float> twiddle<float>(int k) { return cpx<float>(c_tw32[k][0], c_tw32[k][1]); }
+
+__host__ __device__ constexpr int bitrev(int k, int n) {
+  int r = 0;
+  for (int b = 1; b < n; b <<= 1) { r = (r << 1) | (k & 1); k >>= 1; }
+  return r;
+}
+
+// One radix-2 stage of span M (butterflies v[k+j], v[k+j+M/2], twiddle
+// exp(-+2 pi i j/M)); stages recurse at compile time so every index is constant.
+template <typename R, int N, int M, bool INV>
+__device__ __forceinline__ void fft_stage(cpx<R> (&v)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; k += M) {
+#pragma unroll
+    for (int j = 0; j < M / 2; j++) {
+      const int ti = j * (kTw / M);
+      cpx<R> b = v[k + j + M / 2], t;
+      if (ti == 0) {
+        t = b;
+      } else if (ti == kTw / 4) {
+        t = INV ? cpx<R>(-b.im, b.re) : cpx<R>(b.im, -b.re);
+      } else {
+        cpx<R> w = twiddle<R>(ti);
+        if (INV) w.im = -w.im;
+        t = w * b;
+      }
+      v[k + j + M / 2] = v[k + j] - t;
+      v[k + j] = v[k + j] + t;
+    }
+  }
+  if constexpr (M < N) fft_stage<R, N, 2 * M, INV>(v);
+}
+
+// Radix-2 decimation in time, input bit-reversed, output natural order.
+// Forward: exp(-2 pi i jk/N); INV: exp(+2 pi i jk/N), unnormalised.
+template <typename R, int N, bool INV>
+__device__ __forceinline__ void fft_pow2(cpx<R> (&v)[N]) {
+  if constexpr (N > 1) fft_stage<R, N, 2, INV>(v);
+}
+
+// N = 3 M (M a power of two): decimation in time into three size-M transforms
+// of x[3 n2 + n1], then per k2 the twiddles exp(-+2 pi i n1 k2 / N) and a
+// radix-3 butterfly giving X[k2 + M k1] (k1 = 0, 1, 2).  On entry u[n1][.]
+// holds x[3 n2 + n1] in bit-reversed n2 order; on exit v holds X (natural).
+template <typename R, int M, bool INV>
+__device__ __forceinline__ void fft_radix3(cpx<R> (&u)[3][M], cpx<R> (&v)[3 * M]) {
+  constexpr int N = 3 * M;
+  fft_pow2<R, M, INV>(u[0]);
+  fft_pow2<R, M, INV>(u[1]);
+  fft_pow2<R, M, INV>(u[2]);
+  // omega = exp(-+2 pi i / 3) = -1/2 -+ i sqrt(3)/2
+  const R hs = (R)0.86602540378443864676;  // sqrt(3)/2
+#pragma unroll
+  for (int k2 = 0; k2 < M; k2++) {
+    cpx<R> t1 = u[1][k2], t2 = u[2][k2];
+    const int i1 = k2 * (kTw / N), i2 = 2 * k2 * (kTw / N);
+    if (i1 != 0) {
+      cpx<R> w = twiddle<R>(i1 % kTw);
+      if (INV) w.im = -w.im;
+      t1 = w * t1;
+    }
+    if (i2 != 0) {
+      cpx<R> w = twiddle<R>(i2 % kTw);
+      if (INV) w.im = -w.im;
+      t2 = w * t2;
+    }
+    const cpx<R> t0 = u[0][k2];
+    const cpx<R> s = t1 + t2, d = t1 - t2;
+    // X[k2] = t0 + s; X[k2 + M] = t0 - s/2 -+ i hs d; X[k2 + 2M] = t0 - s/2 +- i hs d
+    const cpx<R> m(t0.re - (R)0.5 * s.re, t0.im - (R)0.5 * s.im);
+    const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);  // -+ i hs d
+    v[k2] = t0 + s;
+    v[k2 + M] = m + r;
+    v[k2 + 2 * M] = m - r;
+  }
+}
+
+// --------------------------------------------------------------- FFT pass
+// v[bitrev(k)] = p[k * step] with compile-time indices (keeps v in registers)
+template <typename S, typename R, int N, int... Ks>
+__device__ __forceinline__ void load_bitrev(cpx<R> (&v)[N], const cpx<S>* p, long long step,
+                                            std::integer_sequence<int, Ks...>) {
+  ((v[bitrev(Ks, N)] = cpx<R>(p[Ks * step])), ...);
+}
+
+// u[n1][bitrev(n2)] = p[(3 n2 + n1) * step], compile-time indices
+template <typename S, typename R, int M, int... Ks>
+__device__ __forceinline__ void load_radix3(cpx<R> (&u)[3][M], const cpx<S>* p, long long step,
+                                            std::integer_sequence<int, Ks...>) {
+  ((u[Ks % 3][bitrev(Ks / 3, M)] = cpx<R>(p[Ks * step])), ...);
+}
+
+// Length-N transform of one line (N = 2^k, or 3 * 2^k), natural order in and out.
+template <typename S, typename R, int N, bool INV>
+__device__ __forceinline__ void line_fft(const cpx<S>* p, long long step, cpx<R> (&v)[N]) {
+  if constexpr ((N & (N - 1)) == 0) {
+    load_bitrev<S, R, N>(v, p, step, std::make_integer_sequence<int, N>{});
+    fft_pow2<R, N, INV>(v);
+  } else {
+    constexpr int M = N / 3;
+    cpx<R> u[3][M];
+    load_radix3<S, R, M>(u, p, step, std::make_integer_sequence<int, N>{});
+    fft_radix3<R, M, INV>(u, v);
+  }
+}
+
+__device__ __forceinline__ void line_base(int N, int axis, int line, int& base, int& stride) {
+  const int a = line % N, b = line / N;
+  if (axis == 0) { base = N * (a + N * b); stride = 1; }           // x varies, (y, z) = (a, b)
+  else if (axis == 1) { base = a + N * N * b; stride = N; }        // y varies, (x, z) = (a, b)
+  else { base = a + N * b; stride = N * N; }                       // z varies, (x, y) = (a, b)
+}
+
+// Mode SITE2FIELD (x axis): in[o][site][n_inner] -> out[o][inner][site] (the
+// transpose to field-major storage rides on the first pass; lanes run over
+// the contiguous inner index).
+// Mode FIELD (any axis, in place on in = out): data[n_fields][V]; lanes run
+// over the line index, which is contiguous for the y and z passes.
+// Mode FIELD2OUT (z axis): in[ch][s][V] -> out[ch][r][16] times scale[ch]
+// (the last inverse pass writes the output layout and normalises it).
+// Mode SITE (any axis, in place): data[o][site][n_inner], lanes over inner.
+// Mode SITE2OUT (z axis): in[site][n_ch*16] -> out[ch][r][16] times scale[ch].
+enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4 };
+
+template <typename S, typename R, int N, bool INV, int MODE>
+__global__ void __launch_bounds__(256)
+k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer, int n_inner, int axis,
+      const double* __restrict__ scale) {
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lines = N * N;
+  const long long V = (long long)N * N * N;
+  int line, inner;
+  long long o;
+  if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
+    if (gid >= n_outer * lines * n_inner) return;
+    inner = (int)(gid % n_inner);
+    const long long rest = gid / n_inner;
+    line = (int)(rest % lines);
+    o = rest / lines;
+  } else if (MODE == FFT_FIELD) {
+    if (gid >= n_outer * lines) return;
+    line = (int)(gid % lines);
+    o = gid / lines;
+    inner = 0;
+  } else {  // FIELD2OUT: spin fastest so that each site's 16 spins are written together
+    if (gid >= n_outer * lines * 16) return;
+    inner = (int)(gid % 16);
+    const long long rest = gid / 16;
+    line = (int)(rest % lines);
+    o = rest / lines;  // channel
+  }
+  int base, stride;
+  line_base(N, axis, line, base, stride);
+  cpx<R> v[N];
+  if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
+    line_fft<S, R, N, INV>(in + (o * V + base) * n_inner + inner, (long long)stride * n_inner, v);
+  } else if (MODE == FFT_FIELD) {
+    line_fft<S, R, N, INV>(in + o * V + base, stride, v);
+  } else {
+    line_fft<S, R, N, INV>(in + (o * 16 + inner) * V + base, stride, v);
+  }
+  if (MODE == FFT_SITE2FIELD) {
+    cpx<S>* p = out + (o * n_inner + inner) * V + base;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+  } else if (MODE == FFT_FIELD) {
+    cpx<S>* p = out + o * V + base;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+  } else if (MODE == FFT_SITE) {
+    cpx<S>* p = out + (o * V + base) * n_inner + inner;
+#pragma unroll
+    for (int k = 0; k < N; k++) p[(long long)k * stride * n_inner] = cpx<S>(v[k]);
+  } else if (MODE == FFT_SITE2OUT) {
+    // inner = channel * 16 + spin; out[ch][r][16]
+    const R f = (R)scale[inner >> 4];
+    cpx<S>* p = out + ((long long)(inner >> 4) * V + base) * 16 + (inner & 15);
+#pragma unroll
+    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<S>(cpx<R>(v[k].re * f, v[k].im * f));
+  } else {
+    const R f = (R)scale[o];
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+      cpx<S> w(v[k].re * f, v[k].im * f);
+      out[(o * V + base + (long long)k * stride) * 16 + inner] = w;
+    }
+  }
+}
+
+template <typename S, typename R, int MODE>
+static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
+                                const double* scale, cudaStream_t st) {
+  long long per = (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) ? n_inner
+                  : (MODE == FFT_FIELD ? 1 : 16);
+  long long total = n_outer * (long long)L * L * per;
+  unsigned blocks = (unsigned)((total + 255) / 256);
+  const cpx<S>* i = (const cpx<S>*)in;
+  cpx<S>* o = (cpx<S>*)out;
+#define BBC_FFT_CASE(NN)                                                                                   \
+  case NN:                                                                                                 \
+    if (inv) k_fft<S, R, NN, true, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);    \
+    else k_fft<S, R, NN, false, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);        \
+    break;
+  switch (L) {
+    BBC_FFT_CASE(2)
+    BBC_FFT_CASE(4)
+    BBC_FFT_CASE(8)
+    BBC_FFT_CASE(16)
+    BBC_FFT_CASE(32)
+    BBC_FFT_CASE(24)
+    BBC_FFT_CASE(48)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BBC_FFT_CASE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
+                               cudaStream_t st) {
+  cudaError_t e;
+  if (fp64) {
+    e = fft_dispatch<double, double, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+    for (int axis = 1; axis < 3; axis++) {
+      e = fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
+                                                  nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    e = fft_dispatch<float, float, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+    for (int axis = 1; axis < 3; axis++) {
+      e = fft_dispatch<float, float, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
+                                                nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st) {
+  for (int axis = 0; axis < 3; axis++) {
+    cudaError_t e = fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st)
+                         : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                                    cudaStream_t st) {
+  cudaError_t e;
+  for (int axis = 0; axis < 2; axis++) {
+    e = fp64_compute ? fft_dispatch<double, double, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st)
+                     : fft_dispatch<double, float, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return fp64_compute ? fft_dispatch<double, double, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st)
+                      : fft_dispatch<double, float, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
+}
+
+cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
+                               cudaStream_t st) {
+  cudaError_t e;
+  for (int axis = 0; axis < 2; axis++) {
+    e = fp64_compute ? fft_dispatch<double, double, FFT_FIELD>(ct, ct, L, (long long)n_ch * 16, 1, axis, true, nullptr, st)
+                     : fft_dispatch<double, float, FFT_FIELD>(ct, ct, L, (long long)n_ch * 16, 1, axis, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return fp64_compute ? fft_dispatch<double, double, FFT_FIELD2OUT>(ct, out, L, n_ch, 16, 2, true, scale, st)
+                      : fft_dispatch<double, float, FFT_FIELD2OUT>(ct, out, L, n_ch, 16, 2, true, scale, st);
+}
+
+}  // namespace bbc

@@ -1,0 +1,147 @@
+// fused_contract.cu -- FP32 q-space contraction fused with the FP64 Wick sums, one CTA per pair {q, -q} (mixed precision path)
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "device_common.cuh"
+
+namespace bbc {
+
+// ------------------------------------------------- fused contraction (FP32)
+// One CTA per pair {q, -q}.  The q-row and the -q row of the q-major
+// Fourier-space blocks (blk[q][n_out]) are staged in shared memory once,
+// interleaved as R[i] = (F_q[i], F_-q[i]), so one 16-byte load serves both
+// products A(q) B(-q) (side 0) and A(-q) B(q) (side 1); every block element is
+// read from HBM exactly once.  Warps run units (batch of up to 32 tasks of
+// one shape and one open-index length, k range): lane l takes task l, so
+// control flow is uniform within the warp.  Products accumulate in FP32
+// registers and are added into P[side][task*16 + spin pair] in shared memory.
+// The products are then converted once to FP64 and the signed FP64 sums over
+// Wick diagrams run in the same CTA, writing ct[q][o].
+template <int NA, int NB>
+__device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R, const DevTask& t, int k0, int k1,
+                                                   cpx<float>* P0, cpx<float>* P1, int rot, bool self) {
+  const int n2 = t.n2;
+  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
+  int i1 = k0 / n2, i2 = k0 - i1 * n2;
+  int oA = i1 * sA1 + i2 * sA2, oB = i1 * sB1 + i2 * sB2;
+  const int wrapA = sA1 - (n2 - 1) * sA2, wrapB = sB1 - (n2 - 1) * sB2;
+  cpx<float> acc0[NA * NB], acc1[NA * NB];
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) { acc0[i] = cpx<float>(0.f, 0.f); acc1[i] = cpx<float>(0.f, 0.f); }
+  for (int k = k0; k < k1; k++) {
+    float4 a[NA], b[NB];
+#pragma unroll
+    for (int r = 0; r < NA; r++) a[r] = R[t.offA[r] + oA];
+#pragma unroll
+    for (int r = 0; r < NB; r++) b[r] = R[t.offB[r] + oB];
+#pragma unroll
+    for (int ra = 0; ra < NA; ra++)
+#pragma unroll
+      for (int rb = 0; rb < NB; rb++) {
+        cmac(acc0[ra * NB + rb], cpx<float>(a[ra].x, a[ra].y), cpx<float>(b[rb].z, b[rb].w));
+        cmac(acc1[ra * NB + rb], cpx<float>(a[ra].z, a[ra].w), cpx<float>(b[rb].x, b[rb].y));
+      }
+    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
+    else { oA += sA2; oB += sB2; }
+  }
+  // P slot of product i of task ti: ti*16 + ((i + ti) & 15) -- the rotation
+  // spreads the 32 lanes' (distinct tasks') slots over the shared-memory banks
+#pragma unroll
+  for (int i = 0; i < NA * NB; i++) {
+    cpx<float>* d0 = P0 + ((i + rot) & 15);
+    atomicAdd(&d0->re, acc0[i].re);
+    atomicAdd(&d0->im, acc0[i].im);
+    if (!self) {
+      cpx<float>* d1 = P1 + ((i + rot) & 15);
+      atomicAdd(&d1->re, acc1[i].re);
+      atomicAdd(&d1->im, acc1[i].im);
+    }
+  }
+}
+
+constexpr int kFusedThreads = 512;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ qlist,
+                 const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
+                 const int* __restrict__ wptr, const int4* __restrict__ wunits, const int* __restrict__ cptr,
+                 const int* __restrict__ citem, const double* __restrict__ ccoef, int n_outputs,
+                 cpx<double>* __restrict__ ct) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = n_tasks * 16;                                        // products per side
+  const size_t region = max((size_t)n_out * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
+  float4* R = reinterpret_cast<float4*>(smem_raw);                     // [n_out] (F_q, F_-q)
+  cpx<double>* Pd = reinterpret_cast<cpx<double>*>(smem_raw);         // [2][np], after the products
+  cpx<float>* P = reinterpret_cast<cpx<float>*>(smem_raw + region);   // [2][np]
+  const int q = qlist[blockIdx.x];
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
+  const bool self = nq == q;
+  {
+    const float2* s0 = reinterpret_cast<const float2*>(blk + (size_t)q * n_out);
+    const float2* s1 = reinterpret_cast<const float2*>(blk + (size_t)nq * n_out);
+    for (int i = tid; i < n_out; i += kFusedThreads) {
+      const float2 x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
+      R[i] = make_float4(x.x, x.y, y.x, y.y);
+    }
+    float4* pz = reinterpret_cast<float4*>(P);
+    for (int i = tid; i < np; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  const int u1 = wptr[warp + 1];
+  for (int u = wptr[warp]; u < u1; u++) {
+    const int4 un = wunits[u];  // batch, -, k0, k1
+    const WarpBatch& wb = batches[un.x];
+    if (lane >= wb.n) continue;
+    const int ti = wb.task[lane];
+    const DevTask t = tasks[ti];
+    cpx<float>* p0 = P + ti * 16;
+    cpx<float>* p1 = P + np + ti * 16;
+    if (wb.nA == 4) unit_products_pair<4, 4>(R, t, un.z, un.w, p0, p1, ti, self);
+    else if (wb.nA == 2) unit_products_pair<2, 8>(R, t, un.z, un.w, p0, p1, ti, self);
+    else unit_products_pair<8, 2>(R, t, un.z, un.w, p0, p1, ti, self);
+  }
+  __syncthreads();
+  // products to FP64 once (undoing the slot rotation), over the rows' space
+  const int sides = self ? 1 : 2;
+  for (int j = tid; j < sides * np; j += kFusedThreads) {
+    const int side = j / np, it = j - side * np, ti = it >> 4;
+    const cpx<float> v = P[side * np + (ti << 4) + ((it + ti) & 15)];
+    Pd[j] = cpx<double>((double)v.re, (double)v.im);
+  }
+  __syncthreads();
+  for (int j = tid; j < sides * n_outputs; j += kFusedThreads) {
+    const int side = j / n_outputs, o = j - side * n_outputs;
+    const cpx<double>* Ps = Pd + side * np;
+    cpx<double> acc(0, 0);
+    const int c1 = cptr[o + 1];
+    for (int c = cptr[o]; c < c1; c++) {
+      const double w = ccoef[c];
+      const cpx<double> v = Ps[citem[c]];
+      acc.re = fma(w, v.re, acc.re);
+      acc.im = fma(w, v.im, acc.im);
+    }
+    ct[(size_t)(side ? nq : q) * n_outputs + o] = acc;
+  }
+}
+
+size_t contract_fused_smem(int n_out, int n_tasks) {
+  const size_t np = (size_t)n_tasks * 16;
+  return std::max((size_t)n_out * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
+}
+
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+                                  int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
+                                  const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
+                                  cudaStream_t st) {
+  const size_t sm = contract_fused_smem(n_out, n_tasks);
+  cudaError_t e = cudaFuncSetAttribute(k_contract_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, batches,
+                                                   wptr, wunits, cptr, citem, ccoef, n_ch * 16, (cpx<double>*)ct);
+  return cudaGetLastError();
+}
+
+}  // namespace bbc

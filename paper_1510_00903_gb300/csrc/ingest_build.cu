@@ -1,0 +1,166 @@
+// ingest_build.cu -- propagator ingest with exact power-of-two rescaling, per-site baryon blocks (Sec. 3 blocks, Appendix A aggregation), per-channel normalisation factors (Sec. 2 Eq. 2)
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "device_common.cuh"
+
+namespace bbc {
+
+// ------------------------------------------------------------------ ingest
+__global__ void k_absmax(const void* __restrict__ src, int dtype, long long n_real,
+                         unsigned long long* amax) {
+  double m = 0.0;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
+    double x = dtype == 0 ? ((const double*)src)[i] : (double)((const float*)src)[i];
+    m = fmax(m, fabs(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename R>
+__global__ void k_convert(const void* __restrict__ src, int dtype, long long n_real,
+                          const unsigned long long* __restrict__ amax, int* kexp, R* __restrict__ dst) {
+  double m = __longlong_as_double((long long)*amax);
+  int k = (m > 0.0 && m <= 1.7976931348623157e308) ? ilogb(m) + 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *kexp = k;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
+    double x = dtype == 0 ? ((const double*)src)[i] : (double)((const float*)src)[i];
+    dst[i] = (R)ldexp(x, -k);
+  }
+}
+
+cudaError_t launch_absmax(const void* src, int dtype, long long n_complex, unsigned long long* amax,
+                          cudaStream_t st) {
+  long long n = 2 * n_complex;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  k_absmax<<<blocks, 256, 0, st>>>(src, dtype, n, amax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void* src, int dtype, long long n_complex, const unsigned long long* amax,
+                           int* kexp, void* dst, bool fp64, cudaStream_t st) {
+  long long n = 2 * n_complex;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  if (fp64) k_convert<double><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (double*)dst);
+  else k_convert<float><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (float*)dst);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ block build
+// C gamma5 (Dirac representation): (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1.
+__constant__ int c_cg5[4][3] = {{0, 1, 1}, {1, 0, -1}, {2, 3, 1}, {3, 2, -1}};
+
+constexpr int kBuildThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kBuildThreads)
+k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ row_ptr,
+              const uint32_t* __restrict__ entries, const uint32_t* __restrict__ zneed, DevGroups g,
+              cpx<R>* __restrict__ blk, int n_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][144]  light, strange
+  cpx<R>* sD = sS + 288;                              // [2][432]  diquarks (l,l), (l,s)
+  cpx<R>* sZ = sD + 864;                              // [g.z_slots] the tensor entries the rows read
+  R* sW = reinterpret_cast<R*>(sZ + g.z_slots);       // weights -16..15 (no int->float conversion per term)
+  const int site = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
+  if (tid < 32) sW[tid] = (R)(tid - 16);
+  const cpx<R>* P = prop + (size_t)slot * 2 * V * 144;
+  for (int i = tid; i < 288; i += kBuildThreads) sS[i] = P[(size_t)(i / 144) * V * 144 + (size_t)site * 144 + i % 144];
+  __syncthreads();
+  // D_{l f1}[e0][e1][c2] = sum eps(c0,c1,c2) Cg5(a0,a1) S_l[(a0,c0),e0] S_f1[(a1,c1),e1]
+  for (int i = tid; i < 864; i += kBuildThreads) {
+    const int dq = i / 432, r = i % 432, e0 = r / 36, e1 = (r / 3) % 12, c2 = r % 3;
+    const int ca = (c2 + 1) % 3, cb = (c2 + 2) % 3;  // eps(ca,cb,c2) = +1, eps(cb,ca,c2) = -1
+    const cpx<R>* S0 = sS;
+    const cpx<R>* S1 = sS + 144 * dq;
+    cpx<R> acc(0, 0);
+#pragma unroll
+    for (int gi = 0; gi < 4; gi++) {
+      const int a0 = c_cg5[gi][0], a1 = c_cg5[gi][1];
+      const R sg = (R)c_cg5[gi][2];
+      cpx<R> t(0, 0);
+      cmac(t, S0[(3 * a0 + ca) * 12 + e0], S1[(3 * a1 + cb) * 12 + e1]);
+      cpx<R> u(0, 0);
+      cmac(u, S0[(3 * a0 + cb) * 12 + e0], S1[(3 * a1 + ca) * 12 + e1]);
+      acc.re += sg * (t.re - u.re);
+      acc.im += sg * (t.im - u.im);
+    }
+    sD[i] = acc;
+  }
+  __syncthreads();
+  for (int gi = 0; gi < g.n; gi++) {
+    // the tensor entries this group reads (and the previous group did not leave)
+    const int z1 = g.zneed_first[gi + 1];
+    for (int j = g.zneed_first[gi] + tid; j < z1; j += kBuildThreads) {
+      const uint32_t zn = zneed[j];
+      const int pos = zn & 0x1fff, sl = (zn >> 13) & 1, i = zn >> 14;
+      const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
+      // F[a][e0][e1][e2] = sum_c2 D[e0][e1][c2] S_f2[(a,c2),e2]
+      const int dq = (fam == 2 || fam == 3) ? 1 : 0;  // LSL, LSS read the (l,s) diquark
+      const int f2 = (fam == 1 || fam == 3) ? 1 : 0;  // LLS, LSS: strange third quark
+      const cpx<R>* D = sD + 432 * dq;
+      const cpx<R>* S2 = sS + 144 * f2;
+      const int a = i / 1728, r = i % 1728, e01 = r / 12, e2 = r % 12;
+      cpx<R> acc(0, 0);
+#pragma unroll
+      for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);
+      sZ[pos] = acc;
+    }
+    __syncthreads();
+    const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
+    cpx<R>* out = blk + ((size_t)slot * V + site) * n_out;
+    for (int r = r0 + tid; r < r1; r += kBuildThreads) {
+      cpx<R> acc(0, 0);
+      const int k1 = row_ptr[r + 1];
+      for (int k = row_ptr[r]; k < k1; k++) {
+        const uint32_t e = __ldg(entries + k);
+        const R w = sW[((int)(int16_t)(e >> 16)) + 16];
+        const cpx<R> z = sZ[e & 0xffffu];
+        acc.re = fma(w, z.re, acc.re);
+        acc.im = fma(w, z.im, acc.im);
+      }
+      out[r] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
+                               const uint32_t* entries, const uint32_t* zneed, const DevGroups& g, void* blk,
+                               int n_out, bool fp64, cudaStream_t st) {
+  dim3 grid(V, n_slots);
+  if (fp64) {
+    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<double>) + 32 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_block_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, zneed,
+                                                           g, (cpx<double>*)blk, n_out);
+  } else {
+    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<float>) + 32 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_block_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, zneed,
+                                                          g, (cpx<float>*)blk, n_out);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ normalisation
+// scale[ch] = f[ch] * 2^(nl[ch] k_l + ns[ch] k_s): 1/V, the mass factor and the
+// undoing of the power-of-two propagator rescaling of this slice.
+__global__ void k_scales(ScaleParams p, const int* __restrict__ kexp, double* __restrict__ scale) {
+  const int ch = threadIdx.x;
+  if (ch < p.n_ch) scale[ch] = ldexp(p.f[ch], p.nl[ch] * kexp[0] + p.ns[ch] * kexp[1]);
+}
+
+cudaError_t launch_scales(const ScaleParams& p, const int* kexp, double* scale, cudaStream_t st) {
+  k_scales<<<1, kMaxChannels, 0, st>>>(p, kexp, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace bbc
