@@ -53,9 +53,10 @@ def profiled_traffic(path, kernel_src):
         return None
     fields = {}
     for line in text.splitlines():
-        if ":" in line and line.strip().startswith(("kernels_cu_sha256", "dram_bytes_per_launch")):
+        line = line.strip().lstrip("-* ").strip()
+        if ":" in line and line.startswith(("kernels_cu_sha256", "dram_bytes_per_launch")):
             k, v = line.split(":", 1)
-            fields[k.strip().strip("`- ")] = v.strip().strip("`")
+            fields[k.strip().strip("`")] = v.strip().strip("`")
     if fields.get("kernels_cu_sha256") != sha or "dram_bytes_per_launch" not in fields:
         return None
     return float(fields["dram_bytes_per_launch"])
