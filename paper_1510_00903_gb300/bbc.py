@@ -174,7 +174,7 @@ class Correlators:
 
     def __init__(self, L: int, T: int, t0: int = 0, m_ud: float = 0.3, m_s: float = 0.4,
                  channels=CHANNELS_52, precision: int = BBC_FP64, slices: int = 1, device=None,
-                 stream=None):
+                 stream=None, workspace=None):
         import torch
         self.torch = torch
         dev = torch.device(device or "cuda")
@@ -188,7 +188,12 @@ class Correlators:
         self.ctx = bbc_create(L, T, t0, m_ud, m_s, precision, self.channels, self.stream.cuda_stream)
         self.slices = slices
         nbytes = bbc_workspace_size(self.ctx, slices)
-        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        if workspace is None:
+            workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        elif workspace.numel() < nbytes + 256:
+            raise ValueError(f"workspace needs {nbytes + 256} bytes")
+        # contexts whose work is ordered on one stream may share a workspace
+        self.workspace = workspace
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         with torch.cuda.stream(self.stream):
@@ -231,6 +236,21 @@ class Correlators:
                     self.contract(j, out[i0 + j], normalised)
         return out
 
+    def capture(self, S_light, S_strange, times, out, normalised: bool = True):
+        """Record run(...) for these slices into one CUDA graph (after an eager
+        run that sets kernel attributes); replaying the graph repeats the
+        whole computation into `out` with one launch.  Needs a non-default
+        stream (pass `stream=torch.cuda.Stream()` at construction)."""
+        torch = self.torch
+        if self.stream.cuda_stream == 0:
+            raise ValueError("graph capture needs a non-default stream")
+        self.run(S_light, S_strange, times, out=out, normalised=normalised)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.run(S_light, S_strange, times, out=out, normalised=normalised)
+        return g
+
     def close(self):
         if self.ctx:
             bbc_destroy(self.ctx)
@@ -241,3 +261,68 @@ class Correlators:
             self.close()
         except Exception:
             pass
+
+
+class LatticeBatch:
+    """Several lattices and wall sources run as one CUDA graph on one stream.
+
+    ``lattices``: list of (L, T); every lattice runs ``n_sources`` wall
+    sources at t0 = 0, T/n, 2T/n, ...  Contexts of one lattice share one
+    workspace (their work is ordered on the stream).  ``inputs[i]`` =
+    (S_light, S_strange), each [T, V, 12, 12] on the device, serve every source
+    of lattice i.  ``run()`` computes every slice of every source; the
+    correlators of a slice land in ``outputs[i]`` ([n_channels, V, 16]),
+    overwritten slice after slice (a streaming consumer reads them there).
+    """
+
+    def __init__(self, lattices, inputs, n_sources: int = 4, channels=CHANNELS_52,
+                 precision: int = BBC_MIXED_FP32, m_ud: float = 0.3, m_s: float = 0.4, device=None):
+        import torch
+        self.torch = torch
+        dev = torch.device(device or "cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.stream = torch.cuda.Stream(dev)
+        self.lattices, self.inputs, self.n_sources = list(lattices), list(inputs), n_sources
+        self.cors, self.outputs = [], []
+        for (L, T), _ in zip(self.lattices, self.inputs):
+            per = []
+            ws = None
+            for k in range(n_sources):
+                c = Correlators(L, T, (k * T) // n_sources, m_ud, m_s, channels=channels, precision=precision,
+                                device=dev, stream=self.stream, workspace=ws)
+                ws = c.workspace
+                per.append(c)
+            self.cors.append(per)
+            self.outputs.append(torch.empty((len(channels), L ** 3, 16), dtype=torch.complex128, device=dev))
+
+    def sites_channels(self) -> int:
+        n_ch = self.outputs[0].shape[0]
+        return sum(self.n_sources * T * L ** 3 * n_ch for (L, T) in self.lattices)
+
+    def run(self):
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            for per, (Sl, Ss), out in zip(self.cors, self.inputs, self.outputs):
+                for c in per:
+                    for t in range(c.T):
+                        c.load(BBC_LIGHT, 0, t, Sl[t])
+                        c.load(BBC_STRANGE, 0, t, Ss[t])
+                        c.build(1)
+                        c.contract(0, out, True)
+
+    def capture(self):
+        """One CUDA graph for every slice of every source of every lattice."""
+        torch = self.torch
+        self.run()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            self.run()
+        return g
+
+    def close(self):
+        for per in self.cors:
+            for c in per:
+                c.close()

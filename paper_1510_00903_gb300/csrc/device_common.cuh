@@ -31,4 +31,19 @@ __device__ __forceinline__ void cmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
   acc.im = fma(a.im, b.re, acc.im);
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than was granted before (per device), so that launches captured into a
+// CUDA graph after a first eager run issue no attribute call.
+template <typename K>
+inline cudaError_t ensure_smem(K kernel, size_t bytes, int* granted /* [64] per device */) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if ((int)bytes <= granted[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) granted[dev] = (int)bytes;
+  return e;
+}
+
 }  // namespace bbc

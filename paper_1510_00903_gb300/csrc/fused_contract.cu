@@ -137,7 +137,8 @@ cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* 
                                   const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
                                   cudaStream_t st) {
   const size_t sm = contract_fused_smem(n_out, n_tasks);
-  cudaError_t e = cudaFuncSetAttribute(k_contract_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem(k_contract_fused, sm, granted);
   if (e != cudaSuccess) return e;
   k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, batches,
                                                    wptr, wunits, cptr, citem, ccoef, n_ch * 16, (cpx<double>*)ct);

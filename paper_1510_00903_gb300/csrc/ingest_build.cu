@@ -136,13 +136,15 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* 
   dim3 grid(V, n_slots);
   if (fp64) {
     size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<double>) + 32 * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_block_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static int granted[64] = {0};
+    cudaError_t e = ensure_smem(k_block_build<double>, sm, granted);
     if (e != cudaSuccess) return e;
     k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, zneed,
                                                            g, (cpx<double>*)blk, n_out);
   } else {
     size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<float>) + 32 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_block_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static int granted[64] = {0};
+    cudaError_t e = ensure_smem(k_block_build<float>, sm, granted);
     if (e != cudaSuccess) return e;
     k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, zneed,
                                                           g, (cpx<float>*)blk, n_out);

@@ -1,0 +1,70 @@
+"""CUDA-graph capture of the whole slice loop, and several lattices with
+uneven L and T run as one graph (GPU)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+import oracle.oracle as orc
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+from paper_1510_00903_gb300 import bbc  # noqa: E402
+
+
+@pytest.mark.parametrize("precision", [bbc.BBC_FP64, bbc.BBC_MIXED_FP32])
+def test_graph_replay_equals_eager(precision):
+    L, T = 8, 4
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=31)
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=[0, 10, 51], precision=precision, device=dev,
+                          stream=torch.cuda.Stream(dev))
+    eager = cor.run(Sl, Ss, range(T)).clone()
+    torch.cuda.synchronize(dev)
+    out = torch.zeros_like(eager)
+    g = cor.capture(Sl, Ss, range(T), out)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    if precision == bbc.BBC_FP64:
+        assert torch.equal(out, eager)  # same kernels, same order, no atomics
+    else:
+        # the FP32 products are added into shared memory with atomics, whose
+        # order varies from run to run at the FP32 rounding level
+        scale = eager.abs().amax(dim=(-2, -1), keepdim=True)
+        assert ((out - eager).abs() / scale).max().item() < 1e-5
+    cor.close()
+
+
+def test_lattice_batch_uneven_lattices_one_graph():
+    """Two lattices of different L and T and two sources each in one graph;
+    the last slice of each lattice matches the oracle (mixed tolerance)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lat = [(4, 4), (8, 6)]
+    inputs, Fs = [], []
+    for i, (L, T) in enumerate(lat):
+        F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=40 + i)
+        Fs.append(F)
+        inputs.append((torch.from_numpy(F["u"]).to(torch.complex64).to(dev),
+                       torch.from_numpy(F["s"]).to(torch.complex64).to(dev)))
+    chans = [1, 41]
+    b = bbc.LatticeBatch(lat, inputs, n_sources=2, channels=chans, precision=bbc.BBC_MIXED_FP32, device=dev)
+    g = b.capture()
+    for o in b.outputs:
+        o.zero_()
+    g.replay()
+    torch.cuda.synchronize(dev)
+    for (L, T), F, o in zip(lat, Fs, b.outputs):
+        t, t0 = T - 1, T // 2  # last slice of the second source
+        F32 = {k: v.astype(np.complex64).astype(np.complex128) for k, v in F.items()}
+        want = orc.normalise(orc.correlator(L, F32["u"][t], F32["d"][t], F32["s"][t], chans), chans,
+                             (t - t0) % T, 0.3, 0.4)
+        got = o.cpu().numpy()
+        scale = np.abs(want).reshape(len(chans), -1).max(axis=1)
+        err = np.abs(got - want).reshape(len(chans), -1).max(axis=1) / scale
+        assert err.max() < 2e-5, (L, err)
+    assert b.sites_channels() == 2 * (4 * 64 + 6 * 512) * 2
+    b.close()
