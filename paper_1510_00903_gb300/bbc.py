@@ -234,6 +234,11 @@ class Correlators:
                 self.build(len(chunk))
                 for j in range(len(chunk)):
                     self.contract(j, out[i0 + j], normalised)
+        # the caller's stream sees the results (and may free the inputs) only
+        # after the work queued on the context stream
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
         return out
 
     def capture(self, S_light, S_strange, times, out, normalised: bool = True):
@@ -311,6 +316,9 @@ class LatticeBatch:
                         c.load(BBC_STRANGE, 0, t, Ss[t])
                         c.build(1)
                         c.contract(0, out, True)
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
 
     def capture(self):
         """One CUDA graph for every slice of every source of every lattice."""
