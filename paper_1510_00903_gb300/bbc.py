@@ -225,6 +225,10 @@ class Correlators:
         n_ch = len(self.channels)
         if out is None:
             out = torch.empty((len(times), n_ch, self.V, 16), dtype=torch.complex128, device=self.device)
+        # inputs and output were written or allocated on the caller's stream
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
             for i0 in range(0, len(times), self.slices):
                 chunk = times[i0:i0 + self.slices]
@@ -236,7 +240,6 @@ class Correlators:
                     self.contract(j, out[i0 + j], normalised)
         # the caller's stream sees the results (and may free the inputs) only
         # after the work queued on the context stream
-        cur = torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
         return out
@@ -308,6 +311,9 @@ class LatticeBatch:
 
     def run(self):
         torch = self.torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
             for per, (Sl, Ss), out in zip(self.cors, self.inputs, self.outputs):
                 for c in per:
@@ -316,7 +322,6 @@ class LatticeBatch:
                         c.load(BBC_STRANGE, 0, t, Ss[t])
                         c.build(1)
                         c.contract(0, out, True)
-        cur = torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
 
