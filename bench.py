@@ -39,6 +39,8 @@ PAPER_SITE_CH_PER_S = 16 ** 3 * 32 * 52 / 19.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 #: FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (probe: 74.8 TFLOP/s)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+#: measured STREAM-style copy bandwidth of this GPU model (GB/s)
+HBM_PEAK_GBS = 6803.8
 
 
 def profiled_traffic(path, kernel_src):
@@ -278,6 +280,7 @@ def run_ours(args, torch, rank, world, local):
     ms, stages = timed(cor, args.steps, args.warmup, sampler=sampler)
     clocks = sampler.summary()
     ms_e2e, _ = timed(cor, max(1, args.steps // 2), 1, e2e=True)
+    projection = measure_projection(torch, cor, out, stream)
     cor.close()
     value = shard.job_throughput(V * T * N_CH, world, ms)
     value_e2e = shard.job_throughput(V * T * N_CH, world, ms_e2e)
@@ -335,10 +338,34 @@ def run_ours(args, torch, rank, world, local):
         "stage_ms_per_step": stage_ms,
         "plan": sizes,
         "mixed": mixed,
+        "projection": projection,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_projection(torch, cor, C, stream, reps=20):
+    """Spin-state and cubic-group projections (Sec. 2) of the correlators of
+    every slice of one step (one launch over T x 52 fields): an epilogue
+    outside the timed step, timed on its own.  Algorithmic bytes: C read
+    once, R and Ra1 written once."""
+    R, Ra1 = torch.empty_like(C), torch.empty_like(C)
+    for _ in range(3):
+        cor.project(C, R, Ra1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        cor.project(C, R, Ra1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 3 * C.numel() * 16
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": "k_project", "bound": "hbm", "ms_per_launch": ms, "fields": C.numel() // (C.shape[-2] * 16),
+            "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": HBM_PEAK_GBS,
+            "frac": gbs / HBM_PEAK_GBS, "l2": "C, R, Ra1 of all slices (3 x 1.74 GB) exceed the L2"}
 
 
 def error_report(torch, dev, bbc, synth):

@@ -147,7 +147,8 @@ typedef enum {
   BBC_STAGE_FFT_INV = 4,    /* inverse 3-D FFT with the fused output transpose and normalisation */
   BBC_STAGE_NORMALISE = 5,  /* per-channel normalisation factors */
   BBC_STAGE_WICK = 6,       /* signed FP64 sums of pair products over Wick diagrams */
-  BBC_N_STAGES = 7
+  BBC_STAGE_PROJECT = 7,    /* spin-state and cubic-group projections (bbc_project) */
+  BBC_N_STAGES = 8
 } bbc_stage;
 
 /* enable != 0: from now on bracket every stage launch with CUDA events on the
@@ -164,6 +165,25 @@ bbc_status bbc_stage_timing(bbc_ctx* ctx, double* ms, long long* launches);
 /* Number of kernel launches one bbc_contract call issues, and one
  * bbc_build_blocks call per slot-batch, and one bbc_load_propagator call. */
 bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, int* per_contract);
+
+/* Projections of Sec. 2 (the source operator of total spin J, M in the
+ * equation for R^(J,M), and the operator P of the 3S1 / 3D1 split) applied to
+ * correlators in the layout bbc_contract writes: C_dev[n_fields][L^3][16]
+ * complex128, spin s = a + 2(b + 2(a' + 2 b')), index 0 = spin up.
+ *
+ *   R[f][r][a + 2b + 4 jm]  = sum_{a'b'} P^(J,M)_{a'b'} C[f][r][a + 2b + 4a' + 8b']
+ *   Ra1[f][r][j]            = (1/24) sum over the 24 rotations g of the cube of R[f][g r][j]
+ *
+ * States jm = 0: (J,M) = (0,0) = (|ud> - |du>)/sqrt2, 1: (1,+1) = |uu>,
+ * 2: (1,0) = (|ud> + |du>)/sqrt2, 3: (1,-1) = |dd> (Clebsch-Gordan
+ * coefficients, Condon-Shortley phases); the rotations act on the relative
+ * coordinate r on the periodic lattice, the sink spins a, b are untouched.
+ * The D-wave part of Sec. 2 is R - Ra1.  R_dev or Ra1_dev may be NULL (not
+ * both); neither may overlap C_dev.  All three are device pointers, 16-byte
+ * aligned, of n_fields * L^3 * 16 complex128 (L of the context).  FP64 on the
+ * context stream, asynchronous.  The first call on a device uploads a 24-entry
+ * rotation table (make it before any stream capture).  Errors: EINVAL. */
+bbc_status bbc_project(bbc_ctx* ctx, const void* C_dev, int n_fields, void* R_dev, void* Ra1_dev);
 
 /* Bytes of the static device array used by bbc_run_slice_static. */
 #define BBC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)

@@ -55,6 +55,7 @@ def _load():
         "bbc_stage_timing": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)], I),
         "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "bbc_run_slice_static": ([P, I, P, P, I, P, I], I),
+        "bbc_project": ([P, P, I, P, P], I),
         "bbc_last_error": ([P], ctypes.c_char_p),
         "bbc_destroy": ([P], None),
     }
@@ -125,7 +126,7 @@ def bbc_plan_sizes(ctx):
     return {"blocks": a.value, "block_outputs": b.value, "pair_items": c.value, "pair_macs_per_site": d.value}
 
 
-STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise", "wick"]
+STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise", "wick", "project"]
 
 
 def bbc_enable_stage_timing(ctx, enable: bool):
@@ -152,6 +153,14 @@ def bbc_run_slice_static(ctx, t: int, light_ptr: int, strange_ptr: int, dtype: i
     device allocation); see include/bbc.h for the size limit and sharing."""
     _check(ctx, _lib.bbc_run_slice_static(ctx, t, ctypes.c_void_p(light_ptr), ctypes.c_void_p(strange_ptr), dtype,
                                           ctypes.c_void_p(out_ptr), int(normalised)))
+
+
+def bbc_project(ctx, c_ptr: int, n_fields: int, r_ptr, ra1_ptr):
+    """Source spin states |J M> (R) and their cubic-group A1 average (Ra1) of
+    correlators [n_fields][L^3][16]; either output pointer may be None."""
+    _check(ctx, _lib.bbc_project(ctx, ctypes.c_void_p(c_ptr), n_fields,
+                                 ctypes.c_void_p(r_ptr) if r_ptr else None,
+                                 ctypes.c_void_p(ra1_ptr) if ra1_ptr else None))
 
 
 def bbc_last_error(ctx) -> str:
@@ -243,6 +252,27 @@ class Correlators:
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
         return out
+
+    def project(self, C, R=None, Ra1=None, a1: bool = True):
+        """Spin states |J M> and, with ``a1``, the cubic-group A1 average of
+        correlators C [..., V, 16] complex128 on the GPU (bbc_project).
+        Returns (R, Ra1); Ra1 is None without ``a1``."""
+        torch = self.torch
+        if C.dtype != torch.complex128 or not C.is_cuda or not C.is_contiguous() or C.shape[-2:] != (self.V, 16):
+            raise ValueError(f"C must be a contiguous complex128 CUDA tensor [..., {self.V}, 16]")
+        n_fields = C.numel() // (self.V * 16)
+        if R is None:
+            R = torch.empty_like(C)
+        if a1 and Ra1 is None:
+            Ra1 = torch.empty_like(C)
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            bbc_project(self.ctx, C.data_ptr(), n_fields, R.data_ptr(), Ra1.data_ptr() if a1 else None)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+        return R, (Ra1 if a1 else None)
 
     def capture(self, S_light, S_strange, times, out, normalised: bool = True):
         """Record run(...) for these slices into one CUDA graph (after an eager

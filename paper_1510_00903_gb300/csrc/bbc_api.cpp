@@ -382,6 +382,26 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   return BBC_OK;
 }
 
+bbc_status bbc_project(bbc_ctx* c, const void* C_dev, int n_fields, void* R_dev, void* Ra1_dev) {
+  if (!c) return BBC_EINVAL;
+  if (n_fields < 0 || n_fields > 65535) return fail(c, BBC_EINVAL, "n_fields must be in [0, 65535]");
+  if (!C_dev || (!R_dev && !Ra1_dev)) return fail(c, BBC_EINVAL, "need an input and at least one output");
+  if (((uintptr_t)C_dev | (uintptr_t)R_dev | (uintptr_t)Ra1_dev) & 15)
+    return fail(c, BBC_EINVAL, "pointers must be 16-byte aligned");
+  const size_t n = (size_t)n_fields * c->V * 16 * 16;
+  auto overlap = [n](const void* a, const void* b) {
+    if (!a || !b) return false;
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+  };
+  if (overlap(C_dev, R_dev) || overlap(C_dev, Ra1_dev) || overlap(R_dev, Ra1_dev))
+    return fail(c, BBC_EINVAL, "input and outputs must not overlap");
+  StageScope scope(c, BBC_STAGE_PROJECT);
+  cudaError_t e = bbc::launch_project(C_dev, c->lat.L, n_fields, R_dev, Ra1_dev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "projection");
+  return BBC_OK;
+}
+
 bbc_status bbc_plan_stats(const bbc_ctx* c, int channel_pos, int term3, int term4, int* n_diagrams,
                           int* iters_signed, int cap) {
   if (!c || !n_diagrams) return BBC_EINVAL;

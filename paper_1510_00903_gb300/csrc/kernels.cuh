@@ -89,4 +89,8 @@ cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* ta
 cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
                              void* ct, bool fp64, cudaStream_t st);
 
+// Source spin-state projection R (and, if Ra1 is not null, its average over
+// the 24 cubic rotations of r) of C[n_fields][L^3][16] complex128.
+cudaError_t launch_project(const void* C, int L, int n_fields, void* R, void* Ra1, cudaStream_t st);
+
 }  // namespace bbc

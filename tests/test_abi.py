@@ -67,3 +67,21 @@ def test_mixed_workspace_is_smaller():
     finally:
         bbc.bbc_destroy(a)
         bbc.bbc_destroy(b)
+
+
+def test_project_rejects_bad_arguments():
+    """Argument checks of bbc_project run before any device work."""
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0])
+    try:
+        n = 2 * 64 * 16 * 16  # bytes of two fields at L = 4
+        for args in [(1 << 20, 2, None, None),             # no output
+                     (1 << 20, 2, (1 << 20) + n - 16, None),  # R overlaps C
+                     (1 << 20, 2, None, 1 << 20),           # Ra1 is C
+                     (1 << 20, 2, 1 << 24, (1 << 24) + 256),  # R overlaps Ra1
+                     ((1 << 20) + 8, 2, 1 << 24, None),     # misaligned
+                     (1 << 20, -1, 1 << 24, None)]:         # negative count
+            with pytest.raises(bbc.BBCError) as e:
+                bbc.bbc_project(c, *args)
+            assert e.value.status == bbc.BBC_EINVAL, args
+    finally:
+        bbc.bbc_destroy(c)
