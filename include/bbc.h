@@ -181,8 +181,8 @@ bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, 
  * The D-wave part of Sec. 2 is R - Ra1.  R_dev or Ra1_dev may be NULL (not
  * both); neither may overlap C_dev.  All three are device pointers, 16-byte
  * aligned, of n_fields * L^3 * 16 complex128 (L of the context).  FP64 on the
- * context stream, asynchronous.  The first call on a device uploads a 24-entry
- * rotation table (make it before any stream capture).  Errors: EINVAL. */
+ * context stream, asynchronous; needs the workspace attached (it holds the
+ * orbit table of the rotations on the lattice).  Errors: EINVAL, ESTATE. */
 bbc_status bbc_project(bbc_ctx* ctx, const void* C_dev, int n_fields, void* R_dev, void* Ra1_dev);
 
 /* Bytes of the static device array used by bbc_run_slice_static. */

@@ -27,7 +27,7 @@ size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
   size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
-  size_t batches, wptr, wunits, qlist, tables_end;
+  size_t batches, wptr, wunits, qlist, orb_ptr, orb_site, tables_end;
   size_t stage, prop, amax, kexp, blk, blkf, P, ct, scale, total;
 };
 
@@ -48,6 +48,8 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.wptr = o; o = align256(o + sizeof(int) * c->wptr.size());
   L.wunits = o; o = align256(o + sizeof(int4) * c->wunits.size());
   L.qlist = o; o = align256(o + sizeof(int) * c->qlist.size());
+  L.orb_ptr = o; o = align256(o + sizeof(int) * c->orb_ptr.size());
+  L.orb_site = o; o = align256(o + sizeof(int) * c->orb_site.size());
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -160,6 +162,22 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
     if (q <= nq) c->qlist.push_back(q);
   }
+  bbc::cubic_orbits(lat->L, c->orb_ptr, c->orb_site);
+  {  // the kernel indexes sites through this table: it must be a partition of the lattice
+    std::vector<char> hit(c->V, 0);
+    bool ok = c->orb_ptr.front() == 0 && c->orb_ptr.back() == c->V && (int)c->orb_site.size() == c->V;
+    for (size_t k = 0; ok && k + 1 < c->orb_ptr.size(); k++)
+      ok = c->orb_ptr[k + 1] > c->orb_ptr[k] && c->orb_ptr[k + 1] - c->orb_ptr[k] <= 24;
+    for (int s : c->orb_site) {
+      if (!ok) break;
+      ok = s >= 0 && s < c->V && !hit[s];
+      if (ok) hit[s] = 1;
+    }
+    if (!ok) {
+      delete c;
+      return fail(nullptr, BBC_EINVAL, "internal: cubic orbit table is not a partition of the lattice");
+    }
+  }
   *ctx = c;
   return BBC_OK;
 }
@@ -198,6 +216,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_wptr = (int*)(w + L.wptr);
   c->d_wunits = (int4*)(w + L.wunits);
   c->d_qlist = (int*)(w + L.qlist);
+  c->d_orb_ptr = (int*)(w + L.orb_ptr);
+  c->d_orb_site = (int*)(w + L.orb_site);
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
   c->d_amax = (unsigned long long*)(w + L.amax);
@@ -245,6 +265,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_wptr, c->wptr.data(), sizeof(int) * c->wptr.size()},
       {c->d_wunits, wu.data(), sizeof(int4) * wu.size()},
       {c->d_qlist, c->qlist.data(), sizeof(int) * c->qlist.size()},
+      {c->d_orb_ptr, c->orb_ptr.data(), sizeof(int) * c->orb_ptr.size()},
+      {c->d_orb_site, c->orb_site.data(), sizeof(int) * c->orb_site.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -397,7 +419,9 @@ bbc_status bbc_project(bbc_ctx* c, const void* C_dev, int n_fields, void* R_dev,
   if (overlap(C_dev, R_dev) || overlap(C_dev, Ra1_dev) || overlap(R_dev, Ra1_dev))
     return fail(c, BBC_EINVAL, "input and outputs must not overlap");
   StageScope scope(c, BBC_STAGE_PROJECT);
-  cudaError_t e = bbc::launch_project(C_dev, c->lat.L, n_fields, R_dev, Ra1_dev, c->stream);
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  cudaError_t e = bbc::launch_project(C_dev, c->lat.L, c->d_orb_ptr, c->d_orb_site, (int)c->orb_ptr.size() - 1,
+                                      n_fields, R_dev, Ra1_dev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "projection");
   return BBC_OK;
 }

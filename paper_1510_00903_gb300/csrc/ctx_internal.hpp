@@ -42,6 +42,10 @@ struct bbc_ctx {
   int* d_wptr = nullptr;
   int4* d_wunits = nullptr;
   int* d_qlist = nullptr;
+  // orbits of the cubic rotations on the lattice (bbc_project)
+  std::vector<int> orb_ptr, orb_site;
+  int* d_orb_ptr = nullptr;
+  int* d_orb_site = nullptr;
   char* d_stage = nullptr;               // [slots][2][V*144] c128 staging of host input
   char* d_prop = nullptr;                // [slots][2][V*144] compute precision
   unsigned long long* d_amax = nullptr;  // [slots][2]

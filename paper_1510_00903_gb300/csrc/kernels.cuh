@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -89,8 +90,13 @@ cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* ta
 cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
                              void* ct, bool fp64, cudaStream_t st);
 
-// Source spin-state projection R (and, if Ra1 is not null, its average over
-// the 24 cubic rotations of r) of C[n_fields][L^3][16] complex128.
-cudaError_t launch_project(const void* C, int L, int n_fields, void* R, void* Ra1, cudaStream_t st);
+// Orbits of the 24 cubic rotations on the periodic L^3 lattice (host):
+// orbit k = orb_site[orb_ptr[k] .. orb_ptr[k+1]), each site exactly once.
+void cubic_orbits(int L, std::vector<int>& orb_ptr, std::vector<int>& orb_site);
+// Source spin-state projection R and/or (Ra1 not null) its average over the
+// 24 cubic rotations of r, of C[n_fields][L^3][16] complex128; orbit tables
+// on the device.
+cudaError_t launch_project(const void* C, int L, const int* orb_ptr, const int* orb_site, int n_orb, int n_fields,
+                           void* R, void* Ra1, cudaStream_t st);
 
 }  // namespace bbc
