@@ -87,28 +87,40 @@ __global__ void __launch_bounds__(256) k_project(const double2* __restrict__ C, 
   const int n = m1 - m0;
   const int n_other = __shfl_xor_sync(0xffffffffu, n, 16);
   const int n_max = n > n_other ? n : n_other;  // both groups of the warp loop together (shuffles)
+  // member sites: lane s of the group holds members s and s + 16 (orbits have
+  // at most 24), broadcast by shuffles so the record loads do not wait on them
+  const int site_a = s < n ? __ldg(&orb_site[m0 + s]) : 0;
+  const int site_b = s + 16 < n ? __ldg(&orb_site[m0 + 16 + s]) : 0;
   cpx<double> acc(0.0, 0.0);
-  for (int i = 0; i < n_max; i++) {
-    const bool mine = i < n;
-    const int site = mine ? __ldg(&orb_site[m0 + i]) : 0;
-    cpx<double> v(0.0, 0.0);
-    if (mine) {
-      const double2 d = __ldg(&C[fbase + (size_t)site * 16 + s]);
-      v = cpx<double>(d.x, d.y);
+  for (int i0 = 0; i0 < n_max; i0 += 8) {
+    cpx<double> v[8];
+    int site[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {  // eight independent record loads in flight
+      const int i = i0 + j;
+      site[j] = __shfl_sync(0xffffffffu, i < 16 ? site_a : site_b, grp + (i & 15));
+      v[j] = cpx<double>(0.0, 0.0);
+      if (i < n) {
+        const double2 d = __ldg(&C[fbase + (size_t)site[j] * 16 + s]);
+        v[j] = cpx<double>(d.x, d.y);
+      }
     }
-    acc.re += v.re;
-    acc.im += v.im;
-    if (R) {
-      const cpx<double> o = spin_states(v, grp, s);
-      if (mine) R[fbase + (size_t)site * 16 + s] = make_double2(o.re, o.im);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      acc.re += v[j].re;
+      acc.im += v[j].im;
+      if (R) {
+        const cpx<double> o = spin_states(v[j], grp, s);
+        if (i0 + j < n) R[fbase + (size_t)site[j] * 16 + s] = make_double2(o.re, o.im);
+      }
     }
   }
   if (!Ra1) return;  // uniform over the grid
   const double inv = n > 0 ? 1.0 / n : 0.0;
   const cpx<double> o = spin_states(cpx<double>(acc.re * inv, acc.im * inv), grp, s);
-  for (int i = 0; i < n; i++) {
-    const int site = __ldg(&orb_site[m0 + i]);
-    Ra1[fbase + (size_t)site * 16 + s] = make_double2(o.re, o.im);
+  for (int i = 0; i < n_max; i++) {
+    const int site = __shfl_sync(0xffffffffu, i < 16 ? site_a : site_b, grp + (i & 15));
+    if (i < n) Ra1[fbase + (size_t)site * 16 + s] = make_double2(o.re, o.im);
   }
 }
 
