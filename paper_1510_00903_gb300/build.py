@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                          "-I", INC, "-c", src, "-o", obj])
         elif f.endswith(".cpp"):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-I", INC,
+            jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-I", INC,
                          "-I", os.path.join(cuda, "include"), "-c", src, "-o", obj])
 
     def run(cmd):

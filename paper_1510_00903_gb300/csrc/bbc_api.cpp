@@ -8,6 +8,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -27,7 +29,7 @@ size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
 struct Layout {
   size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
-  size_t batches, wptr, wunits, qlist, orb_ptr, orb_site, tables_end;
+  size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
   size_t stage, prop, amax, kexp, blk, blkf, P, ct, scale, total;
 };
 
@@ -48,6 +50,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.wptr = o; o = align256(o + sizeof(int) * c->wptr.size());
   L.wunits = o; o = align256(o + sizeof(int4) * c->wunits.size());
   L.qlist = o; o = align256(o + sizeof(int) * c->qlist.size());
+  L.row_slot = o; o = align256(o + sizeof(int) * c->row_slot.size());
   L.orb_ptr = o; o = align256(o + sizeof(int) * c->orb_ptr.size());
   L.orb_site = o; o = align256(o + sizeof(int) * c->orb_site.size());
   L.tables_end = o;
@@ -121,6 +124,27 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
   return g;
 }
 
+// Warp batches and shared-memory bank layout of the fused contraction depend
+// on the channel list only; computed once per list and process.
+struct FusedSchedule {
+  std::vector<bbc::Batch> batches;
+  std::vector<int> wptr;
+  std::vector<bbc::BatchUnit> wunits;
+  bbc::FusedLayout layout;
+};
+std::mutex g_sched_mutex;
+std::map<std::vector<int>, FusedSchedule> g_sched;
+
+const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
+  std::lock_guard<std::mutex> lock(g_sched_mutex);
+  auto it = g_sched.find(plan.channels);
+  if (it != g_sched.end()) return it->second;
+  FusedSchedule f;
+  bbc::make_warp_batches(plan, bbc::kFusedWarps, 18, &f.batches, &f.wptr, &f.wunits);
+  bbc::optimise_fused_layout(plan, &f.batches, &f.layout);
+  return g_sched.emplace(plan.channels, std::move(f)).first->second;
+}
+
 }  // namespace
 
 extern "C" {
@@ -155,8 +179,29 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   // warp task groups of the pair products: enough warps per 32 q to fill the
   // GPU several times over at L = 16 (V/32 q tiles x groups warps)
   bbc::make_task_groups(c->plan, 48, &c->group_ptr, &c->group_task);
-  // fused FP32 contraction: warp batches and one q of every pair {q, -q}
-  bbc::make_warp_batches(c->plan, bbc::kFusedWarps, 18, &c->batches, &c->wptr, &c->wunits);
+  // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
+  if (prec == BBC_MIXED_FP32) {
+    try {
+      const FusedSchedule& f = fused_schedule(c->plan);
+      c->batches = f.batches;
+      c->wptr = f.wptr;
+      c->wunits = f.wunits;
+      c->row_slot = f.layout.row_slot;
+      c->n_slots = f.layout.n_slots;
+    } catch (const std::bad_alloc&) {
+      delete c;
+      return fail(nullptr, BBC_ENOMEM, "host allocation failed while scheduling");
+    }
+    // the kernel stages row i at row_slot[i] and reads slot offA + k: slots
+    // must be increasing (no two rows share one) and inside n_slots
+    bool ok = (int)c->row_slot.size() == c->plan.n_out;
+    for (int i = 0; ok && i < c->plan.n_out; i++)
+      ok = c->row_slot[i] >= (i ? c->row_slot[i - 1] + 1 : 0) && c->row_slot[i] < c->n_slots;
+    if (!ok) {
+      delete c;
+      return fail(nullptr, BBC_EINVAL, "internal: fused shared-memory layout is not a valid row map");
+    }
+  }
   for (int q = 0; q < c->V; q++) {
     const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
     const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
@@ -216,6 +261,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_wptr = (int*)(w + L.wptr);
   c->d_wunits = (int4*)(w + L.wunits);
   c->d_qlist = (int*)(w + L.qlist);
+  c->d_row_slot = (int*)(w + L.row_slot);
   c->d_orb_ptr = (int*)(w + L.orb_ptr);
   c->d_orb_site = (int*)(w + L.orb_site);
   c->d_stage = w + L.stage;
@@ -232,9 +278,12 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   for (size_t i = 0; i < p.tasks.size(); i++) {
     const bbc::PairTask& t = p.tasks[i];
     bbc::DevTask& d = tasks[i];
+    // the fused FP32 kernel addresses its shared-memory copy of the rows: a
+    // task side's rows lie in one segment, so slot(off + k) = slot(off) + k
+    const bool slots = c->prec == BBC_MIXED_FP32;
     for (int r = 0; r < 8; r++) {
-      d.offA[r] = r < t.nA ? t.offA[r] : 0;
-      d.offB[r] = r < t.nB ? t.offB[r] : 0;
+      d.offA[r] = r < t.nA ? (slots ? c->row_slot[t.offA[r]] : t.offA[r]) : 0;
+      d.offB[r] = r < t.nB ? (slots ? c->row_slot[t.offB[r]] : t.offB[r]) : 0;
     }
     d.nAnB = t.nA | (t.nB << 8);
     d.n1 = t.n1;
@@ -265,6 +314,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_wptr, c->wptr.data(), sizeof(int) * c->wptr.size()},
       {c->d_wunits, wu.data(), sizeof(int4) * wu.size()},
       {c->d_qlist, c->qlist.data(), sizeof(int) * c->qlist.size()},
+      {c->d_row_slot, c->row_slot.data(), sizeof(int) * c->row_slot.size()},
       {c->d_orb_ptr, c->orb_ptr.data(), sizeof(int) * c->orb_ptr.size()},
       {c->d_orb_site, c->orb_site.data(), sizeof(int) * c->orb_site.size()},
   };
@@ -374,7 +424,8 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   } else {
     const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
     StageScope scope(c, BBC_STAGE_CONTRACT);
-    e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_qlist, (int)c->qlist.size(), c->d_tasks,
+    e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
+                                   (int)c->qlist.size(), c->d_tasks,
                                    (int)p.tasks.size(), c->d_batches, c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem,
                                    c->d_ccoef, n_ch, c->d_ct, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused contraction");

@@ -42,6 +42,9 @@ struct bbc_ctx {
   int* d_wptr = nullptr;
   int4* d_wunits = nullptr;
   int* d_qlist = nullptr;
+  std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
+  int n_slots = 0;
+  int* d_row_slot = nullptr;
   // orbits of the cubic rotations on the lattice (bbc_project)
   std::vector<int> orb_ptr, orb_site;
   int* d_orb_ptr = nullptr;

@@ -63,7 +63,8 @@ __device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R,
 constexpr int kFusedThreads = 512;
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
-k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ qlist,
+k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ row_slot, int n_slots,
+                 const int* __restrict__ qlist,
                  const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
                  const int* __restrict__ wptr, const int4* __restrict__ wunits, const int* __restrict__ cptr,
                  const int* __restrict__ citem, const double* __restrict__ ccoef, int n_outputs,
@@ -71,8 +72,8 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = n_tasks * 16;                                        // products per side
-  const size_t region = max((size_t)n_out * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
-  float4* R = reinterpret_cast<float4*>(smem_raw);                     // [n_out] (F_q, F_-q)
+  const size_t region = max((size_t)n_slots * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
+  float4* R = reinterpret_cast<float4*>(smem_raw);                       // [n_slots] (F_q, F_-q)
   cpx<double>* Pd = reinterpret_cast<cpx<double>*>(smem_raw);         // [2][np], after the products
   cpx<float>* P = reinterpret_cast<cpx<float>*>(smem_raw + region);   // [2][np]
   const int q = qlist[blockIdx.x];
@@ -84,7 +85,7 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
     const float2* s1 = reinterpret_cast<const float2*>(blk + (size_t)nq * n_out);
     for (int i = tid; i < n_out; i += kFusedThreads) {
       const float2 x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
-      R[i] = make_float4(x.x, x.y, y.x, y.y);
+      R[__ldg(row_slot + i)] = make_float4(x.x, x.y, y.x, y.y);
     }
     float4* pz = reinterpret_cast<float4*>(P);
     for (int i = tid; i < np; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -127,20 +128,22 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
   }
 }
 
-size_t contract_fused_smem(int n_out, int n_tasks) {
+size_t contract_fused_smem(int n_slots, int n_tasks) {
   const size_t np = (size_t)n_tasks * 16;
-  return std::max((size_t)n_out * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
+  return std::max((size_t)n_slots * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
 }
 
-cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
+                                  int n_q, const DevTask* tasks,
                                   int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
                                   const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
                                   cudaStream_t st) {
-  const size_t sm = contract_fused_smem(n_out, n_tasks);
+  const size_t sm = contract_fused_smem(n_slots, n_tasks);
   static int granted[64] = {0};
   cudaError_t e = ensure_smem(k_contract_fused, sm, granted);
   if (e != cudaSuccess) return e;
-  k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, qlist, tasks, n_tasks, batches,
+  k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, row_slot, n_slots, qlist, tasks,
+                                                   n_tasks, batches,
                                                    wptr, wunits, cptr, citem, ccoef, n_ch * 16, (cpx<double>*)ct);
   return cudaGetLastError();
 }

@@ -69,11 +69,14 @@ cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, b
 cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
                                     cudaStream_t st);
 // Fused FP32 contraction of one slice from q-major blocks blk[V][n_out]: one
-// CTA per pair {q, -q} (qlist[n_q]), warp units wunits {batch, side, k0, k1}
-// (warp w owns wunits[wptr[w] .. wptr[w+1])), FP64 Wick sums into ct[V][n_ch*16].
+// CTA per pair {q, -q} (qlist[n_q]), block row i staged at shared-memory slot
+// row_slot[i] < n_slots (task offsets are slots), warp units wunits {batch,
+// side, k0, k1} (warp w owns wunits[wptr[w] .. wptr[w+1])), FP64 Wick sums
+// into ct[V][n_ch*16].
 constexpr int kFusedWarps = 16;
-size_t contract_fused_smem(int n_out, int n_tasks);
-cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* qlist, int n_q, const DevTask* tasks,
+size_t contract_fused_smem(int n_slots, int n_tasks);
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
+                                  int n_q, const DevTask* tasks,
                                   int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
                                   const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
                                   cudaStream_t st);

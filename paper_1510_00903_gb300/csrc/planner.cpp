@@ -699,6 +699,195 @@ void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch
   }
 }
 
+namespace {
+
+// Exact bank model of the fused products' 128-bit shared-memory loads.
+struct BankModel {
+  const Plan& p;
+  std::vector<int> seg_of_row;  // n_out
+  std::vector<int> res;         // shift residue (mod 8) per segment
+  std::vector<int> shift;       // non-decreasing shifts with those residues
+  // per task: rows read at (k, operand row), A rows then B rows: [K][nA + nB]
+  std::vector<std::vector<int>> rows, slots;
+
+  void init_rows() {
+    rows.resize(p.tasks.size());
+    for (size_t ti = 0; ti < p.tasks.size(); ti++) {
+      const PairTask& t = p.tasks[ti];
+      std::vector<int>& v = rows[ti];
+      for (int i1 = 0; i1 < t.n1; i1++)
+        for (int i2 = 0; i2 < t.n2; i2++) {
+          for (int r = 0; r < t.nA; r++) v.push_back(t.offA[r] + i1 * t.sA1 + i2 * t.sA2);
+          for (int r = 0; r < t.nB; r++) v.push_back(t.offB[r] + i1 * t.sB1 + i2 * t.sB2);
+        }
+    }
+  }
+  void update_shifts() {
+    shift.assign(res.size(), 0);
+    for (size_t s = 0; s < res.size(); s++) {
+      const int prev = s ? shift[s - 1] : 0;
+      shift[s] = prev + (((res[s] - prev) % 8) + 8) % 8;
+    }
+    slots.resize(rows.size());
+    for (size_t ti = 0; ti < rows.size(); ti++) {
+      slots[ti].resize(rows[ti].size());
+      for (size_t j = 0; j < rows[ti].size(); j++) slots[ti][j] = rows[ti][j] + shift[seg_of_row[rows[ti][j]]];
+    }
+  }
+  int slot(int row) const { return row + shift[seg_of_row[row]]; }
+  // wavefronts of lanes [l0, l1) (one phase) of a batch over every load
+  long long phase_cost(const std::vector<int>& tasks, int l0, int l1) const {
+    if (l0 >= l1) return 0;
+    const size_t n = slots[tasks[l0]].size();
+    const int* sl[8];
+    const int nl = l1 - l0;
+    for (int l = 0; l < nl; l++) sl[l] = slots[tasks[l0 + l]].data();
+    long long w = 0;
+    for (size_t j = 0; j < n; j++) {
+      int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, m = 0;
+      for (int l = 0; l < nl; l++) {
+        const int a = sl[l][j];
+        bool dup = false;
+        for (int i = 0; i < l; i++) dup |= sl[i][j] == a;
+        if (!dup) m = std::max(m, ++cnt[a & 7]);
+      }
+      w += m;
+    }
+    return w;
+  }
+};
+
+}  // namespace
+
+void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedLayout* out) {
+  const int n_out = plan.n_out;
+  BankModel m{plan, std::vector<int>(n_out, 0), {}, {}, {}, {}};
+  m.init_rows();
+  // operand segments: merged row spans of every task side
+  std::vector<std::pair<int, int>> span;
+  for (size_t ti = 0; ti < plan.tasks.size(); ti++) {
+    const PairTask& t = plan.tasks[ti];
+    const std::vector<int>& v = m.rows[ti];
+    for (int side = 0; side < 2; side++) {
+      int lo = n_out, hi = -1;
+      const int nr = t.nA + t.nB, r0 = side ? t.nA : 0, r1 = side ? nr : t.nA;
+      for (size_t j = 0; j < v.size(); j++) {
+        const int r = (int)(j % nr);
+        if (r < r0 || r >= r1) continue;
+        lo = std::min(lo, v[j]);
+        hi = std::max(hi, v[j]);
+      }
+      if (hi >= 0) span.push_back({lo, hi});
+    }
+  }
+  std::sort(span.begin(), span.end());
+  std::vector<int> seg_first(1, 0);
+  int end = -1;
+  for (const auto& sp : span) {
+    if (sp.first > end && sp.first > 0 && sp.first != seg_first.back()) seg_first.push_back(sp.first);
+    end = std::max(end, sp.second);
+  }
+  for (size_t s = 0; s < seg_first.size(); s++) {
+    const int e = s + 1 < seg_first.size() ? seg_first[s + 1] : n_out;
+    for (int r = seg_first[s]; r < e; r++) m.seg_of_row[r] = (int)s;
+  }
+  m.res.assign(seg_first.size(), 0);
+  m.update_shifts();
+  // phases: (batch, first lane); cost cache
+  auto phase_end = [&](int b, int p0) { return std::min((int)(*batches)[b].tasks.size(), p0 + 8); };
+  auto total = [&]() {
+    long long w = 0;
+    for (int b = 0; b < (int)batches->size(); b++)
+      for (int p0 = 0; p0 < (int)(*batches)[b].tasks.size(); p0 += 8) w += m.phase_cost((*batches)[b].tasks, p0, phase_end(b, p0));
+    return w;
+  };
+  // batches of one class (same nA and open-index length) may trade tasks
+  std::map<std::pair<int, int>, std::vector<int>> cls;
+  for (int i = 0; i < (int)batches->size(); i++) {
+    const PairTask& t = plan.tasks[(*batches)[i].tasks[0]];
+    cls[{t.nA, t.n1 * t.n2}].push_back(i);
+  }
+  long long best = total();
+  // segments each task reads.  A residue change of segment s moves later
+  // segments by multiples of 8 only (same bank groups; segments never share
+  // an address), so a trial on s re-costs just the phases that read s.
+  std::vector<std::vector<char>> task_reads(plan.tasks.size(), std::vector<char>(seg_first.size(), 0));
+  for (size_t ti = 0; ti < plan.tasks.size(); ti++)
+    for (int r : m.rows[ti]) task_reads[ti][m.seg_of_row[r]] = 1;
+  for (int sweep = 0; sweep < 3; sweep++) {
+    bool improved = false;
+    for (size_t s = 0; s < m.res.size(); s++) {  // segment shifts, one at a time
+      std::vector<std::pair<int, int>> touched;  // phases reading segment s
+      long long old_cost = 0;
+      for (int b = 0; b < (int)batches->size(); b++) {
+        const std::vector<int>& T = (*batches)[b].tasks;
+        for (int p0 = 0; p0 < (int)T.size(); p0 += 8) {
+          bool hit = false;
+          for (int l = p0; l < phase_end(b, p0); l++) hit |= task_reads[T[l]][s] != 0;
+          if (!hit) continue;
+          touched.push_back({b, p0});
+          old_cost += m.phase_cost(T, p0, phase_end(b, p0));
+        }
+      }
+      int keep = m.res[s];
+      long long keep_cost = old_cost;
+      for (int v = 0; v < 8; v++) {
+        if (v == m.res[s]) continue;
+        const int saved = m.res[s];
+        m.res[s] = v;
+        m.update_shifts();
+        long long w = 0;
+        for (const auto& ph : touched) w += m.phase_cost((*batches)[ph.first].tasks, ph.second, phase_end(ph.first, ph.second));
+        if (w < keep_cost) { keep_cost = w; keep = v; }
+        m.res[s] = saved;
+      }
+      if (keep_cost < old_cost) { best += keep_cost - old_cost; improved = true; }
+      m.res[s] = keep;
+      m.update_shifts();
+    }
+    for (auto& kv : cls) {  // pairwise exchanges of lanes in different phases
+      std::vector<std::pair<int, int>> pos;  // (batch, lane)
+      std::map<std::pair<int, int>, long long> cost, ideal;
+      for (int b : kv.second) {
+        const std::vector<int>& T = (*batches)[b].tasks;
+        for (int l = 0; l < (int)T.size(); l++) pos.push_back({b, l});
+        for (int p0 = 0; p0 < (int)T.size(); p0 += 8) {
+          cost[{b, p0}] = m.phase_cost(T, p0, phase_end(b, p0));
+          ideal[{b, p0}] = (long long)m.slots[T[p0]].size();
+        }
+      }
+      for (size_t i = 0; i < pos.size(); i++)
+        for (size_t j = i + 1; j < pos.size(); j++) {
+          const int b1 = pos[i].first, l1 = pos[i].second, b2 = pos[j].first, l2 = pos[j].second;
+          const int p1 = l1 / 8 * 8, p2 = l2 / 8 * 8;
+          if (b1 == b2 && p1 == p2) continue;
+          const std::pair<int, int> k1{b1, p1}, k2{b2, p2};
+          if (cost[k1] == ideal[k1] && cost[k2] == ideal[k2]) continue;  // both conflict-free already
+          std::vector<int>& T1 = (*batches)[b1].tasks;
+          std::vector<int>& T2 = (*batches)[b2].tasks;
+          std::swap(T1[l1], T2[l2]);
+          const long long c1 = m.phase_cost(T1, p1, phase_end(b1, p1)), c2 = m.phase_cost(T2, p2, phase_end(b2, p2));
+          if (c1 + c2 < cost[k1] + cost[k2]) {
+            best += c1 + c2 - cost[k1] - cost[k2];
+            cost[k1] = c1;
+            cost[k2] = c2;
+            improved = true;
+          } else {
+            std::swap(T1[l1], T2[l2]);
+          }
+        }
+    }
+    if (!improved) break;
+  }
+  out->row_slot.resize(n_out);
+  for (int r = 0; r < n_out; r++) out->row_slot[r] = m.slot(r);
+  out->n_slots = n_out + (m.shift.empty() ? 0 : m.shift.back());
+  out->wavefronts = best;
+  long long ideal = 0;
+  for (const Batch& b : *batches) ideal += (long long)m.slots[b.tasks[0]].size() * (((int)b.tasks.size() + 7) / 8);
+  out->ideal = ideal;
+}
+
 void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task) {
   std::vector<int> order(plan.tasks.size());
   std::iota(order.begin(), order.end(), 0);

@@ -86,6 +86,24 @@ struct BatchUnit {
 void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch>* batches, std::vector<int>* warp_ptr,
                        std::vector<BatchUnit>* units);
 
+// Shared-memory row layout of the fused contraction.  The block rows one task
+// side reads lie in one operand segment (the union of overlapping operand
+// spans); a segment's rows move together by shift[s] (so a task's open-index
+// strides are unchanged), and only shift mod 8 decides the bank group of a
+// 16-byte row (eight groups of four 4-byte banks).  optimise_fused_layout
+// chooses the segment shifts and the task order inside every class of
+// batches (tasks may trade places between batches of one class) to minimise
+// the shared-memory wavefronts of the products' 128-bit loads, on an exact
+// model of the banks: a warp's 128-bit load runs as four phases of eight
+// lanes; distinct addresses in one bank group serialise, equal ones broadcast.
+struct FusedLayout {
+  std::vector<int> row_slot;  // n_out: shared-memory slot of each block row
+  int n_slots = 0;            // slots including the gaps
+  long long wavefronts = 0;   // modelled 128-bit wavefronts of one {q, -q} pair
+  long long ideal = 0;        // the same without any bank conflict
+};
+void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedLayout* out);
+
 // Partition of the tasks into `groups` lists of near-equal cost (longest task
 // first to the cheapest list); each list is run by one warp for 32 q at a time.
 void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task);
