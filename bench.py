@@ -273,9 +273,10 @@ def run_ours(args, torch, rank, world, local):
         bbc.bbc_enable_stage_timing(cor.ctx, False)
         return max_over_ranks(ms), stages
 
-    # plain FP64 path (headline)
+    # plain FP64 path (headline); launch shapes autotuned on slice 0 before timing
     cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=bbc.BBC_FP64, device=dev, stream=stream)
     sizes = cor.sizes()
+    tune_fp64, tune_fp64_ms = cor.autotune(Sl[0], Ss[0], t=0, reps=3)
     sampler = ClockSampler(local)
     ms, stages = timed(cor, args.steps, args.warmup, sampler=sampler)
     clocks = sampler.summary()
@@ -303,6 +304,7 @@ def run_ours(args, torch, rank, world, local):
     if not args.no_mixed:
         corm = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=bbc.BBC_MIXED_FP32, device=dev,
                                stream=stream)
+        tune_m, tune_m_ms = corm.autotune(Sl[0], Ss[0], t=0, reps=3)
         ms_m, st_m = timed(corm, args.steps, args.warmup)
         corm.close()
         cm_ms, cm_n = st_m["contract"]
@@ -310,7 +312,8 @@ def run_ours(args, torch, rank, world, local):
         mixed = {"value": shard.job_throughput(V * T * N_CH, world, ms_m), "ms_per_step": ms_m, "speedup_vs_fp64": ms / ms_m,
                  "stage_ms_per_step": {k: v[0] / args.steps for k, v in st_m.items()},
                  "contract_tflops": flops_per_launch / (cm_avg * 1e-3) / 1e12,
-                 "contract_frac_fp32_peak": flops_per_launch / (cm_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
+                 "contract_frac_fp32_peak": flops_per_launch / (cm_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                 "tuning": tune_m, "autotune_ms": tune_m_ms}
 
     if rank != 0:
         return
@@ -337,6 +340,7 @@ def run_ours(args, torch, rank, world, local):
         "roofline": roofline,
         "stage_ms_per_step": stage_ms,
         "plan": sizes,
+        "tuning": {"chosen": tune_fp64, "autotune_ms": tune_fp64_ms},
         "mixed": mixed,
         "projection": projection,
         "cpu_baseline": cpu,
@@ -418,6 +422,7 @@ def run_batched(args, torch, dev, bbc):
               for i, (L, T) in enumerate(lattices)]
     b = bbc.LatticeBatch(lattices, inputs, n_sources=4, channels=list(range(N_CH)), precision=bbc.BBC_MIXED_FP32,
                          device=dev)
+    tuned = b.autotune()
     t_cap = time.perf_counter()
     g = b.capture()
     t_cap = time.perf_counter() - t_cap
@@ -449,7 +454,8 @@ def run_batched(args, torch, dev, bbc):
                      "(t0 = 0, T/4, T/2, 3T/4), 52 channels, mixed precision, complex64 propagators, "
                      "one CUDA graph per step", "slices_per_step": slices,
                      "l2": "no flush: block fields of one slice (>= 241 MB) exceed the 129 MB L2"},
-          "graph": {"capture_s": t_cap, "launches_per_step": 1}, "clocks": sampler.summary()})
+          "graph": {"capture_s": t_cap, "launches_per_step": 1}, "tuning": {str(k): v for k, v in tuned.items()},
+          "clocks": sampler.summary()})
 
 
 def run_l48(args, torch, dev, bbc):
@@ -469,6 +475,10 @@ def run_l48(args, torch, dev, bbc):
                             precision=bbc.BBC_MIXED_FP32, device=dev, stream=stream, workspace=ws)
         ws = c.workspace
         cors.append(c)
+    with torch.cuda.stream(stream):
+        tuned, _ = cors[0].autotune(S_host[0][0], S_host[1][0], t=0, reps=2)
+    for c in cors[1:]:
+        c.set_tuning(tuned)
     out = torch.empty((N_CH, L ** 3, 16), dtype=torch.complex128, device=dev)
 
     def step():
@@ -507,7 +517,7 @@ def run_l48(args, torch, dev, bbc):
                      "streamed host->device per slice inside the step", "h2d_bytes_per_step": int(
                          n_src * T * 2 * L ** 3 * 144 * 8),
                      "l2": "no flush: block fields of one slice (6.5 GB) exceed the 129 MB L2"},
-          "clocks": sampler.summary()})
+          "tuning": tuned, "clocks": sampler.summary()})
 
 
 class _Null:

@@ -166,6 +166,42 @@ bbc_status bbc_stage_timing(bbc_ctx* ctx, double* ms, long long* launches);
  * bbc_build_blocks call per slot-batch, and one bbc_load_propagator call. */
 bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, int* per_contract);
 
+/* Launch configuration of the two kernels whose shape is tunable:
+ *  build_sites, build_threads: sites per CTA and threads of the block build,
+ *    one of (1, 256), (2, 256), (2, 512), (4, 512); a CTA keeps the
+ *    propagators, diquarks and sink-tensor entries of its sites in shared
+ *    memory (configurations that need more than 227 KB are not valid);
+ *  fused_warps, fused_chunk (BBC_MIXED_FP32 only): warps per CTA (8, 12, 16)
+ *    of the fused q-space contraction and the open-index steps per warp unit
+ *    (9, 18, 36, 72).
+ * A new context starts with (1, 256, 16, 18), or with the configuration
+ * bbc_autotune chose earlier in the process for the same L, precision and
+ * channel list. */
+typedef struct {
+  int build_sites, build_threads;
+  int fused_warps, fused_chunk;
+} bbc_tuning;
+
+bbc_status bbc_get_tuning(const bbc_ctx* ctx, bbc_tuning* out);
+
+/* Set a configuration (EINVAL if unsupported; the fused fields are ignored
+ * for BBC_FP64).  Synchronises the context stream when a workspace is
+ * attached (uploads the warp schedule).  Not inside a stream capture. */
+bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
+
+/* Autotuner: times every valid candidate configuration with CUDA events on
+ * the context stream, `reps` launches each after one untimed launch, on the
+ * propagators loaded in slot 0 -- the block-build candidates in the order
+ * above, then (BBC_MIXED_FP32) every (fused_warps, fused_chunk) pair in
+ * row-major order -- keeps the fastest of each kernel, rebuilds slot 0 with
+ * it, and records it for later contexts with the same L, precision and
+ * channel list.  ms[i] (i < cap) receives the average milliseconds per launch
+ * of candidate i (-1 for a candidate that is not valid here); *n_tried the
+ * number of candidates; *best the chosen configuration.  ms, best, n_tried
+ * may be NULL.  Synchronous; not inside a stream capture.  Errors: ESTATE (no
+ * workspace, slot 0 not loaded), EINVAL (reps outside [1, 1000]), ECUDA. */
+bbc_status bbc_autotune(bbc_ctx* ctx, int reps, bbc_tuning* best, double* ms, int cap, int* n_tried);
+
 /* Projections of Sec. 2 (the source operator of total spin J, M in the
  * equation for R^(J,M), and the operator P of the 3S1 / 3D1 split) applied to
  * correlators in the layout bbc_contract writes: C_dev[n_fields][L^3][16]

@@ -32,6 +32,14 @@ class BBCError(RuntimeError):
         self.status = status
 
 
+class bbc_tuning(ctypes.Structure):
+    _fields_ = [("build_sites", ctypes.c_int), ("build_threads", ctypes.c_int),
+                ("fused_warps", ctypes.c_int), ("fused_chunk", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class bbc_lattice(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("t0", ctypes.c_int),
                 ("m_ud", ctypes.c_double), ("m_s", ctypes.c_double)]
@@ -56,6 +64,10 @@ def _load():
         "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "bbc_run_slice_static": ([P, I, P, P, I, P, I], I),
         "bbc_project": ([P, P, I, P, P], I),
+        "bbc_get_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
+        "bbc_set_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
+        "bbc_autotune": ([P, I, ctypes.POINTER(bbc_tuning), ctypes.POINTER(ctypes.c_double), I,
+                          ctypes.POINTER(I)], I),
         "bbc_last_error": ([P], ctypes.c_char_p),
         "bbc_destroy": ([P], None),
     }
@@ -163,6 +175,27 @@ def bbc_project(ctx, c_ptr: int, n_fields: int, r_ptr, ra1_ptr):
                                  ctypes.c_void_p(ra1_ptr) if ra1_ptr else None))
 
 
+def bbc_get_tuning(ctx) -> dict:
+    t = bbc_tuning()
+    _check(ctx, _lib.bbc_get_tuning(ctx, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def bbc_set_tuning(ctx, build_sites: int, build_threads: int, fused_warps: int = 16, fused_chunk: int = 18):
+    t = bbc_tuning(build_sites, build_threads, fused_warps, fused_chunk)
+    _check(ctx, _lib.bbc_set_tuning(ctx, ctypes.byref(t)))
+
+
+def bbc_autotune(ctx, reps: int = 5):
+    """Times every candidate launch configuration on slot 0 and keeps the
+    fastest; returns (chosen configuration, [ms per candidate])."""
+    t = bbc_tuning()
+    ms = (ctypes.c_double * 64)()
+    n = ctypes.c_int()
+    _check(ctx, _lib.bbc_autotune(ctx, reps, ctypes.byref(t), ms, 64, ctypes.byref(n)))
+    return t.as_dict(), [ms[i] for i in range(min(n.value, 64))]
+
+
 def bbc_last_error(ctx) -> str:
     m = _lib.bbc_last_error(ctx)
     return m.decode() if m else ""
@@ -252,6 +285,24 @@ class Correlators:
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
         return out
+
+    def autotune(self, S_light, S_strange, t: int = 0, reps: int = 5):
+        """Load slice t into slot 0 and run the autotuner (bbc_autotune);
+        returns (configuration, ms per candidate)."""
+        torch = self.torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            self.load(BBC_LIGHT, 0, t, S_light)
+            self.load(BBC_STRANGE, 0, t, S_strange)
+            return bbc_autotune(self.ctx, reps)
+
+    def tuning(self) -> dict:
+        return bbc_get_tuning(self.ctx)
+
+    def set_tuning(self, cfg: dict):
+        bbc_set_tuning(self.ctx, cfg["build_sites"], cfg["build_threads"], cfg["fused_warps"], cfg["fused_chunk"])
 
     def project(self, C, R=None, Ra1=None, a1: bool = True):
         """Spin states |J M> and, with ``a1``, the cubic-group A1 average of
@@ -354,6 +405,19 @@ class LatticeBatch:
                         c.contract(0, out, True)
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
+
+    def autotune(self, reps: int = 3) -> dict:
+        """Autotune the first context of every distinct L on its slice 0 and
+        give the chosen configuration to every context of that L (before
+        capture).  Returns {L: configuration}."""
+        chosen = {}
+        for per, (Sl, Ss) in zip(self.cors, self.inputs):
+            L = per[0].L
+            if L not in chosen:
+                chosen[L], _ = per[0].autotune(Sl[0], Ss[0], t=0, reps=reps)
+            for c in per:
+                c.set_tuning(chosen[L])
+        return chosen
 
     def capture(self):
         """One CUDA graph for every slice of every source of every lattice."""

@@ -27,6 +27,8 @@ std::string g_create_error;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
 
+constexpr int kMaxFusedWarps = 16;
+
 struct Layout {
   size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
@@ -47,8 +49,8 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
   L.ccoef = o; o = align256(o + sizeof(double) * p.tcontrib_coef.size());
   L.batches = o; o = align256(o + sizeof(bbc::WarpBatch) * c->batches.size());
-  L.wptr = o; o = align256(o + sizeof(int) * c->wptr.size());
-  L.wunits = o; o = align256(o + sizeof(int4) * c->wunits.size());
+  L.wptr = o; o = align256(o + sizeof(int) * (kMaxFusedWarps + 1));
+  L.wunits = o; o = align256(o + sizeof(int4) * c->max_units);
   L.qlist = o; o = align256(o + sizeof(int) * c->qlist.size());
   L.row_slot = o; o = align256(o + sizeof(int) * c->row_slot.size());
   L.orb_ptr = o; o = align256(o + sizeof(int) * c->orb_ptr.size());
@@ -128,8 +130,6 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
 // on the channel list only; computed once per list and process.
 struct FusedSchedule {
   std::vector<bbc::Batch> batches;
-  std::vector<int> wptr;
-  std::vector<bbc::BatchUnit> wunits;
   bbc::FusedLayout layout;
 };
 std::mutex g_sched_mutex;
@@ -140,9 +140,73 @@ const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
   auto it = g_sched.find(plan.channels);
   if (it != g_sched.end()) return it->second;
   FusedSchedule f;
-  bbc::make_warp_batches(plan, bbc::kFusedWarps, 18, &f.batches, &f.wptr, &f.wunits);
+  bbc::make_batches(plan, &f.batches);
   bbc::optimise_fused_layout(plan, &f.batches, &f.layout);
   return g_sched.emplace(plan.channels, std::move(f)).first->second;
+}
+
+// Candidate launch configurations of the autotuner.
+const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}};  // (sites per CTA, threads)
+const int kFusedWarpsCand[] = {8, 12, 16};
+const int kChunkCand[] = {9, 18, 36, 72};
+
+// Tuned configurations per (L, precision, channel list), for later contexts.
+std::mutex g_tune_mutex;
+std::map<std::pair<std::pair<int, int>, std::vector<int>>, bbc_tuning> g_tuned;
+
+bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
+  if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
+  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, c->prec == BBC_FP64) > bbc::kMaxSmemPerBlock)
+    return false;
+  if (c->prec == BBC_MIXED_FP32) {
+    if (!bbc::fused_variant_supported(t.fused_warps)) return false;
+    bool chunk_ok = false;
+    for (int k : kChunkCand) chunk_ok |= k == t.fused_chunk;
+    if (!chunk_ok) return false;
+  }
+  return true;
+}
+
+// Warp units of the context's fused configuration, uploaded when a
+// workspace is attached (synchronous: the host vectors are temporaries).
+bbc_status apply_fused_units(bbc_ctx* c) {
+  if (c->prec != BBC_MIXED_FP32) return BBC_OK;
+  const FusedSchedule& f = fused_schedule(c->plan);
+  bbc::make_units(c->plan, f.batches, c->tune.fused_warps, c->tune.fused_chunk, &c->wptr, &c->wunits);
+  if (c->wunits.size() > c->max_units || (int)c->wptr.size() > kMaxFusedWarps + 1)
+    return fail(c, BBC_EINVAL, "internal: warp units exceed their workspace");
+  if (!c->ws) return BBC_OK;
+  std::vector<int4> wu(c->wunits.size());
+  for (size_t i = 0; i < c->wunits.size(); i++)
+    wu[i] = make_int4(c->wunits[i].batch, c->wunits[i].side, c->wunits[i].k0, c->wunits[i].k1);
+  cudaError_t e = cudaMemcpyAsync(c->d_wptr, c->wptr.data(), sizeof(int) * c->wptr.size(), cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess && !wu.empty())
+    e = cudaMemcpyAsync(c->d_wunits, wu.data(), sizeof(int4) * wu.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "warp unit upload");
+  return BBC_OK;
+}
+
+// Average device time of `reps` launches by `launch` on the context stream
+// (one untimed launch first).  Returns a negative value on a failed launch.
+template <typename F>
+double time_launches(bbc_ctx* c, int reps, F launch) {
+  if (launch() != cudaSuccess) return -1.0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return -1.0;
+  }
+  cudaEventRecord(a, c->stream);
+  bool ok = true;
+  for (int i = 0; i < reps && ok; i++) ok = launch() == cudaSuccess;
+  cudaEventRecord(b, c->stream);
+  float ms = -1.f;
+  if (ok && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ok && ms >= 0.f ? ms / reps : -1.0;
 }
 
 }  // namespace
@@ -184,10 +248,14 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     try {
       const FusedSchedule& f = fused_schedule(c->plan);
       c->batches = f.batches;
-      c->wptr = f.wptr;
-      c->wunits = f.wunits;
       c->row_slot = f.layout.row_slot;
       c->n_slots = f.layout.n_slots;
+      std::vector<int> wp;
+      std::vector<bbc::BatchUnit> wu;
+      for (int k : kChunkCand) {
+        bbc::make_units(c->plan, f.batches, 1, k, &wp, &wu);
+        c->max_units = std::max(c->max_units, wu.size());
+      }
     } catch (const std::bad_alloc&) {
       delete c;
       return fail(nullptr, BBC_ENOMEM, "host allocation failed while scheduling");
@@ -206,6 +274,15 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
     const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
     const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
     if (q <= nq) c->qlist.push_back(q);
+  }
+  {  // a configuration tuned earlier in this process for the same problem
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find({{lat->L, (int)prec}, c->plan.channels});
+    if (it != g_tuned.end()) c->tune = it->second;
+  }
+  if (apply_fused_units(c) != BBC_OK) {
+    delete c;
+    return fail(nullptr, BBC_EINVAL, "internal: warp units exceed their workspace");
   }
   bbc::cubic_orbits(lat->L, c->orb_ptr, c->orb_site);
   {  // the kernel indexes sites through this table: it must be a partition of the lattice
@@ -297,9 +374,6 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     wb[i].nA = c->batches[i].nA;
     for (int j = 0; j < 32; j++) wb[i].task[j] = j < wb[i].n ? c->batches[i].tasks[j] : 0;
   }
-  std::vector<int4> wu(c->wunits.size());
-  for (size_t i = 0; i < c->wunits.size(); i++)
-    wu[i] = make_int4(c->wunits[i].batch, c->wunits[i].side, c->wunits[i].k0, c->wunits[i].k1);
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
       {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
       {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
@@ -311,8 +385,6 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_citem, p.tcontrib_item.data(), sizeof(int) * p.tcontrib_item.size()},
       {c->d_ccoef, p.tcontrib_coef.data(), sizeof(double) * p.tcontrib_coef.size()},
       {c->d_batches, wb.data(), sizeof(bbc::WarpBatch) * wb.size()},
-      {c->d_wptr, c->wptr.data(), sizeof(int) * c->wptr.size()},
-      {c->d_wunits, wu.data(), sizeof(int4) * wu.size()},
       {c->d_qlist, c->qlist.data(), sizeof(int) * c->qlist.size()},
       {c->d_row_slot, c->row_slot.data(), sizeof(int) * c->row_slot.size()},
       {c->d_orb_ptr, c->orb_ptr.data(), sizeof(int) * c->orb_ptr.size()},
@@ -330,7 +402,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->slot_t.assign(slices, -1);
   c->slot_loaded.assign(slices, 0);
   c->slot_built.assign(slices, 0);
-  return BBC_OK;
+  return apply_fused_units(c);
 }
 
 bbc_status bbc_load_propagator(bbc_ctx* c, int flavour, int slot, int t, const void* data, int dtype,
@@ -384,7 +456,7 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   {
     StageScope scope(c, BBC_STAGE_BUILD);
     e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_row_ptr, c->d_entries, c->d_zneed, groups_of(p),
-                                c->d_blk, p.n_out, fp64, c->stream);
+                                c->d_blk, p.n_out, fp64, c->stream, c->tune.build_sites, c->tune.build_threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
   {
@@ -427,7 +499,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
                                    (int)c->qlist.size(), c->d_tasks,
                                    (int)p.tasks.size(), c->d_batches, c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem,
-                                   c->d_ccoef, n_ch, c->d_ct, c->stream);
+                                   c->d_ccoef, n_ch, c->d_ct, c->tune.fused_warps, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused contraction");
   }
   bbc::ScaleParams sp{};
@@ -452,6 +524,95 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
              : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
+  return BBC_OK;
+}
+
+bbc_status bbc_get_tuning(const bbc_ctx* c, bbc_tuning* t) {
+  if (!c || !t) return BBC_EINVAL;
+  *t = c->tune;
+  return BBC_OK;
+}
+
+bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
+  if (!c || !t) return BBC_EINVAL;
+  bbc_tuning want = *t;
+  if (c->prec != BBC_MIXED_FP32) {  // the FP64 path has no fused kernel to configure
+    want.fused_warps = c->tune.fused_warps;
+    want.fused_chunk = c->tune.fused_chunk;
+  }
+  if (!tuning_valid(c, want)) return fail(c, BBC_EINVAL, "unsupported launch configuration");
+  const bbc_tuning old = c->tune;
+  c->tune = want;
+  const bbc_status st = apply_fused_units(c);
+  if (st != BBC_OK) c->tune = old;
+  return st;
+}
+
+bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int cap, int* n_tried) {
+  if (!c) return BBC_EINVAL;
+  if (reps < 1 || reps > 1000) return fail(c, BBC_EINVAL, "reps must be in [1, 1000]");
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  if (c->slot_loaded[0] != 3) return fail(c, BBC_ESTATE, "slot 0 needs both propagators loaded");
+  const bbc::Plan& p = c->plan;
+  const bool fp64 = c->prec == BBC_FP64;
+  const bbc::DevGroups g = groups_of(p);
+  int n = 0;
+  auto record = [&](double v) {
+    if (ms && n < cap) ms[n] = v;
+    n++;
+  };
+  // block build: sites per CTA and threads
+  bbc_tuning t = c->tune;
+  double best_ms = -1.0;
+  for (const auto& bc : kBuildCand) {
+    bbc_tuning cand = c->tune;
+    cand.build_sites = bc[0];
+    cand.build_threads = bc[1];
+    if (!tuning_valid(c, cand)) { record(-1.0); continue; }
+    const double v = time_launches(c, reps, [&] {
+      return bbc::launch_block_build(c->d_prop, c->V, 1, c->d_row_ptr, c->d_entries, c->d_zneed, g, c->d_blk,
+                                     p.n_out, fp64, c->stream, bc[0], bc[1]);
+    });
+    record(v);
+    if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: block build");
+    if (best_ms < 0 || v < best_ms) { best_ms = v; t.build_sites = bc[0]; t.build_threads = bc[1]; }
+  }
+  c->tune.build_sites = t.build_sites;
+  c->tune.build_threads = t.build_threads;
+  // slot 0 rebuilt with the chosen configuration (blocks and forward FFT)
+  c->slot_built[0] = 0;
+  bbc_status st = bbc_build_blocks(c, 1);
+  if (st != BBC_OK) return st;
+  if (!fp64) {  // fused contraction: warps per CTA and open-index chunk per warp unit
+    const char* blk = c->d_blk;
+    best_ms = -1.0;
+    for (int wv : kFusedWarpsCand)
+      for (int kv : kChunkCand) {
+        c->tune.fused_warps = wv;
+        c->tune.fused_chunk = kv;
+        st = apply_fused_units(c);
+        if (st != BBC_OK) return st;
+        const double v = time_launches(c, reps, [&] {
+          return bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
+                                            (int)c->qlist.size(), c->d_tasks, (int)p.tasks.size(), c->d_batches,
+                                            c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem, c->d_ccoef,
+                                            (int)p.channels.size(), c->d_ct, wv, c->stream);
+        });
+        record(v);
+        if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: fused contraction");
+        if (best_ms < 0 || v < best_ms) { best_ms = v; t.fused_warps = wv; t.fused_chunk = kv; }
+      }
+    c->tune.fused_warps = t.fused_warps;
+    c->tune.fused_chunk = t.fused_chunk;
+    st = apply_fused_units(c);
+    if (st != BBC_OK) return st;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[{{c->lat.L, c->prec}, p.channels}] = c->tune;
+  }
+  if (best) *best = c->tune;
+  if (n_tried) *n_tried = n;
   return BBC_OK;
 }
 

@@ -18,6 +18,9 @@ namespace bbc {
 // registers and are added into P[side][task*16 + spin pair] in shared memory.
 // The products are then converted once to FP64 and the signed FP64 sums over
 // Wick diagrams run in the same CTA, writing ct[q][o].
+// Products of one warp unit (open-index steps k0 .. k1-1) of one task: NA x NB
+// complex products for q (A(q) B(-q)) and for -q (A(-q) B(q)) in FP32
+// registers.
 template <int NA, int NB>
 __device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R, const DevTask& t, int k0, int k1,
                                                    cpx<float>* P0, cpx<float>* P1, int rot, bool self) {
@@ -60,9 +63,8 @@ __device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R,
   }
 }
 
-constexpr int kFusedThreads = 512;
-
-__global__ void __launch_bounds__(kFusedThreads, 1)
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1)
 k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ row_slot, int n_slots,
                  const int* __restrict__ qlist,
                  const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
@@ -70,6 +72,7 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
                  const int* __restrict__ citem, const double* __restrict__ ccoef, int n_outputs,
                  cpx<double>* __restrict__ ct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kFusedThreads = WARPS * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = n_tasks * 16;                                        // products per side
   const size_t region = max((size_t)n_slots * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
@@ -133,19 +136,39 @@ size_t contract_fused_smem(int n_slots, int n_tasks) {
   return std::max((size_t)n_slots * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
 }
 
-cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
-                                  int n_q, const DevTask* tasks,
-                                  int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
-                                  const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
-                                  cudaStream_t st) {
-  const size_t sm = contract_fused_smem(n_slots, n_tasks);
+template <int WARPS>
+cudaError_t launch_fused_variant(size_t sm, int n_q, cudaStream_t st, const cpx<float>* blk, int L, int n_out,
+                                 const int* row_slot, int n_slots, const int* qlist, const DevTask* tasks, int n_tasks,
+                                 const WarpBatch* batches, const int* wptr, const int4* wunits, const int* cptr,
+                                 const int* citem, const double* ccoef, int n_outputs, cpx<double>* ct) {
   static int granted[64] = {0};
-  cudaError_t e = ensure_smem(k_contract_fused, sm, granted);
+  cudaError_t e = ensure_smem(k_contract_fused<WARPS>, sm, granted);
   if (e != cudaSuccess) return e;
-  k_contract_fused<<<n_q, kFusedThreads, sm, st>>>((const cpx<float>*)blk, L, n_out, row_slot, n_slots, qlist, tasks,
-                                                   n_tasks, batches,
-                                                   wptr, wunits, cptr, citem, ccoef, n_ch * 16, (cpx<double>*)ct);
+  k_contract_fused<WARPS><<<n_q, WARPS * 32, sm, st>>>(blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks,
+                                                        batches, wptr, wunits, cptr, citem, ccoef, n_outputs, ct);
   return cudaGetLastError();
+}
+
+bool fused_variant_supported(int warps) { return warps == 8 || warps == 12 || warps == 16; }
+
+cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
+                                  int n_q, const DevTask* tasks, int n_tasks, const WarpBatch* batches,
+                                  const int* wptr, const int4* wunits, const int* cptr, const int* citem,
+                                  const double* ccoef, int n_ch, void* ct, int warps, cudaStream_t st) {
+  const size_t sm = contract_fused_smem(n_slots, n_tasks);
+  const cpx<float>* b = (const cpx<float>*)blk;
+  cpx<double>* o = (cpx<double>*)ct;
+  const int n_outputs = n_ch * 16;
+  if (warps == 8)
+    return launch_fused_variant<8>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
+                                   wunits, cptr, citem, ccoef, n_outputs, o);
+  if (warps == 12)
+    return launch_fused_variant<12>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
+                                    wunits, cptr, citem, ccoef, n_outputs, o);
+  if (warps == 16)
+    return launch_fused_variant<16>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
+                                    wunits, cptr, citem, ccoef, n_outputs, o);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace bbc

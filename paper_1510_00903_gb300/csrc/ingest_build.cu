@@ -55,29 +55,36 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex, cons
 // C gamma5 (Dirac representation): (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1.
 __constant__ int c_cg5[4][3] = {{0, 1, 1}, {1, 0, -1}, {2, 3, 1}, {3, 2, -1}};
 
-constexpr int kBuildThreads = 256;
-
-template <typename R>
-__global__ void __launch_bounds__(kBuildThreads)
+// One CTA builds the blocks of SITES consecutive sites with THREADS threads:
+// the propagators, diquarks and tensor entries of every site sit in shared
+// memory, and each thread runs one block row for all SITES sites, so every
+// row's entry list is read once per SITES sites.
+template <typename R, int SITES, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ row_ptr,
               const uint32_t* __restrict__ entries, const uint32_t* __restrict__ zneed, DevGroups g,
               cpx<R>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [2][144]  light, strange
-  cpx<R>* sD = sS + 288;                              // [2][432]  diquarks (l,l), (l,s)
-  cpx<R>* sZ = sD + 864;                              // [g.z_slots] the tensor entries the rows read
-  R* sW = reinterpret_cast<R*>(sZ + g.z_slots);       // weights -16..15 (no int->float conversion per term)
-  const int site = blockIdx.x, slot = blockIdx.y, tid = threadIdx.x;
+  cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [SITES][2][144]  light, strange
+  cpx<R>* sD = sS + SITES * 288;                      // [SITES][2][432]  diquarks (l,l), (l,s)
+  cpx<R>* sZ = sD + SITES * 864;                      // [SITES][g.z_slots] the tensor entries the rows read
+  R* sW = reinterpret_cast<R*>(sZ + SITES * g.z_slots);  // weights -16..15 (no int->float conversion per term)
+  const int site0 = blockIdx.x * SITES, slot = blockIdx.y, tid = threadIdx.x;
+  const int zs = g.z_slots;
   if (tid < 32) sW[tid] = (R)(tid - 16);
   const cpx<R>* P = prop + (size_t)slot * 2 * V * 144;
-  for (int i = tid; i < 288; i += kBuildThreads) sS[i] = P[(size_t)(i / 144) * V * 144 + (size_t)site * 144 + i % 144];
+  for (int i = tid; i < SITES * 288; i += THREADS) {
+    const int s = i / 288, j = i - s * 288;
+    sS[i] = P[(size_t)(j / 144) * V * 144 + (size_t)(site0 + s) * 144 + j % 144];
+  }
   __syncthreads();
   // D_{l f1}[e0][e1][c2] = sum eps(c0,c1,c2) Cg5(a0,a1) S_l[(a0,c0),e0] S_f1[(a1,c1),e1]
-  for (int i = tid; i < 864; i += kBuildThreads) {
+  for (int ii = tid; ii < SITES * 864; ii += THREADS) {
+    const int s = ii / 864, i = ii - s * 864;
     const int dq = i / 432, r = i % 432, e0 = r / 36, e1 = (r / 3) % 12, c2 = r % 3;
     const int ca = (c2 + 1) % 3, cb = (c2 + 2) % 3;  // eps(ca,cb,c2) = +1, eps(cb,ca,c2) = -1
-    const cpx<R>* S0 = sS;
-    const cpx<R>* S1 = sS + 144 * dq;
+    const cpx<R>* S0 = sS + s * 288;
+    const cpx<R>* S1 = S0 + 144 * dq;
     cpx<R> acc(0, 0);
 #pragma unroll
     for (int gi = 0; gi < 4; gi++) {
@@ -90,66 +97,90 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
       acc.re += sg * (t.re - u.re);
       acc.im += sg * (t.im - u.im);
     }
-    sD[i] = acc;
+    sD[ii] = acc;
   }
   __syncthreads();
   for (int gi = 0; gi < g.n; gi++) {
     // the tensor entries this group reads (and the previous group did not leave)
-    const int z1 = g.zneed_first[gi + 1];
-    for (int j = g.zneed_first[gi] + tid; j < z1; j += kBuildThreads) {
-      const uint32_t zn = zneed[j];
+    const int z0 = g.zneed_first[gi], nz = g.zneed_first[gi + 1] - z0;
+    for (int jj = tid; jj < nz * SITES; jj += THREADS) {
+      const int j = z0 + jj / SITES, s = jj % SITES;
+      const uint32_t zn = __ldg(zneed + j);
       const int pos = zn & 0x1fff, sl = (zn >> 13) & 1, i = zn >> 14;
       const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
       // F[a][e0][e1][e2] = sum_c2 D[e0][e1][c2] S_f2[(a,c2),e2]
       const int dq = (fam == 2 || fam == 3) ? 1 : 0;  // LSL, LSS read the (l,s) diquark
       const int f2 = (fam == 1 || fam == 3) ? 1 : 0;  // LLS, LSS: strange third quark
-      const cpx<R>* D = sD + 432 * dq;
-      const cpx<R>* S2 = sS + 144 * f2;
+      const cpx<R>* D = sD + s * 864 + 432 * dq;
+      const cpx<R>* S2 = sS + s * 288 + 144 * f2;
       const int a = i / 1728, r = i % 1728, e01 = r / 12, e2 = r % 12;
       cpx<R> acc(0, 0);
 #pragma unroll
       for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);
-      sZ[pos] = acc;
+      sZ[s * zs + pos] = acc;
     }
     __syncthreads();
     const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
-    cpx<R>* out = blk + ((size_t)slot * V + site) * n_out;
-    for (int r = r0 + tid; r < r1; r += kBuildThreads) {
-      cpx<R> acc(0, 0);
+    cpx<R>* out = blk + ((size_t)slot * V + site0) * n_out;
+    for (int r = r0 + tid; r < r1; r += THREADS) {
+      cpx<R> acc[SITES];
+#pragma unroll
+      for (int s = 0; s < SITES; s++) acc[s] = cpx<R>(0, 0);
       const int k1 = row_ptr[r + 1];
       for (int k = row_ptr[r]; k < k1; k++) {
         const uint32_t e = __ldg(entries + k);
         const R w = sW[((int)(int16_t)(e >> 16)) + 16];
-        const cpx<R> z = sZ[e & 0xffffu];
-        acc.re = fma(w, z.re, acc.re);
-        acc.im = fma(w, z.im, acc.im);
+        const int pos = e & 0xffffu;
+#pragma unroll
+        for (int s = 0; s < SITES; s++) {
+          const cpx<R> z = sZ[s * zs + pos];
+          acc[s].re = fma(w, z.re, acc[s].re);
+          acc[s].im = fma(w, z.im, acc[s].im);
+        }
       }
-      out[r] = acc;
+#pragma unroll
+      for (int s = 0; s < SITES; s++) out[(size_t)s * n_out + r] = acc[s];
     }
     __syncthreads();
   }
 }
 
+size_t block_build_smem(int z_slots, int sites, bool fp64) {
+  const size_t cb = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
+  return (size_t)sites * (288 + 864 + z_slots) * cb + 32 * (fp64 ? sizeof(double) : sizeof(float));
+}
+
+bool build_variant_supported(int sites, int threads) {
+  return (sites == 1 && threads == 256) || (sites == 2 && (threads == 256 || threads == 512)) ||
+         (sites == 4 && threads == 512);
+}
+
+template <typename R, int SITES, int THREADS>
+cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int* row_ptr, const uint32_t* entries,
+                                 const uint32_t* zneed, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
+  const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8);
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem(k_block_build<R, SITES, THREADS>, sm, granted);
+  if (e != cudaSuccess) return e;
+  dim3 grid(V / SITES, n_slots);
+  k_block_build<R, SITES, THREADS><<<grid, THREADS, sm, st>>>((const cpx<R>*)prop, V, row_ptr, entries, zneed, g,
+                                                              (cpx<R>*)blk, n_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
                                const uint32_t* entries, const uint32_t* zneed, const DevGroups& g, void* blk,
-                               int n_out, bool fp64, cudaStream_t st) {
-  dim3 grid(V, n_slots);
-  if (fp64) {
-    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<double>) + 32 * sizeof(double);
-    static int granted[64] = {0};
-    cudaError_t e = ensure_smem(k_block_build<double>, sm, granted);
-    if (e != cudaSuccess) return e;
-    k_block_build<double><<<grid, kBuildThreads, sm, st>>>((const cpx<double>*)prop, V, row_ptr, entries, zneed,
-                                                           g, (cpx<double>*)blk, n_out);
-  } else {
-    size_t sm = (288 + 864 + g.z_slots) * sizeof(cpx<float>) + 32 * sizeof(float);
-    static int granted[64] = {0};
-    cudaError_t e = ensure_smem(k_block_build<float>, sm, granted);
-    if (e != cudaSuccess) return e;
-    k_block_build<float><<<grid, kBuildThreads, sm, st>>>((const cpx<float>*)prop, V, row_ptr, entries, zneed,
-                                                          g, (cpx<float>*)blk, n_out);
-  }
-  return cudaGetLastError();
+                               int n_out, bool fp64, cudaStream_t st, int sites, int threads) {
+  if (!build_variant_supported(sites, threads) || V % sites != 0 ||
+      block_build_smem(g.z_slots, sites, fp64) > kMaxSmemPerBlock)
+    return cudaErrorInvalidValue;
+#define BBC_BUILD(S, T)                                                                                            \
+  if (sites == S && threads == T)                                                                                  \
+    return fp64 ? launch_build_variant<double, S, T>(prop, V, n_slots, row_ptr, entries, zneed, g, blk, n_out, st) \
+                : launch_build_variant<float, S, T>(prop, V, n_slots, row_ptr, entries, zneed, g, blk, n_out, st);
+  BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512)
+#undef BBC_BUILD
+  return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------ normalisation

@@ -33,6 +33,7 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
 };
 
 constexpr int kMaxChannels = 64;
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per CTA
 struct ScaleParams {  // per channel: host factor (1/V, mass normalisation) and quark counts
   int n_ch;
   double f[kMaxChannels];
@@ -52,10 +53,14 @@ cudaError_t launch_absmax(const void* src, int dtype, long long n_complex,
 cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
                            const unsigned long long* amax, int* kexp, void* dst, bool fp64,
                            cudaStream_t st);
-// Baryon blocks of every site: prop [slots][2][V][144], blk [slots][V][n_out].
+// Baryon blocks of every site: prop [slots][2][V][144], blk [slots][V][n_out];
+// `sites` consecutive sites per CTA of `threads` threads: (1, 256), (2, 256),
+// (2, 512) or (4, 512) (V a multiple of sites).
+bool build_variant_supported(int sites, int threads);
+size_t block_build_smem(int z_slots, int sites, bool fp64);
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
                                const uint32_t* entries, const uint32_t* zneed, const DevGroups& g,
-                               void* blk, int n_out, bool fp64, cudaStream_t st);
+                               void* blk, int n_out, bool fp64, cudaStream_t st, int sites, int threads);
 // Forward 3-D FFT of every block field: x pass from the site-major build
 // output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],
 // then the y and z passes in place (exp(-i q.x), unnormalised).
@@ -73,13 +78,13 @@ cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const 
 // row_slot[i] < n_slots (task offsets are slots), warp units wunits {batch,
 // side, k0, k1} (warp w owns wunits[wptr[w] .. wptr[w+1])), FP64 Wick sums
 // into ct[V][n_ch*16].
-constexpr int kFusedWarps = 16;
 size_t contract_fused_smem(int n_slots, int n_tasks);
+// Launch configurations: warps per CTA in {8, 12, 16}.
+bool fused_variant_supported(int warps);
 cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
-                                  int n_q, const DevTask* tasks,
-                                  int n_tasks, const WarpBatch* batches, const int* wptr, const int4* wunits,
-                                  const int* cptr, const int* citem, const double* ccoef, int n_ch, void* ct,
-                                  cudaStream_t st);
+                                  int n_q, const DevTask* tasks, int n_tasks, const WarpBatch* batches,
+                                  const int* wptr, const int4* wunits, const int* cptr, const int* citem,
+                                  const double* ccoef, int n_ch, void* ct, int warps, cudaStream_t st);
 // Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z
 // pass writing out[n_ch][V][16] (complex128) multiplied by scale[ch].
 cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,

@@ -644,40 +644,33 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   return true;
 }
 
-void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch>* batches, std::vector<int>* warp_ptr,
-                       std::vector<BatchUnit>* units) {
+void make_batches(const Plan& plan, std::vector<Batch>* batches) {
   std::map<std::array<int, 3>, std::vector<int>> cls;
   for (int t = 0; t < (int)plan.tasks.size(); t++) {
     const PairTask& k = plan.tasks[t];
     cls[{k.nA, k.nB, k.n1 * k.n2}].push_back(t);
   }
   batches->clear();
-  std::vector<BatchUnit> all;
-  for (auto& kv : cls) {
-    const int K = kv.first[2];
-    // order the class so that each run of 32 tasks cycles through the 16
-    // residues of offA[0] mod 16: the lanes' shared-memory rows then fall on
-    // distinct bank pairs (a complex FP32 value spans two banks)
-    std::vector<std::vector<int>> by_res(16);
-    for (int t : kv.second) by_res[plan.tasks[t].offA[0] & 15].push_back(t);
-    std::vector<int> order;
-    for (bool left = true; left;) {
-      left = false;
-      for (auto& v : by_res)
-        if (!v.empty()) { order.push_back(v.back()); v.pop_back(); left = true; }
-    }
-    for (size_t i = 0; i < order.size(); i += 32) {
+  for (auto& kv : cls)
+    for (size_t i = 0; i < kv.second.size(); i += 32) {
       Batch b;
       b.nA = kv.first[0];
-      for (size_t j = i; j < order.size() && j < i + 32; j++) b.tasks.push_back(order[j]);
-      const int id = (int)batches->size();
+      for (size_t j = i; j < kv.second.size() && j < i + 32; j++) b.tasks.push_back(kv.second[j]);
       batches->push_back(b);
-      const int step = K > chunk ? chunk : K;
-      for (int k = 0; k < K; k += step) all.push_back(BatchUnit{id, 0, k, std::min(K, k + step)});
     }
+}
+
+void make_units(const Plan& plan, const std::vector<Batch>& batches, int warps, int chunk, std::vector<int>* warp_ptr,
+                std::vector<BatchUnit>* units) {
+  std::vector<BatchUnit> all;
+  for (int id = 0; id < (int)batches.size(); id++) {
+    const PairTask& t = plan.tasks[batches[id].tasks[0]];
+    const int K = t.n1 * t.n2;
+    const int step = K > chunk ? chunk : K;
+    for (int k = 0; k < K; k += step) all.push_back(BatchUnit{id, 0, k, std::min(K, k + step)});
   }
   auto cost = [&](const BatchUnit& u) {
-    const Batch& b = (*batches)[u.batch];
+    const Batch& b = batches[u.batch];
     const int nB = 16 / b.nA;
     return (long long)(u.k1 - u.k0) * (128 + 4 * (b.nA + nB)) + 128;
   };

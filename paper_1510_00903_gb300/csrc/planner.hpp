@@ -73,9 +73,7 @@ void channel_names(int id, const char* out[4]);
 bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
 
 // Warp batches for the fused contraction: tasks grouped by (nA, nB, n1*n2),
-// at most 32 per batch (one per lane); units (batch, k0, k1) cover both sides
-// {q, -q} and split open indices longer than `chunk`; units go longest first to the least loaded of
-// `warps` warps.  Output: batches (nA, task ids), warp_ptr[warps + 1], units.
+// at most 32 per batch (one per lane).
 struct Batch {
   int nA;
   std::vector<int> tasks;
@@ -83,8 +81,12 @@ struct Batch {
 struct BatchUnit {
   int batch, side, k0, k1;
 };
-void make_warp_batches(const Plan& plan, int warps, int chunk, std::vector<Batch>* batches, std::vector<int>* warp_ptr,
-                       std::vector<BatchUnit>* units);
+void make_batches(const Plan& plan, std::vector<Batch>* batches);
+// Warp units (batch, k0, k1) covering both sides {q, -q}; open indices longer
+// than `chunk` are split; units go longest first to the least loaded of
+// `warps` warps.  Output: warp_ptr[warps + 1], units.
+void make_units(const Plan& plan, const std::vector<Batch>& batches, int warps, int chunk, std::vector<int>* warp_ptr,
+                std::vector<BatchUnit>* units);
 
 // Shared-memory row layout of the fused contraction.  The block rows one task
 // side reads lie in one operand segment (the union of overlapping operand

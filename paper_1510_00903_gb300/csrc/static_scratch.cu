@@ -176,7 +176,7 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   g.z_slots = p.z_slots;
   e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int*)(w + L.row_ptr), (const uint32_t*)(w + L.entries),
-                              (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st);
+                              (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st, 1, 256);
   if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   e = bbc::launch_fft_forward(w + L.blk, w + L.blkf, c->lat.L, 1, p.n_out, fp64, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");

@@ -85,3 +85,30 @@ def test_project_rejects_bad_arguments():
             assert e.value.status == bbc.BBC_EINVAL, args
     finally:
         bbc.bbc_destroy(c)
+
+
+def test_tuning_defaults_validation_and_autotune_state():
+    """Launch configurations: defaults, rejected shapes, and the autotuner's
+    state checks (no device work here)."""
+    c = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, [0, 1])
+    f = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
+    try:
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18}
+        bbc.bbc_set_tuning(c, 2, 512, 12, 36)  # no workspace yet: host schedule only
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 12, "fused_chunk": 36}
+        for bad in [(3, 256, 16, 18), (1, 512, 16, 18), (4, 256, 16, 18), (1, 256, 10, 18), (1, 256, 16, 20)]:
+            with pytest.raises(bbc.BBCError) as e:
+                bbc.bbc_set_tuning(c, *bad)
+            assert e.value.status == bbc.BBC_EINVAL, bad
+        assert bbc.bbc_get_tuning(c)["fused_chunk"] == 36  # a rejected set leaves the configuration
+        # FP64 blocks of four sites need 365 KB of shared memory: not valid
+        with pytest.raises(bbc.BBCError):
+            bbc.bbc_set_tuning(f, 4, 512)
+        bbc.bbc_set_tuning(f, 2, 256, 8, 9)  # fused fields ignored for FP64
+        assert bbc.bbc_get_tuning(f)["fused_warps"] == 16
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_autotune(c)
+        assert e.value.status == bbc.BBC_ESTATE
+    finally:
+        bbc.bbc_destroy(c)
+        bbc.bbc_destroy(f)

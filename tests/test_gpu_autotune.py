@@ -1,0 +1,77 @@
+"""Autotuner and every launch configuration of the block build and the fused
+contraction: each gives the oracle's correlators (GPU)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+import oracle.oracle as orc
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+from paper_1510_00903_gb300 import bbc  # noqa: E402
+
+BUILD = [(1, 256), (2, 256), (2, 512), (4, 512)]
+MIXED_TOL = 2e-5
+
+
+def _err(got, want):
+    scale = np.abs(want).reshape(want.shape[0], -1).max(axis=1)
+    return (np.abs(got - want).reshape(want.shape[0], -1).max(axis=1) / scale).max()
+
+
+@pytest.mark.parametrize("precision", [bbc.BBC_FP64, bbc.BBC_MIXED_FP32])
+def test_autotune_then_oracle(precision):
+    L, T, t = 8, 4, 1
+    chans = [0, 10, 51]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=77)
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
+    cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
+    n_fused = 0 if precision == bbc.BBC_FP64 else 12
+    assert len(ms) == len(BUILD) + n_fused
+    assert all(v > 0 for v in ms[len(BUILD):])
+    assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
+    # a later context for the same problem starts with the tuned configuration
+    cor2 = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
+    assert cor2.tuning() == cfg
+    cor2.close()
+    out = cor.run(Sl[t:t + 1], Ss[t:t + 1], [t])[0].cpu().numpy()
+    want = orc.normalise(orc.correlator(L, F["u"][t], F["d"][t], F["s"][t], chans), chans, t, 0.3, 0.4)
+    assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL)
+    cor.close()
+
+
+@pytest.mark.parametrize("precision", [bbc.BBC_FP64, bbc.BBC_MIXED_FP32])
+def test_every_configuration_matches(precision):
+    L, T, t = 8, 4, 2
+    chans = [1, 14, 41]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=78)
+    Sl, Ss = torch.from_numpy(F["u"][t:t + 1]).to(dev), torch.from_numpy(F["s"][t:t + 1]).to(dev)
+    want = orc.normalise(orc.correlator(L, F["u"][t], F["d"][t], F["s"][t], chans), chans, t, 0.3, 0.4)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
+    ref = None
+    fused = [(16, 18)] if precision == bbc.BBC_FP64 else [(w, k) for w in (8, 12, 16) for k in (9, 18, 36, 72)]
+    tried = 0
+    for sites, threads in BUILD:
+        for warps, chunk in fused:
+            try:
+                cor.set_tuning({"build_sites": sites, "build_threads": threads, "fused_warps": warps,
+                                "fused_chunk": chunk})
+            except bbc.BBCError:
+                assert precision == bbc.BBC_FP64 and sites == 4  # 365 KB of shared memory
+                continue
+            out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
+            assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL), (sites, threads, warps, chunk)
+            if precision == bbc.BBC_FP64:
+                # the build sums every row in the same order whatever the shape
+                if ref is None:
+                    ref = out
+                assert np.array_equal(out, ref)
+            tried += 1
+    assert tried == (3 if precision == bbc.BBC_FP64 else 48)
+    cor.close()
