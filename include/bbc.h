@@ -173,7 +173,8 @@ bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, 
  *    memory (configurations that need more than 227 KB are not valid);
  *  fused_warps, fused_chunk (BBC_MIXED_FP32 only): warps per CTA (8, 12, 16)
  *    of the fused q-space contraction and the open-index steps per warp unit
- *    (9, 18, 36, 72).
+ *    (18, 36, 72, 144), or 0: each warp takes one contiguous run of the
+ *    batches' steps of equal modelled cost.
  * A new context starts with (1, 256, 16, 18), or with the configuration
  * bbc_autotune chose earlier in the process for the same L, precision and
  * channel list. */

@@ -148,7 +148,7 @@ const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
 // Candidate launch configurations of the autotuner.
 const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}};  // (sites per CTA, threads)
 const int kFusedWarpsCand[] = {8, 12, 16};
-const int kChunkCand[] = {9, 18, 36, 72};
+const int kChunkCand[] = {0, 18, 36, 72, 144};  // 0: contiguous equal-cost pieces
 
 // Tuned configurations per (L, precision, channel list), for later contexts.
 std::mutex g_tune_mutex;

@@ -662,6 +662,39 @@ void make_batches(const Plan& plan, std::vector<Batch>* batches) {
 
 void make_units(const Plan& plan, const std::vector<Batch>& batches, int warps, int chunk, std::vector<int>* warp_ptr,
                 std::vector<BatchUnit>* units) {
+  if (chunk <= 0) {
+    // contiguous split: the batches' open-index steps laid end to end and cut
+    // into `warps` pieces of equal modelled cost, so every warp flushes its
+    // products about once per batch it touches
+    std::vector<long long> per_k(batches.size());
+    long long total = 0;
+    for (size_t b = 0; b < batches.size(); b++) {
+      const PairTask& t = plan.tasks[batches[b].tasks[0]];
+      per_k[b] = 128 + 4 * (t.nA + t.nB);
+      total += per_k[b] * t.n1 * t.n2;
+    }
+    warp_ptr->assign(1, 0);
+    units->clear();
+    long long done = 0;
+    size_t b = 0;
+    int k = 0;
+    for (int w = 0; w < warps; w++) {
+      const long long target = total * (w + 1) / warps;
+      while (b < batches.size() && done < target) {
+        const PairTask& t = plan.tasks[batches[b].tasks[0]];
+        const int K = t.n1 * t.n2;
+        long long take = (target - done + per_k[b] - 1) / per_k[b];  // steps to reach the target
+        if (w == warps - 1) take = K - k;
+        const int k1 = (int)std::min<long long>(K, k + std::max<long long>(1, take));
+        units->push_back(BatchUnit{(int)b, 0, k, k1});
+        done += per_k[b] * (k1 - k);
+        k = k1;
+        if (k == K) { b++; k = 0; }
+      }
+      warp_ptr->push_back((int)units->size());
+    }
+    return;
+  }
   std::vector<BatchUnit> all;
   for (int id = 0; id < (int)batches.size(); id++) {
     const PairTask& t = plan.tasks[batches[id].tasks[0]];

@@ -82,9 +82,11 @@ struct BatchUnit {
   int batch, side, k0, k1;
 };
 void make_batches(const Plan& plan, std::vector<Batch>* batches);
-// Warp units (batch, k0, k1) covering both sides {q, -q}; open indices longer
-// than `chunk` are split; units go longest first to the least loaded of
-// `warps` warps.  Output: warp_ptr[warps + 1], units.
+// Warp units (batch, k0, k1) covering both sides {q, -q}.  chunk > 0: open
+// indices longer than `chunk` are split and units go longest first to the
+// least loaded of `warps` warps; chunk = 0: the batches' steps laid end to
+// end are cut into `warps` contiguous pieces of equal modelled cost.
+// Output: warp_ptr[warps + 1], units.
 void make_units(const Plan& plan, const std::vector<Batch>& batches, int warps, int chunk, std::vector<int>* warp_ptr,
                 std::vector<BatchUnit>* units);
 

@@ -104,7 +104,7 @@ def test_tuning_defaults_validation_and_autotune_state():
         # FP64 blocks of four sites need 365 KB of shared memory: not valid
         with pytest.raises(bbc.BBCError):
             bbc.bbc_set_tuning(f, 4, 512)
-        bbc.bbc_set_tuning(f, 2, 256, 8, 9)  # fused fields ignored for FP64
+        bbc.bbc_set_tuning(f, 2, 256, 8, 7)  # fused fields ignored for FP64
         assert bbc.bbc_get_tuning(f)["fused_warps"] == 16
         with pytest.raises(bbc.BBCError) as e:
             bbc.bbc_autotune(c)
