@@ -381,19 +381,22 @@ def error_report(torch, dev, bbc, synth):
     F = synth.flavour_set(L, T, 0, M_UD, M_S, seed=3, times=[t])
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     res = {}
-    for name, prec in (("fp64", bbc.BBC_FP64), ("mixed", bbc.BBC_MIXED_FP32)):
+    for name, prec in (("fp64", bbc.BBC_FP64), ("mixed", bbc.BBC_MIXED_FP32), ("bf16", bbc.BBC_MIXED_BF16)):
         cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
         res[name] = cor.run(Sl, Ss, [t], normalised=True)[0].cpu().numpy()
         cor.close()
     a, b = res["mixed"], res["fp64"]
     scale = np.abs(b).reshape(N_CH, -1).max(axis=1)
     err = np.abs(a - b).reshape(N_CH, -1).max(axis=1) / scale
+    err16 = np.abs(res["bf16"] - b).reshape(N_CH, -1).max(axis=1) / scale
     chans, r_list = [0, 10, 41, 51], [0, 12345, 30001]
     want = orc.normalise(orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], chans, r_list), chans, t, M_UD, M_S)
     o_err = float((np.abs(b[chans][:, r_list] - want).reshape(len(chans), -1).max(axis=1) / scale[chans]).max())
     print(json.dumps({"report": "mixed precision error per channel", "L": L, "T": T, "t": t,
                       "metric": "max_{r,s}|C_mixed - C_fp64| / max_{r,s}|C_fp64|",
                       "per_channel": [float(x) for x in err], "max": float(err.max()), "median": float(np.median(err)),
+                      "bf16_per_channel": [float(x) for x in err16], "bf16_max": float(err16.max()),
+                      "bf16_median": float(np.median(err16)),
                       "fp64_vs_oracle_sampled": o_err}), flush=True)
 
 

@@ -61,9 +61,12 @@ typedef enum {
 
 typedef enum {
   BBC_FP64 = 0,      /* blocks, FFTs, contraction and sums in FP64 */
-  BBC_MIXED_FP32 = 1 /* blocks, FFTs and block-pair products in FP32 after an exact
-                        per-slice power-of-two rescaling of each propagator; the signed
-                        sum over Wick diagrams and the normalisation in FP64 */
+  BBC_MIXED_FP32 = 1, /* blocks, FFTs and block-pair products in FP32 after an exact
+                         per-slice power-of-two rescaling of each propagator; the signed
+                         sum over Wick diagrams and the normalisation in FP64 */
+  BBC_MIXED_BF16 = 2  /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
+                         to bfloat16 (round to nearest even) before the block-pair
+                         products, which multiply and accumulate in FP32 */
 } bbc_precision;
 
 typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
@@ -171,7 +174,7 @@ bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, 
  *    one of (1, 256), (2, 256), (2, 512), (4, 512); a CTA keeps the
  *    propagators, diquarks and sink-tensor entries of its sites in shared
  *    memory (configurations that need more than 227 KB are not valid);
- *  fused_warps, fused_chunk (BBC_MIXED_FP32 only): warps per CTA (8, 12, 16)
+ *  fused_warps, fused_chunk (mixed precisions only): warps per CTA (8, 12, 16)
  *    of the fused q-space contraction and the open-index steps per warp unit
  *    (18, 36, 72, 144), or 0: each warp takes one contiguous run of the
  *    batches' steps of equal modelled cost.
@@ -193,7 +196,7 @@ bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
 /* Autotuner: times every valid candidate configuration with CUDA events on
  * the context stream, `reps` launches each after one untimed launch, on the
  * propagators loaded in slot 0 -- the block-build candidates in the order
- * above, then (BBC_MIXED_FP32) every (fused_warps, fused_chunk) pair in
+ * above, then (mixed precisions) every (fused_warps, fused_chunk) pair in
  * row-major order -- keeps the fastest of each kernel, rebuilds slot 0 with
  * it, and records it for later contexts with the same L, precision and
  * channel list.  ms[i] (i < cap) receives the average milliseconds per launch
@@ -240,6 +243,7 @@ bbc_status bbc_project(bbc_ctx* ctx, const void* C_dev, int n_fields, void* R_de
  * [n_channels][L^3][16] complex128, written fully.  Everything runs
  * asynchronously on the context stream.
  *
+ * Precisions BBC_FP64 and BBC_MIXED_FP32 (EINVAL for BBC_MIXED_BF16).
  * Size limit: the plan tables and one slice of blocks, pair products and
  * q-space correlators must fit in the array -- L <= 4 with all 52 channels;
  * larger lattices or channel lists return BBC_EINVAL with a message.

@@ -26,13 +26,14 @@ std::string g_create_error;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
+bool fused_path(int prec) { return prec != BBC_FP64; }  // FP32 or bfloat16 products
 
 constexpr int kMaxFusedWarps = 16;
 
 struct Layout {
   size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
-  size_t stage, prop, amax, kexp, blk, blkf, P, ct, scale, total;
+  size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -62,6 +63,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.amax = o; o = align256(o + (size_t)slots * 2 * sizeof(unsigned long long));
   L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
   L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
+  L.blk16 = o; o = align256(o + (c->prec == BBC_MIXED_BF16 ? (size_t)slots * V * p.n_out * 4 : 0));
   const bool fp64 = c->prec == BBC_FP64;  // the FP32 path keeps q-major blocks and no product buffer
   L.blkf = o; o = align256(o + (fp64 ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
   L.P = o; o = align256(o + (fp64 ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
@@ -158,7 +160,7 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
   if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, c->prec == BBC_FP64) > bbc::kMaxSmemPerBlock)
     return false;
-  if (c->prec == BBC_MIXED_FP32) {
+  if (fused_path(c->prec)) {
     if (!bbc::fused_variant_supported(t.fused_warps)) return false;
     bool chunk_ok = false;
     for (int k : kChunkCand) chunk_ok |= k == t.fused_chunk;
@@ -170,7 +172,7 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
 // Warp units of the context's fused configuration, uploaded when a
 // workspace is attached (synchronous: the host vectors are temporaries).
 bbc_status apply_fused_units(bbc_ctx* c) {
-  if (c->prec != BBC_MIXED_FP32) return BBC_OK;
+  if (!fused_path(c->prec)) return BBC_OK;
   const FusedSchedule& f = fused_schedule(c->plan);
   bbc::make_units(c->plan, f.batches, c->tune.fused_warps, c->tune.fused_chunk, &c->wptr, &c->wunits);
   if (c->wunits.size() > c->max_units || (int)c->wptr.size() > kMaxFusedWarps + 1)
@@ -219,7 +221,8 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   *ctx = nullptr;
   if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 24, 32, 48)");
   if (lat->T < 1 || lat->t0 < 0 || lat->t0 >= lat->T) return fail(nullptr, BBC_EINVAL, "bad T or t0");
-  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32) return fail(nullptr, BBC_EINVAL, "bad precision");
+  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16)
+    return fail(nullptr, BBC_EINVAL, "bad precision");
   if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");
   bbc_ctx* c = new (std::nothrow) bbc_ctx();
   if (!c) return fail(nullptr, BBC_ENOMEM, "host allocation failed");
@@ -244,7 +247,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   // GPU several times over at L = 16 (V/32 q tiles x groups warps)
   bbc::make_task_groups(c->plan, 48, &c->group_ptr, &c->group_task);
   // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
-  if (prec == BBC_MIXED_FP32) {
+  if (fused_path(prec)) {
     try {
       const FusedSchedule& f = fused_schedule(c->plan);
       c->batches = f.batches;
@@ -252,10 +255,11 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
       c->n_slots = f.layout.n_slots;
       std::vector<int> wp;
       std::vector<bbc::BatchUnit> wu;
-      for (int k : kChunkCand) {
-        bbc::make_units(c->plan, f.batches, 1, k, &wp, &wu);
-        c->max_units = std::max(c->max_units, wu.size());
-      }
+      for (int w : kFusedWarpsCand)
+        for (int k : kChunkCand) {
+          bbc::make_units(c->plan, f.batches, w, k, &wp, &wu);
+          c->max_units = std::max(c->max_units, wu.size());
+        }
     } catch (const std::bad_alloc&) {
       delete c;
       return fail(nullptr, BBC_ENOMEM, "host allocation failed while scheduling");
@@ -346,6 +350,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_amax = (unsigned long long*)(w + L.amax);
   c->d_kexp = (int*)(w + L.kexp);
   c->d_blk = w + L.blk;
+  c->d_blk16 = w + L.blk16;
   c->d_blkf = w + L.blkf;
   c->d_P = w + L.P;
   c->d_ct = w + L.ct;
@@ -357,7 +362,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     bbc::DevTask& d = tasks[i];
     // the fused FP32 kernel addresses its shared-memory copy of the rows: a
     // task side's rows lie in one segment, so slot(off + k) = slot(off) + k
-    const bool slots = c->prec == BBC_MIXED_FP32;
+    const bool slots = fused_path(c->prec);
     for (int r = 0; r < 8; r++) {
       d.offA[r] = r < t.nA ? (slots ? c->row_slot[t.offA[r]] : t.offA[r]) : 0;
       d.offB[r] = r < t.nB ? (slots ? c->row_slot[t.offB[r]] : t.offB[r]) : 0;
@@ -465,6 +470,10 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
     e = fp64 ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
              : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
+    if (c->prec == BBC_MIXED_BF16) {
+      e = bbc::launch_to_bf16(c->d_blk, c->d_blk16, (size_t)n_slots * c->V * p.n_out, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "bfloat16 rounding");
+    }
   }
   for (int s = 0; s < n_slots; s++) c->slot_built[s] = 1;
   return BBC_OK;
@@ -494,12 +503,14 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
       if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
     }
   } else {
-    const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+    const bool bf16 = c->prec == BBC_MIXED_BF16;
+    const char* blk = bf16 ? c->d_blk16 + (size_t)slot * c->V * p.n_out * 4
+                           : c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
     StageScope scope(c, BBC_STAGE_CONTRACT);
     e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
                                    (int)c->qlist.size(), c->d_tasks,
                                    (int)p.tasks.size(), c->d_batches, c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem,
-                                   c->d_ccoef, n_ch, c->d_ct, c->tune.fused_warps, c->stream);
+                                   c->d_ccoef, n_ch, c->d_ct, c->tune.fused_warps, bf16, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused contraction");
   }
   bbc::ScaleParams sp{};
@@ -536,7 +547,7 @@ bbc_status bbc_get_tuning(const bbc_ctx* c, bbc_tuning* t) {
 bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
   if (!c || !t) return BBC_EINVAL;
   bbc_tuning want = *t;
-  if (c->prec != BBC_MIXED_FP32) {  // the FP64 path has no fused kernel to configure
+  if (!fused_path(c->prec)) {  // the FP64 path has no fused kernel to configure
     want.fused_warps = c->tune.fused_warps;
     want.fused_chunk = c->tune.fused_chunk;
   }
@@ -584,7 +595,8 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   bbc_status st = bbc_build_blocks(c, 1);
   if (st != BBC_OK) return st;
   if (!fp64) {  // fused contraction: warps per CTA and open-index chunk per warp unit
-    const char* blk = c->d_blk;
+    const bool bf16 = c->prec == BBC_MIXED_BF16;
+    const char* blk = bf16 ? c->d_blk16 : c->d_blk;
     best_ms = -1.0;
     for (int wv : kFusedWarpsCand)
       for (int kv : kChunkCand) {
@@ -596,7 +608,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
           return bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
                                             (int)c->qlist.size(), c->d_tasks, (int)p.tasks.size(), c->d_batches,
                                             c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem, c->d_ccoef,
-                                            (int)p.channels.size(), c->d_ct, wv, c->stream);
+                                            (int)p.channels.size(), c->d_ct, wv, bf16, c->stream);
         });
         record(v);
         if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: fused contraction");

@@ -57,6 +57,7 @@ struct bbc_ctx {
   unsigned long long* d_amax = nullptr;  // [slots][2]
   int* d_kexp = nullptr;                 // [slots][2]
   char* d_blk = nullptr;                 // [slots][V][n_out] site-major build output
+  char* d_blk16 = nullptr;               // [slots][V][n_out] bfloat16 (re, im) pairs, Fourier space
   char* d_blkf = nullptr;                // [slots][n_out][V] field-major, Fourier space
   char* d_P = nullptr;                   // [n_tasks*16][V] pair products of one slice
   char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators

@@ -1,7 +1,10 @@
 // fused_contract.cu -- FP32 q-space contraction fused with the FP64 Wick sums, one CTA per pair {q, -q} (mixed precision path)
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <utility>
+
+#include <cuda_bf16.h>
 
 #include "device_common.cuh"
 
@@ -21,8 +24,17 @@ namespace bbc {
 // Products of one warp unit (open-index steps k0 .. k1-1) of one task: NA x NB
 // complex products for q (A(q) B(-q)) and for -q (A(-q) B(q)) in FP32
 // registers.
-template <int NA, int NB>
-__device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R, const DevTask& t, int k0, int k1,
+// A staged row: (F_q, F_-q) as complex64 pairs, or as bfloat16 (re, im)
+// pairs widened to FP32 (a bfloat16 is the high half of a float).
+__device__ __forceinline__ float4 load_row(const float4* R, int i) { return R[i]; }
+__device__ __forceinline__ float4 load_row(const uint2* R, int i) {
+  const uint2 u = R[i];
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                     __uint_as_float(u.y & 0xffff0000u));
+}
+
+template <int NA, int NB, typename Row>
+__device__ __forceinline__ void unit_products_pair(const Row* __restrict__ R, const DevTask& t, int k0, int k1,
                                                    cpx<float>* P0, cpx<float>* P1, int rot, bool self) {
   const int n2 = t.n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
@@ -35,9 +47,9 @@ __device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R,
   for (int k = k0; k < k1; k++) {
     float4 a[NA], b[NB];
 #pragma unroll
-    for (int r = 0; r < NA; r++) a[r] = R[t.offA[r] + oA];
+    for (int r = 0; r < NA; r++) a[r] = load_row(R, t.offA[r] + oA);
 #pragma unroll
-    for (int r = 0; r < NB; r++) b[r] = R[t.offB[r] + oB];
+    for (int r = 0; r < NB; r++) b[r] = load_row(R, t.offB[r] + oB);
 #pragma unroll
     for (int ra = 0; ra < NA; ra++)
 #pragma unroll
@@ -63,9 +75,9 @@ __device__ __forceinline__ void unit_products_pair(const float4* __restrict__ R,
   }
 }
 
-template <int WARPS>
+template <int WARPS, bool BF16>
 __global__ void __launch_bounds__(WARPS * 32, 1)
-k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int* __restrict__ row_slot, int n_slots,
+k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __restrict__ row_slot, int n_slots,
                  const int* __restrict__ qlist,
                  const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
                  const int* __restrict__ wptr, const int4* __restrict__ wunits, const int* __restrict__ cptr,
@@ -75,8 +87,9 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
   constexpr int kFusedThreads = WARPS * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = n_tasks * 16;                                        // products per side
-  const size_t region = max((size_t)n_slots * 16, (size_t)2 * np * 16);  // rows, later the FP64 products
-  float4* R = reinterpret_cast<float4*>(smem_raw);                       // [n_slots] (F_q, F_-q)
+  using Row = typename std::conditional<BF16, uint2, float4>::type;
+  const size_t region = max((size_t)n_slots * sizeof(Row), (size_t)2 * np * 16);  // rows, later the FP64 products
+  Row* R = reinterpret_cast<Row*>(smem_raw);                                       // [n_slots] (F_q, F_-q)
   cpx<double>* Pd = reinterpret_cast<cpx<double>*>(smem_raw);         // [2][np], after the products
   cpx<float>* P = reinterpret_cast<cpx<float>*>(smem_raw + region);   // [2][np]
   const int q = qlist[blockIdx.x];
@@ -84,11 +97,20 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
   const bool self = nq == q;
   {
-    const float2* s0 = reinterpret_cast<const float2*>(blk + (size_t)q * n_out);
-    const float2* s1 = reinterpret_cast<const float2*>(blk + (size_t)nq * n_out);
-    for (int i = tid; i < n_out; i += kFusedThreads) {
-      const float2 x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
-      R[__ldg(row_slot + i)] = make_float4(x.x, x.y, y.x, y.y);
+    if constexpr (BF16) {
+      const unsigned* s0 = reinterpret_cast<const unsigned*>(blk) + (size_t)q * n_out;
+      const unsigned* s1 = reinterpret_cast<const unsigned*>(blk) + (size_t)nq * n_out;
+      for (int i = tid; i < n_out; i += kFusedThreads) {
+        const unsigned x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
+        R[__ldg(row_slot + i)] = make_uint2(x, y);
+      }
+    } else {
+      const float2* s0 = reinterpret_cast<const float2*>(blk) + (size_t)q * n_out;
+      const float2* s1 = reinterpret_cast<const float2*>(blk) + (size_t)nq * n_out;
+      for (int i = tid; i < n_out; i += kFusedThreads) {
+        const float2 x = __ldg(s0 + i), y = self ? x : __ldg(s1 + i);
+        R[__ldg(row_slot + i)] = make_float4(x.x, x.y, y.x, y.y);
+      }
     }
     float4* pz = reinterpret_cast<float4*>(P);
     for (int i = tid; i < np; i += kFusedThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -131,21 +153,34 @@ k_contract_fused(const cpx<float>* __restrict__ blk, int L, int n_out, const int
   }
 }
 
-size_t contract_fused_smem(int n_slots, int n_tasks) {
+size_t contract_fused_smem(int n_slots, int n_tasks, bool bf16) {
   const size_t np = (size_t)n_tasks * 16;
-  return std::max((size_t)n_slots * 16, 2 * np * 16) + 2 * np * sizeof(cpx<float>);
+  return std::max((size_t)n_slots * (bf16 ? 8 : 16), 2 * np * 16) + 2 * np * sizeof(cpx<float>);
 }
 
-template <int WARPS>
-cudaError_t launch_fused_variant(size_t sm, int n_q, cudaStream_t st, const cpx<float>* blk, int L, int n_out,
+__global__ void k_to_bf16(const float2* __restrict__ src, __nv_bfloat162* __restrict__ dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __float22bfloat162_rn(src[i]);
+}
+
+cudaError_t launch_to_bf16(const void* src, void* dst, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_to_bf16<<<blocks, 256, 0, st>>>((const float2*)src, (__nv_bfloat162*)dst, n);
+  return cudaGetLastError();
+}
+
+template <int WARPS, bool BF16>
+cudaError_t launch_fused_variant(size_t sm, int n_q, cudaStream_t st, const void* blk, int L, int n_out,
                                  const int* row_slot, int n_slots, const int* qlist, const DevTask* tasks, int n_tasks,
                                  const WarpBatch* batches, const int* wptr, const int4* wunits, const int* cptr,
                                  const int* citem, const double* ccoef, int n_outputs, cpx<double>* ct) {
   static int granted[64] = {0};
-  cudaError_t e = ensure_smem(k_contract_fused<WARPS>, sm, granted);
+  cudaError_t e = ensure_smem(k_contract_fused<WARPS, BF16>, sm, granted);
   if (e != cudaSuccess) return e;
-  k_contract_fused<WARPS><<<n_q, WARPS * 32, sm, st>>>(blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks,
-                                                        batches, wptr, wunits, cptr, citem, ccoef, n_outputs, ct);
+  k_contract_fused<WARPS, BF16><<<n_q, WARPS * 32, sm, st>>>(blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks,
+                                                              batches, wptr, wunits, cptr, citem, ccoef, n_outputs,
+                                                              ct);
   return cudaGetLastError();
 }
 
@@ -154,20 +189,17 @@ bool fused_variant_supported(int warps) { return warps == 8 || warps == 12 || wa
 cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
                                   int n_q, const DevTask* tasks, int n_tasks, const WarpBatch* batches,
                                   const int* wptr, const int4* wunits, const int* cptr, const int* citem,
-                                  const double* ccoef, int n_ch, void* ct, int warps, cudaStream_t st) {
-  const size_t sm = contract_fused_smem(n_slots, n_tasks);
-  const cpx<float>* b = (const cpx<float>*)blk;
+                                  const double* ccoef, int n_ch, void* ct, int warps, bool bf16, cudaStream_t st) {
+  const size_t sm = contract_fused_smem(n_slots, n_tasks, bf16);
   cpx<double>* o = (cpx<double>*)ct;
   const int n_outputs = n_ch * 16;
-  if (warps == 8)
-    return launch_fused_variant<8>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
-                                   wunits, cptr, citem, ccoef, n_outputs, o);
-  if (warps == 12)
-    return launch_fused_variant<12>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
-                                    wunits, cptr, citem, ccoef, n_outputs, o);
-  if (warps == 16)
-    return launch_fused_variant<16>(sm, n_q, st, b, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, wptr,
-                                    wunits, cptr, citem, ccoef, n_outputs, o);
+#define BBC_FUSED(W, B)                                                                                          \
+  if (warps == W && bf16 == B)                                                                                   \
+    return launch_fused_variant<W, B>(sm, n_q, st, blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, \
+                                      wptr, wunits, cptr, citem, ccoef, n_outputs, o);
+  BBC_FUSED(8, false) BBC_FUSED(12, false) BBC_FUSED(16, false)
+  BBC_FUSED(8, true) BBC_FUSED(12, true) BBC_FUSED(16, true)
+#undef BBC_FUSED
   return cudaErrorInvalidValue;
 }
 

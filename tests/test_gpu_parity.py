@@ -22,6 +22,11 @@ from paper_1510_00903_gb300 import bbc  # noqa: E402
 
 FP64_TOL = 1e-12
 MIXED_TOL = 2e-5
+# bfloat16 trial (Fourier-space blocks rounded to 8-bit mantissas before the
+# FP32 products): unit roundoff 2^-9 = 2e-3 per factor, so about 4e-3 per
+# product before the sums; the bound leaves a factor ~5 for the growth of the
+# signed sums over diagrams
+BF16_TOL = 2e-2
 
 
 def gpu_run(L, T, t0, channels, S_l, S_s, times, precision=bbc.BBC_FP64, slices=1, normalised=False,
@@ -79,6 +84,20 @@ def test_all_channels_L4_fp64_and_mixed():
     gm = gpu_run(L, T, 0, ch, F["u"], F["s"], [3], precision=bbc.BBC_MIXED_FP32)[0]
     em, _ = rel_err(gm[:52], want[:52])
     assert em.max() < MIXED_TOL, em
+
+
+@pytest.mark.parametrize("L", [4, 8])
+def test_all_channels_bf16_trial(L):
+    """The bfloat16 trial precision on all 52 channels of one slice."""
+    T = 4
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=11)
+    ch = list(range(52))
+    want = oracle_slice(L, F, 2, ch)
+    got = gpu_run(L, T, 0, ch, F["u"], F["s"], [2], precision=bbc.BBC_MIXED_BF16)[0]
+    e, _ = rel_err(got, want)
+    print(f"bf16 L={L}: max {e.max():.3e} median {np.median(e):.3e}")
+    assert e.max() < BF16_TOL, e
+    assert np.median(e) > 1e-5  # the rounding is really applied
 
 
 def test_L2_and_L8_slices_fp64():
