@@ -233,6 +233,11 @@ def run_ours(args, torch, rank, world, local):
         o = cor.run(torch.from_numpy(F1["u"]).to(dev), torch.from_numpy(F1["s"]).to(dev), [t])
         torch.cuda.synchronize(dev)
         print("single slice done", float(o.abs().max()))
+        if prec == bbc.BBC_FP64:
+            # the Sec. 2 projections of eight copies of the slice (436 MB, above the L2)
+            R, Ra1 = cor.project(o.repeat(8, 1, 1, 1))
+            torch.cuda.synchronize(dev)
+            print("projection done", float(Ra1.abs().max()))
         cor.close()
         return
     from paper_1510_00903_gb300 import shard
