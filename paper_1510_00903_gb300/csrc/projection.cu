@@ -63,16 +63,18 @@ __device__ __forceinline__ cpx<double> shfl(cpx<double> v, int src) {
 }
 
 // Lane s of a 16-lane group holds component a + 2b + 4p (p = a' + 2b') of one
-// site; returns state jm = s >> 2 at sink spins ab = s & 3.
+// site; returns state jm = s >> 2 at sink spins ab = s & 3 as c_x v_x + c_y v_y
+// with the lane's two source-spin components and coefficients:
+//   jm = 0: (|ud> - |du>)/sqrt2 = h v_{p=2} - h v_{p=1}   jm = 1: |uu> = v_{p=0}
+//   jm = 2: (|ud> + |du>)/sqrt2 = h v_{p=2} + h v_{p=1}   jm = 3: |dd> = v_{p=3}
+// (one instruction stream for every lane: no divergent FP64 paths).
 __device__ __forceinline__ cpx<double> spin_states(cpx<double> v, int grp, int s) {
   const int ab = s & 3, jm = s >> 2;
   const double h = 0.70710678118654752440;  // 1/sqrt(2)
-  const cpx<double> v0 = shfl(v, grp + ab), v1 = shfl(v, grp + ab + 4), v2 = shfl(v, grp + ab + 8),
-                    v3 = shfl(v, grp + ab + 12);
-  if (jm == 0) return cpx<double>(h * (v2.re - v1.re), h * (v2.im - v1.im));  // (|ud> - |du>)/sqrt2
-  if (jm == 1) return v0;                                                       // |uu>
-  if (jm == 2) return cpx<double>(h * (v2.re + v1.re), h * (v2.im + v1.im));  // (|ud> + |du>)/sqrt2
-  return v3;                                                                    // |dd>
+  const int px = jm == 1 ? 0 : (jm == 3 ? 3 : 2), py = jm == 1 ? 0 : (jm == 3 ? 3 : 1);
+  const double cx = (jm & 1) ? 1.0 : h, cy = (jm & 1) ? 0.0 : (jm == 0 ? -h : h);
+  const cpx<double> vx = shfl(v, grp + ab + 4 * px), vy = shfl(v, grp + ab + 4 * py);
+  return cpx<double>(fma(cy, vy.re, cx * vx.re), fma(cy, vy.im, cx * vx.im));
 }
 
 // C, R, Ra1: [n_fields][V][16] complex128; one 16-lane group per (orbit, field).
