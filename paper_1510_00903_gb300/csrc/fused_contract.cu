@@ -24,6 +24,20 @@ namespace bbc {
 // Products of one warp unit (open-index steps k0 .. k1-1) of one task: NA x NB
 // complex products for q (A(q) B(-q)) and for -q (A(-q) B(q)) in FP32
 // registers.
+// FP32 -> FP64 by the IEEE-754 bit layouts (sign, exponent rebiased by
+// 1023 - 127 = 896, the 23 mantissa bits at the top of the 52): integer
+// instructions only, leaving GB300's narrow FP64 pipe to the Wick sums.
+// Exact for normal numbers, infinities and NaNs; FP32 subnormals (|x| below
+// 2^-126, far under any product's scale here) become signed zeros.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned sign = u & 0x80000000u;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  const unsigned e64 = e == 0xffu ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)(sign | (e64 << 20) | ((u >> 3) & 0xfffffu)), (int)(u << 29));
+}
+
 // A staged row: (F_q, F_-q) as complex64 pairs, or as bfloat16 (re, im)
 // pairs widened to FP32 (a bfloat16 is the high half of a float).
 __device__ __forceinline__ float4 load_row(const float4* R, int i) { return R[i]; }
@@ -135,7 +149,7 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
   for (int j = tid; j < sides * np; j += kFusedThreads) {
     const int side = j / np, it = j - side * np, ti = it >> 4;
     const cpx<float> v = P[side * np + (ti << 4) + ((it + ti) & 15)];
-    Pd[j] = cpx<double>((double)v.re, (double)v.im);
+    Pd[j] = cpx<double>(widen(v.re), widen(v.im));
   }
   __syncthreads();
   for (int j = tid; j < sides * n_outputs; j += kFusedThreads) {
