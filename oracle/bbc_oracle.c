@@ -203,7 +203,7 @@ void oracle_cg5(double* out16) {
 }
 
 /* Dense baryon tensor T_b(ext; q0, q1, q2) over 12^3 (index 144*q0 + 12*q1 + q2,
- * q = 3*spin + colour), ext in {0,1}.  Shared by sink and source. */
+ * q = 3*spin + colour), Dirac index ext in {0..3}.  Shared by sink and source. */
 static void baryon_tensor(int b, int ext, double* T /* 1728 */) {
   static const int eps_p[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
   static const double eps_s[6] = {1, 1, 1, -1, -1, -1};
@@ -222,11 +222,12 @@ static void baryon_tensor(int b, int ext, double* T /* 1728 */) {
         }
 }
 
-/* U_b(x)[a][eta] for all sites: out[(x*2 + a)*1728 + eta]. */
-static void sink_tensor_field(int b, int V, const cplx* const S[3], cplx* U) {
+/* U_b(x)[a][eta] for all sites: out[(x*2 + a)*1728 + eta], sink spin
+ * a + off (off = 0: upper components, 2: lower components). */
+static void sink_tensor_field(int b, int V, const cplx* const S[3], int off, cplx* U) {
   double T[2][1728];
-  baryon_tensor(b, 0, T[0]);
-  baryon_tensor(b, 1, T[1]);
+  baryon_tensor(b, off, T[0]);
+  baryon_tensor(b, off + 1, T[1]);
   const int* fl = g_bar[b].flav;
 #pragma omp parallel for schedule(static)
   for (int x = 0; x < V; x++) {
@@ -305,7 +306,8 @@ int oracle_wick_count(int ch) {
   return wick_perms(sf, gf, perm, sign);
 }
 
-/* Term list of one channel and one pair of source spins (a', b'). */
+/* Term list of one channel and one pair of source spins (a', b') (Dirac
+ * indices). */
 static term_t* build_terms(int ch, int ap, int bp, int* nout) {
   const channel_t* C = &g_chan[ch];
   int sf[6], gf[6];
@@ -352,8 +354,12 @@ static term_t* build_terms(int ch, int ap, int bp, int* nout) {
   return t;
 }
 
+static int correlator_impl(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int n_ch, const int* channels,
+                           int n_r, const int* r_list, int lower, cplx* out);
+
 /*
- * oracle_correlator: one time slice, raw (un-normalised) correlators.
+ * oracle_correlator: one time slice, raw (un-normalised) correlators of the
+ * upper Dirac components.
  *   L: spatial extent (V = L^3 sites)
  *   Su, Sd, Ss: propagators [V][12][12] complex128 (Su may equal Sd)
  *   channels[n_ch]: channel ids (0..51 printed order, 52..55 omitted channels)
@@ -363,7 +369,27 @@ static term_t* build_terms(int ch, int ap, int bp, int* nout) {
  */
 int oracle_correlator(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int n_ch,
                       const int* channels, int n_r, const int* r_list, cplx* out) {
+  return correlator_impl(L, Su, Sd, Ss, n_ch, channels, n_r, r_list, 0, out);
+}
+
+/*
+ * oracle_correlator_components: as oracle_correlator, for the upper
+ * (lower = 0: Dirac indices 0, 1) or the lower (lower = 1: Dirac indices
+ * 2, 3) two components of all four external spinor indices (Sec. 5: upper
+ * components give the positive-parity baryons forward in time, lower ones
+ * the antibaryons backward in time).  Output spins relabelled to 0, 1:
+ * s = a~ + 2(b~ + 2(a~' + 2 b~')) with a = a~ + 2 lower.
+ */
+int oracle_correlator_components(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int n_ch,
+                                 const int* channels, int n_r, const int* r_list, int lower, cplx* out) {
+  if (lower != 0 && lower != 1) return -1;
+  return correlator_impl(L, Su, Sd, Ss, n_ch, channels, n_r, r_list, lower, out);
+}
+
+static int correlator_impl(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int n_ch, const int* channels,
+                           int n_r, const int* r_list, int lower, cplx* out) {
   init_tables();
+  const int off = 2 * lower;
   if (L < 1 || n_ch < 0) return -1;
   for (int c = 0; c < n_ch; c++)
     if (channels[c] < 0 || channels[c] >= g_nchan) return -1;
@@ -385,7 +411,7 @@ int oracle_correlator(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int
       if (!U[b]) {
         U[b] = (cplx*)malloc(sizeof(cplx) * (size_t)V * 2 * 1728);
         if (!U[b]) { free(rl); return -2; }
-        sink_tensor_field(b, V, S, U[b]);
+        sink_tensor_field(b, V, S, off, U[b]);
       }
     }
   memset(out, 0, sizeof(cplx) * (size_t)n_ch * nr * 16);
@@ -395,7 +421,7 @@ int oracle_correlator(int L, const cplx* Su, const cplx* Sd, const cplx* Ss, int
     const cplx* U2 = U[C->b[1]];
     int nt[4];
     term_t* tl[4];
-    for (int sp = 0; sp < 4; sp++) tl[sp] = build_terms(channels[c], sp & 1, sp >> 1, &nt[sp]);
+    for (int sp = 0; sp < 4; sp++) tl[sp] = build_terms(channels[c], off + (sp & 1), off + (sp >> 1), &nt[sp]);
     cplx* o = out + (size_t)c * nr * 16;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int ir = 0; ir < nr; ir++) {

@@ -45,6 +45,10 @@ def lib():
         L.oracle_correlator.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_correlator_components.restype = ctypes.c_int
+        L.oracle_correlator_components.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         L.oracle_channel_count.restype = ctypes.c_int
         L.oracle_channel_baryons.argtypes = [ctypes.c_int, ctypes.c_void_p]
         L.oracle_wick_count.argtypes = [ctypes.c_int]
@@ -86,11 +90,13 @@ def cg5() -> np.ndarray:
 
 
 def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
-               r_list=None) -> np.ndarray:
+               r_list=None, lower: bool = False) -> np.ndarray:
     """Raw correlators of one time slice: [n_ch, n_r (or V), 16] complex128.
 
     Su, Sd, Ss: [V, 12, 12] complex128 propagator slices (sink row 3a+c,
-    source column 3a'+c').
+    source column 3a'+c').  lower: the lower two Dirac components (2, 3) of
+    every external spinor index instead of the upper two (Sec. 5), output
+    spins relabelled to 0, 1.
     """
     V = L ** 3
     arrs = [np.ascontiguousarray(S, dtype=np.complex128).reshape(V, 12, 12) for S in (Su, Sd, Ss)]
@@ -101,9 +107,10 @@ def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
         rl = np.ascontiguousarray(np.atleast_1d(r_list), dtype=np.int32)
         nr = n_out = len(rl)
     out = np.zeros((len(ch), n_out, 16), dtype=np.complex128)
-    rc = lib().oracle_correlator(L, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
-                                 len(ch), ch.ctypes.data, nr,
-                                 None if rl is None else rl.ctypes.data, out.ctypes.data)
+    rc = lib().oracle_correlator_components(L, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                            len(ch), ch.ctypes.data, nr,
+                                            None if rl is None else rl.ctypes.data, int(bool(lower)),
+                                            out.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_correlator failed ({rc})")
     return out
