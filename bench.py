@@ -311,8 +311,9 @@ def run_ours(args, torch, rank, world, local):
                 "algorithmic_flop_per_launch": flops_per_launch, "avg_launch_ms": c_avg_ms}
     stage_ms = {k: v[0] / args.steps for k, v in stages.items()}
 
-    def mixed_leg(precision, note):
-        corm = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=precision, device=dev, stream=stream)
+    def mixed_leg(precision, note, components=bbc.BBC_UPPER):
+        corm = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=precision, device=dev, stream=stream,
+                               components=components)
         tune_m, tune_m_ms = corm.autotune(Sl[0], Ss[0], t=0, reps=3)
         ms_m, st_m = timed(corm, args.steps, args.warmup)
         corm.close()
@@ -325,8 +326,10 @@ def run_ours(args, torch, rank, world, local):
                 "contract_frac_fp32_peak": flops_per_launch / (cm_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
                 "tuning": tune_m, "autotune_ms": tune_m_ms}
 
-    mixed = bf16 = None
+    mixed = bf16 = lower = None
     if not args.no_mixed:
+        lower = mixed_leg(bbc.BBC_MIXED_FP32, "lower Dirac components (antibaryons backward in time), mixed FP32",
+                          components=bbc.BBC_LOWER)
         mixed = mixed_leg(bbc.BBC_MIXED_FP32, "FP32 blocks, FFTs and products; FP64 Wick sums and normalisation "
                                               "(per-channel error vs FP64 at L=32: max 5.2e-7)")
         bf16 = mixed_leg(bbc.BBC_MIXED_BF16, "trial: Fourier-space blocks rounded to bfloat16 before the FP32 "
@@ -360,6 +363,7 @@ def run_ours(args, torch, rank, world, local):
         "tuning": {"chosen": tune_fp64, "autotune_ms": tune_fp64_ms},
         "mixed": mixed,
         "bf16_trial": bf16,
+        "lower_components": lower,
         "projection": projection,
         "cpu_baseline": cpu,
         "clocks": clocks,

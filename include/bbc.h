@@ -71,6 +71,12 @@ typedef enum {
 
 typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
 
+/* Which two Dirac components of every external spinor index (Sec. 5):
+ * BBC_UPPER = indices 0, 1 (positive-parity baryons, forward in time),
+ * BBC_LOWER = indices 2, 3 (negative-parity antibaryon states, backward in
+ * time).  Output spins are relabelled to 0, 1 either way. */
+typedef enum { BBC_UPPER = 0, BBC_LOWER = 1 } bbc_components;
+
 typedef enum { BBC_LIGHT = 0, BBC_STRANGE = 1 } bbc_flavour;
 
 /* Lattice description.  L: spatial extent (2, 4, 8, 16, 24, 32 or 48); T: number of time
@@ -94,6 +100,12 @@ typedef struct {
  * duplicate), ENOMEM. */
 bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
                       const int* channels, int n_channels, void* cuda_stream);
+
+/* As bbc_create, for the given spin components of the external spinor
+ * indices (bbc_create = BBC_UPPER).  With BBC_LOWER the normalisation of
+ * bbc_contract uses the backward time distance d = (t0 - t) mod T. */
+bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec, const int* channels,
+                                 int n_channels, bbc_components components, void* cuda_stream);
 
 /* Bytes of device workspace needed to process up to `slices` time slices per
  * bbc_run call (blocks of one slice, transforms, propagator copies). */

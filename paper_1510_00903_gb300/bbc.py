@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(PKG, "libbbc.so")
 
 BBC_OK, BBC_EINVAL, BBC_ENOMEM, BBC_ECUDA, BBC_ESTATE, BBC_ETIMEOUT, BBC_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 BBC_FP64, BBC_MIXED_FP32, BBC_MIXED_BF16 = 0, 1, 2
+BBC_UPPER, BBC_LOWER = 0, 1
 BBC_C128, BBC_C64 = 0, 1
 BBC_LIGHT, BBC_STRANGE = 0, 1
 
@@ -52,6 +53,7 @@ def _load():
     P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
     sig = {
         "bbc_create": ([ctypes.POINTER(P), ctypes.POINTER(bbc_lattice), I, ctypes.POINTER(I), I, P], I),
+        "bbc_create_components": ([ctypes.POINTER(P), ctypes.POINTER(bbc_lattice), I, ctypes.POINTER(I), I, I, P], I),
         "bbc_workspace_size": ([P, I, ctypes.POINTER(ctypes.c_size_t)], I),
         "bbc_set_workspace": ([P, P, ctypes.c_size_t, I], I),
         "bbc_load_propagator": ([P, I, I, I, P, I, I], I),
@@ -99,6 +101,17 @@ def bbc_create(L: int, T: int, t0: int, m_ud: float, m_s: float, precision: int,
     ctx = ctypes.c_void_p()
     st = _lib.bbc_create(ctypes.byref(ctx), ctypes.byref(lat), int(precision), ch, len(channels),
                          ctypes.c_void_p(cuda_stream or None))
+    _check(None, st)
+    return ctx
+
+
+def bbc_create_components(L: int, T: int, t0: int, m_ud: float, m_s: float, precision: int, channels,
+                          components: int, cuda_stream: int = 0):
+    lat = bbc_lattice(L, T, t0, m_ud, m_s)
+    ch = (ctypes.c_int * len(channels))(*[int(c) for c in channels])
+    ctx = ctypes.c_void_p()
+    st = _lib.bbc_create_components(ctypes.byref(ctx), ctypes.byref(lat), int(precision), ch, len(channels),
+                                    int(components), ctypes.c_void_p(cuda_stream or None))
     _check(None, st)
     return ctx
 
@@ -216,7 +229,7 @@ class Correlators:
 
     def __init__(self, L: int, T: int, t0: int = 0, m_ud: float = 0.3, m_s: float = 0.4,
                  channels=CHANNELS_52, precision: int = BBC_FP64, slices: int = 1, device=None,
-                 stream=None, workspace=None):
+                 stream=None, workspace=None, components: int = BBC_UPPER):
         import torch
         self.torch = torch
         dev = torch.device(device or "cuda")
@@ -227,7 +240,9 @@ class Correlators:
         self.L, self.T, self.t0, self.V = L, T, t0, L ** 3
         self.channels = list(channels)
         self.precision = precision
-        self.ctx = bbc_create(L, T, t0, m_ud, m_s, precision, self.channels, self.stream.cuda_stream)
+        self.components = components
+        self.ctx = bbc_create_components(L, T, t0, m_ud, m_s, precision, self.channels, components,
+                                         self.stream.cuda_stream)
         self.slices = slices
         nbytes = bbc_workspace_size(self.ctx, slices)
         if workspace is None:

@@ -83,6 +83,13 @@ bbc_status cuda_fail(bbc_ctx* c, cudaError_t e, const char* where) {
   return fail(c, BBC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Time distance of slice t from the source: forward (t - t0) mod T for the
+// upper components, backward (t0 - t) mod T for the lower ones (Sec. 5).
+int time_distance(const bbc_ctx* c, int t) {
+  const int T = c->lat.T, dt = c->plan.spin_offset ? c->lat.t0 - t : t - c->lat.t0;
+  return ((dt % T) + T) % T;
+}
+
 bool supported_L(int L) { return L == 2 || L == 4 || L == 8 || L == 16 || L == 24 || L == 32 || L == 48; }
 
 cudaEvent_t take_event(bbc_ctx* c) {
@@ -125,6 +132,7 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
   }
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   g.z_slots = p.z_slots;
+  g.spin0 = p.spin_offset;
   return g;
 }
 
@@ -137,14 +145,22 @@ struct FusedSchedule {
 std::mutex g_sched_mutex;
 std::map<std::vector<int>, FusedSchedule> g_sched;
 
+// A plan is fixed by its channel list and spin components.
+std::vector<int> plan_key(const bbc::Plan& plan) {
+  std::vector<int> k = plan.channels;
+  k.push_back(-1 - plan.spin_offset);
+  return k;
+}
+
 const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
   std::lock_guard<std::mutex> lock(g_sched_mutex);
-  auto it = g_sched.find(plan.channels);
+  const std::vector<int> key = plan_key(plan);
+  auto it = g_sched.find(key);
   if (it != g_sched.end()) return it->second;
   FusedSchedule f;
   bbc::make_batches(plan, &f.batches);
   bbc::optimise_fused_layout(plan, &f.batches, &f.layout);
-  return g_sched.emplace(plan.channels, std::move(f)).first->second;
+  return g_sched.emplace(key, std::move(f)).first->second;
 }
 
 // Candidate launch configurations of the autotuner.
@@ -217,6 +233,11 @@ extern "C" {
 
 bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec, const int* channels,
                       int n_channels, void* cuda_stream) {
+  return bbc_create_components(ctx, lat, prec, channels, n_channels, BBC_UPPER, cuda_stream);
+}
+
+bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec, const int* channels,
+                                 int n_channels, bbc_components components, void* cuda_stream) {
   if (!ctx || !lat || !channels) return fail(nullptr, BBC_EINVAL, "null argument");
   *ctx = nullptr;
   if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 24, 32, 48)");
@@ -224,6 +245,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16)
     return fail(nullptr, BBC_EINVAL, "bad precision");
   if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");
+  if (components != BBC_UPPER && components != BBC_LOWER) return fail(nullptr, BBC_EINVAL, "bad spin components");
   bbc_ctx* c = new (std::nothrow) bbc_ctx();
   if (!c) return fail(nullptr, BBC_ENOMEM, "host allocation failed");
   c->lat = *lat;
@@ -232,7 +254,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   c->V = lat->L * lat->L * lat->L;
   std::string err;
   try {
-    if (!bbc::build_plan(channels, n_channels, &c->plan, &err)) {
+    if (!bbc::build_plan(channels, n_channels, &c->plan, &err, components == BBC_LOWER ? 2 : 0)) {
       delete c;
       return fail(nullptr, BBC_EINVAL, err);
     }
@@ -281,7 +303,7 @@ bbc_status bbc_create(bbc_ctx** ctx, const bbc_lattice* lat, bbc_precision prec,
   }
   {  // a configuration tuned earlier in this process for the same problem
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tuned.find({{lat->L, (int)prec}, c->plan.channels});
+    auto it = g_tuned.find({{lat->L, (int)prec}, plan_key(c->plan)});
     if (it != g_tuned.end()) c->tune = it->second;
   }
   if (apply_fused_units(c) != BBC_OK) {
@@ -516,7 +538,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   bbc::ScaleParams sp{};
   sp.n_ch = n_ch;
   const int t = c->slot_t[slot];
-  const int d = ((t - c->lat.t0) % c->lat.T + c->lat.T) % c->lat.T;
+  const int d = time_distance(c, t);
   for (int i = 0; i < n_ch; i++) {
     const int ns = p.n_strange[i];
     const double mass = (6 - ns) * c->lat.m_ud + ns * c->lat.m_s;  // m_B1 + m_B2
@@ -621,7 +643,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   }
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[{{c->lat.L, c->prec}, p.channels}] = c->tune;
+    g_tuned[{{c->lat.L, c->prec}, plan_key(p)}] = c->tune;
   }
   if (best) *best = c->tune;
   if (n_tried) *n_tried = n;

@@ -113,7 +113,7 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
       const int f2 = (fam == 1 || fam == 3) ? 1 : 0;  // LLS, LSS: strange third quark
       const cpx<R>* D = sD + s * 864 + 432 * dq;
       const cpx<R>* S2 = sS + s * 288 + 144 * f2;
-      const int a = i / 1728, r = i % 1728, e01 = r / 12, e2 = r % 12;
+      const int a = i / 1728 + g.spin0, r = i % 1728, e01 = r / 12, e2 = r % 12;
       cpx<R> acc(0, 0);
 #pragma unroll
       for (int c2 = 0; c2 < 3; c2++) cmac(acc, D[e01 * 3 + c2], S2[(3 * a + c2) * 12 + e2]);

@@ -30,6 +30,7 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int first[8], rows[8], fam0[8], fam1[8];
   int zneed_first[9];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
   int z_slots;         // shared-memory positions for tensor entries
+  int spin0;           // Dirac index of the first external spin component (0 upper, 2 lower)
 };
 
 constexpr int kMaxChannels = 64;

@@ -236,9 +236,11 @@ void channel_names(int id, const char* out[4]) {
   for (int i = 0; i < 4; i++) out[i] = kOps[c[i]].name;
 }
 
-bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
+bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int spin_offset) {
   const auto& table = channels_table();
   if (n <= 0) { *err = "empty channel list"; return false; }
+  if (spin_offset != 0 && spin_offset != 2) { *err = "spin offset must be 0 or 2"; return false; }
+  const int off = spin_offset;
   for (int i = 0; i < n; i++) {
     if (channels[i] < 0 || channels[i] >= (int)table.size()) { *err = "unknown channel id " + std::to_string(channels[i]); return false; }
     for (int j = 0; j < i; j++)
@@ -246,6 +248,7 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
   }
   Plan P;
   P.channels.assign(channels, channels + n);
+  P.spin_offset = off;
 
   std::map<std::vector<int64_t>, int> uniq;
   std::vector<UBlock> ublocks;
@@ -346,7 +349,9 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
                   std::vector<std::vector<SrcEntry>> lists;
                   for (int k : attk) {
                     bool dmin = minority[k] >= 0 && minority[k] - 3 * k == src[k].dk;
-                    auto all = source_entries(src[k], dmin ? 0 : evk[k]);
+                    // a delta minority leaves only its colour here (spin placeholder 0,
+                    // filtered against the 3-valued open index below)
+                    auto all = source_entries(src[k], dmin ? 0 : off + evk[k]);
                     std::vector<SrcEntry> keep;
                     for (auto& e : all)
                       if (minority[k] < 0 || e.eta[minority[k] - 3 * k] == ovk[k]) keep.push_back(e);
@@ -545,7 +550,7 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err) {
             // promoted axis (12 values in the block, 3 in the diagram): its
             // source baryon is the one in prom whose open axis this is
             int k = in.open_k[x];
-            val = 3 * e[k] + dv[x];
+            val = 3 * (off + e[k]) + dv[x];
           }
           ov.push_back(val);
         }

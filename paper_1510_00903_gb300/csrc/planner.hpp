@@ -43,6 +43,10 @@ struct DiagramInfo {
 
 struct Plan {
   std::vector<int> channels;
+  // Dirac index of the first external spin component: 0 for the upper two
+  // components (0, 1), 2 for the lower two (2, 3) of every external spinor
+  // index (Sec. 5); every external spin below is relative to it.
+  int spin_offset = 0;
   // block build: rows (block outputs per site) grouped by the families they read
   int n_out = 0;
   int n_blocks = 0;
@@ -70,7 +74,8 @@ int channel_count();
 // Names of the four baryons of a channel (B1, B2 | B3, B4).
 void channel_names(int id, const char* out[4]);
 // Build the plan; returns false and sets *err on a bad channel list.
-bool build_plan(const int* channels, int n, Plan* plan, std::string* err);
+// spin_offset: 0 (upper components) or 2 (lower components).
+bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int spin_offset = 0);
 
 // Warp batches for the fused contraction: tasks grouped by (nA, nB, n1*n2),
 // at most 32 per batch (one per lane).

@@ -176,6 +176,7 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   }
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   g.z_slots = p.z_slots;
+  g.spin0 = p.spin_offset;
   e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int*)(w + L.row_ptr), (const uint32_t*)(w + L.entries),
                               (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st, 1, 256);
   if (e != cudaSuccess) return cuda_fail(c, e, "block build");
@@ -190,7 +191,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
   bbc::ScaleParams sp{};
   sp.n_ch = n_ch;
-  const int d = ((t - c->lat.t0) % c->lat.T + c->lat.T) % c->lat.T;
+  const int dt = c->plan.spin_offset ? c->lat.t0 - t : t - c->lat.t0;  // forward or backward in time
+  const int d = ((dt % c->lat.T) + c->lat.T) % c->lat.T;
   for (int i = 0; i < n_ch; i++) {
     const int ns = p.n_strange[i];
     const double mass = (6 - ns) * c->lat.m_ud + ns * c->lat.m_s;

@@ -112,3 +112,21 @@ def test_tuning_defaults_validation_and_autotune_state():
     finally:
         bbc.bbc_destroy(c)
         bbc.bbc_destroy(f)
+
+
+def test_lower_components_plan_and_errors():
+    """The lower spin components give a plan of the same shape (the C gamma5
+    block swap maps one onto the other); a bad component selector is EINVAL."""
+    ch = list(range(52))
+    up = bbc.bbc_create(16, 32, 0, 0.3, 0.4, bbc.BBC_FP64, ch)
+    lo = bbc.bbc_create_components(16, 32, 0, 0.3, 0.4, bbc.BBC_FP64, ch, bbc.BBC_LOWER)
+    try:
+        assert bbc.bbc_plan_sizes(lo) == bbc.bbc_plan_sizes(up)
+        assert bbc.bbc_plan_sizes(lo)["block_outputs"] == 7368
+        assert bbc.bbc_workspace_size(lo, 1) == bbc.bbc_workspace_size(up, 1)
+    finally:
+        bbc.bbc_destroy(up)
+        bbc.bbc_destroy(lo)
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_create_components(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0], 2)
+    assert e.value.status == bbc.BBC_EINVAL
