@@ -301,6 +301,60 @@ class Correlators:
             cur.wait_stream(self.stream)
         return out
 
+    def run_streamed(self, S_light, S_strange, times, out, normalised: bool = True, on_slice=None):
+        """Slices whose propagators live in pinned host memory ([T, V, 12, 12]):
+        the host-to-device copy of slice i+1 (on a copy stream, into one of
+        two device buffers) overlaps the compute of slice i.  The correlators
+        of each slice land in ``out`` ([n_channels, V, 16], overwritten slice
+        after slice); ``on_slice(t, out)``, if given, is called after each
+        slice's work is queued, to queue a consumer on the context stream."""
+        torch = self.torch
+        times = list(times)
+        if not times:
+            return out
+        V = self.V
+        key = (S_light.dtype, S_strange.dtype)
+        if getattr(self, "_stream_key", None) != key:
+            self._copy_stream = torch.cuda.Stream(self.device)
+            self._stream_bufs = [(torch.empty((V, 12, 12), dtype=S_light.dtype, device=self.device),
+                                  torch.empty((V, 12, 12), dtype=S_strange.dtype, device=self.device))
+                                 for _ in range(2)]
+            self._stream_key = key
+        copy, bufs = self._copy_stream, self._stream_bufs
+        copied = [torch.cuda.Event() for _ in range(2)]
+        consumed = [torch.cuda.Event() for _ in range(2)]
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        copy.wait_stream(self.stream)  # earlier readers of the buffers
+
+        def issue_copy(i):
+            b = i % 2
+            with torch.cuda.stream(copy):
+                if i >= 2:
+                    copy.wait_event(consumed[b])
+                bufs[b][0].copy_(S_light[times[i]], non_blocking=True)
+                bufs[b][1].copy_(S_strange[times[i]], non_blocking=True)
+                copied[b].record(copy)
+
+        issue_copy(0)
+        for i, t in enumerate(times):
+            if i + 1 < len(times):
+                issue_copy(i + 1)
+            b = i % 2
+            with torch.cuda.stream(self.stream):
+                self.stream.wait_event(copied[b])
+                self.load(BBC_LIGHT, 0, t, bufs[b][0])
+                self.load(BBC_STRANGE, 0, t, bufs[b][1])
+                consumed[b].record(self.stream)
+                self.build(1)
+                self.contract(0, out, normalised)
+                if on_slice is not None:
+                    on_slice(t, out)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+        return out
+
     def autotune(self, S_light, S_strange, t: int = 0, reps: int = 5):
         """Load slice t into slot 0 and run the autotuner (bbc_autotune);
         returns (configuration, ms per candidate)."""

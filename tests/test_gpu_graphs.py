@@ -68,3 +68,28 @@ def test_lattice_batch_uneven_lattices_one_graph():
         assert err.max() < 2e-5, (L, err)
     assert b.sites_channels() == 2 * (4 * 64 + 6 * 512) * 2
     b.close()
+
+
+def test_run_streamed_overlapped_copies():
+    """Pinned host propagators streamed slice by slice (copy of slice t+1
+    overlapping slice t): every slice equals the oracle."""
+    L, T = 8, 5
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=61)
+    chans = [1, 41]
+    Sl = torch.from_numpy(F["u"]).to(torch.complex64).pin_memory()
+    Ss = torch.from_numpy(F["s"]).to(torch.complex64).pin_memory()
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=bbc.BBC_MIXED_FP32, device=dev,
+                          stream=torch.cuda.Stream(dev))
+    out = torch.empty((len(chans), L ** 3, 16), dtype=torch.complex128, device=dev)
+    res = torch.empty((T,) + tuple(out.shape), dtype=out.dtype, device=dev)
+    cor.run_streamed(Sl, Ss, range(T), out, on_slice=lambda t, o: res[t].copy_(o))
+    torch.cuda.synchronize(dev)
+    got = res.cpu().numpy()
+    for t in range(T):
+        F32 = {k: v[t].astype(np.complex64).astype(np.complex128) for k, v in F.items()}
+        want = orc.normalise(orc.correlator(L, F32["u"], F32["d"], F32["s"], chans), chans, t, 0.3, 0.4)
+        scale = np.abs(want).reshape(len(chans), -1).max(axis=1)
+        err = np.abs(got[t] - want).reshape(len(chans), -1).max(axis=1) / scale
+        assert err.max() < 2e-5, (t, err)
+    cor.close()
