@@ -31,7 +31,7 @@ bool fused_path(int prec) { return prec != BBC_FP64; }  // FP32 or bfloat16 prod
 constexpr int kMaxFusedWarps = 16;
 
 struct Layout {
-  size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
+  size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
   size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, total;
 };
@@ -40,8 +40,8 @@ Layout layout(const bbc_ctx* c, int slots) {
   const bbc::Plan& p = c->plan;
   Layout L{};
   size_t o = 0;
-  L.row_ptr = o; o = align256(o + sizeof(int) * p.row_ptr.size());
-  L.entries = o; o = align256(o + sizeof(uint32_t) * p.entries.size());
+  L.ell_chunk = o; o = align256(o + sizeof(int2) * p.ell_chunk.size());
+  L.ell = o; o = align256(o + sizeof(uint32_t) * p.ell.size());
   L.zneed = o; o = align256(o + sizeof(uint32_t) * p.zneed.size());
   L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
   L.group_ptr = o; o = align256(o + sizeof(int) * c->group_ptr.size());
@@ -133,6 +133,7 @@ bbc::DevGroups groups_of(const bbc::Plan& p) {
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   g.z_slots = p.z_slots;
   g.spin0 = p.spin_offset;
+  for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
   return g;
 }
 
@@ -351,8 +352,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->ws = w;
   c->ws_bytes = bytes;
   c->slots = slices;
-  c->d_row_ptr = (int*)(w + L.row_ptr);
-  c->d_entries = (uint32_t*)(w + L.entries);
+  c->d_ell_chunk = (int2*)(w + L.ell_chunk);
+  c->d_ell = (uint32_t*)(w + L.ell);
   c->d_zneed = (uint32_t*)(w + L.zneed);
   c->d_tasks = (bbc::DevTask*)(w + L.tasks);
   c->d_group_ptr = (int*)(w + L.group_ptr);
@@ -402,8 +403,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     for (int j = 0; j < 32; j++) wb[i].task[j] = j < wb[i].n ? c->batches[i].tasks[j] : 0;
   }
   struct Up { void* dst; const void* src; size_t n; } ups[] = {
-      {c->d_row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
-      {c->d_entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
+      {c->d_ell_chunk, p.ell_chunk.data(), sizeof(int2) * p.ell_chunk.size()},
+      {c->d_ell, p.ell.data(), sizeof(uint32_t) * p.ell.size()},
       {c->d_zneed, p.zneed.data(), sizeof(uint32_t) * p.zneed.size()},
       {c->d_tasks, tasks.data(), sizeof(bbc::DevTask) * tasks.size()},
       {c->d_group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size()},
@@ -482,7 +483,7 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_BUILD);
-    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_row_ptr, c->d_entries, c->d_zneed, groups_of(p),
+    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, groups_of(p),
                                 c->d_blk, p.n_out, fp64, c->stream, c->tune.build_sites, c->tune.build_threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
@@ -603,7 +604,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     cand.build_threads = bc[1];
     if (!tuning_valid(c, cand)) { record(-1.0); continue; }
     const double v = time_launches(c, reps, [&] {
-      return bbc::launch_block_build(c->d_prop, c->V, 1, c->d_row_ptr, c->d_entries, c->d_zneed, g, c->d_blk,
+      return bbc::launch_block_build(c->d_prop, c->V, 1, c->d_ell_chunk, c->d_ell, c->d_zneed, g, c->d_blk,
                                      p.n_out, fp64, c->stream, bc[0], bc[1]);
     });
     record(v);

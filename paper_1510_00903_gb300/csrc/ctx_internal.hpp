@@ -22,8 +22,8 @@ struct bbc_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int slots = 0;
-  int* d_row_ptr = nullptr;
-  uint32_t* d_entries = nullptr;
+  int2* d_ell_chunk = nullptr;           // (offset, length) of each 32-row chunk of block rows
+  uint32_t* d_ell = nullptr;             // lane-interleaved row entries
   uint32_t* d_zneed = nullptr;
   bbc::DevTask* d_tasks = nullptr;
   int* d_group_ptr = nullptr;

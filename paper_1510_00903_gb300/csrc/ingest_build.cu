@@ -61,8 +61,8 @@ __constant__ int c_cg5[4][3] = {{0, 1, 1}, {1, 0, -1}, {2, 3, 1}, {3, 2, -1}};
 // row's entry list is read once per SITES sites.
 template <typename R, int SITES, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ row_ptr,
-              const uint32_t* __restrict__ entries, const uint32_t* __restrict__ zneed, DevGroups g,
+k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ ell_chunk,
+              const uint32_t* __restrict__ ell, const uint32_t* __restrict__ zneed, DevGroups g,
               cpx<R>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [SITES][2][144]  light, strange
@@ -126,9 +126,11 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int* __restrict__ ro
       cpx<R> acc[SITES];
 #pragma unroll
       for (int s = 0; s < SITES; s++) acc[s] = cpx<R>(0, 0);
-      const int k1 = row_ptr[r + 1];
-      for (int k = row_ptr[r]; k < k1; k++) {
-        const uint32_t e = __ldg(entries + k);
+      // the warp's 32 rows are one chunk: entry k of all of them is 128 contiguous bytes
+      const int2 ch = __ldg(ell_chunk + g.chunk_first[gi] + ((r - r0) >> 5));
+      const uint32_t* ep = ell + ch.x + ((r - r0) & 31);
+      for (int k = 0; k < ch.y; k++) {
+        const uint32_t e = __ldg(ep + 32 * k);
         const R w = sW[((int)(int16_t)(e >> 16)) + 16];
         const int pos = e & 0xffffu;
 #pragma unroll
@@ -156,28 +158,28 @@ bool build_variant_supported(int sites, int threads) {
 }
 
 template <typename R, int SITES, int THREADS>
-cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int* row_ptr, const uint32_t* entries,
+cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                  const uint32_t* zneed, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
   const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8);
   static int granted[64] = {0};
   cudaError_t e = ensure_smem(k_block_build<R, SITES, THREADS>, sm, granted);
   if (e != cudaSuccess) return e;
   dim3 grid(V / SITES, n_slots);
-  k_block_build<R, SITES, THREADS><<<grid, THREADS, sm, st>>>((const cpx<R>*)prop, V, row_ptr, entries, zneed, g,
+  k_block_build<R, SITES, THREADS><<<grid, THREADS, sm, st>>>((const cpx<R>*)prop, V, ell_chunk, ell, zneed, g,
                                                               (cpx<R>*)blk, n_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const uint32_t* zneed, const DevGroups& g, void* blk,
+cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
+                               const uint32_t* ell, const uint32_t* zneed, const DevGroups& g, void* blk,
                                int n_out, bool fp64, cudaStream_t st, int sites, int threads) {
   if (!build_variant_supported(sites, threads) || V % sites != 0 ||
       block_build_smem(g.z_slots, sites, fp64) > kMaxSmemPerBlock)
     return cudaErrorInvalidValue;
 #define BBC_BUILD(S, T)                                                                                            \
   if (sites == S && threads == T)                                                                                  \
-    return fp64 ? launch_build_variant<double, S, T>(prop, V, n_slots, row_ptr, entries, zneed, g, blk, n_out, st) \
-                : launch_build_variant<float, S, T>(prop, V, n_slots, row_ptr, entries, zneed, g, blk, n_out, st);
+    return fp64 ? launch_build_variant<double, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st) \
+                : launch_build_variant<float, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st);
   BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512)
 #undef BBC_BUILD
   return cudaErrorInvalidValue;

@@ -31,6 +31,7 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int zneed_first[9];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
   int z_slots;         // shared-memory positions for tensor entries
   int spin0;           // Dirac index of the first external spin component (0 upper, 2 lower)
+  int chunk_first[9];  // first 32-row chunk of each group in the lane-interleaved entry table
 };
 
 constexpr int kMaxChannels = 64;
@@ -59,8 +60,9 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
 // (2, 512) or (4, 512) (V a multiple of sites).
 bool build_variant_supported(int sites, int threads);
 size_t block_build_smem(int z_slots, int sites, bool fp64);
-cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int* row_ptr,
-                               const uint32_t* entries, const uint32_t* zneed, const DevGroups& g,
+// ell_chunk[c] = (offset, length) of 32-row chunk c in ell (lane-interleaved rows).
+cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
+                               const uint32_t* ell, const uint32_t* zneed, const DevGroups& g,
                                void* blk, int n_out, bool fp64, cudaStream_t st, int sites, int threads);
 // Forward 3-D FFT of every block field: x pass from the site-major build
 // output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],

@@ -645,6 +645,30 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
   for (uint32_t z : P.zneed)
     if ((int)(z & 0x1fffu) >= P.z_slots || (z >> 14) >= (uint32_t)kFamEntries) { *err = "internal: tensor entry"; return false; }
   if ((int)P.row_ptr.size() != P.n_out + 1) { *err = "internal: row table"; return false; }
+  // lane-interleaved 32-row chunks of every group (the build kernel's layout)
+  P.chunk_first.assign(1, 0);
+  for (const GroupInfo& g : P.groups) {
+    for (int c0 = 0; c0 < g.n_rows; c0 += 32) {
+      const int r0 = g.first_row + c0, nr = std::min(32, g.n_rows - c0);
+      int len = 0;
+      for (int l = 0; l < nr; l++) len = std::max(len, P.row_ptr[r0 + l + 1] - P.row_ptr[r0 + l]);
+      const int base = (int)P.ell.size();
+      P.ell.resize(P.ell.size() + (size_t)32 * len, 0u);  // weight 0, position 0
+      for (int l = 0; l < nr; l++)
+        for (int k = 0; k < P.row_ptr[r0 + l + 1] - P.row_ptr[r0 + l]; k++)
+          P.ell[base + 32 * k + l] = P.entries[P.row_ptr[r0 + l] + k];
+      P.ell_chunk.push_back({base, len});
+    }
+    P.chunk_first.push_back((int)P.ell_chunk.size());
+  }
+  for (const auto& c : P.ell_chunk)
+    if (c.first < 0 || c.second < 0 || (size_t)c.first + 32 * (size_t)c.second > P.ell.size()) {
+      *err = "internal: row chunk";
+      return false;
+    }
+  for (uint32_t e : P.ell)
+    if ((int)(e & 0xffffu) >= P.z_slots) { *err = "internal: tensor position"; return false; }
+  if (P.groups.size() > 8) { *err = "internal: group count"; return false; }
   *plan = std::move(P);
   return true;
 }

@@ -54,6 +54,14 @@ struct Plan {
   std::vector<int> row_ptr;          // n_out + 1
   std::vector<uint32_t> entries;     // low 16 bits: compact position of a tensor entry in shared memory,
                                      // high 16 bits: signed integer weight
+  // The same rows as 32-row chunks (chunk j of group g: rows first_row + 32j ..
+  // + 31) stored lane-interleaved: entry k of the chunk's lane l at
+  // ell[ell_chunk[c].x + 32 k + l], k < ell_chunk[c].y (the chunk's longest
+  // row; shorter rows padded with weight-0 entries at position 0), so a warp
+  // reading entry k of 32 consecutive rows reads 128 contiguous bytes.
+  std::vector<int> chunk_first;      // groups + 1: first chunk of each group
+  std::vector<std::pair<int, int>> ell_chunk;  // (offset, length) per chunk
+  std::vector<uint32_t> ell;
   std::vector<uint32_t> zneed;       // entries each group computes: pos | slot << 13 | (a*1728 + e0*144 + e1*12 + e2) << 14
   std::vector<int> zneed_first;      // groups + 1 offsets into zneed
   int z_slots = 0;                   // shared-memory positions needed (max over groups)

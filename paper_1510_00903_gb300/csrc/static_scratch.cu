@@ -33,7 +33,7 @@ void* g_scratch_addr[kMaxDevices] = {nullptr};
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct StaticLayout {
-  size_t row_ptr, entries, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
+  size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
   size_t prop, amax, kexp, blk, blkf, P, ct, scale, total;
 };
 
@@ -42,8 +42,8 @@ StaticLayout static_layout(const bbc_ctx* c) {
   const size_t cb = c->prec == BBC_FP64 ? 16 : 8, V = (size_t)c->V;
   StaticLayout L{};
   size_t o = 0;
-  L.row_ptr = o; o = a256(o + sizeof(int) * p.row_ptr.size());
-  L.entries = o; o = a256(o + sizeof(uint32_t) * p.entries.size());
+  L.ell_chunk = o; o = a256(o + sizeof(int2) * p.ell_chunk.size());
+  L.ell = o; o = a256(o + sizeof(uint32_t) * p.ell.size());
   L.zneed = o; o = a256(o + sizeof(uint32_t) * p.zneed.size());
   L.tasks = o; o = a256(o + sizeof(bbc::DevTask) * p.tasks.size());
   L.group_ptr = o; o = a256(o + sizeof(int) * c->group_ptr.size());
@@ -114,8 +114,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   cudaStream_t st = c->stream;
   // plan tables (copies from pageable host memory return once the data is staged)
   struct Up { size_t off; const void* src; size_t n; } ups[] = {
-      {L.row_ptr, p.row_ptr.data(), sizeof(int) * p.row_ptr.size()},
-      {L.entries, p.entries.data(), sizeof(uint32_t) * p.entries.size()},
+      {L.ell_chunk, p.ell_chunk.data(), sizeof(int2) * p.ell_chunk.size()},
+      {L.ell, p.ell.data(), sizeof(uint32_t) * p.ell.size()},
       {L.zneed, p.zneed.data(), sizeof(uint32_t) * p.zneed.size()},
       {L.group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size()},
       {L.group_task, c->group_task.data(), sizeof(int) * c->group_task.size()},
@@ -177,7 +177,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
   g.z_slots = p.z_slots;
   g.spin0 = p.spin_offset;
-  e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int*)(w + L.row_ptr), (const uint32_t*)(w + L.entries),
+  for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
+  e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int2*)(w + L.ell_chunk), (const uint32_t*)(w + L.ell),
                               (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st, 1, 256);
   if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   e = bbc::launch_fft_forward(w + L.blk, w + L.blkf, c->lat.L, 1, p.n_out, fp64, st);
