@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
     ap.add_argument("--tuning", default=None,
-                    help="launch configuration for --single-slice: sites,threads,warps,chunk (as bbc_set_tuning)")
+                    help="launch configuration for --single-slice: sites,threads,warps,chunk[,steps] (as bbc_set_tuning)")
     return ap.parse_args()
 
 
@@ -227,9 +227,9 @@ def run_ours(args, torch, rank, world, local):
         prec = {"fp64": bbc.BBC_FP64, "mixed": bbc.BBC_MIXED_FP32, "bf16": bbc.BBC_MIXED_BF16}[args.single_slice]
         cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
         if args.tuning:
-            sites, threads, warps, chunk = (int(x) for x in args.tuning.split(","))
-            cor.set_tuning({"build_sites": sites, "build_threads": threads, "fused_warps": warps,
-                            "fused_chunk": chunk})
+            v = [int(x) for x in args.tuning.split(",")]
+            cor.set_tuning({"build_sites": v[0], "build_threads": v[1], "fused_warps": v[2], "fused_chunk": v[3],
+                            "fused_steps": v[4] if len(v) > 4 else 1})
         o = cor.run(torch.from_numpy(F1["u"]).to(dev), torch.from_numpy(F1["s"]).to(dev), [t])
         torch.cuda.synchronize(dev)
         print("single slice done", float(o.abs().max()))

@@ -189,13 +189,15 @@ bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, 
  *  fused_warps, fused_chunk (mixed precisions only): warps per CTA (8, 12, 16)
  *    of the fused q-space contraction and the open-index steps per warp unit
  *    (18, 36, 72, 144), or 0: each warp takes one contiguous run of the
- *    batches' steps of equal modelled cost.
- * A new context starts with (1, 256, 16, 18), or with the configuration
+ *    batches' steps of equal modelled cost;
+ *  fused_steps: open-index steps whose rows a lane loads before multiplying
+ *    (1; or 2 with 8 or 12 warps, which leave the registers for it).
+ * A new context starts with (1, 256, 16, 18, 1), or with the configuration
  * bbc_autotune chose earlier in the process for the same L, precision and
  * channel list. */
 typedef struct {
   int build_sites, build_threads;
-  int fused_warps, fused_chunk;
+  int fused_warps, fused_chunk, fused_steps;
 } bbc_tuning;
 
 bbc_status bbc_get_tuning(const bbc_ctx* ctx, bbc_tuning* out);
@@ -208,8 +210,9 @@ bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
 /* Autotuner: times every valid candidate configuration with CUDA events on
  * the context stream, `reps` launches each after one untimed launch, on the
  * propagators loaded in slot 0 -- the block-build candidates in the order
- * above, then (mixed precisions) every (fused_warps, fused_chunk) pair in
- * row-major order -- keeps the fastest of each kernel, rebuilds slot 0 with
+ * above, then (mixed precisions) every valid (fused_warps, fused_steps,
+ * fused_chunk) in row-major order (warps 8, 12, 16; steps 1, 2; chunks 0, 18,
+ * 36, 72, 144) -- keeps the fastest of each kernel, rebuilds slot 0 with
  * it, and records it for later contexts with the same L, precision and
  * channel list.  ms[i] (i < cap) receives the average milliseconds per launch
  * of candidate i (-1 for a candidate that is not valid here); *n_tried the

@@ -35,7 +35,7 @@ class BBCError(RuntimeError):
 
 class bbc_tuning(ctypes.Structure):
     _fields_ = [("build_sites", ctypes.c_int), ("build_threads", ctypes.c_int),
-                ("fused_warps", ctypes.c_int), ("fused_chunk", ctypes.c_int)]
+                ("fused_warps", ctypes.c_int), ("fused_chunk", ctypes.c_int), ("fused_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -194,8 +194,9 @@ def bbc_get_tuning(ctx) -> dict:
     return t.as_dict()
 
 
-def bbc_set_tuning(ctx, build_sites: int, build_threads: int, fused_warps: int = 16, fused_chunk: int = 18):
-    t = bbc_tuning(build_sites, build_threads, fused_warps, fused_chunk)
+def bbc_set_tuning(ctx, build_sites: int, build_threads: int, fused_warps: int = 16, fused_chunk: int = 18,
+                   fused_steps: int = 1):
+    t = bbc_tuning(build_sites, build_threads, fused_warps, fused_chunk, fused_steps)
     _check(ctx, _lib.bbc_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -371,7 +372,8 @@ class Correlators:
         return bbc_get_tuning(self.ctx)
 
     def set_tuning(self, cfg: dict):
-        bbc_set_tuning(self.ctx, cfg["build_sites"], cfg["build_threads"], cfg["fused_warps"], cfg["fused_chunk"])
+        bbc_set_tuning(self.ctx, cfg["build_sites"], cfg["build_threads"], cfg["fused_warps"], cfg["fused_chunk"],
+                       cfg.get("fused_steps", 1))
 
     def project(self, C, R=None, Ra1=None, a1: bool = True):
         """Spin states |J M> and, with ``a1``, the cubic-group A1 average of

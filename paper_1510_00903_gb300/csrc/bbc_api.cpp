@@ -167,6 +167,7 @@ const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
 // Candidate launch configurations of the autotuner.
 const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}};  // (sites per CTA, threads)
 const int kFusedWarpsCand[] = {8, 12, 16};
+const int kFusedStepsCand[] = {1, 2};
 const int kChunkCand[] = {0, 18, 36, 72, 144};  // 0: contiguous equal-cost pieces
 
 // Tuned configurations per (L, precision, channel list), for later contexts.
@@ -178,7 +179,7 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, c->prec == BBC_FP64) > bbc::kMaxSmemPerBlock)
     return false;
   if (fused_path(c->prec)) {
-    if (!bbc::fused_variant_supported(t.fused_warps)) return false;
+    if (!bbc::fused_variant_supported(t.fused_warps, t.fused_steps)) return false;
     bool chunk_ok = false;
     for (int k : kChunkCand) chunk_ok |= k == t.fused_chunk;
     if (!chunk_ok) return false;
@@ -533,7 +534,8 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     e = bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
                                    (int)c->qlist.size(), c->d_tasks,
                                    (int)p.tasks.size(), c->d_batches, c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem,
-                                   c->d_ccoef, n_ch, c->d_ct, c->tune.fused_warps, bf16, c->stream);
+                                   c->d_ccoef, n_ch, c->d_ct, c->tune.fused_warps, c->tune.fused_steps, bf16,
+                                   c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "fused contraction");
   }
   bbc::ScaleParams sp{};
@@ -573,6 +575,7 @@ bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
   if (!fused_path(c->prec)) {  // the FP64 path has no fused kernel to configure
     want.fused_warps = c->tune.fused_warps;
     want.fused_chunk = c->tune.fused_chunk;
+    want.fused_steps = c->tune.fused_steps;
   }
   if (!tuning_valid(c, want)) return fail(c, BBC_EINVAL, "unsupported launch configuration");
   const bbc_tuning old = c->tune;
@@ -622,22 +625,27 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     const char* blk = bf16 ? c->d_blk16 : c->d_blk;
     best_ms = -1.0;
     for (int wv : kFusedWarpsCand)
-      for (int kv : kChunkCand) {
-        c->tune.fused_warps = wv;
-        c->tune.fused_chunk = kv;
-        st = apply_fused_units(c);
-        if (st != BBC_OK) return st;
-        const double v = time_launches(c, reps, [&] {
-          return bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
-                                            (int)c->qlist.size(), c->d_tasks, (int)p.tasks.size(), c->d_batches,
-                                            c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem, c->d_ccoef,
-                                            (int)p.channels.size(), c->d_ct, wv, bf16, c->stream);
-        });
-        record(v);
-        if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: fused contraction");
-        if (best_ms < 0 || v < best_ms) { best_ms = v; t.fused_warps = wv; t.fused_chunk = kv; }
+      for (int sv : kFusedStepsCand) {
+        if (!bbc::fused_variant_supported(wv, sv)) continue;
+        for (int kv : kChunkCand) {
+          c->tune.fused_warps = wv;
+          c->tune.fused_steps = sv;
+          c->tune.fused_chunk = kv;
+          st = apply_fused_units(c);
+          if (st != BBC_OK) return st;
+          const double v = time_launches(c, reps, [&] {
+            return bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
+                                              (int)c->qlist.size(), c->d_tasks, (int)p.tasks.size(), c->d_batches,
+                                              c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem, c->d_ccoef,
+                                              (int)p.channels.size(), c->d_ct, wv, sv, bf16, c->stream);
+          });
+          record(v);
+          if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: fused contraction");
+          if (best_ms < 0 || v < best_ms) { best_ms = v; t.fused_warps = wv; t.fused_steps = sv; t.fused_chunk = kv; }
+        }
       }
     c->tune.fused_warps = t.fused_warps;
+    c->tune.fused_steps = t.fused_steps;
     c->tune.fused_chunk = t.fused_chunk;
     st = apply_fused_units(c);
     if (st != BBC_OK) return st;

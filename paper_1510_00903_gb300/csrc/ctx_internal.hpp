@@ -43,7 +43,7 @@ struct bbc_ctx {
   int4* d_wunits = nullptr;
   int* d_qlist = nullptr;
   // launch configuration (bbc_set_tuning / bbc_autotune)
-  bbc_tuning tune{1, 256, 16, 18};
+  bbc_tuning tune{1, 256, 16, 18, 1};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
   std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
   int n_slots = 0;

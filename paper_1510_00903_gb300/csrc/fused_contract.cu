@@ -47,7 +47,10 @@ __device__ __forceinline__ float4 load_row(const uint2* R, int i) {
                      __uint_as_float(u.y & 0xffff0000u));
 }
 
-template <int NA, int NB, typename Row>
+// STEPS > 1 loads the rows of STEPS consecutive open-index steps before
+// multiplying any of them (more shared-memory loads in flight per warp, for
+// launch shapes with registers to spare).
+template <int NA, int NB, int STEPS, typename Row>
 __device__ __forceinline__ void unit_products_pair(const Row* __restrict__ R, const DevTask& t, int k0, int k1,
                                                    cpx<float>* P0, cpx<float>* P1, int rot, bool self) {
   const int n2 = t.n2;
@@ -58,12 +61,11 @@ __device__ __forceinline__ void unit_products_pair(const Row* __restrict__ R, co
   cpx<float> acc0[NA * NB], acc1[NA * NB];
 #pragma unroll
   for (int i = 0; i < NA * NB; i++) { acc0[i] = cpx<float>(0.f, 0.f); acc1[i] = cpx<float>(0.f, 0.f); }
-  for (int k = k0; k < k1; k++) {
-    float4 a[NA], b[NB];
-#pragma unroll
-    for (int r = 0; r < NA; r++) a[r] = load_row(R, t.offA[r] + oA);
-#pragma unroll
-    for (int r = 0; r < NB; r++) b[r] = load_row(R, t.offB[r] + oB);
+  auto advance = [&]() {
+    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
+    else { oA += sA2; oB += sB2; }
+  };
+  auto multiply = [&](const float4 (&a)[NA], const float4 (&b)[NB]) {
 #pragma unroll
     for (int ra = 0; ra < NA; ra++)
 #pragma unroll
@@ -71,8 +73,31 @@ __device__ __forceinline__ void unit_products_pair(const Row* __restrict__ R, co
         cmac(acc0[ra * NB + rb], cpx<float>(a[ra].x, a[ra].y), cpx<float>(b[rb].z, b[rb].w));
         cmac(acc1[ra * NB + rb], cpx<float>(a[ra].z, a[ra].w), cpx<float>(b[rb].x, b[rb].y));
       }
-    if (++i2 == n2) { i2 = 0; oA += wrapA; oB += wrapB; }
-    else { oA += sA2; oB += sB2; }
+  };
+  int k = k0;
+  if (STEPS > 1) {
+    for (; k + STEPS <= k1; k += STEPS) {
+      float4 a[STEPS][NA], b[STEPS][NB];
+#pragma unroll
+      for (int s = 0; s < STEPS; s++) {
+#pragma unroll
+        for (int r = 0; r < NA; r++) a[s][r] = load_row(R, t.offA[r] + oA);
+#pragma unroll
+        for (int r = 0; r < NB; r++) b[s][r] = load_row(R, t.offB[r] + oB);
+        advance();
+      }
+#pragma unroll
+      for (int s = 0; s < STEPS; s++) multiply(a[s], b[s]);
+    }
+  }
+  for (; k < k1; k++) {
+    float4 a[NA], b[NB];
+#pragma unroll
+    for (int r = 0; r < NA; r++) a[r] = load_row(R, t.offA[r] + oA);
+#pragma unroll
+    for (int r = 0; r < NB; r++) b[r] = load_row(R, t.offB[r] + oB);
+    multiply(a, b);
+    advance();
   }
   // P slot of product i of task ti: ti*16 + ((i + ti) & 15) -- the rotation
   // spreads the 32 lanes' (distinct tasks') slots over the shared-memory banks
@@ -89,7 +114,7 @@ __device__ __forceinline__ void unit_products_pair(const Row* __restrict__ R, co
   }
 }
 
-template <int WARPS, bool BF16>
+template <int WARPS, int STEPS, bool BF16>
 __global__ void __launch_bounds__(WARPS * 32, 1)
 k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __restrict__ row_slot, int n_slots,
                  const int* __restrict__ qlist,
@@ -139,9 +164,9 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
     const DevTask t = tasks[ti];
     cpx<float>* p0 = P + ti * 16;
     cpx<float>* p1 = P + np + ti * 16;
-    if (wb.nA == 4) unit_products_pair<4, 4>(R, t, un.z, un.w, p0, p1, ti, self);
-    else if (wb.nA == 2) unit_products_pair<2, 8>(R, t, un.z, un.w, p0, p1, ti, self);
-    else unit_products_pair<8, 2>(R, t, un.z, un.w, p0, p1, ti, self);
+    if (wb.nA == 4) unit_products_pair<4, 4, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+    else if (wb.nA == 2) unit_products_pair<2, 8, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+    else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
   }
   __syncthreads();
   // products to FP64 once (undoing the slot rotation), over the rows' space
@@ -184,35 +209,41 @@ cudaError_t launch_to_bf16(const void* src, void* dst, size_t n, cudaStream_t st
   return cudaGetLastError();
 }
 
-template <int WARPS, bool BF16>
+template <int WARPS, int STEPS, bool BF16>
 cudaError_t launch_fused_variant(size_t sm, int n_q, cudaStream_t st, const void* blk, int L, int n_out,
                                  const int* row_slot, int n_slots, const int* qlist, const DevTask* tasks, int n_tasks,
                                  const WarpBatch* batches, const int* wptr, const int4* wunits, const int* cptr,
                                  const int* citem, const double* ccoef, int n_outputs, cpx<double>* ct) {
   static int granted[64] = {0};
-  cudaError_t e = ensure_smem(k_contract_fused<WARPS, BF16>, sm, granted);
+  cudaError_t e = ensure_smem(k_contract_fused<WARPS, STEPS, BF16>, sm, granted);
   if (e != cudaSuccess) return e;
-  k_contract_fused<WARPS, BF16><<<n_q, WARPS * 32, sm, st>>>(blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks,
-                                                              batches, wptr, wunits, cptr, citem, ccoef, n_outputs,
-                                                              ct);
+  k_contract_fused<WARPS, STEPS, BF16><<<n_q, WARPS * 32, sm, st>>>(blk, L, n_out, row_slot, n_slots, qlist, tasks,
+                                                                     n_tasks, batches, wptr, wunits, cptr, citem,
+                                                                     ccoef, n_outputs, ct);
   return cudaGetLastError();
 }
 
-bool fused_variant_supported(int warps) { return warps == 8 || warps == 12 || warps == 16; }
+// (warps, steps) shapes: 16 warps leave 128 registers a thread, room for one
+// step of rows; 8 and 12 warps can hold two.
+bool fused_variant_supported(int warps, int steps) {
+  return ((warps == 8 || warps == 12) && (steps == 1 || steps == 2)) || (warps == 16 && steps == 1);
+}
 
 cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
                                   int n_q, const DevTask* tasks, int n_tasks, const WarpBatch* batches,
                                   const int* wptr, const int4* wunits, const int* cptr, const int* citem,
-                                  const double* ccoef, int n_ch, void* ct, int warps, bool bf16, cudaStream_t st) {
+                                  const double* ccoef, int n_ch, void* ct, int warps, int steps, bool bf16,
+                                  cudaStream_t st) {
   const size_t sm = contract_fused_smem(n_slots, n_tasks, bf16);
   cpx<double>* o = (cpx<double>*)ct;
   const int n_outputs = n_ch * 16;
-#define BBC_FUSED(W, B)                                                                                          \
-  if (warps == W && bf16 == B)                                                                                   \
-    return launch_fused_variant<W, B>(sm, n_q, st, blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks, batches, \
-                                      wptr, wunits, cptr, citem, ccoef, n_outputs, o);
-  BBC_FUSED(8, false) BBC_FUSED(12, false) BBC_FUSED(16, false)
-  BBC_FUSED(8, true) BBC_FUSED(12, true) BBC_FUSED(16, true)
+#define BBC_FUSED(W, S, B)                                                                                        \
+  if (warps == W && steps == S && bf16 == B)                                                                      \
+    return launch_fused_variant<W, S, B>(sm, n_q, st, blk, L, n_out, row_slot, n_slots, qlist, tasks, n_tasks,     \
+                                         batches, wptr, wunits, cptr, citem, ccoef, n_outputs, o);
+  BBC_FUSED(8, 1, false) BBC_FUSED(8, 2, false) BBC_FUSED(12, 1, false) BBC_FUSED(12, 2, false)
+  BBC_FUSED(16, 1, false)
+  BBC_FUSED(8, 1, true) BBC_FUSED(8, 2, true) BBC_FUSED(12, 1, true) BBC_FUSED(12, 2, true) BBC_FUSED(16, 1, true)
 #undef BBC_FUSED
   return cudaErrorInvalidValue;
 }

@@ -85,11 +85,14 @@ size_t contract_fused_smem(int n_slots, int n_tasks, bool bf16);
 // Launch configurations: warps per CTA in {8, 12, 16}.
 // bf16: blk holds bfloat16 (re, im) pairs (4 bytes per complex) instead of
 // complex64; the products multiply and accumulate in FP32 either way.
-bool fused_variant_supported(int warps);
+// Shapes: warps per CTA 8, 12 or 16; steps = open-index steps whose rows are
+// loaded before multiplying (1, or 2 with 8 or 12 warps).
+bool fused_variant_supported(int warps, int steps);
 cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* row_slot, int n_slots, const int* qlist,
                                   int n_q, const DevTask* tasks, int n_tasks, const WarpBatch* batches,
                                   const int* wptr, const int4* wunits, const int* cptr, const int* citem,
-                                  const double* ccoef, int n_ch, void* ct, int warps, bool bf16, cudaStream_t st);
+                                  const double* ccoef, int n_ch, void* ct, int warps, int steps, bool bf16,
+                                  cudaStream_t st);
 // dst[i] = (bf16(src[i].re), bf16(src[i].im)), round to nearest even, n complex64 values.
 cudaError_t launch_to_bf16(const void* src, void* dst, size_t n, cudaStream_t st);
 // Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z

@@ -93,10 +93,13 @@ def test_tuning_defaults_validation_and_autotune_state():
     c = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, [0, 1])
     f = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
     try:
-        assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18}
-        bbc.bbc_set_tuning(c, 2, 512, 12, 36)  # no workspace yet: host schedule only
-        assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 12, "fused_chunk": 36}
-        for bad in [(3, 256, 16, 18), (1, 512, 16, 18), (4, 256, 16, 18), (1, 256, 10, 18), (1, 256, 16, 20)]:
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18,
+                                         "fused_steps": 1}
+        bbc.bbc_set_tuning(c, 2, 512, 12, 36, 2)  # no workspace yet: host schedule only
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 12, "fused_chunk": 36,
+                                         "fused_steps": 2}
+        for bad in [(3, 256, 16, 18), (1, 512, 16, 18), (4, 256, 16, 18), (1, 256, 10, 18), (1, 256, 16, 20),
+                    (1, 256, 16, 18, 2), (1, 256, 8, 18, 3)]:
             with pytest.raises(bbc.BBCError) as e:
                 bbc.bbc_set_tuning(c, *bad)
             assert e.value.status == bbc.BBC_EINVAL, bad

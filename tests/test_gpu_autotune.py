@@ -31,7 +31,7 @@ def test_autotune_then_oracle(precision):
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
-    n_fused = 0 if precision == bbc.BBC_FP64 else 15
+    n_fused = 0 if precision == bbc.BBC_FP64 else 25  # (warps, steps) shapes x 5 chunks
     assert len(ms) == len(BUILD) + n_fused
     assert all(v > 0 for v in ms[len(BUILD):])
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
@@ -55,23 +55,26 @@ def test_every_configuration_matches(precision):
     want = orc.normalise(orc.correlator(L, F["u"][t], F["d"][t], F["s"][t], chans), chans, t, 0.3, 0.4)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     ref = None
-    fused = [(16, 18)] if precision == bbc.BBC_FP64 else [(w, k) for w in (8, 12, 16) for k in (0, 18, 36, 72, 144)]
+    shapes = [(8, 1), (8, 2), (12, 1), (12, 2), (16, 1)]
+    fused = [(16, 18, 1)] if precision == bbc.BBC_FP64 else [(w, k, st) for w, st in shapes
+                                                              for k in (0, 18, 36, 72, 144)]
     tried = 0
     for sites, threads in BUILD:
-        for warps, chunk in fused:
+        for warps, chunk, steps in fused:
             try:
                 cor.set_tuning({"build_sites": sites, "build_threads": threads, "fused_warps": warps,
-                                "fused_chunk": chunk})
+                                "fused_chunk": chunk, "fused_steps": steps})
             except bbc.BBCError:
                 assert precision == bbc.BBC_FP64 and sites == 4  # 365 KB of shared memory
                 continue
             out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
-            assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL), (sites, threads, warps, chunk)
+            assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL), (sites, threads, warps,
+                                                                                          chunk, steps)
             if precision == bbc.BBC_FP64:
                 # the build sums every row in the same order whatever the shape
                 if ref is None:
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == (3 if precision == bbc.BBC_FP64 else 60)
+    assert tried == (3 if precision == bbc.BBC_FP64 else 100)
     cor.close()
