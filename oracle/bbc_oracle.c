@@ -75,10 +75,11 @@ enum { B_P, B_N, B_SP, B_SM, B_S0, B_L, B_X0, B_XM, NBARYON };
 static baryon_t g_bar[NBARYON];
 
 /* channel = sink (B1, B2), source (B3, B4); 52 printed channels (Sec. 4,
- * Eqs. GeneralBB_NN ... GeneralBB_XX) followed by the four channels the paper
- * omits because they vanish in the isospin limit. */
+ * Eqs. GeneralBB_NN ... GeneralBB_XX), the four channels the paper omits
+ * because they vanish in the isospin limit, then eight other charge states
+ * (pp, nn, S+S+, S-S-, X0X0, X-X-, pS+, nS-, each onto itself). */
 typedef struct { int b[4]; const char* name; } channel_t;
-#define NCHAN_ALL 56
+#define NCHAN_ALL 64
 static channel_t g_chan[NCHAN_ALL];
 static int g_nchan = 0;
 
@@ -177,6 +178,15 @@ static void init_tables(void) {
   add_chan(B_S0, B_S0, B_S0, B_L);
   add_chan(B_S0, B_L, B_L, B_L);
   add_chan(B_S0, B_L, B_S0, B_S0);
+  /* other charge states (Sec. 4 footnote), ids 56..63 */
+  add_chan(B_P, B_P, B_P, B_P);
+  add_chan(B_N, B_N, B_N, B_N);
+  add_chan(B_SP, B_SP, B_SP, B_SP);
+  add_chan(B_SM, B_SM, B_SM, B_SM);
+  add_chan(B_X0, B_X0, B_X0, B_X0);
+  add_chan(B_XM, B_XM, B_XM, B_XM);
+  add_chan(B_P, B_SP, B_P, B_SP);
+  add_chan(B_N, B_SM, B_N, B_SM);
   g_init = 1;
 }
 
