@@ -36,7 +36,10 @@
  *    GeneralBB_NN .. GeneralBB_XX (row by row); ids 52..55 are the four
  *    channels the paper omits because they vanish in the isospin limit
  *    (Lambda Lambda <- Sigma0 Lambda, Sigma0 Sigma0 <- Sigma0 Lambda,
- *    Sigma0 Lambda <- Lambda Lambda, Sigma0 Lambda <- Sigma0 Sigma0).
+ *    Sigma0 Lambda <- Lambda Lambda, Sigma0 Lambda <- Sigma0 Sigma0);
+ *    ids 56..63 are other charge states (Sec. 4 footnote), each onto itself:
+ *    p p, n n, Sigma+ Sigma+, Sigma- Sigma-, Xi0 Xi0, Xi- Xi-, p Sigma+,
+ *    n Sigma-.
  */
 #ifndef BBC_H
 #define BBC_H

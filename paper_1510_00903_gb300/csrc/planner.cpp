@@ -59,7 +59,7 @@ const Op kOps[8] = {
 };
 
 // Channels of Sec. 4 (Eqs. GeneralBB_NN .. GeneralBB_XX) in printed order,
-// then the four omitted ones.
+// then the four omitted ones, then eight other charge states.
 std::vector<std::array<int, 4>> make_channels() {
   std::vector<std::array<int, 4>> c;
   c.push_back({OP_P, OP_N, OP_P, OP_N});
@@ -83,6 +83,16 @@ std::vector<std::array<int, 4>> make_channels() {
   c.push_back({OP_S0, OP_S0, OP_S0, OP_LA});
   c.push_back({OP_S0, OP_LA, OP_LA, OP_LA});
   c.push_back({OP_S0, OP_LA, OP_S0, OP_S0});
+  // other charge states (Sec. 4 footnote: the extension is the same
+  // construction with other operators): ids 56..63
+  c.push_back({OP_P, OP_P, OP_P, OP_P});
+  c.push_back({OP_N, OP_N, OP_N, OP_N});
+  c.push_back({OP_SP, OP_SP, OP_SP, OP_SP});
+  c.push_back({OP_SM, OP_SM, OP_SM, OP_SM});
+  c.push_back({OP_X0, OP_X0, OP_X0, OP_X0});
+  c.push_back({OP_XM, OP_XM, OP_XM, OP_XM});
+  c.push_back({OP_P, OP_SP, OP_P, OP_SP});
+  c.push_back({OP_N, OP_SM, OP_N, OP_SM});
   return c;
 }
 

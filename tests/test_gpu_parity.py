@@ -71,18 +71,20 @@ def test_pLambda_L4_T4_full_grid_fp64():
 
 
 def test_all_channels_L4_fp64_and_mixed():
-    """All 52 channels and the 4 omitted ones, full grid of one slice."""
+    """All 52 channels, the 4 omitted ones and the 8 other charge states (all
+    64 ids in one context), full grid of one slice."""
     L, T = 4, 4
     F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=1)
-    ch = list(range(56))
+    ch = list(range(64))
+    live = list(range(52)) + list(range(56, 64))
     want = oracle_slice(L, F, 3, ch)
     got = gpu_run(L, T, 0, ch, F["u"], F["s"], [3])[0]
-    e, scale = rel_err(got[:52], want[:52])
+    e, scale = rel_err(got[live], want[live])
     assert e.max() < FP64_TOL, e
     # omitted channels vanish (isospin limit) relative to the others
-    assert np.abs(got[52:]).max() < FP64_TOL * scale.max()
+    assert np.abs(got[52:56]).max() < FP64_TOL * scale.max()
     gm = gpu_run(L, T, 0, ch, F["u"], F["s"], [3], precision=bbc.BBC_MIXED_FP32)[0]
-    em, _ = rel_err(gm[:52], want[:52])
+    em, _ = rel_err(gm[live], want[live])
     assert em.max() < MIXED_TOL, em
 
 
