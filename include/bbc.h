@@ -59,7 +59,7 @@ typedef enum {
   BBC_ECUDA = -3,    /* a CUDA runtime call failed; message in bbc_last_error */
   BBC_ESTATE = -4,   /* call out of order (e.g. contract before build) */
   BBC_ETIMEOUT = -5, /* reserved: a bounded device wait gave up */
-  BBC_ENUMERIC = -6  /* non-finite propagator scale detected */
+  BBC_ENUMERIC = -6  /* NaN or infinity in an input or output (bbc_set_checks) */
 } bbc_status;
 
 typedef enum {
@@ -183,6 +183,39 @@ bbc_status bbc_stage_timing(bbc_ctx* ctx, double* ms, long long* launches);
 /* Number of kernel launches one bbc_contract call issues, and one
  * bbc_build_blocks call per slot-batch, and one bbc_load_propagator call. */
 bbc_status bbc_launch_counts(const bbc_ctx* ctx, int* per_load, int* per_build, int* per_contract);
+
+/* One item of a batch: a time slice of one context. */
+typedef struct {
+  bbc_ctx* ctx;            /* its lattice, precision, channels and workspace */
+  int t;                   /* time slice, 0 <= t < T of the context */
+  const void* S_light;     /* [L^3][12][12] propagators of dtype (as bbc_load_propagator) */
+  const void* S_strange;
+  int dtype;               /* BBC_C128 or BBC_C64 */
+  int on_device;           /* 1: device pointers; 0: host memory (pinned for asynchronous copies) */
+  void* out_dev;           /* [n_channels][L^3][16] complex128 (device) */
+  int normalised;
+} bbc_batch_item;
+
+/* Batch entry point (many slices, sources, gauge samples and uneven
+ * lattices in one call): runs items[0 .. n_items) in order on cuda_stream --
+ * for each, both propagators into slot 0 of its context, block build,
+ * contraction into out_dev -- with every launch and copy on cuda_stream (the
+ * contexts' own streams are not used; they are restored before returning).
+ * Capturing cuda_stream into a CUDA graph around this call records the whole
+ * batch as one graph.  Contexts may share a workspace (their work is ordered
+ * on the one stream).  Asynchronous unless a context has numeric checks on.
+ * Errors: the status of the first failing item, whose index goes to
+ * *failed_item (if not NULL); EINVAL for a null or empty batch. */
+bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_stream, int* failed_item);
+
+/* Numeric checks (off by default).  BBC_CHECK_INPUT: bbc_load_propagator
+ * returns BBC_ENUMERIC when the slice has a NaN or infinite entry.
+ * BBC_CHECK_OUTPUT: bbc_contract returns BBC_ENUMERIC when a correlator it
+ * wrote is NaN or infinite.  Each check synchronises the context stream (not
+ * inside a stream capture). */
+#define BBC_CHECK_INPUT 1
+#define BBC_CHECK_OUTPUT 2
+bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
 
 /* Launch configuration of the two kernels whose shape is tunable:
  *  build_sites, build_threads: sites per CTA and threads of the block build,

@@ -41,6 +41,12 @@ class bbc_tuning(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bbc_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("t", ctypes.c_int), ("S_light", ctypes.c_void_p),
+                ("S_strange", ctypes.c_void_p), ("dtype", ctypes.c_int), ("on_device", ctypes.c_int),
+                ("out_dev", ctypes.c_void_p), ("normalised", ctypes.c_int)]
+
+
 class bbc_lattice(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("t0", ctypes.c_int),
                 ("m_ud", ctypes.c_double), ("m_s", ctypes.c_double)]
@@ -66,6 +72,8 @@ def _load():
         "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "bbc_run_slice_static": ([P, I, P, P, I, P, I], I),
         "bbc_project": ([P, P, I, P, P], I),
+        "bbc_set_checks": ([P, I], I),
+        "bbc_batch_run": ([ctypes.POINTER(bbc_batch_item), I, P, ctypes.POINTER(I)], I),
         "bbc_get_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
         "bbc_set_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
         "bbc_autotune": ([P, I, ctypes.POINTER(bbc_tuning), ctypes.POINTER(ctypes.c_double), I,
@@ -186,6 +194,24 @@ def bbc_project(ctx, c_ptr: int, n_fields: int, r_ptr, ra1_ptr):
     _check(ctx, _lib.bbc_project(ctx, ctypes.c_void_p(c_ptr), n_fields,
                                  ctypes.c_void_p(r_ptr) if r_ptr else None,
                                  ctypes.c_void_p(ra1_ptr) if ra1_ptr else None))
+
+
+def bbc_batch_run(items, n_items: int, cuda_stream: int = 0):
+    """Run a ctypes array of bbc_batch_item in order on one stream."""
+    failed = ctypes.c_int(-1)
+    st = _lib.bbc_batch_run(items, n_items, ctypes.c_void_p(cuda_stream or None), ctypes.byref(failed))
+    if st != BBC_OK:
+        ctx = items[failed.value].ctx if 0 <= failed.value < n_items else None
+        msg = _lib.bbc_last_error(ctx)
+        raise BBCError(st, f"batch item {failed.value}: " + (msg.decode() if msg else ""))
+
+
+BBC_CHECK_INPUT, BBC_CHECK_OUTPUT = 1, 2
+
+
+def bbc_set_checks(ctx, flags: int):
+    """Enable numeric checks: BBC_CHECK_INPUT | BBC_CHECK_OUTPUT (ENUMERIC on NaN/inf)."""
+    _check(ctx, _lib.bbc_set_checks(ctx, int(flags)))
 
 
 def bbc_get_tuning(ctx) -> dict:
@@ -456,6 +482,20 @@ class LatticeBatch:
                 per.append(c)
             self.cors.append(per)
             self.outputs.append(torch.empty((len(channels), L ** 3, 16), dtype=torch.complex128, device=dev))
+        # one batch item per (lattice, source, slice), in that order
+        n = sum(len(per) * per[0].T for per in self.cors)
+        self._items = (bbc_batch_item * n)()
+        i = 0
+        for per, (Sl, Ss), out in zip(self.cors, self.inputs, self.outputs):
+            dt = {torch.complex128: BBC_C128, torch.complex64: BBC_C64}[Sl.dtype]
+            if Ss.dtype != Sl.dtype or not (Sl.is_cuda and Ss.is_cuda and Sl.is_contiguous() and Ss.is_contiguous()):
+                raise ValueError("inputs must be contiguous CUDA tensors of one dtype")
+            for c in per:
+                for t in range(c.T):
+                    self._items[i] = bbc_batch_item(c.ctx, t, Sl[t].data_ptr(), Ss[t].data_ptr(), dt, 1,
+                                                    out.data_ptr(), 1)
+                    i += 1
+        self._n_items = n
 
     def sites_channels(self) -> int:
         n_ch = self.outputs[0].shape[0]
@@ -467,13 +507,7 @@ class LatticeBatch:
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
-            for per, (Sl, Ss), out in zip(self.cors, self.inputs, self.outputs):
-                for c in per:
-                    for t in range(c.T):
-                        c.load(BBC_LIGHT, 0, t, Sl[t])
-                        c.load(BBC_STRANGE, 0, t, Ss[t])
-                        c.build(1)
-                        c.contract(0, out, True)
+            bbc_batch_run(self._items, self._n_items, self.stream.cuda_stream)
         if cur.cuda_stream != self.stream.cuda_stream:
             cur.wait_stream(self.stream)
 

@@ -33,7 +33,7 @@ constexpr int kMaxFusedWarps = 16;
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
-  size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, total;
+  size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, flag, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -69,6 +69,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.P = o; o = align256(o + (fp64 ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
+  L.flag = o; o = align256(o + sizeof(int));
   L.total = o;
   return L;
 }
@@ -379,6 +380,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_P = w + L.P;
   c->d_ct = w + L.ct;
   c->d_scale = (double*)(w + L.scale);
+  c->d_flag = (int*)(w + L.flag);
   const bbc::Plan& p = c->plan;
   std::vector<bbc::DevTask> tasks(p.tasks.size());
   for (size_t i = 0; i < p.tasks.size(); i++) {
@@ -464,6 +466,15 @@ bbc_status bbc_load_propagator(bbc_ctx* c, int flavour, int slot, int t, const v
   char* dst = c->d_prop + ((size_t)slot * 2 + flavour) * nc * cplx_bytes(c->prec);
   e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, c->prec == BBC_FP64, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
+  if (c->checks & BBC_CHECK_INPUT) {
+    unsigned long long bits = 0;
+    e = cudaMemcpyAsync(&bits, amax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "input check");
+    if (bits >= 0x7ff0000000000000ull)
+      return fail(c, BBC_ENUMERIC, std::string(flavour == BBC_LIGHT ? "light" : "strange") +
+                                       " propagator of slice " + std::to_string(t) + " has a NaN or infinite entry");
+  }
   if (c->slot_t[slot] != t) {
     c->slot_loaded[slot] = 0;
     c->slot_t[slot] = t;
@@ -560,6 +571,49 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
              : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
+  if (c->checks & BBC_CHECK_OUTPUT) {
+    int flag = 0;
+    e = cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess)
+      e = bbc::launch_nonfinite((const double*)out_dev, (long long)n_ch * c->V * 32, c->d_flag, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "output check");
+    if (flag) return fail(c, BBC_ENUMERIC, "correlators of slice " + std::to_string(t) + " have a NaN or infinite entry");
+  }
+  return BBC_OK;
+}
+
+bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_stream, int* failed_item) {
+  if (failed_item) *failed_item = -1;
+  if (!items || n_items < 1) return fail(nullptr, BBC_EINVAL, "empty batch");
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (int i = 0; i < n_items; i++) {
+    const bbc_batch_item& it = items[i];
+    bbc_ctx* c = it.ctx;
+    if (!c) {
+      if (failed_item) *failed_item = i;
+      return fail(nullptr, BBC_EINVAL, "batch item " + std::to_string(i) + " has no context");
+    }
+    const cudaStream_t own = c->stream;
+    c->stream = st;
+    bbc_status s = bbc_load_propagator(c, BBC_LIGHT, 0, it.t, it.S_light, it.dtype, it.on_device);
+    if (s == BBC_OK) s = bbc_load_propagator(c, BBC_STRANGE, 0, it.t, it.S_strange, it.dtype, it.on_device);
+    if (s == BBC_OK) s = bbc_build_blocks(c, 1);
+    if (s == BBC_OK) s = bbc_contract(c, 0, it.out_dev, it.normalised);
+    c->stream = own;
+    if (s != BBC_OK) {
+      if (failed_item) *failed_item = i;
+      return s;
+    }
+  }
+  return BBC_OK;
+}
+
+bbc_status bbc_set_checks(bbc_ctx* c, int flags) {
+  if (!c) return BBC_EINVAL;
+  if (flags & ~(BBC_CHECK_INPUT | BBC_CHECK_OUTPUT)) return fail(c, BBC_EINVAL, "unknown check flags");
+  c->checks = flags;
   return BBC_OK;
 }
 

@@ -62,6 +62,8 @@ struct bbc_ctx {
   char* d_P = nullptr;                   // [n_tasks*16][V] pair products of one slice
   char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators
   double* d_scale = nullptr;             // [kMaxChannels]
+  int* d_flag = nullptr;                 // non-finite output flag (bbc_set_checks)
+  int checks = 0;                        // BBC_CHECK_INPUT | BBC_CHECK_OUTPUT
   std::vector<int> slot_t;               // time slice of each slot (-1: none)
   std::vector<int> slot_loaded;          // bit 0: light, bit 1: strange
   std::vector<int> slot_built;

@@ -14,7 +14,8 @@ __global__ void k_absmax(const void* __restrict__ src, int dtype, long long n_re
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
     double x = dtype == 0 ? ((const double*)src)[i] : (double)((const float*)src)[i];
-    m = fmax(m, fabs(x));
+    const double a = fabs(x);
+    m = fmax(m, a == a ? a : (double)INFINITY);  // a NaN counts as infinite (fmax would drop it)
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -183,6 +184,22 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2*
   BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512)
 #undef BBC_BUILD
   return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ checks
+// *flag |= 1 if any of the n doubles is not finite.
+__global__ void k_nonfinite(const double* __restrict__ x, long long n, int* flag) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_nonfinite(const double* x, long long n, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  k_nonfinite<<<blocks, 256, 0, st>>>(x, n, flag);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ normalisation

@@ -48,9 +48,12 @@ cudaError_t launch_scales(const ScaleParams& p, const int* kexp, double* scale, 
 cudaError_t upload_twiddles();
 
 // |S| maximum of one propagator slice (V*144 complex, dtype 0 = c128, 1 = c64)
-// into *amax (bit pattern of a non-negative double; caller zeroes it first).
+// into *amax (bit pattern of a non-negative double; caller zeroes it first);
+// a NaN entry makes it +infinity.
 cudaError_t launch_absmax(const void* src, int dtype, long long n_complex,
                           unsigned long long* amax, cudaStream_t st);
+// *flag |= 1 when one of the n doubles at x is NaN or infinite.
+cudaError_t launch_nonfinite(const double* x, long long n, int* flag, cudaStream_t st);
 // dst = src * 2^-k with k = ilogb(max) + 1 (exact), k stored to *kexp.
 cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
                            const unsigned long long* amax, int* kexp, void* dst, bool fp64,

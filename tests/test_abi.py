@@ -133,3 +133,23 @@ def test_lower_components_plan_and_errors():
     with pytest.raises(bbc.BBCError) as e:
         bbc.bbc_create_components(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0], 2)
     assert e.value.status == bbc.BBC_EINVAL
+
+
+def test_batch_and_check_argument_errors():
+    """bbc_batch_run rejects an empty batch and names a bad item; unknown
+    check flags are EINVAL (no device work)."""
+    items = (bbc.bbc_batch_item * 2)()
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_batch_run(items, 0)
+    assert e.value.status == bbc.BBC_EINVAL
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_batch_run(items, 2)  # item 0 has no context
+    assert e.value.status == bbc.BBC_EINVAL and "item 0" in str(e.value)
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0])
+    try:
+        bbc.bbc_set_checks(c, bbc.BBC_CHECK_INPUT | bbc.BBC_CHECK_OUTPUT)
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_set_checks(c, 4)
+        assert e.value.status == bbc.BBC_EINVAL
+    finally:
+        bbc.bbc_destroy(c)

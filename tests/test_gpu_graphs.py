@@ -93,3 +93,26 @@ def test_run_streamed_overlapped_copies():
         err = np.abs(got[t] - want).reshape(len(chans), -1).max(axis=1) / scale
         assert err.max() < 2e-5, (t, err)
     cor.close()
+
+
+def test_numeric_checks():
+    """BBC_CHECK_INPUT flags a NaN propagator entry, BBC_CHECK_OUTPUT the NaN
+    correlators it produces; finite data passes both."""
+    L, T = 4, 2
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=71)
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=[0], device=dev)
+    bbc.bbc_set_checks(cor.ctx, bbc.BBC_CHECK_INPUT | bbc.BBC_CHECK_OUTPUT)
+    cor.run(Sl, Ss, range(T))  # finite: no error
+    bad = Sl.clone()
+    bad[1, 5, 3, 7] = complex(float("nan"), 0.0)
+    with pytest.raises(bbc.BBCError) as e:
+        cor.run(bad[1:2], Ss[1:2], [1])  # propagators of the listed slices, in order
+    assert e.value.status == bbc.BBC_ENUMERIC and "light" in str(e.value)
+    bbc.bbc_set_checks(cor.ctx, bbc.BBC_CHECK_OUTPUT)
+    with pytest.raises(bbc.BBCError) as e:
+        cor.run(bad[1:2], Ss[1:2], [1])
+    assert e.value.status == bbc.BBC_ENUMERIC and "correlators" in str(e.value)
+    torch.cuda.synchronize(dev)
+    cor.close()
