@@ -222,6 +222,79 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
   }
 }
 
+// x and y passes of the site-major layout data[o][site][n_inner] fused in one
+// kernel: a CTA takes one z plane of one outer index and TI consecutive inner
+// columns, stages the N x N x TI plane in shared memory (compute precision),
+// runs the x lines there, then the y lines, writing the result in place.
+// One HBM round trip for two passes.
+template <int N>
+__host__ __device__ constexpr int xy_tile() {
+  return N <= 16 ? 32 : (N == 24 ? 16 : (N == 32 ? 8 : 4));  // planes of <= 74 KB
+}
+
+template <typename S, typename R, int N, bool INV>
+__global__ void __launch_bounds__(256) k_fft_xy_site(cpx<S>* __restrict__ data, int n_inner) {
+  constexpr int TI = xy_tile<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* tile = reinterpret_cast<cpx<R>*>(smem_raw);  // [N * N][TI]
+  const int i0 = blockIdx.x * TI, z = blockIdx.y;
+  const long long o = blockIdx.z;
+  const long long V = (long long)N * N * N;
+  cpx<S>* plane = data + (o * V + (long long)z * N * N) * n_inner + i0;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < N * N * TI; idx += 256) {
+    const int site = idx / TI, i = idx - site * TI;
+    tile[idx] = i0 + i < n_inner ? cpx<R>(plane[(long long)site * n_inner + i]) : cpx<R>((R)0, (R)0);
+  }
+  __syncthreads();
+  for (int li = tid; li < N * TI; li += 256) {  // x lines: (y, i)
+    const int y = li / TI, i = li - y * TI;
+    cpx<R> v[N];
+    line_fft<R, R, N, INV>(tile + (y * N) * TI + i, TI, v);
+#pragma unroll
+    for (int k = 0; k < N; k++) tile[(y * N + k) * TI + i] = v[k];
+  }
+  __syncthreads();
+  for (int li = tid; li < N * TI; li += 256) {  // y lines: (x, i), straight to global memory
+    const int x = li / TI, i = li - x * TI;
+    cpx<R> v[N];
+    line_fft<R, R, N, INV>(tile + x * TI + i, N * TI, v);
+    if (i0 + i < n_inner) {
+#pragma unroll
+      for (int k = 0; k < N; k++) plane[(long long)(x + N * k) * n_inner + i] = cpx<S>(v[k]);
+    }
+  }
+}
+
+template <typename S, typename R>
+static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner, bool inv, cudaStream_t st) {
+#define BBC_XY_CASE(NN)                                                                                          \
+  case NN: {                                                                                                     \
+    constexpr int TI = xy_tile<NN>();                                                                            \
+    const size_t sm = sizeof(cpx<R>) * NN * NN * TI;                                                             \
+    dim3 grid((unsigned)((n_inner + TI - 1) / TI), NN, (unsigned)n_outer);                                      \
+    static int granted_f[64] = {0}, granted_i[64] = {0};                                                         \
+    cudaError_t e = inv ? ensure_smem(k_fft_xy_site<S, R, NN, true>, sm, granted_i)                              \
+                        : ensure_smem(k_fft_xy_site<S, R, NN, false>, sm, granted_f);                            \
+    if (e != cudaSuccess) return e;                                                                              \
+    if (inv) k_fft_xy_site<S, R, NN, true><<<grid, 256, sm, st>>>((cpx<S>*)data, n_inner);                       \
+    else k_fft_xy_site<S, R, NN, false><<<grid, 256, sm, st>>>((cpx<S>*)data, n_inner);                          \
+    break;                                                                                                       \
+  }
+  switch (L) {
+    BBC_XY_CASE(2)
+    BBC_XY_CASE(4)
+    BBC_XY_CASE(8)
+    BBC_XY_CASE(16)
+    BBC_XY_CASE(24)
+    BBC_XY_CASE(32)
+    BBC_XY_CASE(48)
+    default: return cudaErrorInvalidValue;
+  }
+#undef BBC_XY_CASE
+  return cudaGetLastError();
+}
+
 template <typename S, typename R, int MODE>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
                                 const double* scale, cudaStream_t st) {
@@ -274,22 +347,19 @@ cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int
 }
 
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st) {
-  for (int axis = 0; axis < 3; axis++) {
-    cudaError_t e = fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st)
-                         : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  // x and y fused (one HBM round trip), then z
+  cudaError_t e = fp64 ? fft_xy_site<double, double>(blk, L, n_slots, n_rows, false, st)
+                       : fft_xy_site<float, float>(blk, L, n_slots, n_rows, false, st);
+  if (e != cudaSuccess) return e;
+  return fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, 2, false, nullptr, st)
+              : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, 2, false, nullptr, st);
 }
 
 cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
                                     cudaStream_t st) {
-  cudaError_t e;
-  for (int axis = 0; axis < 2; axis++) {
-    e = fp64_compute ? fft_dispatch<double, double, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st)
-                     : fft_dispatch<double, float, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = fp64_compute ? fft_xy_site<double, double>(ct, L, 1, n_ch * 16, true, st)
+                               : fft_xy_site<double, float>(ct, L, 1, n_ch * 16, true, st);
+  if (e != cudaSuccess) return e;
   return fp64_compute ? fft_dispatch<double, double, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st)
                       : fft_dispatch<double, float, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
 }
