@@ -207,16 +207,18 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
 #pragma unroll
     for (int k = 0; k < N; k++) p[(long long)k * stride * n_inner] = cpx<S>(v[k]);
   } else if (MODE == FFT_SITE2OUT) {
-    // inner = channel * 16 + spin; out[ch][r][16]
-    const R f = (R)scale[inner >> 4];
+    // inner = channel * 16 + spin; out[ch][r][16].  The scale (1/V, the
+    // undone propagator rescaling, the mass factor) may lie far outside the
+    // compute precision's range: it multiplies in the storage precision.
+    const S f = (S)scale[inner >> 4];
     cpx<S>* p = out + ((long long)(inner >> 4) * V + base) * 16 + (inner & 15);
 #pragma unroll
-    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<S>(cpx<R>(v[k].re * f, v[k].im * f));
+    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<S>((S)v[k].re * f, (S)v[k].im * f);
   } else {
-    const R f = (R)scale[o];
+    const S f = (S)scale[o];
 #pragma unroll
     for (int k = 0; k < N; k++) {
-      cpx<S> w(v[k].re * f, v[k].im * f);
+      cpx<S> w((S)v[k].re * f, (S)v[k].im * f);
       out[(o * V + base + (long long)k * stride) * 16 + inner] = w;
     }
   }
