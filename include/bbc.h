@@ -67,9 +67,13 @@ typedef enum {
   BBC_MIXED_FP32 = 1, /* blocks, FFTs and block-pair products in FP32 after an exact
                          per-slice power-of-two rescaling of each propagator; the signed
                          sum over Wick diagrams and the normalisation in FP64 */
-  BBC_MIXED_BF16 = 2  /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
+  BBC_MIXED_BF16 = 2, /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
                          to bfloat16 (round to nearest even) before the block-pair
                          products, which multiply and accumulate in FP32 */
+  BBC_DF64 = 3        /* as BBC_FP64, with the block-pair products in double-float
+                         arithmetic (unevaluated sums of two FP32 values, 48-bit
+                         significand) on the FP32 pipes: FP64-accurate results where
+                         GB300's FP64 pipe would bound the contraction */
 } bbc_precision;
 
 typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
@@ -294,7 +298,7 @@ bbc_status bbc_project(bbc_ctx* ctx, const void* C_dev, int n_fields, void* R_de
  * [n_channels][L^3][16] complex128, written fully.  Everything runs
  * asynchronously on the context stream.
  *
- * Precisions BBC_FP64 and BBC_MIXED_FP32 (EINVAL for BBC_MIXED_BF16).
+ * Precisions BBC_FP64 and BBC_MIXED_FP32 (EINVAL for the others).
  * Size limit: the plan tables and one slice of blocks, pair products and
  * q-space correlators must fit in the array -- L <= 4 with all 52 channels;
  * larger lattices or channel lists return BBC_EINVAL with a message.

@@ -25,8 +25,10 @@ namespace {
 std::string g_create_error;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-size_t cplx_bytes(int prec) { return prec == BBC_FP64 ? 16 : 8; }
-bool fused_path(int prec) { return prec != BBC_FP64; }  // FP32 or bfloat16 products
+// FP64 storage (plain FP64, and FP64 with double-float products) or FP32
+bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
+size_t cplx_bytes(int prec) { return fp64_storage(prec) ? 16 : 8; }
+bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 products
 
 constexpr int kMaxFusedWarps = 16;
 
@@ -64,7 +66,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
   L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
   L.blk16 = o; o = align256(o + (c->prec == BBC_MIXED_BF16 ? (size_t)slots * V * p.n_out * 4 : 0));
-  const bool fp64 = c->prec == BBC_FP64;  // the FP32 path keeps q-major blocks and no product buffer
+  const bool fp64 = fp64_storage(c->prec);  // the FP32 path keeps q-major blocks and no product buffer
   L.blkf = o; o = align256(o + (fp64 ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
   L.P = o; o = align256(o + (fp64 ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
@@ -177,7 +179,7 @@ std::map<std::pair<std::pair<int, int>, std::vector<int>>, bbc_tuning> g_tuned;
 
 bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
-  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, c->prec == BBC_FP64) > bbc::kMaxSmemPerBlock)
+  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec)) > bbc::kMaxSmemPerBlock)
     return false;
   if (fused_path(c->prec)) {
     if (!bbc::fused_variant_supported(t.fused_warps, t.fused_steps)) return false;
@@ -245,7 +247,7 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
   *ctx = nullptr;
   if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 24, 32, 48)");
   if (lat->T < 1 || lat->t0 < 0 || lat->t0 >= lat->T) return fail(nullptr, BBC_EINVAL, "bad T or t0");
-  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16)
+  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16 && prec != BBC_DF64)
     return fail(nullptr, BBC_EINVAL, "bad precision");
   if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");
   if (components != BBC_UPPER && components != BBC_LOWER) return fail(nullptr, BBC_EINVAL, "bad spin components");
@@ -464,7 +466,7 @@ bbc_status bbc_load_propagator(bbc_ctx* c, int flavour, int slot, int t, const v
   e = bbc::launch_absmax(src, dtype, (long long)nc, amax, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "absmax kernel");
   char* dst = c->d_prop + ((size_t)slot * 2 + flavour) * nc * cplx_bytes(c->prec);
-  e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, c->prec == BBC_FP64, c->stream);
+  e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, fp64_storage(c->prec), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   if (c->checks & BBC_CHECK_INPUT) {
     unsigned long long bits = 0;
@@ -490,7 +492,7 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   if (n_slots < 1 || n_slots > c->slots) return fail(c, BBC_EINVAL, "bad slot count");
   for (int s = 0; s < n_slots; s++)
     if (c->slot_loaded[s] != 3) return fail(c, BBC_ESTATE, "slot " + std::to_string(s) + " lacks a propagator");
-  const bool fp64 = c->prec == BBC_FP64;
+  const bool fp64 = fp64_storage(c->prec);
   const bbc::Plan& p = c->plan;
   cudaError_t e;
   {
@@ -502,8 +504,9 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   {
     StageScope scope(c, BBC_STAGE_FFT_FWD);
     // FP64: field-major copy for the lanes-over-q products; FP32: in place, q-major
-    e = fp64 ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
-             : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
+    e = c->prec == BBC_DF64 ? bbc::launch_fft_forward_df(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, c->stream)
+        : fp64              ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
+                            : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
     if (c->prec == BBC_MIXED_BF16) {
       e = bbc::launch_to_bf16(c->d_blk, c->d_blk16, (size_t)n_slots * c->V * p.n_out, c->stream);
@@ -520,7 +523,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   if (slot < 0 || slot >= c->slots) return fail(c, BBC_EINVAL, "bad slot");
   if (!c->slot_built[slot]) return fail(c, BBC_ESTATE, "blocks of this slot are not built");
   if (!out_dev || (((uintptr_t)out_dev) & 15)) return fail(c, BBC_EINVAL, "output must be a 16-byte aligned device pointer");
-  const bool fp64 = c->prec == BBC_FP64;
+  const bool fp64 = fp64_storage(c->prec);
   const bbc::Plan& p = c->plan;
   const int n_ch = (int)p.channels.size();
   cudaError_t e;
@@ -528,8 +531,11 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
     {
       StageScope scope(c, BBC_STAGE_CONTRACT);
-      e = bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
-                                    (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
+      e = c->prec == BBC_DF64
+              ? bbc::launch_pair_products_df(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                             (int)c->group_ptr.size() - 1, c->d_P, c->stream)
+              : bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                          (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "pair products");
     }
     {
@@ -645,7 +651,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
   if (c->slot_loaded[0] != 3) return fail(c, BBC_ESTATE, "slot 0 needs both propagators loaded");
   const bbc::Plan& p = c->plan;
-  const bool fp64 = c->prec == BBC_FP64;
+  const bool fp64 = fp64_storage(c->prec);
   const bbc::DevGroups g = groups_of(p);
   int n = 0;
   auto record = [&](double v) {

@@ -31,6 +31,57 @@ __device__ __forceinline__ void cmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
   acc.im = fma(a.im, b.re, acc.im);
 }
 
+// ---------------------------------------------------------- double-float
+// A real as an unevaluated sum hi + lo of two FP32 values (48-bit
+// significand), for FP64-accurate arithmetic on the FP32 pipes.  Built from
+// error-free transformations: Knuth's TwoSum (the exact rounding error of a
+// sum) and the FMA-based TwoProduct (the exact error of a product, Ogita,
+// Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)).  The _rn intrinsics keep
+// the compiler from contracting the products and sums these rely on.
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Accumulator s + e, normalised only now and then (|e| stays far below |s|
+// for the short sums it is used for).
+struct df64acc {
+  float s, e;
+};
+
+// acc += x * y (x, y double-float): TwoProduct of the high parts, the cross
+// terms into the error word, TwoSum of the product into the accumulator.
+__device__ __forceinline__ void df_mac(df64acc& acc, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -p);
+  e = __fmaf_rn(xh, yl, e);
+  e = __fmaf_rn(xl, yh, e);
+  float s, t;
+  two_sum(acc.s, p, s, t);
+  acc.s = s;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ void df_renorm(df64acc& acc) {
+  float s, e;
+  two_sum(acc.s, acc.e, s, e);
+  acc.s = s;
+  acc.e = e;
+}
+
+__device__ __forceinline__ double df_to_double(const df64acc& a) { return (double)a.s + (double)a.e; }
+
+// Split a double into hi (round to nearest FP32) and lo (the rounded rest).
+__device__ __forceinline__ df64 df_split(double x) {
+  const float h = __double2float_rn(x);
+  return df64{h, __double2float_rn(x - (double)h)};
+}
+
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
 // than was granted before (per device), so that launches captured into a
 // CUDA graph after a first eager run issue no attribute call.

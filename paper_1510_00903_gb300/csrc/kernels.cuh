@@ -72,6 +72,10 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2*
 // then the y and z passes in place (exp(-i q.x), unnormalised).
 cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
                                cudaStream_t st);
+// FP64 forward transform as above whose last pass stores every value split
+// into a double-float (re.hi, re.lo, im.hi, im.lo), in place.
+cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows,
+                                  cudaStream_t st);
 // Forward 3-D FFT in place on site-major blocks blk[slots][V][n_rows] (lanes
 // over the contiguous row index); output is q-major.
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st);
@@ -107,6 +111,10 @@ cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const doubl
 // P[n_tasks*16][V] ...
 cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
                                  const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st);
+// Double-float variant: blk_field holds (re.hi, re.lo, im.hi, im.lo) FP32
+// quadruples per complex value; P is complex128.
+cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
+                                    const int* group_task, int n_groups, void* P, cudaStream_t st);
 // ... then the signed FP64 sums over Wick diagrams into ct[n_ch*16][V] (complex128).
 cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
                              void* ct, bool fp64, cudaStream_t st);

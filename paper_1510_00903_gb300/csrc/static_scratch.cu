@@ -80,7 +80,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   if (!c) return BBC_EINVAL;
   if (t < 0 || t >= c->lat.T) return fail(c, BBC_EINVAL, "bad time slice");
   if (dtype != BBC_C128 && dtype != BBC_C64) return fail(c, BBC_EINVAL, "bad dtype");
-  if (c->prec == BBC_MIXED_BF16) return fail(c, BBC_EINVAL, "the static entry point runs BBC_FP64 and BBC_MIXED_FP32");
+  if (c->prec != BBC_FP64 && c->prec != BBC_MIXED_FP32)
+    return fail(c, BBC_EINVAL, "the static entry point runs BBC_FP64 and BBC_MIXED_FP32");
   if (!S_light || !S_strange || !out_dev || (((uintptr_t)S_light | (uintptr_t)S_strange | (uintptr_t)out_dev) & 15))
     return fail(c, BBC_EINVAL, "propagators and output must be 16-byte aligned device pointers");
   const StaticLayout L = static_layout(c);
