@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--error-report", action="store_true",
                     help="per-channel error of the mixed path against the FP64 path (L=32, T=64, t=32), "
                          "the FP64 path checked against the oracle at sampled points")
-    ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16"], default=None,
+    ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16", "df64"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
     ap.add_argument("--tuning", default=None,
                     help="launch configuration for --single-slice: sites,threads,warps,chunk[,steps] (as bbc_set_tuning)")
@@ -224,7 +224,8 @@ def run_ours(args, torch, rank, world, local):
     if args.single_slice:
         t = T // 2
         F1 = synth.flavour_set(L, T, 0, M_UD, M_S, seed=1000, times=[t])
-        prec = {"fp64": bbc.BBC_FP64, "mixed": bbc.BBC_MIXED_FP32, "bf16": bbc.BBC_MIXED_BF16}[args.single_slice]
+        prec = {"fp64": bbc.BBC_FP64, "mixed": bbc.BBC_MIXED_FP32, "bf16": bbc.BBC_MIXED_BF16,
+                "df64": bbc.BBC_DF64}[args.single_slice]
         cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
         if args.tuning:
             v = [int(x) for x in args.tuning.split(",")]
