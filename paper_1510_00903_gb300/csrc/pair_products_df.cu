@@ -48,7 +48,7 @@ __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, l
   for (int i = 0; i < NA * NB; i++) P[(long long)i * V] = cpx<double>(df_to_double(re[i]), df_to_double(im[i]));
 }
 
-__global__ void __launch_bounds__(32 * kPairWarpsDf)
+__global__ void __launch_bounds__(32 * kPairWarpsDf, 4)
 k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restrict__ tasks,
                    const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
                    cpx<double>* __restrict__ P) {
