@@ -31,12 +31,20 @@ __device__ __forceinline__ void tile_products_df(const float4* __restrict__ F, l
 #pragma unroll
   for (int i = 0; i < TA * TB; i++) { re[i] = df64acc{0.f, 0.f}; im[i] = df64acc{0.f, 0.f}; }
   int i1 = 0, i2 = 0, oA = 0, oB = 0;
+  float4 a[TA], b[TB];  // (re.hi, re.lo, im.hi, im.lo) of step k; loads of step k + 1 are issued before its products
+#pragma unroll
+  for (int r = 0; r < TA; r++) a[r] = F[(long long)offA[r] * V + q];
+#pragma unroll
+  for (int r = 0; r < TB; r++) b[r] = F[(long long)offB[r] * V + nq];
   for (int k = 0; k < K; k++) {
-    float4 a[TA], b[TB];  // (re.hi, re.lo, im.hi, im.lo)
+    if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
+    else { oA += sA2; oB += sB2; }
+    float4 an[TA], bn[TB];
+    const bool more = k + 1 < K;
 #pragma unroll
-    for (int r = 0; r < TA; r++) a[r] = F[(long long)(offA[r] + oA) * V + q];
+    for (int r = 0; r < TA; r++) an[r] = more ? F[(long long)(offA[r] + oA) * V + q] : a[r];
 #pragma unroll
-    for (int r = 0; r < TB; r++) b[r] = F[(long long)(offB[r] + oB) * V + nq];
+    for (int r = 0; r < TB; r++) bn[r] = more ? F[(long long)(offB[r] + oB) * V + nq] : b[r];
 #pragma unroll
     for (int ra = 0; ra < TA; ra++)
 #pragma unroll
@@ -51,8 +59,10 @@ __device__ __forceinline__ void tile_products_df(const float4* __restrict__ F, l
 #pragma unroll
       for (int i = 0; i < TA * TB; i++) { df_renorm(re[i]); df_renorm(im[i]); }
     }
-    if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
-    else { oA += sA2; oB += sB2; }
+#pragma unroll
+    for (int r = 0; r < TA; r++) a[r] = an[r];
+#pragma unroll
+    for (int r = 0; r < TB; r++) b[r] = bn[r];
   }
 #pragma unroll
   for (int ra = 0; ra < TA; ra++)
@@ -62,7 +72,7 @@ __device__ __forceinline__ void tile_products_df(const float4* __restrict__ F, l
           cpx<double>(df_to_double(re[ra * TB + rb]), df_to_double(im[ra * TB + rb]));
 }
 
-__global__ void __launch_bounds__(32 * kPairWarpsDf, 5)
+__global__ void __launch_bounds__(32 * kPairWarpsDf, 4)
 k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restrict__ tasks,
                    const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
                    cpx<double>* __restrict__ P) {
