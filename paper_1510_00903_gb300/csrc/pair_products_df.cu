@@ -11,45 +11,27 @@ constexpr int kPairWarpsDf = 4;
 // im.lo) FP32 quadruples (written by the last forward FFT pass), every
 // complex product as four double-float multiply-adds on the FP32 pipes,
 // accumulators renormalised every 16 open-index steps, the products stored
-// as complex128 for the FP64 Wick sums.  Each task's 16 products run as two
-// register tiles of 8.
-// One register tile of a task: rows ra0 .. ra0+TA-1 of A against rows
-// rb0 .. rb0+TB-1 of B (the task's full nA x nB products are split into two
-// tiles, so a lane holds half the accumulators and more warps fit on an SM).
-template <int TA, int TB>
-__device__ __forceinline__ void tile_products_df(const float4* __restrict__ F, long long V, int q, int nq,
-                                                 const DevTask& t, int nB, int ra0, int rb0,
-                                                 cpx<double>* __restrict__ P) {
+// as complex128 for the FP64 Wick sums.
+template <int NA, int NB>
+__device__ __forceinline__ void task_products_df(const float4* __restrict__ F, long long V, int q, int nq,
+                                                 const DevTask& t, cpx<double>* __restrict__ P) {
   const int n2 = t.n2, K = t.n1 * n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
-  int offA[TA], offB[TB];
+  df64acc re[NA * NB], im[NA * NB];
 #pragma unroll
-  for (int r = 0; r < TA; r++) offA[r] = t.offA[ra0 + r];
-#pragma unroll
-  for (int r = 0; r < TB; r++) offB[r] = t.offB[rb0 + r];
-  df64acc re[TA * TB], im[TA * TB];
-#pragma unroll
-  for (int i = 0; i < TA * TB; i++) { re[i] = df64acc{0.f, 0.f}; im[i] = df64acc{0.f, 0.f}; }
+  for (int i = 0; i < NA * NB; i++) { re[i] = df64acc{0.f, 0.f}; im[i] = df64acc{0.f, 0.f}; }
   int i1 = 0, i2 = 0, oA = 0, oB = 0;
-  float4 a[TA], b[TB];  // (re.hi, re.lo, im.hi, im.lo) of step k; loads of step k + 1 are issued before its products
-#pragma unroll
-  for (int r = 0; r < TA; r++) a[r] = F[(long long)offA[r] * V + q];
-#pragma unroll
-  for (int r = 0; r < TB; r++) b[r] = F[(long long)offB[r] * V + nq];
   for (int k = 0; k < K; k++) {
-    if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
-    else { oA += sA2; oB += sB2; }
-    float4 an[TA], bn[TB];
-    const bool more = k + 1 < K;
+    float4 a[NA], b[NB];  // (re.hi, re.lo, im.hi, im.lo)
 #pragma unroll
-    for (int r = 0; r < TA; r++) an[r] = more ? F[(long long)(offA[r] + oA) * V + q] : a[r];
+    for (int r = 0; r < NA; r++) a[r] = F[(long long)(t.offA[r] + oA) * V + q];
 #pragma unroll
-    for (int r = 0; r < TB; r++) bn[r] = more ? F[(long long)(offB[r] + oB) * V + nq] : b[r];
+    for (int r = 0; r < NB; r++) b[r] = F[(long long)(t.offB[r] + oB) * V + nq];
 #pragma unroll
-    for (int ra = 0; ra < TA; ra++)
+    for (int ra = 0; ra < NA; ra++)
 #pragma unroll
-      for (int rb = 0; rb < TB; rb++) {
-        const int i = ra * TB + rb;
+      for (int rb = 0; rb < NB; rb++) {
+        const int i = ra * NB + rb;
         df_mac(re[i], a[ra].x, a[ra].y, b[rb].x, b[rb].y);    // + Re a Re b
         df_mac(re[i], -a[ra].z, -a[ra].w, b[rb].z, b[rb].w);  // - Im a Im b
         df_mac(im[i], a[ra].x, a[ra].y, b[rb].z, b[rb].w);    // + Re a Im b
@@ -57,19 +39,13 @@ __device__ __forceinline__ void tile_products_df(const float4* __restrict__ F, l
       }
     if ((k & 15) == 15) {
 #pragma unroll
-      for (int i = 0; i < TA * TB; i++) { df_renorm(re[i]); df_renorm(im[i]); }
+      for (int i = 0; i < NA * NB; i++) { df_renorm(re[i]); df_renorm(im[i]); }
     }
-#pragma unroll
-    for (int r = 0; r < TA; r++) a[r] = an[r];
-#pragma unroll
-    for (int r = 0; r < TB; r++) b[r] = bn[r];
+    if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
+    else { oA += sA2; oB += sB2; }
   }
 #pragma unroll
-  for (int ra = 0; ra < TA; ra++)
-#pragma unroll
-    for (int rb = 0; rb < TB; rb++)
-      P[(long long)((ra0 + ra) * nB + rb0 + rb) * V] =
-          cpx<double>(df_to_double(re[ra * TB + rb]), df_to_double(im[ra * TB + rb]));
+  for (int i = 0; i < NA * NB; i++) P[(long long)i * V] = cpx<double>(df_to_double(re[i]), df_to_double(im[i]));
 }
 
 __global__ void __launch_bounds__(32 * kPairWarpsDf, 4)
@@ -89,16 +65,9 @@ k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restric
     const DevTask t = tasks[ti];
     cpx<double>* p = P + (long long)ti * 16 * V + q;
     const int nA = t.nAnB & 0xff;
-    if (nA == 4) {         // 4 x 4 as two 4 x 2 tiles
-      tile_products_df<4, 2>(F, V, q, nq, t, 4, 0, 0, p);
-      tile_products_df<4, 2>(F, V, q, nq, t, 4, 0, 2, p);
-    } else if (nA == 2) {  // 2 x 8 as two 2 x 4 tiles
-      tile_products_df<2, 4>(F, V, q, nq, t, 8, 0, 0, p);
-      tile_products_df<2, 4>(F, V, q, nq, t, 8, 0, 4, p);
-    } else {               // 8 x 2 as two 4 x 2 tiles
-      tile_products_df<4, 2>(F, V, q, nq, t, 2, 0, 0, p);
-      tile_products_df<4, 2>(F, V, q, nq, t, 2, 4, 0, p);
-    }
+    if (nA == 4) task_products_df<4, 4>(F, V, q, nq, t, p);
+    else if (nA == 2) task_products_df<2, 8>(F, V, q, nq, t, p);
+    else task_products_df<8, 2>(F, V, q, nq, t, p);
   }
 }
 
