@@ -29,6 +29,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
 size_t cplx_bytes(int prec) { return fp64_storage(prec) ? 16 : 8; }
 bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 products
+int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP64 ? bbc::RK_F64 : bbc::RK_F32); }
 
 constexpr int kMaxFusedWarps = 16;
 
@@ -466,7 +467,7 @@ bbc_status bbc_load_propagator(bbc_ctx* c, int flavour, int slot, int t, const v
   e = bbc::launch_absmax(src, dtype, (long long)nc, amax, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "absmax kernel");
   char* dst = c->d_prop + ((size_t)slot * 2 + flavour) * nc * cplx_bytes(c->prec);
-  e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, fp64_storage(c->prec), c->stream);
+  e = bbc::launch_convert(src, dtype, (long long)nc, amax, kexp, dst, real_kind(c->prec), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   if (c->checks & BBC_CHECK_INPUT) {
     unsigned long long bits = 0;
@@ -498,7 +499,8 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   {
     StageScope scope(c, BBC_STAGE_BUILD);
     e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, groups_of(p),
-                                c->d_blk, p.n_out, fp64, c->stream, c->tune.build_sites, c->tune.build_threads);
+                                c->d_blk, p.n_out, real_kind(c->prec), c->stream, c->tune.build_sites,
+                                c->tune.build_threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
   {
@@ -668,7 +670,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     if (!tuning_valid(c, cand)) { record(-1.0); continue; }
     const double v = time_launches(c, reps, [&] {
       return bbc::launch_block_build(c->d_prop, c->V, 1, c->d_ell_chunk, c->d_ell, c->d_zneed, g, c->d_blk,
-                                     p.n_out, fp64, c->stream, bc[0], bc[1]);
+                                     p.n_out, real_kind(c->prec), c->stream, bc[0], bc[1]);
     });
     record(v);
     if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: block build");

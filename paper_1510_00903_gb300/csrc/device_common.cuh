@@ -76,10 +76,62 @@ __device__ __forceinline__ void df_renorm(df64acc& acc) {
 
 __device__ __forceinline__ double df_to_double(const df64acc& a) { return (double)a.s + (double)a.e; }
 
-// Split a double into hi (round to nearest FP32) and lo (the rounded rest).
-__device__ __forceinline__ df64 df_split(double x) {
-  const float h = __double2float_rn(x);
-  return df64{h, __double2float_rn(x - (double)h)};
+// Double-float real with arithmetic operators, for kernels templated on the
+// real type (block build, FFT).  Addition is the cheap variant (TwoSum of the
+// high words, the low words added, one renormalisation), whose error is
+// bounded by about 2^-44 (|a| + |b|): an absolute error at the scale of the
+// operands, which is what the correlator tolerance measures.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // needs |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+struct dfr {
+  float hi, lo;
+  __host__ __device__ dfr() {}
+  __host__ __device__ constexpr dfr(float h, float l) : hi(h), lo(l) {}
+  // split of a double (constant-folded for literals; FP64 instructions otherwise)
+  __host__ __device__ constexpr explicit dfr(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr dfr(int x) : hi((float)x), lo(0.f) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dfr operator-(dfr a) { return dfr(-a.hi, -a.lo); }
+__device__ __forceinline__ dfr operator+(dfr a, dfr b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  float h, l;
+  fast_two_sum(s, e, h, l);
+  return dfr(h, l);
+}
+__device__ __forceinline__ dfr operator-(dfr a, dfr b) { return a + (-b); }
+__device__ __forceinline__ dfr operator*(dfr a, dfr b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float h, l;
+  fast_two_sum(p, e, h, l);
+  return dfr(h, l);
+}
+__device__ __forceinline__ dfr& operator+=(dfr& a, dfr b) { return a = a + b; }
+// Multiply-add overloads in this namespace (the double-float one would
+// otherwise hide the floating-point ones from unqualified calls).
+__device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+// a * b + c: the product's two words folded into the sum before one renormalisation
+__device__ __forceinline__ dfr fma(dfr a, dfr b, dfr c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float s, t;
+  two_sum(c.hi, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  float h, l;
+  fast_two_sum(s, t, h, l);
+  return dfr(h, l);
 }
 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more

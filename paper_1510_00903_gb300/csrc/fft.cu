@@ -11,6 +11,7 @@ namespace bbc {
 constexpr int kTw = 96;  // common multiple of every supported transform length
 __constant__ double c_tw64[kTw][2];
 __constant__ float c_tw32[kTw][2];
+__constant__ float c_twdf[kTw][4];  // double-float (re.hi, re.lo, im.hi, im.lo)
 
 cudaError_t upload_twiddles() {
   double h64[kTw][2];
@@ -22,7 +23,18 @@ cudaError_t upload_twiddles() {
     h32[k][0] = (float)cosl(a);
     h32[k][1] = (float)-sinl(a);
   }
+  float hdf[kTw][4];
+  for (int k = 0; k < kTw; k++) {
+    long double a = 2.0L * 3.14159265358979323846264338327950288L * k / kTw;
+    const long double c = cosl(a), sn = -sinl(a);
+    hdf[k][0] = (float)c;
+    hdf[k][1] = (float)(c - (long double)hdf[k][0]);
+    hdf[k][2] = (float)sn;
+    hdf[k][3] = (float)(sn - (long double)hdf[k][2]);
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_tw64, h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_twdf, hdf, sizeof(hdf));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_tw32, h32, sizeof(h32));
 }
@@ -33,6 +45,10 @@ template <>
 __device__ __forceinline__ cpx<double> twiddle<double>(int k) { return cpx<double>(c_tw64[k][0], c_tw64[k][1]); }
 template <>
 __device__ __forceinline__ cpx<float> twiddle<float>(int k) { return cpx<float>(c_tw32[k][0], c_tw32[k][1]); }
+template <>
+__device__ __forceinline__ cpx<dfr> twiddle<dfr>(int k) {
+  return cpx<dfr>(dfr(c_twdf[k][0], c_twdf[k][1]), dfr(c_twdf[k][2], c_twdf[k][3]));
+}
 
 __host__ __device__ constexpr int bitrev(int k, int n) {
   int r = 0;
@@ -155,9 +171,7 @@ __device__ __forceinline__ void line_base(int N, int axis, int line, int& base, 
 // (the last inverse pass writes the output layout and normalises it).
 // Mode SITE (any axis, in place): data[o][site][n_inner], lanes over inner.
 // Mode SITE2OUT (z axis): in[site][n_ch*16] -> out[ch][r][16] times scale[ch].
-// Mode FIELD2DF (any axis, in place, S = R = double): as FIELD, storing each
-// result split into a double-float (re.hi, re.lo, im.hi, im.lo).
-enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4, FFT_FIELD2DF = 5 };
+enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4 };
 
 template <typename S, typename R, int N, bool INV, int MODE>
 __global__ void __launch_bounds__(256)
@@ -174,7 +188,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
     const long long rest = gid / n_inner;
     line = (int)(rest % lines);
     o = rest / lines;
-  } else if (MODE == FFT_FIELD || MODE == FFT_FIELD2DF) {
+  } else if (MODE == FFT_FIELD) {
     if (gid >= n_outer * lines) return;
     line = (int)(gid % lines);
     o = gid / lines;
@@ -191,7 +205,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
   cpx<R> v[N];
   if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
     line_fft<S, R, N, INV>(in + (o * V + base) * n_inner + inner, (long long)stride * n_inner, v);
-  } else if (MODE == FFT_FIELD || MODE == FFT_FIELD2DF) {
+  } else if (MODE == FFT_FIELD) {
     line_fft<S, R, N, INV>(in + o * V + base, stride, v);
   } else {
     line_fft<S, R, N, INV>(in + (o * 16 + inner) * V + base, stride, v);
@@ -204,13 +218,6 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
     cpx<S>* p = out + o * V + base;
 #pragma unroll
     for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
-  } else if (MODE == FFT_FIELD2DF) {
-    float4* p = reinterpret_cast<float4*>(out + o * V + base);
-#pragma unroll
-    for (int k = 0; k < N; k++) {
-      const df64 re = df_split((double)v[k].re), im = df_split((double)v[k].im);
-      p[k * stride] = make_float4(re.hi, re.lo, im.hi, im.lo);
-    }
   } else if (MODE == FFT_SITE) {
     cpx<S>* p = out + (o * V + base) * n_inner + inner;
 #pragma unroll
@@ -310,7 +317,7 @@ template <typename S, typename R, int MODE>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
                                 const double* scale, cudaStream_t st) {
   long long per = (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) ? n_inner
-                  : ((MODE == FFT_FIELD || MODE == FFT_FIELD2DF) ? 1 : 16);
+                  : (MODE == FFT_FIELD ? 1 : 16);
   long long total = n_outer * (long long)L * L * per;
   unsigned blocks = (unsigned)((total + 255) / 256);
   const cpx<S>* i = (const cpx<S>*)in;
@@ -360,13 +367,14 @@ cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int
 cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows,
                                   cudaStream_t st) {
   cudaError_t e =
-      fft_dispatch<double, double, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
+      fft_dispatch<dfr, dfr, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
   if (e != cudaSuccess) return e;
-  e = fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, 1, false,
-                                              nullptr, st);
-  if (e != cudaSuccess) return e;
-  return fft_dispatch<double, double, FFT_FIELD2DF>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, 2,
-                                                    false, nullptr, st);
+  for (int axis = 1; axis < 3; axis++) {
+    e = fft_dispatch<dfr, dfr, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
+                                          nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st) {

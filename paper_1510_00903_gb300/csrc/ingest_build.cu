@@ -44,10 +44,11 @@ cudaError_t launch_absmax(const void* src, int dtype, long long n_complex, unsig
 }
 
 cudaError_t launch_convert(const void* src, int dtype, long long n_complex, const unsigned long long* amax,
-                           int* kexp, void* dst, bool fp64, cudaStream_t st) {
+                           int* kexp, void* dst, int kind, cudaStream_t st) {
   long long n = 2 * n_complex;
   int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 8);
-  if (fp64) k_convert<double><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (double*)dst);
+  if (kind == RK_F64) k_convert<double><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (double*)dst);
+  else if (kind == RK_DF) k_convert<dfr><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (dfr*)dst);
   else k_convert<float><<<blocks, 256, 0, st>>>(src, dtype, n, amax, kexp, (float*)dst);
   return cudaGetLastError();
 }
@@ -148,7 +149,7 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
   }
 }
 
-size_t block_build_smem(int z_slots, int sites, bool fp64) {
+size_t block_build_smem(int z_slots, int sites, bool fp64) {  // fp64: 8-byte reals (FP64 or double-float)
   const size_t cb = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
   return (size_t)sites * (288 + 864 + z_slots) * cb + 32 * (fp64 ? sizeof(double) : sizeof(float));
 }
@@ -161,7 +162,7 @@ bool build_variant_supported(int sites, int threads) {
 template <typename R, int SITES, int THREADS>
 cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                  const uint32_t* zneed, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
-  const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8);
+  const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8);  // double or double-float
   static int granted[64] = {0};
   cudaError_t e = ensure_smem(k_block_build<R, SITES, THREADS>, sm, granted);
   if (e != cudaSuccess) return e;
@@ -173,14 +174,16 @@ cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int
 
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
                                const uint32_t* ell, const uint32_t* zneed, const DevGroups& g, void* blk,
-                               int n_out, bool fp64, cudaStream_t st, int sites, int threads) {
+                               int n_out, int kind, cudaStream_t st, int sites, int threads) {
+  const bool wide = kind != RK_F32;
   if (!build_variant_supported(sites, threads) || V % sites != 0 ||
-      block_build_smem(g.z_slots, sites, fp64) > kMaxSmemPerBlock)
+      block_build_smem(g.z_slots, sites, wide) > kMaxSmemPerBlock)
     return cudaErrorInvalidValue;
 #define BBC_BUILD(S, T)                                                                                            \
   if (sites == S && threads == T)                                                                                  \
-    return fp64 ? launch_build_variant<double, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st) \
-                : launch_build_variant<float, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st);
+    return kind == RK_F64 ? launch_build_variant<double, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st) \
+         : kind == RK_DF  ? launch_build_variant<dfr, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st)    \
+                          : launch_build_variant<float, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st);
   BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512)
 #undef BBC_BUILD
   return cudaErrorInvalidValue;

@@ -35,6 +35,9 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
 };
 
 constexpr int kMaxChannels = 64;
+// Real type of the propagators, blocks and forward transforms: FP32, FP64,
+// or double-float (two FP32 words, FP64-accurate on the FP32 pipes).
+enum RealKind { RK_F32 = 0, RK_F64 = 1, RK_DF = 2 };
 constexpr size_t kMaxSmemPerBlock = 227 * 1024;  // opt-in dynamic shared memory per CTA
 struct ScaleParams {  // per channel: host factor (1/V, mass normalisation) and quark counts
   int n_ch;
@@ -56,7 +59,7 @@ cudaError_t launch_absmax(const void* src, int dtype, long long n_complex,
 cudaError_t launch_nonfinite(const double* x, long long n, int* flag, cudaStream_t st);
 // dst = src * 2^-k with k = ilogb(max) + 1 (exact), k stored to *kexp.
 cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
-                           const unsigned long long* amax, int* kexp, void* dst, bool fp64,
+                           const unsigned long long* amax, int* kexp, void* dst, int kind,
                            cudaStream_t st);
 // Baryon blocks of every site: prop [slots][2][V][144], blk [slots][V][n_out];
 // `sites` consecutive sites per CTA of `threads` threads: (1, 256), (2, 256),
@@ -66,14 +69,14 @@ size_t block_build_smem(int z_slots, int sites, bool fp64);
 // ell_chunk[c] = (offset, length) of 32-row chunk c in ell (lane-interleaved rows).
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
                                const uint32_t* ell, const uint32_t* zneed, const DevGroups& g,
-                               void* blk, int n_out, bool fp64, cudaStream_t st, int sites, int threads);
+                               void* blk, int n_out, int kind, cudaStream_t st, int sites, int threads);
 // Forward 3-D FFT of every block field: x pass from the site-major build
 // output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],
 // then the y and z passes in place (exp(-i q.x), unnormalised).
 cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
                                cudaStream_t st);
-// FP64 forward transform as above whose last pass stores every value split
-// into a double-float (re.hi, re.lo, im.hi, im.lo), in place.
+// The same transform on double-float blocks in double-float arithmetic; the
+// field-major result holds (re.hi, re.lo, im.hi, im.lo) per value.
 cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows,
                                   cudaStream_t st);
 // Forward 3-D FFT in place on site-major blocks blk[slots][V][n_rows] (lanes

@@ -164,7 +164,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   for (int f = 0; f < 2; f++) {
     e = bbc::launch_absmax(src[f], dtype, (long long)nc, amax + f, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "absmax kernel");
-    e = bbc::launch_convert(src[f], dtype, (long long)nc, amax + f, kexp + f, w + L.prop + f * nc * cb, fp64, st);
+    e = bbc::launch_convert(src[f], dtype, (long long)nc, amax + f, kexp + f, w + L.prop + f * nc * cb,
+                           fp64 ? bbc::RK_F64 : bbc::RK_F32, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   }
   bbc::DevGroups g{};
@@ -180,7 +181,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   g.spin0 = p.spin_offset;
   for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
   e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int2*)(w + L.ell_chunk), (const uint32_t*)(w + L.ell),
-                              (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64, st, 1, 256);
+                              (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64 ? bbc::RK_F64 : bbc::RK_F32,
+                              st, 1, 256);
   if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   e = bbc::launch_fft_forward(w + L.blk, w + L.blkf, c->lat.L, 1, p.n_out, fp64, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
