@@ -275,7 +275,7 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
   // GPU several times over at L = 16 (V/32 q tiles x groups warps)
   // (the double-float products keep fewer q tiles in flight with more, shorter groups: their
   // rows stay in L2)
-  bbc::make_task_groups(c->plan, prec == BBC_DF64 ? 192 : 48, &c->group_ptr, &c->group_task);
+  bbc::make_task_groups(c->plan, prec == BBC_DF64 ? 192 : 48, &c->group_ptr, &c->group_task, prec == BBC_DF64);
   // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
   if (fused_path(prec)) {
     try {

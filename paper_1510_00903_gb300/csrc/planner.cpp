@@ -953,29 +953,46 @@ void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedL
   out->ideal = ideal;
 }
 
-void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task) {
-  std::vector<int> order(plan.tasks.size());
-  std::iota(order.begin(), order.end(), 0);
+void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task,
+                      bool by_shape) {
   auto cost = [&](int t) {
     const PairTask& k = plan.tasks[t];
     return (long long)k.n1 * k.n2 * (4 * k.nA * k.nB + 2 * (k.nA + k.nB)) + 64;  // FMAs + loads + stores
   };
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-  std::vector<long long> load(groups, 0);
-  std::vector<std::vector<int>> per(groups);
-  for (int t : order) {
-    int best = 0;
-    for (int g = 1; g < groups; g++)
-      if (load[g] < load[best]) best = g;
-    load[best] += cost(t);
-    per[best].push_back(t);
-  }
+  // classes of tasks that share a code path (all tasks, or one class per nA)
+  std::map<int, std::vector<int>> cls;
+  for (int t = 0; t < (int)plan.tasks.size(); t++) cls[by_shape ? plan.tasks[t].nA : 0].push_back(t);
+  long long total = 0;
+  for (int t = 0; t < (int)plan.tasks.size(); t++) total += cost(t);
   group_ptr->assign(1, 0);
   group_task->clear();
-  for (auto& v : per) {
-    std::sort(v.begin(), v.end());
-    for (int t : v) group_task->push_back(t);
-    group_ptr->push_back((int)group_task->size());
+  int left = groups;
+  size_t ci = 0;
+  for (auto& kv : cls) {
+    long long ccost = 0;
+    for (int t : kv.second) ccost += cost(t);
+    // groups for this class in proportion to its cost (at least one each)
+    const int remaining_classes = (int)(cls.size() - ci);
+    int g = ci + 1 == cls.size() ? left : (int)std::max<long long>(1, (long long)groups * ccost / std::max(total, 1LL));
+    g = std::min(g, left - (remaining_classes - 1));
+    left -= g;
+    ci++;
+    std::vector<int> order = kv.second;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<long long> load(g, 0);
+    std::vector<std::vector<int>> per(g);
+    for (int t : order) {
+      int best = 0;
+      for (int i = 1; i < g; i++)
+        if (load[i] < load[best]) best = i;
+      load[best] += cost(t);
+      per[best].push_back(t);
+    }
+    for (auto& v : per) {
+      std::sort(v.begin(), v.end());
+      for (int t : v) group_task->push_back(t);
+      group_ptr->push_back((int)group_task->size());
+    }
   }
 }
 

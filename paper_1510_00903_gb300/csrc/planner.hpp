@@ -123,6 +123,9 @@ void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedL
 
 // Partition of the tasks into `groups` lists of near-equal cost (longest task
 // first to the cheapest list); each list is run by one warp for 32 q at a time.
-void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task);
+// by_shape: lists hold tasks of one shape (nA) only and come shape by shape,
+// so warps that run side by side run the same code (instruction cache).
+void make_task_groups(const Plan& plan, int groups, std::vector<int>* group_ptr, std::vector<int>* group_task,
+                      bool by_shape = false);
 
 }  // namespace bbc
