@@ -239,3 +239,30 @@ def test_config_L32_T64_sampled_fp64_and_mixed():
         scale = np.abs(g[chans]).reshape(len(chans), -1).max(axis=1)
         e = np.abs(g[chans][:, r_list] - want).reshape(len(chans), -1).max(axis=1) / scale
         assert e.max() < tol, (prec, e)
+
+
+def test_config_L48_streamed_mixed_vs_fp64():
+    """The L=48 streaming configuration (complex64 host propagators copied per
+    slice, mixed precision, run_streamed) against the FP64 path on the same
+    inputs (the FP64 path is pinned to the oracle at L <= 32 and by the
+    plane-wave closed form at L = 48)."""
+    L, T = 48, 2
+    dev = torch.device("cuda")
+    ch = [0, 10, 41, 51]
+    g = torch.Generator(device=dev)
+    g.manual_seed(48)
+    S = [torch.randn((T, L ** 3, 12, 12), dtype=torch.complex64, device=dev, generator=g) for _ in range(2)]
+    host = [x.cpu().pin_memory() for x in S]
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=ch, precision=bbc.BBC_MIXED_FP32, device=dev,
+                          stream=torch.cuda.Stream())
+    out = torch.empty((len(ch), L ** 3, 16), dtype=torch.complex128, device=dev)
+    res = torch.empty((T,) + tuple(out.shape), dtype=out.dtype, device=dev)
+    cor.run_streamed(host[0], host[1], range(T), out, on_slice=lambda t, o: res[t].copy_(o))
+    cor.close()
+    ref = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=ch, precision=bbc.BBC_FP64, device=dev)
+    want = ref.run(S[0].to(torch.complex128), S[1].to(torch.complex128), range(T))
+    torch.cuda.synchronize()
+    for t in range(T):
+        e, _ = rel_err(res[t].cpu().numpy(), want[t].cpu().numpy())
+        assert e.max() < MIXED_TOL, (t, e)
+    ref.close()
