@@ -90,10 +90,11 @@ def test_all_channels_L4_fp64_and_mixed():
 
 @pytest.mark.parametrize("L", [4, 8])
 def test_all_channels_bf16_trial(L):
-    """The bfloat16 trial precision on all 52 channels of one slice."""
+    """The bfloat16 trial precision on one slice: all 52 channels at L = 4,
+    twelve at L = 8 (oracle time)."""
     T = 4
     F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=11)
-    ch = list(range(52))
+    ch = list(range(52)) if L == 4 else [0, 1, 5, 10, 14, 16, 27, 33, 41, 44, 48, 51]
     want = oracle_slice(L, F, 2, ch)
     got = gpu_run(L, T, 0, ch, F["u"], F["s"], [2], precision=bbc.BBC_MIXED_BF16)[0]
     e, _ = rel_err(got, want)
