@@ -544,7 +544,10 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     }
     {
       StageScope scope(c, BBC_STAGE_WICK);
-      e = bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64, c->stream);
+      e = c->prec == BBC_DF64
+              ? bbc::launch_wick_sums_df(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, c->stream)
+              : bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64,
+                                      c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
     }
   } else {
@@ -577,8 +580,9 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   }
   {
     StageScope scope(c, BBC_STAGE_FFT_INV);
-    e = fp64 ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
-             : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
+    e = c->prec == BBC_DF64 ? bbc::launch_fft_inverse_df(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, c->stream)
+        : fp64 ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
+               : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
   if (c->checks & BBC_CHECK_OUTPUT) {

@@ -173,9 +173,11 @@ __device__ __forceinline__ void line_base(int N, int axis, int line, int& base, 
 // Mode SITE2OUT (z axis): in[site][n_ch*16] -> out[ch][r][16] times scale[ch].
 enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4 };
 
-template <typename S, typename R, int N, bool INV, int MODE>
+// S: storage of the input (and of the output in the in-place modes), R:
+// compute type, O: storage of the output of the last inverse pass.
+template <typename S, typename R, int N, bool INV, int MODE, typename O = S>
 __global__ void __launch_bounds__(256)
-k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer, int n_inner, int axis,
+k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer, int n_inner, int axis,
       const double* __restrict__ scale) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int lines = N * N;
@@ -211,30 +213,30 @@ k_fft(const cpx<S>* __restrict__ in, cpx<S>* __restrict__ out, long long n_outer
     line_fft<S, R, N, INV>(in + (o * 16 + inner) * V + base, stride, v);
   }
   if (MODE == FFT_SITE2FIELD) {
-    cpx<S>* p = out + (o * n_inner + inner) * V + base;
+    cpx<O>* p = out + (o * n_inner + inner) * V + base;
 #pragma unroll
-    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<O>(v[k]);
   } else if (MODE == FFT_FIELD) {
-    cpx<S>* p = out + o * V + base;
+    cpx<O>* p = out + o * V + base;
 #pragma unroll
-    for (int k = 0; k < N; k++) p[k * stride] = cpx<S>(v[k]);
+    for (int k = 0; k < N; k++) p[k * stride] = cpx<O>(v[k]);
   } else if (MODE == FFT_SITE) {
-    cpx<S>* p = out + (o * V + base) * n_inner + inner;
+    cpx<O>* p = out + (o * V + base) * n_inner + inner;
 #pragma unroll
-    for (int k = 0; k < N; k++) p[(long long)k * stride * n_inner] = cpx<S>(v[k]);
+    for (int k = 0; k < N; k++) p[(long long)k * stride * n_inner] = cpx<O>(v[k]);
   } else if (MODE == FFT_SITE2OUT) {
     // inner = channel * 16 + spin; out[ch][r][16].  The scale (1/V, the
     // undone propagator rescaling, the mass factor) may lie far outside the
-    // compute precision's range: it multiplies in the storage precision.
-    const S f = (S)scale[inner >> 4];
-    cpx<S>* p = out + ((long long)(inner >> 4) * V + base) * 16 + (inner & 15);
+    // compute precision's range: it multiplies in the output precision.
+    const O f = (O)scale[inner >> 4];
+    cpx<O>* p = out + ((long long)(inner >> 4) * V + base) * 16 + (inner & 15);
 #pragma unroll
-    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<S>((S)v[k].re * f, (S)v[k].im * f);
+    for (int k = 0; k < N; k++) p[(long long)k * stride * 16] = cpx<O>((O)v[k].re * f, (O)v[k].im * f);
   } else {
-    const S f = (S)scale[o];
+    const O f = (O)scale[o];
 #pragma unroll
     for (int k = 0; k < N; k++) {
-      cpx<S> w((S)v[k].re * f, (S)v[k].im * f);
+      cpx<O> w((O)v[k].re * f, (O)v[k].im * f);
       out[(o * V + base + (long long)k * stride) * 16 + inner] = w;
     }
   }
@@ -313,7 +315,7 @@ static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner
   return cudaGetLastError();
 }
 
-template <typename S, typename R, int MODE>
+template <typename S, typename R, int MODE, typename O = S>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
                                 const double* scale, cudaStream_t st) {
   long long per = (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) ? n_inner
@@ -321,11 +323,11 @@ static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_ou
   long long total = n_outer * (long long)L * L * per;
   unsigned blocks = (unsigned)((total + 255) / 256);
   const cpx<S>* i = (const cpx<S>*)in;
-  cpx<S>* o = (cpx<S>*)out;
-#define BBC_FFT_CASE(NN)                                                                                   \
-  case NN:                                                                                                 \
-    if (inv) k_fft<S, R, NN, true, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);    \
-    else k_fft<S, R, NN, false, MODE><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);        \
+  cpx<O>* o = (cpx<O>*)out;
+#define BBC_FFT_CASE(NN)                                                                                      \
+  case NN:                                                                                                    \
+    if (inv) k_fft<S, R, NN, true, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);    \
+    else k_fft<S, R, NN, false, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);        \
     break;
   switch (L) {
     BBC_FFT_CASE(2)
@@ -393,6 +395,15 @@ cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const 
   if (e != cudaSuccess) return e;
   return fp64_compute ? fft_dispatch<double, double, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st)
                       : fft_dispatch<double, float, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
+}
+
+cudaError_t launch_fft_inverse_df(void* ct, void* out, int L, int n_ch, const double* scale, cudaStream_t st) {
+  cudaError_t e;
+  for (int axis = 0; axis < 2; axis++) {
+    e = fft_dispatch<dfr, dfr, FFT_FIELD>(ct, ct, L, (long long)n_ch * 16, 1, axis, true, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return fft_dispatch<dfr, dfr, FFT_FIELD2OUT, double>(ct, out, L, n_ch, 16, 2, true, scale, st);
 }
 
 cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,

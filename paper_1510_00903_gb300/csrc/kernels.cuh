@@ -118,6 +118,12 @@ cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* ta
 // quadruples per complex value; P is complex128.
 cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
                                     const int* group_task, int n_groups, void* P, cudaStream_t st);
+// Wick sums as launch_wick_sums (FP64) storing ct as double-float pairs, and
+// the inverse transform of such ct in double-float arithmetic whose last
+// pass writes complex128 out[n_ch][V][16] times scale[ch].
+cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
+                                void* ct, cudaStream_t st);
+cudaError_t launch_fft_inverse_df(void* ct, void* out, int L, int n_ch, const double* scale, cudaStream_t st);
 // ... then the signed FP64 sums over Wick diagrams into ct[n_ch*16][V] (complex128).
 cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
                              void* ct, bool fp64, cudaStream_t st);

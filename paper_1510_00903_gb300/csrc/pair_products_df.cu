@@ -80,4 +80,30 @@ cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask*
   return cudaGetLastError();
 }
 
+// Signed FP64 sums over Wick diagrams as k_wick_sums, each result stored
+// split into a double-float for the double-float inverse transform.
+__global__ void __launch_bounds__(128)
+k_wick_sums_df(const cpx<double>* __restrict__ P, int V, const int* __restrict__ cptr, const int* __restrict__ citem,
+               const double* __restrict__ ccoef, cpx<dfr>* __restrict__ Ct) {
+  const int q = blockIdx.x * 128 + threadIdx.x, o = blockIdx.y;
+  if (q >= V) return;
+  cpx<double> s(0, 0);
+  const int c1 = cptr[o + 1];
+  for (int c = cptr[o]; c < c1; c++) {
+    const double w = ccoef[c];
+    const cpx<double> p = P[(long long)citem[c] * V + q];
+    s.re = fma(w, p.re, s.re);
+    s.im = fma(w, p.im, s.im);
+  }
+  Ct[(long long)o * V + q] = cpx<dfr>(dfr(s.re), dfr(s.im));
+}
+
+cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
+                                void* ct, cudaStream_t st) {
+  const int V = L * L * L;
+  dim3 g2((V + 127) / 128, n_ch * 16);
+  k_wick_sums_df<<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<dfr>*)ct);
+  return cudaGetLastError();
+}
+
 }  // namespace bbc
