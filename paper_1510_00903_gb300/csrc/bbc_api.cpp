@@ -34,7 +34,7 @@ int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP
 constexpr int kMaxFusedWarps = 16;
 
 struct Layout {
-  size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef;
+  size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
   size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, flag, total;
 };
@@ -52,6 +52,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.cptr = o; o = align256(o + sizeof(int) * p.tcontrib_ptr.size());
   L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
   L.ccoef = o; o = align256(o + sizeof(double) * p.tcontrib_coef.size());
+  L.ccoef_df = o; o = align256(o + (c->prec == BBC_DF64 ? sizeof(float2) * p.tcontrib_coef.size() : 0));
   L.batches = o; o = align256(o + sizeof(bbc::WarpBatch) * c->batches.size());
   L.wptr = o; o = align256(o + sizeof(int) * (kMaxFusedWarps + 1));
   L.wunits = o; o = align256(o + sizeof(int4) * c->max_units);
@@ -368,6 +369,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_cptr = (int*)(w + L.cptr);
   c->d_citem = (int*)(w + L.citem);
   c->d_ccoef = (double*)(w + L.ccoef);
+  c->d_ccoef_df = (float2*)(w + L.ccoef_df);
   c->d_batches = (bbc::WarpBatch*)(w + L.batches);
   c->d_wptr = (int*)(w + L.wptr);
   c->d_wunits = (int4*)(w + L.wunits);
@@ -404,6 +406,12 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     d.sA = t.sA1 | (t.sA2 << 16);
     d.sB = t.sB1 | (t.sB2 << 16);
   }
+  std::vector<float2> coef_df;  // double-float split of the Wick coefficients
+  if (c->prec == BBC_DF64)
+    for (double x : p.tcontrib_coef) {
+      const float h = (float)x;
+      coef_df.push_back(make_float2(h, (float)(x - (double)h)));
+    }
   std::vector<bbc::WarpBatch> wb(c->batches.size());
   for (size_t i = 0; i < c->batches.size(); i++) {
     wb[i].n = (int)c->batches[i].tasks.size();
@@ -420,6 +428,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_cptr, p.tcontrib_ptr.data(), sizeof(int) * p.tcontrib_ptr.size()},
       {c->d_citem, p.tcontrib_item.data(), sizeof(int) * p.tcontrib_item.size()},
       {c->d_ccoef, p.tcontrib_coef.data(), sizeof(double) * p.tcontrib_coef.size()},
+      {c->d_ccoef_df, coef_df.data(), sizeof(float2) * coef_df.size()},
       {c->d_batches, wb.data(), sizeof(bbc::WarpBatch) * wb.size()},
       {c->d_qlist, c->qlist.data(), sizeof(int) * c->qlist.size()},
       {c->d_row_slot, c->row_slot.data(), sizeof(int) * c->row_slot.size()},
@@ -545,7 +554,8 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     {
       StageScope scope(c, BBC_STAGE_WICK);
       e = c->prec == BBC_DF64
-              ? bbc::launch_wick_sums_df(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, c->stream)
+              ? bbc::launch_wick_sums_df(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef_df, n_ch, c->d_ct,
+                                         c->stream)
               : bbc::launch_wick_sums(c->d_P, c->lat.L, c->d_cptr, c->d_citem, c->d_ccoef, n_ch, c->d_ct, fp64,
                                       c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");

@@ -31,6 +31,7 @@ struct bbc_ctx {
   int* d_cptr = nullptr;
   int* d_citem = nullptr;
   double* d_ccoef = nullptr;
+  float2* d_ccoef_df = nullptr;          // the coefficients as double-float pairs (BBC_DF64)
   std::vector<int> group_ptr;            // warp task groups of the pair products (FP64)
   std::vector<int> group_task;
   // fused FP32 contraction: warp batches, per-warp units, one q per pair {q, -q}

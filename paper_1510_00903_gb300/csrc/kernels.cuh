@@ -114,15 +114,16 @@ cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const doubl
 // P[n_tasks*16][V] ...
 cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
                                  const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st);
-// Double-float variant: blk_field holds (re.hi, re.lo, im.hi, im.lo) FP32
-// quadruples per complex value; P is complex128.
+// Double-float variant: blk_field and P hold (re.hi, re.lo, im.hi, im.lo)
+// FP32 quadruples per complex value.
 cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
                                     const int* group_task, int n_groups, void* P, cudaStream_t st);
-// Wick sums as launch_wick_sums (FP64) storing ct as double-float pairs, and
-// the inverse transform of such ct in double-float arithmetic whose last
-// pass writes complex128 out[n_ch][V][16] times scale[ch].
-cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
-                                void* ct, cudaStream_t st);
+// Wick sums of double-float products with double-float coefficients
+// (ccoef_df[c] = (hi, lo) of ccoef[c]) into double-float ct, and the inverse
+// transform of such ct in double-float arithmetic whose last pass writes
+// complex128 out[n_ch][V][16] times scale[ch].
+cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const float2* ccoef_df,
+                                int n_ch, void* ct, cudaStream_t st);
 cudaError_t launch_fft_inverse_df(void* ct, void* out, int L, int n_ch, const double* scale, cudaStream_t st);
 // ... then the signed FP64 sums over Wick diagrams into ct[n_ch*16][V] (complex128).
 cudaError_t launch_wick_sums(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,

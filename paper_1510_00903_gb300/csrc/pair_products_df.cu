@@ -8,13 +8,13 @@ namespace bbc {
 constexpr int kPairWarpsDf = 4;
 
 // Double-float variant: the Fourier-space blocks as (re.hi, re.lo, im.hi,
-// im.lo) FP32 quadruples (written by the last forward FFT pass), every
-// complex product as four double-float multiply-adds on the FP32 pipes,
-// accumulators renormalised every 16 open-index steps, the products stored
-// as complex128 for the FP64 Wick sums.
+// im.lo) FP32 quadruples (from the double-float forward FFT), every complex
+// product as four double-float multiply-adds on the FP32 pipes, accumulators
+// renormalised every 16 open-index steps, the products stored as
+// double-float pairs for the double-float Wick sums.
 template <int NA, int NB>
 __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, long long V, int q, int nq,
-                                                 const DevTask& t, cpx<double>* __restrict__ P) {
+                                                 const DevTask& t, cpx<dfr>* __restrict__ P) {
   const int n2 = t.n2, K = t.n1 * n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
   df64acc re[NA * NB], im[NA * NB];
@@ -45,13 +45,17 @@ __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, l
     else { oA += sA2; oB += sB2; }
   }
 #pragma unroll
-  for (int i = 0; i < NA * NB; i++) P[(long long)i * V] = cpx<double>(df_to_double(re[i]), df_to_double(im[i]));
+  for (int i = 0; i < NA * NB; i++) {
+    df_renorm(re[i]);
+    df_renorm(im[i]);
+    P[(long long)i * V] = cpx<dfr>(dfr(re[i].s, re[i].e), dfr(im[i].s, im[i].e));
+  }
 }
 
 __global__ void __launch_bounds__(32 * kPairWarpsDf, 4)
 k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restrict__ tasks,
                    const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
-                   cpx<double>* __restrict__ P) {
+                   cpx<dfr>* __restrict__ P) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = blockIdx.x * kPairWarpsDf + warp;
   const int V = L * L * L;
@@ -63,7 +67,7 @@ k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restric
   for (int j = group_ptr[g]; j < j1; j++) {
     const int ti = group_task[j];
     const DevTask t = tasks[ti];
-    cpx<double>* p = P + (long long)ti * 16 * V + q;
+    cpx<dfr>* p = P + (long long)ti * 16 * V + q;
     const int nA = t.nAnB & 0xff;
     if (nA == 4) task_products_df<4, 4>(F, V, q, nq, t, p);
     else if (nA == 2) task_products_df<2, 8>(F, V, q, nq, t, p);
@@ -76,33 +80,38 @@ cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask*
   const int V = L * L * L;
   dim3 g1((n_groups + kPairWarpsDf - 1) / kPairWarpsDf, (V + 31) / 32);
   k_pair_products_df<<<g1, 32 * kPairWarpsDf, 0, st>>>((const float4*)blk_field, L, tasks, group_ptr, group_task,
-                                                       n_groups, (cpx<double>*)P);
+                                                       n_groups, (cpx<dfr>*)P);
   return cudaGetLastError();
 }
 
-// Signed FP64 sums over Wick diagrams as k_wick_sums, each result stored
-// split into a double-float for the double-float inverse transform.
+// Signed sums over Wick diagrams in double-float arithmetic: the products and
+// the coefficients (split once on the host) as double-float pairs, every
+// term one double-float multiply-add per real part; ct stored as
+// double-float pairs for the double-float inverse transform.
 __global__ void __launch_bounds__(128)
-k_wick_sums_df(const cpx<double>* __restrict__ P, int V, const int* __restrict__ cptr, const int* __restrict__ citem,
-               const double* __restrict__ ccoef, cpx<dfr>* __restrict__ Ct) {
+k_wick_sums_df(const cpx<dfr>* __restrict__ P, int V, const int* __restrict__ cptr, const int* __restrict__ citem,
+               const float2* __restrict__ ccoef, cpx<dfr>* __restrict__ Ct) {
   const int q = blockIdx.x * 128 + threadIdx.x, o = blockIdx.y;
   if (q >= V) return;
-  cpx<double> s(0, 0);
+  df64acc re{0.f, 0.f}, im{0.f, 0.f};
   const int c1 = cptr[o + 1];
   for (int c = cptr[o]; c < c1; c++) {
-    const double w = ccoef[c];
-    const cpx<double> p = P[(long long)citem[c] * V + q];
-    s.re = fma(w, p.re, s.re);
-    s.im = fma(w, p.im, s.im);
+    const float2 w = __ldg(ccoef + c);
+    const cpx<dfr> p = P[(long long)citem[c] * V + q];
+    df_mac(re, w.x, w.y, p.re.hi, p.re.lo);
+    df_mac(im, w.x, w.y, p.im.hi, p.im.lo);
+    if (((c - cptr[o]) & 15) == 15) { df_renorm(re); df_renorm(im); }
   }
-  Ct[(long long)o * V + q] = cpx<dfr>(dfr(s.re), dfr(s.im));
+  df_renorm(re);
+  df_renorm(im);
+  Ct[(long long)o * V + q] = cpx<dfr>(dfr(re.s, re.e), dfr(im.s, im.e));
 }
 
-cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const double* ccoef, int n_ch,
-                                void* ct, cudaStream_t st) {
+cudaError_t launch_wick_sums_df(const void* P, int L, const int* cptr, const int* citem, const float2* ccoef_df,
+                                int n_ch, void* ct, cudaStream_t st) {
   const int V = L * L * L;
   dim3 g2((V + 127) / 128, n_ch * 16);
-  k_wick_sums_df<<<g2, 128, 0, st>>>((const cpx<double>*)P, V, cptr, citem, ccoef, (cpx<dfr>*)ct);
+  k_wick_sums_df<<<g2, 128, 0, st>>>((const cpx<dfr>*)P, V, cptr, citem, ccoef_df, (cpx<dfr>*)ct);
   return cudaGetLastError();
 }
 
