@@ -286,61 +286,6 @@ __global__ void __launch_bounds__(256) k_fft_xy_site(cpx<S>* __restrict__ data, 
   }
 }
 
-// y and z passes of field-major data[n_fields][V] fused in one kernel: a CTA
-// stages one whole field in shared memory (V complex values of R: fits for
-// L <= 24 in double-float), runs every y line, then every z line, and writes
-// the field back in place.  One HBM round trip for two passes.
-template <typename S, typename R, int N, bool INV>
-__global__ void __launch_bounds__(256) k_fft_yz_field(cpx<S>* __restrict__ data) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* f = reinterpret_cast<cpx<R>*>(smem_raw);  // [V]
-  constexpr int V = N * N * N;
-  cpx<S>* field = data + (long long)blockIdx.x * V;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < V; i += 256) f[i] = cpx<R>(field[i]);
-  __syncthreads();
-  for (int li = tid; li < N * N; li += 256) {  // y lines: (x, z)
-    const int x = li % N, z = li / N;
-    cpx<R> v[N];
-    line_fft<R, R, N, INV>(f + x + N * N * z, N, v);
-#pragma unroll
-    for (int k = 0; k < N; k++) f[x + N * (k + N * z)] = v[k];
-  }
-  __syncthreads();
-  for (int li = tid; li < N * N; li += 256) {  // z lines: (x, y)
-    const int x = li % N, y = li / N;
-    cpx<R> v[N];
-    line_fft<R, R, N, INV>(f + x + N * y, N * N, v);
-#pragma unroll
-    for (int k = 0; k < N; k++) field[x + N * (y + N * k)] = cpx<S>(v[k]);
-  }
-}
-
-template <typename S, typename R>
-static cudaError_t fft_yz_field(void* data, int L, long long n_fields, bool inv, cudaStream_t st) {
-#define BBC_YZ_CASE(NN)                                                                                    \
-  case NN: {                                                                                               \
-    const size_t sm = sizeof(cpx<R>) * NN * NN * NN;                                                       \
-    static int granted_f[64] = {0}, granted_i[64] = {0};                                                   \
-    cudaError_t e = inv ? ensure_smem(k_fft_yz_field<S, R, NN, true>, sm, granted_i)                       \
-                        : ensure_smem(k_fft_yz_field<S, R, NN, false>, sm, granted_f);                     \
-    if (e != cudaSuccess) return e;                                                                        \
-    if (inv) k_fft_yz_field<S, R, NN, true><<<(unsigned)n_fields, 256, sm, st>>>((cpx<S>*)data);           \
-    else k_fft_yz_field<S, R, NN, false><<<(unsigned)n_fields, 256, sm, st>>>((cpx<S>*)data);              \
-    break;                                                                                                 \
-  }
-  switch (L) {
-    BBC_YZ_CASE(2)
-    BBC_YZ_CASE(4)
-    BBC_YZ_CASE(8)
-    BBC_YZ_CASE(16)
-    BBC_YZ_CASE(24)
-    default: return cudaErrorInvalidValue;
-  }
-#undef BBC_YZ_CASE
-  return cudaGetLastError();
-}
-
 template <typename S, typename R>
 static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner, bool inv, cudaStream_t st) {
 #define BBC_XY_CASE(NN)                                                                                          \
@@ -426,8 +371,6 @@ cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, 
   cudaError_t e =
       fft_dispatch<dfr, dfr, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
   if (e != cudaSuccess) return e;
-  if (L <= 24)  // a whole field fits in shared memory: y and z in one pass
-    return fft_yz_field<dfr, dfr>(blk_field, L, (long long)n_slots * n_rows, false, st);
   for (int axis = 1; axis < 3; axis++) {
     e = fft_dispatch<dfr, dfr, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
                                           nullptr, st);
