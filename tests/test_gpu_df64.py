@@ -37,7 +37,7 @@ def test_df64_all_channels_L4():
     cor.close()
 
 
-@pytest.mark.parametrize("L", [16, 32])
+@pytest.mark.parametrize("L", [16, 24, 32])
 def test_df64_sampled(L):
     T, t = 8, 5
     dev = torch.device("cuda", torch.cuda.current_device())
