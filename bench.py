@@ -334,9 +334,9 @@ def run_ours(args, torch, rank, world, local):
     cord.close()
     cd_ms, cd_n = st_d["contract"]
     df64 = {"value": shard.job_throughput(V * T * N_CH, world, ms_d), "ms_per_step": ms_d, "speedup_vs_fp64": ms / ms_d,
-            "precision": "propagators, block build, forward FFT and block-pair products in double-float "
-                         "arithmetic (two FP32 words, 48-bit significand) on the FP32 pipes; Wick sums, inverse FFT "
-                         "and normalisation in FP64; parity with the FP64 oracle at 1e-12 (measured <= 4e-14)",
+            "precision": "propagators, block build, FFTs, block-pair products and Wick sums in double-float "
+                         "arithmetic (two FP32 words, 48-bit significand) on the FP32 pipes; FP64 for the input split "
+                         "and the normalisation; parity with the FP64 oracle at 1e-12 (measured <= 4e-14)",
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in st_d.items()},
             "contract_ms_per_slice": cd_ms / max(cd_n, 1), "tuning": tune_d}
 

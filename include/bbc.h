@@ -70,10 +70,10 @@ typedef enum {
   BBC_MIXED_BF16 = 2, /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
                          to bfloat16 (round to nearest even) before the block-pair
                          products, which multiply and accumulate in FP32 */
-  BBC_DF64 = 3        /* as BBC_FP64, with the block-pair products in double-float
-                         arithmetic (unevaluated sums of two FP32 values, 48-bit
-                         significand) on the FP32 pipes: FP64-accurate results where
-                         GB300's FP64 pipe would bound the contraction */
+  BBC_DF64 = 3        /* FP64-accurate results from double-float arithmetic
+                         (unevaluated sums of two FP32 values, 48-bit significand) on
+                         the FP32 pipes: propagators, blocks, FFTs, block-pair products
+                         and Wick sums; FP64 only to split the input and to normalise */
 } bbc_precision;
 
 typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
