@@ -664,9 +664,62 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
       for (int l = 0; l < nr; l++) len = std::max(len, P.row_ptr[r0 + l + 1] - P.row_ptr[r0 + l]);
       const int base = (int)P.ell.size();
       P.ell.resize(P.ell.size() + (size_t)32 * len, 0u);  // weight 0, position 0
+      // A row's terms may be summed in any order: at every step k, give each
+      // lane a term whose tensor position falls in a bank group (position
+      // mod 16: an 8-byte FP32 complex spans two of the 32 banks) that no
+      // other lane of its half-warp uses at that step, where it can.
+      std::vector<std::vector<uint32_t>> left(nr);
       for (int l = 0; l < nr; l++)
-        for (int k = 0; k < P.row_ptr[r0 + l + 1] - P.row_ptr[r0 + l]; k++)
-          P.ell[base + 32 * k + l] = P.entries[P.row_ptr[r0 + l] + k];
+        left[l].assign(P.entries.begin() + P.row_ptr[r0 + l], P.entries.begin() + P.row_ptr[r0 + l + 1]);
+      for (int k = 0; k < len; k++)
+        for (int h = 0; h < 32; h += 16) {
+          bool used[16] = {false};
+          for (int l = h; l < std::min(nr, h + 16); l++) {
+            std::vector<uint32_t>& v = left[l];
+            if (v.empty()) continue;
+            size_t pick = 0;
+            for (size_t j = 0; j < v.size(); j++)
+              if (!used[(v[j] & 0xffffu) % 16]) { pick = j; break; }
+            used[(v[pick] & 0xffffu) % 16] = true;
+            P.ell[base + 32 * k + l] = v[pick];
+            v.erase(v.begin() + (long)pick);
+          }
+        }
+      // then exchanges of two steps of one lane (terms or padding) while the
+      // modelled shared-memory wavefronts of the two steps drop: distinct
+      // positions in one bank group serialise, equal ones broadcast, padding
+      // (weight 0) reads nothing
+      auto half_cost = [&](int k, int h) {
+        int cnt[16] = {0}, seen[16][16], m = 0;
+        for (int l = h; l < std::min(nr, h + 16); l++) {
+          const uint32_t e = P.ell[base + 32 * k + l];
+          if ((e >> 16) == 0) continue;
+          const int pos = (int)(e & 0xffffu), b = pos % 16;
+          bool dup = false;
+          for (int j = 0; j < cnt[b]; j++) dup |= seen[b][j] == pos;
+          if (!dup && cnt[b] < 16) {
+            seen[b][cnt[b]++] = pos;
+            m = std::max(m, cnt[b]);
+          }
+        }
+        return m;
+      };
+      for (int sweep = 0; sweep < 4; sweep++) {
+        bool improved = false;
+        for (int l = 0; l < nr; l++)
+          for (int k1 = 0; k1 < len; k1++)
+            for (int k2 = k1 + 1; k2 < len; k2++) {
+              uint32_t& a = P.ell[base + 32 * k1 + l];
+              uint32_t& b = P.ell[base + 32 * k2 + l];
+              if (a == b) continue;
+              const int h = l / 16 * 16;
+              const int before = half_cost(k1, h) + half_cost(k2, h);
+              std::swap(a, b);
+              if (half_cost(k1, h) + half_cost(k2, h) < before) improved = true;
+              else std::swap(a, b);
+            }
+        if (!improved) break;
+      }
       P.ell_chunk.push_back({base, len});
     }
     P.chunk_first.push_back((int)P.ell_chunk.size());
