@@ -132,8 +132,7 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
       const int2 ch = __ldg(ell_chunk + g.chunk_first[gi] + ((r - r0) >> 5));
       const uint32_t* ep = ell + ch.x + ((r - r0) & 31);
       for (int k = 0; k < ch.y; k++) {
-        const uint32_t e = __ldg(ep + 32 * k);
-        if ((e >> 16) == 0) continue;  // padding of a shorter row: no shared-memory read
+        const uint32_t e = __ldg(ep + 32 * k);  // padding: weight 0 at position 0
         const R w = sW[((int)(int16_t)(e >> 16)) + 16];
         const int pos = e & 0xffffu;
 #pragma unroll

@@ -688,12 +688,11 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
       // then exchanges of two steps of one lane (terms or padding) while the
       // modelled shared-memory wavefronts of the two steps drop: distinct
       // positions in one bank group serialise, equal ones broadcast, padding
-      // (weight 0) reads nothing
+      // (weight 0) reads position 0
       auto half_cost = [&](int k, int h) {
         int cnt[16] = {0}, seen[16][16], m = 0;
         for (int l = h; l < std::min(nr, h + 16); l++) {
           const uint32_t e = P.ell[base + 32 * k + l];
-          if ((e >> 16) == 0) continue;
           const int pos = (int)(e & 0xffffu), b = pos % 16;
           bool dup = false;
           for (int j = 0; j < cnt[b]; j++) dup |= seen[b][j] == pos;
