@@ -1,6 +1,7 @@
 // ingest_build.cu -- propagator ingest with exact power-of-two rescaling, per-site baryon blocks (Sec. 3 blocks, Appendix A aggregation), per-channel normalisation factors (Sec. 2 Eq. 2)
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <utility>
 
 #include "device_common.cuh"
@@ -133,6 +134,10 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
       const uint32_t* ep = ell + ch.x + ((r - r0) & 31);
       for (int k = 0; k < ch.y; k++) {
         const uint32_t e = __ldg(ep + 32 * k);  // padding: weight 0 at position 0
+        // FP64 is bound by its narrow pipe: skip the padding's multiply-adds
+        // there; the other types run them (no divergent branch)
+        if constexpr (sizeof(R) == 8 && std::is_floating_point<R>::value)
+          if ((e >> 16) == 0) continue;
         const R w = sW[((int)(int16_t)(e >> 16)) + 16];
         const int pos = e & 0xffffu;
 #pragma unroll
