@@ -380,19 +380,36 @@ cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, 
 }
 
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st) {
-  // x and y fused (one HBM round trip), then z
-  cudaError_t e = fp64 ? fft_xy_site<double, double>(blk, L, n_slots, n_rows, false, st)
-                       : fft_xy_site<float, float>(blk, L, n_slots, n_rows, false, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (L <= 32) {  // x and y fused (one HBM round trip), then z
+    e = fp64 ? fft_xy_site<double, double>(blk, L, n_slots, n_rows, false, st)
+             : fft_xy_site<float, float>(blk, L, n_slots, n_rows, false, st);
+    if (e != cudaSuccess) return e;
+  } else {  // L = 48: the 48-point lines leave too few registers for a fused plane
+    for (int axis = 0; axis < 2; axis++) {
+      e = fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st)
+               : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, axis, false, nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return fp64 ? fft_dispatch<double, double, FFT_SITE>(blk, blk, L, n_slots, n_rows, 2, false, nullptr, st)
               : fft_dispatch<float, float, FFT_SITE>(blk, blk, L, n_slots, n_rows, 2, false, nullptr, st);
 }
 
 cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
                                     cudaStream_t st) {
-  cudaError_t e = fp64_compute ? fft_xy_site<double, double>(ct, L, 1, n_ch * 16, true, st)
-                               : fft_xy_site<double, float>(ct, L, 1, n_ch * 16, true, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (L <= 32) {
+    e = fp64_compute ? fft_xy_site<double, double>(ct, L, 1, n_ch * 16, true, st)
+                     : fft_xy_site<double, float>(ct, L, 1, n_ch * 16, true, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (int axis = 0; axis < 2; axis++) {
+      e = fp64_compute ? fft_dispatch<double, double, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st)
+                       : fft_dispatch<double, float, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
   return fp64_compute ? fft_dispatch<double, double, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st)
                       : fft_dispatch<double, float, FFT_SITE2OUT>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
 }
