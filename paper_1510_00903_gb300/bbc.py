@@ -382,6 +382,51 @@ class Correlators:
             cur.wait_stream(self.stream)
         return out
 
+    def run_to_host(self, S_light, S_strange, times, out_host, normalised: bool = True):
+        """End to end from pinned host propagators ([T, V, 12, 12]) to pinned
+        host correlators out_host [len(times), n_channels, V, 16] complex128:
+        the host-to-device copy of slice i+1, the compute of slice i and the
+        device-to-host copy of slice i-1 overlap (two copy streams, double
+        buffers on the device)."""
+        torch = self.torch
+        times = list(times)
+        if not times:
+            return out_host
+        n_ch = len(self.channels)
+        if getattr(self, "_d2h_bufs", None) is None:
+            self._d2h_stream = torch.cuda.Stream(self.device)
+            self._d2h_bufs = [torch.empty((n_ch, self.V, 16), dtype=torch.complex128, device=self.device)
+                              for _ in range(2)]
+        d2h, obufs = self._d2h_stream, self._d2h_bufs
+        done = [torch.cuda.Event() for _ in range(2)]
+        drained = [torch.cuda.Event() for _ in range(2)]
+        state = {"i": 0}
+
+        def on_slice(t, out):
+            i = state["i"]
+            b = i % 2
+            if i >= 2:
+                self.stream.wait_event(drained[b])  # the copy out of this buffer two slices ago
+            # the slice was written into the shared buffer: move it to its own one
+            obufs[b].copy_(out, non_blocking=True)
+            done[b].record(self.stream)
+            with torch.cuda.stream(d2h):
+                d2h.wait_event(done[b])
+                out_host[i].copy_(obufs[b], non_blocking=True)
+                drained[b].record(d2h)
+            state["i"] = i + 1
+
+        out = self._d2h_out = getattr(self, "_d2h_out", None)
+        if out is None:
+            out = self._d2h_out = torch.empty((n_ch, self.V, 16), dtype=torch.complex128, device=self.device)
+        d2h.wait_stream(self.stream)
+        self.run_streamed(S_light, S_strange, times, out, normalised, on_slice=on_slice)
+        cur = torch.cuda.current_stream(self.device)
+        cur.wait_stream(d2h)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+        return out_host
+
     def autotune(self, S_light, S_strange, t: int = 0, reps: int = 5):
         """Load slice t into slot 0 and run the autotuner (bbc_autotune);
         returns (configuration, ms per candidate)."""
