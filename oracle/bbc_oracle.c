@@ -14,6 +14,10 @@
  * Each baryon is eps_{c0 c1 c2} (q0 Gamma1 q1) delta q2 with Gamma1 = C gamma5
  * in the Dirac representation (Sec. 2 Eq. for p,n; Sec. 2 Eqs. for Sigma, Xi,
  * Lambda and X_u, X_d, X_s); the source uses the same real tensors (Sec. 3).
+ * The decuplet Omega- (Sec. 4 footnote: the same operator form with
+ * Gamma1 = C gamma_l, Gamma2 = 1, spatial vector index l) is taken as
+ * eta_l eps (s C gamma_l s) s with eta = (i, 1, -i) for l = x, y, z, the
+ * phase that makes its tensor real like the octet ones.
  * The six-quark matrix element is the Wick determinant
  *
  *   < Q1..Q6 Qbar'6..Qbar'1 > = det_{ij} [ delta(f_i, g_j) S_{f_i}(x_i)[xi_i, eta_j] ]
@@ -60,30 +64,36 @@ typedef double _Complex cplx;
 
 enum { FL_U = 0, FL_D = 1, FL_S = 2 };
 
-/* One baryon operator: quark string flavours and up to three terms
- * coef * eps(c0,c1,c2) * Cg5(a_i, a_j) * delta(ext, a_k). */
+/* One baryon operator: quark string flavours, its diquark matrix Gamma1
+ * (gam: 0 = C gamma5, 1..3 = eta_l C gamma_l) and up to three terms
+ * coef * eps(c0,c1,c2) * Gamma1(a_i, a_j) * delta(ext, a_k). */
 typedef struct {
   const char* name;
   int flav[3];
+  int gam;
   int nterm;
   double coef[3];
   int gi[3], gj[3], dk[3];
 } baryon_t;
 
-enum { B_P, B_N, B_SP, B_SM, B_S0, B_L, B_X0, B_XM, NBARYON };
+enum { B_P, B_N, B_SP, B_SM, B_S0, B_L, B_X0, B_XM, B_OX, B_OY, B_OZ, NBARYON };
 
 static baryon_t g_bar[NBARYON];
 
 /* channel = sink (B1, B2), source (B3, B4); 52 printed channels (Sec. 4,
  * Eqs. GeneralBB_NN ... GeneralBB_XX), the four channels the paper omits
  * because they vanish in the isospin limit, then eight other charge states
- * (pp, nn, S+S+, S-S-, X0X0, X-X-, pS+, nS-, each onto itself). */
+ * (pp, nn, S+S+, S-S-, X0X0, X-X-, pS+, nS-, each onto itself), then the
+ * decuplet channels of the Sec. 4 footnote: Omega_l1 Omega_l2 <- Omega_l3
+ * Omega_l4 at id 64 + 27 l1 + 9 l2 + 3 l3 + l4 and p Omega_l <- p Omega_l'
+ * at id 145 + 3 l + l' (l = 0, 1, 2 for x, y, z). */
 typedef struct { int b[4]; const char* name; } channel_t;
-#define NCHAN_ALL 64
+#define NCHAN_ALL 154
 static channel_t g_chan[NCHAN_ALL];
 static int g_nchan = 0;
 
-static double g_cg5[4][4];
+static double g_gam[4][4][4]; /* [0] = C gamma5, [l] = eta_l C gamma_l */
+static int g_gam_ok = 1;      /* every eta_l C gamma_l came out real */
 static int g_init = 0;
 
 static void add_chan(int b1, int b2, int b3, int b4) {
@@ -95,6 +105,7 @@ static void add_chan(int b1, int b2, int b3, int b4) {
 static void set_bar(int id, const char* name, int f0, int f1, int f2) {
   g_bar[id].name = name;
   g_bar[id].flav[0] = f0; g_bar[id].flav[1] = f1; g_bar[id].flav[2] = f2;
+  g_bar[id].gam = 0;
   g_bar[id].nterm = 0;
 }
 static void add_term(int id, double coef, int gi, int gj, int dk) {
@@ -133,7 +144,19 @@ static void init_tables(void) {
   matmul4(g[3], g[1], cm); /* C = gamma4 gamma2 */
   matmul4(cm, g5, cg5);
   for (int i = 0; i < 4; i++)
-    for (int j = 0; j < 4; j++) g_cg5[i][j] = creal(cg5[i][j]);
+    for (int j = 0; j < 4; j++) g_gam[0][i][j] = creal(cg5[i][j]);
+  /* eta_l C gamma_l, eta = (i, 1, -i): real symmetric matrices */
+  const cplx eta[3] = {I, 1, -I};
+  for (int l = 0; l < 3; l++) {
+    cplx cgl[4][4];
+    matmul4(cm, g[l], cgl);
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) {
+        const cplx v = eta[l] * cgl[i][j];
+        if (cimag(v) != 0.0) g_gam_ok = 0;
+        g_gam[1 + l][i][j] = creal(v);
+      }
+  }
 
   const double r6 = 1.0 / sqrt(6.0), r2 = 1.0 / sqrt(2.0);
   set_bar(B_P, "p", FL_U, FL_D, FL_U);    add_term(B_P, +1.0, 0, 1, 2);
@@ -148,6 +171,16 @@ static void init_tables(void) {
   add_term(B_L, r6, 0, 1, 2); add_term(B_L, r6, 1, 2, 0); add_term(B_L, -2.0 * r6, 2, 0, 1);
   set_bar(B_S0, "Sigma0", FL_D, FL_S, FL_U);
   add_term(B_S0, r2, 0, 1, 2); add_term(B_S0, -r2, 1, 2, 0);
+  /* Omega-_l = eta_l eps (s C gamma_l s) s (Sec. 4 footnote) */
+  {
+    const int ids[3] = {B_OX, B_OY, B_OZ};
+    const char* names[3] = {"Omega_x", "Omega_y", "Omega_z"};
+    for (int l = 0; l < 3; l++) {
+      set_bar(ids[l], names[l], FL_S, FL_S, FL_S);
+      g_bar[ids[l]].gam = 1 + l;
+      add_term(ids[l], 1.0, 0, 1, 2);
+    }
+  }
 
   /* 52 channels in printed order */
   g_nchan = 0;
@@ -187,6 +220,16 @@ static void init_tables(void) {
   add_chan(B_XM, B_XM, B_XM, B_XM);
   add_chan(B_P, B_SP, B_P, B_SP);
   add_chan(B_N, B_SM, B_N, B_SM);
+  /* decuplet channels (Sec. 4 footnote), ids 64..153 */
+  {
+    const int om[3] = {B_OX, B_OY, B_OZ};
+    for (int l1 = 0; l1 < 3; l1++)
+      for (int l2 = 0; l2 < 3; l2++)
+        for (int l3 = 0; l3 < 3; l3++)
+          for (int l4 = 0; l4 < 3; l4++) add_chan(om[l1], om[l2], om[l3], om[l4]);
+    for (int l = 0; l < 3; l++)
+      for (int m = 0; m < 3; m++) add_chan(B_P, om[l], B_P, om[m]);
+  }
   g_init = 1;
 }
 
@@ -209,7 +252,17 @@ const char* oracle_baryon_name(int b) {
 void oracle_cg5(double* out16) {
   init_tables();
   for (int i = 0; i < 4; i++)
-    for (int j = 0; j < 4; j++) out16[4 * i + j] = g_cg5[i][j];
+    for (int j = 0; j < 4; j++) out16[4 * i + j] = g_gam[0][i][j];
+}
+
+/* Diquark matrix gam (0 = C gamma5, 1..3 = eta_l C gamma_l) as used by the
+ * tensors; returns -1 for a bad index or if eta_l C gamma_l was not real. */
+int oracle_gamma(int gam, double* out16) {
+  init_tables();
+  if (gam < 0 || gam > 3 || !g_gam_ok) return -1;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) out16[4 * i + j] = g_gam[gam][i][j];
+  return 0;
 }
 
 /* Dense baryon tensor T_b(ext; q0, q1, q2) over 12^3 (index 144*q0 + 12*q1 + q2,
@@ -223,7 +276,7 @@ static void baryon_tensor(int b, int ext, double* T /* 1728 */) {
     for (int e = 0; e < 6; e++)
       for (int ai = 0; ai < 4; ai++)
         for (int aj = 0; aj < 4; aj++) {
-          double g = g_cg5[ai][aj];
+          double g = g_gam[B->gam][ai][aj];
           if (g == 0.0) continue;
           int sp[3];
           sp[B->gi[t]] = ai; sp[B->gj[t]] = aj; sp[B->dk[t]] = ext;
@@ -372,7 +425,8 @@ static int correlator_impl(int L, const cplx* Su, const cplx* Sd, const cplx* Ss
  * upper Dirac components.
  *   L: spatial extent (V = L^3 sites)
  *   Su, Sd, Ss: propagators [V][12][12] complex128 (Su may equal Sd)
- *   channels[n_ch]: channel ids (0..51 printed order, 52..55 omitted channels)
+ *   channels[n_ch]: channel ids (0..51 printed order, 52..55 omitted channels,
+ *     56..63 other charge states, 64..144 Omega Omega, 145..153 p Omega)
  *   r_list[n_r]: output sites r (site index), or n_r <= 0 for all V sites
  *   out: [n_ch][n_r or V][16] complex128, spin s = a + 2(b + 2(a' + 2 b'))
  * Returns 0, or -1 on a bad argument, -2 on allocation failure.
@@ -400,7 +454,7 @@ static int correlator_impl(int L, const cplx* Su, const cplx* Sd, const cplx* Ss
                            int n_r, const int* r_list, int lower, cplx* out) {
   init_tables();
   const int off = 2 * lower;
-  if (L < 1 || n_ch < 0) return -1;
+  if (L < 1 || n_ch < 0 || !g_gam_ok) return -1;
   for (int c = 0; c < n_ch; c++)
     if (channels[c] < 0 || channels[c] >= g_nchan) return -1;
   const int V = L * L * L;

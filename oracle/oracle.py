@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "bbc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libbbc_oracle.so")
 _lib = None
 
-BARYONS = ["p", "n", "Sigma+", "Sigma-", "Sigma0", "Lambda", "Xi0", "Xi-"]
+BARYONS = ["p", "n", "Sigma+", "Sigma-", "Sigma0", "Lambda", "Xi0", "Xi-", "Omega_x", "Omega_y", "Omega_z"]
 
 
 def build(force: bool = False) -> str:
@@ -54,12 +54,15 @@ def lib():
         L.oracle_wick_count.argtypes = [ctypes.c_int]
         L.oracle_term_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.oracle_cg5.argtypes = [ctypes.c_void_p]
+        L.oracle_gamma.argtypes = [ctypes.c_int, ctypes.c_void_p]
+        L.oracle_gamma.restype = ctypes.c_int
         _lib = L
     return _lib
 
 
 def n_channels() -> int:
-    """52 printed channels followed by the 4 channels omitted in the isospin limit."""
+    """52 printed channels, the 4 omitted in the isospin limit, 8 other charge
+    states, 81 Omega Omega and 9 p Omega channels."""
     return lib().oracle_channel_count()
 
 
@@ -87,6 +90,24 @@ def cg5() -> np.ndarray:
     out = np.zeros(16)
     lib().oracle_cg5(out.ctypes.data)
     return out.reshape(4, 4)
+
+
+def gamma(g: int) -> np.ndarray:
+    """Diquark matrix of the oracle's tensors: 0 = C gamma5, 1..3 = eta_l C gamma_l."""
+    out = np.zeros(16)
+    if lib().oracle_gamma(g, out.ctypes.data) != 0:
+        raise ValueError(f"bad diquark matrix {g}")
+    return out.reshape(4, 4)
+
+
+def omega_channel(l1: int, l2: int, l3: int, l4: int) -> int:
+    """Id of Omega_l1 Omega_l2 <- Omega_l3 Omega_l4 (l = 0, 1, 2 for x, y, z)."""
+    return 64 + 27 * l1 + 9 * l2 + 3 * l3 + l4
+
+
+def p_omega_channel(l: int, lp: int) -> int:
+    """Id of p Omega_l <- p Omega_l'."""
+    return 145 + 3 * l + lp
 
 
 def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
@@ -119,7 +140,8 @@ def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
 #: synthetic hadron masses for the normalisation: the sum of the quark decay
 #: masses of the generator (the paper divides by exp(-(m_B1 + m_B2)(t - t0))).
 def baryon_mass(name: str, m_ud: float, m_s: float) -> float:
-    n_s = {"p": 0, "n": 0, "Sigma+": 1, "Sigma-": 1, "Sigma0": 1, "Lambda": 1, "Xi0": 2, "Xi-": 2}[name]
+    n_s = {"p": 0, "n": 0, "Sigma+": 1, "Sigma-": 1, "Sigma0": 1, "Lambda": 1, "Xi0": 2, "Xi-": 2,
+           "Omega_x": 3, "Omega_y": 3, "Omega_z": 3}[name]
     return (3 - n_s) * m_ud + n_s * m_s
 
 

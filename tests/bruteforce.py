@@ -11,7 +11,9 @@ flavours included) for every pair of non-zero sink and source tensor entries:
 x_1..3 = X + r, x_4..6 = X (Sec. 3 Eq. for the p-Lambda correlator and the
 Wick expansion after it, which is this determinant written out).  The
 operators are the paper's Sec. 2 definitions (p, n: Eq. FieldOperator_N;
-Sigma, Lambda, Xi, X_q: Eqs. FieldOperator_SLXi and FieldOperator_xxx).
+Sigma, Lambda, Xi, X_q: Eqs. FieldOperator_SLXi and FieldOperator_xxx) and
+the decuplet Omega- of the Sec. 4 footnote (Gamma1 = C gamma_l, Gamma2 = 1),
+taken with the phase eta_l = (i, 1, -i) that makes its matrix real.
 Cost grows as (#sink entries) x (#source entries) x V: tiny lattices only.
 """
 from __future__ import annotations
@@ -28,6 +30,8 @@ GAMMA = [np.block([[_Z, -1j * s], [1j * s, _Z]]) for s in _s] + [np.diag([1, 1, 
 GAMMA5 = GAMMA[0] @ GAMMA[1] @ GAMMA[2] @ GAMMA[3]
 CMAT = GAMMA[3] @ GAMMA[1]
 CG5 = CMAT @ GAMMA5
+ETA = [1j, 1.0, -1j]
+CGL = [ETA[l] * CMAT @ GAMMA[l] for l in range(3)]  # eta_l C gamma_l, l = x, y, z
 
 r6, r2 = 1 / np.sqrt(6), 1 / np.sqrt(2)
 # name -> (string flavours, [(coef, gamma slot i, gamma slot j, delta slot k)])
@@ -40,7 +44,12 @@ OPS = {
     "Xi-": ("dss", [(-1.0, 0, 1, 2)]),
     "Lambda": ("dsu", [(r6, 0, 1, 2), (r6, 1, 2, 0), (-2 * r6, 2, 0, 1)]),
     "Sigma0": ("dsu", [(r2, 0, 1, 2), (-r2, 1, 2, 0)]),
+    "Omega_x": ("sss", [(1.0, 0, 1, 2)]),
+    "Omega_y": ("sss", [(1.0, 0, 1, 2)]),
+    "Omega_z": ("sss", [(1.0, 0, 1, 2)]),
 }
+# diquark matrix Gamma1 of each operator (C gamma5 unless listed)
+GAM = {"Omega_x": CGL[0], "Omega_y": CGL[1], "Omega_z": CGL[2]}
 
 
 def _eps():
@@ -54,12 +63,14 @@ def _eps():
 def tensor_entries(name: str, ext: int):
     """Non-zero entries {(q0, q1, q2): value} of the baryon tensor, q = 3*spin + colour."""
     flav, terms = OPS[name]
+    gam = GAM.get(name, CG5)
+    assert np.allclose(gam.imag, 0)
     ent = {}
     for coef, i, j, k in terms:
         for cols, es in _eps():
             for ai in range(4):
                 for aj in range(4):
-                    g = CG5[ai, aj].real
+                    g = gam[ai, aj].real
                     if g == 0:
                         continue
                     sp = [0, 0, 0]
