@@ -39,7 +39,15 @@
  *    Sigma0 Lambda <- Lambda Lambda, Sigma0 Lambda <- Sigma0 Sigma0);
  *    ids 56..63 are other charge states (Sec. 4 footnote), each onto itself:
  *    p p, n n, Sigma+ Sigma+, Sigma- Sigma-, Xi0 Xi0, Xi- Xi-, p Sigma+,
- *    n Sigma-.
+ *    n Sigma-.  Ids 64..153 are decuplet channels (Sec. 4 footnote: the
+ *    same operator form with Gamma1 = C gamma_l, Gamma2 = 1 and a spatial
+ *    vector index l), with Omega-_l = eta_l eps (s^T C gamma_l s) s and
+ *    eta = (i, 1, -i) for l = x, y, z (the phase that makes the operator's
+ *    tensor real, like the octet ones): Omega_l1 Omega_l2 <- Omega_l3
+ *    Omega_l4 at 64 + 27 l1 + 9 l2 + 3 l3 + l4, and p Omega_l <- p Omega_l'
+ *    at 145 + 3 l + l' (l = 0, 1, 2).  The output keeps the 16 spin
+ *    components of the upper (or lower) Dirac indices of each channel.
+ *    One context holds at most 160 channels.
  */
 #ifndef BBC_H
 #define BBC_H
@@ -66,10 +74,15 @@ typedef enum {
   BBC_FP64 = 0,      /* blocks, FFTs, contraction and sums in FP64 */
   BBC_MIXED_FP32 = 1, /* blocks, FFTs and block-pair products in FP32 after an exact
                          per-slice power-of-two rescaling of each propagator; the signed
-                         sum over Wick diagrams and the normalisation in FP64 */
+                         sum over Wick diagrams and the normalisation in FP64.  One fused
+                         kernel per pair {q, -q} when the channel list's block rows and
+                         products fit one CTA's shared memory (the 64 octet ids do);
+                         larger lists (e.g. all 81 Omega Omega ids) run the products and
+                         the Wick sums as two kernels through a product buffer */
   BBC_MIXED_BF16 = 2, /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
                          to bfloat16 (round to nearest even) before the block-pair
-                         products, which multiply and accumulate in FP32 */
+                         products, which multiply and accumulate in FP32; fused kernel
+                         only (EINVAL at creation for channel lists that do not fit it) */
   BBC_DF64 = 3        /* FP64-accurate results from double-float arithmetic
                          (unevaluated sums of two FP32 values, 48-bit significand) on
                          the FP32 pipes: propagators, blocks, FFTs, block-pair products
@@ -226,7 +239,7 @@ bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
  *    one of (1, 256), (2, 256), (2, 512), (4, 512); a CTA keeps the
  *    propagators, diquarks and sink-tensor entries of its sites in shared
  *    memory (configurations that need more than 227 KB are not valid);
- *  fused_warps, fused_chunk (mixed precisions only): warps per CTA (8, 12, 16)
+ *  fused_warps, fused_chunk (mixed precisions with the fused kernel only): warps per CTA (8, 12, 16)
  *    of the fused q-space contraction and the open-index steps per warp unit
  *    (18, 36, 72, 144), or 0: each warp takes one contiguous run of the
  *    batches' steps of equal modelled cost;

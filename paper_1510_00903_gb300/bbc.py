@@ -23,8 +23,26 @@ BBC_LIGHT, BBC_STRANGE = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", -5: "ETIMEOUT", -6: "ENUMERIC"}
 
-#: the 52 channels of Sec. 4 in printed order, then the 4 omitted ones
+#: the 52 channels of Sec. 4 in printed order (ids 52..55: the 4 omitted
+#: ones, 56..63: other charge states)
 CHANNELS_52 = list(range(52))
+#: decuplet channels (Sec. 4 footnote, Gamma1 = C gamma_l): Omega Omega and p Omega
+OMEGA_OMEGA = list(range(64, 145))
+P_OMEGA = list(range(145, 154))
+
+
+def omega_channel(l1: int, l2: int, l3: int, l4: int) -> int:
+    """Id of Omega_l1 Omega_l2 <- Omega_l3 Omega_l4 (l = 0, 1, 2 for x, y, z)."""
+    if not all(0 <= v < 3 for v in (l1, l2, l3, l4)):
+        raise ValueError("vector indices are 0, 1, 2")
+    return 64 + 27 * l1 + 9 * l2 + 3 * l3 + l4
+
+
+def p_omega_channel(l: int, lp: int) -> int:
+    """Id of p Omega_l <- p Omega_l'."""
+    if not (0 <= l < 3 and 0 <= lp < 3):
+        raise ValueError("vector indices are 0, 1, 2")
+    return 145 + 3 * l + lp
 
 
 class BBCError(RuntimeError):

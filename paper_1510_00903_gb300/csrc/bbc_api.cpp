@@ -28,7 +28,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // FP64 storage (plain FP64, and FP64 with double-float products) or FP32
 bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
 size_t cplx_bytes(int prec) { return fp64_storage(prec) ? 16 : 8; }
-bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 products
+bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 products (if they fit one CTA)
 int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP64 ? bbc::RK_F64 : bbc::RK_F32); }
 
 constexpr int kMaxFusedWarps = 16;
@@ -68,9 +68,9 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.kexp = o; o = align256(o + (size_t)slots * 2 * sizeof(int));
   L.blk = o; o = align256(o + (size_t)slots * V * p.n_out * cplx_bytes(c->prec));
   L.blk16 = o; o = align256(o + (c->prec == BBC_MIXED_BF16 ? (size_t)slots * V * p.n_out * 4 : 0));
-  const bool fp64 = fp64_storage(c->prec);  // the FP32 path keeps q-major blocks and no product buffer
-  L.blkf = o; o = align256(o + (fp64 ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
-  L.P = o; o = align256(o + (fp64 ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
+  const bool split = !c->fused;  // the fused path keeps q-major blocks and no product buffer
+  L.blkf = o; o = align256(o + (split ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
+  L.P = o; o = align256(o + (split ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
   L.flag = o; o = align256(o + sizeof(int));
@@ -126,22 +126,6 @@ struct StageScope {
   }
 };
 
-bbc::DevGroups groups_of(const bbc::Plan& p) {
-  bbc::DevGroups g{};
-  g.n = (int)p.groups.size();
-  for (int i = 0; i < g.n; i++) {
-    g.first[i] = p.groups[i].first_row;
-    g.rows[i] = p.groups[i].n_rows;
-    g.fam0[i] = p.groups[i].fam[0];
-    g.fam1[i] = p.groups[i].fam[1];
-  }
-  for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
-  g.z_slots = p.z_slots;
-  g.spin0 = p.spin_offset;
-  for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
-  return g;
-}
-
 // Warp batches and shared-memory bank layout of the fused contraction depend
 // on the channel list only; computed once per list and process.
 struct FusedSchedule {
@@ -181,9 +165,9 @@ std::map<std::pair<std::pair<int, int>, std::vector<int>>, bbc_tuning> g_tuned;
 
 bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
-  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec)) > bbc::kMaxSmemPerBlock)
+  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec), (int)c->plan.diquarks.size()) > bbc::kMaxSmemPerBlock)
     return false;
-  if (fused_path(c->prec)) {
+  if (c->fused) {
     if (!bbc::fused_variant_supported(t.fused_warps, t.fused_steps)) return false;
     bool chunk_ok = false;
     for (int k : kChunkCand) chunk_ok |= k == t.fused_chunk;
@@ -195,7 +179,7 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
 // Warp units of the context's fused configuration, uploaded when a
 // workspace is attached (synchronous: the host vectors are temporaries).
 bbc_status apply_fused_units(bbc_ctx* c) {
-  if (!fused_path(c->prec)) return BBC_OK;
+  if (!c->fused) return BBC_OK;
   const FusedSchedule& f = fused_schedule(c->plan);
   bbc::make_units(c->plan, f.batches, c->tune.fused_warps, c->tune.fused_chunk, &c->wptr, &c->wunits);
   if (c->wunits.size() > c->max_units || (int)c->wptr.size() > kMaxFusedWarps + 1)
@@ -304,6 +288,20 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
       delete c;
       return fail(nullptr, BBC_EINVAL, "internal: fused shared-memory layout is not a valid row map");
     }
+    c->fused = bbc::contract_fused_smem(c->n_slots, (int)c->plan.tasks.size(), prec == BBC_MIXED_BF16) <=
+               bbc::kMaxSmemPerBlock;
+    if (!c->fused) {
+      if (prec == BBC_MIXED_BF16) {
+        delete c;
+        return fail(nullptr, BBC_EINVAL,
+                    "the bfloat16 trial needs the fused contraction, and this channel list's rows and products "
+                    "do not fit one CTA's shared memory: use BBC_MIXED_FP32");
+      }
+      c->batches.clear();
+      c->row_slot.clear();
+      c->n_slots = 0;
+      c->max_units = 0;
+    }
   }
   for (int q = 0; q < c->V; q++) {
     const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
@@ -395,7 +393,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
     bbc::DevTask& d = tasks[i];
     // the fused FP32 kernel addresses its shared-memory copy of the rows: a
     // task side's rows lie in one segment, so slot(off + k) = slot(off) + k
-    const bool slots = fused_path(c->prec);
+    const bool slots = c->fused;
     for (int r = 0; r < 8; r++) {
       d.offA[r] = r < t.nA ? (slots ? c->row_slot[t.offA[r]] : t.offA[r]) : 0;
       d.offB[r] = r < t.nB ? (slots ? c->row_slot[t.offB[r]] : t.offB[r]) : 0;
@@ -509,16 +507,17 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_BUILD);
-    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, groups_of(p),
+    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, bbc::dev_groups(p),
                                 c->d_blk, p.n_out, real_kind(c->prec), c->stream, c->tune.build_sites,
                                 c->tune.build_threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
   {
     StageScope scope(c, BBC_STAGE_FFT_FWD);
-    // FP64: field-major copy for the lanes-over-q products; FP32: in place, q-major
+    // FP64 and unfused FP32: field-major copy for the lanes-over-q products;
+    // fused FP32: in place, q-major
     e = c->prec == BBC_DF64 ? bbc::launch_fft_forward_df(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, c->stream)
-        : fp64              ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
+        : !c->fused         ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
                             : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
     if (c->prec == BBC_MIXED_BF16) {
@@ -540,7 +539,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   const bbc::Plan& p = c->plan;
   const int n_ch = (int)p.channels.size();
   cudaError_t e;
-  if (fp64) {
+  if (!c->fused) {
     const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
     {
       StageScope scope(c, BBC_STAGE_CONTRACT);
@@ -591,7 +590,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   {
     StageScope scope(c, BBC_STAGE_FFT_INV);
     e = c->prec == BBC_DF64 ? bbc::launch_fft_inverse_df(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, c->stream)
-        : fp64 ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
+        : !c->fused ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
                : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
@@ -650,7 +649,7 @@ bbc_status bbc_get_tuning(const bbc_ctx* c, bbc_tuning* t) {
 bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
   if (!c || !t) return BBC_EINVAL;
   bbc_tuning want = *t;
-  if (!fused_path(c->prec)) {  // the FP64 path has no fused kernel to configure
+  if (!c->fused) {  // the FP64 and unfused FP32 paths have no fused kernel to configure
     want.fused_warps = c->tune.fused_warps;
     want.fused_chunk = c->tune.fused_chunk;
     want.fused_steps = c->tune.fused_steps;
@@ -669,8 +668,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
   if (c->slot_loaded[0] != 3) return fail(c, BBC_ESTATE, "slot 0 needs both propagators loaded");
   const bbc::Plan& p = c->plan;
-  const bool fp64 = fp64_storage(c->prec);
-  const bbc::DevGroups g = groups_of(p);
+  const bbc::DevGroups g = bbc::dev_groups(p);
   int n = 0;
   auto record = [&](double v) {
     if (ms && n < cap) ms[n] = v;
@@ -698,7 +696,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   c->slot_built[0] = 0;
   bbc_status st = bbc_build_blocks(c, 1);
   if (st != BBC_OK) return st;
-  if (!fp64) {  // fused contraction: warps per CTA and open-index chunk per warp unit
+  if (c->fused) {  // fused contraction: warps per CTA and open-index chunk per warp unit
     const bool bf16 = c->prec == BBC_MIXED_BF16;
     const char* blk = bf16 ? c->d_blk16 : c->d_blk;
     best_ms = -1.0;

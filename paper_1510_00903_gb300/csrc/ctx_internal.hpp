@@ -44,6 +44,10 @@ struct bbc_ctx {
   int4* d_wunits = nullptr;
   int* d_qlist = nullptr;
   // launch configuration (bbc_set_tuning / bbc_autotune)
+  // FP32 / bfloat16 products in one fused kernel per pair {q, -q}; plans
+  // whose rows and products do not fit one CTA's shared memory take the
+  // unfused FP32 route (field-major FFT, pair products, Wick sums)
+  bool fused = false;
   bbc_tuning tune{1, 256, 16, 18, 1};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
   std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
@@ -80,3 +84,41 @@ struct bbc_ctx {
   }
 };
 
+
+namespace bbc {
+
+static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies, "diquark and family tables");
+
+// The block-build groups of a plan as the kernel reads them: row ranges,
+// families per tensor slot, and the diquarks (flavours, Gamma1) those
+// families are made of, in the plan's shared-memory order.
+inline DevGroups dev_groups(const Plan& p) {
+  DevGroups g{};
+  g.n = (int)p.groups.size();
+  for (int i = 0; i < g.n; i++) {
+    g.first[i] = p.groups[i].first_row;
+    g.rows[i] = p.groups[i].n_rows;
+    g.fam0[i] = p.groups[i].fam[0];
+    g.fam1[i] = p.groups[i].fam[1];
+  }
+  for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
+  g.z_slots = p.z_slots;
+  g.spin0 = p.spin_offset;
+  for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
+  g.n_dq = (int)p.diquarks.size();
+  for (int j = 0; j < g.n_dq; j++) {
+    const int d = p.diquarks[j];
+    g.dq_f0[j] = kDqFlavour[d][0];
+    g.dq_f1[j] = kDqFlavour[d][1];
+    g.dq_gam[j] = kDqGamma[d];
+  }
+  for (int f = 0; f < N_FAMILY; f++) {
+    g.fam_dq[f] = 0;  // families no group reads point at diquark 0
+    for (int j = 0; j < g.n_dq; j++)
+      if (p.diquarks[j] == kFamDiquark[f]) g.fam_dq[f] = j;
+    g.fam_f2[f] = kFamThird[f];
+  }
+  return g;
+}
+
+}  // namespace bbc

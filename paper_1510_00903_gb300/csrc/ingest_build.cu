@@ -55,8 +55,14 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex, cons
 }
 
 // ------------------------------------------------------------ block build
-// C gamma5 (Dirac representation): (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1.
-__constant__ int c_cg5[4][3] = {{0, 1, 1}, {1, 0, -1}, {2, 3, 1}, {3, 2, -1}};
+// Diquark matrices Gamma1 (Dirac representation, C = gamma4 gamma2), four
+// non-zero entries (a0, a1, sign) each: C gamma5 = diag(J, J); the decuplet's
+// i C gamma_1 = diag(s3, -s3), C gamma_2 = diag(1, -1), -i C gamma_3 =
+// diag(s1, -s1) (Sec. 4 footnote, with the phase that makes them real).
+__constant__ int c_gam[4][4][3] = {{{0, 1, 1}, {1, 0, -1}, {2, 3, 1}, {3, 2, -1}},
+                                   {{0, 0, 1}, {1, 1, -1}, {2, 2, -1}, {3, 3, 1}},
+                                   {{0, 0, 1}, {1, 1, 1}, {2, 2, -1}, {3, 3, -1}},
+                                   {{0, 1, 1}, {1, 0, 1}, {2, 3, -1}, {3, 2, -1}}};
 
 // One CTA builds the blocks of SITES consecutive sites with THREADS threads:
 // the propagators, diquarks and tensor entries of every site sit in shared
@@ -68,9 +74,10 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
               const uint32_t* __restrict__ ell, const uint32_t* __restrict__ zneed, DevGroups g,
               cpx<R>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nd = g.n_dq * 432;
   cpx<R>* sS = reinterpret_cast<cpx<R>*>(smem_raw);  // [SITES][2][144]  light, strange
-  cpx<R>* sD = sS + SITES * 288;                      // [SITES][2][432]  diquarks (l,l), (l,s)
-  cpx<R>* sZ = sD + SITES * 864;                      // [SITES][g.z_slots] the tensor entries the rows read
+  cpx<R>* sD = sS + SITES * 288;                      // [SITES][n_dq][432]  the diquarks the families read
+  cpx<R>* sZ = sD + SITES * nd;                       // [SITES][g.z_slots] the tensor entries the rows read
   R* sW = reinterpret_cast<R*>(sZ + SITES * g.z_slots);  // weights -16..15 (no int->float conversion per term)
   const int site0 = blockIdx.x * SITES, slot = blockIdx.y, tid = threadIdx.x;
   const int zs = g.z_slots;
@@ -81,18 +88,19 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
     sS[i] = P[(size_t)(j / 144) * V * 144 + (size_t)(site0 + s) * 144 + j % 144];
   }
   __syncthreads();
-  // D_{l f1}[e0][e1][c2] = sum eps(c0,c1,c2) Cg5(a0,a1) S_l[(a0,c0),e0] S_f1[(a1,c1),e1]
-  for (int ii = tid; ii < SITES * 864; ii += THREADS) {
-    const int s = ii / 864, i = ii - s * 864;
+  // D_{f0 f1}[e0][e1][c2] = sum eps(c0,c1,c2) Gamma1(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1]
+  for (int ii = tid; ii < SITES * nd; ii += THREADS) {
+    const int s = ii / nd, i = ii - s * nd;
     const int dq = i / 432, r = i % 432, e0 = r / 36, e1 = (r / 3) % 12, c2 = r % 3;
     const int ca = (c2 + 1) % 3, cb = (c2 + 2) % 3;  // eps(ca,cb,c2) = +1, eps(cb,ca,c2) = -1
-    const cpx<R>* S0 = sS + s * 288;
-    const cpx<R>* S1 = S0 + 144 * dq;
+    const cpx<R>* S0 = sS + s * 288 + 144 * g.dq_f0[dq];
+    const cpx<R>* S1 = sS + s * 288 + 144 * g.dq_f1[dq];
+    const int gam = g.dq_gam[dq];
     cpx<R> acc(0, 0);
 #pragma unroll
     for (int gi = 0; gi < 4; gi++) {
-      const int a0 = c_cg5[gi][0], a1 = c_cg5[gi][1];
-      const R sg = (R)c_cg5[gi][2];
+      const int a0 = c_gam[gam][gi][0], a1 = c_gam[gam][gi][1];
+      const R sg = (R)c_gam[gam][gi][2];
       cpx<R> t(0, 0);
       cmac(t, S0[(3 * a0 + ca) * 12 + e0], S1[(3 * a1 + cb) * 12 + e1]);
       cpx<R> u(0, 0);
@@ -112,10 +120,8 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
       const int pos = zn & 0x1fff, sl = (zn >> 13) & 1, i = zn >> 14;
       const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
       // F[a][e0][e1][e2] = sum_c2 D[e0][e1][c2] S_f2[(a,c2),e2]
-      const int dq = (fam == 2 || fam == 3) ? 1 : 0;  // LSL, LSS read the (l,s) diquark
-      const int f2 = (fam == 1 || fam == 3) ? 1 : 0;  // LLS, LSS: strange third quark
-      const cpx<R>* D = sD + s * 864 + 432 * dq;
-      const cpx<R>* S2 = sS + s * 288 + 144 * f2;
+      const cpx<R>* D = sD + s * nd + 432 * g.fam_dq[fam];
+      const cpx<R>* S2 = sS + s * 288 + 144 * g.fam_f2[fam];
       const int a = i / 1728 + g.spin0, r = i % 1728, e01 = r / 12, e2 = r % 12;
       cpx<R> acc(0, 0);
 #pragma unroll
@@ -154,9 +160,9 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
   }
 }
 
-size_t block_build_smem(int z_slots, int sites, bool fp64) {  // fp64: 8-byte reals (FP64 or double-float)
+size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq) {  // fp64: 8-byte reals (FP64 or double-float)
   const size_t cb = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
-  return (size_t)sites * (288 + 864 + z_slots) * cb + 32 * (fp64 ? sizeof(double) : sizeof(float));
+  return (size_t)sites * (288 + 432 * (size_t)n_dq + z_slots) * cb + 32 * (fp64 ? sizeof(double) : sizeof(float));
 }
 
 bool build_variant_supported(int sites, int threads) {
@@ -167,7 +173,7 @@ bool build_variant_supported(int sites, int threads) {
 template <typename R, int SITES, int THREADS>
 cudaError_t launch_build_variant(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                  const uint32_t* zneed, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
-  const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8);  // double or double-float
+  const size_t sm = block_build_smem(g.z_slots, SITES, sizeof(R) == 8, g.n_dq);  // double or double-float
   static int granted[64] = {0};
   cudaError_t e = ensure_smem(k_block_build<R, SITES, THREADS>, sm, granted);
   if (e != cudaSuccess) return e;
@@ -181,8 +187,8 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2*
                                const uint32_t* ell, const uint32_t* zneed, const DevGroups& g, void* blk,
                                int n_out, int kind, cudaStream_t st, int sites, int threads) {
   const bool wide = kind != RK_F32;
-  if (!build_variant_supported(sites, threads) || V % sites != 0 ||
-      block_build_smem(g.z_slots, sites, wide) > kMaxSmemPerBlock)
+  if (!build_variant_supported(sites, threads) || V % sites != 0 || g.n_dq < 1 || g.n_dq > kMaxDiquarks ||
+      block_build_smem(g.z_slots, sites, wide, g.n_dq) > kMaxSmemPerBlock)
     return cudaErrorInvalidValue;
 #define BBC_BUILD(S, T)                                                                                            \
   if (sites == S && threads == T)                                                                                  \

@@ -25,6 +25,8 @@ struct WarpBatch {
   int task[32];
 };
 
+constexpr int kMaxDiquarks = 5;   // (l,l) and (l,s) with C gamma5; (s,s) with eta_l C gamma_l, l = x, y, z
+constexpr int kMaxFamilies = 7;   // lll, lls, lsl, lss (C gamma5); sss_x, sss_y, sss_z (vector)
 struct DevGroups {  // block-build groups (rows that read the same tensor families)
   int n;
   int first[8], rows[8], fam0[8], fam1[8];
@@ -32,9 +34,14 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int z_slots;         // shared-memory positions for tensor entries
   int spin0;           // Dirac index of the first external spin component (0 upper, 2 lower)
   int chunk_first[9];  // first 32-row chunk of each group in the lane-interleaved entry table
+  int n_dq;            // diquarks computed per site
+  int dq_f0[kMaxDiquarks], dq_f1[kMaxDiquarks];  // their quark flavours (0 light, 1 strange)
+  int dq_gam[kMaxDiquarks];                      // their Gamma1: 0 = C gamma5, l = eta_l C gamma_l
+  int fam_dq[kMaxFamilies];                      // per family: index of its diquark in shared memory
+  int fam_f2[kMaxFamilies];                      // per family: third quark strange (1) or light (0)
 };
 
-constexpr int kMaxChannels = 64;
+constexpr int kMaxChannels = 160;  // channels of one context (every id fits)
 // Real type of the propagators, blocks and forward transforms: FP32, FP64,
 // or double-float (two FP32 words, FP64-accurate on the FP32 pipes).
 enum RealKind { RK_F32 = 0, RK_F64 = 1, RK_DF = 2 };
@@ -65,7 +72,7 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
 // `sites` consecutive sites per CTA of `threads` threads: (1, 256), (2, 256),
 // (2, 512) or (4, 512) (V a multiple of sites).
 bool build_variant_supported(int sites, int threads);
-size_t block_build_smem(int z_slots, int sites, bool fp64);
+size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq);
 // ell_chunk[c] = (offset, length) of 32-row chunk c in ell (lane-interleaved rows).
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
                                const uint32_t* ell, const uint32_t* zneed, const DevGroups& g,

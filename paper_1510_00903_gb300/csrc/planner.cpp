@@ -29,7 +29,8 @@ namespace bbc {
 namespace {
 
 struct Term {
-  int coef, gi, gj, dk;  // coef * eps * Cg5(a_gi, a_gj) * delta(ext, a_dk)
+  int coef, gi, gj, dk;  // coef * eps * Gamma1(a_gi, a_gj) * delta(ext, a_dk)
+  int g;                 // Gamma1: 0 = C gamma5, 1..3 = eta_l C gamma_l (l = x, y, z)
 };
 struct Op {
   const char* name;
@@ -44,10 +45,13 @@ struct Op {
 // (Eq. FieldOperator_SLXi) with X_u = eps(d Cg5 s)u, X_d = eps(s Cg5 u)d,
 // X_s = eps(u Cg5 d)s (Eq. FieldOperator_xxx) written on the common string
 // (d, s, u) (cyclic reorderings of three quark fields are even).
-enum { OP_P, OP_N, OP_SP, OP_SM, OP_S0, OP_LA, OP_X0, OP_XM };
+// The decuplet Omega-_l of the Sec. 4 footnote (the same operator form with
+// Gamma1 = C gamma_l, Gamma2 = 1) is eta_l eps (s C gamma_l s) s with
+// eta = (i, 1, -i), the phase that makes its matrix real.
+enum { OP_P, OP_N, OP_SP, OP_SM, OP_S0, OP_LA, OP_X0, OP_XM, OP_OX, OP_OY, OP_OZ };
 const double kInvSqrt6 = 0.40824829046386301637;
 const double kInvSqrt2 = 0.70710678118654752440;
-const Op kOps[8] = {
+const Op kOps[11] = {
     {"p", "udu", 1.0, 1, {{1, 0, 1, 2}}, 0},
     {"n", "udd", -1.0, 1, {{1, 0, 1, 2}}, 0},
     {"Sigma+", "usu", -1.0, 1, {{1, 0, 1, 2}}, 1},
@@ -56,10 +60,15 @@ const Op kOps[8] = {
     {"Lambda", "dsu", kInvSqrt6, 3, {{1, 0, 1, 2}, {1, 1, 2, 0}, {-2, 2, 0, 1}}, 1},
     {"Xi0", "uss", 1.0, 1, {{1, 0, 1, 2}}, 2},
     {"Xi-", "dss", -1.0, 1, {{1, 0, 1, 2}}, 2},
+    {"Omega_x", "sss", 1.0, 1, {{1, 0, 1, 2, 1}}, 3},
+    {"Omega_y", "sss", 1.0, 1, {{1, 0, 1, 2, 2}}, 3},
+    {"Omega_z", "sss", 1.0, 1, {{1, 0, 1, 2, 3}}, 3},
 };
 
 // Channels of Sec. 4 (Eqs. GeneralBB_NN .. GeneralBB_XX) in printed order,
-// then the four omitted ones, then eight other charge states.
+// then the four omitted ones, eight other charge states, and the decuplet
+// channels: Omega_l1 Omega_l2 <- Omega_l3 Omega_l4 at 64 + 27 l1 + 9 l2 +
+// 3 l3 + l4, p Omega_l <- p Omega_l' at 145 + 3 l + l'.
 std::vector<std::array<int, 4>> make_channels() {
   std::vector<std::array<int, 4>> c;
   c.push_back({OP_P, OP_N, OP_P, OP_N});
@@ -93,6 +102,13 @@ std::vector<std::array<int, 4>> make_channels() {
   c.push_back({OP_XM, OP_XM, OP_XM, OP_XM});
   c.push_back({OP_P, OP_SP, OP_P, OP_SP});
   c.push_back({OP_N, OP_SM, OP_N, OP_SM});
+  const int om[3] = {OP_OX, OP_OY, OP_OZ};
+  for (int l1 = 0; l1 < 3; l1++)
+    for (int l2 = 0; l2 < 3; l2++)
+      for (int l3 = 0; l3 < 3; l3++)
+        for (int l4 = 0; l4 < 3; l4++) c.push_back({om[l1], om[l2], om[l3], om[l4]});
+  for (int l = 0; l < 3; l++)
+    for (int m = 0; m < 3; m++) c.push_back({OP_P, om[l], OP_P, om[m]});
   return c;
 }
 
@@ -101,9 +117,17 @@ const std::vector<std::array<int, 4>>& channels_table() {
   return t;
 }
 
-// C gamma5 in the Dirac representation (gamma4 = diag(1,1,-1,-1),
-// C = gamma4 gamma2): non-zero entries (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1.
-const int kCg5[4][3] = {{0, 1, +1}, {1, 0, -1}, {2, 3, +1}, {3, 2, -1}};
+// Diquark matrices in the Dirac representation (gamma4 = diag(1,1,-1,-1),
+// gamma_k = [[0, -i s_k], [i s_k, 0]], C = gamma4 gamma2), four non-zero
+// entries each: C gamma_k = diag(s2 s_k, -s2 s_k), so
+//   C gamma5       = diag(J, J), J = -i s2:  (0,1)=+1, (1,0)=-1, (2,3)=+1, (3,2)=-1
+//   i C gamma_1    = diag(s3, -s3)
+//   C gamma_2      = diag(1, -1)
+//   -i C gamma_3   = diag(s1, -s1)
+const int kGam[4][4][3] = {{{0, 1, +1}, {1, 0, -1}, {2, 3, +1}, {3, 2, -1}},
+                           {{0, 0, +1}, {1, 1, -1}, {2, 2, -1}, {3, 3, +1}},
+                           {{0, 0, +1}, {1, 1, +1}, {2, 2, -1}, {3, 3, -1}},
+                           {{0, 1, +1}, {1, 0, +1}, {2, 3, -1}, {3, 2, -1}}};
 // Permutations of three colours and their signs (eps tensor).
 const int kEps[6][4] = {{0, 1, 2, +1}, {1, 2, 0, +1}, {2, 0, 1, +1},
                         {0, 2, 1, -1}, {2, 1, 0, -1}, {1, 0, 2, -1}};
@@ -112,20 +136,29 @@ bool is_strange(char f) { return f == 's'; }
 
 // Family of a sink term and the slot order (Gamma pair, delta) in it.
 // D_sl[x, y] = D_ls[y, x] (eps and Cg5 both antisymmetric), so an (s, l)
-// diquark is read as (l, s) with its two slots swapped.
+// diquark is read as (l, s) with its two slots swapped.  A vector diquark
+// (Gamma1 = eta_l C gamma_l) is an (s, s) one of the Omega family.
 int family_of(const char* flav, const Term& t, int slots[3]) {
   bool a = is_strange(flav[t.gi]), b = is_strange(flav[t.gj]), c = is_strange(flav[t.dk]);
   slots[0] = t.gi; slots[1] = t.gj; slots[2] = t.dk;
+  if (t.g > 0) return (a && b && c) ? F_SSS_X + t.g - 1 : -1;
   if (a && !b) { std::swap(a, b); std::swap(slots[0], slots[1]); }
   if (!a && !b) return c ? F_LLS : F_LLL;
   if (!a && b) return c ? F_LSS : F_LSL;
   return -1;  // (s, s) diquark: not in the octet operators
 }
 
-// Global tensor index; families with two light diquark quarks are symmetric
-// in their first two indices, which are then stored ordered.
-int zindex(int fam, int a, int e0, int e1, int e2) {
+// Global tensor index and sign; families with two identical diquark quarks
+// are stored with their first two indices ordered: symmetric under the
+// exchange for C gamma5 (eps and C gamma5 both antisymmetric), antisymmetric
+// for the symmetric vector matrices (zero at e0 = e1: returns -1).
+int zindex(int fam, int a, int e0, int e1, int e2, int* sgn) {
+  *sgn = 1;
   if ((fam == F_LLL || fam == F_LLS) && e1 < e0) std::swap(e0, e1);
+  if (fam >= F_SSS_X) {
+    if (e0 == e1) return -1;
+    if (e1 < e0) { std::swap(e0, e1); *sgn = -1; }
+  }
   return (fam * 2 + a) * 1728 + e0 * 144 + e1 * 12 + e2;
 }
 
@@ -134,7 +167,7 @@ struct SrcEntry { int eta[3]; int val; };
 std::vector<SrcEntry> source_entries(const Term& t, int ext) {
   std::vector<SrcEntry> out;
   for (auto& e : kEps)
-    for (auto& g : kCg5) {
+    for (auto& g : kGam[t.g]) {
       int sp[3];
       sp[t.gi] = g[0]; sp[t.gj] = g[1]; sp[t.dk] = ext;
       SrcEntry s;
@@ -385,10 +418,10 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
                         int ein[3];
                         for (int s = 0; s < 3; s++) ein[s] = eta[pos[pi[s]]];
                         for (int t = 0; t < sink->nterm; t++) {
-                          int sl[3];
+                          int sl[3], zs;
                           int fam = family_of(sink->flav, sink->t[t], sl);
-                          int z = zindex(fam, a, ein[sl[0]], ein[sl[1]], ein[sl[2]]);
-                          acc[z] += w * pi[3] * sink->t[t].coef;
+                          int z = zindex(fam, a, ein[sl[0]], ein[sl[1]], ein[sl[2]], &zs);
+                          if (z >= 0) acc[z] += zs * w * pi[3] * sink->t[t].coef;
                         }
                       }
                     }
@@ -444,15 +477,20 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
   }
 
   // --- group blocks by the families they read, assign row offsets ---------
-  // group order: lll | lss | lsl | lsl+lls (the last two share slot 0)
-  const std::vector<std::array<int, 2>> gfam = {{F_LLL, -1}, {F_LSS, -1}, {F_LSL, -1}, {F_LSL, F_LLS}};
+  // group order: lll | lss | lsl | lsl+lls (the last two share slot 0) |
+  // sss_x | sss_y | sss_z
+  const std::vector<std::array<int, 2>> gfam = {{F_LLL, -1},   {F_LSS, -1},   {F_LSL, -1},  {F_LSL, F_LLS},
+                                                {F_SSS_X, -1}, {F_SSS_Y, -1}, {F_SSS_Z, -1}};
   std::vector<std::vector<int>> members(gfam.size());
   for (int u = 0; u < (int)ublocks.size(); u++) {
     int m = ublocks[u].fam_mask, g = -1;
     if (m == (1 << F_LLL)) g = 0;
     else if (m == (1 << F_LSS)) g = 1;
     else if (m == (1 << F_LSL)) g = 2;
-    else if ((m & ~((1 << F_LSL) | (1 << F_LLS))) == 0) g = 3;
+    else if ((m & ~((1 << F_LSL) | (1 << F_LLS))) == 0) g = 3;  // (or a block of empty rows)
+    else if (m == (1 << F_SSS_X)) g = 4;
+    else if (m == (1 << F_SSS_Y)) g = 5;
+    else if (m == (1 << F_SSS_Z)) g = 6;
     if (g < 0) { *err = "internal: block reads an unexpected family set"; return false; }
     members[g].push_back(u);
   }
@@ -485,6 +523,15 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
   }
   P.n_out = row;
   P.n_blocks = (int)ublocks.size();
+  // the diquarks the groups' families need, in kind order
+  {
+    bool need[N_DIQUARK] = {false};
+    for (const GroupInfo& gi : P.groups)
+      for (int sl = 0; sl < 2; sl++)
+        if (gi.fam[sl] >= 0) need[kFamDiquark[gi.fam[sl]]] = true;
+    for (int d = 0; d < N_DIQUARK; d++)
+      if (need[d]) P.diquarks.push_back(d);
+  }
   // Compact shared-memory storage of the tensor entries: each group gets
   // positions for the entries its rows read; an entry the previous group left
   // in place (same family in the same slot) keeps its position, so it is

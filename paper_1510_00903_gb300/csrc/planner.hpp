@@ -13,10 +13,21 @@
 
 namespace bbc {
 
-// Sink-tensor families: the diquark (Gamma1 = C gamma5) pair and the third
-// (delta) quark of a baryon term, by numeric flavour (l = u = d, s).
-//   F[a][e0][e1][e2] = sum eps(c0,c1,c2) Cg5(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1] S_f2[(a,c2),e2]
-enum Family { F_LLL = 0, F_LLS = 1, F_LSL = 2, F_LSS = 3, N_FAMILY = 4 };
+// Sink-tensor families: the diquark pair and the third (delta) quark of a
+// baryon term, by numeric flavour (l = u = d, s) and diquark matrix Gamma1
+// (C gamma5 for the octet; eta_l C gamma_l, l = x, y, z, for the decuplet
+// Omega of the Sec. 4 footnote):
+//   F[a][e0][e1][e2] = sum eps(c0,c1,c2) Gamma1(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1] S_f2[(a,c2),e2]
+enum Family { F_LLL = 0, F_LLS = 1, F_LSL = 2, F_LSS = 3, F_SSS_X = 4, F_SSS_Y = 5, F_SSS_Z = 6, N_FAMILY = 7 };
+// Diquarks D[e0][e1][c2] = sum eps Gamma1(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1]
+// the families read: (l, l) and (l, s) with C gamma5, (s, s) with eta_l C gamma_l.
+enum Diquark { DQ_LL5 = 0, DQ_LS5 = 1, DQ_SSX = 2, DQ_SSY = 3, DQ_SSZ = 4, N_DIQUARK = 5 };
+// Diquark and strange third quark (0 / 1) of each family.
+constexpr int kFamDiquark[N_FAMILY] = {DQ_LL5, DQ_LL5, DQ_LS5, DQ_LS5, DQ_SSX, DQ_SSY, DQ_SSZ};
+constexpr int kFamThird[N_FAMILY] = {0, 1, 0, 1, 1, 1, 1};
+// Flavours (0 light, 1 strange) and Gamma1 (0 = C gamma5, l = eta_l C gamma_l) of each diquark.
+constexpr int kDqFlavour[N_DIQUARK][2] = {{0, 0}, {0, 1}, {1, 1}, {1, 1}, {1, 1}};
+constexpr int kDqGamma[N_DIQUARK] = {0, 0, 1, 2, 3};
 constexpr int kFamEntries = 2 * 1728;  // sink spin a in {0,1} (upper) x 12^3
 
 struct GroupInfo {
@@ -62,6 +73,7 @@ struct Plan {
   std::vector<int> chunk_first;      // groups + 1: first chunk of each group
   std::vector<std::pair<int, int>> ell_chunk;  // (offset, length) per chunk
   std::vector<uint32_t> ell;
+  std::vector<int> diquarks;         // the Diquark kinds the groups' families need, in shared-memory order
   std::vector<uint32_t> zneed;       // entries each group computes: pos | slot << 13 | (a*1728 + e0*144 + e1*12 + e2) << 14
   std::vector<int> zneed_first;      // groups + 1 offsets into zneed
   int z_slots = 0;                   // shared-memory positions needed (max over groups)
@@ -77,7 +89,8 @@ struct Plan {
   std::vector<DiagramInfo> diagrams;
 };
 
-// Number of supported channel ids (52 printed + 4 omitted).
+// Number of supported channel ids (52 printed, 4 omitted, 8 other charge
+// states, 81 Omega Omega, 9 p Omega).
 int channel_count();
 // Names of the four baryons of a channel (B1, B2 | B3, B4).
 void channel_names(int id, const char* out[4]);

@@ -168,18 +168,7 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
                            fp64 ? bbc::RK_F64 : bbc::RK_F32, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "convert kernel");
   }
-  bbc::DevGroups g{};
-  g.n = (int)p.groups.size();
-  for (int i = 0; i < g.n; i++) {
-    g.first[i] = p.groups[i].first_row;
-    g.rows[i] = p.groups[i].n_rows;
-    g.fam0[i] = p.groups[i].fam[0];
-    g.fam1[i] = p.groups[i].fam[1];
-  }
-  for (int i = 0; i <= g.n; i++) g.zneed_first[i] = p.zneed_first[i];
-  g.z_slots = p.z_slots;
-  g.spin0 = p.spin_offset;
-  for (int i = 0; i <= g.n; i++) g.chunk_first[i] = p.chunk_first[i];
+  const bbc::DevGroups g = bbc::dev_groups(p);
   e = bbc::launch_block_build(w + L.prop, c->V, 1, (const int2*)(w + L.ell_chunk), (const uint32_t*)(w + L.ell),
                               (const uint32_t*)(w + L.zneed), g, w + L.blk, p.n_out, fp64 ? bbc::RK_F64 : bbc::RK_F32,
                               st, 1, 256);

@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol():
 
 @pytest.mark.parametrize("L,T,t0,ch,prec", [
     (5, 8, 0, [0], 0), (16, 0, 0, [0], 0), (16, 8, 8, [0], 0),
-    (16, 8, 0, [64], 0), (16, 8, 0, [-1], 0), (16, 8, 0, [3, 3], 0), (16, 8, 0, [0], 7)])
+    (16, 8, 0, [154], 0), (16, 8, 0, [-1], 0), (16, 8, 0, [3, 3], 0), (16, 8, 0, [0], 7)])
 def test_create_rejects_bad_arguments(L, T, t0, ch, prec):
     with pytest.raises(bbc.BBCError) as e:
         bbc.bbc_create(L, T, t0, 0.3, 0.4, prec, ch)
@@ -153,3 +153,14 @@ def test_batch_and_check_argument_errors():
         assert e.value.status == bbc.BBC_EINVAL
     finally:
         bbc.bbc_destroy(c)
+
+
+def test_bf16_trial_rejects_channel_lists_beyond_the_fused_kernel():
+    """The bfloat16 trial runs only in the fused contraction; the 90 decuplet
+    ids need more shared memory than one CTA has (the FP32 path then takes
+    the unfused route, which is accepted)."""
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_BF16, bbc.OMEGA_OMEGA + bbc.P_OMEGA)
+    assert e.value.status == bbc.BBC_EINVAL and "BBC_MIXED_FP32" in str(e.value)
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, bbc.OMEGA_OMEGA + bbc.P_OMEGA)
+    bbc.bbc_destroy(c)
