@@ -72,10 +72,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["config2", "batched", "L48"], default="config2",
+    ap.add_argument("--workload", choices=["config2", "batched", "L48", "decuplet"], default="config2",
                     help="config2: 52 channels, 16^3 x 32, FP64 and mixed (default); batched: 8 lattices, "
                          "L in {16,24,32}, T in {32,48,64}, 4 sources each, mixed, one CUDA graph per step; "
-                         "L48: 48^3 x 96, 4 sources, mixed, complex64 propagators streamed from pinned host memory")
+                         "L48: 48^3 x 96, 4 sources, mixed, complex64 propagators streamed from pinned host memory; "
+                         "decuplet: the 90 Omega Omega and p Omega ids, 16^3 x 32, FP64, double-float and mixed")
     ap.add_argument("--error-report", action="store_true",
                     help="per-channel error of the mixed path against the FP64 path (L=32, T=64, t=32), "
                          "the FP64 path checked against the oracle at sampled points")
@@ -219,6 +220,8 @@ def run_ours(args, torch, rank, world, local):
         return run_batched(args, torch, dev, bbc)
     if args.workload == "L48":
         return run_l48(args, torch, dev, bbc)
+    if args.workload == "decuplet":
+        return run_decuplet(args, torch, dev, bbc, synth)
     L, T = L_BENCH, T_BENCH
     V = L ** 3
     if args.single_slice:
@@ -497,6 +500,71 @@ def run_batched(args, torch, dev, bbc):
                      "l2": "no flush: block fields of one slice (>= 241 MB) exceed the 129 MB L2"},
           "graph": {"capture_s": t_cap, "launches_per_step": 1}, "tuning": {str(k): v for k, v in tuned.items()},
           "clocks": sampler.summary()})
+
+
+def run_decuplet(args, torch, dev, bbc, synth):
+    """The decuplet channels of the Sec. 4 footnote: all 81 Omega_l1 Omega_l2 <-
+    Omega_l3 Omega_l4 and 9 p Omega_l <- p Omega_l' ids in one context, 16^3 x 32,
+    one wall source, device-resident complex128 propagators; FP64 (headline),
+    double-float and mixed FP32 (the unfused product route: this list's rows
+    and products exceed one CTA's shared memory)."""
+    from paper_1510_00903_gb300 import shard
+    rank, world, _ = dist_env()
+    L, T = L_BENCH, T_BENCH
+    V = L ** 3
+    chans = bbc.OMEGA_OMEGA + bbc.P_OMEGA
+    F = synth.flavour_set(L, T, 0, M_UD, M_S, **shard.rank_source(rank))
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = torch.empty((T, len(chans), V, 16), dtype=torch.complex128, device=dev)
+    legs = {}
+    sizes = None
+    clocks = None
+    for name, prec in (("fp64", bbc.BBC_FP64), ("df64", bbc.BBC_DF64), ("mixed", bbc.BBC_MIXED_FP32)):
+        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=prec, device=dev, stream=stream)
+        sizes = cor.sizes()
+        tune, _ = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
+        for _ in range(args.warmup):
+            cor.run(Sl, Ss, range(T), out=out, normalised=True)
+        torch.cuda.synchronize(dev)
+        shard.barrier(world)
+        torch.cuda.synchronize(dev)
+        bbc.bbc_enable_stage_timing(cor.ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(dev.index) if name == "fp64" else _Null()
+        with sampler:
+            e0.record(stream)
+            for _ in range(args.steps):
+                cor.run(Sl, Ss, range(T), out=out, normalised=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        shard.barrier(world)
+        torch.cuda.synchronize(dev)
+        if name == "fp64":
+            clocks = sampler.summary()
+        stages = bbc.bbc_stage_timing(cor.ctx)
+        cor.close()
+        ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+        c_ms, c_n = stages["contract"]
+        flop = 8.0 * sizes["pair_macs_per_site"] * V
+        legs[name] = {"value": shard.job_throughput(V * T * len(chans), world, ms), "ms_per_step": ms,
+                      "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                      "contract_ms_per_slice": c_ms / max(c_n, 1),
+                      "contract_tflops": flop / (c_ms / max(c_n, 1) * 1e-3) / 1e12, "tuning": tune}
+    if rank != 0:
+        return
+    fp = legs["fp64"]
+    emit({"metric": "BB correlator site*channels/s", "value": fp["value"], "unit": "site*channels/s",
+          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fp["ms_per_step"],
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": "90 decuplet channels (81 Omega Omega, 9 p Omega), L=16, T=32, one wall source, "
+                                 "complex128 propagators, plain FP64", "L": L, "T": T, "channels": len(chans),
+                     "l2": f"no flush: block fields of one slice ({V * sizes['block_outputs'] * 16 / 1e6:.0f} MB) "
+                           "exceed the 129 MB L2"},
+          "roofline": {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": fp["contract_tflops"],
+                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": fp["contract_tflops"] / FP64_PEAK_TFLOPS,
+                       "traffic": None, "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2070 MHz"},
+          "plan": sizes, "fp64": fp, "df64": legs["df64"], "mixed": legs["mixed"], "clocks": clocks})
 
 
 def run_l48(args, torch, dev, bbc):
