@@ -36,7 +36,7 @@ constexpr int kMaxFusedWarps = 16;
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
-  size_t stage, prop, amax, kexp, blk, blk16, blkf, P, ct, scale, flag, total;
+  size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, ct, scale, flag, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -70,6 +70,8 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.blk16 = o; o = align256(o + (c->prec == BBC_MIXED_BF16 ? (size_t)slots * V * p.n_out * 4 : 0));
   const bool split = !c->fused;  // the fused path keeps q-major blocks and no product buffer
   L.blkf = o; o = align256(o + (split ? (size_t)slots * V * p.n_out * cplx_bytes(c->prec) : 0));
+  // FP64: re + im of every Fourier-space block value (the FP64 products' sums)
+  L.blks = o; o = align256(o + (c->prec == BBC_FP64 ? (size_t)slots * V * p.n_out * sizeof(double) : 0));
   L.P = o; o = align256(o + (split ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
@@ -382,6 +384,7 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_blk = w + L.blk;
   c->d_blk16 = w + L.blk16;
   c->d_blkf = w + L.blkf;
+  c->d_blks = c->prec == BBC_FP64 ? (double*)(w + L.blks) : nullptr;
   c->d_P = w + L.P;
   c->d_ct = w + L.ct;
   c->d_scale = (double*)(w + L.scale);
@@ -517,7 +520,8 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
     // FP64 and unfused FP32: field-major copy for the lanes-over-q products;
     // fused FP32: in place, q-major
     e = c->prec == BBC_DF64 ? bbc::launch_fft_forward_df(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, c->stream)
-        : !c->fused         ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream)
+        : !c->fused         ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream,
+                                                      c->d_blks)
                             : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
     if (c->prec == BBC_MIXED_BF16) {
@@ -541,13 +545,14 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
   cudaError_t e;
   if (!c->fused) {
     const char* blkf = c->d_blkf + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+    const double* blks = c->d_blks ? c->d_blks + (size_t)slot * c->V * p.n_out : nullptr;
     {
       StageScope scope(c, BBC_STAGE_CONTRACT);
       e = c->prec == BBC_DF64
               ? bbc::launch_pair_products_df(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
                                              (int)c->group_ptr.size() - 1, c->d_P, c->stream)
               : bbc::launch_pair_products(blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
-                                          (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream);
+                                          (int)c->group_ptr.size() - 1, c->d_P, fp64, c->stream, blks);
       if (e != cudaSuccess) return cuda_fail(c, e, "pair products");
     }
     {

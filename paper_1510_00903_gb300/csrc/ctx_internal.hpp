@@ -64,6 +64,7 @@ struct bbc_ctx {
   char* d_blk = nullptr;                 // [slots][V][n_out] site-major build output
   char* d_blk16 = nullptr;               // [slots][V][n_out] bfloat16 (re, im) pairs, Fourier space
   char* d_blkf = nullptr;                // [slots][n_out][V] field-major, Fourier space
+  double* d_blks = nullptr;              // [slots][n_out][V] re + im of d_blkf (BBC_FP64)
   char* d_P = nullptr;                   // [n_tasks*16][V] pair products of one slice
   char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators
   double* d_scale = nullptr;             // [kMaxChannels]

@@ -171,14 +171,16 @@ __device__ __forceinline__ void line_base(int N, int axis, int line, int& base, 
 // (the last inverse pass writes the output layout and normalises it).
 // Mode SITE (any axis, in place): data[o][site][n_inner], lanes over inner.
 // Mode SITE2OUT (z axis): in[site][n_ch*16] -> out[ch][r][16] times scale[ch].
-enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4 };
+// Mode FIELD_SUM: FIELD, and sum[o][q] = re + im of every value written (the
+// sums the three-multiplication complex products of the contraction read).
+enum { FFT_SITE2FIELD = 0, FFT_FIELD = 1, FFT_FIELD2OUT = 2, FFT_SITE = 3, FFT_SITE2OUT = 4, FFT_FIELD_SUM = 5 };
 
 // S: storage of the input (and of the output in the in-place modes), R:
 // compute type, O: storage of the output of the last inverse pass.
 template <typename S, typename R, int N, bool INV, int MODE, typename O = S>
 __global__ void __launch_bounds__(256)
 k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer, int n_inner, int axis,
-      const double* __restrict__ scale) {
+      const double* __restrict__ scale, O* __restrict__ sum) {
   const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int lines = N * N;
   const long long V = (long long)N * N * N;
@@ -190,7 +192,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer
     const long long rest = gid / n_inner;
     line = (int)(rest % lines);
     o = rest / lines;
-  } else if (MODE == FFT_FIELD) {
+  } else if (MODE == FFT_FIELD || MODE == FFT_FIELD_SUM) {
     if (gid >= n_outer * lines) return;
     line = (int)(gid % lines);
     o = gid / lines;
@@ -207,7 +209,7 @@ k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer
   cpx<R> v[N];
   if (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) {
     line_fft<S, R, N, INV>(in + (o * V + base) * n_inner + inner, (long long)stride * n_inner, v);
-  } else if (MODE == FFT_FIELD) {
+  } else if (MODE == FFT_FIELD || MODE == FFT_FIELD_SUM) {
     line_fft<S, R, N, INV>(in + o * V + base, stride, v);
   } else {
     line_fft<S, R, N, INV>(in + (o * 16 + inner) * V + base, stride, v);
@@ -220,6 +222,15 @@ k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer
     cpx<O>* p = out + o * V + base;
 #pragma unroll
     for (int k = 0; k < N; k++) p[k * stride] = cpx<O>(v[k]);
+  } else if (MODE == FFT_FIELD_SUM) {
+    cpx<O>* p = out + o * V + base;
+    O* ps = sum + o * V + base;
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+      const cpx<O> w(v[k]);
+      p[k * stride] = w;
+      ps[k * stride] = w.re + w.im;
+    }
   } else if (MODE == FFT_SITE) {
     cpx<O>* p = out + (o * V + base) * n_inner + inner;
 #pragma unroll
@@ -317,17 +328,17 @@ static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner
 
 template <typename S, typename R, int MODE, typename O = S>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
-                                const double* scale, cudaStream_t st) {
+                                const double* scale, cudaStream_t st, O* sum = nullptr) {
   long long per = (MODE == FFT_SITE2FIELD || MODE == FFT_SITE || MODE == FFT_SITE2OUT) ? n_inner
-                  : (MODE == FFT_FIELD ? 1 : 16);
+                  : ((MODE == FFT_FIELD || MODE == FFT_FIELD_SUM) ? 1 : 16);
   long long total = n_outer * (long long)L * L * per;
   unsigned blocks = (unsigned)((total + 255) / 256);
   const cpx<S>* i = (const cpx<S>*)in;
   cpx<O>* o = (cpx<O>*)out;
 #define BBC_FFT_CASE(NN)                                                                                      \
   case NN:                                                                                                    \
-    if (inv) k_fft<S, R, NN, true, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);    \
-    else k_fft<S, R, NN, false, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale);        \
+    if (inv) k_fft<S, R, NN, true, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale, sum); \
+    else k_fft<S, R, NN, false, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale, sum);     \
     break;
   switch (L) {
     BBC_FFT_CASE(2)
@@ -344,16 +355,20 @@ static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_ou
 }
 
 cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
-                               cudaStream_t st) {
+                               cudaStream_t st, double* blk_sum) {
   cudaError_t e;
   if (fp64) {
     e = fft_dispatch<double, double, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
     if (e != cudaSuccess) return e;
-    for (int axis = 1; axis < 3; axis++) {
-      e = fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, axis, false,
-                                                  nullptr, st);
-      if (e != cudaSuccess) return e;
-    }
+    e = fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, 1, false,
+                                                nullptr, st);
+    if (e != cudaSuccess) return e;
+    // z pass; with blk_sum it also writes re + im of every Fourier-space value
+    e = blk_sum ? fft_dispatch<double, double, FFT_FIELD_SUM>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1,
+                                                              2, false, nullptr, st, blk_sum)
+                : fft_dispatch<double, double, FFT_FIELD>(blk_field, blk_field, L, (long long)n_slots * n_rows, 1, 2,
+                                                          false, nullptr, st);
+    if (e != cudaSuccess) return e;
   } else {
     e = fft_dispatch<float, float, FFT_SITE2FIELD>(blk_site, blk_field, L, n_slots, n_rows, 0, false, nullptr, st);
     if (e != cudaSuccess) return e;

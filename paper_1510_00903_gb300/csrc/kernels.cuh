@@ -80,8 +80,10 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2*
 // Forward 3-D FFT of every block field: x pass from the site-major build
 // output blk_site[slots][V][n_rows] into field-major blk_field[slots][n_rows][V],
 // then the y and z passes in place (exp(-i q.x), unnormalised).
+// fp64 with blk_sum: the last pass also writes blk_sum[slots][n_rows][V] =
+// re + im of every FP64 value (read by the FP64 pair products).
 cudaError_t launch_fft_forward(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows, bool fp64,
-                               cudaStream_t st);
+                               cudaStream_t st, double* blk_sum = nullptr);
 // The same transform on double-float blocks in double-float arithmetic; the
 // field-major result holds (re.hi, re.lo, im.hi, im.lo) per value.
 cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, int n_slots, int n_rows,
@@ -119,8 +121,10 @@ cudaError_t launch_fft_inverse(void* ct, void* out, int L, int n_ch, const doubl
 // q-space contraction of one slice from field-major blocks blk_field[n_rows][V]:
 // pair products of every task (warp task groups group_ptr/group_task) into
 // P[n_tasks*16][V] ...
+// fp64: blk_sum (or nullptr) is the re + im plane launch_fft_forward wrote.
 cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
-                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st);
+                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st,
+                                 const double* blk_sum = nullptr);
 // Double-float variant: blk_field and P hold (re.hi, re.lo, im.hi, im.lo)
 // FP32 quadruples per complex value.
 cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,

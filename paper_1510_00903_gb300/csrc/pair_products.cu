@@ -12,10 +12,12 @@ namespace bbc {
 // consecutive q (uniform control flow, coalesced loads from the field-major
 // block storage), every nA x nB spin product of a task accumulated in
 // registers over its open index; P[task*16 + rA*nB + rB][q] is stored for the
-// signed sums.
-template <typename R, int NA, int NB>
-__device__ __forceinline__ void task_products(const cpx<R>* __restrict__ F, long long V, int q, int nq,
-                                              const DevTask& t, cpx<R>* __restrict__ P) {
+// signed sums.  FP64 with Fs: the sums re + im of every value come from the
+// plane the forward FFT wrote (the same FP64 additions, made once per value
+// instead of once per use), so each complex multiply-add is three FMAs.
+template <typename R, int NA, int NB, bool SUMS>
+__device__ __forceinline__ void task_products(const cpx<R>* __restrict__ F, const double* __restrict__ Fs,
+                                              long long V, int q, int nq, const DevTask& t, cpx<R>* __restrict__ P) {
   const int n2 = t.n2, K = t.n1 * n2;
   const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
   cpx<R> acc[NA * NB];
@@ -31,10 +33,23 @@ __device__ __forceinline__ void task_products(const cpx<R>* __restrict__ F, long
     for (int k = 0; k < K; k++) {
       cpx<R> a[NA], b[NB];
       double as[NA], bs[NB];
+      if constexpr (SUMS) {
 #pragma unroll
-      for (int r = 0; r < NA; r++) { a[r] = F[(long long)(t.offA[r] + oA) * V + q]; as[r] = a[r].re + a[r].im; }
+        for (int r = 0; r < NA; r++) {
+          a[r] = F[(long long)(t.offA[r] + oA) * V + q];
+          as[r] = __ldg(Fs + (long long)(t.offA[r] + oA) * V + q);
+        }
 #pragma unroll
-      for (int r = 0; r < NB; r++) { b[r] = F[(long long)(t.offB[r] + oB) * V + nq]; bs[r] = b[r].re + b[r].im; }
+        for (int r = 0; r < NB; r++) {
+          b[r] = F[(long long)(t.offB[r] + oB) * V + nq];
+          bs[r] = __ldg(Fs + (long long)(t.offB[r] + oB) * V + nq);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < NA; r++) { a[r] = F[(long long)(t.offA[r] + oA) * V + q]; as[r] = a[r].re + a[r].im; }
+#pragma unroll
+        for (int r = 0; r < NB; r++) { b[r] = F[(long long)(t.offB[r] + oB) * V + nq]; bs[r] = b[r].re + b[r].im; }
+      }
 #pragma unroll
       for (int ra = 0; ra < NA; ra++)
 #pragma unroll
@@ -71,9 +86,9 @@ __device__ __forceinline__ void task_products(const cpx<R>* __restrict__ F, long
 
 constexpr int kPairWarps = 4;
 
-template <typename R>
+template <typename R, bool SUMS>
 __global__ void __launch_bounds__(32 * kPairWarps)
-k_pair_products(const cpx<R>* __restrict__ F, int L, const DevTask* __restrict__ tasks,
+k_pair_products(const cpx<R>* __restrict__ F, const double* __restrict__ Fs, int L, const DevTask* __restrict__ tasks,
                 const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
                 cpx<R>* __restrict__ P) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -91,9 +106,9 @@ k_pair_products(const cpx<R>* __restrict__ F, int L, const DevTask* __restrict__
     const DevTask t = tasks[ti];
     cpx<R>* p = P + (long long)ti * 16 * V + q;
     const int nA = t.nAnB & 0xff;
-    if (nA == 4) task_products<R, 4, 4>(F, V, q, nq, t, p);
-    else if (nA == 2) task_products<R, 2, 8>(F, V, q, nq, t, p);
-    else task_products<R, 8, 2>(F, V, q, nq, t, p);
+    if (nA == 4) task_products<R, 4, 4, SUMS>(F, Fs, V, q, nq, t, p);
+    else if (nA == 2) task_products<R, 2, 8, SUMS>(F, Fs, V, q, nq, t, p);
+    else task_products<R, 8, 2, SUMS>(F, Fs, V, q, nq, t, p);
   }
 }
 
@@ -117,15 +132,19 @@ k_wick_sums(const cpx<R>* __restrict__ P, int V, const int* __restrict__ cptr, c
 }
 
 cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
-                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st) {
+                                 const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st,
+                                 const double* blk_sum) {
   const int V = L * L * L;
   dim3 g1((n_groups + kPairWarps - 1) / kPairWarps, (V + 31) / 32);
-  if (fp64)
-    k_pair_products<double><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, L, tasks, group_ptr,
-                                                            group_task, n_groups, (cpx<double>*)P);
+  if (fp64 && blk_sum)
+    k_pair_products<double, true><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, blk_sum, L, tasks,
+                                                                  group_ptr, group_task, n_groups, (cpx<double>*)P);
+  else if (fp64)
+    k_pair_products<double, false><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, nullptr, L, tasks,
+                                                                   group_ptr, group_task, n_groups, (cpx<double>*)P);
   else
-    k_pair_products<float><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<float>*)blk_field, L, tasks, group_ptr,
-                                                           group_task, n_groups, (cpx<float>*)P);
+    k_pair_products<float, false><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<float>*)blk_field, nullptr, L, tasks,
+                                                                  group_ptr, group_task, n_groups, (cpx<float>*)P);
   return cudaGetLastError();
 }
 
