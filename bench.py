@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16", "df64"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
     ap.add_argument("--tuning", default=None,
-                    help="launch configuration for --single-slice: sites,threads,warps,chunk[,steps] (as bbc_set_tuning)")
+                    help="launch configuration for --single-slice: sites,threads,warps,chunk[,steps[,pair_groups]] "
+                         "(as bbc_set_tuning)")
     return ap.parse_args()
 
 
@@ -240,7 +241,7 @@ def run_ours(args, torch, rank, world, local):
         if args.tuning:
             v = [int(x) for x in args.tuning.split(",")]
             cor.set_tuning({"build_sites": v[0], "build_threads": v[1], "fused_warps": v[2], "fused_chunk": v[3],
-                            "fused_steps": v[4] if len(v) > 4 else 1})
+                            "fused_steps": v[4] if len(v) > 4 else 1, "pair_groups": v[5] if len(v) > 5 else 0})
         o = cor.run(torch.from_numpy(F1["u"]).to(dev), torch.from_numpy(F1["s"]).to(dev), [t])
         torch.cuda.synchronize(dev)
         print("single slice done", float(o.abs().max()))

@@ -244,28 +244,34 @@ bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
  *    (18, 36, 72, 144), or 0: each warp takes one contiguous run of the
  *    batches' steps of equal modelled cost;
  *  fused_steps: open-index steps whose rows a lane loads before multiplying
- *    (1; or 2 with 8 or 12 warps, which leave the registers for it).
- * A new context starts with (1, 256, 16, 18, 1), or with the configuration
- * bbc_autotune chose earlier in the process for the same L, precision and
- * channel list. */
+ *    (1; or 2 with 8 or 12 warps, which leave the registers for it);
+ *  pair_groups (BBC_FP64, BBC_DF64 and the unfused FP32 route): warp task
+ *    lists of the block-pair products per 32 q (48, 96 or 192); more, shorter
+ *    lists shorten the tail of the launch.
+ * A new context starts with (1, 256, 16, 18, 1, 48) (pair_groups 192 for
+ * BBC_DF64), or with the configuration bbc_autotune chose earlier in the
+ * process for the same L, precision and channel list. */
 typedef struct {
   int build_sites, build_threads;
   int fused_warps, fused_chunk, fused_steps;
+  int pair_groups;
 } bbc_tuning;
 
 bbc_status bbc_get_tuning(const bbc_ctx* ctx, bbc_tuning* out);
 
 /* Set a configuration (EINVAL if unsupported; the fused fields are ignored
- * for BBC_FP64).  Synchronises the context stream when a workspace is
- * attached (uploads the warp schedule).  Not inside a stream capture. */
+ * without the fused kernel, pair_groups with it).  Synchronises the context
+ * stream when a workspace is attached (uploads the warp schedule).  Not
+ * inside a stream capture. */
 bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
 
 /* Autotuner: times every valid candidate configuration with CUDA events on
  * the context stream, `reps` launches each after one untimed launch, on the
  * propagators loaded in slot 0 -- the block-build candidates in the order
- * above, then (mixed precisions) every valid (fused_warps, fused_steps,
+ * above, then (fused kernel) every valid (fused_warps, fused_steps,
  * fused_chunk) in row-major order (warps 8, 12, 16; steps 1, 2; chunks 0, 18,
- * 36, 72, 144) -- keeps the fastest of each kernel, rebuilds slot 0 with
+ * 36, 72, 144), or (otherwise) pair_groups 48, 96, 192 for the block-pair
+ * products -- keeps the fastest of each kernel, rebuilds slot 0 with
  * it, and records it for later contexts with the same L, precision and
  * channel list.  ms[i] (i < cap) receives the average milliseconds per launch
  * of candidate i (-1 for a candidate that is not valid here); *n_tried the

@@ -32,6 +32,9 @@ bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 p
 int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP64 ? bbc::RK_F64 : bbc::RK_F32); }
 
 constexpr int kMaxFusedWarps = 16;
+// Warp task lists of the block-pair products per 32 q (autotuned).
+const int kPairGroupsCand[] = {48, 96, 192};
+constexpr int kMaxPairGroups = 192;
 
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
@@ -47,7 +50,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.ell = o; o = align256(o + sizeof(uint32_t) * p.ell.size());
   L.zneed = o; o = align256(o + sizeof(uint32_t) * p.zneed.size());
   L.tasks = o; o = align256(o + sizeof(bbc::DevTask) * p.tasks.size());
-  L.group_ptr = o; o = align256(o + sizeof(int) * c->group_ptr.size());
+  L.group_ptr = o; o = align256(o + sizeof(int) * (kMaxPairGroups + 1));
   L.group_task = o; o = align256(o + sizeof(int) * c->group_task.size());
   L.cptr = o; o = align256(o + sizeof(int) * p.tcontrib_ptr.size());
   L.citem = o; o = align256(o + sizeof(int) * p.tcontrib_item.size());
@@ -167,6 +170,9 @@ std::map<std::pair<std::pair<int, int>, std::vector<int>>, bbc_tuning> g_tuned;
 
 bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
+  bool groups_ok = false;
+  for (int g : kPairGroupsCand) groups_ok |= g == t.pair_groups;
+  if (!groups_ok) return false;
   if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec), (int)c->plan.diquarks.size()) > bbc::kMaxSmemPerBlock)
     return false;
   if (c->fused) {
@@ -176,6 +182,25 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
     if (!chunk_ok) return false;
   }
   return true;
+}
+
+// Task lists of the block-pair products for the context's pair_groups,
+// uploaded when a workspace is attached (synchronous).
+// (The host lists exist for fused contexts too: the static entry point runs
+// the unfused products for them.)
+bbc_status apply_pair_groups(bbc_ctx* c) {
+  bbc::make_task_groups(c->plan, c->tune.pair_groups, &c->group_ptr, &c->group_task, c->prec == BBC_DF64);
+  if ((int)c->group_ptr.size() > kMaxPairGroups + 1 || c->group_task.size() != c->plan.tasks.size())
+    return fail(c, BBC_EINVAL, "internal: task groups exceed their workspace");
+  if (!c->ws || c->fused) return BBC_OK;
+  cudaError_t e = cudaMemcpyAsync(c->d_group_ptr, c->group_ptr.data(), sizeof(int) * c->group_ptr.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !c->group_task.empty())
+    e = cudaMemcpyAsync(c->d_group_task, c->group_task.data(), sizeof(int) * c->group_task.size(),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "task group upload");
+  return BBC_OK;
 }
 
 // Warp units of the context's fused configuration, uploaded when a
@@ -259,10 +284,10 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
   // warp task groups of the pair products: enough warps per 32 q to fill the
-  // GPU several times over at L = 16 (V/32 q tiles x groups warps)
-  // (the double-float products keep fewer q tiles in flight with more, shorter groups: their
-  // rows stay in L2)
-  bbc::make_task_groups(c->plan, prec == BBC_DF64 ? 192 : 48, &c->group_ptr, &c->group_task, prec == BBC_DF64);
+  // GPU several times over at L = 16 (V/32 q tiles x groups warps); the
+  // double-float products start with more, shorter groups (fewer q tiles in
+  // flight, so their rows stay in L2); the autotuner may choose others
+  c->tune.pair_groups = prec == BBC_DF64 ? 192 : 48;
   // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
   if (fused_path(prec)) {
     try {
@@ -315,9 +340,9 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
     auto it = g_tuned.find({{lat->L, (int)prec}, plan_key(c->plan)});
     if (it != g_tuned.end()) c->tune = it->second;
   }
-  if (apply_fused_units(c) != BBC_OK) {
+  if (apply_fused_units(c) != BBC_OK || apply_pair_groups(c) != BBC_OK) {
     delete c;
-    return fail(nullptr, BBC_EINVAL, "internal: warp units exceed their workspace");
+    return fail(nullptr, BBC_EINVAL, "internal: warp units or task groups exceed their workspace");
   }
   bbc::cubic_orbits(lat->L, c->orb_ptr, c->orb_site);
   {  // the kernel indexes sites through this table: it must be a partition of the lattice
@@ -658,12 +683,19 @@ bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
     want.fused_warps = c->tune.fused_warps;
     want.fused_chunk = c->tune.fused_chunk;
     want.fused_steps = c->tune.fused_steps;
+  } else {  // and the fused kernel has no pair-product task lists
+    want.pair_groups = c->tune.pair_groups;
   }
   if (!tuning_valid(c, want)) return fail(c, BBC_EINVAL, "unsupported launch configuration");
   const bbc_tuning old = c->tune;
   c->tune = want;
-  const bbc_status st = apply_fused_units(c);
-  if (st != BBC_OK) c->tune = old;
+  bbc_status st = apply_fused_units(c);
+  if (st == BBC_OK) st = apply_pair_groups(c);
+  if (st != BBC_OK) {
+    c->tune = old;
+    apply_fused_units(c);
+    apply_pair_groups(c);
+  }
   return st;
 }
 
@@ -729,6 +761,29 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     c->tune.fused_steps = t.fused_steps;
     c->tune.fused_chunk = t.fused_chunk;
     st = apply_fused_units(c);
+    if (st != BBC_OK) return st;
+  } else {  // block-pair products: task lists per 32 q
+    const bool fp64 = fp64_storage(c->prec);
+    const double* blks = c->d_blks;
+    best_ms = -1.0;
+    for (int gv : kPairGroupsCand) {
+      c->tune.pair_groups = gv;
+      st = apply_pair_groups(c);
+      if (st != BBC_OK) return st;
+      const int n_groups = (int)c->group_ptr.size() - 1;
+      const double v = time_launches(c, reps, [&] {
+        return c->prec == BBC_DF64
+                   ? bbc::launch_pair_products_df(c->d_blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                                  n_groups, c->d_P, c->stream)
+                   : bbc::launch_pair_products(c->d_blkf, c->lat.L, c->d_tasks, c->d_group_ptr, c->d_group_task,
+                                               n_groups, c->d_P, fp64, c->stream, blks);
+      });
+      record(v);
+      if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: pair products");
+      if (best_ms < 0 || v < best_ms) { best_ms = v; t.pair_groups = gv; }
+    }
+    c->tune.pair_groups = t.pair_groups;
+    st = apply_pair_groups(c);
     if (st != BBC_OK) return st;
   }
   {

@@ -48,7 +48,7 @@ struct bbc_ctx {
   // whose rows and products do not fit one CTA's shared memory take the
   // unfused FP32 route (field-major FFT, pair products, Wick sums)
   bool fused = false;
-  bbc_tuning tune{1, 256, 16, 18, 1};
+  bbc_tuning tune{1, 256, 16, 18, 1, 48};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
   std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
   int n_slots = 0;

@@ -94,10 +94,10 @@ def test_tuning_defaults_validation_and_autotune_state():
     f = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
     try:
         assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18,
-                                         "fused_steps": 1}
+                                         "fused_steps": 1, "pair_groups": 48}
         bbc.bbc_set_tuning(c, 2, 512, 12, 36, 2)  # no workspace yet: host schedule only
         assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 12, "fused_chunk": 36,
-                                         "fused_steps": 2}
+                                         "fused_steps": 2, "pair_groups": 48}
         for bad in [(3, 256, 16, 18), (1, 512, 16, 18), (4, 256, 16, 18), (1, 256, 10, 18), (1, 256, 16, 20),
                     (1, 256, 16, 18, 2), (1, 256, 8, 18, 3)]:
             with pytest.raises(bbc.BBCError) as e:
@@ -164,3 +164,22 @@ def test_bf16_trial_rejects_channel_lists_beyond_the_fused_kernel():
     assert e.value.status == bbc.BBC_EINVAL and "BBC_MIXED_FP32" in str(e.value)
     c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, bbc.OMEGA_OMEGA + bbc.P_OMEGA)
     bbc.bbc_destroy(c)
+
+
+def test_tuning_pair_groups():
+    """pair_groups defaults to 48 (192 for double-float) and takes 48, 96 or
+    192; other values are rejected (CPU: no workspace attached)."""
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
+    d = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_DF64, [0, 1])
+    try:
+        assert bbc.bbc_get_tuning(c)["pair_groups"] == 48
+        assert bbc.bbc_get_tuning(d)["pair_groups"] == 192
+        bbc.bbc_set_tuning(c, 1, 256, pair_groups=96)
+        assert bbc.bbc_get_tuning(c)["pair_groups"] == 96
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_set_tuning(c, 1, 256, pair_groups=64)
+        assert e.value.status == bbc.BBC_EINVAL
+        assert bbc.bbc_get_tuning(c)["pair_groups"] == 96
+    finally:
+        bbc.bbc_destroy(c)
+        bbc.bbc_destroy(d)

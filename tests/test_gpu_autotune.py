@@ -31,9 +31,11 @@ def test_autotune_then_oracle(precision):
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
-    n_fused = 0 if precision == bbc.BBC_FP64 else 25  # (warps, steps) shapes x 5 chunks
-    assert len(ms) == len(BUILD) + n_fused
+    # FP64: three pair_groups candidates; mixed: (warps, steps) shapes x 5 chunks
+    n_second = 3 if precision == bbc.BBC_FP64 else 25
+    assert len(ms) == len(BUILD) + n_second
     assert all(v > 0 for v in ms[len(BUILD):])
+    assert cfg["pair_groups"] in (48, 96, 192)
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
     # a later context for the same problem starts with the tuned configuration
     cor2 = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
@@ -56,25 +58,27 @@ def test_every_configuration_matches(precision):
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     ref = None
     shapes = [(8, 1), (8, 2), (12, 1), (12, 2), (16, 1)]
-    fused = [(16, 18, 1)] if precision == bbc.BBC_FP64 else [(w, k, st) for w, st in shapes
-                                                              for k in (0, 18, 36, 72, 144)]
+    # FP64: every pair_groups value (the fused fields are ignored there)
+    fused = [(16, 18, 1, g) for g in (48, 96, 192)] if precision == bbc.BBC_FP64 else \
+        [(w, k, st, 48) for w, st in shapes for k in (0, 18, 36, 72, 144)]
     tried = 0
     for sites, threads in BUILD:
-        for warps, chunk, steps in fused:
+        for warps, chunk, steps, groups in fused:
             try:
                 cor.set_tuning({"build_sites": sites, "build_threads": threads, "fused_warps": warps,
-                                "fused_chunk": chunk, "fused_steps": steps})
+                                "fused_chunk": chunk, "fused_steps": steps, "pair_groups": groups})
             except bbc.BBCError:
                 assert precision == bbc.BBC_FP64 and sites == 4  # 365 KB of shared memory
                 continue
             out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
             assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL), (sites, threads, warps,
-                                                                                          chunk, steps)
+                                                                                          chunk, steps, groups)
             if precision == bbc.BBC_FP64:
-                # the build sums every row in the same order whatever the shape
+                # the build sums every row in the same order whatever the shape, and
+                # a task's products do not depend on the list it is in
                 if ref is None:
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == (3 if precision == bbc.BBC_FP64 else 100)
+    assert tried == (9 if precision == bbc.BBC_FP64 else 100)
     cor.close()
