@@ -5,12 +5,14 @@
 //
 // The average over the 24 rotations of a site is the mean over the site's
 // orbit under O (each orbit member is hit 24 / |orbit| times), and it is the
-// same for every member.  So the kernel walks orbits: a 16-lane group (one
-// lane per spin component, one 256-byte record per site) reads every member
-// of one orbit once, writes its spin-state projection R, sums the records in
-// FP64, and writes the projected mean to every member of Ra1.  Every site is
-// read once and written once per output: the HBM minimum.  Both projections
-// are linear and act on different indices, so they commute.
+// same for every member.  So the kernel walks orbits: a 4-lane group (one
+// lane per sink spin pair ab, holding the four source-spin components of a
+// site) reads every member of one orbit once, writes its spin-state
+// projection R (two of the four states are copies, the other two
+// (v2 -+ v1)/sqrt2), sums the records in FP64, and writes the projected mean
+// to every member of Ra1: every site is read once and written once per
+// output (the HBM minimum) with four FP64 instructions per value read.
+// Both projections are linear and act on different indices, so they commute.
 #include <algorithm>
 #include <cstring>
 
@@ -20,14 +22,13 @@ namespace bbc {
 
 // Orbits of the 24 proper cube rotations (signed axis permutations with
 // determinant +1) on the periodic L^3 lattice: orbit k is
-// orb_site[orb_ptr[k] .. orb_ptr[k+1]), every site exactly once.
+// orb_site[orb_ptr[k] .. orb_ptr[k+1]), every site exactly once; orbits come
+// in order of size, so that the orbits a warp walks have equal lengths.
 void cubic_orbits(int L, std::vector<int>& orb_ptr, std::vector<int>& orb_site) {
   const int perms[6][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}, {0, 2, 1}, {2, 1, 0}, {1, 0, 2}};
   const int V = L * L * L;
   std::vector<char> seen(V, 0);
-  orb_ptr.assign(1, 0);
-  orb_site.clear();
-  orb_site.reserve(V);
+  std::vector<std::vector<int>> orbits;
   int img[24];
   for (int r = 0; r < V; r++) {
     if (seen[r]) continue;
@@ -48,82 +49,60 @@ void cubic_orbits(int L, std::vector<int>& orb_ptr, std::vector<int>& orb_site) 
     }
     std::sort(img, img + n);
     const int m = (int)(std::unique(img, img + n) - img);
-    for (int i = 0; i < m; i++) {
-      seen[img[i]] = 1;
-      orb_site.push_back(img[i]);
-    }
+    for (int i = 0; i < m; i++) seen[img[i]] = 1;
+    orbits.emplace_back(img, img + m);
+  }
+  std::stable_sort(orbits.begin(), orbits.end(),
+                   [](const std::vector<int>& a, const std::vector<int>& b) { return a.size() < b.size(); });
+  orb_ptr.assign(1, 0);
+  orb_site.clear();
+  orb_site.reserve(V);
+  for (const auto& o : orbits) {
+    orb_site.insert(orb_site.end(), o.begin(), o.end());
     orb_ptr.push_back((int)orb_site.size());
   }
 }
 
 namespace {
 
-__device__ __forceinline__ cpx<double> shfl(cpx<double> v, int src) {
-  return cpx<double>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
-}
-
-// Lane s of a 16-lane group holds component a + 2b + 4p (p = a' + 2b') of one
-// site; returns state jm = s >> 2 at sink spins ab = s & 3 as c_x v_x + c_y v_y
-// with the lane's two source-spin components and coefficients:
-//   jm = 0: (|ud> - |du>)/sqrt2 = h v_{p=2} - h v_{p=1}   jm = 1: |uu> = v_{p=0}
-//   jm = 2: (|ud> + |du>)/sqrt2 = h v_{p=2} + h v_{p=1}   jm = 3: |dd> = v_{p=3}
-// (one instruction stream for every lane: no divergent FP64 paths).
-__device__ __forceinline__ cpx<double> spin_states(cpx<double> v, int grp, int s) {
-  const int ab = s & 3, jm = s >> 2;
+// The four source spin states of one sink spin pair (index 0 = spin up,
+// p = a' + 2b'): |0 0> = (|ud> - |du>)/sqrt2 = h (v2 - v1), |1 1> = v0,
+// |1 0> = h (v2 + v1), |1 -1> = v3; written at o[4 jm].
+__device__ __forceinline__ void write_states(double2* __restrict__ o, const double2 (&v)[4]) {
   const double h = 0.70710678118654752440;  // 1/sqrt(2)
-  const int px = jm == 1 ? 0 : (jm == 3 ? 3 : 2), py = jm == 1 ? 0 : (jm == 3 ? 3 : 1);
-  const double cx = (jm & 1) ? 1.0 : h, cy = (jm & 1) ? 0.0 : (jm == 0 ? -h : h);
-  const cpx<double> vx = shfl(v, grp + ab + 4 * px), vy = shfl(v, grp + ab + 4 * py);
-  return cpx<double>(fma(cy, vy.re, cx * vx.re), fma(cy, vy.im, cx * vx.im));
+  o[0] = make_double2(h * (v[2].x - v[1].x), h * (v[2].y - v[1].y));
+  o[4] = v[0];
+  o[8] = make_double2(h * (v[2].x + v[1].x), h * (v[2].y + v[1].y));
+  o[12] = v[3];
 }
 
-// C, R, Ra1: [n_fields][V][16] complex128; one 16-lane group per (orbit, field).
+// C, R, Ra1: [n_fields][V][16] complex128 (component ab + 4p); one 4-lane
+// group per (orbit, field), lane ab.
 __global__ void __launch_bounds__(256) k_project(const double2* __restrict__ C, int V, const int* __restrict__ orb_ptr,
                                                  const int* __restrict__ orb_site, int n_orb, double2* __restrict__ R,
                                                  double2* __restrict__ Ra1) {
-  const int s = threadIdx.x & 15, grp = threadIdx.x & 16;
-  const int k = blockIdx.x * 16 + (threadIdx.x >> 4);
-  const size_t fbase = (size_t)blockIdx.y * V * 16;
-  const bool valid = k < n_orb;
-  const int m0 = valid ? orb_ptr[k] : 0, m1 = valid ? orb_ptr[k + 1] : 0;
-  const int n = m1 - m0;
-  const int n_other = __shfl_xor_sync(0xffffffffu, n, 16);
-  const int n_max = n > n_other ? n : n_other;  // both groups of the warp loop together (shuffles)
-  // member sites: lane s of the group holds members s and s + 16 (orbits have
-  // at most 24), broadcast by shuffles so the record loads do not wait on them
-  const int site_a = s < n ? __ldg(&orb_site[m0 + s]) : 0;
-  const int site_b = s + 16 < n ? __ldg(&orb_site[m0 + 16 + s]) : 0;
-  cpx<double> acc(0.0, 0.0);
-  for (int i0 = 0; i0 < n_max; i0 += 8) {
-    cpx<double> v[8];
-    int site[8];
+  const int ab = threadIdx.x & 3;
+  const int k = blockIdx.x * 64 + (threadIdx.x >> 2);
+  if (k >= n_orb) return;  // no warp-wide operation follows
+  const size_t fbase = (size_t)blockIdx.y * V * 16 + ab;
+  const int m0 = __ldg(orb_ptr + k), m1 = __ldg(orb_ptr + k + 1);
+  double2 acc[4];
 #pragma unroll
-    for (int j = 0; j < 8; j++) {  // eight independent record loads in flight
-      const int i = i0 + j;
-      site[j] = __shfl_sync(0xffffffffu, i < 16 ? site_a : site_b, grp + (i & 15));
-      v[j] = cpx<double>(0.0, 0.0);
-      if (i < n) {
-        const double2 d = __ldg(&C[fbase + (size_t)site[j] * 16 + s]);
-        v[j] = cpx<double>(d.x, d.y);
-      }
-    }
+  for (int p = 0; p < 4; p++) acc[p] = make_double2(0.0, 0.0);
+  for (int m = m0; m < m1; m++) {
+    const size_t base = fbase + (size_t)__ldg(orb_site + m) * 16;
+    double2 v[4];
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-      acc.re += v[j].re;
-      acc.im += v[j].im;
-      if (R) {
-        const cpx<double> o = spin_states(v[j], grp, s);
-        if (i0 + j < n) R[fbase + (size_t)site[j] * 16 + s] = make_double2(o.re, o.im);
-      }
-    }
+    for (int p = 0; p < 4; p++) v[p] = __ldg(C + base + 4 * p);
+#pragma unroll
+    for (int p = 0; p < 4; p++) { acc[p].x += v[p].x; acc[p].y += v[p].y; }
+    if (R) write_states(R + base, v);
   }
-  if (!Ra1) return;  // uniform over the grid
-  const double inv = n > 0 ? 1.0 / n : 0.0;
-  const cpx<double> o = spin_states(cpx<double>(acc.re * inv, acc.im * inv), grp, s);
-  for (int i = 0; i < n_max; i++) {
-    const int site = __shfl_sync(0xffffffffu, i < 16 ? site_a : site_b, grp + (i & 15));
-    if (i < n) Ra1[fbase + (size_t)site * 16 + s] = make_double2(o.re, o.im);
-  }
+  if (!Ra1) return;
+  const double inv = 1.0 / (m1 - m0);
+#pragma unroll
+  for (int p = 0; p < 4; p++) acc[p] = make_double2(acc[p].x * inv, acc[p].y * inv);
+  for (int m = m0; m < m1; m++) write_states(Ra1 + fbase + (size_t)__ldg(orb_site + m) * 16, acc);
 }
 
 }  // namespace
@@ -132,7 +111,7 @@ cudaError_t launch_project(const void* C, int L, const int* orb_ptr, const int* 
                            void* R, void* Ra1, cudaStream_t st) {
   if (n_fields <= 0 || n_orb <= 0) return cudaSuccess;
   const int V = L * L * L;
-  dim3 grid((n_orb + 15) / 16, n_fields);
+  dim3 grid((n_orb + 63) / 64, n_fields);
   k_project<<<grid, 256, 0, st>>>((const double2*)C, V, orb_ptr, orb_site, n_orb, (double2*)R, (double2*)Ra1);
   return cudaGetLastError();
 }
