@@ -1,6 +1,7 @@
 // fft.cu -- batched in-register 3-D FFT passes (radix 2 and 3) of the block fields and of the q-space correlators (Sec. 3 Eq. LN.pLLp.FFT)
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <utility>
 
 #include "device_common.cuh"
@@ -58,6 +59,9 @@ __host__ __device__ constexpr int bitrev(int k, int n) {
 
 // One radix-2 stage of span M (butterflies v[k+j], v[k+j+M/2], twiddle
 // exp(-+2 pi i j/M)); stages recurse at compile time so every index is constant.
+// FP32 / FP64 butterflies with a non-trivial twiddle fold the product into
+// FMAs, hi = a + w b (four FMAs), and take lo = 2a - hi (two): six
+// instructions instead of eight, with the same absolute error bound.
 template <typename R, int N, int M, bool INV>
 __device__ __forceinline__ void fft_stage(cpx<R> (&v)[N]) {
 #pragma unroll
@@ -65,18 +69,24 @@ __device__ __forceinline__ void fft_stage(cpx<R> (&v)[N]) {
 #pragma unroll
     for (int j = 0; j < M / 2; j++) {
       const int ti = j * (kTw / M);
-      cpx<R> b = v[k + j + M / 2], t;
-      if (ti == 0) {
-        t = b;
-      } else if (ti == kTw / 4) {
-        t = INV ? cpx<R>(-b.im, b.re) : cpx<R>(b.im, -b.re);
+      const cpx<R> a = v[k + j], b = v[k + j + M / 2];
+      if (ti == 0 || ti == kTw / 4) {
+        const cpx<R> t = ti == 0 ? b : (INV ? cpx<R>(-b.im, b.re) : cpx<R>(b.im, -b.re));
+        v[k + j + M / 2] = a - t;
+        v[k + j] = a + t;
       } else {
         cpx<R> w = twiddle<R>(ti);
         if (INV) w.im = -w.im;
-        t = w * b;
+        if constexpr (std::is_floating_point<R>::value) {
+          const cpx<R> hi(fma(-w.im, b.im, fma(w.re, b.re, a.re)), fma(w.im, b.re, fma(w.re, b.im, a.im)));
+          v[k + j] = hi;
+          v[k + j + M / 2] = cpx<R>(fma((R)2, a.re, -hi.re), fma((R)2, a.im, -hi.im));
+        } else {
+          const cpx<R> t = w * b;
+          v[k + j + M / 2] = a - t;
+          v[k + j] = a + t;
+        }
       }
-      v[k + j + M / 2] = v[k + j] - t;
-      v[k + j] = v[k + j] + t;
     }
   }
   if constexpr (M < N) fft_stage<R, N, 2 * M, INV>(v);
