@@ -357,7 +357,7 @@ def run_ours(args, torch, rank, world, local):
         lower = mixed_leg(bbc.BBC_MIXED_FP32, "lower Dirac components (antibaryons backward in time), mixed FP32",
                           components=bbc.BBC_LOWER)
         mixed = mixed_leg(bbc.BBC_MIXED_FP32, "FP32 blocks, FFTs and products; FP64 Wick sums and normalisation "
-                                              "(per-channel error vs FP64 at L=32: max 5.2e-7)")
+                                              "(per-channel error vs FP64 at L=32: max 4.7e-7)")
         bf16 = mixed_leg(bbc.BBC_MIXED_BF16, "trial: Fourier-space blocks rounded to bfloat16 before the FP32 "
                                              "products (per-channel error vs FP64 at L=32: max 2.9e-3)")
 

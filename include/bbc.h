@@ -246,8 +246,8 @@ bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
  *  fused_steps: open-index steps whose rows a lane loads before multiplying
  *    (1; or 2 with 8 or 12 warps, which leave the registers for it);
  *  pair_groups (BBC_FP64, BBC_DF64 and the unfused FP32 route): warp task
- *    lists of the block-pair products per 32 q (48, 96 or 192); more, shorter
- *    lists shorten the tail of the launch.
+ *    lists of the block-pair products per 32 q (48, 96, 192 or 384); more,
+ *    shorter lists shorten the tail of the launch.
  * A new context starts with (1, 256, 16, 18, 1, 48) (pair_groups 192 for
  * BBC_DF64), or with the configuration bbc_autotune chose earlier in the
  * process for the same L, precision and channel list. */
@@ -270,7 +270,7 @@ bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
  * propagators loaded in slot 0 -- the block-build candidates in the order
  * above, then (fused kernel) every valid (fused_warps, fused_steps,
  * fused_chunk) in row-major order (warps 8, 12, 16; steps 1, 2; chunks 0, 18,
- * 36, 72, 144), or (otherwise) pair_groups 48, 96, 192 for the block-pair
+ * 36, 72, 144), or (otherwise) pair_groups 48, 96, 192, 384 for the block-pair
  * products -- keeps the fastest of each kernel, rebuilds slot 0 with
  * it, and records it for later contexts with the same L, precision and
  * channel list.  ms[i] (i < cap) receives the average milliseconds per launch

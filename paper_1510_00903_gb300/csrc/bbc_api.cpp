@@ -33,8 +33,8 @@ int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP
 
 constexpr int kMaxFusedWarps = 16;
 // Warp task lists of the block-pair products per 32 q (autotuned).
-const int kPairGroupsCand[] = {48, 96, 192};
-constexpr int kMaxPairGroups = 192;
+const int kPairGroupsCand[] = {48, 96, 192, 384};
+constexpr int kMaxPairGroups = 384;
 
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;

@@ -167,8 +167,8 @@ def test_bf16_trial_rejects_channel_lists_beyond_the_fused_kernel():
 
 
 def test_tuning_pair_groups():
-    """pair_groups defaults to 48 (192 for double-float) and takes 48, 96 or
-    192; other values are rejected (CPU: no workspace attached)."""
+    """pair_groups defaults to 48 (192 for double-float) and takes 48, 96, 192
+    or 384; other values are rejected (CPU: no workspace attached)."""
     c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
     d = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_DF64, [0, 1])
     try:

@@ -31,11 +31,11 @@ def test_autotune_then_oracle(precision):
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
-    # FP64: three pair_groups candidates; mixed: (warps, steps) shapes x 5 chunks
-    n_second = 3 if precision == bbc.BBC_FP64 else 25
+    # FP64: four pair_groups candidates; mixed: (warps, steps) shapes x 5 chunks
+    n_second = 4 if precision == bbc.BBC_FP64 else 25
     assert len(ms) == len(BUILD) + n_second
     assert all(v > 0 for v in ms[len(BUILD):])
-    assert cfg["pair_groups"] in (48, 96, 192)
+    assert cfg["pair_groups"] in (48, 96, 192, 384)
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
     # a later context for the same problem starts with the tuned configuration
     cor2 = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
@@ -59,7 +59,7 @@ def test_every_configuration_matches(precision):
     ref = None
     shapes = [(8, 1), (8, 2), (12, 1), (12, 2), (16, 1)]
     # FP64: every pair_groups value (the fused fields are ignored there)
-    fused = [(16, 18, 1, g) for g in (48, 96, 192)] if precision == bbc.BBC_FP64 else \
+    fused = [(16, 18, 1, g) for g in (48, 96, 192, 384)] if precision == bbc.BBC_FP64 else \
         [(w, k, st, 48) for w, st in shapes for k in (0, 18, 36, 72, 144)]
     tried = 0
     for sites, threads in BUILD:
@@ -80,5 +80,5 @@ def test_every_configuration_matches(precision):
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == (9 if precision == bbc.BBC_FP64 else 100)
+    assert tried == (12 if precision == bbc.BBC_FP64 else 100)
     cor.close()
