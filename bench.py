@@ -421,18 +421,33 @@ def measure_projection(torch, cor, C, stream, reps=20):
             "frac": gbs / HBM_PEAK_GBS, "l2": "C, R, Ra1 of all slices (3 x 1.74 GB) exceed the L2"}
 
 
-def error_report(torch, dev, bbc, synth):
+def error_report(torch, dev, bbc, synth, reps=3):
     """Per-channel max |mixed - fp64| / max |fp64| over r and spin on one slice
     of the L=32, T=64 workload; the FP64 result against the oracle at r = 0
-    and two random r for four channels."""
+    and two random r for four channels; and the time of that slice in each
+    precision (launch shapes autotuned on it, device-resident inputs, CUDA
+    events over `reps` runs after one untimed run)."""
     import oracle.oracle as orc
     L, T, t = 32, 64, 32
     F = synth.flavour_set(L, T, 0, M_UD, M_S, seed=3, times=[t])
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
-    res = {}
-    for name, prec in (("fp64", bbc.BBC_FP64), ("mixed", bbc.BBC_MIXED_FP32), ("bf16", bbc.BBC_MIXED_BF16)):
-        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
-        res[name] = cor.run(Sl, Ss, [t], normalised=True)[0].cpu().numpy()
+    res, ms = {}, {}
+    stream = torch.cuda.current_stream(dev)
+    for name, prec in (("fp64", bbc.BBC_FP64), ("df64", bbc.BBC_DF64), ("mixed", bbc.BBC_MIXED_FP32),
+                       ("bf16", bbc.BBC_MIXED_BF16)):
+        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev,
+                              stream=stream)
+        cor.autotune(Sl[0], Ss[0], t=t, reps=2)
+        out = cor.run(Sl, Ss, [t], normalised=True)
+        res[name] = out[0].cpu().numpy()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            cor.run(Sl, Ss, [t], out=out, normalised=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms[name] = e0.elapsed_time(e1) / reps
         cor.close()
     a, b = res["mixed"], res["fp64"]
     scale = np.abs(b).reshape(N_CH, -1).max(axis=1)
@@ -441,12 +456,15 @@ def error_report(torch, dev, bbc, synth):
     chans, r_list = [0, 10, 41, 51], [0, 12345, 30001]
     want = orc.normalise(orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], chans, r_list), chans, t, M_UD, M_S)
     o_err = float((np.abs(b[chans][:, r_list] - want).reshape(len(chans), -1).max(axis=1) / scale[chans]).max())
+    errdf = np.abs(res["df64"] - b).reshape(N_CH, -1).max(axis=1) / scale
     print(json.dumps({"report": "mixed precision error per channel", "L": L, "T": T, "t": t,
                       "metric": "max_{r,s}|C_mixed - C_fp64| / max_{r,s}|C_fp64|",
                       "per_channel": [float(x) for x in err], "max": float(err.max()), "median": float(np.median(err)),
                       "bf16_per_channel": [float(x) for x in err16], "bf16_max": float(err16.max()),
-                      "bf16_median": float(np.median(err16)),
-                      "fp64_vs_oracle_sampled": o_err}), flush=True)
+                      "bf16_median": float(np.median(err16)), "df64_max": float(errdf.max()),
+                      "fp64_vs_oracle_sampled": o_err,
+                      "ms_per_slice": ms, "site_channels_per_s": {k: L ** 3 * N_CH / (v * 1e-3) for k, v in ms.items()},
+                      "speedup_vs_fp64": {k: ms["fp64"] / v for k, v in ms.items()}}), flush=True)
 
 
 def device_propagators(torch, dev, L, T, t0, mass, seed):

@@ -19,8 +19,8 @@ namespace bbc {
 // one shape and one open-index length, k range): lane l takes task l, so
 // control flow is uniform within the warp.  Products accumulate in FP32
 // registers and are added into P[side][task*16 + spin pair] in shared memory.
-// The products are then converted once to FP64 and the signed FP64 sums over
-// Wick diagrams run in the same CTA, writing ct[q][o].
+// The signed FP64 sums over Wick diagrams then run in the same CTA, widening
+// each FP32 product as they read it, and write ct[q][o].
 // Products of one warp unit (open-index steps k0 .. k1-1) of one task: NA x NB
 // complex products for q (A(q) B(-q)) and for -q (A(-q) B(q)) in FP32
 // registers.
@@ -127,9 +127,8 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = n_tasks * 16;                                        // products per side
   using Row = typename std::conditional<BF16, uint2, float4>::type;
-  const size_t region = max((size_t)n_slots * sizeof(Row), (size_t)2 * np * 16);  // rows, later the FP64 products
-  Row* R = reinterpret_cast<Row*>(smem_raw);                                       // [n_slots] (F_q, F_-q)
-  cpx<double>* Pd = reinterpret_cast<cpx<double>*>(smem_raw);         // [2][np], after the products
+  const size_t region = ((size_t)n_slots * sizeof(Row) + 15) & ~(size_t)15;  // P is zeroed as float4
+  Row* R = reinterpret_cast<Row*>(smem_raw);                          // [n_slots] (F_q, F_-q)
   cpx<float>* P = reinterpret_cast<cpx<float>*>(smem_raw + region);   // [2][np]
   const int q = qlist[blockIdx.x];
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
@@ -169,24 +168,20 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
     else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
   }
   __syncthreads();
-  // products to FP64 once (undoing the slot rotation), over the rows' space
+  // signed FP64 sums, each FP32 product widened as it is read (undoing the
+  // slot rotation of its spin pair)
   const int sides = self ? 1 : 2;
-  for (int j = tid; j < sides * np; j += kFusedThreads) {
-    const int side = j / np, it = j - side * np, ti = it >> 4;
-    const cpx<float> v = P[side * np + (ti << 4) + ((it + ti) & 15)];
-    Pd[j] = cpx<double>(widen(v.re), widen(v.im));
-  }
-  __syncthreads();
   for (int j = tid; j < sides * n_outputs; j += kFusedThreads) {
     const int side = j / n_outputs, o = j - side * n_outputs;
-    const cpx<double>* Ps = Pd + side * np;
+    const cpx<float>* Ps = P + side * np;
     cpx<double> acc(0, 0);
     const int c1 = cptr[o + 1];
     for (int c = cptr[o]; c < c1; c++) {
       const double w = ccoef[c];
-      const cpx<double> v = Ps[citem[c]];
-      acc.re = fma(w, v.re, acc.re);
-      acc.im = fma(w, v.im, acc.im);
+      const int item = citem[c], ti = item >> 4;
+      const cpx<float> v = Ps[(ti << 4) + ((item + ti) & 15)];
+      acc.re = fma(w, widen(v.re), acc.re);
+      acc.im = fma(w, widen(v.im), acc.im);
     }
     ct[(size_t)(side ? nq : q) * n_outputs + o] = acc;
   }
@@ -194,7 +189,7 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
 
 size_t contract_fused_smem(int n_slots, int n_tasks, bool bf16) {
   const size_t np = (size_t)n_tasks * 16;
-  return std::max((size_t)n_slots * (bf16 ? 8 : 16), 2 * np * 16) + 2 * np * sizeof(cpx<float>);
+  return (((size_t)n_slots * (bf16 ? 8 : 16) + 15) & ~(size_t)15) + 2 * np * sizeof(cpx<float>);
 }
 
 __global__ void k_to_bf16(const float2* __restrict__ src, __nv_bfloat162* __restrict__ dst, size_t n) {
