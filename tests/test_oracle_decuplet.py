@@ -167,7 +167,7 @@ def test_exchange_antisymmetry():
         b = run(L, S, [orc.omega_channel(l2, l1, l3, l4)]).reshape(L ** 3, 2, 2, 2, 2)
         c = run(L, S, [orc.omega_channel(l1, l2, l4, l3)]).reshape(L ** 3, 2, 2, 2, 2)
         assert close(a, -b[neg].swapaxes(-1, -2))
-        assert close(a, -c.swapaxes(0 + 1, 1 + 1))
+        assert close(a, -c.swapaxes(1, 2))
         assert np.abs(a).max() > 0
 
 
@@ -185,11 +185,13 @@ def test_homogeneity():
         assert close(C2[i], C[i] * lam ** (6 - ns) * mu ** ns)
 
 
-def _two_point(name, S, ext_sink, ext_src):
-    """Three-quark two-point function of one operator on one site, per site:
-    sum T(a; xi) T(a'; eta) det_{ij}[delta(f_i, f_j) S_{f_i}[xi_i, eta_j]]."""
-    flav = bf.OPS[name][0]
-    e1, e3 = bf.tensor_entries(name, ext_sink), bf.tensor_entries(name, ext_src)
+def _two_point(sink, src, S, ext_sink, ext_src):
+    """Three-quark two-point function on one site, per site (sink and source
+    operators of the same flavour string):
+    sum T_sink(a; xi) T_src(a'; eta) det_{ij}[delta(f_i, f_j) S_{f_i}[xi_i, eta_j]]."""
+    flav = bf.OPS[sink][0]
+    assert bf.OPS[src][0] == flav
+    e1, e3 = bf.tensor_entries(sink, ext_sink), bf.tensor_entries(src, ext_src)
     V = S["s"].shape[0]
     out = np.zeros(V, complex)
     for x in range(V):
@@ -209,32 +211,20 @@ def test_p_omega_factorises():
     L = 2
     V = L ** 3
     S = one_slice(L, isospin=False, seed=67)
-    l, m = 2, 0
-    C = run(L, S, [orc.p_omega_channel(l, m)])[0]
-    Gp = {(a, ap): _two_point("p", S, a, ap) for a in range(2) for ap in range(2)}
-    Go = {(b, bp): _two_point("Omega_" + AX[l], S, b, bp) if l == m else None for b in range(2) for bp in range(2)}
-    # l != m: the Omega two-point function with different vector indices
-    if l != m:
-        for b in range(2):
-            for bp in range(2):
-                e2 = bf.tensor_entries("Omega_" + AX[l], b)
-                e4 = bf.tensor_entries("Omega_" + AX[m], bp)
-                g = np.zeros(V, complex)
-                for x in range(V):
-                    for k2, v2 in e2.items():
-                        for k4, v4 in e4.items():
-                            M = np.array([[S["s"][x][k2[i], k4[j]] for j in range(3)] for i in range(3)])
-                            g[x] += v2 * v4 * np.linalg.det(M)
-                Go[(b, bp)] = g
-    want = np.zeros((V, 16), complex)
-    for r in range(V):
-        rx, ry, rz = r % L, (r // L) % L, r // (L * L)
-        for X in range(V):
-            x, y, z = X % L, (X // L) % L, X // (L * L)
-            Xr = (x + rx) % L + L * ((y + ry) % L + L * ((z + rz) % L))
-            for a, b, ap, bp in itertools.product(range(2), repeat=4):
-                want[r, sidx(a, b, ap, bp)] += Gp[(a, ap)][Xr] * Go[(b, bp)][X]
-    assert close(C, want)
+    for l, m in ((2, 0), (1, 1)):
+        C = run(L, S, [orc.p_omega_channel(l, m)])[0]
+        Gp = {(a, ap): _two_point("p", "p", S, a, ap) for a in range(2) for ap in range(2)}
+        Go = {(b, bp): _two_point("Omega_" + AX[l], "Omega_" + AX[m], S, b, bp) for b in range(2) for bp in range(2)}
+        want = np.zeros((V, 16), complex)
+        for r in range(V):
+            rx, ry, rz = r % L, (r // L) % L, r // (L * L)
+            for X in range(V):
+                x, y, z = X % L, (X // L) % L, X // (L * L)
+                Xr = (x + rx) % L + L * ((y + ry) % L + L * ((z + rz) % L))
+                for a, b, ap, bp in itertools.product(range(2), repeat=4):
+                    want[r, sidx(a, b, ap, bp)] += Gp[(a, ap)][Xr] * Go[(b, bp)][X]
+        assert close(C, want)
+        assert np.abs(want).max() > 0
 
 
 def test_plane_wave_closed_form():
@@ -258,3 +248,32 @@ def test_plane_wave_closed_form():
             assert close(C, want)
         else:
             assert np.abs(C).max() <= 1e-12 * V * np.abs(K).max()
+
+
+@pytest.mark.parametrize("ch,spins", [
+    (orc.omega_channel(0, 2, 1, 1), [(2, 3, 2, 3), (3, 3, 3, 2)]),
+    (orc.p_omega_channel(2, 0), [(2, 3, 3, 2)]),
+])
+def test_lower_components_bruteforce(ch, spins):
+    """Lower Dirac components (Sec. 5) of decuplet channels: the determinant
+    expansion with Dirac indices 2, 3 on all four external spinors."""
+    S = one_slice(1, isospin=False, seed=69)
+    B = bf.correlator(1, S, orc.channel_baryons(ch), spins, [0])[0]
+    C = orc.correlator(1, S["u"], S["d"], S["s"], [ch], lower=True)[0, 0, [sidx(*(x - 2 for x in s)) for s in spins]]
+    assert close(C, B)
+
+
+def test_lower_equals_upper_of_block_swapped_propagators():
+    """eta_l C gamma_l = diag(X, -X) changes sign when the upper and lower
+    spin blocks are swapped, and every decuplet channel has an even number
+    of Omega operators (C gamma5 of the proton is unchanged), so
+    C_lower(S) = C_upper(Pi S Pi)."""
+    L = 2
+    S = one_slice(L, isospin=True, seed=70)
+    Pi = np.kron(np.block([[np.zeros((2, 2)), np.eye(2)], [np.eye(2), np.zeros((2, 2))]]), np.eye(3))
+    Sp = {f: Pi @ S[f] @ Pi for f in "uds"}
+    chans = [64, 77, 130, 146, 152]
+    lo = orc.correlator(L, S["u"], S["d"], S["s"], chans, lower=True)
+    up = orc.correlator(L, Sp["u"], Sp["d"], Sp["s"], chans)
+    assert close(lo, up)
+    assert np.abs(lo).max() > 0
