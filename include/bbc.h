@@ -8,8 +8,9 @@
  *   C_ch(r, t) = sum_X < B1_a(X + r, t) B2_b(X, t) Jbar_{B3_a' B4_b'}(t0) >
  *
  * (Sec. 2 Eq. 2 without the spin projection; Sec. 3 for the block/FFT method;
- * Sec. 4 for the 52 channels) from wall-source quark propagators of a light
- * (u = d) and a strange quark.  Per time slice the work is: baryon blocks per
+ * Sec. 4 for the 52 channels; other charge states and the decuplet Omega
+ * channels of the Sec. 4 footnote) from wall-source quark propagators of a
+ * light (u = d) and a strange quark.  Per time slice the work is: baryon blocks per
  * site (Sec. 3, diagrams (i)-(vi); Appendix A aggregation), a forward 3-D FFT
  * of every block field, the q-space contraction of block pairs into channels
  * (Sec. 3 Eq. LN.pLLp.FFT), an inverse 3-D FFT and the normalisation by
