@@ -174,6 +174,30 @@ bbc_status bbc_plan_stats(const bbc_ctx* ctx, int channel_pos, int term3, int te
 bbc_status bbc_plan_sizes(const bbc_ctx* ctx, int* n_blocks, int* n_block_outputs,
                           int* n_pair_items, long long* pair_macs_per_site);
 
+/* The whole contraction plan as host tables (no device work), so that a host
+ * program can evaluate the block algorithm of Sec. 3 step by step (the tests
+ * do, on tiny lattices, against the oracle).  Call once with every array
+ * NULL to receive sizes[5] = {n_out (block rows per site), n_terms,
+ * n_tasks, n_items, n_outputs = 16 x channels}; then again with arrays of
+ * those sizes (the caller owns them; the call fills them all or, if any of
+ * them is NULL, none):
+ *  row_ptr[n_out + 1], terms[n_terms][3]: block row r is the sum over terms
+ *    row_ptr[r] .. row_ptr[r+1]-1 of weight x F_family[index], with
+ *    (family, index, weight) per term; family 0..6 = (l,l,l), (l,l,s),
+ *    (l,s,l), (l,s,s) with Gamma1 = C gamma5 and (s,s,s) with eta_l C
+ *    gamma_l, l = x, y, z; index = a*1728 + e0*144 + e1*12 + e2 of
+ *    F[a][e0][e1][e2] = sum eps(c0,c1,c2) Gamma1(a0,a1) S_f0[(a0,c0),e0]
+ *    S_f1[(a1,c1),e1] S_f2[(a+o,c2),e2] (o = 0 upper, 2 lower components);
+ *  tasks[n_tasks][24] = nA, nB, n1, n2, sA1, sA2, sB1, sB2, offA[8],
+ *    offB[8]: P[16 t + rA nB + rB](q) = sum over i1 < n1, i2 < n2 of
+ *    A[offA[rA] + i1 sA1 + i2 sA2](q) A[offB[rB] + i1 sB1 + i2 sB2](-q), A
+ *    the Fourier transform (exp(-i q.x)) of the block rows;
+ *  out_ptr[n_outputs + 1], items[n_items], coefs[n_items]: Ct[o](q) = sum
+ *    of coefs[c] P[items[c]](q), o = 16 channel_pos + spin; the raw
+ *    correlator is the inverse transform of Ct divided by V. */
+bbc_status bbc_plan_export(const bbc_ctx* ctx, int* sizes, int* row_ptr, int* terms, int* tasks, int* out_ptr,
+                           int* items, double* coefs);
+
 /* Stages timed by bbc_stage_timing. */
 typedef enum {
   BBC_STAGE_INGEST = 0,     /* propagator rescaling copy (per flavour and slice) */

@@ -86,6 +86,7 @@ def _load():
         "bbc_contract": ([P, I, P, I], I),
         "bbc_plan_stats": ([P, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), I], I),
         "bbc_plan_sizes": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(LL)], I),
+        "bbc_plan_export": ([P, P, P, P, P, P, P, P], I),
         "bbc_enable_stage_timing": ([P, I], I),
         "bbc_stage_timing": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(LL)], I),
         "bbc_launch_counts": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)], I),
@@ -176,6 +177,22 @@ def bbc_plan_sizes(ctx):
     a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
     _check(ctx, _lib.bbc_plan_sizes(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
     return {"blocks": a.value, "block_outputs": b.value, "pair_items": c.value, "pair_macs_per_site": d.value}
+
+
+def bbc_plan_export(ctx) -> dict:
+    """The plan's host tables (see include/bbc.h): block rows as weighted sums
+    of sink-tensor entries, the block-pair tasks and the signed sums."""
+    import numpy as np
+    sizes = np.zeros(5, dtype=np.int32)
+    _check(ctx, _lib.bbc_plan_export(ctx, sizes.ctypes.data, None, None, None, None, None, None))
+    n_out, n_terms, n_tasks, n_items, n_outputs = (int(x) for x in sizes)
+    t = {"row_ptr": np.zeros(n_out + 1, np.int32), "terms": np.zeros((n_terms, 3), np.int32),
+         "tasks": np.zeros((n_tasks, 24), np.int32), "out_ptr": np.zeros(n_outputs + 1, np.int32),
+         "items": np.zeros(n_items, np.int32), "coefs": np.zeros(n_items, np.float64)}
+    _check(ctx, _lib.bbc_plan_export(ctx, sizes.ctypes.data, *(t[k].ctypes.data for k in
+                                                               ("row_ptr", "terms", "tasks", "out_ptr", "items",
+                                                                "coefs"))))
+    return t
 
 
 STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise", "wick", "project"]

@@ -841,6 +841,63 @@ bbc_status bbc_plan_sizes(const bbc_ctx* c, int* n_blocks, int* n_block_outputs,
   return BBC_OK;
 }
 
+bbc_status bbc_plan_export(const bbc_ctx* c, int* sizes, int* row_ptr, int* terms, int* tasks, int* out_ptr,
+                           int* items, double* coefs) {
+  if (!c || !sizes) return BBC_EINVAL;
+  const bbc::Plan& p = c->plan;
+  sizes[0] = p.n_out;
+  sizes[1] = (int)p.entries.size();
+  sizes[2] = (int)p.tasks.size();
+  sizes[3] = (int)p.tcontrib_item.size();
+  sizes[4] = (int)p.tcontrib_ptr.size() - 1;
+  if (!row_ptr || !terms || !tasks || !out_ptr || !items || !coefs) return BBC_OK;
+  // the tensor entry behind each shared-memory position, group by group, as
+  // the build kernel lays them out: a group's zneed list fills positions,
+  // and positions of a slot whose family is unchanged carry over
+  std::vector<int> pos_slot(8192, -1), pos_local(8192, -1);
+  int prev_fam[2] = {-1, -1};
+  try {
+    for (size_t g = 0; g < p.groups.size(); g++) {
+      const bbc::GroupInfo& gi = p.groups[g];
+      for (int sl = 0; sl < 2; sl++)
+        if (gi.fam[sl] != prev_fam[sl])
+          for (int k = 0; k < 8192; k++)
+            if (pos_slot[k] == sl) pos_slot[k] = -1;
+      for (int z = p.zneed_first[g]; z < p.zneed_first[g + 1]; z++) {
+        const uint32_t zn = p.zneed[z];
+        const int pos = (int)(zn & 0x1fff);
+        pos_slot[pos] = (int)((zn >> 13) & 1);
+        pos_local[pos] = (int)(zn >> 14);
+      }
+      for (int r = gi.first_row; r < gi.first_row + gi.n_rows; r++)
+        for (int k = p.row_ptr[r]; k < p.row_ptr[r + 1]; k++) {
+          const uint32_t e = p.entries[k];
+          const int pos = (int)(e & 0xffff);
+          if (pos >= 8192 || pos_slot[pos] < 0 || gi.fam[pos_slot[pos]] < 0)
+            return fail(const_cast<bbc_ctx*>(c), BBC_EINVAL, "internal: plan position");
+          terms[3 * k] = gi.fam[pos_slot[pos]];
+          terms[3 * k + 1] = pos_local[pos];
+          terms[3 * k + 2] = (int)(int16_t)(e >> 16);
+        }
+      prev_fam[0] = gi.fam[0];
+      prev_fam[1] = gi.fam[1];
+    }
+  } catch (...) {
+    return fail(const_cast<bbc_ctx*>(c), BBC_ENOMEM, "host allocation failed");
+  }
+  for (int r = 0; r <= p.n_out; r++) row_ptr[r] = p.row_ptr[r];
+  for (size_t t = 0; t < p.tasks.size(); t++) {
+    const bbc::PairTask& k = p.tasks[t];
+    int* o = tasks + 24 * t;
+    o[0] = k.nA; o[1] = k.nB; o[2] = k.n1; o[3] = k.n2;
+    o[4] = k.sA1; o[5] = k.sA2; o[6] = k.sB1; o[7] = k.sB2;
+    for (int i = 0; i < 8; i++) { o[8 + i] = i < k.nA ? k.offA[i] : 0; o[16 + i] = i < k.nB ? k.offB[i] : 0; }
+  }
+  for (size_t i = 0; i < p.tcontrib_ptr.size(); i++) out_ptr[i] = p.tcontrib_ptr[i];
+  for (size_t i = 0; i < p.tcontrib_item.size(); i++) { items[i] = p.tcontrib_item[i]; coefs[i] = p.tcontrib_coef[i]; }
+  return BBC_OK;
+}
+
 bbc_status bbc_enable_stage_timing(bbc_ctx* c, int enable) {
   if (!c) return BBC_EINVAL;
   cudaError_t e = cudaStreamSynchronize(c->stream);
