@@ -38,10 +38,6 @@ __device__ __forceinline__ void cmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
 // sum) and the FMA-based TwoProduct (the exact error of a product, Ogita,
 // Rump and Oishi, SIAM J. Sci. Comput. 26 (2005)).  The _rn intrinsics keep
 // the compiler from contracting the products and sums these rely on.
-struct df64 {
-  float hi, lo;
-};
-
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
@@ -73,8 +69,6 @@ __device__ __forceinline__ void df_renorm(df64acc& acc) {
   acc.s = s;
   acc.e = e;
 }
-
-__device__ __forceinline__ double df_to_double(const df64acc& a) { return (double)a.s + (double)a.e; }
 
 // Double-float real with arithmetic operators, for kernels templated on the
 // real type (block build, FFT).  Addition is the cheap variant (TwoSum of the
