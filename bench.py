@@ -50,10 +50,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 HBM_PEAK_GBS = 6803.8
 
 
-def profiled_traffic(path, kernel_src):
+def profiled_traffic(path, kernel_src, pair_items):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     summary, if the summary was taken on the current kernel source (its
-    SHA-256 is recorded beside the counters); else None."""
+    SHA-256 is recorded beside the counters) and on a plan of the same size
+    (its block-pair products per q); else None."""
     import hashlib
     try:
         text = open(path).read()
@@ -63,10 +64,12 @@ def profiled_traffic(path, kernel_src):
     fields = {}
     for line in text.splitlines():
         line = line.strip().lstrip("-* ").strip()
-        if ":" in line and line.startswith(("kernels_cu_sha256", "dram_bytes_per_launch")):
+        if ":" in line and line.startswith(("kernels_cu_sha256", "dram_bytes_per_launch", "pair_items_per_q")):
             k, v = line.split(":", 1)
             fields[k.strip().strip("`")] = v.strip().strip("`")
     if fields.get("kernels_cu_sha256") != sha or "dram_bytes_per_launch" not in fields:
+        return None
+    if fields.get("pair_items_per_q") != str(pair_items):
         return None
     return float(fields["dram_bytes_per_launch"])
 
@@ -317,7 +320,8 @@ def run_ours(args, torch, rank, world, local):
     achieved = flops_per_launch / (c_avg_ms * 1e-3) / 1e12
     here = os.path.dirname(os.path.abspath(__file__))
     traffic = profiled_traffic(os.path.join(here, "profiles", "k_pair_products_f64_L16_slice.md"),
-                               os.path.join(here, "paper_1510_00903_gb300", "csrc", "pair_products.cu"))
+                               os.path.join(here, "paper_1510_00903_gb300", "csrc", "pair_products.cu"),
+                               sizes["pair_items"])
     roofline = {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": achieved,
                 "peak": FP64_CMAC_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_CMAC_PEAK_TFLOPS,
                 "traffic": traffic, "peak_source": CMAC_PEAK_SOURCE,
@@ -532,8 +536,8 @@ def run_decuplet(args, torch, dev, bbc, synth):
     """The decuplet channels of the Sec. 4 footnote: all 81 Omega_l1 Omega_l2 <-
     Omega_l3 Omega_l4 and 9 p Omega_l <- p Omega_l' ids in one context, 16^3 x 32,
     one wall source, device-resident complex128 propagators; FP64 (headline),
-    double-float and mixed FP32 (the unfused product route: this list's rows
-    and products exceed one CTA's shared memory)."""
+    double-float and mixed FP32 (fused: this list's rows and products fit
+    one CTA's shared memory)."""
     from paper_1510_00903_gb300 import shard
     rank, world, _ = dist_env()
     L, T = L_BENCH, T_BENCH

@@ -77,9 +77,10 @@ typedef enum {
                          per-slice power-of-two rescaling of each propagator; the signed
                          sum over Wick diagrams and the normalisation in FP64.  One fused
                          kernel per pair {q, -q} when the channel list's block rows and
-                         products fit one CTA's shared memory (the 64 octet ids do);
-                         larger lists (e.g. all 81 Omega Omega ids) run the products and
-                         the Wick sums as two kernels through a product buffer */
+                         products fit one CTA's shared memory (the 64 octet ids do, and
+                         so do the 90 decuplet ids); larger lists (e.g. all octet and
+                         decuplet ids together) run the products and the Wick sums as
+                         two kernels through a product buffer */
   BBC_MIXED_BF16 = 2, /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
                          to bfloat16 (round to nearest even) before the block-pair
                          products, which multiply and accumulate in FP32; fused kernel

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <map>
 #include <numeric>
+#include <tuple>
 #include <utility>
 
 namespace bbc {
@@ -646,6 +647,15 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
           const int s2 = n2 > 1 ? side_offset(B, in.vB, in.extB, in.promB, in.oszB, b, e, 0, 1) - t.offB[rB] : 0;
           if (s1 != t.sB1 || s2 != t.sB2) { *err = "internal: row-dependent stride"; return false; }
         }
+      }
+      // The product sums over both open axes, so listing them in the other
+      // order gives the same task: put them in a canonical order before the
+      // identical tasks are merged (the diagrams of one block pair often
+      // meet the two open indices in opposite orders).
+      if (std::tie(t.n2, t.sA2, t.sB2) > std::tie(t.n1, t.sA1, t.sB1)) {
+        std::swap(t.n1, t.n2);
+        std::swap(t.sA1, t.sA2);
+        std::swap(t.sB1, t.sB2);
       }
       std::vector<int> key = {t.nA, t.nB, t.n1, t.n2, t.sA1, t.sA2, t.sB1, t.sB2};
       for (int r = 0; r < t.nA; r++) key.push_back(t.offA[r]);

@@ -156,14 +156,17 @@ def test_batch_and_check_argument_errors():
 
 
 def test_bf16_trial_rejects_channel_lists_beyond_the_fused_kernel():
-    """The bfloat16 trial runs only in the fused contraction; the 90 decuplet
-    ids need more shared memory than one CTA has (the FP32 path then takes
-    the unfused route, which is accepted)."""
+    """The bfloat16 trial runs only in the fused contraction; all 52 octet
+    channels with the 90 decuplet ids need more shared memory than one CTA
+    has (the FP32 path then takes the unfused route, which is accepted).
+    The 90 decuplet ids alone fit."""
+    big = bbc.CHANNELS_52 + bbc.OMEGA_OMEGA + bbc.P_OMEGA
     with pytest.raises(bbc.BBCError) as e:
-        bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_BF16, bbc.OMEGA_OMEGA + bbc.P_OMEGA)
+        bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_BF16, big)
     assert e.value.status == bbc.BBC_EINVAL and "BBC_MIXED_FP32" in str(e.value)
-    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, bbc.OMEGA_OMEGA + bbc.P_OMEGA)
-    bbc.bbc_destroy(c)
+    for prec, chans in ((bbc.BBC_MIXED_FP32, big), (bbc.BBC_MIXED_BF16, bbc.OMEGA_OMEGA + bbc.P_OMEGA)):
+        c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, prec, chans)
+        bbc.bbc_destroy(c)
 
 
 def test_tuning_pair_groups():

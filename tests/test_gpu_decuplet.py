@@ -59,6 +59,18 @@ def test_all_decuplet_channels_L4(decuplet_L4, precision, tol):
     assert np.abs(want).reshape(len(DECUPLET), -1).max(axis=1).min() > 0
 
 
+def test_mixed_unfused_route(decuplet_L4):
+    """All 52 octet channels with the 90 decuplet ids exceed one CTA's shared
+    memory in the fused kernel: mixed FP32 then runs the products and the
+    Wick sums through a product buffer."""
+    L, T, t, F, want_dec = decuplet_L4
+    chans = list(range(52)) + DECUPLET
+    want = np.concatenate([orc.correlator(L, F["u"][t], F["d"][t], F["s"][t], list(range(52))), want_dec])
+    got = _run(L, T, 0, chans, F, t, bbc.BBC_MIXED_FP32)
+    e = _err(got, want)
+    assert e.max() < MIXED_TOL, (e.max(), chans[int(e.argmax())])
+
+
 def test_octet_and_decuplet_in_one_context():
     """Octet and decuplet families side by side in one block build (five
     diquarks per site), with the normalisation of each channel."""
