@@ -24,10 +24,19 @@ def rank_source(rank: int) -> dict:
     return {"seed": 1000 + rank, "source": rank}
 
 
-def barrier(world: int):
+def barrier(world: int, timeout_s: float | None = None):
+    """All ranks meet.  With ``timeout_s`` (gloo process groups) a rank that
+    does not arrive in time -- it failed, exited or hangs between steps --
+    makes the call raise RuntimeError naming it, instead of waiting forever:
+    the surviving ranks learn of the failure on the host before their next
+    launch."""
     if world > 1:
         import torch.distributed as dist
-        dist.barrier()
+        if timeout_s is None:
+            dist.barrier()
+        else:
+            import datetime
+            dist.monitored_barrier(timeout=datetime.timedelta(seconds=timeout_s))
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:

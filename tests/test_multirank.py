@@ -1,6 +1,7 @@
 """Multi-rank host logic on CPU: two gloo ranks take disjoint shares of the
 independent units, draw independent wall-source propagators, agree on the
-slowest rank's time and on the whole-job throughput."""
+slowest rank's time and on the whole-job throughput; a rank that fails
+between steps is detected by the other at the next barrier."""
 import os
 import socket
 
@@ -75,3 +76,43 @@ def test_shard_single_rank_and_errors():
         shard.job_throughput(1, 1, 0.0)
     k0, k1 = shard.rank_source(0), shard.rank_source(1)
     assert k0 != k1 and np.isscalar(k0["seed"])
+
+
+def _failing_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1510_00903_gb300 import shard
+    shard.barrier(world, timeout_s=30)      # step 1: both ranks arrive
+
+    def report_and_exit(msg, code):
+        q.put((rank, msg))
+        q.close()
+        q.join_thread()                     # the message is out before the process ends
+        os._exit(code)
+
+    if rank == 1:
+        report_and_exit("failed", 3)        # fails between steps, never reaches the next barrier
+    try:
+        shard.barrier(world, timeout_s=3)
+        msg = "no error"
+    except RuntimeError as e:
+        msg = "detected: " + str(e)
+    report_and_exit(msg, 0)
+
+
+def test_failed_rank_is_detected_at_the_next_barrier():
+    """Host-side failure detection (no GPU): rank 1 exits between steps; rank 0's
+    monitored barrier ends with an error naming rank 1 instead of hanging."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "failed"
+    assert res[0].startswith("detected") and "1" in res[0], res[0]
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
