@@ -195,6 +195,35 @@ def bbc_plan_export(ctx) -> dict:
     return t
 
 
+def tuning_cache_key(device_name: str, L: int, precision: int, components: int, channels) -> str:
+    """Key of a tuned launch configuration: it depends on the GPU model and on
+    the problem (lattice extent, precision, spin components, channel list)."""
+    return f"{device_name}|L={L}|prec={precision}|comp={components}|ch={','.join(str(int(c)) for c in channels)}"
+
+
+def tuning_cache_load(path: str) -> dict:
+    """{key: configuration} from a cache file ({} if it does not exist or is not valid JSON)."""
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return data if isinstance(data, dict) else {}
+
+
+def tuning_cache_store(path: str, key: str, cfg: dict):
+    """Add one configuration to a cache file (written to a temporary file,
+    then renamed over the old one, so a reader never sees half a file)."""
+    import json
+    data = tuning_cache_load(path)
+    data[key] = {k: int(v) for k, v in cfg.items()}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 STAGES = ["ingest", "build", "fft_fwd", "contract", "fft_inv", "normalise", "wick", "project"]
 
 
@@ -466,17 +495,35 @@ class Correlators:
             cur.wait_stream(self.stream)
         return out_host
 
-    def autotune(self, S_light, S_strange, t: int = 0, reps: int = 5):
+    def autotune(self, S_light, S_strange, t: int = 0, reps: int = 5, cache: str | None = None):
         """Load slice t into slot 0 and run the autotuner (bbc_autotune);
-        returns (configuration, ms per candidate)."""
+        returns (configuration, ms per candidate).
+
+        cache: a JSON file of tuned configurations (default: the
+        BBC_AUTOTUNE_CACHE environment variable, if set).  A configuration
+        stored there for this GPU model, L, precision, spin components and
+        channel list is applied without timing (ms is then empty); otherwise
+        the tuned one is added to it."""
         torch = self.torch
+        path = cache if cache is not None else os.environ.get("BBC_AUTOTUNE_CACHE")
+        key = None
+        if path:
+            key = tuning_cache_key(torch.cuda.get_device_name(self.device), self.L, self.precision,
+                                   self.components, self.channels)
+            cached = tuning_cache_load(path).get(key)
+            if cached is not None:
+                self.set_tuning(cached)
+                return self.tuning(), []
         cur = torch.cuda.current_stream(self.device)
         if cur.cuda_stream != self.stream.cuda_stream:
             self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
             self.load(BBC_LIGHT, 0, t, S_light)
             self.load(BBC_STRANGE, 0, t, S_strange)
-            return bbc_autotune(self.ctx, reps)
+            cfg, ms = bbc_autotune(self.ctx, reps)
+        if path:
+            tuning_cache_store(path, key, cfg)
+        return cfg, ms
 
     def tuning(self) -> dict:
         return bbc_get_tuning(self.ctx)

@@ -186,3 +186,30 @@ def test_tuning_pair_groups():
     finally:
         bbc.bbc_destroy(c)
         bbc.bbc_destroy(d)
+
+
+def test_tuning_cache_file(tmp_path):
+    """The autotune cache: keyed by GPU model and problem, JSON round trip,
+    atomic replace, a missing or broken file reads as empty, and a cached
+    configuration applies to a context (CPU: no workspace needed)."""
+    path = str(tmp_path / "tune.json")
+    assert bbc.tuning_cache_load(path) == {}
+    k1 = bbc.tuning_cache_key("GB300", 16, bbc.BBC_FP64, bbc.BBC_UPPER, range(52))
+    k2 = bbc.tuning_cache_key("GB300", 16, bbc.BBC_MIXED_FP32, bbc.BBC_UPPER, range(52))
+    assert k1 != k2 and k1 != bbc.tuning_cache_key("B200", 16, bbc.BBC_FP64, bbc.BBC_UPPER, range(52))
+    cfg = {"build_sites": 2, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18, "fused_steps": 1,
+           "pair_groups": 96}
+    bbc.tuning_cache_store(path, k1, cfg)
+    bbc.tuning_cache_store(path, k2, dict(cfg, fused_chunk=72))
+    data = bbc.tuning_cache_load(path)
+    assert data[k1] == cfg and data[k2]["fused_chunk"] == 72
+    assert not any(n.startswith("tune.json.tmp") for n in os.listdir(tmp_path))
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
+    try:
+        bbc.bbc_set_tuning(c, **{k: v for k, v in data[k1].items()})
+        assert bbc.bbc_get_tuning(c)["pair_groups"] == 96 and bbc.bbc_get_tuning(c)["build_sites"] == 2
+    finally:
+        bbc.bbc_destroy(c)
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert bbc.tuning_cache_load(path) == {}
