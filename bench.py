@@ -389,6 +389,13 @@ def run_ours(args, torch, rank, world, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "stage_ms_per_step": stage_ms,
+        # the paper's split of a step (Sec. 5, Table ElapsedTime): Step-1 = blocks
+        # and forward FFT, Step-2 = contraction and inverse FFT (best 32-node BG/Q
+        # split: 6 s + 13 s)
+        "paper_steps_ms": {"step1": stage_ms.get("ingest", 0) + stage_ms.get("build", 0) + stage_ms.get("fft_fwd", 0),
+                           "step2": stage_ms.get("contract", 0) + stage_ms.get("wick", 0) + stage_ms.get("fft_inv", 0)
+                           + stage_ms.get("normalise", 0),
+                           "paper_best_bgq_s": {"step1": 6, "step2": 13}},
         "plan": sizes,
         "tuning": {"chosen": tune_fp64, "autotune_ms": tune_fp64_ms},
         "df64": df64,
