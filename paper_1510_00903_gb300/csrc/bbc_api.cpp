@@ -83,7 +83,7 @@ Layout layout(const bbc_ctx* c, int slots) {
   return L;
 }
 
-bbc_status fail(bbc_ctx* c, bbc_status s, const std::string& m) {
+bbc_status fail(const bbc_ctx* c, bbc_status s, const std::string& m) {
   if (c) c->err = m;
   else g_create_error = m;
   return s;
@@ -874,7 +874,7 @@ bbc_status bbc_plan_export(const bbc_ctx* c, int* sizes, int* row_ptr, int* term
           const uint32_t e = p.entries[k];
           const int pos = (int)(e & 0xffff);
           if (pos >= 8192 || pos_slot[pos] < 0 || gi.fam[pos_slot[pos]] < 0)
-            return fail(const_cast<bbc_ctx*>(c), BBC_EINVAL, "internal: plan position");
+            return fail(c, BBC_EINVAL, "internal: plan position");
           terms[3 * k] = gi.fam[pos_slot[pos]];
           terms[3 * k + 1] = pos_local[pos];
           terms[3 * k + 2] = (int)(int16_t)(e >> 16);
@@ -883,7 +883,7 @@ bbc_status bbc_plan_export(const bbc_ctx* c, int* sizes, int* row_ptr, int* term
       prev_fam[1] = gi.fam[1];
     }
   } catch (...) {
-    return fail(const_cast<bbc_ctx*>(c), BBC_ENOMEM, "host allocation failed");
+    return fail(c, BBC_ENOMEM, "host allocation failed");
   }
   for (int r = 0; r <= p.n_out; r++) row_ptr[r] = p.row_ptr[r];
   for (size_t t = 0; t < p.tasks.size(); t++) {

@@ -17,7 +17,7 @@ struct bbc_ctx {
   cudaStream_t stream = nullptr;
   int V = 0;
   bbc::Plan plan;
-  std::string err;
+  mutable std::string err;  // last failure message (inspection calls on a const context set it too)
   // workspace view
   char* ws = nullptr;
   size_t ws_bytes = 0;
