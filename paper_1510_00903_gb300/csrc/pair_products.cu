@@ -135,6 +135,7 @@ cudaError_t launch_pair_products(const void* blk_field, int L, const DevTask* ta
                                  const int* group_task, int n_groups, void* P, bool fp64, cudaStream_t st,
                                  const double* blk_sum) {
   const int V = L * L * L;
+  if (n_groups <= 0) return cudaSuccess;  // a plan whose products all vanish has no tasks
   dim3 g1((n_groups + kPairWarps - 1) / kPairWarps, (V + 31) / 32);
   if (fp64 && blk_sum)
     k_pair_products<double, true><<<g1, 32 * kPairWarps, 0, st>>>((const cpx<double>*)blk_field, blk_sum, L, tasks,

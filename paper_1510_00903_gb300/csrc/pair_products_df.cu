@@ -78,6 +78,7 @@ k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restric
 cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask* tasks, const int* group_ptr,
                                     const int* group_task, int n_groups, void* P, cudaStream_t st) {
   const int V = L * L * L;
+  if (n_groups <= 0) return cudaSuccess;  // a plan whose products all vanish has no tasks
   dim3 g1((n_groups + kPairWarpsDf - 1) / kPairWarpsDf, (V + 31) / 32);
   k_pair_products_df<<<g1, 32 * kPairWarpsDf, 0, st>>>((const float4*)blk_field, L, tasks, group_ptr, group_task,
                                                        n_groups, (cpx<dfr>*)P);

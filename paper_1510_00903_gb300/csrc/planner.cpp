@@ -689,6 +689,53 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
     }
   }
 
+  // Products that vanish for every q: at each open-index step one of the two
+  // rows has no terms (its weights cancelled), so it is exactly zero.  Their
+  // contributions are dropped, and so are tasks none of whose products is
+  // still read (all of them vanish, or the channels' sums cancelled them).
+  {
+    std::vector<char> empty_row(P.n_out);
+    for (int r = 0; r < P.n_out; r++) empty_row[r] = P.row_ptr[r + 1] == P.row_ptr[r];
+    const int nt = (int)P.tasks.size();
+    std::vector<char> zero_prod((size_t)nt * 16, 1);
+    for (int t = 0; t < nt; t++) {
+      const PairTask& k = P.tasks[t];
+      for (int ra = 0; ra < k.nA; ra++)
+        for (int rb = 0; rb < k.nB; rb++) {
+          bool z = true;
+          for (int i1 = 0; i1 < k.n1 && z; i1++)
+            for (int i2 = 0; i2 < k.n2 && z; i2++)
+              z = empty_row[k.offA[ra] + i1 * k.sA1 + i2 * k.sA2] || empty_row[k.offB[rb] + i1 * k.sB1 + i2 * k.sB2];
+          zero_prod[(size_t)t * 16 + ra * k.nB + rb] = z;
+        }
+    }
+    std::vector<char> used(nt, 0);
+    for (int it : P.tcontrib_item)
+      if (!zero_prod[it]) used[it / 16] = 1;
+    std::vector<int> new_id(nt, -1);
+    std::vector<PairTask> kept;
+    for (int t = 0; t < nt; t++)
+      if (used[t]) {
+        new_id[t] = (int)kept.size();
+        kept.push_back(P.tasks[t]);
+      }
+    std::vector<int> ptr(1, 0), item;
+    std::vector<double> coef;
+    for (size_t o = 0; o + 1 < P.tcontrib_ptr.size(); o++) {
+      for (int c = P.tcontrib_ptr[o]; c < P.tcontrib_ptr[o + 1]; c++) {
+        const int it = P.tcontrib_item[c];
+        if (zero_prod[it]) continue;
+        item.push_back(new_id[it / 16] * 16 + it % 16);
+        coef.push_back(P.tcontrib_coef[c]);
+      }
+      ptr.push_back((int)item.size());
+    }
+    P.tasks.swap(kept);
+    P.tcontrib_ptr.swap(ptr);
+    P.tcontrib_item.swap(item);
+    P.tcontrib_coef.swap(coef);
+  }
+
   P.pair_macs = 0;
   for (const PairTask& t : P.tasks) P.pair_macs += 16LL * t.n1 * t.n2;
   // bounds of every device table index (checked once on the host so that no

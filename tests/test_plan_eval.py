@@ -57,6 +57,23 @@ def test_single_channel_plans(slice3):
         _check([ch], bbc.BBC_UPPER, slice3)
 
 
+def test_plans_whose_products_all_vanish(slice3):
+    """The four channels the paper omits cancel exactly in the isospin limit:
+    their plans keep no block-pair task and no signed term, and evaluate to
+    zero (as the oracle does with S_u = S_d)."""
+    Sl, Ss = slice3
+    ctx = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [52, 53, 54, 55])
+    try:
+        plan = bbc.bbc_plan_export(ctx)
+    finally:
+        bbc.bbc_destroy(ctx)
+    assert len(plan["tasks"]) == 0 and len(plan["items"]) == 0
+    got = plan_eval.correlator(plan, L, Sl, Ss)
+    want = orc.correlator(L, Sl, Sl, Ss, [52, 53, 54, 55])
+    ref = np.abs(orc.correlator(L, Sl, Sl, Ss, [10])).max()
+    assert np.abs(got).max() == 0 and np.abs(want).max() < 1e-13 * ref
+
+
 def test_export_sizes_and_bounds():
     ctx = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, list(range(52)))
     try:

@@ -54,14 +54,16 @@ def test_aggregation_sizes(ctx52):
     """52 channels, upper spin components: 655 diagram instances with
     43,507 open-index iterations per spin (sum of the Tables' totals), stored
     as 24 shared blocks of 7,368 complex entries per site (Appendix A
-    aggregation, including the sub-block identity n^(2) in n^(3)), and 175
-    distinct block-pair products (tasks equal up to the order of their two
-    open indices merged): 180,928 complex multiply-adds per site per q."""
+    aggregation, including the sub-block identity n^(2) in n^(3)), and 153
+    block-pair tasks: 255 distinct ones, 175 once tasks equal up to the order
+    of their two open indices are merged, 153 once tasks whose products all
+    vanish (every step meets a row whose weights cancelled) are dropped --
+    174,208 complex multiply-adds per site per q."""
     s = bbc.bbc_plan_sizes(ctx52)
     assert s["blocks"] == 24
     assert s["block_outputs"] == 7368
-    assert s["pair_items"] == 16 * 175
-    assert s["pair_macs_per_site"] == 180928
+    assert s["pair_items"] == 16 * 153
+    assert s["pair_macs_per_site"] == 174208
     total, n_diag = 0, 0
     for pos in range(52):
         for t3 in range(3):
