@@ -213,3 +213,23 @@ def test_tuning_cache_file(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert bbc.tuning_cache_load(path) == {}
+
+
+def test_plan_export_arguments():
+    """bbc_plan_export: EINVAL without a context or sizes array; sizes alone
+    when any table pointer is NULL (nothing else is written)."""
+    import numpy as np
+    assert bbc.lib().bbc_plan_export(None, None, None, None, None, None, None, None) == bbc.BBC_EINVAL
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
+    try:
+        assert bbc.lib().bbc_plan_export(c, None, None, None, None, None, None, None) == bbc.BBC_EINVAL
+        sizes = np.zeros(5, dtype=np.int32)
+        row_ptr = np.full(8, -7, dtype=np.int32)
+        assert bbc.lib().bbc_plan_export(c, sizes.ctypes.data, row_ptr.ctypes.data, None, None, None, None,
+                                         None) == bbc.BBC_OK
+        assert sizes[0] == bbc.bbc_plan_sizes(c)["block_outputs"] and np.all(row_ptr == -7)
+        p = bbc.bbc_plan_export(c)
+        assert p["row_ptr"][0] == 0 and p["row_ptr"][-1] == len(p["terms"]) == sizes[1]
+        assert p["out_ptr"][-1] == len(p["items"]) == sizes[3] and len(p["out_ptr"]) == 2 * 16 + 1
+    finally:
+        bbc.bbc_destroy(c)
