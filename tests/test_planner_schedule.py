@@ -8,7 +8,9 @@ lists and every launch-shape candidate that
 * the shared-memory row map is increasing and keeps every task side's rows
   at the planner's strides (the kernel addresses slot(off) + i1 s1 + i2 s2);
 * the warp units of every (warps, chunk) candidate cover each batch's open
-  index exactly once.
+  index exactly once;
+* the block build's lane-interleaved 32-row chunks hold exactly each row's
+  terms (in the bank-conflict order) and weight-0 padding at position 0.
 """
 import os
 import subprocess
@@ -20,6 +22,8 @@ CSRC = os.path.join(ROOT, "paper_1510_00903_gb300", "csrc")
 
 CHECKER = r"""
 #include "planner.hpp"
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -90,6 +94,31 @@ static int check(const std::vector<int>& ch, int off) {
       for (const auto& c : cover)
         for (int x : c) CHECK(x == 1, "open index covered once");
     }
+  // block build: lane l of chunk j of group g holds the terms of row
+  // first_row + 32 j + l (in some order) and weight-0 padding otherwise
+  CHECK((int)P.chunk_first.size() == (int)P.groups.size() + 1, "chunk table");
+  for (size_t g = 0; g < P.groups.size(); g++) {
+    const GroupInfo& gi = P.groups[g];
+    const int n_chunks = (gi.n_rows + 31) / 32;
+    CHECK(P.chunk_first[g + 1] - P.chunk_first[g] == n_chunks, "chunks per group");
+    for (int j = 0; j < n_chunks; j++) {
+      const auto& ch = P.ell_chunk[P.chunk_first[g] + j];
+      CHECK(ch.first >= 0 && (size_t)ch.first + 32 * (size_t)ch.second <= P.ell.size(), "chunk range");
+      for (int l = 0; l < 32; l++) {
+        const int r = gi.first_row + 32 * j + l;
+        std::vector<uint32_t> got, want;
+        for (int k = 0; k < ch.second; k++) {
+          const uint32_t e = P.ell[ch.first + 32 * k + l];
+          if ((e >> 16) != 0) got.push_back(e);
+          else CHECK((e & 0xffffu) == 0, "padding reads position 0");
+        }
+        if (32 * j + l < gi.n_rows) want.assign(P.entries.begin() + P.row_ptr[r], P.entries.begin() + P.row_ptr[r + 1]);
+        std::sort(got.begin(), got.end());
+        std::sort(want.begin(), want.end());
+        CHECK(got == want, "row terms in the chunk");
+      }
+    }
+  }
   std::printf("OK %d tasks %zu batches\n", nt, batches.size());
   return 0;
 }
