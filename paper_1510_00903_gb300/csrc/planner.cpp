@@ -750,7 +750,12 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
       if (t.offA[r] < 0 || t.offA[r] + (t.n1 - 1) * t.sA1 + (t.n2 - 1) * t.sA2 >= P.n_out) { *err = "internal: task A range"; return false; }
     for (int r = 0; r < t.nB; r++)
       if (t.offB[r] < 0 || t.offB[r] + (t.n1 - 1) * t.sB1 + (t.n2 - 1) * t.sB2 >= P.n_out) { *err = "internal: task B range"; return false; }
-    if (t.sA1 < 0 || t.sA2 < 0 || t.sB1 < 0 || t.sB2 < 0) { *err = "internal: task stride"; return false; }
+    // strides are packed two per 32-bit word on the device (sA1 | sA2 << 16)
+    if (t.sA1 < 0 || t.sA2 < 0 || t.sB1 < 0 || t.sB2 < 0 || t.sA1 > 0xffff || t.sA2 > 0xffff || t.sB1 > 0xffff ||
+        t.sB2 > 0xffff) {
+      *err = "internal: task stride";
+      return false;
+    }
   }
   for (int id : P.tcontrib_item)
     if (id < 0 || id >= 16 * (int)P.tasks.size()) { *err = "internal: task contribution index"; return false; }
