@@ -179,9 +179,11 @@ bbc_status bbc_plan_sizes(const bbc_ctx* ctx, int* n_blocks, int* n_block_output
  * program can evaluate the block algorithm of Sec. 3 step by step (the tests
  * do, on tiny lattices, against the oracle).  Call once with every array
  * NULL to receive sizes[5] = {n_out (block rows per site), n_terms,
- * n_tasks, n_items, n_outputs = 16 x channels}; then again with arrays of
- * those sizes (the caller owns them; the call fills them all or, if any of
- * them is NULL, none):
+ * n_tasks, n_items, n_outputs = 16 x channels}; then again with the arrays
+ * (owned by the caller) and sizes[] holding their capacities in the same
+ * units: the call fills them all, or, if any array is NULL, none; if a
+ * capacity is too small it fills none, returns BBC_EINVAL and leaves the
+ * needed sizes in sizes[]:
  *  row_ptr[n_out + 1], terms[n_terms][3]: block row r is the sum over terms
  *    row_ptr[r] .. row_ptr[r+1]-1 of weight x F_family[index], with
  *    (family, index, weight) per term; family 0..6 = (l,l,l), (l,l,s),

@@ -185,7 +185,7 @@ def bbc_plan_export(ctx) -> dict:
     import numpy as np
     sizes = np.zeros(5, dtype=np.int32)
     _check(ctx, _lib.bbc_plan_export(ctx, sizes.ctypes.data, None, None, None, None, None, None))
-    n_out, n_terms, n_tasks, n_items, n_outputs = (int(x) for x in sizes)
+    n_out, n_terms, n_tasks, n_items, n_outputs = (int(x) for x in sizes)  # also the capacities below
     t = {"row_ptr": np.zeros(n_out + 1, np.int32), "terms": np.zeros((n_terms, 3), np.int32),
          "tasks": np.zeros((n_tasks, 24), np.int32), "out_ptr": np.zeros(n_outputs + 1, np.int32),
          "items": np.zeros(n_items, np.int32), "coefs": np.zeros(n_items, np.float64)}

@@ -845,12 +845,16 @@ bbc_status bbc_plan_export(const bbc_ctx* c, int* sizes, int* row_ptr, int* term
                            int* items, double* coefs) {
   if (!c || !sizes) return BBC_EINVAL;
   const bbc::Plan& p = c->plan;
-  sizes[0] = p.n_out;
-  sizes[1] = (int)p.entries.size();
-  sizes[2] = (int)p.tasks.size();
-  sizes[3] = (int)p.tcontrib_item.size();
-  sizes[4] = (int)p.tcontrib_ptr.size() - 1;
-  if (!row_ptr || !terms || !tasks || !out_ptr || !items || !coefs) return BBC_OK;
+  const int need[5] = {p.n_out, (int)p.entries.size(), (int)p.tasks.size(), (int)p.tcontrib_item.size(),
+                       (int)p.tcontrib_ptr.size() - 1};
+  const bool fill = row_ptr && terms && tasks && out_ptr && items && coefs;
+  bool fits = true;
+  for (int i = 0; i < 5; i++) {
+    if (fill && sizes[i] < need[i]) fits = false;  // the caller's capacities
+    sizes[i] = need[i];
+  }
+  if (!fill) return BBC_OK;
+  if (!fits) return fail(c, BBC_EINVAL, "plan export: an array is smaller than the plan needs");
   // the tensor entry behind each shared-memory position, group by group, as
   // the build kernel lays them out: a group's zneed list fills positions,
   // and positions of a slot whose family is unchanged carry over

@@ -228,6 +228,15 @@ def test_plan_export_arguments():
         assert bbc.lib().bbc_plan_export(c, sizes.ctypes.data, row_ptr.ctypes.data, None, None, None, None,
                                          None) == bbc.BBC_OK
         assert sizes[0] == bbc.bbc_plan_sizes(c)["block_outputs"] and np.all(row_ptr == -7)
+        # capacities too small: nothing is written, EINVAL, the needed sizes come back
+        need = sizes.copy()
+        small = need.copy()
+        small[1] -= 1
+        arrays = [np.full(int(need[0]) + 1, -7, np.int32), np.zeros((int(need[1]), 3), np.int32),
+                  np.zeros((int(need[2]), 24), np.int32), np.zeros(int(need[4]) + 1, np.int32),
+                  np.zeros(int(need[3]), np.int32), np.zeros(int(need[3]), np.float64)]
+        assert bbc.lib().bbc_plan_export(c, small.ctypes.data, *(a.ctypes.data for a in arrays)) == bbc.BBC_EINVAL
+        assert np.array_equal(small, need) and np.all(arrays[0] == -7)
         p = bbc.bbc_plan_export(c)
         assert p["row_ptr"][0] == 0 and p["row_ptr"][-1] == len(p["terms"]) == sizes[1]
         assert p["out_ptr"][-1] == len(p["items"]) == sizes[3] and len(p["out_ptr"]) == 2 * 16 + 1
