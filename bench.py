@@ -46,8 +46,22 @@ CMAC_PEAK_SOURCE = ("derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz = 629.3 G FMA/s
                     "FP64 pipe's ceiling is 209.8 G complex MACs/s = 1.678 TFLOP/s")
 #: FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz (probe: 74.8 TFLOP/s)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-#: measured STREAM-style copy bandwidth of this GPU model (GB/s)
-HBM_PEAK_GBS = 6803.8
+
+
+def measured_hbm_gbs(path=os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")):
+    """STREAM-style copy bandwidth (GB/s) measured on this GPU model, from
+    the peaks file beside this script; 6803.8 (the same measurement, taken
+    earlier on a GB300) when the file is absent or has no such figure."""
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        if v > 0:
+            return v, "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6803.8, "measured copy bandwidth of an earlier GB300 run (no MEASURED_PEAKS.json)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = measured_hbm_gbs()
 
 
 def profiled_traffic(path, kernel_src, pair_items):
@@ -117,7 +131,7 @@ def oracle_sample(seed=0, n_points=1):
     t0 = time.perf_counter()
     orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], list(range(N_CH)), r)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = orc.threads()  # the OpenMP threads the oracle ran on
     return N_CH * n_points / dt, dt, cores
 
 
@@ -429,7 +443,7 @@ def measure_projection(torch, cor, C, stream, reps=20):
     gbs = nbytes / (ms * 1e-3) / 1e9
     return {"kernel": "k_project", "bound": "hbm", "ms_per_launch": ms, "fields": C.numel() // (C.shape[-2] * 16),
             "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "peak_gbs": HBM_PEAK_GBS,
-            "frac": gbs / HBM_PEAK_GBS, "l2": "C, R, Ra1 of all slices (3 x 1.74 GB) exceed the L2"}
+            "peak_source": HBM_PEAK_SOURCE, "frac": gbs / HBM_PEAK_GBS, "l2": "C, R, Ra1 of all slices (3 x 1.74 GB) exceed the L2"}
 
 
 def error_report(torch, dev, bbc, synth, reps=3):

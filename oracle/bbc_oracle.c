@@ -57,6 +57,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -236,6 +237,9 @@ static void init_tables(void) {
 /* ---- public helpers ---------------------------------------------------- */
 
 int oracle_channel_count(void) { init_tables(); return g_nchan; }
+
+/* OpenMP threads the parallel loops over X use (the timing reports it). */
+int oracle_threads(void) { return omp_get_max_threads(); }
 
 int oracle_channel_baryons(int ch, int* out4) {
   init_tables();

@@ -50,6 +50,7 @@ def lib():
                                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         L.oracle_channel_count.restype = ctypes.c_int
+        L.oracle_threads.restype = ctypes.c_int
         L.oracle_channel_baryons.argtypes = [ctypes.c_int, ctypes.c_void_p]
         L.oracle_wick_count.argtypes = [ctypes.c_int]
         L.oracle_term_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -58,6 +59,11 @@ def lib():
         L.oracle_gamma.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops over X run on."""
+    return lib().oracle_threads()
 
 
 def n_channels() -> int:

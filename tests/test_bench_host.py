@@ -1,0 +1,56 @@
+"""Host-side helpers of the benchmark (CPU only): the DRAM-traffic lookup in
+an ncu summary and the thread count the oracle timing reports."""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import oracle.oracle as orc  # noqa: E402
+
+
+def _summary(tmp_path, sha, items, dram="123456"):
+    p = tmp_path / "summary.md"
+    p.write_text("# k\n\n| metric | value |\n|---|---|\n\n"
+                 f"- kernels_cu_sha256: {sha}\n- pair_items_per_q: {items}\n- dram_bytes_per_launch: {dram}\n")
+    return str(p)
+
+
+def test_profiled_traffic_needs_the_same_kernel_and_plan(tmp_path):
+    src = tmp_path / "kernel.cu"
+    src.write_text("__global__ void k() {}\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    assert bench.profiled_traffic(_summary(tmp_path, sha, 2448), str(src), 2448) == 123456.0
+    # another plan size, another kernel source, no summary: no traffic figure
+    assert bench.profiled_traffic(_summary(tmp_path, sha, 4080), str(src), 2448) is None
+    assert bench.profiled_traffic(_summary(tmp_path, "0" * 64, 2448), str(src), 2448) is None
+    assert bench.profiled_traffic(str(tmp_path / "missing.md"), str(src), 2448) is None
+
+
+def test_committed_pair_products_summary_has_the_fields():
+    text = open(os.path.join(ROOT, "profiles", "k_pair_products_f64_L16_slice.md")).read()
+    for key in ("kernels_cu_sha256:", "pair_items_per_q:", "dram_bytes_per_launch:"):
+        assert key in text, key
+
+
+def test_roofline_denominators():
+    # FP64 pipe: 152 SMs x 2 FMA x 2 flop x 2070 MHz; complex MAC = 3 FMAs for 8 flops
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.2586) < 1e-3
+    assert abs(bench.FP64_CMAC_PEAK_TFLOPS - 1.6781) < 1e-3
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.54) < 1e-2
+
+
+def test_oracle_reports_its_threads():
+    n = orc.threads()
+    assert 1 <= n <= (os.cpu_count() or 1) * 4
+
+
+def test_hbm_peak_from_the_peaks_file(tmp_path):
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 7000.5, "bf16_tflops": 1945.0}')
+    assert bench.measured_hbm_gbs(str(f))[0] == 7000.5
+    f.write_text("{}")
+    assert bench.measured_hbm_gbs(str(f))[0] == 6803.8
+    assert bench.measured_hbm_gbs(str(tmp_path / "none.json"))[0] == 6803.8
