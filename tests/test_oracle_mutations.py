@@ -44,7 +44,7 @@ CASES = [
     (1, 51, [(0, 1, 0, 1), (1, 1, 1, 0)], [0]),     # Xi- Xi0 <- Xi- Xi0
     (1, 0, [(0, 1, 0, 1), (1, 1, 0, 1)], [0]),      # p n <- p n
     (1, 90, [(0, 1, 1, 0)], [0]),                   # Omega_x Omega_z <- Omega_y Omega_z
-    (3, 5, [(0, 1, 0, 1)], [1, 5]),                 # translation (odd L: -r differs from r): B1 at X + r
+    (3, 5, [(0, 1, 0, 1)], [1]),                    # translation (odd L: -r differs from r): B1 at X + r
 ]
 
 
