@@ -88,6 +88,68 @@ def profiled_traffic(path, kernel_src, pair_items):
     return float(fields["dram_bytes_per_launch"])
 
 
+#: diquark kind read by each sink-tensor family (the families' Gamma1 and the
+#: flavours of their first two quarks): (l l) C gamma5, (l s) C gamma5,
+#: (s s) C gamma_1, C gamma_2, C gamma_3
+FAMILY_DIQUARK = [0, 0, 1, 1, 2, 3, 4]
+
+
+def plan_counts(plan, sizes):
+    """Algorithmic work counts of a plan, from its exported tables: block rows,
+    their weighted terms, the distinct sink-tensor entries they read, the
+    diquark kinds behind those, the block-pair complex multiply-adds and
+    products per q, the signed Wick terms and the outputs (channel x spin)."""
+    terms = plan["terms"]
+    fams = {int(f) for f in terms[:, 0]}
+    return {"block_rows": len(plan["row_ptr"]) - 1, "row_terms": int(len(terms)),
+            "tensor_entries": len({(int(f), int(e)) for f, e in terms[:, :2]}),
+            "diquarks": len({FAMILY_DIQUARK[f] for f in fams}),
+            "pair_macs": int(sizes["pair_macs_per_site"]), "pair_items": int(sizes["pair_items"]),
+            "wick_terms": int(len(plan["items"])), "outputs": len(plan["out_ptr"]) - 1}
+
+
+def step_roofline(counts, V, slices, stage_ms, step_ms, hbm_gbs=None, fp64_tflops=FP64_PEAK_TFLOPS,
+                  cmac_tflops=FP64_CMAC_PEAK_TFLOPS):
+    """Stage-wise roofline of one plain-FP64 step of `slices` time slices:
+    per stage the larger of its algorithmic bytes over the copy bandwidth and
+    its algorithmic flops over the FP64 pipe (the contraction over the pipe's
+    complex multiply-add ceiling); the step's floor is the sum over stages and
+    frac = floor / measured step time.  Algorithmic work per slice (V sites,
+    16-byte complex values):
+      ingest   2 x 144 values read (complex128) and written;
+      build    the propagators read, the block rows written; 432 entries x 8
+               complex products per diquark kind, 3 complex multiply-adds per
+               sink-tensor entry (8 flops each), 4 flops per weighted term;
+      fft_fwd  one read and one write of every block field, 5 V log2 V flops each;
+      contract the block fields read, the pair products written, 8 flops per
+               complex multiply-add;
+      wick     the products read, the outputs written, 4 flops per signed term;
+      fft_inv  the outputs read and the correlators written, 5 V log2 V flops each."""
+    import math
+    hbm = HBM_PEAK_GBS if hbm_gbs is None else hbm_gbs
+    c, b, lg = counts, 16.0, math.log2(V)
+    work = {
+        "ingest": (2 * 144 * V * 2 * b, 0.0, fp64_tflops),
+        "build": ((2 * 144 + c["block_rows"]) * V * b,
+                  V * (64.0 * 432 * c["diquarks"] + 24.0 * c["tensor_entries"] + 4.0 * c["row_terms"]), fp64_tflops),
+        "fft_fwd": (2.0 * c["block_rows"] * V * b, 5.0 * V * lg * c["block_rows"], fp64_tflops),
+        "contract": ((c["block_rows"] + c["pair_items"]) * V * b, 8.0 * V * c["pair_macs"], cmac_tflops),
+        "wick": ((c["pair_items"] + c["outputs"]) * V * b, 4.0 * V * c["wick_terms"], fp64_tflops),
+        "fft_inv": (2.0 * c["outputs"] * V * b, 5.0 * V * lg * c["outputs"], fp64_tflops),
+    }
+    stages, floor = {}, 0.0
+    for k, (nbytes, flops, peak) in work.items():
+        t_hbm = nbytes * slices / (hbm * 1e9) * 1e3
+        t_alu = flops * slices / (peak * 1e12) * 1e3
+        f = max(t_hbm, t_alu)
+        ms = stage_ms.get(k)
+        stages[k] = {"floor_ms": f, "bound": "hbm" if t_hbm >= t_alu else "fp64", "ms": ms,
+                     "frac": f / ms if ms else None}
+        floor += f
+    return {"floor_ms": floor, "ms_per_step": step_ms, "frac": floor / step_ms, "hbm_gbs": hbm,
+            "fp64_tflops": fp64_tflops, "cmac_tflops": cmac_tflops, "counts": counts, "stages": stages}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,6 +379,7 @@ def run_ours(args, torch, rank, world, local):
     # plain FP64 path (headline); launch shapes autotuned on slice 0 before timing
     cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=bbc.BBC_FP64, device=dev, stream=stream)
     sizes = cor.sizes()
+    counts = plan_counts(bbc.bbc_plan_export(cor.ctx), sizes)
     tune_fp64, tune_fp64_ms = cor.autotune(Sl[0], Ss[0], t=0, reps=3)
     sampler = ClockSampler(local)
     ms, stages = timed(cor, args.steps, args.warmup, sampler=sampler)
@@ -341,6 +404,7 @@ def run_ours(args, torch, rank, world, local):
                 "traffic": traffic, "peak_source": CMAC_PEAK_SOURCE,
                 "algorithmic_flop_per_launch": flops_per_launch, "avg_launch_ms": c_avg_ms}
     stage_ms = {k: v[0] / args.steps for k, v in stages.items()}
+    step_roof = step_roofline(counts, V, T, stage_ms, ms)
 
     def mixed_leg(precision, note, components=bbc.BBC_UPPER):
         corm = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=precision, device=dev, stream=stream,
@@ -403,6 +467,7 @@ def run_ours(args, torch, rank, world, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "stage_ms_per_step": stage_ms,
+        "step_roofline": step_roof,
         # the paper's split of a step (Sec. 5, Table ElapsedTime): Step-1 = blocks
         # and forward FFT, Step-2 = contraction and inverse FFT (best 32-node BG/Q
         # split: 6 s + 13 s)

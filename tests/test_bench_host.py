@@ -54,3 +54,31 @@ def test_hbm_peak_from_the_peaks_file(tmp_path):
     f.write_text("{}")
     assert bench.measured_hbm_gbs(str(f))[0] == 6803.8
     assert bench.measured_hbm_gbs(str(tmp_path / "none.json"))[0] == 6803.8
+
+
+def test_step_roofline_of_the_52_channel_plan():
+    """Work counts of the bench plan and the stage-wise floor of an FP64 step."""
+    from paper_1510_00903_gb300 import bbc
+    ctx = bbc.bbc_create(16, 32, 0, 0.3, 0.4, bbc.BBC_FP64, list(range(52)))
+    try:
+        counts = bench.plan_counts(bbc.bbc_plan_export(ctx), bbc.bbc_plan_sizes(ctx))
+    finally:
+        bbc.bbc_destroy(ctx)
+    assert counts["block_rows"] == 7368 and counts["row_terms"] == 33816 and counts["outputs"] == 52 * 16
+    assert counts["diquarks"] == 2  # (l l) and (l s) C gamma5: octet families only
+    assert 0 < counts["tensor_entries"] <= 2 * 1728 * 4
+    assert counts["pair_items"] == 16 * (counts["pair_items"] // 16) and counts["wick_terms"] > 0
+    V, T = 16 ** 3, 32
+    stage_ms = {"ingest": 2.0, "build": 60.0, "fft_fwd": 50.0, "contract": 120.0, "wick": 3.0, "fft_inv": 7.0,
+                "normalise": 0.1, "project": 0.0}
+    r = bench.step_roofline(counts, V, T, stage_ms, 250.0, hbm_gbs=6800.0)
+    st = r["stages"]
+    # the contraction: three FP64 FMAs per complex multiply-add on 152 SMs x 2 FMA/clk x 2.07 GHz
+    want = 3.0 * counts["pair_macs"] * V * T / (152 * 2 * 2.070e9) * 1e3
+    assert abs(st["contract"]["floor_ms"] - want) < 1e-9 * want and st["contract"]["bound"] == "fp64"
+    # ingest moves 2 x 144 complex128 values in and out per site: copy-bandwidth bound
+    want = 2 * 144 * 32 * V * T / 6800e9 * 1e3
+    assert abs(st["ingest"]["floor_ms"] - want) < 1e-9 * want and st["ingest"]["bound"] == "hbm"
+    assert abs(r["floor_ms"] - sum(s["floor_ms"] for s in st.values())) < 1e-9
+    assert abs(r["frac"] - r["floor_ms"] / 250.0) < 1e-12
+    assert all(abs(s["frac"] - s["floor_ms"] / stage_ms[k]) < 1e-12 for k, s in st.items())
