@@ -108,46 +108,59 @@ def plan_counts(plan, sizes):
             "wick_terms": int(len(plan["items"])), "outputs": len(plan["out_ptr"]) - 1}
 
 
-def step_roofline(counts, V, slices, stage_ms, step_ms, hbm_gbs=None, fp64_tflops=FP64_PEAK_TFLOPS,
-                  cmac_tflops=FP64_CMAC_PEAK_TFLOPS):
-    """Stage-wise roofline of one plain-FP64 step of `slices` time slices:
-    per stage the larger of its algorithmic bytes over the copy bandwidth and
-    its algorithmic flops over the FP64 pipe (the contraction over the pipe's
-    complex multiply-add ceiling); the step's floor is the sum over stages and
-    frac = floor / measured step time.  Algorithmic work per slice (V sites,
-    16-byte complex values):
-      ingest   2 x 144 values read (complex128) and written;
+def step_roofline(counts, V, slices, stage_ms, step_ms, mixed=False, hbm_gbs=None, fp64_tflops=FP64_PEAK_TFLOPS,
+                  cmac_tflops=FP64_CMAC_PEAK_TFLOPS, fp32_tflops=FP32_PEAK_TFLOPS):
+    """Stage-wise roofline of one step of `slices` time slices: per stage the
+    larger of its algorithmic bytes over the copy bandwidth and its
+    algorithmic flops over the pipe that runs them; the step's floor is the
+    sum over stages and frac = floor / measured step time.
+
+    Algorithmic work per slice (V sites), blocks as b-byte complex values
+    (16 plain FP64, 8 mixed FP32), correlators and Wick sums 16-byte:
+      ingest   2 x 144 complex128 values read, written as blocks' type;
       build    the propagators read, the block rows written; 432 entries x 8
                complex products per diquark kind, 3 complex multiply-adds per
                sink-tensor entry (8 flops each), 4 flops per weighted term;
       fft_fwd  one read and one write of every block field, 5 V log2 V flops each;
       contract the block fields read, the pair products written, 8 flops per
-               complex multiply-add;
-      wick     the products read, the outputs written, 4 flops per signed term;
-      fft_inv  the outputs read and the correlators written, 5 V log2 V flops each."""
+               complex multiply-add (FP64: over the pipe's complex-MAC ceiling);
+      wick     the products read, the outputs written, 4 FP64 flops per signed term;
+      fft_inv  the outputs read and the correlators written, 5 V log2 V flops each.
+    Mixed precision with the fused contraction (no separate Wick stage
+    timed): the contraction reads the block fields once and writes the
+    outputs, its FP32 products and FP64 Wick sums bounded by their own pipes."""
     import math
     hbm = HBM_PEAK_GBS if hbm_gbs is None else hbm_gbs
-    c, b, lg = counts, 16.0, math.log2(V)
-    work = {
-        "ingest": (2 * 144 * V * 2 * b, 0.0, fp64_tflops),
-        "build": ((2 * 144 + c["block_rows"]) * V * b,
-                  V * (64.0 * 432 * c["diquarks"] + 24.0 * c["tensor_entries"] + 4.0 * c["row_terms"]), fp64_tflops),
-        "fft_fwd": (2.0 * c["block_rows"] * V * b, 5.0 * V * lg * c["block_rows"], fp64_tflops),
-        "contract": ((c["block_rows"] + c["pair_items"]) * V * b, 8.0 * V * c["pair_macs"], cmac_tflops),
-        "wick": ((c["pair_items"] + c["outputs"]) * V * b, 4.0 * V * c["wick_terms"], fp64_tflops),
-        "fft_inv": (2.0 * c["outputs"] * V * b, 5.0 * V * lg * c["outputs"], fp64_tflops),
+    c, lg = counts, math.log2(V)
+    b = 8.0 if mixed else 16.0
+    alu, alu_name = (fp32_tflops, "fp32") if mixed else (fp64_tflops, "fp64")
+    build_flops = V * (64.0 * 432 * c["diquarks"] + 24.0 * c["tensor_entries"] + 4.0 * c["row_terms"])
+    work = {  # stage: (bytes, [(flops, peak TFLOP/s, pipe)])
+        "ingest": (2 * 144 * V * (16.0 + b), []),
+        "build": ((2 * 144 + c["block_rows"]) * V * b, [(build_flops, alu, alu_name)]),
+        "fft_fwd": (2.0 * c["block_rows"] * V * b, [(5.0 * V * lg * c["block_rows"], alu, alu_name)]),
     }
+    products = 8.0 * V * c["pair_macs"]
+    sums = 4.0 * V * c["wick_terms"]
+    if mixed and not stage_ms.get("wick"):
+        work["contract"] = ((c["block_rows"] * b + c["outputs"] * 16.0) * V,
+                            [(products, fp32_tflops, "fp32"), (sums, fp64_tflops, "fp64")])
+    else:
+        work["contract"] = ((c["block_rows"] + c["pair_items"]) * V * b,
+                            [(products, fp32_tflops, "fp32") if mixed else (products, cmac_tflops, "fp64")])
+        work["wick"] = ((c["pair_items"] * b + c["outputs"] * 16.0) * V, [(sums, fp64_tflops, "fp64")])
+    work["fft_inv"] = (2.0 * c["outputs"] * V * 16.0, [(5.0 * V * lg * c["outputs"], alu, alu_name)])
     stages, floor = {}, 0.0
-    for k, (nbytes, flops, peak) in work.items():
-        t_hbm = nbytes * slices / (hbm * 1e9) * 1e3
-        t_alu = flops * slices / (peak * 1e12) * 1e3
-        f = max(t_hbm, t_alu)
+    for k, (nbytes, pipes) in work.items():
+        times = [(nbytes * slices / (hbm * 1e9) * 1e3, "hbm")]
+        times += [(flops * slices / (peak * 1e12) * 1e3, name) for flops, peak, name in pipes]
+        f, bound = max(times)
         ms = stage_ms.get(k)
-        stages[k] = {"floor_ms": f, "bound": "hbm" if t_hbm >= t_alu else "fp64", "ms": ms,
-                     "frac": f / ms if ms else None}
+        stages[k] = {"floor_ms": f, "bound": bound, "ms": ms, "frac": f / ms if ms else None}
         floor += f
     return {"floor_ms": floor, "ms_per_step": step_ms, "frac": floor / step_ms, "hbm_gbs": hbm,
-            "fp64_tflops": fp64_tflops, "cmac_tflops": cmac_tflops, "counts": counts, "stages": stages}
+            "pipes_tflops": {"fp64": fp64_tflops, "fp64_cmac": cmac_tflops, "fp32": fp32_tflops},
+            "counts": counts, "stages": stages}
 
 
 def parse():
@@ -414,12 +427,15 @@ def run_ours(args, torch, rank, world, local):
         corm.close()
         cm_ms, cm_n = st_m["contract"]
         cm_avg = cm_ms / max(cm_n, 1)
-        return {"value": shard.job_throughput(V * T * N_CH, world, ms_m), "ms_per_step": ms_m,
-                "speedup_vs_fp64": ms / ms_m, "precision": note,
-                "stage_ms_per_step": {k: v[0] / args.steps for k, v in st_m.items()},
-                "contract_tflops": flops_per_launch / (cm_avg * 1e-3) / 1e12,
-                "contract_frac_fp32_peak": flops_per_launch / (cm_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                "tuning": tune_m, "autotune_ms": tune_m_ms}
+        stage_m = {k: v[0] / args.steps for k, v in st_m.items()}
+        leg = {"value": shard.job_throughput(V * T * N_CH, world, ms_m), "ms_per_step": ms_m,
+               "speedup_vs_fp64": ms / ms_m, "precision": note, "stage_ms_per_step": stage_m,
+               "contract_tflops": flops_per_launch / (cm_avg * 1e-3) / 1e12,
+               "contract_frac_fp32_peak": flops_per_launch / (cm_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+               "tuning": tune_m, "autotune_ms": tune_m_ms}
+        if precision == bbc.BBC_MIXED_FP32 and components == bbc.BBC_UPPER:
+            leg["step_roofline"] = step_roofline(counts, V, T, stage_m, ms_m, mixed=True)
+        return leg
 
     # FP64 with double-float block-pair products (FP64-accurate, FP32 pipes)
     cord = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=bbc.BBC_DF64, device=dev, stream=stream)

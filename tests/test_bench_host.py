@@ -82,3 +82,25 @@ def test_step_roofline_of_the_52_channel_plan():
     assert abs(r["floor_ms"] - sum(s["floor_ms"] for s in st.values())) < 1e-9
     assert abs(r["frac"] - r["floor_ms"] / 250.0) < 1e-12
     assert all(abs(s["frac"] - s["floor_ms"] / stage_ms[k]) < 1e-12 for k, s in st.items())
+
+
+def test_step_roofline_mixed_routes():
+    """Mixed precision: the fused contraction (no Wick stage timed) is one
+    stage bounded by the FP32 products, the FP64 sums or the traffic; the
+    unfused route has products and sums as two stages."""
+    counts = {"block_rows": 7368, "row_terms": 33816, "tensor_entries": 8880, "diquarks": 2, "pair_macs": 174208,
+              "pair_items": 2448, "wick_terms": 5504, "outputs": 832}
+    V, T = 16 ** 3, 32
+    fused = {"ingest": 2.0, "build": 11.0, "fft_fwd": 6.0, "contract": 15.0, "fft_inv": 2.7, "wick": 0.0}
+    r = bench.step_roofline(counts, V, T, fused, 40.0, mixed=True, hbm_gbs=6800.0)
+    st = r["stages"]
+    assert "wick" not in st
+    fp32 = 8.0 * 174208 * V * T / (bench.FP32_PEAK_TFLOPS * 1e12) * 1e3
+    fp64 = 4.0 * 5504 * V * T / (bench.FP64_PEAK_TFLOPS * 1e12) * 1e3
+    hbm = (7368 * 8 + 832 * 16) * V * T / 6800e9 * 1e3
+    assert abs(st["contract"]["floor_ms"] - max(fp32, fp64, hbm)) < 1e-12
+    assert st["fft_fwd"]["bound"] == "hbm"  # FP32 transforms of 8-byte values
+    unfused = dict(fused, wick=3.0)
+    st = bench.step_roofline(counts, V, T, unfused, 45.0, mixed=True, hbm_gbs=6800.0)["stages"]
+    assert abs(st["wick"]["floor_ms"] - max(fp64, (2448 * 8 + 832 * 16) * V * T / 6800e9 * 1e3)) < 1e-12
+    assert st["contract"]["bound"] in ("fp32", "hbm")
