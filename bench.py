@@ -655,6 +655,7 @@ def run_decuplet(args, torch, dev, bbc, synth):
     for name, prec in (("fp64", bbc.BBC_FP64), ("df64", bbc.BBC_DF64), ("mixed", bbc.BBC_MIXED_FP32)):
         cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=prec, device=dev, stream=stream)
         sizes = cor.sizes()
+        counts = plan_counts(bbc.bbc_plan_export(cor.ctx), sizes)
         tune, _ = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
         for _ in range(args.warmup):
             cor.run(Sl, Ss, range(T), out=out, normalised=True)
@@ -679,10 +680,13 @@ def run_decuplet(args, torch, dev, bbc, synth):
         ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
         c_ms, c_n = stages["contract"]
         flop = 8.0 * sizes["pair_macs_per_site"] * V
+        stage_ms = {k: v[0] / args.steps for k, v in stages.items()}
         legs[name] = {"value": shard.job_throughput(V * T * len(chans), world, ms), "ms_per_step": ms,
-                      "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+                      "stage_ms_per_step": stage_ms,
                       "contract_ms_per_slice": c_ms / max(c_n, 1),
                       "contract_tflops": flop / (c_ms / max(c_n, 1) * 1e-3) / 1e12, "tuning": tune}
+        if name != "df64":  # double-float arithmetic has no pipe peak of its own
+            legs[name]["step_roofline"] = step_roofline(counts, V, T, stage_ms, ms, mixed=name == "mixed")
     if rank != 0:
         return
     fp = legs["fp64"]
