@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         objs = list(ex.map(run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
-    run([nvcc, ARCH, "-shared", "-o", tmp] + objs)
+    run([nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-ldl"])  # dlopen of an NVTX tool, if one is attached
     os.replace(tmp, LIB)
     return LIB
 

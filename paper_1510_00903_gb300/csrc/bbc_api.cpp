@@ -15,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ctx_internal.hpp"
 #include "kernels.cuh"
@@ -113,21 +114,30 @@ cudaEvent_t take_event(bbc_ctx* c) {
   return e;
 }
 
-// Brackets one stage launch with events when timing is enabled.
+// NVTX range names of the stages (host-side launch ranges, visible to
+// profilers that attach an NVTX tool; no-ops otherwise).
+const char* const kStageRange[BBC_N_STAGES] = {"bbc ingest",  "bbc build",     "bbc fft_fwd", "bbc contract",
+                                               "bbc fft_inv", "bbc normalise", "bbc wick",    "bbc project"};
+
+// Brackets one stage launch with an NVTX range, and with events when timing
+// is enabled.
 struct StageScope {
   bbc_ctx* c;
   int stage;
   cudaEvent_t a = nullptr, b = nullptr;
   StageScope(bbc_ctx* ctx, int s) : c(ctx), stage(s) {
+    nvtxRangePushA(kStageRange[s]);
     if (!c->timing) return;
     a = take_event(c);
     b = take_event(c);
     if (a) cudaEventRecord(a, c->stream);
   }
   ~StageScope() {
-    if (!a || !b) return;
-    cudaEventRecord(b, c->stream);
-    c->pending[stage].push_back({a, b});
+    if (a && b) {
+      cudaEventRecord(b, c->stream);
+      c->pending[stage].push_back({a, b});
+    }
+    nvtxRangePop();
   }
 };
 
