@@ -137,3 +137,42 @@ def test_run_to_host_end_to_end():
         err = np.abs(out[t].numpy() - want).reshape(len(chans), -1).max(axis=1) / scale
         assert err.max() < 1e-12, (t, err)
     cor.close()
+
+
+def test_batch_failure_names_the_item_and_resumes():
+    """Failure and resume of a batch without any device fault: item 2 asks for
+    a time slice outside the lattice, so bbc_batch_run returns EINVAL naming
+    item 2 after items 0 and 1 ran, and item 2 writes nothing.  Work items are
+    independent, so running the batch again from item 2 (slice fixed)
+    completes it; every output equals the eager run of the same context."""
+    L, T = 4, 4
+    chans = [1, 41]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = synth.flavour_set(L, T, 0, 0.3, 0.4, seed=44)
+    Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
+    cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=bbc.BBC_FP64, device=dev)
+    want = cor.run(Sl, Ss, range(T)).cpu().numpy()
+    outs = [torch.zeros((len(chans), L ** 3, 16), dtype=torch.complex128, device=dev) for _ in range(T)]
+    items = (bbc.bbc_batch_item * T)()
+    for t in range(T):
+        items[t] = bbc.bbc_batch_item(cor.ctx, t, Sl[t].data_ptr(), Ss[t].data_ptr(), bbc.BBC_C128, 1,
+                                      outs[t].data_ptr(), 1)
+    items[2].t = T  # outside 0 <= t < T
+    stream = torch.cuda.current_stream(dev)
+    with pytest.raises(bbc.BBCError) as e:
+        bbc.bbc_batch_run(items, T, stream.cuda_stream)
+    assert e.value.status == bbc.BBC_EINVAL and "batch item 2" in str(e.value)
+    torch.cuda.synchronize(dev)
+
+    def close(t):
+        got = outs[t].cpu().numpy()
+        return np.abs(got - want[t]).max() <= 1e-14 * np.abs(want[t]).max()
+
+    assert close(0) and close(1)
+    assert outs[2].abs().max().item() == 0 and outs[3].abs().max().item() == 0
+    items[2].t = 2
+    rest = (bbc.bbc_batch_item * (T - 2))(*[items[i] for i in range(2, T)])
+    bbc.bbc_batch_run(rest, T - 2, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    assert all(close(t) for t in range(T))
+    cor.close()
