@@ -75,20 +75,33 @@ typedef enum {
   BBC_FP64 = 0,      /* blocks, FFTs, contraction and sums in FP64 */
   BBC_MIXED_FP32 = 1, /* blocks, FFTs and block-pair products in FP32 after an exact
                          per-slice power-of-two rescaling of each propagator; the signed
-                         sum over Wick diagrams and the normalisation in FP64.  One fused
-                         kernel per pair {q, -q} when the channel list's block rows and
-                         products fit one CTA's shared memory (the 64 octet ids do, and
-                         so do the 90 decuplet ids); larger lists (e.g. all octet and
-                         decuplet ids together) run the products and the Wick sums as
-                         two kernels through a product buffer */
+                         sum over Wick diagrams in double-float arithmetic (two FP32
+                         words, 48-bit significand) and the normalisation in FP64.  The
+                         block pairs whose operands are whole 12 x 12 open-index blocks
+                         in the trace form tr(M_A(q) M_B(-q)) (most of the work for the
+                         octet channels) run on the tensor cores as one complex matrix
+                         product per pair {q, -q}, G(q)[i][j] = tr(M_i(q) M_j(-q)),
+                         G(-q) = G(q)^T, with every FP32 operand split into two TF32
+                         words (FP32-accurate products, FP32 accumulation); the other
+                         pairs run on the CUDA cores in FP32.  Channel lists without such
+                         pairs, or whose rows and products do not fit one CTA's shared
+                         memory, run one fused CUDA-core kernel per pair {q, -q} with
+                         FP64 Wick sums (the 64 octet ids fit it, and so do the 90
+                         decuplet ids), or, beyond that (e.g. all octet and decuplet
+                         ids together), the products and the Wick sums as two kernels
+                         through a product buffer */
   BBC_MIXED_BF16 = 2, /* trial: as BBC_MIXED_FP32, with the Fourier-space blocks rounded
                          to bfloat16 (round to nearest even) before the block-pair
                          products, which multiply and accumulate in FP32; fused kernel
                          only (EINVAL at creation for channel lists that do not fit it) */
-  BBC_DF64 = 3        /* FP64-accurate results from double-float arithmetic
+  BBC_DF64 = 3,       /* FP64-accurate results from double-float arithmetic
                          (unevaluated sums of two FP32 values, 48-bit significand) on
                          the FP32 pipes: propagators, blocks, FFTs, block-pair products
                          and Wick sums; FP64 only to split the input and to normalise */
+  BBC_MIXED_TF32 = 4  /* trial: as BBC_MIXED_FP32, with the tensor-core operands rounded
+                         once to TF32 (10-bit mantissa, round to nearest) instead of
+                         split into two TF32 words: a third of the tensor-core work at
+                         about 1e-3 relative error of the products */
 } bbc_precision;
 
 typedef enum { BBC_C128 = 0, BBC_C64 = 1 } bbc_dtype;
@@ -345,16 +358,21 @@ bbc_status bbc_project(bbc_ctx* ctx, const void* C_dev, int n_fields, void* R_de
  * [n_channels][L^3][16] complex128, written fully.  Everything runs
  * asynchronously on the context stream.
  *
- * Precisions BBC_FP64 and BBC_MIXED_FP32 (EINVAL for the others).
+ * Precisions BBC_FP64 and BBC_MIXED_FP32 (EINVAL for the others); the
+ * contraction runs on the CUDA cores (block-pair products, then Wick sums)
+ * whatever the context's precision would pick otherwise.  Contexts with
+ * numeric checks (bbc_set_checks) are rejected with EINVAL.
  * Size limit: the plan tables and one slice of blocks, pair products and
  * q-space correlators must fit in the array -- L <= 4 with all 52 channels;
  * larger lattices or channel lists return BBC_EINVAL with a message.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and leave their
- * data in it: calls whose work overlaps on the GPU (other streams, other host
- * threads without ordering) race on it.  Allocates no device memory; host
- * memory only for the error message of a failed call. */
+ * Every call copies the plan tables from host memory into the array.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, and the first call with a
+ * context uploads the FFT twiddle tables (synchronously); make that first
+ * call before any stream capture.  All calls share the one array and leave
+ * their data in it: calls whose work overlaps on the GPU (other streams,
+ * other host threads without ordering) race on it.  Allocates no device
+ * memory; host memory only for the error message of a failed call. */
 bbc_status bbc_run_slice_static(bbc_ctx* ctx, int t, const void* S_light, const void* S_strange, int dtype,
                                 void* out_dev, int normalised);
 

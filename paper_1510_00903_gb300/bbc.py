@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libbbc.so")
 
 BBC_OK, BBC_EINVAL, BBC_ENOMEM, BBC_ECUDA, BBC_ESTATE, BBC_ETIMEOUT, BBC_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
-BBC_FP64, BBC_MIXED_FP32, BBC_MIXED_BF16, BBC_DF64 = 0, 1, 2, 3
+BBC_FP64, BBC_MIXED_FP32, BBC_MIXED_BF16, BBC_DF64, BBC_MIXED_TF32 = 0, 1, 2, 3, 4
 BBC_UPPER, BBC_LOWER = 0, 1
 BBC_C128, BBC_C64 = 0, 1
 BBC_LIGHT, BBC_STRANGE = 0, 1

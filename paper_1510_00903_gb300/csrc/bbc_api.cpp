@@ -25,6 +25,13 @@ namespace {
 
 std::string g_create_error;
 
+// The bits of an int as a float (a table column that holds indices).
+float __int_as_float_host(int x) {
+  float f;
+  std::memcpy(&f, &x, sizeof f);
+  return f;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // FP64 storage (plain FP64, and FP64 with double-float products) or FP32
 bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
@@ -33,14 +40,17 @@ bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 p
 int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP64 ? bbc::RK_F64 : bbc::RK_F32); }
 
 constexpr int kMaxFusedWarps = 16;
+// tensor-core contexts: precisions whose trace-form block pairs run on the tensor cores
+bool tensor_path(int prec) { return prec == BBC_MIXED_FP32 || prec == BBC_MIXED_TF32; }
 // Warp task lists of the block-pair products per 32 q (autotuned).
 const int kPairGroupsCand[] = {48, 96, 192, 384};
 constexpr int kMaxPairGroups = 384;
 
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
-  size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site, tables_end;
-  size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, ct, scale, flag, total;
+  size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site;
+  size_t tc_base, tc_units, row_src, tc_cptr, tc_terms, tables_end;
+  size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, G, ct, scale, flag, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -64,6 +74,11 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.row_slot = o; o = align256(o + sizeof(int) * c->row_slot.size());
   L.orb_ptr = o; o = align256(o + sizeof(int) * c->orb_ptr.size());
   L.orb_site = o; o = align256(o + sizeof(int) * c->orb_site.size());
+  L.tc_base = o; o = align256(o + sizeof(int) * c->tcs.base.size());
+  L.tc_units = o; o = align256(o + sizeof(int) * c->tcs.units.size());
+  L.row_src = o; o = align256(o + sizeof(int) * c->tcs.row_src.size());
+  L.tc_cptr = o; o = align256(o + sizeof(int) * c->tcs.out_ptr.size());
+  L.tc_terms = o; o = align256(o + sizeof(float4) * c->tcs.coef.size());
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -77,6 +92,8 @@ Layout layout(const bbc_ctx* c, int slots) {
   // FP64: re + im of every Fourier-space block value (the FP64 products' sums)
   L.blks = o; o = align256(o + (c->prec == BBC_FP64 ? (size_t)slots * V * p.n_out * sizeof(double) : 0));
   L.P = o; o = align256(o + (split ? (size_t)p.tasks.size() * 16 * V * cplx_bytes(c->prec) : 0));
+  // tensor-core products of one slice: G(q) per pair {q, -q}, complex64
+  L.G = o; o = align256(o + (c->tc ? c->qlist.size() * (size_t)c->tcs.nbp * c->tcs.nbp * 8 : 0));
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
   L.flag = o; o = align256(o + sizeof(int));
@@ -157,20 +174,27 @@ std::vector<int> plan_key(const bbc::Plan& plan) {
   return k;
 }
 
-const FusedSchedule& fused_schedule(const bbc::Plan& plan) {
+// The plan the fused kernels run: the whole plan, or (tensor-core contexts)
+// the tasks left to the CUDA cores on their compact rows.
+const bbc::Plan& fused_plan(const bbc_ctx* c) { return c->tc ? c->tcs.rest : c->plan; }
+
+// plan: the context's plan (the cache key); run: the plan the kernel runs
+const FusedSchedule& fused_schedule(const bbc::Plan& plan, const bbc::Plan& run, bool tc) {
   std::lock_guard<std::mutex> lock(g_sched_mutex);
-  const std::vector<int> key = plan_key(plan);
+  std::vector<int> key = plan_key(plan);
+  if (tc) key.push_back(-100);
   auto it = g_sched.find(key);
   if (it != g_sched.end()) return it->second;
   FusedSchedule f;
-  bbc::make_batches(plan, &f.batches);
-  bbc::optimise_fused_layout(plan, &f.batches, &f.layout);
+  bbc::make_batches(run, &f.batches);
+  bbc::optimise_fused_layout(run, &f.batches, &f.layout);
   return g_sched.emplace(key, std::move(f)).first->second;
 }
 
 // Candidate launch configurations of the autotuner.
 const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}};  // (sites per CTA, threads)
 const int kFusedWarpsCand[] = {8, 12, 16};
+const int kRestWarpsCand[] = {4, 8};  // k_contract_rest (two CTAs per SM)
 const int kFusedStepsCand[] = {1, 2};
 const int kChunkCand[] = {0, 18, 36, 72, 144};  // 0: contiguous equal-cost pieces
 
@@ -186,7 +210,9 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec), (int)c->plan.diquarks.size()) > bbc::kMaxSmemPerBlock)
     return false;
   if (c->fused) {
-    if (!bbc::fused_variant_supported(t.fused_warps, t.fused_steps)) return false;
+    if (c->tc ? !bbc::rest_variant_supported(t.fused_warps, t.fused_steps)
+              : !bbc::fused_variant_supported(t.fused_warps, t.fused_steps))
+      return false;
     bool chunk_ok = false;
     for (int k : kChunkCand) chunk_ok |= k == t.fused_chunk;
     if (!chunk_ok) return false;
@@ -217,8 +243,8 @@ bbc_status apply_pair_groups(bbc_ctx* c) {
 // workspace is attached (synchronous: the host vectors are temporaries).
 bbc_status apply_fused_units(bbc_ctx* c) {
   if (!c->fused) return BBC_OK;
-  const FusedSchedule& f = fused_schedule(c->plan);
-  bbc::make_units(c->plan, f.batches, c->tune.fused_warps, c->tune.fused_chunk, &c->wptr, &c->wunits);
+  const FusedSchedule& f = fused_schedule(c->plan, fused_plan(c), c->tc);
+  bbc::make_units(fused_plan(c), f.batches, c->tune.fused_warps, c->tune.fused_chunk, &c->wptr, &c->wunits);
   if (c->wunits.size() > c->max_units || (int)c->wptr.size() > kMaxFusedWarps + 1)
     return fail(c, BBC_EINVAL, "internal: warp units exceed their workspace");
   if (!c->ws) return BBC_OK;
@@ -255,6 +281,23 @@ double time_launches(bbc_ctx* c, int reps, F launch) {
   return ok && ms >= 0.f ? ms / reps : -1.0;
 }
 
+// The tensor-core contraction of one slot: G(q) of every pair {q, -q} on
+// the tensor cores, then the CUDA-core products and the Wick sums.
+cudaError_t launch_tc(bbc_ctx* c, int slot) {
+  const bbc::Plan& p = c->plan;
+  const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
+  const int n_q = (int)c->qlist.size();
+  cudaError_t e = bbc::launch_contract_tc(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist, n_q,
+                                          c->d_tc_units, (int)c->tcs.units.size(), c->d_G,
+                                          c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x, c->stream);
+  if (e != cudaSuccess) return e;
+  return bbc::launch_contract_rest(blk, c->lat.L, p.n_out, c->d_row_src, c->d_row_slot, c->tcs.rest.n_out, c->n_slots,
+                                   c->d_qlist, n_q, c->d_tasks, (int)c->tcs.rest.tasks.size(), c->d_batches,
+                                   c->d_wptr, c->d_wunits, c->d_G, c->tcs.nbp * c->tcs.nbp, c->d_tc_cptr,
+                                   c->d_tc_terms, (int)p.channels.size(), c->d_ct, c->tune.fused_warps,
+                                   c->tune.fused_steps, c->stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -270,7 +313,8 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
   *ctx = nullptr;
   if (!supported_L(lat->L)) return fail(nullptr, BBC_EINVAL, "unsupported L (supported: 2, 4, 8, 16, 24, 32, 48)");
   if (lat->T < 1 || lat->t0 < 0 || lat->t0 >= lat->T) return fail(nullptr, BBC_EINVAL, "bad T or t0");
-  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16 && prec != BBC_DF64)
+  if (prec != BBC_FP64 && prec != BBC_MIXED_FP32 && prec != BBC_MIXED_BF16 && prec != BBC_DF64 &&
+      prec != BBC_MIXED_TF32)
     return fail(nullptr, BBC_EINVAL, "bad precision");
   if (n_channels < 1 || n_channels > bbc::kMaxChannels) return fail(nullptr, BBC_EINVAL, "bad channel count");
   if (components != BBC_UPPER && components != BBC_LOWER) return fail(nullptr, BBC_EINVAL, "bad spin components");
@@ -298,10 +342,75 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
   // double-float products start with more, shorter groups (fewer q tiles in
   // flight, so their rows stay in L2); the autotuner may choose others
   c->tune.pair_groups = prec == BBC_DF64 ? 192 : 48;
-  // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
-  if (fused_path(prec)) {
+  for (int q = 0; q < c->V; q++) {  // one q of every pair {q, -q}
+    const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
+    const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
+    if (q <= nq) c->qlist.push_back(q);
+  }
+  // tensor cores for the trace-form block pairs (mixed FP32 and TF32): the
+  // rest kernel must fit one CTA's shared memory, else the contraction stays
+  // on the CUDA cores
+  if (tensor_path(prec)) {
     try {
-      const FusedSchedule& f = fused_schedule(c->plan);
+      std::string serr;
+      if (!bbc::split_tensor_tasks(c->plan, &c->tcs, &serr)) {
+        delete c;
+        return fail(nullptr, BBC_EINVAL, serr);
+      }
+      if (c->tcs.nb > 0) {
+        c->tc = true;
+        const FusedSchedule& f = fused_schedule(c->plan, c->tcs.rest, true);
+        const int n_slots = f.layout.n_slots;
+        const int g_elems = c->tcs.nbp * c->tcs.nbp;
+        if (bbc::contract_rest_smem(n_slots, (int)c->tcs.rest.tasks.size(), g_elems) > bbc::kMaxSmemPerBlock ||
+            bbc::contract_tc_smem(c->tcs.nbp) > bbc::kMaxSmemPerBlock || c->tcs.rest.tasks.empty()) {
+          c->tc = false;
+          c->tcs = bbc::TcSplit();
+        }
+      } else {
+        c->tcs = bbc::TcSplit();
+      }
+    } catch (const std::bad_alloc&) {
+      delete c;
+      return fail(nullptr, BBC_ENOMEM, "host allocation failed while scheduling");
+    }
+  }
+  if (c->tc) {
+    const FusedSchedule& f = fused_schedule(c->plan, c->tcs.rest, true);
+    c->fused = true;
+    c->batches = f.batches;
+    c->row_slot = f.layout.row_slot;
+    c->n_slots = f.layout.n_slots;
+    c->tune.fused_warps = 8;
+    c->tune.fused_steps = 1;
+    std::vector<int> wp;
+    std::vector<bbc::BatchUnit> wu;
+    for (int w : kRestWarpsCand)
+      for (int k : kChunkCand) {
+        bbc::make_units(c->tcs.rest, f.batches, w, k, &wp, &wu);
+        c->max_units = std::max(c->max_units, wu.size());
+      }
+    bool ok = (int)c->row_slot.size() == c->tcs.rest.n_out;
+    for (int i = 0; ok && i < c->tcs.rest.n_out; i++)
+      ok = c->row_slot[i] >= (i ? c->row_slot[i - 1] + 1 : 0) && c->row_slot[i] < c->n_slots;
+    for (size_t i = 0; ok && i < c->tcs.row_src.size(); i++) ok = c->tcs.row_src[i] >= 0 && c->tcs.row_src[i] < c->plan.n_out;
+    const int n_v = 2 * 16 * (int)c->tcs.rest.tasks.size() + c->tcs.nbp * c->tcs.nbp;
+    for (size_t i = 0; ok && i < c->tcs.src_q.size(); i++)
+      ok = c->tcs.src_q[i] >= 0 && c->tcs.src_q[i] < n_v && c->tcs.src_mq[i] >= 0 && c->tcs.src_mq[i] < n_v;
+    for (int u : c->tcs.units) {
+      if (!ok) break;
+      const int mt = u & 0xff, nt0 = (u >> 8) & 0xff, cnt = u >> 16;
+      ok = cnt >= 1 && cnt <= bbc::kTcTilesPerWarp && 16 * (mt + 1) <= c->tcs.nbp && 8 * (nt0 + cnt) <= c->tcs.nbp;
+    }
+    if (!ok) {
+      delete c;
+      return fail(nullptr, BBC_EINVAL, "internal: tensor-core schedule is not valid");
+    }
+  }
+  // fused FP32 contraction: warp batches, bank layout, one q of every pair {q, -q}
+  if (fused_path(prec) && !c->tc) {
+    try {
+      const FusedSchedule& f = fused_schedule(c->plan, c->plan, false);
       c->batches = f.batches;
       c->row_slot = f.layout.row_slot;
       c->n_slots = f.layout.n_slots;
@@ -339,11 +448,6 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
       c->n_slots = 0;
       c->max_units = 0;
     }
-  }
-  for (int q = 0; q < c->V; q++) {
-    const int Ls = lat->L, qx = q % Ls, qy = (q / Ls) % Ls, qz = q / (Ls * Ls);
-    const int nq = (Ls - qx) % Ls + Ls * ((Ls - qy) % Ls + Ls * ((Ls - qz) % Ls));
-    if (q <= nq) c->qlist.push_back(q);
   }
   {  // a configuration tuned earlier in this process for the same problem
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -412,6 +516,12 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_row_slot = (int*)(w + L.row_slot);
   c->d_orb_ptr = (int*)(w + L.orb_ptr);
   c->d_orb_site = (int*)(w + L.orb_site);
+  c->d_tc_base = (int*)(w + L.tc_base);
+  c->d_tc_units = (int*)(w + L.tc_units);
+  c->d_row_src = (int*)(w + L.row_src);
+  c->d_tc_cptr = (int*)(w + L.tc_cptr);
+  c->d_tc_terms = (float4*)(w + L.tc_terms);
+  c->d_G = c->tc ? w + L.G : nullptr;
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
   c->d_amax = (unsigned long long*)(w + L.amax);
@@ -425,22 +535,16 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_scale = (double*)(w + L.scale);
   c->d_flag = (int*)(w + L.flag);
   const bbc::Plan& p = c->plan;
-  std::vector<bbc::DevTask> tasks(p.tasks.size());
-  for (size_t i = 0; i < p.tasks.size(); i++) {
-    const bbc::PairTask& t = p.tasks[i];
-    bbc::DevTask& d = tasks[i];
-    // the fused FP32 kernel addresses its shared-memory copy of the rows: a
-    // task side's rows lie in one segment, so slot(off + k) = slot(off) + k
-    const bool slots = c->fused;
-    for (int r = 0; r < 8; r++) {
-      d.offA[r] = r < t.nA ? (slots ? c->row_slot[t.offA[r]] : t.offA[r]) : 0;
-      d.offB[r] = r < t.nB ? (slots ? c->row_slot[t.offB[r]] : t.offB[r]) : 0;
-    }
-    d.nAnB = t.nA | (t.nB << 8);
-    d.n1 = t.n1;
-    d.n2 = t.n2;
-    d.sA = t.sA1 | (t.sA2 << 16);
-    d.sB = t.sB1 | (t.sB2 << 16);
+  // the fused kernels address their shared-memory copy of the rows (slots)
+  const std::vector<bbc::PairTask>& run_tasks = fused_plan(c).tasks;
+  std::vector<bbc::DevTask> tasks(run_tasks.size());
+  bbc::to_dev_tasks(run_tasks.data(), run_tasks.size(), c->fused ? &c->row_slot : nullptr, tasks.data());
+  std::vector<float4> tc_terms(c->tcs.coef.size());  // Wick terms of the tensor-core path
+  for (size_t i = 0; i < tc_terms.size(); i++) {
+    const double x = c->tcs.coef[i];
+    const float h = (float)x;
+    tc_terms[i] = make_float4(h, (float)(x - (double)h), __int_as_float_host(c->tcs.src_q[i]),
+                              __int_as_float_host(c->tcs.src_mq[i]));
   }
   std::vector<float2> coef_df;  // double-float split of the Wick coefficients
   if (c->prec == BBC_DF64)
@@ -470,6 +574,11 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_row_slot, c->row_slot.data(), sizeof(int) * c->row_slot.size()},
       {c->d_orb_ptr, c->orb_ptr.data(), sizeof(int) * c->orb_ptr.size()},
       {c->d_orb_site, c->orb_site.data(), sizeof(int) * c->orb_site.size()},
+      {c->d_tc_base, c->tcs.base.data(), sizeof(int) * c->tcs.base.size()},
+      {c->d_tc_units, c->tcs.units.data(), sizeof(int) * c->tcs.units.size()},
+      {c->d_row_src, c->tcs.row_src.data(), sizeof(int) * c->tcs.row_src.size()},
+      {c->d_tc_cptr, c->tcs.out_ptr.data(), sizeof(int) * c->tcs.out_ptr.size()},
+      {c->d_tc_terms, tc_terms.data(), sizeof(float4) * tc_terms.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -599,6 +708,10 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
                                       c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "Wick sums");
     }
+  } else if (c->tc) {
+    StageScope scope(c, BBC_STAGE_CONTRACT);
+    e = launch_tc(c, slot);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core contraction");
   } else {
     const bool bf16 = c->prec == BBC_MIXED_BF16;
     const char* blk = bf16 ? c->d_blk16 + (size_t)slot * c->V * p.n_out * 4
@@ -747,9 +860,11 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     const bool bf16 = c->prec == BBC_MIXED_BF16;
     const char* blk = bf16 ? c->d_blk16 : c->d_blk;
     best_ms = -1.0;
-    for (int wv : kFusedWarpsCand)
+    const std::vector<int> warps_cand = c->tc ? std::vector<int>(std::begin(kRestWarpsCand), std::end(kRestWarpsCand))
+                                              : std::vector<int>(std::begin(kFusedWarpsCand), std::end(kFusedWarpsCand));
+    for (int wv : warps_cand)
       for (int sv : kFusedStepsCand) {
-        if (!bbc::fused_variant_supported(wv, sv)) continue;
+        if (c->tc ? !bbc::rest_variant_supported(wv, sv) : !bbc::fused_variant_supported(wv, sv)) continue;
         for (int kv : kChunkCand) {
           c->tune.fused_warps = wv;
           c->tune.fused_steps = sv;
@@ -757,6 +872,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
           st = apply_fused_units(c);
           if (st != BBC_OK) return st;
           const double v = time_launches(c, reps, [&] {
+            if (c->tc) return launch_tc(c, 0);
             return bbc::launch_contract_fused(blk, c->lat.L, p.n_out, c->d_row_slot, c->n_slots, c->d_qlist,
                                               (int)c->qlist.size(), c->d_tasks, (int)p.tasks.size(), c->d_batches,
                                               c->d_wptr, c->d_wunits, c->d_cptr, c->d_citem, c->d_ccoef,
@@ -947,9 +1063,14 @@ bbc_status bbc_stage_timing(bbc_ctx* c, double* ms, long long* launches) {
 
 bbc_status bbc_launch_counts(const bbc_ctx* c, int* per_load, int* per_build, int* per_contract) {
   if (!c) return BBC_EINVAL;
-  if (per_load) *per_load = 2;          // absmax, convert
-  if (per_build) *per_build = 1 + 3;    // block build, three FFT passes
-  if (per_contract) *per_contract = 2 + 1 + 3;  // pair products, Wick sums, scales, three inverse passes
+  // forward and inverse FFT passes: the fused (q-major) layout fuses the x and
+  // y passes for L <= 32; the field-major layout runs three
+  const bool xy = c->fused && c->lat.L <= 32;
+  const int passes = xy ? 2 : 3;
+  if (per_load) *per_load = 2;  // absmax, convert
+  if (per_build) *per_build = 1 + passes + (c->prec == BBC_MIXED_BF16 ? 1 : 0);  // build, FFT (, bfloat16 rounding)
+  // contraction kernel(s), scales, inverse passes
+  if (per_contract) *per_contract = (c->tc ? 2 : c->fused ? 1 : 2) + 1 + passes;
   return BBC_OK;
 }
 

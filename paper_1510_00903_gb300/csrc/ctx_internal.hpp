@@ -48,6 +48,18 @@ struct bbc_ctx {
   // whose rows and products do not fit one CTA's shared memory take the
   // unfused FP32 route (field-major FFT, pair products, Wick sums)
   bool fused = false;
+  // mixed FP32 / TF32 with tensor cores: the trace-form block pairs as one
+  // complex matrix product per pair {q, -q} (k_contract_tc), the other tasks
+  // and the Wick sums in k_contract_rest; the fused fields above then
+  // describe the rest kernel (its tasks, rows and warp units)
+  bool tc = false;
+  bbc::TcSplit tcs;
+  int* d_tc_base = nullptr;              // [nb] first block row of each block of G
+  int* d_tc_units = nullptr;             // [warps] tiles of G per warp
+  int* d_row_src = nullptr;              // [rest rows] block row of each compact row
+  int* d_tc_cptr = nullptr;              // [n_ch*16 + 1] Wick-term ranges per output
+  float4* d_tc_terms = nullptr;          // [terms] (coef hi, coef lo, source q, source -q)
+  char* d_G = nullptr;                   // [pairs][nbp][nbp] complex64
   bbc_tuning tune{1, 256, 16, 18, 1, 48};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
   std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
@@ -87,6 +99,25 @@ struct bbc_ctx {
 
 
 namespace bbc {
+
+// Device copies of plan tasks; with row_slot (fused kernels) the offsets
+// become shared-memory slots (a task side's rows lie in one segment, so
+// slot(off + k) = slot(off) + k).
+inline void to_dev_tasks(const PairTask* src, size_t n, const std::vector<int>* row_slot, DevTask* dst) {
+  for (size_t i = 0; i < n; i++) {
+    const PairTask& t = src[i];
+    DevTask& d = dst[i];
+    for (int r = 0; r < 8; r++) {
+      d.offA[r] = r < t.nA ? (row_slot ? (*row_slot)[t.offA[r]] : t.offA[r]) : 0;
+      d.offB[r] = r < t.nB ? (row_slot ? (*row_slot)[t.offB[r]] : t.offB[r]) : 0;
+    }
+    d.nAnB = t.nA | (t.nB << 8);
+    d.n1 = t.n1;
+    d.n2 = t.n2;
+    d.sA = t.sA1 | (t.sA2 << 16);
+    d.sB = t.sB1 | (t.sB2 << 16);
+  }
+}
 
 static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies, "diquark and family tables");
 

@@ -187,6 +187,134 @@ k_contract_fused(const void* __restrict__ blk, int L, int n_out, const int* __re
   }
 }
 
+// ------------------------------------- rest of the tensor-core contraction
+// acc (s + e) += (ch + cl) x v in double-float arithmetic: the product's
+// rounding error is kept exactly by an FMA, the sum's by TwoSum, and the error
+// word gathers both (a few terms per output: no renormalisation needed).
+__device__ __forceinline__ void df_axpy(float& s, float& e, float ch, float cl, float v) {
+  const float p = __fmul_rn(ch, v);
+  float err = __fmaf_rn(ch, v, -p);
+  err = __fmaf_rn(cl, v, err);
+  float sum, t;
+  two_sum(s, p, sum, t);
+  s = sum;
+  e = __fadd_rn(e, __fadd_rn(t, err));
+}
+
+// The CUDA-core half of the mixed contraction beside k_contract_tc.  One CTA
+// per pair {q, -q}: the rows the remaining tasks read are staged from the
+// q-major blocks through the compact row map (row i is block row row_src[i],
+// stored interleaved (F_q, F_-q) at slot row_slot[i]); their products run as
+// in k_contract_fused; G(q) of the pair is staged beside them; the signed
+// sums over Wick diagrams add coef x V, V = [P_q | P_-q | G], in double-float
+// arithmetic on the FP32 pipes (the products are FP32; the sums keep their
+// cancellations exact to 2^-48 of the terms).
+template <int WARPS, int STEPS>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const int* __restrict__ row_src,
+                const int* __restrict__ row_slot, int n_rows, int n_slots, const int* __restrict__ qlist,
+                const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
+                const int* __restrict__ wptr, const int4* __restrict__ wunits, const float4* __restrict__ G,
+                int g_elems, const int* __restrict__ cptr, const float4* __restrict__ terms, int n_outputs,
+                cpx<double>* __restrict__ ct) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kThreads = WARPS * 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = n_tasks * 16;                                      // products per side
+  float4* R = reinterpret_cast<float4*>(smem_raw);                  // [n_slots] (F_q, F_-q)
+  cpx<float>* V = reinterpret_cast<cpx<float>*>(smem_raw + (size_t)n_slots * sizeof(float4));  // [2 np | g_elems]
+  const int p = blockIdx.x, q = qlist[p];
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
+  const bool self = nq == q;
+  {
+    const float2* s0 = blk + (size_t)q * n_out;
+    const float2* s1 = blk + (size_t)nq * n_out;
+    for (int i = tid; i < n_rows; i += kThreads) {
+      const int src = __ldg(row_src + i);
+      const float2 x = __ldg(s0 + src), y = self ? x : __ldg(s1 + src);
+      R[__ldg(row_slot + i)] = make_float4(x.x, x.y, y.x, y.y);
+    }
+    float4* pz = reinterpret_cast<float4*>(V);
+    for (int i = tid; i < np; i += kThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* gp = G + (size_t)p * (g_elems >> 1);
+    float4* gs = reinterpret_cast<float4*>(V + 2 * np);
+    for (int i = tid; i < (g_elems >> 1); i += kThreads) gs[i] = __ldg(gp + i);
+  }
+  __syncthreads();
+  const int u1 = wptr[warp + 1];
+  for (int u = wptr[warp]; u < u1; u++) {
+    const int4 un = wunits[u];  // batch, -, k0, k1
+    const WarpBatch& wb = batches[un.x];
+    if (lane >= wb.n) continue;
+    const int ti = wb.task[lane];
+    const DevTask t = tasks[ti];
+    cpx<float>* p0 = V + ti * 16;
+    cpx<float>* p1 = V + np + ti * 16;
+    if (wb.nA == 4) unit_products_pair<4, 4, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+    else if (wb.nA == 2) unit_products_pair<2, 8, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+    else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+  }
+  __syncthreads();
+  const int sides = self ? 1 : 2;
+  for (int j = tid; j < sides * n_outputs; j += kThreads) {
+    const int side = j >= n_outputs, o = side ? j - n_outputs : j;
+    float rs = 0.f, re = 0.f, is = 0.f, ie = 0.f;
+    const int c1 = __ldg(cptr + o + 1);
+    for (int c = __ldg(cptr + o); c < c1; c++) {
+      const float4 tm = __ldg(terms + c);  // coef hi, coef lo, source for q, source for -q
+      const cpx<float> v = V[__float_as_int(side ? tm.w : tm.z)];
+      df_axpy(rs, re, tm.x, tm.y, v.re);
+      df_axpy(is, ie, tm.x, tm.y, v.im);
+    }
+    ct[(size_t)(side ? nq : q) * n_outputs + o] = cpx<double>((double)rs + (double)re, (double)is + (double)ie);
+  }
+}
+
+size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems) {
+  return (size_t)n_slots * sizeof(float4) + (size_t)2 * n_tasks * 16 * sizeof(cpx<float>) +
+         (size_t)g_elems * sizeof(cpx<float>);
+}
+
+bool rest_variant_supported(int warps, int steps) {
+  return (warps == 4 && (steps == 1 || steps == 2)) || (warps == 8 && steps == 1);
+}
+
+template <int WARPS, int STEPS>
+cudaError_t launch_rest_variant(size_t sm, int n_q, cudaStream_t st, const void* blk, int L, int n_out,
+                                const int* row_src, const int* row_slot, int n_rows, int n_slots, const int* qlist,
+                                const DevTask* tasks, int n_tasks, const WarpBatch* batches, const int* wptr,
+                                const int4* wunits, const void* G, int g_elems, const int* cptr, const float4* terms,
+                                int n_outputs, cpx<double>* ct) {
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem(k_contract_rest<WARPS, STEPS>, sm, granted);
+  if (e != cudaSuccess) return e;
+  k_contract_rest<WARPS, STEPS><<<n_q, WARPS * 32, sm, st>>>((const float2*)blk, L, n_out, row_src, row_slot, n_rows,
+                                                             n_slots, qlist, tasks, n_tasks, batches, wptr, wunits,
+                                                             (const float4*)G, g_elems, cptr, terms, n_outputs, ct);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const int* row_src, const int* row_slot, int n_rows,
+                                 int n_slots, const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
+                                 const WarpBatch* batches, const int* wptr, const int4* wunits, const void* G,
+                                 int g_elems, const int* cptr, const float4* terms, int n_ch, void* ct, int warps,
+                                 int steps, cudaStream_t st) {
+  if (n_q == 0) return cudaSuccess;
+  if ((g_elems & 1) || (g_elems && !G)) return cudaErrorInvalidValue;
+  const size_t sm = contract_rest_smem(n_slots, n_tasks, g_elems);
+  if (sm > kMaxSmemPerBlock) return cudaErrorInvalidValue;
+  cpx<double>* o = (cpx<double>*)ct;
+  const int n_outputs = n_ch * 16;
+#define BBC_REST(W, S)                                                                                            \
+  if (warps == W && steps == S)                                                                                   \
+    return launch_rest_variant<W, S>(sm, n_q, st, blk, L, n_out, row_src, row_slot, n_rows, n_slots, qlist, tasks, \
+                                     n_tasks, batches, wptr, wunits, G, g_elems, cptr, terms, n_outputs, o);
+  BBC_REST(4, 1) BBC_REST(4, 2) BBC_REST(8, 1)
+#undef BBC_REST
+  return cudaErrorInvalidValue;
+}
+
 size_t contract_fused_smem(int n_slots, int n_tasks, bool bf16) {
   const size_t np = (size_t)n_tasks * 16;
   return (((size_t)n_slots * (bf16 ? 8 : 16) + 15) & ~(size_t)15) + 2 * np * sizeof(cpx<float>);

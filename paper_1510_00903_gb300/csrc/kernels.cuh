@@ -112,6 +112,34 @@ cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* 
                                   const int* wptr, const int4* wunits, const int* cptr, const int* citem,
                                   const double* ccoef, int n_ch, void* ct, int warps, int steps, bool bf16,
                                   cudaStream_t st);
+// Tensor-core products of the trace-form block pairs (tc_contract.cu): per
+// pair {q, -q} (qlist[n_q]) the complex matrix G(q)[i][j] = sum_{u,v}
+// M_i(q)[u][v] M_j(-q)[v][u] of the nb blocks at rows base[nb] of the q-major
+// blocks blk[V][n_out] (complex64), written to G[n_q][nbp][nbp] (complex64);
+// warp w computes the tiles units[w] = m-tile | first n-tile << 8 | n-tiles << 16.
+// mode kTc3x: operands split into two TF32 words (FP32 accuracy); kTc1x: one
+// TF32 rounding per operand (trial precision).
+constexpr int kMaxTcBlocks = 64;     // blocks of G (G is at most 64 x 64)
+constexpr int kTcTilesPerWarp = 3;   // 16 x 8 complex tiles of G per warp
+constexpr int kTcMaxWarps = 16;
+constexpr int kTc3x = 0, kTc1x = 1;
+size_t contract_tc_smem(int nbp);
+cudaError_t launch_contract_tc(const void* blk, int L, int n_out, const int* base, int nb, int nbp, const int* qlist,
+                               int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st);
+// The rest of the mixed contraction (fused_contract.cu): per pair {q, -q}
+// the CUDA-core products of the other tasks on compact rows (row i of
+// n_rows is block row row_src[i], staged at row_slot[i]) and the signed
+// double-float sums over Wick diagrams of V = [P_q | P_-q | G(q)]: output o of
+// side q (-q) sums terms[c] = (coef hi, coef lo, src_q, src_mq) over c in
+// [cptr[o], cptr[o+1]), reading V[src_q] (V[src_mq]); g_elems = nbp^2 (0
+// without tensor-core products).  ct[V][n_ch*16] complex128.
+size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems);
+bool rest_variant_supported(int warps, int steps);
+cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const int* row_src, const int* row_slot, int n_rows,
+                                 int n_slots, const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
+                                 const WarpBatch* batches, const int* wptr, const int4* wunits, const void* G,
+                                 int g_elems, const int* cptr, const float4* terms, int n_ch, void* ct, int warps,
+                                 int steps, cudaStream_t st);
 // dst[i] = (bf16(src[i].re), bf16(src[i].im)), round to nearest even, n complex64 values.
 cudaError_t launch_to_bf16(const void* src, void* dst, size_t n, cudaStream_t st);
 // Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z

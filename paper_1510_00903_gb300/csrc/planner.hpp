@@ -134,6 +134,31 @@ struct FusedLayout {
 };
 void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedLayout* out);
 
+// Tensor-core split of a plan (tensor_split.cpp).  Tasks whose operands are
+// whole 12 x 12 blocks in the trace form tr(M_A(q) M_B(-q)) become entries
+// of one complex matrix product per pair {q, -q} over the blocks they read,
+//   G(q)[i][j] = sum_{u,v} M_i(q)[u][v] M_j(-q)[v][u],  G(-q) = G(q)^T;
+// the other tasks keep the CUDA-core products on a compact copy of the rows
+// they read.  (G's limits kMaxTcBlocks, kTcTilesPerWarp, kTcMaxWarps are in
+// kernels.cuh.)
+struct TcSplit {
+  int nb = 0, nbp = 0;               // blocks in G, and nb rounded up to 16 (G is nbp x nbp)
+  std::vector<int> base;             // nb: first block row of each block (M[u][v] at base + 12 u + v)
+  std::vector<int> units;            // per warp: m-tile | first n-tile << 8 | n-tiles << 16
+  long long tc_macs = 0;             // complex multiply-adds per site taken by G (as the plan counts them)
+  Plan rest;                         // the other tasks (tasks, pair_macs, n_out = compact rows)
+  std::vector<int> row_src;          // rest.n_out: block row behind each compact row
+  // signed sums over Wick diagrams into output o = 16 channel_pos + spin:
+  // terms [out_ptr[o], out_ptr[o+1]) of coef x V[src_q] for q and coef x
+  // V[src_mq] for -q, V = [P_q (16 n_rest) | P_-q (16 n_rest) | G (nbp^2)]
+  std::vector<int> out_ptr;
+  std::vector<double> coef;
+  std::vector<int> src_q, src_mq;
+};
+// nb = 0 when no task has the trace form (or G would exceed kMaxTcBlocks):
+// then every task is in rest.  Returns false only on an internal inconsistency.
+bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err);
+
 // Partition of the tasks into `groups` lists of near-equal cost (longest task
 // first to the cheapest list); each list is run by one warp for 32 q at a time.
 // by_shape: lists hold tasks of one shape (nA) only and come shape by shape,

@@ -82,6 +82,8 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
   if (dtype != BBC_C128 && dtype != BBC_C64) return fail(c, BBC_EINVAL, "bad dtype");
   if (c->prec != BBC_FP64 && c->prec != BBC_MIXED_FP32)
     return fail(c, BBC_EINVAL, "the static entry point runs BBC_FP64 and BBC_MIXED_FP32");
+  if (c->checks)  // the numeric checks need a flag word and a synchronising read-back
+    return fail(c, BBC_EINVAL, "the static entry point runs without numeric checks (bbc_set_checks(ctx, 0))");
   if (!S_light || !S_strange || !out_dev || (((uintptr_t)S_light | (uintptr_t)S_strange | (uintptr_t)out_dev) & 15))
     return fail(c, BBC_EINVAL, "propagators and output must be 16-byte aligned device pointers");
   const StaticLayout L = static_layout(c);
@@ -135,19 +137,7 @@ extern "C" bbc_status bbc_run_slice_static(bbc_ctx* c, int t, const void* S_ligh
     const size_t nt = p.tasks.size();
     for (size_t i0 = 0; i0 < nt; i0 += 64) {
       const size_t n = nt - i0 < 64 ? nt - i0 : 64;
-      for (size_t j = 0; j < n; j++) {
-        const bbc::PairTask& s = p.tasks[i0 + j];
-        bbc::DevTask& d = buf[j];
-        for (int r = 0; r < 8; r++) {
-          d.offA[r] = r < s.nA ? s.offA[r] : 0;
-          d.offB[r] = r < s.nB ? s.offB[r] : 0;
-        }
-        d.nAnB = s.nA | (s.nB << 8);
-        d.n1 = s.n1;
-        d.n2 = s.n2;
-        d.sA = s.sA1 | (s.sA2 << 16);
-        d.sB = s.sB1 | (s.sB2 << 16);
-      }
+      bbc::to_dev_tasks(p.tasks.data() + i0, n, nullptr, buf);
       e = cudaMemcpyAsync(w + L.tasks + i0 * sizeof(bbc::DevTask), buf, n * sizeof(bbc::DevTask),
                           cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return cuda_fail(c, e, "task upload");

@@ -6,7 +6,8 @@ It imports only ``synth`` (the seeded inputs) and ``oracle`` (the CPU FP64
 direct Wick enumeration), never the CUDA library, and writes one
 ``oracle_<case>.npz`` per case beside this file.  Each file holds the raw
 correlator C_ch(r) of one time slice (Sec. 2 Eq. 2 without the normalisation
-factor) at the listed relative distances r for all 52 channels of Sec. 4,
+factor) at the listed relative distances r for the 52 channels of Sec. 4 (three of
+them on the largest lattice),
 plus what the GPU tests need to rebuild the same inputs: the lattice, the
 generator tags, the storage type the propagators are rounded to, and a
 checksum of the propagators (sum of |S|^2 per flavour) so that a test can
@@ -33,7 +34,7 @@ import oracle.oracle as orc  # noqa: E402
 
 M_UD, M_S = 0.3, 0.4
 
-#: name -> (L, T, t0, seed, lattice, source, slices, n_r, storage)
+#: name -> (L, T, t0, seed, lattice, source, slices, n_r, storage[, channels])
 CASES = {
     # 16^3 x 32, one wall source, complex128 (the bench lattice of Sec. 5)
     "config2_L16_T32": (16, 32, 0, 0, 0, 0, [1, 8, 16, 31], 64, "c128"),
@@ -42,6 +43,9 @@ CASES = {
     # two items of the uneven batch: complex64 storage, sources at t0 = T/4, T/2
     "config4_L24_T48": (24, 48, 12, 0, 3, 1, [20], 32, "c64"),
     "config4_L32_T64": (32, 64, 32, 0, 6, 2, [40], 16, "c64"),
+    # 48^3 x 96, complex64 storage (the streamed lattice): three channels, as
+    # the oracle's sink tensors of five baryons take 30 GB of host memory here
+    "config5_L48_T96": (48, 96, 0, 0, 0, 0, [5], 8, "c64", [0, 10, 51]),
 }
 
 
@@ -64,9 +68,9 @@ def inputs(L, T, t0, seed, lattice, source, t, storage):
 
 
 def make(name: str) -> str:
-    L, T, t0, seed, lattice, source, slices, n_r, storage = CASES[name]
+    L, T, t0, seed, lattice, source, slices, n_r, storage = CASES[name][:9]
+    chans = list(CASES[name][9]) if len(CASES[name]) > 9 else list(range(52))
     r = r_samples(L, n_r, seed=1510 + L)
-    chans = list(range(52))
     C = np.zeros((len(slices), len(chans), len(r), 16), dtype=np.complex128)
     chk = np.zeros((len(slices), 2))
     for i, t in enumerate(slices):

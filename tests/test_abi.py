@@ -89,21 +89,31 @@ def test_project_rejects_bad_arguments():
 
 def test_tuning_defaults_validation_and_autotune_state():
     """Launch configurations: defaults, rejected shapes, and the autotuner's
-    state checks (no device work here)."""
+    state checks (no device work here).  Mixed FP32 runs the tensor-core
+    contraction (its CUDA-core kernel: 4 or 8 warps, two CTAs per SM); the
+    bfloat16 trial runs the fused CUDA-core kernel (8, 12 or 16 warps)."""
     c = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, [0, 1])
+    b = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_BF16, [0, 1])
     f = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
     try:
-        assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18,
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 8, "fused_chunk": 18,
                                          "fused_steps": 1, "pair_groups": 48}
-        bbc.bbc_set_tuning(c, 2, 512, 12, 36, 2)  # no workspace yet: host schedule only
-        assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 12, "fused_chunk": 36,
+        bbc.bbc_set_tuning(c, 2, 512, 4, 36, 2)  # no workspace yet: host schedule only
+        assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 512, "fused_warps": 4, "fused_chunk": 36,
                                          "fused_steps": 2, "pair_groups": 48}
-        for bad in [(3, 256, 16, 18), (1, 512, 16, 18), (4, 256, 16, 18), (1, 256, 10, 18), (1, 256, 16, 20),
-                    (1, 256, 16, 18, 2), (1, 256, 8, 18, 3)]:
+        for bad in [(3, 256, 8, 18), (1, 512, 8, 18), (4, 256, 8, 18), (1, 256, 10, 18), (1, 256, 8, 20),
+                    (1, 256, 8, 18, 2), (1, 256, 4, 18, 3), (1, 256, 16, 18), (1, 256, 12, 18)]:
             with pytest.raises(bbc.BBCError) as e:
                 bbc.bbc_set_tuning(c, *bad)
             assert e.value.status == bbc.BBC_EINVAL, bad
         assert bbc.bbc_get_tuning(c)["fused_chunk"] == 36  # a rejected set leaves the configuration
+        assert bbc.bbc_get_tuning(b) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18,
+                                         "fused_steps": 1, "pair_groups": 48}
+        bbc.bbc_set_tuning(b, 2, 512, 12, 36, 2)
+        for bad in [(1, 256, 16, 18, 2), (1, 256, 8, 18, 3), (1, 256, 4, 18)]:
+            with pytest.raises(bbc.BBCError) as e:
+                bbc.bbc_set_tuning(b, *bad)
+            assert e.value.status == bbc.BBC_EINVAL, bad
         # FP64 blocks of four sites need 365 KB of shared memory: not valid
         with pytest.raises(bbc.BBCError):
             bbc.bbc_set_tuning(f, 4, 512)
@@ -114,7 +124,22 @@ def test_tuning_defaults_validation_and_autotune_state():
         assert e.value.status == bbc.BBC_ESTATE
     finally:
         bbc.bbc_destroy(c)
+        bbc.bbc_destroy(b)
         bbc.bbc_destroy(f)
+
+
+def test_launch_counts_follow_the_path():
+    """Kernel launches per call: the tensor-core path runs two contraction
+    kernels, the fused CUDA-core path one, the FP64 path two (products and
+    Wick sums); the q-major layout fuses the x and y FFT passes up to L = 32."""
+    want = {bbc.BBC_MIXED_FP32: (2, 3, 5), bbc.BBC_MIXED_TF32: (2, 3, 5), bbc.BBC_MIXED_BF16: (2, 4, 4),
+            bbc.BBC_FP64: (2, 4, 6), bbc.BBC_DF64: (2, 4, 6)}
+    for prec, (load, build, contract) in want.items():
+        c = bbc.bbc_create(16, 4, 0, 0.3, 0.4, prec, list(range(52)))
+        try:
+            assert bbc.bbc_launch_counts(c) == {"load": load, "build": build, "contract": contract}, prec
+        finally:
+            bbc.bbc_destroy(c)
 
 
 def test_lower_components_plan_and_errors():
@@ -241,4 +266,27 @@ def test_plan_export_arguments():
         assert p["row_ptr"][0] == 0 and p["row_ptr"][-1] == len(p["terms"]) == sizes[1]
         assert p["out_ptr"][-1] == len(p["items"]) == sizes[3] and len(p["out_ptr"]) == 2 * 16 + 1
     finally:
+        bbc.bbc_destroy(c)
+
+
+def test_static_entry_point_argument_checks():
+    """bbc_run_slice_static rejects, before any device work: other precisions,
+    contexts with numeric checks, and misaligned pointers."""
+    fake = 1 << 20  # 16-byte aligned stand-ins: never dereferenced on these paths
+    t = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_TF32, [0])
+    c = bbc.bbc_create(4, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0])
+    try:
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_run_slice_static(t, 1, fake, fake, bbc.BBC_C128, fake, True)
+        assert e.value.status == bbc.BBC_EINVAL and "BBC_FP64" in str(e.value)
+        bbc.bbc_set_checks(c, bbc.BBC_CHECK_OUTPUT)
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_run_slice_static(c, 1, fake, fake, bbc.BBC_C128, fake, True)
+        assert e.value.status == bbc.BBC_EINVAL and "numeric checks" in str(e.value)
+        bbc.bbc_set_checks(c, 0)
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_run_slice_static(c, 1, fake + 8, fake, bbc.BBC_C128, fake, True)
+        assert e.value.status == bbc.BBC_EINVAL
+    finally:
+        bbc.bbc_destroy(t)
         bbc.bbc_destroy(c)

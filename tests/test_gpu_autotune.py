@@ -31,8 +31,9 @@ def test_autotune_then_oracle(precision):
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
-    # FP64: four pair_groups candidates; mixed: (warps, steps) shapes x 5 chunks
-    n_second = 4 if precision == bbc.BBC_FP64 else 25
+    # FP64: four pair_groups candidates; mixed (tensor cores): the CUDA-core
+    # kernel's (warps, steps) shapes x 5 chunks
+    n_second = 4 if precision == bbc.BBC_FP64 else 15
     assert len(ms) == len(BUILD) + n_second
     assert all(v > 0 for v in ms[len(BUILD):])
     assert cfg["pair_groups"] in (48, 96, 192, 384)
@@ -47,7 +48,7 @@ def test_autotune_then_oracle(precision):
     cor.close()
 
 
-@pytest.mark.parametrize("precision", [bbc.BBC_FP64, bbc.BBC_MIXED_FP32])
+@pytest.mark.parametrize("precision", [bbc.BBC_FP64, bbc.BBC_MIXED_FP32, bbc.BBC_MIXED_BF16])
 def test_every_configuration_matches(precision):
     L, T, t = 8, 4, 2
     chans = [1, 14, 41]
@@ -57,7 +58,9 @@ def test_every_configuration_matches(precision):
     want = orc.normalise(orc.correlator(L, F["u"][t], F["d"][t], F["s"][t], chans), chans, t, 0.3, 0.4)
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     ref = None
-    shapes = [(8, 1), (8, 2), (12, 1), (12, 2), (16, 1)]
+    # mixed FP32: the tensor-core path's CUDA-core kernel; bfloat16: the fused kernel
+    shapes = [(4, 1), (4, 2), (8, 1)] if precision == bbc.BBC_MIXED_FP32 else [(8, 1), (8, 2), (12, 1), (12, 2), (16, 1)]
+    tol = {bbc.BBC_FP64: 1e-12, bbc.BBC_MIXED_FP32: MIXED_TOL, bbc.BBC_MIXED_BF16: 2e-2}[precision]
     # FP64: every pair_groups value (the fused fields are ignored there)
     fused = [(16, 18, 1, g) for g in (48, 96, 192, 384)] if precision == bbc.BBC_FP64 else \
         [(w, k, st, 48) for w, st in shapes for k in (0, 18, 36, 72, 144)]
@@ -71,8 +74,7 @@ def test_every_configuration_matches(precision):
                 assert precision == bbc.BBC_FP64 and sites == 4  # 365 KB of shared memory
                 continue
             out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
-            assert _err(out, want) < (1e-12 if precision == bbc.BBC_FP64 else MIXED_TOL), (sites, threads, warps,
-                                                                                          chunk, steps, groups)
+            assert _err(out, want) < tol, (sites, threads, warps, chunk, steps, groups)
             if precision == bbc.BBC_FP64:
                 # the build sums every row in the same order whatever the shape, and
                 # a task's products do not depend on the list it is in
@@ -80,5 +82,5 @@ def test_every_configuration_matches(precision):
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == (12 if precision == bbc.BBC_FP64 else 100)
+    assert tried == {bbc.BBC_FP64: 12, bbc.BBC_MIXED_FP32: 60, bbc.BBC_MIXED_BF16: 100}[precision]
     cor.close()

@@ -48,7 +48,7 @@ def test_df64_sampled(L):
                   normalised=False)[0].cpu().numpy()
     rs = [0, 1, L ** 3 // 3, L ** 3 - 1]
     want = orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], ch, rs)
-    scale = np.abs(got).reshape(len(ch), -1).max(axis=1)
+    scale = np.abs(want).reshape(len(ch), -1).max(axis=1)  # the oracle's scale
     err = np.abs(got[:, rs] - want).reshape(len(ch), -1).max(axis=1) / scale
     print(f"df64 L={L} sampled: max {err.max():.2e}")
     assert err.max() < FP64_TOL, err

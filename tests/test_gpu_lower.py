@@ -47,7 +47,7 @@ def test_lower_sampled_L16():
                   normalised=False)[0].cpu().numpy()
     rs = [0, 1, 777, 4095]
     want = orc.correlator(L, F["u"][0], F["d"][0], F["s"][0], ch, rs, lower=True)
-    scale = np.abs(got).reshape(len(ch), -1).max(axis=1)
+    scale = np.abs(want).reshape(len(ch), -1).max(axis=1)  # the oracle's scale
     err = np.abs(got[:, rs] - want).reshape(len(ch), -1).max(axis=1) / scale
     assert err.max() < FP64_TOL, err
     cor.close()
