@@ -171,11 +171,17 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", choices=["config2", "batched", "L48", "decuplet"], default="config2",
-                    help="config2: 52 channels, 16^3 x 32, FP64 and mixed (default); batched: 8 lattices, "
-                         "L in {16,24,32}, T in {32,48,64}, 4 sources each, mixed, one CUDA graph per step; "
-                         "L48: 48^3 x 96, 4 sources, mixed, complex64 propagators streamed from pinned host memory; "
-                         "decuplet: the 90 Omega Omega and p Omega ids, 16^3 x 32, FP64, double-float and mixed")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: time the headline only (no legs, no CPU baseline), e.g. under a profiler")
+    ap.add_argument("--workload", choices=["default", "config2", "batched", "L48", "decuplet"], default="default",
+                    help="default: headline 48^3 x 96 (4 wall sources, 52 channels, complex64 propagators) in "
+                         "FP64-accurate double-float arithmetic, with short legs (the same lattice in mixed "
+                         "precision streamed from the host, the uneven batch, 16^3 x 32 in FP64 and double-float, "
+                         "the 32^3 x 64 precision comparison); config2: 52 channels, 16^3 x 32, FP64 and mixed; "
+                         "batched: 8 lattices, L in {16,24,32}, T in {32,48,64}, 4 sources each, mixed, one CUDA "
+                         "graph per step; L48: 48^3 x 96, 4 sources, mixed, complex64 propagators streamed from "
+                         "pinned host memory; decuplet: the 90 Omega Omega and p Omega ids, 16^3 x 32, FP64, "
+                         "double-float and mixed")
     ap.add_argument("--error-report", action="store_true",
                     help="per-channel error of the mixed path against the FP64 path (L=32, T=64, t=32), "
                          "the FP64 path checked against the oracle at sampled points")
@@ -214,24 +220,26 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    n_pts = 16
     for _ in range(args.warmup):
-        oracle_sample(seed=1)
-    vals, secs = [], []
+        oracle_sample_L48(n_pts)
+    secs = []
     for k in range(args.steps):
-        v, dt, cores = oracle_sample(seed=2 + k)
-        vals.append(v)
+        v, dt, cores = oracle_sample_L48(n_pts)
         secs.append(dt)
-    value = args.steps * N_CH / sum(secs)
+    value = args.steps * n_pts / sum(secs)
     line = {
         "impl": "reference", "metric": "BB correlator site*channels/s", "value": value,
         "unit": "site*channels/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "52 channels, L=16, T=32, one wall source; each step the CPU FP64 oracle "
-                               "(direct Wick sum over X) at one (t, r) point, all 52 channels x 16 spins",
-                   "L": L_BENCH, "T": T_BENCH, "channels": N_CH},
+        "config": {"workload": "all 52 channels, L=48, T=96, 4 wall sources (the headline lattice); each step the "
+                               "CPU FP64 oracle (direct Wick sum over X) at 16 (r, channel) points: t=T/2, channel "
+                               "p Xi- <- p Xi- (the cheapest octet channel), 16 random r, 16 spins each",
+                   "L": L5, "T": T5, "sources": N_SRC5, "channels": N_CH},
         "cpu_baseline": {"value": value, "unit": "site*channels/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: t=T/2, one random r, 52 channels, 16 spins, sum over all 4096 X"},
+                         "sample": "per step: 48^3 lattice, t=T/2, p Xi- <- p Xi-, 16 random r, 16 spins, sums "
+                                   "over all 110592 X"},
         "e2e": {"value": value, "unit": "site*channels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -322,6 +330,8 @@ def run_ours(args, torch, rank, world, local):
         return run_l48(args, torch, dev, bbc)
     if args.workload == "decuplet":
         return run_decuplet(args, torch, dev, bbc, synth)
+    if args.workload == "default" and not args.single_slice:
+        return run_default(args, torch, dev, bbc, synth)
     L, T = L_BENCH, T_BENCH
     V = L ** 3
     if args.single_slice:
@@ -761,6 +771,330 @@ def run_l48(args, torch, dev, bbc):
                          n_src * T * 2 * L ** 3 * 144 * 8),
                      "l2": "no flush: block fields of one slice (6.5 GB) exceed the 129 MB L2"},
           "tuning": tuned, "clocks": sampler.summary()})
+
+
+# ------------------------------------------------------------ default run
+#: headline lattice: 48^3 x 96, four wall sources, 52 channels, complex64 storage
+L5, T5, N_SRC5 = 48, 96, 4
+#: slices per headline step: a quarter of one source's time slices, so 16
+#: steps cover the four sources once and 20 timed steps stay near a minute
+HEAD_SLICES = 24
+#: double-float arithmetic on the FP32 pipes: one complex multiply-add of the
+#: block-pair products is four double-float multiply-adds of 12 FP32
+#: instructions each (TwoProduct of the high words, the cross terms, TwoSum
+#: into the accumulator)
+DF_INSTR_PER_CMAC = 48
+#: FP32 instruction issue of the whole GPU: 152 SMs x 128 lanes x 2070 MHz
+FP32_ISSUE_TOPS = 152 * 128 * 2.070e9 / 1e12
+DF_CMAC_PEAK_TFLOPS = FP32_ISSUE_TOPS / DF_INSTR_PER_CMAC * 8.0
+DF_PEAK_SOURCE = "derived: 40.27 T FP32 instr/s / 48 instr per double-float complex MAC x 8 flop"
+
+
+def channel_errors(torch, got, ref):
+    """Per channel: max over r and spin of |got - ref| / max |ref| (device tensors [n_ch, V, 16]);
+    returns the maximum and median over channels and the worst channel."""
+    num = (got - ref).abs().flatten(1).amax(dim=1)
+    den = ref.abs().flatten(1).amax(dim=1)
+    e = (num / den).double().cpu().numpy()
+    return {"max": float("%.3g" % e.max()), "median": float("%.3g" % np.median(e)), "worst_channel": int(e.argmax())}
+
+
+def timed_steps(torch, dev, stream, step, K, W, world, sampler=None):
+    """W untimed then K timed calls of step(k) between barriers; CUDA events on `stream`."""
+    from paper_1510_00903_gb300 import shard
+    for k in range(W):
+        step(k)
+    torch.cuda.synchronize(dev)
+    shard.barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with (sampler if sampler else _Null()):
+        e0.record(stream)
+        for k in range(K):
+            step(W + k)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    shard.barrier(world)
+    torch.cuda.synchronize(dev)
+    return shard.max_over_ranks(e0.elapsed_time(e1) / K, world, dev)
+
+
+def oracle_sample_L48(n_points):
+    """The oracle on the headline lattice: one channel (p Xi- <- p Xi-, the
+    cheapest octet channel), n_points random r at t = T/2, each a sum over all
+    48^3 X (sink tensors included); returns (site*channels/s, seconds, cores)."""
+    import synth
+    import oracle.oracle as orc
+    orc.build()
+    t = T5 // 2
+    F = synth.flavour_set(L5, T5, 0, M_UD, M_S, seed=5, times=[t])
+    rng = np.random.default_rng(t)
+    r = list(rng.integers(0, L5 ** 3, size=n_points))
+    t0 = time.perf_counter()
+    orc.correlator(L5, F["u"][0], F["d"][0], F["s"][0], [16], r)
+    dt = time.perf_counter() - t0
+    return n_points / dt, dt, min(n_points, orc.threads())
+
+
+def run_default(args, torch, dev, bbc, synth):
+    """Headline: 48^3 x 96, 4 wall sources, 52 channels, complex64 propagators,
+    FP64-accurate double-float arithmetic, inputs resident in HBM; e2e the same
+    through Correlators.run_to_host (pinned host in and out).  Legs: the same
+    lattice in mixed precision streamed from pinned host memory, the uneven
+    batch as one CUDA graph, 16^3 x 32 in FP64 and double-float, the
+    precision comparison on one 32^3 x 64 slice; each leg's error is measured
+    against the FP64 path on one slice."""
+    from paper_1510_00903_gb300 import shard
+    rank, world, local = dist_env()
+    chans = list(range(N_CH))
+    V5 = L5 ** 3
+    here = os.path.dirname(os.path.abspath(__file__))
+    stream = torch.cuda.Stream(dev)
+    # one source's wall-source propagators (complex64); the four sources share the draw
+    S_dev = [device_propagators(torch, dev, L5, T5, 0, m, 1000 * rank + s) for m, s in ((M_UD, 91), (M_S, 92))]
+    torch.cuda.synchronize(dev)
+    out = torch.empty((N_CH, V5, 16), dtype=torch.complex128, device=dev)
+
+    # ---- headline: double-float, HEAD_SLICES slices of one source per step
+    cors, ws = [], None
+    for k in range(N_SRC5):
+        c = bbc.Correlators(L5, T5, (k * T5) // N_SRC5, M_UD, M_S, channels=chans, precision=bbc.BBC_DF64,
+                            device=dev, stream=stream, workspace=ws)
+        ws = c.workspace
+        cors.append(c)
+    sizes = cors[0].sizes()
+    tune, _ = cors[0].autotune(S_dev[0][0], S_dev[1][0], t=0, reps=1)
+    for c in cors[1:]:
+        c.set_tuning(tune)
+    def head_step(k):
+        src, part = (k // 4) % N_SRC5, k % 4
+        cors[src].run_each(S_dev[0], S_dev[1], range(HEAD_SLICES * part, HEAD_SLICES * (part + 1)), out)
+
+    bbc.bbc_enable_stage_timing(cors[0].ctx, True)
+    for c in cors[1:]:
+        bbc.bbc_enable_stage_timing(c.ctx, True)
+    sampler = ClockSampler(local)
+    ms = timed_steps(torch, dev, stream, head_step, args.steps, args.warmup, world, sampler)
+    clocks = sampler.summary()
+    stage_tot = {}
+    n_contract = 0
+    for c in cors:
+        st = bbc.bbc_stage_timing(c.ctx)
+        for key, (v, n) in st.items():
+            stage_tot[key] = stage_tot.get(key, 0.0) + v
+        n_contract += st["contract"][1]
+        bbc.bbc_enable_stage_timing(c.ctx, False)
+    # timing covered warm-up and timed steps: the per-step stage times are averages over both
+    n_steps_timed = args.steps + args.warmup
+    stage_ms = {k: v / n_steps_timed for k, v in stage_tot.items()}
+    c_avg = stage_tot["contract"] / max(n_contract, 1)
+    flop = 8.0 * sizes["pair_macs_per_site"] * V5
+    achieved = flop / (c_avg * 1e-3) / 1e12
+    # DRAM bytes per launch from the ncu capture of the 16^3 slice (the full-size
+    # launch is too large to capture), scaled to 48^3 by the sites processed
+    traffic16 = profiled_traffic(os.path.join(here, "profiles", "k_pair_products_df_L16_slice.md"),
+                                 os.path.join(here, "paper_1510_00903_gb300", "csrc", "pair_products_df.cu"),
+                                 sizes["pair_items"])
+    traffic = None if traffic16 is None else traffic16 * V5 / L_BENCH ** 3
+    value = shard.job_throughput(HEAD_SLICES * V5 * N_CH, world, ms)
+    # e2e: pinned host propagators in, pinned host correlators out (two-slice ring)
+    S_host = [x[:HEAD_SLICES].cpu().pin_memory() for x in S_dev]
+    ring = torch.empty((2, N_CH, V5, 16), dtype=torch.complex128, pin_memory=True)
+
+    def e2e_step(k):
+        cors[k % N_SRC5].run_to_host(S_host[0], S_host[1], range(HEAD_SLICES), ring)
+
+    k_e2e = max(1, args.steps // 4)
+    ms_e2e = timed_steps(torch, dev, stream, e2e_step, k_e2e, 1, world)
+    del S_host, ring
+    # error of one slice against the FP64 path on the same inputs
+    t_chk = 50
+    cors[0].run_each(S_dev[0], S_dev[1], [t_chk], out)
+    ref64 = bbc.Correlators(L5, T5, 0, M_UD, M_S, channels=chans, precision=bbc.BBC_FP64, device=dev, stream=stream)
+    ref_out = torch.empty_like(out)
+    ref64.run_each(S_dev[0], S_dev[1], [t_chk], ref_out)
+    torch.cuda.synchronize(dev)
+    head_err = channel_errors(torch, out, ref_out)
+    for c in cors:
+        c.close()
+    del cors, ws
+
+    if args.headline_only:
+        ref64.close()
+        if rank == 0:
+            print(json.dumps({"metric": "BB correlator site*channels/s", "value": value, "ms_per_step": ms,
+                              "roofline_achieved": achieved, "err_vs_fp64": head_err,
+                              "stage_ms_per_step": stage_ms}), flush=True)
+        return
+    # ---- leg: the same lattice, mixed precision (tensor cores), streamed from pinned host memory
+    mcors, mws = [], None
+    for k in range(N_SRC5):
+        c = bbc.Correlators(L5, T5, (k * T5) // N_SRC5, M_UD, M_S, channels=chans, precision=bbc.BBC_MIXED_FP32,
+                            device=dev, stream=stream, workspace=mws)
+        mws = c.workspace
+        mcors.append(c)
+    S_host_all = [x.cpu().pin_memory() for x in S_dev]
+    mtune, _ = mcors[0].autotune(S_dev[0][0], S_dev[1][0], t=0, reps=1)
+    for c in mcors[1:]:
+        c.set_tuning(mtune)
+    bbc.bbc_enable_stage_timing(mcors[0].ctx, True)
+
+    def mixed_step(k):
+        mcors[k % N_SRC5].run_streamed(S_host_all[0], S_host_all[1], range(T5), out)
+
+    k_leg = max(2, min(3, args.steps))
+    ms_mixed = timed_steps(torch, dev, stream, mixed_step, k_leg, 1, world)
+    st_m = bbc.bbc_stage_timing(mcors[0].ctx)
+    mcors[0].run_each(S_dev[0], S_dev[1], [t_chk], out)
+    torch.cuda.synchronize(dev)
+    mixed_err = channel_errors(torch, out, ref_out)
+    mcounts = plan_counts(bbc.bbc_plan_export(mcors[0].ctx), mcors[0].sizes())
+    n_m = max(st_m["build"][1], 1)
+    mstage = {k: v[0] / n_m * T5 for k, v in st_m.items()}  # per source of 96 slices
+    mixed_roof = step_roofline(mcounts, V5, T5, mstage, ms_mixed, mixed=True)
+    for c in mcors:
+        c.close()
+    ref64.close()
+    del mcors, mws, S_host_all, ref64, ref_out, S_dev, out
+
+    # ---- leg: 16^3 x 32 in FP64 and double-float (the paper's lattice), inputs in HBM
+    L2_, T2_ = L_BENCH, T_BENCH
+    V2 = L2_ ** 3
+    F2 = synth.flavour_set(L2_, T2_, 0, M_UD, M_S, **shard.rank_source(rank))
+    S2 = [torch.from_numpy(F2["u"]).to(dev), torch.from_numpy(F2["s"]).to(dev)]
+    out2 = torch.empty((T2_, N_CH, V2, 16), dtype=torch.complex128, device=dev)
+    legs16 = {}
+    ref16 = None
+    for name, prec in (("fp64", bbc.BBC_FP64), ("df64", bbc.BBC_DF64), ("mixed", bbc.BBC_MIXED_FP32),
+                       ("tf32_trial", bbc.BBC_MIXED_TF32)):
+        c = bbc.Correlators(L2_, T2_, 0, M_UD, M_S, channels=chans, precision=prec, device=dev, stream=stream)
+        sz = c.sizes()
+        cnt = plan_counts(bbc.bbc_plan_export(c.ctx), sz)
+        tn, _ = c.autotune(S2[0][0], S2[1][0], t=0, reps=2)
+        bbc.bbc_enable_stage_timing(c.ctx, True)
+        k16 = max(2, min(5, args.steps))
+        m16 = timed_steps(torch, dev, stream, lambda k: c.run(S2[0], S2[1], range(T2_), out=out2), k16, 2, world)
+        st16 = bbc.bbc_stage_timing(c.ctx)
+        sm16 = {k: v[0] / (k16 + 2) for k, v in st16.items()}
+        leg = {"value": shard.job_throughput(V2 * T2_ * N_CH, world, m16), "ms_per_step": round(m16, 3)}
+        if name == "fp64":
+            ref16 = out2[16].clone()
+            ca = st16["contract"][0] / max(st16["contract"][1], 1)
+            ach = 8.0 * sz["pair_macs_per_site"] * V2 / (ca * 1e-3) / 1e12
+            leg["roofline"] = {"kernel": "k_pair_products<double>", "achieved": round(ach, 4),
+                               "peak": FP64_CMAC_PEAK_TFLOPS, "frac": round(ach / FP64_CMAC_PEAK_TFLOPS, 4),
+                               "traffic": profiled_traffic(
+                                   os.path.join(here, "profiles", "k_pair_products_f64_L16_slice.md"),
+                                   os.path.join(here, "paper_1510_00903_gb300", "csrc", "pair_products.cu"),
+                                   sz["pair_items"])}
+        else:
+            leg["err_vs_fp64"] = channel_errors(torch, out2[16], ref16)
+        if prec in (bbc.BBC_FP64, bbc.BBC_MIXED_FP32):
+            roof = step_roofline(cnt, V2, T2_, sm16, m16, mixed=prec == bbc.BBC_MIXED_FP32)
+            leg["step_roofline"] = {"floor_ms": round(roof["floor_ms"], 3), "frac": round(roof["frac"], 4)}
+            leg["stage_ms"] = {k: round(v, 2) for k, v in sm16.items() if v}
+        if name == "fp64":
+            pj = measure_projection(torch, c, out2, stream)
+            leg["projection"] = {"ms": round(pj["ms_per_launch"], 3), "gbs": round(pj["achieved_gbs"], 1),
+                                 "frac": round(pj["frac"], 4)}
+        legs16[name] = leg
+        c.close()
+    del out2, S2
+
+    # ---- leg: the uneven batch (8 lattices x 4 sources, mixed, complex64) as one CUDA graph per step
+    batched = batched_leg(args, torch, dev, bbc, world)
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt, cores = oracle_sample_L48(16)
+        cpu = {"value": v, "unit": "site*channels/s", "cores": cores, "kind": "oracle",
+               "sample": f"48^3, t=T/2, p Xi- <- p Xi- (cheapest channel), 16 random r x 16 spins, all X ({dt:.1f} s)"}
+    c0 = bbc.bbc_create(L5, T5, 0, M_UD, M_S, bbc.BBC_DF64, chans)
+    lc = bbc.bbc_launch_counts(c0)
+    bbc.bbc_destroy(c0)
+    launches = args.steps * HEAD_SLICES * (2 * lc["load"] + lc["build"] + lc["contract"])
+    line = {
+        "metric": "BB correlator site*channels/s", "value": value, "unit": "site*channels/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "df64", "data": "synthetic",
+        "config": {"workload": "52 channels, L=48, T=96, 4 wall sources (one shared synthetic draw), complex64 "
+                               "propagators in HBM, FP64-accurate double-float arithmetic; a step is "
+                               f"{HEAD_SLICES} slices of one source (16 steps = the 4 sources)",
+                   "L": L5, "T": T5, "sources": N_SRC5, "channels": N_CH, "slices_per_step": HEAD_SLICES,
+                   "l2": "no flush: one slice's blocks (13 GB) exceed the 129 MB L2"},
+        "e2e": {"value": shard.job_throughput(HEAD_SLICES * V5 * N_CH, world, ms_e2e), "unit": "site*channels/s",
+                "h2d_bytes_per_step": int(HEAD_SLICES * 2 * V5 * 144 * 8),
+                "d2h_bytes_per_step": int(HEAD_SLICES * N_CH * V5 * 16 * 16)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_pair_products_df", "achieved": achieved, "peak": DF_CMAC_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / DF_CMAC_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": DF_PEAK_SOURCE, "avg_launch_ms": round(c_avg, 3)},
+        "err_vs_fp64": head_err,
+        "stage_ms_per_step": {k: round(v, 1) for k, v in stage_ms.items() if v > 0.5},
+        # legs, one array each: [site*channels/s, ms per step, step roofline frac, max per-channel error vs FP64]
+        "legs": {
+            "fields": ["value", "ms_per_step", "step_roofline_frac", "err_vs_fp64_max"],
+            "mixed_L48_streamed": [shard.job_throughput(T5 * V5 * N_CH, world, ms_mixed), round(ms_mixed, 1),
+                                   round(mixed_roof["frac"], 3), mixed_err["max"]],
+            "batched_config4": [batched["value"], batched["ms_per_step"], None, batched["err_vs_fp64"]["max"]],
+        },
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    for name, leg in legs16.items():
+        line["legs"][name + "_L16"] = [leg["value"], leg["ms_per_step"], leg.get("step_roofline", {}).get("frac"),
+                                       leg.get("err_vs_fp64", {}).get("max")]
+    line["legs"]["fp64_L16_kernel_roofline"] = legs16["fp64"]["roofline"]
+    line["legs"]["projection_L16"] = legs16["fp64"]["projection"]
+    # the legs in full (stage times, floors, errors), one line before the result line
+    detail = {"detail": "legs of the line below", "mixed_L48_streamed": {
+        "value": shard.job_throughput(T5 * V5 * N_CH, world, ms_mixed), "ms_per_step": ms_mixed,
+        "slices_per_step": T5, "step_roofline": {"floor_ms": mixed_roof["floor_ms"], "frac": mixed_roof["frac"]},
+        "err_vs_fp64": mixed_err, "stage_ms": {k: round(v, 1) for k, v in mstage.items() if v > 0.5}},
+        "L16_T32": legs16, "batched": batched, "headline_tuning": tune}
+    print(json.dumps(detail), flush=True)
+    print(json.dumps(line), flush=True)
+
+
+def batched_leg(args, torch, dev, bbc, world):
+    """The uneven batch (8 lattices, 4 sources each, 52 channels, mixed,
+    complex64) recorded as one CUDA graph; a step is one replay.  Error: one
+    L=32 slice of the batch against the FP64 path."""
+    lattices = [(16, 32), (16, 48), (24, 32), (24, 48), (24, 64), (32, 48), (32, 64), (16, 64)]
+    rank = dist_env()[0]
+    sd = 1000 * rank
+    inputs = [(device_propagators(torch, dev, L, T, 0, M_UD, sd + 10 + i),
+               device_propagators(torch, dev, L, T, 0, M_S, sd + 50 + i))
+              for i, (L, T) in enumerate(lattices)]
+    b = bbc.LatticeBatch(lattices, inputs, n_sources=4, channels=list(range(N_CH)), precision=bbc.BBC_MIXED_FP32,
+                         device=dev)
+    tuned = b.autotune(reps=1)
+    t_cap = time.perf_counter()
+    g = b.capture()
+    t_cap = time.perf_counter() - t_cap
+    ms = timed_steps(torch, dev, b.stream, lambda k: g.replay(), max(2, min(3, args.steps)), 1, world)
+    # error: slice 40 of the (32, 64) lattice, first source, against the FP64 path
+    i32 = lattices.index((32, 64))
+    Sl, Ss = inputs[i32]
+    c = b.cors[i32][0]
+    o = torch.empty((N_CH, 32 ** 3, 16), dtype=torch.complex128, device=dev)
+    c.run_each(Sl, Ss, [40], o)
+    ref = bbc.Correlators(32, 64, 0, M_UD, M_S, channels=list(range(N_CH)), precision=bbc.BBC_FP64, device=dev)
+    ro = torch.empty_like(o)
+    ref.run_each(Sl, Ss, [40], ro)
+    torch.cuda.synchronize(dev)
+    err = channel_errors(torch, o, ro)
+    ref.close()
+    units = b.sites_channels()
+    slices = sum(4 * T for _, T in lattices)
+    b.close()
+    from paper_1510_00903_gb300 import shard
+    return {"value": shard.job_throughput(units, world, ms), "ms_per_step": round(ms, 2), "slices_per_step": slices,
+            "workload": "8 lattices, L 16/24/32, T 32/48/64, 4 sources, mixed, complex64, one CUDA graph per step",
+            "err_vs_fp64": err}
 
 
 class _Null:

@@ -450,12 +450,36 @@ class Correlators:
             cur.wait_stream(self.stream)
         return out
 
+    def run_each(self, S_light, S_strange, times, out, normalised: bool = True, on_slice=None):
+        """Slices whose propagators are already on the device ([T, V, 12, 12]):
+        one slice after the other through the context's first slot, every
+        slice's correlators written into the same ``out`` ([n_channels, V,
+        16]); ``on_slice(t, out)``, if given, is called after each slice's work
+        is queued (to queue a consumer on the context stream)."""
+        torch = self.torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            for t in times:
+                self.load(BBC_LIGHT, 0, t, S_light[t])
+                self.load(BBC_STRANGE, 0, t, S_strange[t])
+                self.build(1)
+                self.contract(0, out, normalised)
+                if on_slice is not None:
+                    on_slice(t, out)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+        return out
+
     def run_to_host(self, S_light, S_strange, times, out_host, normalised: bool = True):
         """End to end from pinned host propagators ([T, V, 12, 12]) to pinned
         host correlators out_host [len(times), n_channels, V, 16] complex128:
         the host-to-device copy of slice i+1, the compute of slice i and the
         device-to-host copy of slice i-1 overlap (two copy streams, double
-        buffers on the device)."""
+        buffers on the device).  An out_host of R < len(times) slices is used
+        as a ring: slice i lands in out_host[i % R] (a consumer reads it before
+        slice i + R is copied there)."""
         torch = self.torch
         times = list(times)
         if not times:
@@ -480,7 +504,7 @@ class Correlators:
             done[b].record(self.stream)
             with torch.cuda.stream(d2h):
                 d2h.wait_event(done[b])
-                out_host[i].copy_(obufs[b], non_blocking=True)
+                out_host[i % out_host.shape[0]].copy_(obufs[b], non_blocking=True)
                 drained[b].record(d2h)
             state["i"] = i + 1
 

@@ -25,13 +25,6 @@ namespace {
 
 std::string g_create_error;
 
-// The bits of an int as a float (a table column that holds indices).
-float __int_as_float_host(int x) {
-  float f;
-  std::memcpy(&f, &x, sizeof f);
-  return f;
-}
-
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // FP64 storage (plain FP64, and FP64 with double-float products) or FP32
 bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
@@ -49,7 +42,7 @@ constexpr int kMaxPairGroups = 384;
 struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site;
-  size_t tc_base, tc_units, row_src, tc_cptr, tc_terms, tables_end;
+  size_t tc_base, tc_units, row_map, tc_cptr, tc_terms, tc_coefs, dtuples, dchunk, dell, tables_end;
   size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, G, ct, scale, flag, total;
 };
 
@@ -76,9 +69,13 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.orb_site = o; o = align256(o + sizeof(int) * c->orb_site.size());
   L.tc_base = o; o = align256(o + sizeof(int) * c->tcs.base.size());
   L.tc_units = o; o = align256(o + sizeof(int) * c->tcs.units.size());
-  L.row_src = o; o = align256(o + sizeof(int) * c->tcs.row_src.size());
+  L.row_map = o; o = align256(o + sizeof(uint32_t) * c->tcs.row_src.size());
   L.tc_cptr = o; o = align256(o + sizeof(int) * c->tcs.out_ptr.size());
-  L.tc_terms = o; o = align256(o + sizeof(float4) * c->tcs.coef.size());
+  L.tc_terms = o; o = align256(o + sizeof(uint2) * c->tcs.coef.size());
+  L.tc_coefs = o; o = align256(o + sizeof(float2) * c->tcs.coef_values.size());
+  L.dtuples = o; o = align256(o + sizeof(uint32_t) * c->db.tuples.size());
+  L.dchunk = o; o = align256(o + sizeof(int2) * c->db.ell_chunk.size());
+  L.dell = o; o = align256(o + sizeof(uint32_t) * c->db.ell.size());
   L.tables_end = o;
   const size_t V = c->V;
   L.stage = o; o = align256(o + (size_t)slots * 2 * V * 144 * 16);
@@ -207,8 +204,14 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   bool groups_ok = false;
   for (int g : kPairGroupsCand) groups_ok |= g == t.pair_groups;
   if (!groups_ok) return false;
-  if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec), (int)c->plan.diquarks.size()) > bbc::kMaxSmemPerBlock)
+  if (c->dense) {
+    if (!bbc::dense_build_supported(t.build_sites, t.build_threads) ||
+        bbc::dense_build_smem(bbc::dev_groups(c->plan, &c->db), t.build_sites) > bbc::kMaxSmemPerBlock)
+      return false;
+  } else if (bbc::block_build_smem(c->plan.z_slots, t.build_sites, fp64_storage(c->prec),
+                                   (int)c->plan.diquarks.size()) > bbc::kMaxSmemPerBlock) {
     return false;
+  }
   if (c->fused) {
     if (c->tc ? !bbc::rest_variant_supported(t.fused_warps, t.fused_steps)
               : !bbc::fused_variant_supported(t.fused_warps, t.fused_steps))
@@ -281,6 +284,17 @@ double time_launches(bbc_ctx* c, int reps, F launch) {
   return ok && ms >= 0.f ? ms / reps : -1.0;
 }
 
+// The block build of slots [0, n_slots): the dense-tuple FP32 kernel, or the
+// entry-per-thread kernel (FP64, double-float, and FP32 without dense tables).
+cudaError_t launch_build(bbc_ctx* c, int n_slots, int sites, int threads) {
+  const bbc::Plan& p = c->plan;
+  if (c->dense)
+    return bbc::launch_block_build_dense(c->d_prop, c->V, n_slots, c->d_dchunk, c->d_dell, c->d_dtuples,
+                                         bbc::dev_groups(p, &c->db), c->d_blk, p.n_out, c->stream, sites);
+  return bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, bbc::dev_groups(p),
+                                 c->d_blk, p.n_out, real_kind(c->prec), c->stream, sites, threads);
+}
+
 // The tensor-core contraction of one slot: G(q) of every pair {q, -q} on
 // the tensor cores, then the CUDA-core products and the Wick sums.
 cudaError_t launch_tc(bbc_ctx* c, int slot) {
@@ -291,11 +305,11 @@ cudaError_t launch_tc(bbc_ctx* c, int slot) {
                                           c->d_tc_units, (int)c->tcs.units.size(), c->d_G,
                                           c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x, c->stream);
   if (e != cudaSuccess) return e;
-  return bbc::launch_contract_rest(blk, c->lat.L, p.n_out, c->d_row_src, c->d_row_slot, c->tcs.rest.n_out, c->n_slots,
-                                   c->d_qlist, n_q, c->d_tasks, (int)c->tcs.rest.tasks.size(), c->d_batches,
-                                   c->d_wptr, c->d_wunits, c->d_G, c->tcs.nbp * c->tcs.nbp, c->d_tc_cptr,
-                                   c->d_tc_terms, (int)p.channels.size(), c->d_ct, c->tune.fused_warps,
-                                   c->tune.fused_steps, c->stream);
+  return bbc::launch_contract_rest(blk, c->lat.L, p.n_out, c->d_row_map, c->tcs.rest.n_out, c->n_slots, c->d_qlist,
+                                   n_q, c->d_tasks, (int)c->tcs.rest.tasks.size(), c->d_batches, c->d_wptr,
+                                   c->d_wunits, c->d_G, c->tcs.nbp * c->tcs.nbp, c->d_tc_cptr, c->d_tc_terms,
+                                   c->d_tc_coefs, (int)c->tcs.coef_values.size(), (int)p.channels.size(), c->d_ct,
+                                   c->tune.fused_warps, c->tune.fused_steps, c->stream);
 }
 
 }  // namespace
@@ -337,6 +351,17 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
     delete c;
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
+  // FP32 blocks from dense entry tuples when the tables and shared memory allow
+  if (real_kind(prec) == bbc::RK_F32 && c->plan.groups.size() <= 8) {
+    std::string derr;
+    try {
+      c->dense = bbc::make_dense_build(c->plan, &c->db, &derr) &&
+                 bbc::dense_build_smem(bbc::dev_groups(c->plan, &c->db), 1) <= bbc::kMaxSmemPerBlock;
+    } catch (const std::bad_alloc&) {
+      c->dense = false;
+    }
+    if (!c->dense) c->db = bbc::DenseBuild();
+  }
   // warp task groups of the pair products: enough warps per 32 q to fill the
   // GPU several times over at L = 16 (V/32 q tiles x groups warps); the
   // double-float products start with more, shorter groups (fewer q tiles in
@@ -362,7 +387,10 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
         const FusedSchedule& f = fused_schedule(c->plan, c->tcs.rest, true);
         const int n_slots = f.layout.n_slots;
         const int g_elems = c->tcs.nbp * c->tcs.nbp;
-        if (bbc::contract_rest_smem(n_slots, (int)c->tcs.rest.tasks.size(), g_elems) > bbc::kMaxSmemPerBlock ||
+        if (bbc::contract_rest_smem(n_slots, (int)c->tcs.rest.tasks.size(), g_elems,
+                                    (int)c->tcs.coef_values.size()) > bbc::kMaxSmemPerBlock ||
+            c->tcs.rest.n_out > 65536 || n_slots > 65536 || c->plan.n_out > 65536 ||
+            2 * 16 * (int)c->tcs.rest.tasks.size() + g_elems > 65536 ||
             bbc::contract_tc_smem(c->tcs.nbp) > bbc::kMaxSmemPerBlock || c->tcs.rest.tasks.empty()) {
           c->tc = false;
           c->tcs = bbc::TcSplit();
@@ -518,9 +546,13 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_orb_site = (int*)(w + L.orb_site);
   c->d_tc_base = (int*)(w + L.tc_base);
   c->d_tc_units = (int*)(w + L.tc_units);
-  c->d_row_src = (int*)(w + L.row_src);
+  c->d_row_map = (uint32_t*)(w + L.row_map);
   c->d_tc_cptr = (int*)(w + L.tc_cptr);
-  c->d_tc_terms = (float4*)(w + L.tc_terms);
+  c->d_tc_terms = (uint2*)(w + L.tc_terms);
+  c->d_tc_coefs = (float2*)(w + L.tc_coefs);
+  c->d_dtuples = (uint32_t*)(w + L.dtuples);
+  c->d_dchunk = (int2*)(w + L.dchunk);
+  c->d_dell = (uint32_t*)(w + L.dell);
   c->d_G = c->tc ? w + L.G : nullptr;
   c->d_stage = w + L.stage;
   c->d_prop = w + L.prop;
@@ -539,12 +571,17 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   const std::vector<bbc::PairTask>& run_tasks = fused_plan(c).tasks;
   std::vector<bbc::DevTask> tasks(run_tasks.size());
   bbc::to_dev_tasks(run_tasks.data(), run_tasks.size(), c->fused ? &c->row_slot : nullptr, tasks.data());
-  std::vector<float4> tc_terms(c->tcs.coef.size());  // Wick terms of the tensor-core path
-  for (size_t i = 0; i < tc_terms.size(); i++) {
-    const double x = c->tcs.coef[i];
+  // tensor-core path: compact rows (block row | slot << 16), Wick terms and
+  // their distinct coefficients split into two FP32 words
+  std::vector<uint32_t> row_map(c->tcs.row_src.size());
+  for (size_t i = 0; i < row_map.size(); i++) row_map[i] = (uint32_t)c->tcs.row_src[i] | ((uint32_t)c->row_slot[i] << 16);
+  std::vector<uint2> tc_terms(c->tcs.coef.size());
+  for (size_t i = 0; i < tc_terms.size(); i++)
+    tc_terms[i] = make_uint2((uint32_t)c->tcs.src_q[i] | ((uint32_t)c->tcs.src_mq[i] << 16), (uint32_t)c->tcs.coef_index[i]);
+  std::vector<float2> tc_coefs;
+  for (double x : c->tcs.coef_values) {
     const float h = (float)x;
-    tc_terms[i] = make_float4(h, (float)(x - (double)h), __int_as_float_host(c->tcs.src_q[i]),
-                              __int_as_float_host(c->tcs.src_mq[i]));
+    tc_coefs.push_back(make_float2(h, (float)(x - (double)h)));
   }
   std::vector<float2> coef_df;  // double-float split of the Wick coefficients
   if (c->prec == BBC_DF64)
@@ -576,9 +613,13 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_orb_site, c->orb_site.data(), sizeof(int) * c->orb_site.size()},
       {c->d_tc_base, c->tcs.base.data(), sizeof(int) * c->tcs.base.size()},
       {c->d_tc_units, c->tcs.units.data(), sizeof(int) * c->tcs.units.size()},
-      {c->d_row_src, c->tcs.row_src.data(), sizeof(int) * c->tcs.row_src.size()},
+      {c->d_row_map, row_map.data(), sizeof(uint32_t) * row_map.size()},
       {c->d_tc_cptr, c->tcs.out_ptr.data(), sizeof(int) * c->tcs.out_ptr.size()},
-      {c->d_tc_terms, tc_terms.data(), sizeof(float4) * tc_terms.size()},
+      {c->d_tc_terms, tc_terms.data(), sizeof(uint2) * tc_terms.size()},
+      {c->d_tc_coefs, tc_coefs.data(), sizeof(float2) * tc_coefs.size()},
+      {c->d_dtuples, c->db.tuples.data(), sizeof(uint32_t) * c->db.tuples.size()},
+      {c->d_dchunk, c->db.ell_chunk.data(), sizeof(int2) * c->db.ell_chunk.size()},
+      {c->d_dell, c->db.ell.data(), sizeof(uint32_t) * c->db.ell.size()},
   };
   for (auto& u : ups) {
     if (u.n == 0) continue;
@@ -654,9 +695,7 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
   cudaError_t e;
   {
     StageScope scope(c, BBC_STAGE_BUILD);
-    e = bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, bbc::dev_groups(p),
-                                c->d_blk, p.n_out, real_kind(c->prec), c->stream, c->tune.build_sites,
-                                c->tune.build_threads);
+    e = launch_build(c, n_slots, c->tune.build_sites, c->tune.build_threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "block build");
   }
   {
@@ -744,7 +783,7 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     StageScope scope(c, BBC_STAGE_FFT_INV);
     e = c->prec == BBC_DF64 ? bbc::launch_fft_inverse_df(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, c->stream)
         : !c->fused ? bbc::launch_fft_inverse(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream)
-               : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream);
+               : bbc::launch_fft_inverse_site(c->d_ct, out_dev, c->lat.L, n_ch, c->d_scale, fp64, c->stream, c->tc);
     if (e != cudaSuccess) return cuda_fail(c, e, "inverse FFT");
   }
   if (c->checks & BBC_CHECK_OUTPUT) {
@@ -828,7 +867,6 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
   if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
   if (c->slot_loaded[0] != 3) return fail(c, BBC_ESTATE, "slot 0 needs both propagators loaded");
   const bbc::Plan& p = c->plan;
-  const bbc::DevGroups g = bbc::dev_groups(p);
   int n = 0;
   auto record = [&](double v) {
     if (ms && n < cap) ms[n] = v;
@@ -842,10 +880,7 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     cand.build_sites = bc[0];
     cand.build_threads = bc[1];
     if (!tuning_valid(c, cand)) { record(-1.0); continue; }
-    const double v = time_launches(c, reps, [&] {
-      return bbc::launch_block_build(c->d_prop, c->V, 1, c->d_ell_chunk, c->d_ell, c->d_zneed, g, c->d_blk,
-                                     p.n_out, real_kind(c->prec), c->stream, bc[0], bc[1]);
-    });
+    const double v = time_launches(c, reps, [&] { return launch_build(c, 1, bc[0], bc[1]); });
     record(v);
     if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: block build");
     if (best_ms < 0 || v < best_ms) { best_ms = v; t.build_sites = bc[0]; t.build_threads = bc[1]; }

@@ -54,11 +54,18 @@ struct bbc_ctx {
   // describe the rest kernel (its tasks, rows and warp units)
   bool tc = false;
   bbc::TcSplit tcs;
+  // FP32 block build from dense entry tuples (k_block_build_dense)
+  bool dense = false;
+  bbc::DenseBuild db;
+  uint32_t* d_dtuples = nullptr;
+  int2* d_dchunk = nullptr;
+  uint32_t* d_dell = nullptr;
   int* d_tc_base = nullptr;              // [nb] first block row of each block of G
   int* d_tc_units = nullptr;             // [warps] tiles of G per warp
-  int* d_row_src = nullptr;              // [rest rows] block row of each compact row
+  uint32_t* d_row_map = nullptr;         // [rest rows] block row | shared-memory slot << 16
   int* d_tc_cptr = nullptr;              // [n_ch*16 + 1] Wick-term ranges per output
-  float4* d_tc_terms = nullptr;          // [terms] (coef hi, coef lo, source q, source -q)
+  uint2* d_tc_terms = nullptr;           // [terms] (source q | source -q << 16, coefficient index)
+  float2* d_tc_coefs = nullptr;          // [distinct coefficients] (hi, lo)
   char* d_G = nullptr;                   // [pairs][nbp][nbp] complex64
   bbc_tuning tune{1, 256, 16, 18, 1, 48};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
@@ -124,8 +131,14 @@ static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies, "diquark an
 // The block-build groups of a plan as the kernel reads them: row ranges,
 // families per tensor slot, and the diquarks (flavours, Gamma1) those
 // families are made of, in the plan's shared-memory order.
-inline DevGroups dev_groups(const Plan& p) {
+inline DevGroups dev_groups(const Plan& p, const DenseBuild* db = nullptr) {
   DevGroups g{};
+  if (db) {  // the dense-tuple FP32 build's tables
+    for (size_t i = 0; i < db->tuple_first.size() && i < 9; i++) g.tuple_first[i] = db->tuple_first[i];
+    for (size_t i = 0; i < db->stride.size() && i < 8; i++) g.stride[i] = db->stride[i];
+    for (size_t i = 0; i < db->chunk_first.size() && i < 9; i++) g.dchunk_first[i] = db->chunk_first[i];
+    g.dense_z_slots = db->z_slots;
+  }
   g.n = (int)p.groups.size();
   for (int i = 0; i < g.n; i++) {
     g.first[i] = p.groups[i].first_row;

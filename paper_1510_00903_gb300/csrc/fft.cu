@@ -263,6 +263,95 @@ k_fft(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer
   }
 }
 
+// Lines of N = 3 M points in FP64 or double-float (N = 48: a whole line in
+// one thread's registers would spill) split over three threads: thread j of a
+// line transforms the decimated sequence x[3 n2 + j] (M points, in registers),
+// applies the twiddles exp(-+2 pi i j k2 / N) and leaves the result in shared
+// memory; after a barrier, thread j combines k2 = j, j + 3, ... with the
+// radix-3 butterfly into X[k2], X[k2 + M], X[k2 + 2M] and stores them.  The
+// modes, index decomposition and output forms are those of k_fft
+// (FIELD-type passes and the site-major first pass).
+constexpr int kSplitLines = 64;  // lines per CTA of 3 x 64 threads
+template <typename S, typename R, int M, bool INV, int MODE, typename O = S>
+__global__ void __launch_bounds__(3 * kSplitLines)
+k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer, int n_inner, int axis,
+            const double* __restrict__ scale, O* __restrict__ sum) {
+  constexpr int N = 3 * M;
+  __shared__ cpx<R> sh[kSplitLines][3][M];
+  const int ls = threadIdx.x % kSplitLines, j = threadIdx.x / kSplitLines;
+  const long long gid = blockIdx.x * (long long)kSplitLines + ls;
+  const int lines = N * N;
+  const long long V = (long long)N * N * N;
+  int line = 0, inner = 0;
+  long long o = 0;
+  bool live;
+  if (MODE == FFT_SITE2FIELD) {
+    live = gid < n_outer * lines * n_inner;
+    inner = (int)(gid % n_inner);
+    const long long rest = gid / n_inner;
+    line = (int)(rest % lines);
+    o = rest / lines;
+  } else if (MODE == FFT_FIELD || MODE == FFT_FIELD_SUM) {
+    live = gid < n_outer * lines;
+    line = (int)(gid % lines);
+    o = gid / lines;
+  } else {  // FIELD2OUT
+    live = gid < n_outer * lines * 16;
+    inner = (int)(gid % 16);
+    const long long rest = gid / 16;
+    line = (int)(rest % lines);
+    o = rest / lines;
+  }
+  int base = 0, stride = 0;
+  line_base(N, axis, line, base, stride);
+  if (live) {
+    const cpx<S>* p;
+    long long step;
+    if (MODE == FFT_SITE2FIELD) { p = in + (o * V + base) * n_inner + inner; step = (long long)stride * n_inner; }
+    else if (MODE == FFT_FIELD || MODE == FFT_FIELD_SUM) { p = in + o * V + base; step = stride; }
+    else { p = in + (o * 16 + inner) * V + base; step = stride; }
+    cpx<R> u[M];
+    load_bitrev<S, R, M>(u, p + j * step, 3 * step, std::make_integer_sequence<int, M>{});
+    fft_pow2<R, M, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < M; k2++) {
+      const int ti = (j * k2 * (kTw / N)) % kTw;
+      if (ti != 0) {
+        cpx<R> w = twiddle<R>(ti);
+        if (INV) w.im = -w.im;
+        u[k2] = w * u[k2];
+      }
+      sh[ls][j][k2] = u[k2];
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  const R hs = (R)0.86602540378443864676;  // sqrt(3)/2
+  for (int k2 = j; k2 < M; k2 += 3) {
+    const cpx<R> t0 = sh[ls][0][k2], t1 = sh[ls][1][k2], t2 = sh[ls][2][k2];
+    const cpx<R> sm = t1 + t2, d = t1 - t2;
+    const cpx<R> m(t0.re - (R)0.5 * sm.re, t0.im - (R)0.5 * sm.im);
+    const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);
+    const cpx<R> x[3] = {t0 + sm, m + r, m - r};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const int k = k2 + c * M;
+      if (MODE == FFT_SITE2FIELD) {
+        out[(o * n_inner + inner) * V + base + (long long)k * stride] = cpx<O>(x[c]);
+      } else if (MODE == FFT_FIELD) {
+        out[o * V + base + (long long)k * stride] = cpx<O>(x[c]);
+      } else if (MODE == FFT_FIELD_SUM) {
+        const cpx<O> w(x[c]);
+        out[o * V + base + (long long)k * stride] = w;
+        sum[o * V + base + (long long)k * stride] = w.re + w.im;
+      } else {  // FIELD2OUT, the scale in the output precision
+        const O f = (O)scale[o];
+        out[(o * V + base + (long long)k * stride) * 16 + inner] = cpx<O>((O)x[c].re * f, (O)x[c].im * f);
+      }
+    }
+  }
+}
+
 // x and y passes of the site-major layout data[o][site][n_inner] fused in one
 // kernel: a CTA takes one z plane of one outer index and TI consecutive inner
 // columns, stages the N x N x TI plane in shared memory (compute precision),
@@ -345,6 +434,15 @@ static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_ou
   unsigned blocks = (unsigned)((total + 255) / 256);
   const cpx<S>* i = (const cpx<S>*)in;
   cpx<O>* o = (cpx<O>*)out;
+  if constexpr (sizeof(R) == 8 && MODE != FFT_SITE && MODE != FFT_SITE2OUT) {
+    // FP64 and double-float 48-point lines: three threads per line
+    if (L == 48) {
+      const unsigned b3 = (unsigned)((total + kSplitLines - 1) / kSplitLines);
+      if (inv) k_fft3split<S, R, 16, true, MODE, O><<<b3, 3 * kSplitLines, 0, st>>>(i, o, n_outer, n_inner, axis, scale, sum);
+      else k_fft3split<S, R, 16, false, MODE, O><<<b3, 3 * kSplitLines, 0, st>>>(i, o, n_outer, n_inner, axis, scale, sum);
+      return cudaGetLastError();
+    }
+  }
 #define BBC_FFT_CASE(NN)                                                                                      \
   case NN:                                                                                                    \
     if (inv) k_fft<S, R, NN, true, MODE, O><<<blocks, 256, 0, st>>>(i, o, n_outer, n_inner, axis, scale, sum); \
@@ -422,8 +520,19 @@ cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, b
 }
 
 cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, bool ct_f32) {
   cudaError_t e;
+  if (ct_f32) {  // complex64 q-space correlators, FP32 transform, complex128 output
+    if (L <= 32) {
+      e = fft_xy_site<float, float>(ct, L, 1, n_ch * 16, true, st);
+    } else {
+      e = cudaSuccess;
+      for (int axis = 0; axis < 2 && e == cudaSuccess; axis++)
+        e = fft_dispatch<float, float, FFT_SITE>(ct, ct, L, 1, n_ch * 16, axis, true, nullptr, st);
+    }
+    if (e != cudaSuccess) return e;
+    return fft_dispatch<float, float, FFT_SITE2OUT, double>(ct, out, L, 1, n_ch * 16, 2, true, scale, st);
+  }
   if (L <= 32) {
     e = fp64_compute ? fft_xy_site<double, double>(ct, L, 1, n_ch * 16, true, st)
                      : fft_xy_site<double, float>(ct, L, 1, n_ch * 16, true, st);

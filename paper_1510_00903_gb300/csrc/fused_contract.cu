@@ -203,26 +203,30 @@ __device__ __forceinline__ void df_axpy(float& s, float& e, float ch, float cl, 
 
 // The CUDA-core half of the mixed contraction beside k_contract_tc.  One CTA
 // per pair {q, -q}: the rows the remaining tasks read are staged from the
-// q-major blocks through the compact row map (row i is block row row_src[i],
-// stored interleaved (F_q, F_-q) at slot row_slot[i]); their products run as
-// in k_contract_fused; G(q) of the pair is staged beside them; the signed
-// sums over Wick diagrams add coef x V, V = [P_q | P_-q | G], in double-float
-// arithmetic on the FP32 pipes (the products are FP32; the sums keep their
-// cancellations exact to 2^-48 of the terms).
+// q-major blocks through the compact row map (row_map[i] = block row |
+// shared-memory slot << 16; stored interleaved (F_q, F_-q)) with asynchronous
+// copies; their products run as in k_contract_fused; G(q) of the pair is
+// staged beside them; the signed sums over Wick diagrams add coef x V, V =
+// [P_q | P_-q | G], in double-float arithmetic on the FP32 pipes (the
+// products are FP32; the sums keep their cancellations exact to 2^-48 of the
+// terms), one thread per output for both q and -q.  A term is (source q |
+// source -q << 16, coefficient index) into the pair's coefficient table
+// (hi, lo).  The sums are rounded to FP32 and stored as complex64 (the inverse
+// transform computes in FP32).
 template <int WARPS, int STEPS>
 __global__ void __launch_bounds__(WARPS * 32, 2)
-k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const int* __restrict__ row_src,
-                const int* __restrict__ row_slot, int n_rows, int n_slots, const int* __restrict__ qlist,
-                const DevTask* __restrict__ tasks, int n_tasks, const WarpBatch* __restrict__ batches,
-                const int* __restrict__ wptr, const int4* __restrict__ wunits, const float4* __restrict__ G,
-                int g_elems, const int* __restrict__ cptr, const float4* __restrict__ terms, int n_outputs,
-                cpx<double>* __restrict__ ct) {
+k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const uint32_t* __restrict__ row_map, int n_rows,
+                int n_slots, const int* __restrict__ qlist, const DevTask* __restrict__ tasks, int n_tasks,
+                const WarpBatch* __restrict__ batches, const int* __restrict__ wptr, const int4* __restrict__ wunits,
+                const float4* __restrict__ G, int g_elems, const int* __restrict__ cptr, const uint2* __restrict__ terms,
+                const float2* __restrict__ coefs, int n_coefs, int n_outputs, float2* __restrict__ ct) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kThreads = WARPS * 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = n_tasks * 16;                                      // products per side
   float4* R = reinterpret_cast<float4*>(smem_raw);                  // [n_slots] (F_q, F_-q)
   cpx<float>* V = reinterpret_cast<cpx<float>*>(smem_raw + (size_t)n_slots * sizeof(float4));  // [2 np | g_elems]
+  float2* C = reinterpret_cast<float2*>(V + 2 * np + g_elems);      // [n_coefs] (hi, lo)
   const int p = blockIdx.x, q = qlist[p];
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
@@ -230,16 +234,21 @@ k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const int* __r
   {
     const float2* s0 = blk + (size_t)q * n_out;
     const float2* s1 = blk + (size_t)nq * n_out;
+#pragma unroll 4
     for (int i = tid; i < n_rows; i += kThreads) {
-      const int src = __ldg(row_src + i);
-      const float2 x = __ldg(s0 + src), y = self ? x : __ldg(s1 + src);
-      R[__ldg(row_slot + i)] = make_float4(x.x, x.y, y.x, y.y);
+      const uint32_t m = __ldg(row_map + i);
+      const int src = (int)(m & 0xffffu), slot = (int)(m >> 16);
+      cp_async8(R + slot, s0 + src);
+      cp_async8(reinterpret_cast<float2*>(R + slot) + 1, s1 + src);
     }
-    float4* pz = reinterpret_cast<float4*>(V);
-    for (int i = tid; i < np; i += kThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const float4* gp = G + (size_t)p * (g_elems >> 1);
     float4* gs = reinterpret_cast<float4*>(V + 2 * np);
-    for (int i = tid; i < (g_elems >> 1); i += kThreads) gs[i] = __ldg(gp + i);
+#pragma unroll 4
+    for (int i = tid; i < (g_elems >> 1); i += kThreads) cp_async16(gs + i, gp + i);
+    float4* pz = reinterpret_cast<float4*>(V);
+    for (int i = tid; i < np; i += kThreads) pz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < n_coefs; i += kThreads) C[i] = __ldg(coefs + i);
+    cp_async_wait_all();
   }
   __syncthreads();
   const int u1 = wptr[warp + 1];
@@ -256,24 +265,29 @@ k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const int* __r
     else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
   }
   __syncthreads();
-  const int sides = self ? 1 : 2;
-  for (int j = tid; j < sides * n_outputs; j += kThreads) {
-    const int side = j >= n_outputs, o = side ? j - n_outputs : j;
-    float rs = 0.f, re = 0.f, is = 0.f, ie = 0.f;
+  for (int o = tid; o < n_outputs; o += kThreads) {
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // (re s, re e, im s, im e) for q, then -q
     const int c1 = __ldg(cptr + o + 1);
     for (int c = __ldg(cptr + o); c < c1; c++) {
-      const float4 tm = __ldg(terms + c);  // coef hi, coef lo, source for q, source for -q
-      const cpx<float> v = V[__float_as_int(side ? tm.w : tm.z)];
-      df_axpy(rs, re, tm.x, tm.y, v.re);
-      df_axpy(is, ie, tm.x, tm.y, v.im);
+      const uint2 tm = __ldg(terms + c);
+      const float2 cf = C[tm.y];
+      const cpx<float> vq = V[tm.x & 0xffffu];
+      df_axpy(a[0], a[1], cf.x, cf.y, vq.re);
+      df_axpy(a[2], a[3], cf.x, cf.y, vq.im);
+      if (!self) {
+        const cpx<float> vm = V[tm.x >> 16];
+        df_axpy(a[4], a[5], cf.x, cf.y, vm.re);
+        df_axpy(a[6], a[7], cf.x, cf.y, vm.im);
+      }
     }
-    ct[(size_t)(side ? nq : q) * n_outputs + o] = cpx<double>((double)rs + (double)re, (double)is + (double)ie);
+    ct[(size_t)q * n_outputs + o] = make_float2(__fadd_rn(a[0], a[1]), __fadd_rn(a[2], a[3]));
+    if (!self) ct[(size_t)nq * n_outputs + o] = make_float2(__fadd_rn(a[4], a[5]), __fadd_rn(a[6], a[7]));
   }
 }
 
-size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems) {
+size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems, int n_coefs) {
   return (size_t)n_slots * sizeof(float4) + (size_t)2 * n_tasks * 16 * sizeof(cpx<float>) +
-         (size_t)g_elems * sizeof(cpx<float>);
+         (size_t)g_elems * sizeof(cpx<float>) + (size_t)n_coefs * sizeof(float2);
 }
 
 bool rest_variant_supported(int warps, int steps) {
@@ -282,34 +296,36 @@ bool rest_variant_supported(int warps, int steps) {
 
 template <int WARPS, int STEPS>
 cudaError_t launch_rest_variant(size_t sm, int n_q, cudaStream_t st, const void* blk, int L, int n_out,
-                                const int* row_src, const int* row_slot, int n_rows, int n_slots, const int* qlist,
+                                const uint32_t* row_map, int n_rows, int n_slots, const int* qlist,
                                 const DevTask* tasks, int n_tasks, const WarpBatch* batches, const int* wptr,
-                                const int4* wunits, const void* G, int g_elems, const int* cptr, const float4* terms,
-                                int n_outputs, cpx<double>* ct) {
+                                const int4* wunits, const void* G, int g_elems, const int* cptr, const uint2* terms,
+                                const float2* coefs, int n_coefs, int n_outputs, float2* ct) {
   static int granted[64] = {0};
   cudaError_t e = ensure_smem(k_contract_rest<WARPS, STEPS>, sm, granted);
   if (e != cudaSuccess) return e;
-  k_contract_rest<WARPS, STEPS><<<n_q, WARPS * 32, sm, st>>>((const float2*)blk, L, n_out, row_src, row_slot, n_rows,
-                                                             n_slots, qlist, tasks, n_tasks, batches, wptr, wunits,
-                                                             (const float4*)G, g_elems, cptr, terms, n_outputs, ct);
+  k_contract_rest<WARPS, STEPS><<<n_q, WARPS * 32, sm, st>>>((const float2*)blk, L, n_out, row_map, n_rows, n_slots,
+                                                             qlist, tasks, n_tasks, batches, wptr, wunits,
+                                                             (const float4*)G, g_elems, cptr, terms, coefs, n_coefs,
+                                                             n_outputs, ct);
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const int* row_src, const int* row_slot, int n_rows,
-                                 int n_slots, const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
+cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const uint32_t* row_map, int n_rows, int n_slots,
+                                 const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
                                  const WarpBatch* batches, const int* wptr, const int4* wunits, const void* G,
-                                 int g_elems, const int* cptr, const float4* terms, int n_ch, void* ct, int warps,
-                                 int steps, cudaStream_t st) {
+                                 int g_elems, const int* cptr, const uint2* terms, const float2* coefs, int n_coefs,
+                                 int n_ch, void* ct, int warps, int steps, cudaStream_t st) {
   if (n_q == 0) return cudaSuccess;
-  if ((g_elems & 1) || (g_elems && !G)) return cudaErrorInvalidValue;
-  const size_t sm = contract_rest_smem(n_slots, n_tasks, g_elems);
+  if ((g_elems & 1) || (g_elems && !G) || n_out > 65536 || n_slots > 65536 || 2 * n_tasks * 16 + g_elems > 65536)
+    return cudaErrorInvalidValue;
+  const size_t sm = contract_rest_smem(n_slots, n_tasks, g_elems, n_coefs);
   if (sm > kMaxSmemPerBlock) return cudaErrorInvalidValue;
-  cpx<double>* o = (cpx<double>*)ct;
+  float2* o = (float2*)ct;
   const int n_outputs = n_ch * 16;
-#define BBC_REST(W, S)                                                                                            \
-  if (warps == W && steps == S)                                                                                   \
-    return launch_rest_variant<W, S>(sm, n_q, st, blk, L, n_out, row_src, row_slot, n_rows, n_slots, qlist, tasks, \
-                                     n_tasks, batches, wptr, wunits, G, g_elems, cptr, terms, n_outputs, o);
+#define BBC_REST(W, S)                                                                                             \
+  if (warps == W && steps == S)                                                                                    \
+    return launch_rest_variant<W, S>(sm, n_q, st, blk, L, n_out, row_map, n_rows, n_slots, qlist, tasks, n_tasks,   \
+                                     batches, wptr, wunits, G, g_elems, cptr, terms, coefs, n_coefs, n_outputs, o);
   BBC_REST(4, 1) BBC_REST(4, 2) BBC_REST(8, 1)
 #undef BBC_REST
   return cudaErrorInvalidValue;

@@ -160,6 +160,132 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
   }
 }
 
+// FP32 blocks from dense entry tuples (host tables: dense_build.cpp).  Per
+// site: the propagators (16-byte loads) and the diquarks as above; then per
+// group one thread forms the twelve e2 entries of a tuple (slot, a, e0 e1),
+// F[e2] = sum_c2 D[e0 e1][c2] S_f2[(a, c2)][e2], with the three diquark values
+// in registers and the propagator row shared by the warp (consecutive tuples
+// mostly share (slot, a): broadcast loads), writing entry (j, e2) to position
+// e2 * stride + j (contiguous stores); the rows then sum their terms, weight
+// = the top 16 bits of the table entry read as an FP32 value.
+template <int SITES>
+__global__ void __launch_bounds__(256)
+k_block_build_dense(const cpx<float>* __restrict__ prop, int V, const int2* __restrict__ ell_chunk,
+                    const uint32_t* __restrict__ ell, const uint32_t* __restrict__ tuples, DevGroups g,
+                    cpx<float>* __restrict__ blk, int n_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kThreads = 256;
+  const int nd = g.n_dq * 432, zs = g.dense_z_slots;
+  cpx<float>* sS = reinterpret_cast<cpx<float>*>(smem_raw);  // [SITES][2][144]  light, strange
+  cpx<float>* sD = sS + SITES * 288;                          // [SITES][n_dq][432]
+  cpx<float>* sZ = sD + SITES * nd;                           // [SITES][zs]
+  const int site0 = blockIdx.x * SITES, slot = blockIdx.y, tid = threadIdx.x;
+  {
+    const float4* P4 = reinterpret_cast<const float4*>(prop + (size_t)slot * 2 * V * 144);
+    for (int i = tid; i < SITES * 144; i += kThreads) {  // 72 16-byte loads per site and flavour
+      const int s = i / 144, j = i - 144 * s, f = j / 72, w = j - 72 * f;
+      reinterpret_cast<float4*>(sS + s * 288 + f * 144)[w] = __ldg(P4 + ((size_t)f * V + site0 + s) * 72 + w);
+    }
+  }
+  __syncthreads();
+  for (int ii = tid; ii < SITES * nd; ii += kThreads) {
+    const int s = ii / nd, i = ii - s * nd;
+    const int dq = i / 432, r = i % 432, e0 = r / 36, e1 = (r / 3) % 12, c2 = r % 3;
+    const int ca = (c2 + 1) % 3, cb = (c2 + 2) % 3;  // eps(ca,cb,c2) = +1, eps(cb,ca,c2) = -1
+    const cpx<float>* S0 = sS + s * 288 + 144 * g.dq_f0[dq];
+    const cpx<float>* S1 = sS + s * 288 + 144 * g.dq_f1[dq];
+    const int gam = g.dq_gam[dq];
+    cpx<float> acc(0.f, 0.f);
+#pragma unroll
+    for (int gi = 0; gi < 4; gi++) {
+      const int a0 = c_gam[gam][gi][0], a1 = c_gam[gam][gi][1];
+      const float sg = (float)c_gam[gam][gi][2];
+      cpx<float> t(0.f, 0.f);
+      cmac(t, S0[(3 * a0 + ca) * 12 + e0], S1[(3 * a1 + cb) * 12 + e1]);
+      cpx<float> u(0.f, 0.f);
+      cmac(u, S0[(3 * a0 + cb) * 12 + e0], S1[(3 * a1 + ca) * 12 + e1]);
+      acc.re += sg * (t.re - u.re);
+      acc.im += sg * (t.im - u.im);
+    }
+    sD[ii] = acc;
+  }
+  __syncthreads();
+  for (int gi = 0; gi < g.n; gi++) {
+    const int t0 = g.tuple_first[gi], nt = g.tuple_first[gi + 1] - t0, str = g.stride[gi];
+    for (int jj = tid; jj < nt * SITES; jj += kThreads) {
+      const int s = jj / nt, j = jj - s * nt;
+      const uint32_t tu = __ldg(tuples + t0 + j);
+      const int sl = tu / 288, a = (tu % 288) / 144, e01 = tu % 144;
+      const int fam = sl == 0 ? g.fam0[gi] : g.fam1[gi];
+      const cpx<float>* D = sD + s * nd + 432 * g.fam_dq[fam] + 3 * e01;
+      const cpx<float>* S2 = sS + s * 288 + 144 * g.fam_f2[fam] + 36 * (a + g.spin0);
+      const cpx<float> d0 = D[0], d1 = D[1], d2 = D[2];
+      cpx<float>* z = sZ + s * zs + j;
+#pragma unroll
+      for (int e2 = 0; e2 < 12; e2++) {
+        cpx<float> acc(0.f, 0.f);
+        cmac(acc, d0, S2[e2]);
+        cmac(acc, d1, S2[12 + e2]);
+        cmac(acc, d2, S2[24 + e2]);
+        z[e2 * str] = acc;
+      }
+    }
+    __syncthreads();
+    const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
+    cpx<float>* out = blk + ((size_t)slot * V + site0) * n_out;
+    for (int r = r0 + tid; r < r1; r += kThreads) {
+      cpx<float> acc[SITES];
+#pragma unroll
+      for (int s = 0; s < SITES; s++) acc[s] = cpx<float>(0.f, 0.f);
+      const int2 ch = __ldg(ell_chunk + g.dchunk_first[gi] + ((r - r0) >> 5));
+      const uint32_t* ep = ell + ch.x + ((r - r0) & 31);
+      for (int k = 0; k < ch.y; k++) {
+        const uint32_t e = __ldg(ep + 32 * k);  // padding: weight 0 at position 0
+        const float w = __uint_as_float(e & 0xffff0000u);
+        const int pos = e & 0xffffu;
+#pragma unroll
+        for (int s = 0; s < SITES; s++) {
+          const cpx<float> zv = sZ[s * zs + pos];
+          acc[s].re = fmaf(w, zv.re, acc[s].re);
+          acc[s].im = fmaf(w, zv.im, acc[s].im);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < SITES; s++) out[(size_t)s * n_out + r] = acc[s];
+    }
+    __syncthreads();
+  }
+}
+
+bool dense_build_supported(int sites, int threads) { return threads == 256 && (sites == 1 || sites == 2); }
+
+size_t dense_build_smem(const DevGroups& g, int sites) {
+  return (size_t)sites * (288 + 432 * (size_t)g.n_dq + g.dense_z_slots) * sizeof(cpx<float>);
+}
+
+template <int SITES>
+cudaError_t launch_dense_variant(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
+                                 const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
+  const size_t sm = dense_build_smem(g, SITES);
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem(k_block_build_dense<SITES>, sm, granted);
+  if (e != cudaSuccess) return e;
+  dim3 grid(V / SITES, n_slots);
+  k_block_build_dense<SITES><<<grid, 256, sm, st>>>((const cpx<float>*)prop, V, ell_chunk, ell, tuples, g,
+                                                     (cpx<float>*)blk, n_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_build_dense(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
+                                     const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st,
+                                     int sites) {
+  if (!dense_build_supported(sites, 256) || V % sites != 0 || g.n_dq < 1 || g.n_dq > kMaxDiquarks ||
+      dense_build_smem(g, sites) > kMaxSmemPerBlock)
+    return cudaErrorInvalidValue;
+  if (sites == 1) return launch_dense_variant<1>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+  return launch_dense_variant<2>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+}
+
 size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq) {  // fp64: 8-byte reals (FP64 or double-float)
   const size_t cb = fp64 ? sizeof(cpx<double>) : sizeof(cpx<float>);
   return (size_t)sites * (288 + 432 * (size_t)n_dq + z_slots) * cb + 32 * (fp64 ? sizeof(double) : sizeof(float));

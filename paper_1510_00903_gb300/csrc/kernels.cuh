@@ -39,6 +39,9 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int dq_gam[kMaxDiquarks];                      // their Gamma1: 0 = C gamma5, l = eta_l C gamma_l
   int fam_dq[kMaxFamilies];                      // per family: index of its diquark in shared memory
   int fam_f2[kMaxFamilies];                      // per family: third quark strange (1) or light (0)
+  // dense-tuple FP32 build (k_block_build_dense): tuples of each group, their
+  // entry stride, entry positions per site, 32-row chunks of each group
+  int tuple_first[9], stride[8], dense_z_slots, dchunk_first[9];
 };
 
 constexpr int kMaxChannels = 160;  // channels of one context (every id fits)
@@ -72,6 +75,14 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
 // `sites` consecutive sites per CTA of `threads` threads: (1, 256), (2, 256),
 // (2, 512) or (4, 512) (V a multiple of sites).
 bool build_variant_supported(int sites, int threads);
+// FP32 blocks from dense entry tuples (dense_build.cpp tables): prop
+// [slots][2][V][144] complex64, blk [slots][V][n_out]; `sites` (1 or 2)
+// consecutive sites per CTA of 256 threads.
+bool dense_build_supported(int sites, int threads);
+size_t dense_build_smem(const DevGroups& g, int sites);
+cudaError_t launch_block_build_dense(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
+                                     const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st,
+                                     int sites);
 size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq);
 // ell_chunk[c] = (offset, length) of 32-row chunk c in ell (lane-interleaved rows).
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,
@@ -93,8 +104,9 @@ cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, 
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st);
 // Inverse 3-D FFT of q-major ct[V][n_ch*16] (complex128, x and y in place),
 // the z pass writing out[n_ch][V][16] multiplied by scale[ch].
+// ct_f32: ct holds complex64 values (then the transform computes in FP32).
 cudaError_t launch_fft_inverse_site(void* ct, void* out, int L, int n_ch, const double* scale, bool fp64_compute,
-                                    cudaStream_t st);
+                                    cudaStream_t st, bool ct_f32 = false);
 // Fused FP32 contraction of one slice from q-major blocks blk[V][n_out]: one
 // CTA per pair {q, -q} (qlist[n_q]), block row i staged at shared-memory slot
 // row_slot[i] < n_slots (task offsets are slots), warp units wunits {batch,
@@ -127,19 +139,19 @@ size_t contract_tc_smem(int nbp);
 cudaError_t launch_contract_tc(const void* blk, int L, int n_out, const int* base, int nb, int nbp, const int* qlist,
                                int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st);
 // The rest of the mixed contraction (fused_contract.cu): per pair {q, -q}
-// the CUDA-core products of the other tasks on compact rows (row i of
-// n_rows is block row row_src[i], staged at row_slot[i]) and the signed
-// double-float sums over Wick diagrams of V = [P_q | P_-q | G(q)]: output o of
-// side q (-q) sums terms[c] = (coef hi, coef lo, src_q, src_mq) over c in
-// [cptr[o], cptr[o+1]), reading V[src_q] (V[src_mq]); g_elems = nbp^2 (0
-// without tensor-core products).  ct[V][n_ch*16] complex128.
-size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems);
+// the CUDA-core products of the other tasks on compact rows (row_map[i] =
+// block row | shared-memory slot << 16, i < n_rows) and the signed
+// double-float sums over Wick diagrams of V = [P_q | P_-q | G(q)]: output o
+// sums, over terms c in [cptr[o], cptr[o+1]), coefs[terms[c].y] (hi, lo) x
+// V[terms[c].x & 0xffff] for q and x V[terms[c].x >> 16] for -q; g_elems =
+// nbp^2 (0 without tensor-core products).  ct[V][n_ch*16] complex64.
+size_t contract_rest_smem(int n_slots, int n_tasks, int g_elems, int n_coefs);
 bool rest_variant_supported(int warps, int steps);
-cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const int* row_src, const int* row_slot, int n_rows,
-                                 int n_slots, const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
+cudaError_t launch_contract_rest(const void* blk, int L, int n_out, const uint32_t* row_map, int n_rows, int n_slots,
+                                 const int* qlist, int n_q, const DevTask* tasks, int n_tasks,
                                  const WarpBatch* batches, const int* wptr, const int4* wunits, const void* G,
-                                 int g_elems, const int* cptr, const float4* terms, int n_ch, void* ct, int warps,
-                                 int steps, cudaStream_t st);
+                                 int g_elems, const int* cptr, const uint2* terms, const float2* coefs, int n_coefs,
+                                 int n_ch, void* ct, int warps, int steps, cudaStream_t st);
 // dst[i] = (bf16(src[i].re), bf16(src[i].im)), round to nearest even, n complex64 values.
 cudaError_t launch_to_bf16(const void* src, void* dst, size_t n, cudaStream_t st);
 // Inverse 3-D FFT of ct[n_ch][16][V] (complex128, x and y in place), the z

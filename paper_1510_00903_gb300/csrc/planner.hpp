@@ -134,6 +134,22 @@ struct FusedLayout {
 };
 void optimise_fused_layout(const Plan& plan, std::vector<Batch>* batches, FusedLayout* out);
 
+// FP32 block build with dense entry tuples (dense_build.cpp): per group, the
+// tuples (family slot, a, e0 e1) its rows read; one thread forms the twelve
+// e2 entries of a tuple at positions e2 * stride + j; the rows re-addressed
+// to them as 32-row lane-interleaved chunks, entry = position | (weight as
+// bfloat16 bits in the top 16 bits).
+struct DenseBuild {
+  std::vector<uint32_t> tuples;      // group by group: slot * 288 + a * 144 + e01
+  std::vector<int> tuple_first;      // groups + 1
+  std::vector<int> stride;           // per group (odd, >= its tuple count)
+  int z_slots = 0;                   // entry positions per site (max over groups)
+  std::vector<int> chunk_first;      // groups + 1
+  std::vector<std::pair<int, int>> ell_chunk;
+  std::vector<uint32_t> ell;
+};
+bool make_dense_build(const Plan& plan, DenseBuild* out, std::string* err);
+
 // Tensor-core split of a plan (tensor_split.cpp).  Tasks whose operands are
 // whole 12 x 12 blocks in the trace form tr(M_A(q) M_B(-q)) become entries
 // of one complex matrix product per pair {q, -q} over the blocks they read,
@@ -154,6 +170,8 @@ struct TcSplit {
   std::vector<int> out_ptr;
   std::vector<double> coef;
   std::vector<int> src_q, src_mq;
+  std::vector<double> coef_values;   // the distinct coefficients (exact copies)
+  std::vector<int> coef_index;       // per term: its coefficient in coef_values
 };
 // nb = 0 when no task has the trace form (or G would exceed kMaxTcBlocks):
 // then every task is in rest.  Returns false only on an internal inconsistency.

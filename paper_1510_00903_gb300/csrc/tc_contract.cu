@@ -11,11 +11,14 @@
 // = M_i(q)[u][v] and the -q row transposed, Y[j][k] = M_j(-q)[v][u] (k =
 // 12 u + v), so that G = X Y^T over k = 0..143.  A warp owns one 16-row
 // m-tile and up to three 8-column n-tiles of G and runs the complex product
-// as four real products (Gr += Xr Yr - Xi Yi, Gi += Xr Yi + Xi Yr) with
-// mma.sync m16n8k8 on TF32 operands and FP32 accumulators.  FP32 accuracy
-// (kTc3x) comes from splitting every operand into two TF32 words, x = hi +
-// lo, and summing hi lo + lo hi + hi hi (the products the TF32 rounding of
-// one word would drop); the TF32 trial (kTc1x) rounds every operand once.
+// as three real products (t1 = Xr Yr, t2 = Xi Yi, t3 = (Xr + Xi)(Yr + Yi);
+// Gr = t1 - t2, Gi = t3 - t1 - t2) with mma.sync m16n8k8 on TF32 operands and
+// FP32 accumulators.  FP32 accuracy (kTc3x) comes from splitting every
+// operand into two TF32 words, x = hi + lo, and summing lo hi + hi lo + hi hi
+// (the products the TF32 rounding of one word would drop); the TF32 trial
+// (kTc1x) rounds every operand once.  The rows are staged with asynchronous
+// copies (cp.async) in two groups by open-index half, so the second half
+// lands while the first is multiplied.
 // Rows are padded to 148 complex (1184 bytes): the fragment loads of a warp
 // (rows g, columns t) then fall in distinct shared-memory banks.
 #include "device_common.cuh"
@@ -48,7 +51,6 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ uint32_t neg(uint32_t x) { return x ^ 0x80000000u; }
 
 }  // namespace
 
@@ -63,93 +65,96 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
   const int p = blockIdx.x, q = qlist[p];
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
-  const float4* rq = reinterpret_cast<const float4*>(blk + (size_t)q * n_out);
-  const float4* rmq = reinterpret_cast<const float4*>(blk + (size_t)nq * n_out);
+  const float2* rq = blk + (size_t)q * n_out;
+  const float2* rmq = blk + (size_t)nq * n_out;
   // rows nb .. nbp-1 are padding: zero (they enter G's unread rows and columns only)
   for (int i = nb * kLd + tid; i < nbp * kLd; i += nthr) {
     X[i] = make_float2(0.f, 0.f);
     Y[i] = make_float2(0.f, 0.f);
   }
-  // staging: six 16-byte loads in flight per thread before their stores
-  constexpr int U = 6;
-  const int n_chunks = nb * kChunks;
-  for (int c0 = tid; c0 < 2 * n_chunks; c0 += U * nthr) {
-    float4 v[U];
+  // staging with asynchronous copies, in two groups: k < 72 (rows u < 6 of
+  // every X block, columns u < 6 of every Y block) first, then k >= 72, so
+  // that the second half lands while the first half is multiplied.  X moves
+  // in 16-byte chunks, Y element by element to its transposed place.
 #pragma unroll
-    for (int s = 0; s < U; s++) {
-      const int c = c0 + s * nthr;
-      if (c < 2 * n_chunks) {
-        const int side = c >= n_chunks, cc = side ? c - n_chunks : c;
-        const int b = cc / kChunks, w = cc - b * kChunks;
-        v[s] = __ldg((side ? rmq : rq) + (base[b] >> 1) + w);
-      }
+  for (int half = 0; half < 2; half++) {
+    const int n_chunks = nb * (kChunks / 2);
+#pragma unroll 4
+    for (int c = tid; c < n_chunks; c += nthr) {
+      const int b = c / (kChunks / 2), w = half * (kChunks / 2) + (c - b * (kChunks / 2));
+      cp_async16(X + (size_t)b * kLd + 2 * w, rq + base[b] + 2 * w);
     }
-#pragma unroll
-    for (int s = 0; s < U; s++) {
-      const int c = c0 + s * nthr;
-      if (c < 2 * n_chunks) {
-        const int side = c >= n_chunks, cc = side ? c - n_chunks : c;
-        const int b = cc / kChunks, w = cc - b * kChunks;
-        if (!side) {
-          reinterpret_cast<float4*>(X + (size_t)b * kLd)[w] = v[s];
-        } else {  // elements e = 2w, 2w + 1 of M_b(-q): (u, v) and (u, v + 1) -> k = 12 v + u
-          const int e = 2 * w, u = e / 12, vv = e - 12 * u;
-          Y[(size_t)b * kLd + 12 * vv + u] = make_float2(v[s].x, v[s].y);
-          Y[(size_t)b * kLd + 12 * (vv + 1) + u] = make_float2(v[s].z, v[s].w);
-        }
-      }
+#pragma unroll 4
+    for (int c = tid; c < 72 * nb; c += nthr) {
+      const int b = c / 72, i = c - 72 * b, v = i / 6, u = half * 6 + (i - 6 * v);  // element (v, u) of M_b(-q)
+      cp_async8(Y + (size_t)b * kLd + 12 * u + v, rmq + base[b] + 12 * v + u);
     }
+    cp_async_commit();
   }
+  cp_async_wait_group<1>();
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  if (warp >= n_units) return;
+  // launched with n_units warps: every warp owns tiles (and reaches both barriers)
   const int un = units[warp], mt = un & 0xff, nt0 = (un >> 8) & 0xff, cnt = un >> 16;
-  float dr[kTcTilesPerWarp][4], di[kTcTilesPerWarp][4];
+  // three real products per complex one: t1 = Xr Yr, t2 = Xi Yi, t3 = (Xr + Xi)(Yr + Yi);
+  // Gr = t1 - t2, Gi = t3 - t1 - t2
+  float acc[3][kTcTilesPerWarp][4];
 #pragma unroll
-  for (int n = 0; n < kTcTilesPerWarp; n++)
+  for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int i = 0; i < 4; i++) dr[n][i] = di[n][i] = 0.f;
+    for (int n = 0; n < kTcTilesPerWarp; n++)
+#pragma unroll
+      for (int i = 0; i < 4; i++) acc[k][n][i] = 0.f;
   const float2* xa = X + (size_t)(16 * mt + g) * kLd + t;
   const float2* yb = Y + (size_t)(8 * nt0 + g) * kLd + t;
-#pragma unroll 2
   for (int k0 = 0; k0 < 144; k0 += 8) {
+    if (k0 == 72) {  // the second half of the rows
+      cp_async_wait_group<0>();
+      __syncthreads();
+    }
     // A fragment: (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4)
     const float2 x[4] = {xa[k0], xa[8 * kLd + k0], xa[k0 + 4], xa[8 * kLd + k0 + 4]};
-    uint32_t arh[4], arl[4], aih[4], ail[4], naih[4], nail[4];
+    uint32_t ah[3][4], al[3][4];  // [re, im, re + im][fragment register]
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-      if (MODE == kTc3x) {
-        split_tf32(x[i].x, arh[i], arl[i]);
-        split_tf32(x[i].y, aih[i], ail[i]);
-        nail[i] = neg(ail[i]);
-      } else {
-        arh[i] = tf32_rna(x[i].x);
-        aih[i] = tf32_rna(x[i].y);
+      const float v[3] = {x[i].x, x[i].y, __fadd_rn(x[i].x, x[i].y)};
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        if (MODE == kTc3x) split_tf32(v[k], ah[k][i], al[k][i]);
+        else ah[k][i] = tf32_rna(v[k]);
       }
-      naih[i] = neg(aih[i]);
     }
+    // B fragments of every tile: (k = t, col g), (k = t + 4, col g)
+    uint32_t bh[kTcTilesPerWarp][3][2], bl[kTcTilesPerWarp][3][2];
 #pragma unroll
     for (int n = 0; n < kTcTilesPerWarp; n++) {
       if (n >= cnt) break;
-      // B fragment: (k = t, col g), (k = t + 4, col g)
-      const float2 y0 = yb[(size_t)8 * n * kLd + k0], y1 = yb[(size_t)8 * n * kLd + k0 + 4];
-      uint32_t brh[2], brl[2], bih[2], bil[2];
-      if (MODE == kTc3x) {
-        split_tf32(y0.x, brh[0], brl[0]);
-        split_tf32(y1.x, brh[1], brl[1]);
-        split_tf32(y0.y, bih[0], bil[0]);
-        split_tf32(y1.y, bih[1], bil[1]);
-        // small terms first
-        mma_tf32(dr[n], arl, brh); mma_tf32(dr[n], arh, brl); mma_tf32(dr[n], arh, brh);
-        mma_tf32(dr[n], nail, bih); mma_tf32(dr[n], naih, bil); mma_tf32(dr[n], naih, bih);
-        mma_tf32(di[n], arl, bih); mma_tf32(di[n], arh, bil); mma_tf32(di[n], arh, bih);
-        mma_tf32(di[n], ail, brh); mma_tf32(di[n], aih, brl); mma_tf32(di[n], aih, brh);
-      } else {
-        brh[0] = tf32_rna(y0.x); brh[1] = tf32_rna(y1.x);
-        bih[0] = tf32_rna(y0.y); bih[1] = tf32_rna(y1.y);
-        mma_tf32(dr[n], arh, brh); mma_tf32(dr[n], naih, bih);
-        mma_tf32(di[n], arh, bih); mma_tf32(di[n], aih, brh);
+      const float2 y[2] = {yb[(size_t)8 * n * kLd + k0], yb[(size_t)8 * n * kLd + k0 + 4]};
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const float v[3] = {y[j].x, y[j].y, __fadd_rn(y[j].x, y[j].y)};
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          if (MODE == kTc3x) split_tf32(v[k], bh[n][k][j], bl[n][k][j]);
+          else bh[n][k][j] = tf32_rna(v[k]);
+        }
       }
+    }
+    // products interleaved over the tiles (independent accumulators back to
+    // back); 3xTF32: the two small cross terms before the large one
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      if (MODE == kTc3x) {
+#pragma unroll
+        for (int n = 0; n < kTcTilesPerWarp; n++)
+          if (n < cnt) mma_tf32(acc[k][n], al[k], bh[n][k]);
+#pragma unroll
+        for (int n = 0; n < kTcTilesPerWarp; n++)
+          if (n < cnt) mma_tf32(acc[k][n], ah[k], bl[n][k]);
+      }
+#pragma unroll
+      for (int n = 0; n < kTcTilesPerWarp; n++)
+        if (n < cnt) mma_tf32(acc[k][n], ah[k], bh[n][k]);
     }
   }
   // D fragment: (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1); G[p][m][n] complex64
@@ -157,9 +162,15 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
 #pragma unroll
   for (int n = 0; n < kTcTilesPerWarp; n++) {
     if (n >= cnt) break;
+    float gr[4], gi[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      gr[i] = acc[0][n][i] - acc[1][n][i];
+      gi[i] = acc[2][n][i] - acc[0][n][i] - acc[1][n][i];
+    }
     const int col = 8 * (nt0 + n) + 2 * t, m0 = 16 * mt + g;
-    Gp[((size_t)m0 * nbp + col) >> 1] = make_float4(dr[n][0], di[n][0], dr[n][1], di[n][1]);
-    Gp[((size_t)(m0 + 8) * nbp + col) >> 1] = make_float4(dr[n][2], di[n][2], dr[n][3], di[n][3]);
+    Gp[((size_t)m0 * nbp + col) >> 1] = make_float4(gr[0], gi[0], gr[1], gi[1]);
+    Gp[((size_t)(m0 + 8) * nbp + col) >> 1] = make_float4(gr[2], gi[2], gr[3], gi[3]);
   }
 }
 

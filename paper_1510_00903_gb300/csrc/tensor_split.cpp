@@ -166,6 +166,15 @@ bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err) {
     }
     S.out_ptr.push_back((int)S.coef.size());
   }
+  std::map<double, int> distinct;
+  for (double x : S.coef) {
+    auto it = distinct.find(x);
+    if (it == distinct.end()) {
+      it = distinct.emplace(x, (int)S.coef_values.size()).first;
+      S.coef_values.push_back(x);
+    }
+    S.coef_index.push_back(it->second);
+  }
   *out = std::move(S);
   return true;
 }

@@ -38,6 +38,8 @@ def test_autotune_then_oracle(precision):
     assert all(v > 0 for v in ms[len(BUILD):])
     assert cfg["pair_groups"] in (48, 96, 192, 384)
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
+    if precision != bbc.BBC_FP64:  # the dense-tuple FP32 build runs 1 or 2 sites per CTA of 256 threads
+        assert all(v > 0 for v in ms[:2]) and all(v == -1 for v in ms[2:len(BUILD)])
     # a later context for the same problem starts with the tuned configuration
     cor2 = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     assert cor2.tuning() == cfg
@@ -71,7 +73,10 @@ def test_every_configuration_matches(precision):
                 cor.set_tuning({"build_sites": sites, "build_threads": threads, "fused_warps": warps,
                                 "fused_chunk": chunk, "fused_steps": steps, "pair_groups": groups})
             except bbc.BBCError:
-                assert precision == bbc.BBC_FP64 and sites == 4  # 365 KB of shared memory
+                # FP64: four sites need 365 KB of shared memory; FP32 (dense-tuple
+                # build): one or two sites per CTA of 256 threads
+                assert (precision == bbc.BBC_FP64 and sites == 4) or \
+                    (precision != bbc.BBC_FP64 and (sites, threads) not in ((1, 256), (2, 256)))
                 continue
             out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
             assert _err(out, want) < tol, (sites, threads, warps, chunk, steps, groups)
@@ -82,5 +87,5 @@ def test_every_configuration_matches(precision):
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == {bbc.BBC_FP64: 12, bbc.BBC_MIXED_FP32: 60, bbc.BBC_MIXED_BF16: 100}[precision]
+    assert tried == {bbc.BBC_FP64: 12, bbc.BBC_MIXED_FP32: 30, bbc.BBC_MIXED_BF16: 50}[precision]
     cor.close()

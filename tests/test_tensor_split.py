@@ -112,6 +112,10 @@ static int check(const std::vector<int>& ch, int off, int plant) {
     worst = std::max(worst, std::max(std::abs(gq - ref_q[o]), std::abs(gmq - ref_mq[o])));
   }
   CHECK(worst <= 1e-12 * scale, "signed sums through the split differ from the plan's");
+  CHECK(S.coef_index.size() == S.coef.size(), "coefficient index per term");
+  for (size_t c = 0; c < S.coef.size(); c++)
+    CHECK(S.coef_index[c] >= 0 && S.coef_index[c] < (int)S.coef_values.size() &&
+              S.coef_values[S.coef_index[c]] == S.coef[c], "coefficient table");
   // G's warp tiles: inside G, and covering every entry the sums read
   std::vector<char> cov((size_t)nbp * nbp, 0);
   CHECK((int)S.units.size() <= kTcMaxWarps, "warps");
