@@ -187,6 +187,11 @@ def parse():
                          "the FP64 path checked against the oracle at sampled points")
     ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16", "df64"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
+    ap.add_argument("--slice-L", type=int, default=None,
+                    help="--single-slice on an L^3 x 2L lattice instead of 16^3 x 32")
+    ap.add_argument("--slice-channels", default=None,
+                    help="--single-slice on these comma-separated channel ids instead of the 52 (a smaller case "
+                         "of the same kernels for profilers)")
     ap.add_argument("--tuning", default=None,
                     help="launch configuration for --single-slice: sites,threads,warps,chunk[,steps[,pair_groups]] "
                          "(as bbc_set_tuning)")
@@ -335,11 +340,14 @@ def run_ours(args, torch, rank, world, local):
     L, T = L_BENCH, T_BENCH
     V = L ** 3
     if args.single_slice:
+        if args.slice_L:
+            L, T = args.slice_L, 2 * args.slice_L
+        chans = [int(x) for x in args.slice_channels.split(",")] if args.slice_channels else list(range(N_CH))
         t = T // 2
         F1 = synth.flavour_set(L, T, 0, M_UD, M_S, seed=1000, times=[t])
         prec = {"fp64": bbc.BBC_FP64, "mixed": bbc.BBC_MIXED_FP32, "bf16": bbc.BBC_MIXED_BF16,
                 "df64": bbc.BBC_DF64}[args.single_slice]
-        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=list(range(N_CH)), precision=prec, device=dev)
+        cor = bbc.Correlators(L, T, 0, M_UD, M_S, channels=chans, precision=prec, device=dev)
         if args.tuning:
             v = [int(x) for x in args.tuning.split(",")]
             cor.set_tuning({"build_sites": v[0], "build_threads": v[1], "fused_warps": v[2], "fused_chunk": v[3],

@@ -260,9 +260,10 @@ k_contract_rest(const float2* __restrict__ blk, int L, int n_out, const uint32_t
     const DevTask t = tasks[ti];
     cpx<float>* p0 = V + ti * 16;
     cpx<float>* p1 = V + np + ti * 16;
-    if (wb.nA == 4) unit_products_pair<4, 4, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
-    else if (wb.nA == 2) unit_products_pair<2, 8, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
-    else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, self);
+    // both sides even for q = -q: a swapped task's products for q are read from its -q side
+    if (wb.nA == 4) unit_products_pair<4, 4, STEPS>(R, t, un.z, un.w, p0, p1, ti, false);
+    else if (wb.nA == 2) unit_products_pair<2, 8, STEPS>(R, t, un.z, un.w, p0, p1, ti, false);
+    else unit_products_pair<8, 2, STEPS>(R, t, un.z, un.w, p0, p1, ti, false);
   }
   __syncthreads();
   for (int o = tid; o < n_outputs; o += kThreads) {

@@ -132,12 +132,13 @@ cudaError_t launch_contract_fused(const void* blk, int L, int n_out, const int* 
 // mode kTc3x: operands split into two TF32 words (FP32 accuracy); kTc1x: one
 // TF32 rounding per operand (trial precision).
 constexpr int kMaxTcBlocks = 64;     // blocks of G (G is at most 64 x 64)
-constexpr int kTcTilesPerWarp = 3;   // 16 x 8 complex tiles of G per warp
+constexpr int kTcTilesPerWarp = 3;   // 16 x 8 complex tiles of G per warp (at most)
 constexpr int kTcMaxWarps = 16;
 constexpr int kTc3x = 0, kTc1x = 1;
 size_t contract_tc_smem(int nbp);
 cudaError_t launch_contract_tc(const void* blk, int L, int n_out, const int* base, int nb, int nbp, const int* qlist,
-                               int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st);
+                               int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st,
+                               int tiles = kTcTilesPerWarp);
 // The rest of the mixed contraction (fused_contract.cu): per pair {q, -q}
 // the CUDA-core products of the other tasks on compact rows (row_map[i] =
 // block row | shared-memory slot << 16, i < n_rows) and the signed

@@ -6,43 +6,89 @@
 namespace bbc {
 
 constexpr int kPairWarpsDf = 4;
+constexpr int kDfStages = 2;      // open-index steps of rows in flight per lane
+constexpr int kDfMaxRows = 10;    // nA + nB of the widest task shape (2 x 8, 8 x 2)
 
 // Double-float variant: the Fourier-space blocks as (re.hi, re.lo, im.hi,
 // im.lo) FP32 quadruples (from the double-float forward FFT), every complex
 // product as four double-float multiply-adds on the FP32 pipes, accumulators
 // renormalised every 16 open-index steps, the products stored as
 // double-float pairs for the double-float Wick sums.
+//
+// The rows of an open-index step reach the lane through a ring of kDfStages
+// shared-memory stages filled by cp.async: while the lane multiplies step k,
+// the rows of step k + 1 are on their way, so the L2 and DRAM latency of the
+// row loads overlaps the arithmetic instead of stalling it.  A lane reads
+// only the 16-byte slots it copied itself (slot [stage][row][lane]), so the
+// ring needs no barrier, and the 32 lanes' slots of one row are contiguous
+// (conflict-free 128-bit shared loads).
+template <int NA, int NB>
+struct DfRows {
+  static constexpr int NR = NA + NB;
+  const float4* F;
+  long long V;
+  int q, nq;
+  int i1, i2, oA, oB;  // open-index position of the next step to fetch
+  // rows of the next step into stage `st` of this lane's ring, then advance
+  __device__ __forceinline__ void fetch(const DevTask& t, float4* ring, int st) {
+    float4* dst = ring + st * NR * 32;
+#pragma unroll
+    for (int r = 0; r < NA; r++) cp_async16(dst + r * 32, F + (long long)(t.offA[r] + oA) * V + q);
+#pragma unroll
+    for (int r = 0; r < NB; r++) cp_async16(dst + (NA + r) * 32, F + (long long)(t.offB[r] + oB) * V + nq);
+    if (++i2 == t.n2) {
+      i2 = 0;
+      ++i1;
+      oA = i1 * (t.sA & 0xffff);
+      oB = i1 * (t.sB & 0xffff);
+    } else {
+      oA += t.sA >> 16;
+      oB += t.sB >> 16;
+    }
+  }
+};
+
 template <int NA, int NB>
 __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, long long V, int q, int nq,
-                                                 const DevTask& t, cpx<dfr>* __restrict__ P) {
-  const int n2 = t.n2, K = t.n1 * n2;
-  const int sA1 = t.sA & 0xffff, sA2 = t.sA >> 16, sB1 = t.sB & 0xffff, sB2 = t.sB >> 16;
+                                                 const DevTask& t, cpx<dfr>* __restrict__ P, float4* ring) {
+  constexpr int NR = NA + NB;
+  const int K = t.n1 * t.n2;
+  DfRows<NA, NB> rows{F, V, q, nq, 0, 0, 0, 0};
   df64acc re[NA * NB], im[NA * NB];
 #pragma unroll
   for (int i = 0; i < NA * NB; i++) { re[i] = df64acc{0.f, 0.f}; im[i] = df64acc{0.f, 0.f}; }
-  int i1 = 0, i2 = 0, oA = 0, oB = 0;
+#pragma unroll
+  for (int s = 0; s < kDfStages; s++) {
+    if (s < K) rows.fetch(t, ring, s);
+    cp_async_commit();
+  }
   for (int k = 0; k < K; k++) {
-    float4 a[NA], b[NB];  // (re.hi, re.lo, im.hi, im.lo)
+    const int st = k % kDfStages;
+    cp_async_wait_group<kDfStages - 1>();  // the rows of step k have landed
+    const float4* src = ring + st * NR * 32;
+    float4 b[NB];  // (re.hi, re.lo, im.hi, im.lo)
 #pragma unroll
-    for (int r = 0; r < NA; r++) a[r] = F[(long long)(t.offA[r] + oA) * V + q];
+    for (int r = 0; r < NB; r++) b[r] = src[(NA + r) * 32];
 #pragma unroll
-    for (int r = 0; r < NB; r++) b[r] = F[(long long)(t.offB[r] + oB) * V + nq];
-#pragma unroll
-    for (int ra = 0; ra < NA; ra++)
+    for (int ra = 0; ra < NA; ra++) {
+      const float4 a = src[ra * 32];
 #pragma unroll
       for (int rb = 0; rb < NB; rb++) {
         const int i = ra * NB + rb;
-        df_mac(re[i], a[ra].x, a[ra].y, b[rb].x, b[rb].y);    // + Re a Re b
-        df_mac(re[i], -a[ra].z, -a[ra].w, b[rb].z, b[rb].w);  // - Im a Im b
-        df_mac(im[i], a[ra].x, a[ra].y, b[rb].z, b[rb].w);    // + Re a Im b
-        df_mac(im[i], a[ra].z, a[ra].w, b[rb].x, b[rb].y);    // + Im a Re b
+        df_mac(re[i], a.x, a.y, b[rb].x, b[rb].y);    // + Re a Re b
+        df_mac(re[i], -a.z, -a.w, b[rb].z, b[rb].w);  // - Im a Im b
+        df_mac(im[i], a.x, a.y, b[rb].z, b[rb].w);    // + Re a Im b
+        df_mac(im[i], a.z, a.w, b[rb].x, b[rb].y);    // + Im a Re b
       }
+    }
     if ((k & 15) == 15) {
 #pragma unroll
       for (int i = 0; i < NA * NB; i++) { df_renorm(re[i]); df_renorm(im[i]); }
     }
-    if (++i2 == n2) { i2 = 0; ++i1; oA = i1 * sA1; oB = i1 * sB1; }
-    else { oA += sA2; oB += sB2; }
+    // the stage just read takes the rows of step k + kDfStages (an empty
+    // group past the end keeps the group count in step)
+    if (k + kDfStages < K) rows.fetch(t, ring, st);
+    cp_async_commit();
   }
 #pragma unroll
   for (int i = 0; i < NA * NB; i++) {
@@ -56,11 +102,13 @@ __global__ void __launch_bounds__(32 * kPairWarpsDf, 4)
 k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restrict__ tasks,
                    const int* __restrict__ group_ptr, const int* __restrict__ group_task, int n_groups,
                    cpx<dfr>* __restrict__ P) {
+  extern __shared__ float4 df_ring[];  // [warp][kDfStages][kDfMaxRows][32]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = blockIdx.x * kPairWarpsDf + warp;
   const int V = L * L * L;
   const int q = blockIdx.y * 32 + lane;
   if (g >= n_groups || q >= V) return;
+  float4* ring = df_ring + warp * kDfStages * kDfMaxRows * 32 + lane;
   const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
   const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
   const int j1 = group_ptr[g + 1];
@@ -69,9 +117,9 @@ k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restric
     const DevTask t = tasks[ti];
     cpx<dfr>* p = P + (long long)ti * 16 * V + q;
     const int nA = t.nAnB & 0xff;
-    if (nA == 4) task_products_df<4, 4>(F, V, q, nq, t, p);
-    else if (nA == 2) task_products_df<2, 8>(F, V, q, nq, t, p);
-    else task_products_df<8, 2>(F, V, q, nq, t, p);
+    if (nA == 4) task_products_df<4, 4>(F, V, q, nq, t, p, ring);
+    else if (nA == 2) task_products_df<2, 8>(F, V, q, nq, t, p, ring);
+    else task_products_df<8, 2>(F, V, q, nq, t, p, ring);
   }
 }
 
@@ -79,9 +127,11 @@ cudaError_t launch_pair_products_df(const void* blk_field, int L, const DevTask*
                                     const int* group_task, int n_groups, void* P, cudaStream_t st) {
   const int V = L * L * L;
   if (n_groups <= 0) return cudaSuccess;  // a plan whose products all vanish has no tasks
+  constexpr size_t sm = sizeof(float4) * kPairWarpsDf * kDfStages * kDfMaxRows * 32;
+  static_assert(sm <= 48 * 1024, "the ring fits the default dynamic shared-memory limit");
   dim3 g1((n_groups + kPairWarpsDf - 1) / kPairWarpsDf, (V + 31) / 32);
-  k_pair_products_df<<<g1, 32 * kPairWarpsDf, 0, st>>>((const float4*)blk_field, L, tasks, group_ptr, group_task,
-                                                       n_groups, (cpx<dfr>*)P);
+  k_pair_products_df<<<g1, 32 * kPairWarpsDf, sm, st>>>((const float4*)blk_field, L, tasks, group_ptr, group_task,
+                                                        n_groups, (cpx<dfr>*)P);
   return cudaGetLastError();
 }
 

@@ -172,7 +172,11 @@ struct TcSplit {
   std::vector<int> src_q, src_mq;
   std::vector<double> coef_values;   // the distinct coefficients (exact copies)
   std::vector<int> coef_index;       // per term: its coefficient in coef_values
+  std::vector<char> need;            // [mt_n][nt_n]: 16 x 8 tiles of G with an entry the sums read
+  int mt_n = 0, nt_n = 0;
 };
+// Warp units of G for `tiles` (2 or 3) n-tiles per warp.
+void tc_units(const TcSplit& split, int tiles, std::vector<int>* units);
 // nb = 0 when no task has the trace form (or G would exceed kMaxTcBlocks):
 // then every task is in rest.  Returns false only on an internal inconsistency.
 bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err);

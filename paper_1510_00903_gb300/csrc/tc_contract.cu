@@ -10,7 +10,7 @@
 // One CTA per pair {q, -q}.  The q row of every block is staged as X[i][k]
 // = M_i(q)[u][v] and the -q row transposed, Y[j][k] = M_j(-q)[v][u] (k =
 // 12 u + v), so that G = X Y^T over k = 0..143.  A warp owns one 16-row
-// m-tile and up to three 8-column n-tiles of G and runs the complex product
+// m-tile and up to TILES (2 or 3, tuned) 8-column n-tiles of G and runs the complex product
 // as three real products (t1 = Xr Yr, t2 = Xi Yi, t3 = (Xr + Xi)(Yr + Yi);
 // Gr = t1 - t2, Gi = t3 - t1 - t2) with mma.sync m16n8k8 on TF32 operands and
 // FP32 accumulators.  FP32 accuracy (kTc3x) comes from splitting every
@@ -54,7 +54,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 
 }  // namespace
 
-template <int MODE>
+template <int MODE, int TILES>
 __global__ void __launch_bounds__(kTcMaxWarps * 32)
 k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __restrict__ base, int nb, int nbp,
               const int* __restrict__ qlist, const int* __restrict__ units, int n_units, float2* __restrict__ G) {
@@ -98,11 +98,11 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
   const int un = units[warp], mt = un & 0xff, nt0 = (un >> 8) & 0xff, cnt = un >> 16;
   // three real products per complex one: t1 = Xr Yr, t2 = Xi Yi, t3 = (Xr + Xi)(Yr + Yi);
   // Gr = t1 - t2, Gi = t3 - t1 - t2
-  float acc[3][kTcTilesPerWarp][4];
+  float acc[3][TILES][4];
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int n = 0; n < kTcTilesPerWarp; n++)
+    for (int n = 0; n < TILES; n++)
 #pragma unroll
       for (int i = 0; i < 4; i++) acc[k][n][i] = 0.f;
   const float2* xa = X + (size_t)(16 * mt + g) * kLd + t;
@@ -125,9 +125,9 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
       }
     }
     // B fragments of every tile: (k = t, col g), (k = t + 4, col g)
-    uint32_t bh[kTcTilesPerWarp][3][2], bl[kTcTilesPerWarp][3][2];
+    uint32_t bh[TILES][3][2], bl[TILES][3][2];
 #pragma unroll
-    for (int n = 0; n < kTcTilesPerWarp; n++) {
+    for (int n = 0; n < TILES; n++) {
       if (n >= cnt) break;
       const float2 y[2] = {yb[(size_t)8 * n * kLd + k0], yb[(size_t)8 * n * kLd + k0 + 4]};
 #pragma unroll
@@ -146,21 +146,21 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
     for (int k = 0; k < 3; k++) {
       if (MODE == kTc3x) {
 #pragma unroll
-        for (int n = 0; n < kTcTilesPerWarp; n++)
+        for (int n = 0; n < TILES; n++)
           if (n < cnt) mma_tf32(acc[k][n], al[k], bh[n][k]);
 #pragma unroll
-        for (int n = 0; n < kTcTilesPerWarp; n++)
+        for (int n = 0; n < TILES; n++)
           if (n < cnt) mma_tf32(acc[k][n], ah[k], bl[n][k]);
       }
 #pragma unroll
-      for (int n = 0; n < kTcTilesPerWarp; n++)
+      for (int n = 0; n < TILES; n++)
         if (n < cnt) mma_tf32(acc[k][n], ah[k], bh[n][k]);
     }
   }
   // D fragment: (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1); G[p][m][n] complex64
   float4* Gp = reinterpret_cast<float4*>(G + (size_t)p * nbp * nbp);
 #pragma unroll
-  for (int n = 0; n < kTcTilesPerWarp; n++) {
+  for (int n = 0; n < TILES; n++) {
     if (n >= cnt) break;
     float gr[4], gi[4];
 #pragma unroll
@@ -176,26 +176,32 @@ k_contract_tc(const float2* __restrict__ blk, int L, int n_out, const int* __res
 
 size_t contract_tc_smem(int nbp) { return (size_t)2 * nbp * kLd * sizeof(float2); }
 
+template <int MODE, int TILES>
+static cudaError_t launch_tc_variant(size_t sm, int n_q, int n_units, cudaStream_t st, const void* blk, int L, int n_out,
+                                    const int* base, int nb, int nbp, const int* qlist, const int* units, void* G) {
+  static int granted[64] = {0};
+  cudaError_t e = ensure_smem(k_contract_tc<MODE, TILES>, sm, granted);
+  if (e != cudaSuccess) return e;
+  k_contract_tc<MODE, TILES><<<n_q, n_units * 32, sm, st>>>((const float2*)blk, L, n_out, base, nb, nbp, qlist, units,
+                                                           n_units, (float2*)G);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_contract_tc(const void* blk, int L, int n_out, const int* base, int nb, int nbp, const int* qlist,
-                               int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st) {
+                               int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st, int tiles) {
   if (n_q == 0) return cudaSuccess;
   if (nb < 1 || nb > nbp || nbp % 16 || nbp > kMaxTcBlocks || n_units < 1 || n_units > kTcMaxWarps || (n_out & 1))
     return cudaErrorInvalidValue;
   const size_t sm = contract_tc_smem(nbp);
-  static int granted[2][64] = {{0}};
-  cudaError_t e;
-  if (mode == kTc3x) {
-    e = ensure_smem(k_contract_tc<kTc3x>, sm, granted[0]);
-    if (e != cudaSuccess) return e;
-    k_contract_tc<kTc3x><<<n_q, n_units * 32, sm, st>>>((const float2*)blk, L, n_out, base, nb, nbp, qlist, units,
-                                                        n_units, (float2*)G);
-  } else {
-    e = ensure_smem(k_contract_tc<kTc1x>, sm, granted[1]);
-    if (e != cudaSuccess) return e;
-    k_contract_tc<kTc1x><<<n_q, n_units * 32, sm, st>>>((const float2*)blk, L, n_out, base, nb, nbp, qlist, units,
-                                                        n_units, (float2*)G);
-  }
-  return cudaGetLastError();
+  if (mode == kTc3x && tiles == 3)
+    return launch_tc_variant<kTc3x, 3>(sm, n_q, n_units, st, blk, L, n_out, base, nb, nbp, qlist, units, G);
+  if (mode == kTc3x && tiles == 2)
+    return launch_tc_variant<kTc3x, 2>(sm, n_q, n_units, st, blk, L, n_out, base, nb, nbp, qlist, units, G);
+  if (mode == kTc1x && tiles == 3)
+    return launch_tc_variant<kTc1x, 3>(sm, n_q, n_units, st, blk, L, n_out, base, nb, nbp, qlist, units, G);
+  if (mode == kTc1x && tiles == 2)
+    return launch_tc_variant<kTc1x, 2>(sm, n_q, n_units, st, blk, L, n_out, base, nb, nbp, qlist, units, G);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace bbc

@@ -34,6 +34,22 @@ bool trace_form(const PairTask& t) {
 
 }  // namespace
 
+void tc_units(const TcSplit& S, int tiles, std::vector<int>* units) {
+  // one m-tile and up to `tiles` consecutive n-tiles per warp (unneeded tiles
+  // inside a run are computed and not read)
+  units->clear();
+  for (int mt = 0; mt < S.mt_n; mt++) {
+    int nt = 0;
+    while (nt < S.nt_n) {
+      if (!S.need[(size_t)mt * S.nt_n + nt]) { nt++; continue; }
+      int cnt = 1;
+      while (nt + cnt < S.nt_n && cnt < tiles && S.need[(size_t)mt * S.nt_n + nt + cnt]) cnt++;
+      units->push_back(mt | (nt << 8) | (cnt << 16));
+      nt += cnt;
+    }
+  }
+}
+
 bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err) {
   TcSplit S;
   const int n_tasks = (int)plan.tasks.size();
@@ -81,18 +97,10 @@ bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err) {
         need[(size_t)(j / 16) * nt_n + i / 8] = 1;
       }
   }
-  // warp units: one m-tile and up to kTcTilesPerWarp consecutive n-tiles
-  // (unneeded tiles inside a run are computed and not read)
-  for (int mt = 0; mt < mt_n; mt++) {
-    int nt = 0;
-    while (nt < nt_n) {
-      if (!need[(size_t)mt * nt_n + nt]) { nt++; continue; }
-      int cnt = 1;
-      while (nt + cnt < nt_n && cnt < kTcTilesPerWarp && need[(size_t)mt * nt_n + nt + cnt]) cnt++;
-      S.units.push_back(mt | (nt << 8) | (cnt << 16));
-      nt += cnt;
-    }
-  }
+  S.need = need;
+  S.mt_n = mt_n;
+  S.nt_n = nt_n;
+  tc_units(S, kTcTilesPerWarp, &S.units);
   if ((int)S.units.size() > kTcMaxWarps) {
     *err = "internal: tensor-core tiles exceed one CTA's warps";
     return false;
@@ -130,12 +138,32 @@ bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err) {
       S.row_src.push_back(row);
     }
   S.rest.n_out = (int)S.row_src.size();
+  // A task of shape 2 x 8 runs as the 8 x 2 task with its operands swapped:
+  // sum_k B(q; k) A(-q; k) is the original product at -q, transposed, so the
+  // kernel's two sides trade places and the swapped tasks share the lanes of
+  // one batch class with the 8 x 2 ones.
   std::vector<int> rest_index(n_tasks, -1);
+  std::vector<char> swapped(n_tasks, 0);
   for (int t = 0; t < n_tasks; t++) {
     if (tc[t]) continue;
     PairTask k = plan.tasks[t];
     for (int r = 0; r < k.nA; r++) k.offA[r] = compact[k.offA[r]];
     for (int r = 0; r < k.nB; r++) k.offB[r] = compact[k.offB[r]];
+    if (k.nA == 2 && k.nB == 8) {
+      PairTask w = k;
+      w.nA = k.nB;
+      w.nB = k.nA;
+      for (int r = 0; r < 8; r++) {
+        w.offA[r] = r < k.nB ? k.offB[r] : 0;
+        w.offB[r] = r < k.nA ? k.offA[r] : 0;
+      }
+      w.sA1 = k.sB1;
+      w.sA2 = k.sB2;
+      w.sB1 = k.sA1;
+      w.sB2 = k.sA2;
+      k = w;
+      swapped[t] = 1;
+    }
     rest_index[t] = (int)S.rest.tasks.size();
     S.rest.tasks.push_back(k);
   }
@@ -155,10 +183,14 @@ bool split_tensor_tasks(const Plan& plan, TcSplit* out, std::string* err) {
         const int a = block_of[k.offA[ra]], b = block_of[k.offB[rb]];
         sq = 2 * np + a * S.nbp + b;
         smq = 2 * np + b * S.nbp + a;
-      } else {
+      } else if (!swapped[t]) {
         const int rt = rest_index[t];
         sq = 16 * rt + ((i + rt) & 15);
         smq = np + sq;
+      } else {  // product (rA, rB) of the original is (rB, rA) of the swapped task, sides exchanged
+        const int rt = rest_index[t], ra = i / k.nB, rb = i % k.nB, j = rb * k.nA + ra;
+        smq = 16 * rt + ((j + rt) & 15);
+        sq = np + smq;
       }
       S.coef.push_back(plan.tcontrib_coef[c]);
       S.src_q.push_back(sq);
