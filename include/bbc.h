@@ -67,7 +67,7 @@ typedef enum {
   BBC_ENOMEM = -2,   /* workspace missing or too small, host allocation failure */
   BBC_ECUDA = -3,    /* a CUDA runtime call failed; message in bbc_last_error */
   BBC_ESTATE = -4,   /* call out of order (e.g. contract before build) */
-  BBC_ETIMEOUT = -5, /* reserved: a bounded device wait gave up */
+  BBC_ETIMEOUT = -5, /* a bounded device wait gave up (bbc_device_status) */
   BBC_ENUMERIC = -6  /* NaN or infinity in an input or output (bbc_set_checks) */
 } bbc_status;
 
@@ -274,6 +274,28 @@ bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_st
 #define BBC_CHECK_INPUT 1
 #define BBC_CHECK_OUTPUT 2
 bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
+
+/* Bounded device waits.  In the mixed precisions (L <= 32) the forward 3-D FFT
+ * of bbc_build_blocks is one persistent launch whose CTAs take (row tile,
+ * z plane) and (row tile, z lines) units from a device work queue; a z-lines
+ * unit waits for the planes of its row tile, at most about a second, and a
+ * wait that gives up sets a sticky device word and stops the launch.
+ * bbc_device_status synchronises the context stream and returns
+ * BBC_ETIMEOUT if that happened since the last call (the word is cleared and
+ * every slot marked unbuilt: its blocks are not valid), else BBC_OK (also
+ * without a workspace).  BBC_CHECK_OUTPUT runs the same check in
+ * bbc_contract.  Not inside a stream capture. */
+bbc_status bbc_device_status(bbc_ctx* ctx);
+
+/* Self-test of those waits: one queue-driven forward FFT of slot 0's blocks
+ * with a dependency count no unit reaches, so that every wait runs out after
+ * spin_limit polls (1 .. 2^22, each about 0.3 us).  Synchronous.  Returns
+ * BBC_ETIMEOUT when the kernel reported the timeout (the expected outcome;
+ * slot 0 is then unbuilt and the context usable), BBC_OK if no wait gave up
+ * (a fault in the waits), EINVAL for spin_limit out of range, ESTATE without a
+ * workspace or without the queue-driven FFT (FP64, double-float, L = 48, or
+ * a plan too large for the fused kernels).  Not inside a stream capture. */
+bbc_status bbc_check_bounded_wait(bbc_ctx* ctx, long long spin_limit);
 
 /* Launch configuration of the two kernels whose shape is tunable:
  *  build_sites, build_threads: sites per CTA and threads of the block build,

@@ -93,6 +93,8 @@ def _load():
         "bbc_run_slice_static": ([P, I, P, P, I, P, I], I),
         "bbc_project": ([P, P, I, P, P], I),
         "bbc_set_checks": ([P, I], I),
+        "bbc_device_status": ([P], I),
+        "bbc_check_bounded_wait": ([P, LL], I),
         "bbc_batch_run": ([ctypes.POINTER(bbc_batch_item), I, P, ctypes.POINTER(I)], I),
         "bbc_get_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
         "bbc_set_tuning": ([P, ctypes.POINTER(bbc_tuning)], I),
@@ -277,6 +279,17 @@ BBC_CHECK_INPUT, BBC_CHECK_OUTPUT = 1, 2
 def bbc_set_checks(ctx, flags: int):
     """Enable numeric checks: BBC_CHECK_INPUT | BBC_CHECK_OUTPUT (ENUMERIC on NaN/inf)."""
     _check(ctx, _lib.bbc_set_checks(ctx, int(flags)))
+
+
+def bbc_device_status(ctx):
+    """Synchronise the context stream; raise BBCError(BBC_ETIMEOUT) if a bounded
+    wait of the queue-driven forward FFT gave up since the last call."""
+    _check(ctx, _lib.bbc_device_status(ctx))
+
+
+def bbc_check_bounded_wait(ctx, spin_limit: int) -> int:
+    """Self-test of the bounded waits; returns the status (BBC_ETIMEOUT expected)."""
+    return int(_lib.bbc_check_bounded_wait(ctx, int(spin_limit)))
 
 
 def bbc_get_tuning(ctx) -> dict:
@@ -549,6 +562,10 @@ class Correlators:
             tuning_cache_store(path, key, cfg)
         return cfg, ms
 
+    def status(self):
+        """Synchronise and raise BBCError(BBC_ETIMEOUT) if a bounded device wait gave up."""
+        bbc_device_status(self.ctx)
+
     def tuning(self) -> dict:
         return bbc_get_tuning(self.ctx)
 
@@ -688,6 +705,13 @@ class LatticeBatch:
         with torch.cuda.graph(g, stream=self.stream):
             self.run()
         return g
+
+    def status(self):
+        """Synchronise and raise BBCError(BBC_ETIMEOUT) if a bounded device wait of
+        any context gave up."""
+        for per in self.cors:
+            for c in per:
+                c.status()
 
     def close(self):
         for per in self.cors:

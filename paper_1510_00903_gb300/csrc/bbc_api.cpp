@@ -30,6 +30,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 bool fp64_storage(int prec) { return prec == BBC_FP64 || prec == BBC_DF64; }
 size_t cplx_bytes(int prec) { return fp64_storage(prec) ? 16 : 8; }
 bool fused_path(int prec) { return !fp64_storage(prec); }  // FP32 or bfloat16 products (if they fit one CTA)
+// The fused FP32 path's forward FFT runs as one queue-driven persistent launch for L <= 32.
+bool queue_fft(const bbc_ctx* c) { return c->fused && bbc::fft_queue_supported(c->lat.L); }
 int real_kind(int prec) { return prec == BBC_DF64 ? bbc::RK_DF : (prec == BBC_FP64 ? bbc::RK_F64 : bbc::RK_F32); }
 
 constexpr int kMaxFusedWarps = 16;
@@ -43,7 +45,7 @@ struct Layout {
   size_t ell_chunk, ell, zneed, tasks, group_ptr, group_task, cptr, citem, ccoef, ccoef_df;
   size_t batches, wptr, wunits, qlist, row_slot, orb_ptr, orb_site;
   size_t tc_base, tc_units, row_map, tc_cptr, tc_terms, tc_coefs, dtuples, dchunk, dell, tables_end;
-  size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, G, ct, scale, flag, total;
+  size_t stage, prop, amax, kexp, blk, blk16, blkf, blks, P, G, ct, scale, flag, qerr, fftq, total;
 };
 
 Layout layout(const bbc_ctx* c, int slots) {
@@ -94,6 +96,9 @@ Layout layout(const bbc_ctx* c, int slots) {
   L.ct = o; o = align256(o + (size_t)p.channels.size() * 16 * V * 16);
   L.scale = o; o = align256(o + sizeof(double) * bbc::kMaxChannels);
   L.flag = o; o = align256(o + sizeof(int));
+  // queue-driven forward FFT: its sticky timeout word, ticket counter and per-tile counters
+  L.qerr = o; o = align256(o + sizeof(int));
+  L.fftq = o; o = align256(o + (queue_fft(c) ? sizeof(int) * bbc::fft_queue_ints(c->lat.L, slots, p.n_out) : 0));
   L.total = o;
   return L;
 }
@@ -282,6 +287,22 @@ double time_launches(bbc_ctx* c, int reps, F launch) {
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return ok && ms >= 0.f ? ms / reps : -1.0;
+}
+
+// Sticky record of the queue-driven forward FFT's bounded waits (synchronous):
+// BBC_ETIMEOUT, the record cleared and every slot marked unbuilt, if a wait
+// gave up since the last read.
+bbc_status wait_status(bbc_ctx* c) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, c->d_qerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device status");
+  if (!err) return BBC_OK;
+  e = cudaMemsetAsync(c->d_qerr, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device status");
+  for (auto& b : c->slot_built) b = 0;
+  return fail(c, BBC_ETIMEOUT, "a bounded wait of the queue-driven forward FFT gave up: the blocks are not valid");
 }
 
 // The block build of slots [0, n_slots): the dense-tuple FP32 kernel, or the
@@ -566,6 +587,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
   c->d_ct = w + L.ct;
   c->d_scale = (double*)(w + L.scale);
   c->d_flag = (int*)(w + L.flag);
+  c->d_qerr = (int*)(w + L.qerr);
+  c->d_fftq = queue_fft(c) ? (int*)(w + L.fftq) : nullptr;
   const bbc::Plan& p = c->plan;
   // the fused kernels address their shared-memory copy of the rows (slots)
   const std::vector<bbc::PairTask>& run_tasks = fused_plan(c).tasks;
@@ -621,6 +644,8 @@ bbc_status bbc_set_workspace(bbc_ctx* c, void* dev_ptr, size_t bytes, int slices
       {c->d_dchunk, c->db.ell_chunk.data(), sizeof(int2) * c->db.ell_chunk.size()},
       {c->d_dell, c->db.ell.data(), sizeof(uint32_t) * c->db.ell.size()},
   };
+  cudaError_t e0 = cudaMemsetAsync(c->d_qerr, 0, sizeof(int), c->stream);
+  if (e0 != cudaSuccess) return cuda_fail(c, e0, "workspace status word");
   for (auto& u : ups) {
     if (u.n == 0) continue;
     // synchronous copy from pageable host memory: the tables are live only
@@ -705,6 +730,9 @@ bbc_status bbc_build_blocks(bbc_ctx* c, int n_slots) {
     e = c->prec == BBC_DF64 ? bbc::launch_fft_forward_df(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, c->stream)
         : !c->fused         ? bbc::launch_fft_forward(c->d_blk, c->d_blkf, c->lat.L, n_slots, p.n_out, fp64, c->stream,
                                                       c->d_blks)
+        : queue_fft(c)      ? bbc::launch_fft_forward_queue(c->d_blk, c->lat.L, n_slots, p.n_out,
+                                                        bbc::FftQueue{c->d_fftq, c->d_qerr}, -1, bbc::kFftSpinLimit,
+                                                        c->stream)
                             : bbc::launch_fft_forward_site(c->d_blk, c->lat.L, n_slots, p.n_out, fp64, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "forward FFT");
     if (c->prec == BBC_MIXED_BF16) {
@@ -794,9 +822,30 @@ bbc_status bbc_contract(bbc_ctx* c, int slot, void* out_dev, int normalised) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "output check");
+    const bbc_status ws = wait_status(c);  // a timed-out FFT wait explains any output
+    if (ws != BBC_OK) return ws;
     if (flag) return fail(c, BBC_ENUMERIC, "correlators of slice " + std::to_string(t) + " have a NaN or infinite entry");
   }
   return BBC_OK;
+}
+
+bbc_status bbc_device_status(bbc_ctx* c) {
+  if (!c) return BBC_EINVAL;
+  if (!c->ws) return BBC_OK;  // nothing has run
+  return wait_status(c);
+}
+
+bbc_status bbc_check_bounded_wait(bbc_ctx* c, long long spin_limit) {
+  if (!c) return BBC_EINVAL;
+  if (spin_limit < 1 || spin_limit > bbc::kFftSpinLimit) return fail(c, BBC_EINVAL, "spin_limit outside [1, 2^22]");
+  if (!c->ws) return fail(c, BBC_ESTATE, "no workspace attached");
+  if (!queue_fft(c)) return fail(c, BBC_ESTATE, "this context has no queue-driven forward FFT");
+  // a dependency count of L + 1 planes: no line unit's wait can end
+  cudaError_t e = bbc::launch_fft_forward_queue(c->d_blk, c->lat.L, 1, c->plan.n_out,
+                                                bbc::FftQueue{c->d_fftq, c->d_qerr}, c->lat.L + 1, spin_limit,
+                                                c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "bounded-wait self-test");
+  return wait_status(c);
 }
 
 bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_stream, int* failed_item) {
@@ -1099,11 +1148,13 @@ bbc_status bbc_stage_timing(bbc_ctx* c, double* ms, long long* launches) {
 bbc_status bbc_launch_counts(const bbc_ctx* c, int* per_load, int* per_build, int* per_contract) {
   if (!c) return BBC_EINVAL;
   // forward and inverse FFT passes: the fused (q-major) layout fuses the x and
-  // y passes for L <= 32; the field-major layout runs three
+  // y passes for L <= 32 (and runs the forward transform as one queue-driven
+  // launch there); the field-major layout runs three
   const bool xy = c->fused && c->lat.L <= 32;
   const int passes = xy ? 2 : 3;
+  const int fwd = queue_fft(c) ? 1 : passes;
   if (per_load) *per_load = 2;  // absmax, convert
-  if (per_build) *per_build = 1 + passes + (c->prec == BBC_MIXED_BF16 ? 1 : 0);  // build, FFT (, bfloat16 rounding)
+  if (per_build) *per_build = 1 + fwd + (c->prec == BBC_MIXED_BF16 ? 1 : 0);  // build, FFT (, bfloat16 rounding)
   // contraction kernel(s), scales, inverse passes
   if (per_contract) *per_contract = (c->tc ? 2 : c->fused ? 1 : 2) + 1 + passes;
   return BBC_OK;

@@ -88,6 +88,8 @@ struct bbc_ctx {
   char* d_ct = nullptr;                  // [n_ch*16][V] complex128 q-space correlators
   double* d_scale = nullptr;             // [kMaxChannels]
   int* d_flag = nullptr;                 // non-finite output flag (bbc_set_checks)
+  int* d_qerr = nullptr;                 // sticky: a bounded wait of the queue-driven FFT gave up
+  int* d_fftq = nullptr;                 // queue-driven FFT: ticket counter, per-tile counters
   int checks = 0;                        // BBC_CHECK_INPUT | BBC_CHECK_OUTPUT
   std::vector<int> slot_t;               // time slice of each slot (-1: none)
   std::vector<int> slot_loaded;          // bit 0: light, bit 1: strange

@@ -425,6 +425,206 @@ static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ persistent site-major FFT
+// The forward x, y and z passes of the site-major layout data[o][site][n_inner]
+// (L <= 32) in one persistent launch over a device work queue.  The inner
+// columns are cut into row tiles g of TI columns of one outer index; tile g
+// has N plane units (the x and y lines of one z plane, staged in shared
+// memory as in k_fft_xy_site) and ZU line units (its z lines, 256 (line,
+// column) pairs each).  A CTA takes the next ticket from a global counter;
+// tickets run in steps of N + ZU, step s holding the plane units of tile s
+// and the line units of tile s - lag, so a tile's z lines are read back from
+// L2 soon after its planes were written (one HBM round trip for the three
+// passes instead of two).  A line unit waits until the N plane units of its
+// tile have signalled (q.words = [ticket counter, done[n_tiles]], zeroed
+// before the launch).  The wait ends: every ticket below its own was taken
+// by a CTA that is running, and plane units wait on nothing.  It is bounded
+// all the same: after spin_limit polls the CTA sets the sticky word *q.err
+// (cleared only by the host), and no CTA takes a ticket while it is set.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ float2 ldcg_f2(const cpx<float>* p) { return __ldcg(reinterpret_cast<const float2*>(p)); }
+
+template <int N, int... Ks>
+__device__ __forceinline__ void load_bitrev_cg(cpx<float> (&v)[N], const cpx<float>* p, long long step,
+                                               std::integer_sequence<int, Ks...>) {
+  ((v[bitrev(Ks, N)] = [](float2 f) { return cpx<float>(f.x, f.y); }(ldcg_f2(p + Ks * step))), ...);
+}
+template <int M, int... Ks>
+__device__ __forceinline__ void load_radix3_cg(cpx<float> (&u)[3][M], const cpx<float>* p, long long step,
+                                               std::integer_sequence<int, Ks...>) {
+  ((u[Ks % 3][bitrev(Ks / 3, M)] = [](float2 f) { return cpx<float>(f.x, f.y); }(ldcg_f2(p + Ks * step))), ...);
+}
+// line_fft with L2-only loads (the line was written by other CTAs of the launch)
+template <int N, bool INV>
+__device__ __forceinline__ void line_fft_cg(const cpx<float>* p, long long step, cpx<float> (&v)[N]) {
+  if constexpr ((N & (N - 1)) == 0) {
+    load_bitrev_cg<N>(v, p, step, std::make_integer_sequence<int, N>{});
+    fft_pow2<float, N, INV>(v);
+  } else {
+    constexpr int M = N / 3;
+    cpx<float> u[3][M];
+    load_radix3_cg<M>(u, p, step, std::make_integer_sequence<int, N>{});
+    fft_radix3<float, M, INV>(u, v);
+  }
+}
+
+template <int N>
+__host__ __device__ constexpr int queue_line_units() {
+  return (N * N * xy_tile<N>() + 255) / 256;
+}
+
+template <int N, bool INV>
+__global__ void __launch_bounds__(256)
+k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer, int n_tiles, int lag,
+                 FftQueue q, int expect, long long spin_limit) {
+  constexpr int TI = xy_tile<N>();
+  constexpr int ZU = queue_line_units<N>();
+  constexpr int U = N + ZU;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(smem_raw);  // [N * N][TI]
+  __shared__ int s_ticket, s_ok;
+  const long long V = (long long)N * N * N;
+  const long long total = (long long)(n_tiles + lag) * U;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_ticket = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
+    __syncthreads();
+    const long long t = s_ticket;
+    if (t < 0 || t >= total) break;
+    const int st = (int)(t / U), j = (int)(t % U);
+    if (j < N) {  // plane unit: x and y lines of z plane j of tile st
+      const int g = st;
+      if (g < n_tiles) {
+        const long long o = g / tiles_per_outer;
+        const int i0 = (g % tiles_per_outer) * TI, z = j;
+        cpx<float>* plane = data + (o * V + (long long)z * N * N) * n_inner + i0;
+        for (int idx = tid; idx < N * N * TI; idx += 256) {
+          const int site = idx / TI, i = idx - site * TI;
+          if (i0 + i < n_inner) {
+            const float2 f = ldcg_f2(plane + (long long)site * n_inner + i);
+            tile[idx] = cpx<float>(f.x, f.y);
+          } else {
+            tile[idx] = cpx<float>(0.f, 0.f);
+          }
+        }
+        __syncthreads();
+        for (int li = tid; li < N * TI; li += 256) {  // x lines: (y, i)
+          const int y = li / TI, i = li - y * TI;
+          cpx<float> v[N];
+          line_fft<float, float, N, INV>(tile + (y * N) * TI + i, TI, v);
+#pragma unroll
+          for (int k = 0; k < N; k++) tile[(y * N + k) * TI + i] = v[k];
+        }
+        __syncthreads();
+        for (int li = tid; li < N * TI; li += 256) {  // y lines: (x, i), to global memory
+          const int x = li / TI, i = li - x * TI;
+          cpx<float> v[N];
+          line_fft<float, float, N, INV>(tile + x * TI + i, N * TI, v);
+          if (i0 + i < n_inner) {
+#pragma unroll
+            for (int k = 0; k < N; k++) plane[(long long)(x + N * k) * n_inner + i] = v[k];
+          }
+        }
+        __syncthreads();  // the plane is written ...
+        if (tid == 0) {   // ... and released to the line units of the tile
+          __threadfence();
+          atomicAdd(q.words + 1 + g, 1);
+        }
+      }
+    } else {  // line unit j - N: z lines of tile st - lag
+      const int g = st - lag;
+      if (g >= 0) {
+        if (tid == 0) {
+          int ok = 1;
+          long long polls = 0;
+          while (ld_acquire_gpu(q.words + 1 + g) < expect) {
+            if (++polls > spin_limit) {
+              atomicExch(q.err, 1);
+              ok = 0;
+              break;
+            }
+            __nanosleep(256);
+          }
+          s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const long long o = g / tiles_per_outer;
+        const int i0 = (g % tiles_per_outer) * TI;
+        const int pr = (j - N) * 256 + tid;  // (line, column) pair, column fastest
+        const int line = pr / TI, i = pr - line * TI;
+        if (line < N * N && i0 + i < n_inner) {
+          cpx<float>* p = data + (o * V + line) * n_inner + i0 + i;
+          cpx<float> v[N];
+          line_fft_cg<N, INV>(p, (long long)N * N * n_inner, v);
+#pragma unroll
+          for (int k = 0; k < N; k++) p[(long long)k * N * N * n_inner] = v[k];
+        }
+      }
+    }
+    __syncthreads();  // s_ticket and the tile are reused
+  }
+}
+
+template <int N>
+static cudaError_t fft_site_queue_n(void* data, int n_outer, int n_inner, const FftQueue& q, int expect,
+                                    long long spin_limit, cudaStream_t st) {
+  constexpr int TI = xy_tile<N>();
+  constexpr int U = N + queue_line_units<N>();
+  const size_t sm = sizeof(cpx<float>) * N * N * TI;
+  static int granted[64] = {0};
+  static int resident[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  e = ensure_smem(k_fft_site_queue<N, false>, sm, granted);
+  if (e != cudaSuccess) return e;
+  if (resident[dev] == 0) {  // CTAs resident on the device (queried once per device)
+    int n = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fft_site_queue<N, false>, 256, sm);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    resident[dev] = std::max(1, n) * std::max(1, sms);
+  }
+  const int tiles_per_outer = (n_inner + TI - 1) / TI;
+  const int n_tiles = n_outer * tiles_per_outer;
+  // lag: about 1.5 x the CTAs in flight, in steps, so that a tile's planes
+  // are done before its line units are taken
+  const int lag = std::max(1, (3 * resident[dev] / 2 + U - 1) / U);
+  const long long units = (long long)(n_tiles + lag) * U;
+  const int grid = (int)std::min<long long>(resident[dev], units);
+  e = cudaMemsetAsync(q.words, 0, sizeof(int) * (1 + (size_t)n_tiles), st);  // ticket counter, done[]
+  if (e != cudaSuccess) return e;
+  k_fft_site_queue<N, false><<<grid, 256, sm, st>>>((cpx<float>*)data, n_inner, tiles_per_outer, n_tiles, lag, q,
+                                                    expect < 0 ? N : expect, spin_limit);
+  return cudaGetLastError();
+}
+
+int fft_queue_ints(int L, int n_outer, int n_inner) {
+  const int ti = L <= 16 ? 32 : (L == 24 ? 16 : (L == 32 ? 8 : 4));
+  return 1 + n_outer * ((n_inner + ti - 1) / ti);
+}
+
+bool fft_queue_supported(int L) { return L == 2 || L == 4 || L == 8 || L == 16 || L == 24 || L == 32; }
+
+cudaError_t launch_fft_forward_queue(void* blk, int L, int n_slots, int n_rows, const FftQueue& q, int expect,
+                                     long long spin_limit, cudaStream_t st) {
+  switch (L) {
+    case 2: return fft_site_queue_n<2>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    case 4: return fft_site_queue_n<4>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    case 8: return fft_site_queue_n<8>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    case 16: return fft_site_queue_n<16>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    case 24: return fft_site_queue_n<24>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    case 32: return fft_site_queue_n<32>(blk, n_slots, n_rows, q, expect, spin_limit, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename S, typename R, int MODE, typename O = S>
 static cudaError_t fft_dispatch(const void* in, void* out, int L, long long n_outer, int n_inner, int axis, bool inv,
                                 const double* scale, cudaStream_t st, O* sum = nullptr) {

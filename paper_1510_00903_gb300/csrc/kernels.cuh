@@ -102,6 +102,21 @@ cudaError_t launch_fft_forward_df(const void* blk_site, void* blk_field, int L, 
 // Forward 3-D FFT in place on site-major blocks blk[slots][V][n_rows] (lanes
 // over the contiguous row index); output is q-major.
 cudaError_t launch_fft_forward_site(void* blk, int L, int n_slots, int n_rows, bool fp64, cudaStream_t st);
+// The forward FP32 transform of launch_fft_forward_site (L <= 32) as one
+// persistent launch over a device work queue (fft.cu): words = [ticket
+// counter, done[tiles]] (fft_queue_ints(L, n_slots, n_rows) ints, zeroed by the
+// launch), err a sticky word the kernel sets to 1 when a bounded wait gives
+// up (after spin_limit polls); expect < 0 for the plane count the waits need
+// (a larger value makes them run out: the timeout self-test).
+struct FftQueue {
+  int* words;
+  int* err;
+};
+int fft_queue_ints(int L, int n_outer, int n_inner);
+bool fft_queue_supported(int L);
+constexpr long long kFftSpinLimit = 1LL << 22;  // polls of about 0.3 us: about a second
+cudaError_t launch_fft_forward_queue(void* blk, int L, int n_slots, int n_rows, const FftQueue& q, int expect,
+                                     long long spin_limit, cudaStream_t st);
 // Inverse 3-D FFT of q-major ct[V][n_ch*16] (complex128, x and y in place),
 // the z pass writing out[n_ch][V][16] multiplied by scale[ch].
 // ct_f32: ct holds complex64 values (then the transform computes in FP32).

@@ -133,8 +133,9 @@ def test_tuning_defaults_validation_and_autotune_state():
 def test_launch_counts_follow_the_path():
     """Kernel launches per call: the tensor-core path runs two contraction
     kernels, the fused CUDA-core path one, the FP64 path two (products and
-    Wick sums); the q-major layout fuses the x and y FFT passes up to L = 32."""
-    want = {bbc.BBC_MIXED_FP32: (2, 3, 5), bbc.BBC_MIXED_TF32: (2, 3, 5), bbc.BBC_MIXED_BF16: (2, 4, 4),
+    Wick sums); the q-major layout fuses the x and y FFT passes up to L = 32
+    and runs the forward transform there as one queue-driven launch."""
+    want = {bbc.BBC_MIXED_FP32: (2, 2, 5), bbc.BBC_MIXED_TF32: (2, 2, 5), bbc.BBC_MIXED_BF16: (2, 3, 4),
             bbc.BBC_FP64: (2, 4, 6), bbc.BBC_DF64: (2, 4, 6)}
     for prec, (load, build, contract) in want.items():
         c = bbc.bbc_create(16, 4, 0, 0.3, 0.4, prec, list(range(52)))
@@ -142,6 +143,26 @@ def test_launch_counts_follow_the_path():
             assert bbc.bbc_launch_counts(c) == {"load": load, "build": build, "contract": contract}, prec
         finally:
             bbc.bbc_destroy(c)
+    # L = 48: three forward passes of the q-major layout, no queue-driven launch
+    c = bbc.bbc_create(48, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, list(range(52)))
+    try:
+        assert bbc.bbc_launch_counts(c) == {"load": 2, "build": 4, "contract": 6}
+    finally:
+        bbc.bbc_destroy(c)
+
+
+def test_bounded_wait_entry_points_without_a_workspace():
+    """bbc_device_status is OK before anything ran; the bounded-wait self-test
+    checks its limit (EINVAL) and needs a workspace (ESTATE), with no CUDA call."""
+    c = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_MIXED_FP32, list(range(52)))
+    try:
+        bbc.bbc_device_status(c)
+        assert bbc.bbc_check_bounded_wait(c, 0) == bbc.BBC_EINVAL
+        assert bbc.bbc_check_bounded_wait(c, (1 << 22) + 1) == bbc.BBC_EINVAL
+        assert bbc.bbc_check_bounded_wait(c, 1000) == bbc.BBC_ESTATE
+        assert "workspace" in bbc.lib().bbc_last_error(c).decode()
+    finally:
+        bbc.bbc_destroy(c)
 
 
 def test_lower_components_plan_and_errors():
