@@ -325,8 +325,41 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
     }
   }
   __syncthreads();
-  if (!live) return;
   const R hs = (R)0.86602540378443864676;  // sqrt(3)/2
+  if (MODE == FFT_SITE2FIELD) {
+    // The x lines of consecutive inner columns land in different output rows:
+    // the radix-3 results go back into the line's own shared-memory slots
+    // (column k2 of line ls is read and written by one thread only), and the
+    // CTA then stores each line's N points as one contiguous run, consecutive
+    // threads on consecutive points.
+    if (live) {
+      for (int k2 = j; k2 < M; k2 += 3) {
+        const cpx<R> t0 = sh[ls][0][k2], t1 = sh[ls][1][k2], t2 = sh[ls][2][k2];
+        const cpx<R> sm = t1 + t2, d = t1 - t2;
+        const cpx<R> m(t0.re - (R)0.5 * sm.re, t0.im - (R)0.5 * sm.im);
+        const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);
+        sh[ls][0][k2] = t0 + sm;  // X[k2 + c M] at sh[ls][c][k2]
+        sh[ls][1][k2] = m + r;
+        sh[ls][2][k2] = m - r;
+      }
+    }
+    __syncthreads();
+    const long long g0 = blockIdx.x * (long long)kSplitLines;
+    for (int e = threadIdx.x; e < kSplitLines * N; e += 3 * kSplitLines) {
+      const int l = e / N, k = e - l * N;
+      const long long gl = g0 + l;
+      if (gl >= n_outer * lines * n_inner) break;  // e grows with l: the rest is past the end too
+      const int inn = (int)(gl % n_inner);
+      const long long rst = gl / n_inner;
+      const int ln = (int)(rst % lines);
+      const long long oo = rst / lines;
+      int b = 0, sd = 0;
+      line_base(N, axis, ln, b, sd);
+      out[(oo * n_inner + inn) * V + b + (long long)k * sd] = cpx<O>(sh[l][k / M][k % M]);
+    }
+    return;
+  }
+  if (!live) return;
   for (int k2 = j; k2 < M; k2 += 3) {
     const cpx<R> t0 = sh[ls][0][k2], t1 = sh[ls][1][k2], t2 = sh[ls][2][k2];
     const cpx<R> sm = t1 + t2, d = t1 - t2;
@@ -336,9 +369,7 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const int k = k2 + c * M;
-      if (MODE == FFT_SITE2FIELD) {
-        out[(o * n_inner + inner) * V + base + (long long)k * stride] = cpx<O>(x[c]);
-      } else if (MODE == FFT_FIELD) {
+      if (MODE == FFT_FIELD) {
         out[o * V + base + (long long)k * stride] = cpx<O>(x[c]);
       } else if (MODE == FFT_FIELD_SUM) {
         const cpx<O> w(x[c]);

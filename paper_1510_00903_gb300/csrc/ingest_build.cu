@@ -9,20 +9,43 @@
 namespace bbc {
 
 // ------------------------------------------------------------------ ingest
+// Largest |x| of the slice (a NaN counts as infinite: a max would drop it),
+// as the bits of a non-negative double, which order like the values.  The
+// scan runs on the bit patterns in integer arithmetic: |x| is x with the sign
+// bit cleared, and every NaN pattern lies above the infinite one (clamped to
+// it); complex64 input is widened to double bits once per warp.
 __global__ void k_absmax(const void* __restrict__ src, int dtype, long long n_real,
                          unsigned long long* amax) {
-  double m = 0.0;
+  unsigned long long m = 0;
   long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
-    double x = dtype == 0 ? ((const double*)src)[i] : (double)((const float*)src)[i];
-    const double a = fabs(x);
-    m = fmax(m, a == a ? a : (double)INFINITY);  // a NaN counts as infinite (fmax would drop it)
+  if (dtype == 0) {
+    const unsigned long long* x = (const unsigned long long*)src;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
+      const unsigned long long a = x[i] & 0x7fffffffffffffffull;
+      m = a > m ? a : m;
+    }
+    m = m > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : m;
+  } else {
+    const unsigned* x = (const unsigned*)src;
+    unsigned mf = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
+      const unsigned a = x[i] & 0x7fffffffu;
+      mf = a > mf ? a : mf;
+    }
+    mf = mf > 0x7f800000u ? 0x7f800000u : mf;
+    m = (unsigned long long)__double_as_longlong((double)__uint_as_float(mf));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(amax, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, m);
 }
 
+// x * 2^-k with k = ilogb(max |x|) + 1, an exact rescaling into [-1, 1).
+// complex64 input into FP32 or double-float storage scales in FP32 (exact
+// for every result in the normal range; the double-float low word is 0).
 template <typename R>
 __global__ void k_convert(const void* __restrict__ src, int dtype, long long n_real,
                           const unsigned long long* __restrict__ amax, int* kexp, R* __restrict__ dst) {
@@ -30,6 +53,16 @@ __global__ void k_convert(const void* __restrict__ src, int dtype, long long n_r
   int k = (m > 0.0 && m <= 1.7976931348623157e308) ? ilogb(m) + 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) *kexp = k;
   long long stride = (long long)gridDim.x * blockDim.x;
+  if constexpr (!std::is_same<R, double>::value) {
+    if (dtype == 1) {
+      for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
+        const float y = ldexpf(((const float*)src)[i], -k);
+        if constexpr (std::is_same<R, dfr>::value) dst[i] = dfr(y, 0.f);
+        else dst[i] = y;
+      }
+      return;
+    }
+  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_real; i += stride) {
     double x = dtype == 0 ? ((const double*)src)[i] : (double)((const float*)src)[i];
     dst[i] = (R)ldexp(x, -k);
@@ -132,12 +165,12 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
     const int r0 = g.first[gi], r1 = r0 + g.rows[gi];
     cpx<R>* out = blk + ((size_t)slot * V + site0) * n_out;
     for (int r = r0 + tid; r < r1; r += THREADS) {
-      cpx<R> acc[SITES];
-#pragma unroll
-      for (int s = 0; s < SITES; s++) acc[s] = cpx<R>(0, 0);
       // the warp's 32 rows are one chunk: entry k of all of them is 128 contiguous bytes
       const int2 ch = __ldg(ell_chunk + g.chunk_first[gi] + ((r - r0) >> 5));
       const uint32_t* ep = ell + ch.x + ((r - r0) & 31);
+      cpx<R> acc[SITES];
+#pragma unroll
+      for (int s = 0; s < SITES; s++) acc[s] = cpx<R>(0, 0);
       for (int k = 0; k < ch.y; k++) {
         const uint32_t e = __ldg(ep + 32 * k);  // padding: weight 0 at position 0
         // FP64 is bound by its narrow pipe: skip the padding's multiply-adds
