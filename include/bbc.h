@@ -255,15 +255,21 @@ typedef struct {
 } bbc_batch_item;
 
 /* Batch entry point (many slices, sources, gauge samples and uneven
- * lattices in one call): runs items[0 .. n_items) in order on cuda_stream --
- * for each, both propagators into slot 0 of its context, block build,
- * contraction into out_dev -- with every launch and copy on cuda_stream (the
- * contexts' own streams are not used; they are restored before returning).
- * Capturing cuda_stream into a CUDA graph around this call records the whole
- * batch as one graph.  Contexts may share a workspace (their work is ordered
- * on the one stream).  Asynchronous unless a context has numeric checks on.
- * Errors: the status of the first failing item, whose index goes to
- * *failed_item (if not NULL); EINVAL for a null or empty batch. */
+ * lattices in one call): runs items[0 .. n_items) in order on cuda_stream.
+ * Consecutive items of one context form waves of up to its slot count
+ * (bbc_set_workspace's slices): the propagators of the wave's items go into
+ * slots 0 .. k-1, one block build and one forward FFT run over the k slots
+ * (in the mixed precisions at L <= 32 the FFT is one queue-driven launch over
+ * every row tile of the k slices), then the k contractions write each item's
+ * out_dev.  Every launch and copy is on cuda_stream (the contexts' own
+ * streams are not used; they are restored before returning).  Capturing
+ * cuda_stream into a CUDA graph around this call records the whole batch as
+ * one graph.  Contexts may share a workspace (their work is ordered on the
+ * one stream).  Asynchronous unless a context has numeric checks on.
+ * Errors: the status of the first failing call; *failed_item (if not NULL)
+ * gets the item whose load or contraction failed, or the first item of the
+ * wave whose build failed (a batch resumes from there); EINVAL for a null or
+ * empty batch. */
 bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_stream, int* failed_item);
 
 /* Numeric checks (off by default).  BBC_CHECK_INPUT: bbc_load_propagator

@@ -631,10 +631,13 @@ class LatticeBatch:
     of lattice i.  ``run()`` computes every slice of every source; the
     correlators of a slice land in ``outputs[i]`` ([n_channels, V, 16]),
     overwritten slice after slice (a streaming consumer reads them there).
+    Each context holds ``slices`` slots: bbc_batch_run takes a source's slices
+    in waves of that many (one block build and one forward FFT per wave).
     """
 
     def __init__(self, lattices, inputs, n_sources: int = 4, channels=CHANNELS_52,
-                 precision: int = BBC_MIXED_FP32, m_ud: float = 0.3, m_s: float = 0.4, device=None):
+                 precision: int = BBC_MIXED_FP32, m_ud: float = 0.3, m_s: float = 0.4, device=None,
+                 slices: int = 4):
         import torch
         self.torch = torch
         dev = torch.device(device or "cuda")
@@ -649,7 +652,7 @@ class LatticeBatch:
             ws = None
             for k in range(n_sources):
                 c = Correlators(L, T, (k * T) // n_sources, m_ud, m_s, channels=channels, precision=precision,
-                                device=dev, stream=self.stream, workspace=ws)
+                                slices=min(slices, T), device=dev, stream=self.stream, workspace=ws)
                 ws = c.workspace
                 per.append(c)
             self.cors.append(per)

@@ -852,24 +852,41 @@ bbc_status bbc_batch_run(const bbc_batch_item* items, int n_items, void* cuda_st
   if (failed_item) *failed_item = -1;
   if (!items || n_items < 1) return fail(nullptr, BBC_EINVAL, "empty batch");
   const cudaStream_t st = (cudaStream_t)cuda_stream;
-  for (int i = 0; i < n_items; i++) {
-    const bbc_batch_item& it = items[i];
-    bbc_ctx* c = it.ctx;
+  for (int i0 = 0; i0 < n_items;) {
+    bbc_ctx* c = items[i0].ctx;
     if (!c) {
-      if (failed_item) *failed_item = i;
-      return fail(nullptr, BBC_EINVAL, "batch item " + std::to_string(i) + " has no context");
+      if (failed_item) *failed_item = i0;
+      return fail(nullptr, BBC_EINVAL, "batch item " + std::to_string(i0) + " has no context");
     }
+    // a wave: the consecutive items of this context, up to its slot count
+    const int cap = std::max(1, c->slots);
+    int n = 1;
+    while (n < cap && i0 + n < n_items && items[i0 + n].ctx == c) n++;
     const cudaStream_t own = c->stream;
     c->stream = st;
-    bbc_status s = bbc_load_propagator(c, BBC_LIGHT, 0, it.t, it.S_light, it.dtype, it.on_device);
-    if (s == BBC_OK) s = bbc_load_propagator(c, BBC_STRANGE, 0, it.t, it.S_strange, it.dtype, it.on_device);
-    if (s == BBC_OK) s = bbc_build_blocks(c, 1);
-    if (s == BBC_OK) s = bbc_contract(c, 0, it.out_dev, it.normalised);
+    bbc_status s = BBC_OK;
+    int bad = i0;
+    for (int j = 0; j < n && s == BBC_OK; j++) {
+      const bbc_batch_item& it = items[i0 + j];
+      bad = i0 + j;
+      s = bbc_load_propagator(c, BBC_LIGHT, j, it.t, it.S_light, it.dtype, it.on_device);
+      if (s == BBC_OK) s = bbc_load_propagator(c, BBC_STRANGE, j, it.t, it.S_strange, it.dtype, it.on_device);
+    }
+    if (s == BBC_OK) {
+      bad = i0;
+      s = bbc_build_blocks(c, n);  // one block build and one forward FFT over the wave's slots
+    }
+    for (int j = 0; j < n && s == BBC_OK; j++) {
+      const bbc_batch_item& it = items[i0 + j];
+      bad = i0 + j;
+      s = bbc_contract(c, j, it.out_dev, it.normalised);
+    }
     c->stream = own;
     if (s != BBC_OK) {
-      if (failed_item) *failed_item = i;
+      if (failed_item) *failed_item = bad;
       return s;
     }
+    i0 += n;
   }
   return BBC_OK;
 }

@@ -462,16 +462,19 @@ static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner
 // columns are cut into row tiles g of TI columns of one outer index; tile g
 // has N plane units (the x and y lines of one z plane, staged in shared
 // memory as in k_fft_xy_site) and ZU line units (its z lines, 256 (line,
-// column) pairs each).  A CTA takes the next ticket from a global counter;
-// tickets run in steps of N + ZU, step s holding the plane units of tile s
-// and the line units of tile s - lag, so a tile's z lines are read back from
-// L2 soon after its planes were written (one HBM round trip for the three
-// passes instead of two).  A line unit waits until the N plane units of its
-// tile have signalled (q.words = [ticket counter, done[n_tiles]], zeroed
-// before the launch).  The wait ends: every ticket below its own was taken
-// by a CTA that is running, and plane units wait on nothing.  It is bounded
-// all the same: after spin_limit polls the CTA sets the sticky word *q.err
-// (cleared only by the host), and no CTA takes a ticket while it is set.
+// column) pairs each).  A CTA takes tickets from a global counter; tickets
+// run in steps of N + ZU, step s holding the plane units of tile s and the
+// line units of tile s - lag, so a tile's z lines are read back from L2 soon
+// after its planes were written (one HBM round trip for the three passes
+// instead of two).  A CTA holds the ticket it runs and the next one, whose
+// plane it copies into its second buffer (cp.async) meanwhile.  A line unit
+// waits until the N plane units of its tile have signalled (q.words =
+// [ticket counter, done[n_tiles]], zeroed before the launch).  The wait
+// ends: it points at smaller tickets only, all taken by running CTAs, and
+// the smallest unfinished ticket is always a running unit whose own
+// dependencies are done.  It is bounded all the same: after spin_limit polls
+// the CTA sets the sticky word *q.err (cleared only by the host), and no CTA
+// takes a ticket while it is set.
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -503,45 +506,77 @@ __device__ __forceinline__ void line_fft_cg(const cpx<float>* p, long long step,
   }
 }
 
+// Row-tile width of the queue-driven transform: two plane buffers of
+// N * N * QT complex64 values fit three CTAs per SM.
+template <int N>
+__host__ __device__ constexpr int queue_tile() {
+  return N <= 16 ? 16 : (N == 24 ? 8 : 4);
+}
 template <int N>
 __host__ __device__ constexpr int queue_line_units() {
-  return (N * N * xy_tile<N>() + 255) / 256;
+  return (N * N * queue_tile<N>() + 255) / 256;
 }
 
 template <int N, bool INV>
 __global__ void __launch_bounds__(256)
 k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer, int n_tiles, int lag,
                  FftQueue q, int expect, long long spin_limit) {
-  constexpr int TI = xy_tile<N>();
+  constexpr int TI = queue_tile<N>();
   constexpr int ZU = queue_line_units<N>();
   constexpr int U = N + ZU;
+  constexpr int PLANE = N * N * TI;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<float>* tile = reinterpret_cast<cpx<float>*>(smem_raw);  // [N * N][TI]
-  __shared__ int s_ticket, s_ok;
+  cpx<float>* bufs = reinterpret_cast<cpx<float>*>(smem_raw);  // [2][N * N][TI]
+  __shared__ int s_next, s_ok;
   const long long V = (long long)N * N * N;
   const long long total = (long long)(n_tiles + lag) * U;
   const int tid = threadIdx.x;
-  for (;;) {
-    if (tid == 0) s_ticket = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
-    __syncthreads();
-    const long long t = s_ticket;
-    if (t < 0 || t >= total) break;
+  // plane unit of ticket t, or -1
+  auto plane_tile = [&](long long t) -> int {
+    if (t < 0 || t >= total) return -1;
     const int st = (int)(t / U), j = (int)(t % U);
+    return (j < N && st < n_tiles) ? st : -1;
+  };
+  // asynchronous copy of a plane unit's N x N x TI values into buffer b
+  // (columns past n_inner are zeroed with plain stores: the buffer is idle)
+  auto fetch_plane = [&](long long t, cpx<float>* buf) {
+    const int g = plane_tile(t);
+    if (g < 0) return;
+    const long long o = g / tiles_per_outer;
+    const int i0 = (g % tiles_per_outer) * TI, z = (int)(t % U);
+    const cpx<float>* plane = data + (o * V + (long long)z * N * N) * n_inner + i0;
+    for (int idx = tid; idx < PLANE; idx += 256) {
+      const int site = idx / TI, i = idx - site * TI;
+      if (i0 + i < n_inner) cp_async8(buf + idx, plane + (long long)site * n_inner + i);
+      else buf[idx] = cpx<float>(0.f, 0.f);
+    }
+  };
+  // Each CTA holds two tickets: the unit it runs and the next one, whose
+  // plane is on its way meanwhile.  Waits still point only at smaller
+  // tickets, so the smallest unfinished ticket always belongs to a unit that
+  // is running and whose own dependencies are complete.
+  if (tid == 0) s_next = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
+  __syncthreads();
+  long long cur = s_next;
+  int b = 0;
+  fetch_plane(cur, bufs);
+  cp_async_commit();
+  __syncthreads();
+  while (cur >= 0 && cur < total) {
+    if (tid == 0) s_next = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
+    __syncthreads();
+    const long long nxt = s_next;
+    fetch_plane(nxt, bufs + (b ^ 1) * PLANE);
+    cp_async_commit();
+    const int st = (int)(cur / U), j = (int)(cur % U);
     if (j < N) {  // plane unit: x and y lines of z plane j of tile st
       const int g = st;
       if (g < n_tiles) {
         const long long o = g / tiles_per_outer;
         const int i0 = (g % tiles_per_outer) * TI, z = j;
+        cpx<float>* tile = bufs + b * PLANE;
         cpx<float>* plane = data + (o * V + (long long)z * N * N) * n_inner + i0;
-        for (int idx = tid; idx < N * N * TI; idx += 256) {
-          const int site = idx / TI, i = idx - site * TI;
-          if (i0 + i < n_inner) {
-            const float2 f = ldcg_f2(plane + (long long)site * n_inner + i);
-            tile[idx] = cpx<float>(f.x, f.y);
-          } else {
-            tile[idx] = cpx<float>(0.f, 0.f);
-          }
-        }
+        cp_async_wait_group<1>();  // this unit's plane has landed (the next one may still fly)
         __syncthreads();
         for (int li = tid; li < N * TI; li += 256) {  // x lines: (y, i)
           const int y = li / TI, i = li - y * TI;
@@ -597,16 +632,19 @@ k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer
         }
       }
     }
-    __syncthreads();  // s_ticket and the tile are reused
+    __syncthreads();  // s_next and the current buffer are reused
+    cur = nxt;
+    b ^= 1;
   }
+  cp_async_wait_all();  // no copy outlives the CTA
 }
 
 template <int N>
 static cudaError_t fft_site_queue_n(void* data, int n_outer, int n_inner, const FftQueue& q, int expect,
                                     long long spin_limit, cudaStream_t st) {
-  constexpr int TI = xy_tile<N>();
+  constexpr int TI = queue_tile<N>();
   constexpr int U = N + queue_line_units<N>();
-  const size_t sm = sizeof(cpx<float>) * N * N * TI;
+  const size_t sm = 2 * sizeof(cpx<float>) * N * N * TI;
   static int granted[64] = {0};
   static int resident[64] = {0};
   int dev = 0;
@@ -637,7 +675,7 @@ static cudaError_t fft_site_queue_n(void* data, int n_outer, int n_inner, const 
 }
 
 int fft_queue_ints(int L, int n_outer, int n_inner) {
-  const int ti = L <= 16 ? 32 : (L == 24 ? 16 : (L == 32 ? 8 : 4));
+  const int ti = L <= 16 ? 16 : (L == 24 ? 8 : 4);  // queue_tile
   return 1 + n_outer * ((n_inner + ti - 1) / ti);
 }
 
