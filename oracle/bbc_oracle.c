@@ -17,7 +17,12 @@
  * The decuplet Omega- (Sec. 4 footnote: the same operator form with
  * Gamma1 = C gamma_l, Gamma2 = 1, spatial vector index l) is taken as
  * eta_l eps (s C gamma_l s) s with eta = (i, 1, -i) for l = x, y, z, the
- * phase that makes its tensor real like the octet ones.
+ * phase that makes its tensor real like the octet ones.  The other decuplet
+ * baryons take the same form with the flavour-symmetric combinations (a
+ * reading: the footnote names only the form): Delta++_l = eta_l eps
+ * (u C gamma_l u) u, Sigma*+_l = eta_l [eps (u C gamma_l u) s + 2 eps
+ * (u C gamma_l s) u] / sqrt3, Xi*0_l = eta_l [eps (s C gamma_l s) u + 2 eps
+ * (s C gamma_l u) s] / sqrt3.
  * The six-quark matrix element is the Wick determinant
  *
  *   < Q1..Q6 Qbar'6..Qbar'1 > = det_{ij} [ delta(f_i, g_j) S_{f_i}(x_i)[xi_i, eta_j] ]
@@ -77,7 +82,8 @@ typedef struct {
   int gi[3], gj[3], dk[3];
 } baryon_t;
 
-enum { B_P, B_N, B_SP, B_SM, B_S0, B_L, B_X0, B_XM, B_OX, B_OY, B_OZ, NBARYON };
+enum { B_P, B_N, B_SP, B_SM, B_S0, B_L, B_X0, B_XM, B_OX, B_OY, B_OZ, B_DX, B_DY, B_DZ, B_SSX, B_SSY, B_SSZ,
+       B_XSX, B_XSY, B_XSZ, NBARYON };
 
 static baryon_t g_bar[NBARYON];
 
@@ -87,9 +93,12 @@ static baryon_t g_bar[NBARYON];
  * (pp, nn, S+S+, S-S-, X0X0, X-X-, pS+, nS-, each onto itself), then the
  * decuplet channels of the Sec. 4 footnote: Omega_l1 Omega_l2 <- Omega_l3
  * Omega_l4 at id 64 + 27 l1 + 9 l2 + 3 l3 + l4 and p Omega_l <- p Omega_l'
- * at id 145 + 3 l + l' (l = 0, 1, 2 for x, y, z). */
+ * at id 145 + 3 l + l' (l = 0, 1, 2 for x, y, z); the same 81 vector
+ * combinations of Delta++ Delta++ at 154 + ..., Sigma*+ Sigma*+ at 235 + ...
+ * and Xi*0 Xi*0 at 316 + ..., and p Delta++_l <- p Delta++_l' at
+ * 397 + 3 l + l'. */
 typedef struct { int b[4]; const char* name; } channel_t;
-#define NCHAN_ALL 154
+#define NCHAN_ALL 406
 static channel_t g_chan[NCHAN_ALL];
 static int g_nchan = 0;
 
@@ -182,6 +191,27 @@ static void init_tables(void) {
       add_term(ids[l], 1.0, 0, 1, 2);
     }
   }
+  /* Delta++_l = eta_l eps (u C gamma_l u) u; Sigma*+_l on the string (u, u, s):
+   * [eps (q0 G q1) q2 + 2 eps (q0 G q2) q1] / sqrt3; Xi*0_l the same on (s, s, u) */
+  {
+    const double r3 = 1.0 / sqrt(3.0);
+    const char* dn[3] = {"Delta++_x", "Delta++_y", "Delta++_z"};
+    const char* sn[3] = {"Sigma*+_x", "Sigma*+_y", "Sigma*+_z"};
+    const char* xn[3] = {"Xi*0_x", "Xi*0_y", "Xi*0_z"};
+    for (int l = 0; l < 3; l++) {
+      set_bar(B_DX + l, dn[l], FL_U, FL_U, FL_U);
+      g_bar[B_DX + l].gam = 1 + l;
+      add_term(B_DX + l, 1.0, 0, 1, 2);
+      set_bar(B_SSX + l, sn[l], FL_U, FL_U, FL_S);
+      g_bar[B_SSX + l].gam = 1 + l;
+      add_term(B_SSX + l, r3, 0, 1, 2);
+      add_term(B_SSX + l, 2.0 * r3, 0, 2, 1);
+      set_bar(B_XSX + l, xn[l], FL_S, FL_S, FL_U);
+      g_bar[B_XSX + l].gam = 1 + l;
+      add_term(B_XSX + l, r3, 0, 1, 2);
+      add_term(B_XSX + l, 2.0 * r3, 0, 2, 1);
+    }
+  }
 
   /* 52 channels in printed order */
   g_nchan = 0;
@@ -230,6 +260,17 @@ static void init_tables(void) {
           for (int l4 = 0; l4 < 3; l4++) add_chan(om[l1], om[l2], om[l3], om[l4]);
     for (int l = 0; l < 3; l++)
       for (int m = 0; m < 3; m++) add_chan(B_P, om[l], B_P, om[m]);
+  }
+  /* ids 154..405: Delta++, Sigma*+, Xi*0 pairs (81 vector combinations each), p Delta++ */
+  {
+    const int base[3] = {B_DX, B_SSX, B_XSX};
+    for (int f = 0; f < 3; f++)
+      for (int l1 = 0; l1 < 3; l1++)
+        for (int l2 = 0; l2 < 3; l2++)
+          for (int l3 = 0; l3 < 3; l3++)
+            for (int l4 = 0; l4 < 3; l4++) add_chan(base[f] + l1, base[f] + l2, base[f] + l3, base[f] + l4);
+    for (int l = 0; l < 3; l++)
+      for (int m = 0; m < 3; m++) add_chan(B_P, B_DX + l, B_P, B_DX + m);
   }
   g_init = 1;
 }
@@ -430,7 +471,9 @@ static int correlator_impl(int L, const cplx* Su, const cplx* Sd, const cplx* Ss
  *   L: spatial extent (V = L^3 sites)
  *   Su, Sd, Ss: propagators [V][12][12] complex128 (Su may equal Sd)
  *   channels[n_ch]: channel ids (0..51 printed order, 52..55 omitted channels,
- *     56..63 other charge states, 64..144 Omega Omega, 145..153 p Omega)
+ *     56..63 other charge states, 64..144 Omega Omega, 145..153 p Omega,
+ *     154..234 Delta++ Delta++, 235..315 Sigma*+ Sigma*+, 316..396 Xi*0 Xi*0,
+ *     397..405 p Delta++)
  *   r_list[n_r]: output sites r (site index), or n_r <= 0 for all V sites
  *   out: [n_ch][n_r or V][16] complex128, spin s = a + 2(b + 2(a' + 2 b'))
  * Returns 0, or -1 on a bad argument, -2 on allocation failure.

@@ -22,7 +22,8 @@ _SRC = os.path.join(_HERE, "bbc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libbbc_oracle.so")
 _lib = None
 
-BARYONS = ["p", "n", "Sigma+", "Sigma-", "Sigma0", "Lambda", "Xi0", "Xi-", "Omega_x", "Omega_y", "Omega_z"]
+BARYONS = ["p", "n", "Sigma+", "Sigma-", "Sigma0", "Lambda", "Xi0", "Xi-", "Omega_x", "Omega_y", "Omega_z",
+           "Delta++_x", "Delta++_y", "Delta++_z", "Sigma*+_x", "Sigma*+_y", "Sigma*+_z", "Xi*0_x", "Xi*0_y", "Xi*0_z"]
 
 
 def build(force: bool = False) -> str:
@@ -116,6 +117,20 @@ def p_omega_channel(l: int, lp: int) -> int:
     return 145 + 3 * l + lp
 
 
+#: first id of the 81 vector combinations of each decuplet pair family
+DECUPLET_PAIR_BASE = {"Omega": 64, "Delta++": 154, "Sigma*+": 235, "Xi*0": 316}
+
+
+def decuplet_channel(family: str, l1: int, l2: int, l3: int, l4: int) -> int:
+    """Id of D_l1 D_l2 <- D_l3 D_l4 for D in Omega, Delta++, Sigma*+, Xi*0."""
+    return DECUPLET_PAIR_BASE[family] + 27 * l1 + 9 * l2 + 3 * l3 + l4
+
+
+def p_delta_channel(l: int, lp: int) -> int:
+    """Id of p Delta++_l <- p Delta++_l'."""
+    return 397 + 3 * l + lp
+
+
 def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
                r_list=None, lower: bool = False) -> np.ndarray:
     """Raw correlators of one time slice: [n_ch, n_r (or V), 16] complex128.
@@ -147,7 +162,8 @@ def correlator(L: int, Su: np.ndarray, Sd: np.ndarray, Ss: np.ndarray, channels,
 #: masses of the generator (the paper divides by exp(-(m_B1 + m_B2)(t - t0))).
 def baryon_mass(name: str, m_ud: float, m_s: float) -> float:
     n_s = {"p": 0, "n": 0, "Sigma+": 1, "Sigma-": 1, "Sigma0": 1, "Lambda": 1, "Xi0": 2, "Xi-": 2,
-           "Omega_x": 3, "Omega_y": 3, "Omega_z": 3}[name]
+           "Omega_x": 3, "Omega_y": 3, "Omega_z": 3, "Delta++_x": 0, "Delta++_y": 0, "Delta++_z": 0,
+           "Sigma*+_x": 1, "Sigma*+_y": 1, "Sigma*+_z": 1, "Xi*0_x": 2, "Xi*0_y": 2, "Xi*0_z": 2}[name]
     return (3 - n_s) * m_ud + n_s * m_s
 
 

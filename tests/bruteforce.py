@@ -12,8 +12,9 @@ x_1..3 = X + r, x_4..6 = X (Sec. 3 Eq. for the p-Lambda correlator and the
 Wick expansion after it, which is this determinant written out).  The
 operators are the paper's Sec. 2 definitions (p, n: Eq. FieldOperator_N;
 Sigma, Lambda, Xi, X_q: Eqs. FieldOperator_SLXi and FieldOperator_xxx) and
-the decuplet Omega- of the Sec. 4 footnote (Gamma1 = C gamma_l, Gamma2 = 1),
-taken with the phase eta_l = (i, 1, -i) that makes its matrix real.
+the decuplet of the Sec. 4 footnote (Gamma1 = C gamma_l, Gamma2 = 1): Omega-,
+Delta++ and the flavour-symmetric Sigma*+, Xi*0, taken with the phase
+eta_l = (i, 1, -i) that makes the matrix real.
 Cost grows as (#sink entries) x (#source entries) x V: tiny lattices only.
 """
 from __future__ import annotations
@@ -48,8 +49,19 @@ OPS = {
     "Omega_y": ("sss", [(1.0, 0, 1, 2)]),
     "Omega_z": ("sss", [(1.0, 0, 1, 2)]),
 }
+# the other decuplet baryons in the same form (flavour-symmetric combinations):
+# Delta++ = eps (u G u) u; Sigma*+ = [eps (u G u) s + 2 eps (u G s) u] / sqrt3 on
+# the string (u, u, s); Xi*0 the same on (s, s, u)
+_r3 = 1 / np.sqrt(3)
+for _l, _ax in enumerate("xyz"):
+    OPS["Delta++_" + _ax] = ("uuu", [(1.0, 0, 1, 2)])
+    OPS["Sigma*+_" + _ax] = ("uus", [(_r3, 0, 1, 2), (2 * _r3, 0, 2, 1)])
+    OPS["Xi*0_" + _ax] = ("ssu", [(_r3, 0, 1, 2), (2 * _r3, 0, 2, 1)])
 # diquark matrix Gamma1 of each operator (C gamma5 unless listed)
-GAM = {"Omega_x": CGL[0], "Omega_y": CGL[1], "Omega_z": CGL[2]}
+GAM = {}
+for _l, _ax in enumerate("xyz"):
+    for _b in ("Omega_", "Delta++_", "Sigma*+_", "Xi*0_"):
+        GAM[_b + _ax] = CGL[_l]
 
 
 def _eps():

@@ -32,7 +32,7 @@ def close(a, b, tol=1e-12):
 def test_names():
     want = ["p p <- p p", "n n <- n n", "Sigma+ Sigma+ <- Sigma+ Sigma+", "Sigma- Sigma- <- Sigma- Sigma-",
             "Xi0 Xi0 <- Xi0 Xi0", "Xi- Xi- <- Xi- Xi-", "p Sigma+ <- p Sigma+", "n Sigma- <- n Sigma-"]
-    assert orc.n_channels() == 154  # then the decuplet ids 64..153
+    assert orc.n_channels() == 406  # then the decuplet ids 64..405
     assert [orc.channel_name(c) for c in OTHER] == want
 
 

@@ -45,7 +45,7 @@ def neg_site(r, L):
 
 
 def test_channel_table():
-    assert orc.n_channels() == 154
+    assert orc.n_channels() == 406
     for l1, l2, l3, l4 in itertools.product(range(3), repeat=4):
         ch = orc.omega_channel(l1, l2, l3, l4)
         assert orc.channel_baryons(ch) == tuple("Omega_" + AX[l] for l in (l1, l2, l3, l4))
@@ -53,7 +53,7 @@ def test_channel_table():
         assert orc.channel_baryons(orc.p_omega_channel(l, m)) == ("p", "Omega_" + AX[l], "p", "Omega_" + AX[m])
     assert orc.channel_baryons(63) == ("n", "Sigma-", "n", "Sigma-")
     with pytest.raises(ValueError):
-        orc.channel_baryons(154)
+        orc.channel_baryons(406)
 
 
 def test_vector_diquark_matrices():
