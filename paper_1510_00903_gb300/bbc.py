@@ -26,16 +26,36 @@ STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ESTATE", 
 #: the 52 channels of Sec. 4 in printed order (ids 52..55: the 4 omitted
 #: ones, 56..63: other charge states)
 CHANNELS_52 = list(range(52))
-#: decuplet channels (Sec. 4 footnote, Gamma1 = C gamma_l): Omega Omega and p Omega
+#: decuplet channels (Sec. 4 footnote, Gamma1 = C gamma_l): Omega Omega and
+#: p Omega; Delta++ Delta++, Sigma*+ Sigma*+, Xi*0 Xi*0 (81 vector combinations
+#: each) and p Delta++
 OMEGA_OMEGA = list(range(64, 145))
 P_OMEGA = list(range(145, 154))
+DELTA_DELTA = list(range(154, 235))
+SIGMA_STAR_PAIRS = list(range(235, 316))
+XI_STAR_PAIRS = list(range(316, 397))
+P_DELTA = list(range(397, 406))
+N_CHANNEL_IDS = 406
+DECUPLET_PAIR_BASE = {"Omega": 64, "Delta++": 154, "Sigma*+": 235, "Xi*0": 316}
 
 
 def omega_channel(l1: int, l2: int, l3: int, l4: int) -> int:
     """Id of Omega_l1 Omega_l2 <- Omega_l3 Omega_l4 (l = 0, 1, 2 for x, y, z)."""
+    return decuplet_channel("Omega", l1, l2, l3, l4)
+
+
+def decuplet_channel(family: str, l1: int, l2: int, l3: int, l4: int) -> int:
+    """Id of D_l1 D_l2 <- D_l3 D_l4, D one of Omega, Delta++, Sigma*+, Xi*0."""
     if not all(0 <= v < 3 for v in (l1, l2, l3, l4)):
         raise ValueError("vector indices are 0, 1, 2")
-    return 64 + 27 * l1 + 9 * l2 + 3 * l3 + l4
+    return DECUPLET_PAIR_BASE[family] + 27 * l1 + 9 * l2 + 3 * l3 + l4
+
+
+def p_delta_channel(l: int, lp: int) -> int:
+    """Id of p Delta++_l <- p Delta++_l'."""
+    if not (0 <= l < 3 and 0 <= lp < 3):
+        raise ValueError("vector indices are 0, 1, 2")
+    return 397 + 3 * l + lp
 
 
 def p_omega_channel(l: int, lp: int) -> int:

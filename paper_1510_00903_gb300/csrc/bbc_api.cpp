@@ -373,7 +373,7 @@ bbc_status bbc_create_components(bbc_ctx** ctx, const bbc_lattice* lat, bbc_prec
     return fail(nullptr, BBC_EINVAL, "planner failed");
   }
   // FP32 blocks from dense entry tuples when the tables and shared memory allow
-  if (real_kind(prec) == bbc::RK_F32 && c->plan.groups.size() <= 8) {
+  if (real_kind(prec) == bbc::RK_F32 && c->plan.groups.size() <= (size_t)bbc::kMaxBuildGroups) {
     std::string derr;
     try {
       c->dense = bbc::make_dense_build(c->plan, &c->db, &derr) &&

@@ -128,7 +128,8 @@ inline void to_dev_tasks(const PairTask* src, size_t n, const std::vector<int>* 
   }
 }
 
-static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies, "diquark and family tables");
+static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies && kMaxGroups == kMaxBuildGroups,
+              "diquark, family and group tables");
 
 // The block-build groups of a plan as the kernel reads them: row ranges,
 // families per tensor slot, and the diquarks (flavours, Gamma1) those
@@ -136,9 +137,11 @@ static_assert(N_DIQUARK == kMaxDiquarks && N_FAMILY == kMaxFamilies, "diquark an
 inline DevGroups dev_groups(const Plan& p, const DenseBuild* db = nullptr) {
   DevGroups g{};
   if (db) {  // the dense-tuple FP32 build's tables
-    for (size_t i = 0; i < db->tuple_first.size() && i < 9; i++) g.tuple_first[i] = db->tuple_first[i];
-    for (size_t i = 0; i < db->stride.size() && i < 8; i++) g.stride[i] = db->stride[i];
-    for (size_t i = 0; i < db->chunk_first.size() && i < 9; i++) g.dchunk_first[i] = db->chunk_first[i];
+    for (size_t i = 0; i < db->tuple_first.size() && i <= (size_t)kMaxBuildGroups; i++)
+      g.tuple_first[i] = db->tuple_first[i];
+    for (size_t i = 0; i < db->stride.size() && i < (size_t)kMaxBuildGroups; i++) g.stride[i] = db->stride[i];
+    for (size_t i = 0; i < db->chunk_first.size() && i <= (size_t)kMaxBuildGroups; i++)
+      g.dchunk_first[i] = db->chunk_first[i];
     g.dense_z_slots = db->z_slots;
   }
   g.n = (int)p.groups.size();

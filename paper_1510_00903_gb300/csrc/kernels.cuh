@@ -25,15 +25,16 @@ struct WarpBatch {
   int task[32];
 };
 
-constexpr int kMaxDiquarks = 5;   // (l,l) and (l,s) with C gamma5; (s,s) with eta_l C gamma_l, l = x, y, z
-constexpr int kMaxFamilies = 7;   // lll, lls, lsl, lss (C gamma5); sss_x, sss_y, sss_z (vector)
+constexpr int kMaxDiquarks = 11;   // (l,l), (l,s) with C gamma5; (s,s), (l,l), (l,s) with eta_l C gamma_l
+constexpr int kMaxFamilies = 22;   // lll, lls, lsl, lss (C gamma5); sss, lll, lls, lsl, lss, ssl (vector, x y z)
+constexpr int kMaxBuildGroups = 16;
 struct DevGroups {  // block-build groups (rows that read the same tensor families)
   int n;
-  int first[8], rows[8], fam0[8], fam1[8];
-  int zneed_first[9];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
+  int first[kMaxBuildGroups], rows[kMaxBuildGroups], fam0[kMaxBuildGroups], fam1[kMaxBuildGroups];
+  int zneed_first[kMaxBuildGroups + 1];  // group gi computes tensor entries zneed[zneed_first[gi] .. zneed_first[gi+1])
   int z_slots;         // shared-memory positions for tensor entries
   int spin0;           // Dirac index of the first external spin component (0 upper, 2 lower)
-  int chunk_first[9];  // first 32-row chunk of each group in the lane-interleaved entry table
+  int chunk_first[kMaxBuildGroups + 1];  // first 32-row chunk of each group in the lane-interleaved entry table
   int n_dq;            // diquarks computed per site
   int dq_f0[kMaxDiquarks], dq_f1[kMaxDiquarks];  // their quark flavours (0 light, 1 strange)
   int dq_gam[kMaxDiquarks];                      // their Gamma1: 0 = C gamma5, l = eta_l C gamma_l
@@ -41,7 +42,7 @@ struct DevGroups {  // block-build groups (rows that read the same tensor famili
   int fam_f2[kMaxFamilies];                      // per family: third quark strange (1) or light (0)
   // dense-tuple FP32 build (k_block_build_dense): tuples of each group, their
   // entry stride, entry positions per site, 32-row chunks of each group
-  int tuple_first[9], stride[8], dense_z_slots, dchunk_first[9];
+  int tuple_first[kMaxBuildGroups + 1], stride[kMaxBuildGroups], dense_z_slots, dchunk_first[kMaxBuildGroups + 1];
 };
 
 constexpr int kMaxChannels = 160;  // channels of one context (every id fits)

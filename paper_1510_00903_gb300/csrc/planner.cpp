@@ -48,11 +48,18 @@ struct Op {
 // (d, s, u) (cyclic reorderings of three quark fields are even).
 // The decuplet Omega-_l of the Sec. 4 footnote (the same operator form with
 // Gamma1 = C gamma_l, Gamma2 = 1) is eta_l eps (s C gamma_l s) s with
-// eta = (i, 1, -i), the phase that makes its matrix real.
-enum { OP_P, OP_N, OP_SP, OP_SM, OP_S0, OP_LA, OP_X0, OP_XM, OP_OX, OP_OY, OP_OZ };
+// eta = (i, 1, -i), the phase that makes its matrix real.  The other
+// decuplet baryons take the same form with the flavour-symmetric
+// combinations: Delta++_l = eta_l eps (u C gamma_l u) u, Sigma*+_l =
+// eta_l [eps (u C gamma_l u) s + 2 eps (u C gamma_l s) u] / sqrt3 and Xi*0_l
+// = eta_l [eps (s C gamma_l s) u + 2 eps (s C gamma_l u) s] / sqrt3, the
+// latter two on the strings (u, u, s) and (s, s, u).
+enum { OP_P, OP_N, OP_SP, OP_SM, OP_S0, OP_LA, OP_X0, OP_XM, OP_OX, OP_OY, OP_OZ, OP_DX = 11, OP_SSX = 14,
+       OP_XSX = 17, N_OP = 20 };
 const double kInvSqrt6 = 0.40824829046386301637;
 const double kInvSqrt2 = 0.70710678118654752440;
-const Op kOps[11] = {
+const double kInvSqrt3 = 0.57735026918962576451;
+const Op kOps[N_OP] = {
     {"p", "udu", 1.0, 1, {{1, 0, 1, 2}}, 0},
     {"n", "udd", -1.0, 1, {{1, 0, 1, 2}}, 0},
     {"Sigma+", "usu", -1.0, 1, {{1, 0, 1, 2}}, 1},
@@ -64,12 +71,23 @@ const Op kOps[11] = {
     {"Omega_x", "sss", 1.0, 1, {{1, 0, 1, 2, 1}}, 3},
     {"Omega_y", "sss", 1.0, 1, {{1, 0, 1, 2, 2}}, 3},
     {"Omega_z", "sss", 1.0, 1, {{1, 0, 1, 2, 3}}, 3},
+    {"Delta++_x", "uuu", 1.0, 1, {{1, 0, 1, 2, 1}}, 0},
+    {"Delta++_y", "uuu", 1.0, 1, {{1, 0, 1, 2, 2}}, 0},
+    {"Delta++_z", "uuu", 1.0, 1, {{1, 0, 1, 2, 3}}, 0},
+    {"Sigma*+_x", "uus", kInvSqrt3, 2, {{1, 0, 1, 2, 1}, {2, 0, 2, 1, 1}}, 1},
+    {"Sigma*+_y", "uus", kInvSqrt3, 2, {{1, 0, 1, 2, 2}, {2, 0, 2, 1, 2}}, 1},
+    {"Sigma*+_z", "uus", kInvSqrt3, 2, {{1, 0, 1, 2, 3}, {2, 0, 2, 1, 3}}, 1},
+    {"Xi*0_x", "ssu", kInvSqrt3, 2, {{1, 0, 1, 2, 1}, {2, 0, 2, 1, 1}}, 2},
+    {"Xi*0_y", "ssu", kInvSqrt3, 2, {{1, 0, 1, 2, 2}, {2, 0, 2, 1, 2}}, 2},
+    {"Xi*0_z", "ssu", kInvSqrt3, 2, {{1, 0, 1, 2, 3}, {2, 0, 2, 1, 3}}, 2},
 };
 
 // Channels of Sec. 4 (Eqs. GeneralBB_NN .. GeneralBB_XX) in printed order,
 // then the four omitted ones, eight other charge states, and the decuplet
 // channels: Omega_l1 Omega_l2 <- Omega_l3 Omega_l4 at 64 + 27 l1 + 9 l2 +
-// 3 l3 + l4, p Omega_l <- p Omega_l' at 145 + 3 l + l'.
+// 3 l3 + l4, p Omega_l <- p Omega_l' at 145 + 3 l + l'; the same 81 vector
+// combinations for Delta++ Delta++ (154 + ...), Sigma*+ Sigma*+ (235 + ...)
+// and Xi*0 Xi*0 (316 + ...), then p Delta++_l <- p Delta++_l' at 397 + 3 l + l'.
 std::vector<std::array<int, 4>> make_channels() {
   std::vector<std::array<int, 4>> c;
   c.push_back({OP_P, OP_N, OP_P, OP_N});
@@ -110,6 +128,13 @@ std::vector<std::array<int, 4>> make_channels() {
         for (int l4 = 0; l4 < 3; l4++) c.push_back({om[l1], om[l2], om[l3], om[l4]});
   for (int l = 0; l < 3; l++)
     for (int m = 0; m < 3; m++) c.push_back({OP_P, om[l], OP_P, om[m]});
+  for (int base : {OP_DX, OP_SSX, OP_XSX})
+    for (int l1 = 0; l1 < 3; l1++)
+      for (int l2 = 0; l2 < 3; l2++)
+        for (int l3 = 0; l3 < 3; l3++)
+          for (int l4 = 0; l4 < 3; l4++) c.push_back({base + l1, base + l2, base + l3, base + l4});
+  for (int l = 0; l < 3; l++)
+    for (int m = 0; m < 3; m++) c.push_back({OP_P, OP_DX + l, OP_P, OP_DX + m});
   return c;
 }
 
@@ -135,18 +160,34 @@ const int kEps[6][4] = {{0, 1, 2, +1}, {1, 2, 0, +1}, {2, 0, 1, +1},
 
 bool is_strange(char f) { return f == 's'; }
 
-// Family of a sink term and the slot order (Gamma pair, delta) in it.
-// D_sl[x, y] = D_ls[y, x] (eps and Cg5 both antisymmetric), so an (s, l)
-// diquark is read as (l, s) with its two slots swapped.  A vector diquark
-// (Gamma1 = eta_l C gamma_l) is an (s, s) one of the Omega family.
-int family_of(const char* flav, const Term& t, int slots[3]) {
+// Family of a sink term, the slot order (Gamma pair, delta) in it and the
+// sign of that order.  A family tensor takes eps over (Gamma pair, delta) in
+// that order; the operator's eps runs over the quark string, so a term whose
+// (gi, gj, dk) is an odd permutation of the string carries a sign -1 (the
+// octet terms are all cyclic).  Renaming the two summed (spin, colour) pairs
+// of a diquark gives D_sl[x, y] = -(Gamma1 symmetry) D_ls[y, x]: +D_ls[y, x]
+// for C gamma5 (antisymmetric, like eps), -D_ls[y, x] for the symmetric
+// eta_l C gamma_l, so an (s, l) diquark is read as (l, s) with its two slots
+// swapped and that sign.
+int perm_parity(const int* p, int n);
+int family_of(const char* flav, const Term& t, int slots[3], int* sign) {
   bool a = is_strange(flav[t.gi]), b = is_strange(flav[t.gj]), c = is_strange(flav[t.dk]);
   slots[0] = t.gi; slots[1] = t.gj; slots[2] = t.dk;
-  if (t.g > 0) return (a && b && c) ? F_SSS_X + t.g - 1 : -1;
-  if (a && !b) { std::swap(a, b); std::swap(slots[0], slots[1]); }
-  if (!a && !b) return c ? F_LLS : F_LLL;
-  if (!a && b) return c ? F_LSS : F_LSL;
-  return -1;  // (s, s) diquark: not in the octet operators
+  *sign = perm_parity(slots, 3);
+  if (a && !b) {
+    std::swap(a, b);
+    std::swap(slots[0], slots[1]);
+    if (t.g > 0) *sign = -*sign;
+  }
+  if (t.g == 0) {
+    if (!a && !b) return c ? F_LLS : F_LLL;
+    if (!a && b) return c ? F_LSS : F_LSL;
+    return -1;  // (s, s) C gamma5 diquark: in no operator here
+  }
+  const int l = t.g - 1;
+  if (!a && !b) return (c ? F_LLSV_X : F_LLLV_X) + l;
+  if (!a && b) return (c ? F_LSSV_X : F_LSLV_X) + l;
+  return (c ? F_SSS_X : F_SSLV_X) + l;
 }
 
 // Global tensor index and sign; families with two identical diquark quarks
@@ -155,8 +196,8 @@ int family_of(const char* flav, const Term& t, int slots[3]) {
 // for the symmetric vector matrices (zero at e0 = e1: returns -1).
 int zindex(int fam, int a, int e0, int e1, int e2, int* sgn) {
   *sgn = 1;
-  if ((fam == F_LLL || fam == F_LLS) && e1 < e0) std::swap(e0, e1);
-  if (fam >= F_SSS_X) {
+  if (kFamSym[fam] > 0 && e1 < e0) std::swap(e0, e1);
+  if (kFamSym[fam] < 0) {
     if (e0 == e1) return -1;
     if (e1 < e0) { std::swap(e0, e1); *sgn = -1; }
   }
@@ -419,10 +460,10 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
                         int ein[3];
                         for (int s = 0; s < 3; s++) ein[s] = eta[pos[pi[s]]];
                         for (int t = 0; t < sink->nterm; t++) {
-                          int sl[3], zs;
-                          int fam = family_of(sink->flav, sink->t[t], sl);
+                          int sl[3], zs, fs;
+                          int fam = family_of(sink->flav, sink->t[t], sl, &fs);
                           int z = zindex(fam, a, ein[sl[0]], ein[sl[1]], ein[sl[2]], &zs);
-                          if (z >= 0) acc[z] += zs * w * pi[3] * sink->t[t].coef;
+                          if (z >= 0) acc[z] += fs * zs * w * pi[3] * sink->t[t].coef;
                         }
                       }
                     }
@@ -479,19 +520,24 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
 
   // --- group blocks by the families they read, assign row offsets ---------
   // group order: lll | lss | lsl | lsl+lls (the last two share slot 0) |
-  // sss_x | sss_y | sss_z
-  const std::vector<std::array<int, 2>> gfam = {{F_LLL, -1},   {F_LSS, -1},   {F_LSL, -1},  {F_LSL, F_LLS},
-                                                {F_SSS_X, -1}, {F_SSS_Y, -1}, {F_SSS_Z, -1}};
+  // sss_x | sss_y | sss_z | per vector index l: lll_l | lsl_l+lls_l |
+  // lss_l+ssl_l.  A block goes to the first group whose families cover the
+  // ones it reads (a block of empty rows to lsl+lls).
+  std::vector<std::array<int, 2>> gfam = {{F_LLL, -1},   {F_LSS, -1},   {F_LSL, -1},  {F_LSL, F_LLS},
+                                          {F_SSS_X, -1}, {F_SSS_Y, -1}, {F_SSS_Z, -1}};
+  for (int l = 0; l < 3; l++) {
+    gfam.push_back({F_LLLV_X + l, -1});
+    gfam.push_back({F_LSLV_X + l, F_LLSV_X + l});
+    gfam.push_back({F_LSSV_X + l, F_SSLV_X + l});
+  }
   std::vector<std::vector<int>> members(gfam.size());
   for (int u = 0; u < (int)ublocks.size(); u++) {
-    int m = ublocks[u].fam_mask, g = -1;
-    if (m == (1 << F_LLL)) g = 0;
-    else if (m == (1 << F_LSS)) g = 1;
-    else if (m == (1 << F_LSL)) g = 2;
-    else if ((m & ~((1 << F_LSL) | (1 << F_LLS))) == 0) g = 3;  // (or a block of empty rows)
-    else if (m == (1 << F_SSS_X)) g = 4;
-    else if (m == (1 << F_SSS_Y)) g = 5;
-    else if (m == (1 << F_SSS_Z)) g = 6;
+    const int m = ublocks[u].fam_mask;
+    int g = m == 0 ? 3 : -1;
+    for (size_t k = 0; k < gfam.size() && g < 0; k++) {
+      const int cover = (1 << gfam[k][0]) | (gfam[k][1] >= 0 ? 1 << gfam[k][1] : 0);
+      if ((m & ~cover) == 0) g = (int)k;
+    }
     if (g < 0) { *err = "internal: block reads an unexpected family set"; return false; }
     members[g].push_back(u);
   }
@@ -839,7 +885,7 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
     }
   for (uint32_t e : P.ell)
     if ((int)(e & 0xffffu) >= P.z_slots) { *err = "internal: tensor position"; return false; }
-  if (P.groups.size() > 8) { *err = "internal: group count"; return false; }
+  if (P.groups.size() > (size_t)kMaxGroups) { *err = "internal: group count"; return false; }
   *plan = std::move(P);
   return true;
 }

@@ -15,19 +15,37 @@ namespace bbc {
 
 // Sink-tensor families: the diquark pair and the third (delta) quark of a
 // baryon term, by numeric flavour (l = u = d, s) and diquark matrix Gamma1
-// (C gamma5 for the octet; eta_l C gamma_l, l = x, y, z, for the decuplet
-// Omega of the Sec. 4 footnote):
+// (C gamma5 for the octet; eta_l C gamma_l, l = x, y, z, for the decuplet of
+// the Sec. 4 footnote: Omega (s s s), Delta++ (l l l), Sigma*+ (l l s and
+// l s l terms), Xi*0 (s s l and l s s terms)):
 //   F[a][e0][e1][e2] = sum eps(c0,c1,c2) Gamma1(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1] S_f2[(a,c2),e2]
-enum Family { F_LLL = 0, F_LLS = 1, F_LSL = 2, F_LSS = 3, F_SSS_X = 4, F_SSS_Y = 5, F_SSS_Z = 6, N_FAMILY = 7 };
+enum Family {
+  F_LLL = 0, F_LLS = 1, F_LSL = 2, F_LSS = 3,  // C gamma5
+  F_SSS_X = 4, F_SSS_Y = 5, F_SSS_Z = 6,       // eta_l C gamma_l, l = x, y, z (each vector family below too)
+  F_LLLV_X = 7, F_LLSV_X = 10, F_LSLV_X = 13, F_LSSV_X = 16, F_SSLV_X = 19,
+  N_FAMILY = 22
+};
 // Diquarks D[e0][e1][c2] = sum eps Gamma1(a0,a1) S_f0[(a0,c0),e0] S_f1[(a1,c1),e1]
-// the families read: (l, l) and (l, s) with C gamma5, (s, s) with eta_l C gamma_l.
-enum Diquark { DQ_LL5 = 0, DQ_LS5 = 1, DQ_SSX = 2, DQ_SSY = 3, DQ_SSZ = 4, N_DIQUARK = 5 };
+// the families read: (l, l) and (l, s) with C gamma5; (s, s), (l, l) and
+// (l, s) with eta_l C gamma_l.
+enum Diquark { DQ_LL5 = 0, DQ_LS5 = 1, DQ_SSX = 2, DQ_LLX = 5, DQ_LSX = 8, N_DIQUARK = 11 };
 // Diquark and strange third quark (0 / 1) of each family.
-constexpr int kFamDiquark[N_FAMILY] = {DQ_LL5, DQ_LL5, DQ_LS5, DQ_LS5, DQ_SSX, DQ_SSY, DQ_SSZ};
-constexpr int kFamThird[N_FAMILY] = {0, 1, 0, 1, 1, 1, 1};
+constexpr int kFamDiquark[N_FAMILY] = {DQ_LL5,  DQ_LL5,     DQ_LS5,     DQ_LS5,     DQ_SSX,     DQ_SSX + 1,
+                                       DQ_SSX + 2, DQ_LLX,  DQ_LLX + 1, DQ_LLX + 2, DQ_LLX,     DQ_LLX + 1,
+                                       DQ_LLX + 2, DQ_LSX,  DQ_LSX + 1, DQ_LSX + 2, DQ_LSX,     DQ_LSX + 1,
+                                       DQ_LSX + 2, DQ_SSX,  DQ_SSX + 1, DQ_SSX + 2};
+constexpr int kFamThird[N_FAMILY] = {0, 1, 0, 1, 1, 1, 1, 0, 0, 0, 1, 1, 1, 0, 0, 0, 1, 1, 1, 0, 0, 0};
+// Exchange symmetry of a family's first two indices (e0, e1): +1 for a
+// C gamma5 diquark of two equal flavours (eps and C gamma5 both
+// antisymmetric), -1 for a vector diquark of two equal flavours (eta_l C
+// gamma_l is symmetric), 0 for two different flavours.
+constexpr int kFamSym[N_FAMILY] = {1, 1, 0, 0, -1, -1, -1, -1, -1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, -1, -1, -1};
 // Flavours (0 light, 1 strange) and Gamma1 (0 = C gamma5, l = eta_l C gamma_l) of each diquark.
-constexpr int kDqFlavour[N_DIQUARK][2] = {{0, 0}, {0, 1}, {1, 1}, {1, 1}, {1, 1}};
-constexpr int kDqGamma[N_DIQUARK] = {0, 0, 1, 2, 3};
+constexpr int kDqFlavour[N_DIQUARK][2] = {{0, 0}, {0, 1}, {1, 1}, {1, 1}, {1, 1}, {0, 0},
+                                          {0, 0}, {0, 0}, {0, 1}, {0, 1}, {0, 1}};
+constexpr int kDqGamma[N_DIQUARK] = {0, 0, 1, 2, 3, 1, 2, 3, 1, 2, 3};
+// Block-build groups (rows that read the same families) a plan may have.
+constexpr int kMaxGroups = 16;
 constexpr int kFamEntries = 2 * 1728;  // sink spin a in {0,1} (upper) x 12^3
 
 struct GroupInfo {

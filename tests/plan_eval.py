@@ -19,12 +19,17 @@ import numpy as np
 import bruteforce as bf
 
 # (flavour of diquark quark 0, of diquark quark 1, of the third quark) with
-# 0 = light, 1 = strange, and the diquark matrix Gamma1 of families 0..6
+# 0 = light, 1 = strange, and the diquark matrix Gamma1 of families 0..21:
+# the four C gamma5 families, then (s s s) with eta_l C gamma_l (l = x, y, z),
+# then, l = x, y, z each, (l l l), (l l s), (l s l), (l s s), (s s l) with
+# eta_l C gamma_l (the family order of the plan's tensor indices)
 _EPS = np.zeros((3, 3, 3))
 for _p in itertools.permutations(range(3)):
     _EPS[_p] = 1.0 if sum(_p[i] > _p[j] for i in range(3) for j in range(i + 1, 3)) % 2 == 0 else -1.0
 FAMILIES = [((0, 0, 0), bf.CG5), ((0, 0, 1), bf.CG5), ((0, 1, 0), bf.CG5), ((0, 1, 1), bf.CG5),
             ((1, 1, 1), bf.CGL[0]), ((1, 1, 1), bf.CGL[1]), ((1, 1, 1), bf.CGL[2])]
+for _fl in ((0, 0, 0), (0, 0, 1), (0, 1, 0), (0, 1, 1), (1, 1, 0)):
+    FAMILIES += [(_fl, bf.CGL[_l]) for _l in range(3)]
 
 
 def family_tensors(S_light: np.ndarray, S_strange: np.ndarray, spin_offset: int) -> np.ndarray:

@@ -33,7 +33,7 @@ def test_exports_every_declared_symbol():
 
 @pytest.mark.parametrize("L,T,t0,ch,prec", [
     (5, 8, 0, [0], 0), (16, 0, 0, [0], 0), (16, 8, 8, [0], 0),
-    (16, 8, 0, [154], 0), (16, 8, 0, [-1], 0), (16, 8, 0, [3, 3], 0), (16, 8, 0, [0], 7)])
+    (16, 8, 0, [406], 0), (16, 8, 0, [-1], 0), (16, 8, 0, [3, 3], 0), (16, 8, 0, [0], 7)])
 def test_create_rejects_bad_arguments(L, T, t0, ch, prec):
     with pytest.raises(bbc.BBCError) as e:
         bbc.bbc_create(L, T, t0, 0.3, 0.4, prec, ch)

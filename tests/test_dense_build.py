@@ -133,7 +133,10 @@ def checker(tmp_path_factory):
 
 
 LISTS = {"52": list(range(52)), "64 octet ids": list(range(64)), "90 decuplet ids": list(range(64, 154)),
-         "octet and decuplet": list(range(52)) + list(range(64, 154)), "one channel": [1]}
+         "octet and decuplet": list(range(52)) + list(range(64, 154)), "one channel": [1],
+         "Delta++ and p Delta++": list(range(154, 235)) + list(range(397, 406)),
+         "Sigma*+ pairs": list(range(235, 316)), "Xi*0 pairs": list(range(316, 397)),
+         "every family": [0, 10, 51, 64, 150, 154, 200, 240, 300, 320, 396, 400]}
 
 
 @pytest.mark.parametrize("name", list(LISTS))

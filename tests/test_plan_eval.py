@@ -51,6 +51,16 @@ def test_decuplet(slice3, components):
     _check(list(range(64, 154)), components, slice3)
 
 
+@pytest.mark.parametrize("components", [bbc.BBC_UPPER, bbc.BBC_LOWER])
+@pytest.mark.parametrize("ids", [bbc.DELTA_DELTA + bbc.P_DELTA, bbc.SIGMA_STAR_PAIRS, bbc.XI_STAR_PAIRS],
+                         ids=["Delta++ and p Delta++", "Sigma*+ pairs", "Xi*0 pairs"])
+def test_decuplet_families(slice3, components, ids):
+    """The (l, l), (l, s) and (s, l) vector diquarks, the two-term operators
+    (one term's eps over an odd reordering of its quark string) and the
+    (s, l) -> (l, s) slot swap of a symmetric diquark matrix."""
+    _check(ids, components, slice3)
+
+
 def test_single_channel_plans(slice3):
     """Plans of one channel (other block sets, families and diquark lists)."""
     for ch in (0, 1, 10, 37, 51, 60, 64, 121, 150):

@@ -188,6 +188,8 @@ LISTS = {
     "90 decuplet ids": list(range(64, 154)),
     "one channel": [1],
     "p n only": [0],
+    "Delta++ ids": list(range(154, 163)) + [397, 405],
+    "Sigma*+ and Xi*0 ids": [235, 260, 300, 316, 340, 396],
 }
 
 
