@@ -277,7 +277,13 @@ __global__ void __launch_bounds__(3 * kSplitLines)
 k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n_outer, int n_inner, int axis,
             const double* __restrict__ scale, O* __restrict__ sum) {
   constexpr int N = 3 * M;
+  // sh[line][j][k2 ^ (line & 7)]: a line's 3 M values are 3 M x 16 bytes
+  // apart from the next line's, a multiple of the 128-byte bank period, so the
+  // XOR spreads eight lanes' 16-byte accesses over the eight 16-byte slots of
+  // a wavefront (without it the 32 lanes of a warp hit the same four banks)
+  static_assert(M >= 8 && (M & (M - 1)) == 0, "swizzle within a power-of-two line of 8 or more");
   __shared__ cpx<R> sh[kSplitLines][3][M];
+  auto at = [&](int l, int jj, int k2) -> cpx<R>& { return sh[l][jj][k2 ^ (l & 7)]; };
   const int ls = threadIdx.x % kSplitLines, j = threadIdx.x / kSplitLines;
   const long long gid = blockIdx.x * (long long)kSplitLines + ls;
   const int lines = N * N;
@@ -321,7 +327,7 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
         if (INV) w.im = -w.im;
         u[k2] = w * u[k2];
       }
-      sh[ls][j][k2] = u[k2];
+      at(ls, j, k2) = u[k2];
     }
   }
   __syncthreads();
@@ -334,13 +340,13 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
     // threads on consecutive points.
     if (live) {
       for (int k2 = j; k2 < M; k2 += 3) {
-        const cpx<R> t0 = sh[ls][0][k2], t1 = sh[ls][1][k2], t2 = sh[ls][2][k2];
+        const cpx<R> t0 = at(ls, 0, k2), t1 = at(ls, 1, k2), t2 = at(ls, 2, k2);
         const cpx<R> sm = t1 + t2, d = t1 - t2;
         const cpx<R> m(t0.re - (R)0.5 * sm.re, t0.im - (R)0.5 * sm.im);
         const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);
-        sh[ls][0][k2] = t0 + sm;  // X[k2 + c M] at sh[ls][c][k2]
-        sh[ls][1][k2] = m + r;
-        sh[ls][2][k2] = m - r;
+        at(ls, 0, k2) = t0 + sm;  // X[k2 + c M] at (ls, c, k2)
+        at(ls, 1, k2) = m + r;
+        at(ls, 2, k2) = m - r;
       }
     }
     __syncthreads();
@@ -355,13 +361,13 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
       const long long oo = rst / lines;
       int b = 0, sd = 0;
       line_base(N, axis, ln, b, sd);
-      out[(oo * n_inner + inn) * V + b + (long long)k * sd] = cpx<O>(sh[l][k / M][k % M]);
+      out[(oo * n_inner + inn) * V + b + (long long)k * sd] = cpx<O>(at(l, k / M, k % M));
     }
     return;
   }
   if (!live) return;
   for (int k2 = j; k2 < M; k2 += 3) {
-    const cpx<R> t0 = sh[ls][0][k2], t1 = sh[ls][1][k2], t2 = sh[ls][2][k2];
+    const cpx<R> t0 = at(ls, 0, k2), t1 = at(ls, 1, k2), t2 = at(ls, 2, k2);
     const cpx<R> sm = t1 + t2, d = t1 - t2;
     const cpx<R> m(t0.re - (R)0.5 * sm.re, t0.im - (R)0.5 * sm.im);
     const cpx<R> r = INV ? cpx<R>(-hs * d.im, hs * d.re) : cpx<R>(hs * d.im, -hs * d.re);
