@@ -305,7 +305,7 @@ bbc_status bbc_check_bounded_wait(bbc_ctx* ctx, long long spin_limit);
 
 /* Launch configuration of the two kernels whose shape is tunable:
  *  build_sites, build_threads: sites per CTA and threads of the block build,
- *    one of (1, 256), (2, 256), (2, 512), (4, 512); a CTA keeps the
+ *    one of (1, 256), (2, 256), (2, 512), (4, 512), (1, 512); a CTA keeps the
  *    propagators, diquarks and sink-tensor entries of its sites in shared
  *    memory (configurations that need more than 227 KB are not valid);
  *  fused_warps, fused_chunk (mixed precisions with the fused kernel only): warps per CTA (8, 12, 16)

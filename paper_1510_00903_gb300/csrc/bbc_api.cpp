@@ -194,7 +194,7 @@ const FusedSchedule& fused_schedule(const bbc::Plan& plan, const bbc::Plan& run,
 }
 
 // Candidate launch configurations of the autotuner.
-const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}};  // (sites per CTA, threads)
+const int kBuildCand[][2] = {{1, 256}, {2, 256}, {2, 512}, {4, 512}, {1, 512}};  // (sites per CTA, threads)
 const int kFusedWarpsCand[] = {8, 12, 16};
 const int kRestWarpsCand[] = {4, 8};  // k_contract_rest (two CTAs per SM)
 const int kFusedStepsCand[] = {1, 2};

@@ -325,7 +325,7 @@ size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq) {  // fp64:
 }
 
 bool build_variant_supported(int sites, int threads) {
-  return (sites == 1 && threads == 256) || (sites == 2 && (threads == 256 || threads == 512)) ||
+  return (sites == 1 && (threads == 256 || threads == 512)) || (sites == 2 && (threads == 256 || threads == 512)) ||
          (sites == 4 && threads == 512);
 }
 
@@ -354,7 +354,7 @@ cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2*
     return kind == RK_F64 ? launch_build_variant<double, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st) \
          : kind == RK_DF  ? launch_build_variant<dfr, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st)    \
                           : launch_build_variant<float, S, T>(prop, V, n_slots, ell_chunk, ell, zneed, g, blk, n_out, st);
-  BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512)
+  BBC_BUILD(1, 256) BBC_BUILD(2, 256) BBC_BUILD(2, 512) BBC_BUILD(4, 512) BBC_BUILD(1, 512)
 #undef BBC_BUILD
   return cudaErrorInvalidValue;
 }
