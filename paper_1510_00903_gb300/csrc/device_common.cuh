@@ -71,15 +71,17 @@ __device__ __forceinline__ void df_renorm(df64acc& acc) {
 }
 
 // Double-float real with arithmetic operators, for kernels templated on the
-// real type (block build, FFT).  Addition is the cheap variant (TwoSum of the
-// high words, the low words added, one renormalisation), whose error is
-// bounded by about 2^-44 (|a| + |b|): an absolute error at the scale of the
-// operands, which is what the correlator tolerance measures.
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // needs |a| >= |b|
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
+// real type (block build, FFT).  The operators keep the pair unnormalised: a
+// sum is the TwoSum of the high words with the low words added into its
+// error word, a product the TwoProduct of the high words with the cross
+// terms added into its error word, and neither renormalises (hi, lo) so that
+// |lo| <= ulp(hi) / 2.  The low word then holds the accumulated rounding
+// errors of a few operations at most a few ulps of the high word; every
+// later TwoSum and TwoProduct on the high words is still exact, so the error
+// of a sum or product stays about 2^-44 (|a| + |b|) or 2^-44 |a b|: an
+// absolute error at the scale of the operands, which is what the correlator
+// tolerance measures.  Consumers read hi + lo (the pair products, the
+// conversion to double), never hi alone.
 struct dfr {
   float hi, lo;
   __host__ __device__ dfr() {}
@@ -94,10 +96,7 @@ __device__ __forceinline__ dfr operator-(dfr a) { return dfr(-a.hi, -a.lo); }
 __device__ __forceinline__ dfr operator+(dfr a, dfr b) {
   float s, e;
   two_sum(a.hi, b.hi, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  float h, l;
-  fast_two_sum(s, e, h, l);
-  return dfr(h, l);
+  return dfr(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ dfr operator-(dfr a, dfr b) { return a + (-b); }
 __device__ __forceinline__ dfr operator*(dfr a, dfr b) {
@@ -105,16 +104,15 @@ __device__ __forceinline__ dfr operator*(dfr a, dfr b) {
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  float h, l;
-  fast_two_sum(p, e, h, l);
-  return dfr(h, l);
+  return dfr(p, e);
 }
 __device__ __forceinline__ dfr& operator+=(dfr& a, dfr b) { return a = a + b; }
 // Multiply-add overloads in this namespace (the double-float one would
 // otherwise hide the floating-point ones from unqualified calls).
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
-// a * b + c: the product's two words folded into the sum before one renormalisation
+// a * b + c: the product's two words folded into the sum (TwoSum of the high
+// words), unnormalised like the operators
 __device__ __forceinline__ dfr fma(dfr a, dfr b, dfr c) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -122,10 +120,7 @@ __device__ __forceinline__ dfr fma(dfr a, dfr b, dfr c) {
   e = __fmaf_rn(a.lo, b.hi, e);
   float s, t;
   two_sum(c.hi, p, s, t);
-  t = __fadd_rn(t, __fadd_rn(e, c.lo));
-  float h, l;
-  fast_two_sum(s, t, h, l);
-  return dfr(h, l);
+  return dfr(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
 }
 
 // Asynchronous global -> shared copies (cp.async; the data bypasses the
