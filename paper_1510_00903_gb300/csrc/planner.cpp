@@ -620,6 +620,43 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
         }
       prev_fam[0] = gi.fam[0];
       prev_fam[1] = gi.fam[1];
+      // The entries of a group are formed one per thread in list order; with
+      // 16-byte entries (FP64, double-float) eight consecutive threads share a
+      // wavefront.  Order the list so that each such eight differ, where they
+      // can, in the bank group (mod 8) of the three shared-memory addresses a
+      // thread touches: its diquark row (3 e01 + c2), its propagator row
+      // (12 (3 a + c2) + e2) and its store position.
+      {
+        const size_t z0 = (size_t)P.zneed_first.back(), z1 = P.zneed.size();
+        std::vector<uint32_t> rest(P.zneed.begin() + (long)z0, P.zneed.end());
+        auto keys = [](uint32_t zn, int out[3]) {
+          const int local = (int)(zn >> 14), pos = (int)(zn & 0x1fffu);
+          const int a = local / 1728, e01 = (local % 1728) / 12, e2 = local % 12;
+          out[0] = (3 * e01) & 7;
+          out[1] = (36 * a + e2) & 7;
+          out[2] = pos & 7;
+        };
+        size_t w = z0;
+        while (!rest.empty()) {
+          bool used[3][8] = {{false}};
+          for (int lane = 0; lane < 8 && !rest.empty(); lane++) {
+            size_t best = 0;
+            int best_clash = 4;
+            for (size_t j = 0; j < rest.size() && best_clash > 0; j++) {
+              int k[3];
+              keys(rest[j], k);
+              const int clash = (int)used[0][k[0]] + (int)used[1][k[1]] + (int)used[2][k[2]];
+              if (clash < best_clash) { best_clash = clash; best = j; }
+            }
+            int k[3];
+            keys(rest[best], k);
+            for (int m = 0; m < 3; m++) used[m][k[m]] = true;
+            P.zneed[w++] = rest[best];
+            rest.erase(rest.begin() + (long)best);
+          }
+        }
+        if (w != z1) { *err = "internal: tensor entry order"; return false; }
+      }
       P.zneed_first.push_back((int)P.zneed.size());
     }
   }
@@ -820,22 +857,25 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
       const int base = (int)P.ell.size();
       P.ell.resize(P.ell.size() + (size_t)32 * len, 0u);  // weight 0, position 0
       // A row's terms may be summed in any order: at every step k, give each
-      // lane a term whose tensor position falls in a bank group (position
-      // mod 16: an 8-byte FP32 complex spans two of the 32 banks) that no
-      // other lane of its half-warp uses at that step, where it can.
+      // lane a term whose tensor position falls in a bank group that no other
+      // lane of its wavefront uses at that step, where it can.  The tables
+      // serve the FP64 and double-float builds: a 16-byte entry spans four of
+      // the 32 banks, so a 128-byte wavefront serves eight lanes and the bank
+      // group is the position mod 8.
+      constexpr int kLanes = 8, kGroups = 8;
       std::vector<std::vector<uint32_t>> left(nr);
       for (int l = 0; l < nr; l++)
         left[l].assign(P.entries.begin() + P.row_ptr[r0 + l], P.entries.begin() + P.row_ptr[r0 + l + 1]);
       for (int k = 0; k < len; k++)
-        for (int h = 0; h < 32; h += 16) {
-          bool used[16] = {false};
-          for (int l = h; l < std::min(nr, h + 16); l++) {
+        for (int h = 0; h < 32; h += kLanes) {
+          bool used[kGroups] = {false};
+          for (int l = h; l < std::min(nr, h + kLanes); l++) {
             std::vector<uint32_t>& v = left[l];
             if (v.empty()) continue;
             size_t pick = 0;
             for (size_t j = 0; j < v.size(); j++)
-              if (!used[(v[j] & 0xffffu) % 16]) { pick = j; break; }
-            used[(v[pick] & 0xffffu) % 16] = true;
+              if (!used[(v[j] & 0xffffu) % kGroups]) { pick = j; break; }
+            used[(v[pick] & 0xffffu) % kGroups] = true;
             P.ell[base + 32 * k + l] = v[pick];
             v.erase(v.begin() + (long)pick);
           }
@@ -844,14 +884,14 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
       // modelled shared-memory wavefronts of the two steps drop: distinct
       // positions in one bank group serialise, equal ones broadcast, padding
       // (weight 0) reads position 0
-      auto half_cost = [&](int k, int h) {
-        int cnt[16] = {0}, seen[16][16], m = 0;
-        for (int l = h; l < std::min(nr, h + 16); l++) {
+      auto group_cost = [&](int k, int h) {
+        int cnt[kGroups] = {0}, seen[kGroups][kLanes], m = 0;
+        for (int l = h; l < std::min(nr, h + kLanes); l++) {
           const uint32_t e = P.ell[base + 32 * k + l];
-          const int pos = (int)(e & 0xffffu), b = pos % 16;
+          const int pos = (int)(e & 0xffffu), b = pos % kGroups;
           bool dup = false;
           for (int j = 0; j < cnt[b]; j++) dup |= seen[b][j] == pos;
-          if (!dup && cnt[b] < 16) {
+          if (!dup && cnt[b] < kLanes) {
             seen[b][cnt[b]++] = pos;
             m = std::max(m, cnt[b]);
           }
@@ -866,10 +906,10 @@ bool build_plan(const int* channels, int n, Plan* plan, std::string* err, int sp
               uint32_t& a = P.ell[base + 32 * k1 + l];
               uint32_t& b = P.ell[base + 32 * k2 + l];
               if (a == b) continue;
-              const int h = l / 16 * 16;
-              const int before = half_cost(k1, h) + half_cost(k2, h);
+              const int h = l / kLanes * kLanes;
+              const int before = group_cost(k1, h) + group_cost(k2, h);
               std::swap(a, b);
-              if (half_cost(k1, h) + half_cost(k2, h) < before) improved = true;
+              if (group_cost(k1, h) + group_cost(k2, h) < before) improved = true;
               else std::swap(a, b);
             }
         if (!improved) break;
