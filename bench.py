@@ -187,6 +187,9 @@ def parse():
                          "the FP64 path checked against the oracle at sampled points")
     ap.add_argument("--single-slice", choices=["fp64", "mixed", "bf16", "df64"], default=None,
                     help="run one time slice of the workload once and exit (small case for profilers)")
+    ap.add_argument("--family", choices=["omega", "delta", "sigma", "xi"], default="omega",
+                    help="--workload decuplet: the 90 Omega Omega and p Omega ids, the 90 Delta++ Delta++ and "
+                         "p Delta++ ids, or the 81 Sigma*+ Sigma*+ or Xi*0 Xi*0 ids")
     ap.add_argument("--slice-L", type=int, default=None,
                     help="--single-slice on an L^3 x 2L lattice instead of 16^3 x 32")
     ap.add_argument("--slice-channels", default=None,
@@ -662,7 +665,10 @@ def run_decuplet(args, torch, dev, bbc, synth):
     rank, world, _ = dist_env()
     L, T = L_BENCH, T_BENCH
     V = L ** 3
-    chans = bbc.OMEGA_OMEGA + bbc.P_OMEGA
+    chans, label = {"omega": (bbc.OMEGA_OMEGA + bbc.P_OMEGA, "90 decuplet channels (81 Omega Omega, 9 p Omega)"),
+                    "delta": (bbc.DELTA_DELTA + bbc.P_DELTA, "90 decuplet channels (81 Delta++ Delta++, 9 p Delta++)"),
+                    "sigma": (bbc.SIGMA_STAR_PAIRS, "81 decuplet channels (Sigma*+ Sigma*+)"),
+                    "xi": (bbc.XI_STAR_PAIRS, "81 decuplet channels (Xi*0 Xi*0)")}[args.family]
     F = synth.flavour_set(L, T, 0, M_UD, M_S, **shard.rank_source(rank))
     Sl, Ss = torch.from_numpy(F["u"]).to(dev), torch.from_numpy(F["s"]).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -711,8 +717,8 @@ def run_decuplet(args, torch, dev, bbc, synth):
     emit({"metric": "BB correlator site*channels/s", "value": fp["value"], "unit": "site*channels/s",
           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fp["ms_per_step"],
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-          "config": {"workload": "90 decuplet channels (81 Omega Omega, 9 p Omega), L=16, T=32, one wall source, "
-                                 "complex128 propagators, plain FP64", "L": L, "T": T, "channels": len(chans),
+          "config": {"workload": label + ", L=16, T=32, one wall source, complex128 propagators, plain FP64",
+                     "L": L, "T": T, "channels": len(chans),
                      "l2": f"no flush: block fields of one slice ({V * sizes['block_outputs'] * 16 / 1e6:.0f} MB) "
                            "exceed the 129 MB L2"},
           "roofline": {"bound": "alu", "kernel": "k_pair_products<double>", "achieved": fp["contract_tflops"],

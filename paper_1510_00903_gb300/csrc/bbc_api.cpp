@@ -311,7 +311,7 @@ cudaError_t launch_build(bbc_ctx* c, int n_slots, int sites, int threads) {
   const bbc::Plan& p = c->plan;
   if (c->dense)
     return bbc::launch_block_build_dense(c->d_prop, c->V, n_slots, c->d_dchunk, c->d_dell, c->d_dtuples,
-                                         bbc::dev_groups(p, &c->db), c->d_blk, p.n_out, c->stream, sites);
+                                         bbc::dev_groups(p, &c->db), c->d_blk, p.n_out, c->stream, sites, threads);
   return bbc::launch_block_build(c->d_prop, c->V, n_slots, c->d_ell_chunk, c->d_ell, c->d_zneed, bbc::dev_groups(p),
                                  c->d_blk, p.n_out, real_kind(c->prec), c->stream, sites, threads);
 }

@@ -201,13 +201,13 @@ k_block_build(const cpx<R>* __restrict__ prop, int V, const int2* __restrict__ e
 // mostly share (slot, a): broadcast loads), writing entry (j, e2) to position
 // e2 * stride + j (contiguous stores); the rows then sum their terms, weight
 // = the top 16 bits of the table entry read as an FP32 value.
-template <int SITES>
-__global__ void __launch_bounds__(256)
+template <int SITES, int THREADS>
+__global__ void __launch_bounds__(THREADS)
 k_block_build_dense(const cpx<float>* __restrict__ prop, int V, const int2* __restrict__ ell_chunk,
                     const uint32_t* __restrict__ ell, const uint32_t* __restrict__ tuples, DevGroups g,
                     cpx<float>* __restrict__ blk, int n_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kThreads = 256;
+  constexpr int kThreads = THREADS;
   const int nd = g.n_dq * 432, zs = g.dense_z_slots;
   cpx<float>* sS = reinterpret_cast<cpx<float>*>(smem_raw);  // [SITES][2][144]  light, strange
   cpx<float>* sD = sS + SITES * 288;                          // [SITES][n_dq][432]
@@ -290,33 +290,39 @@ k_block_build_dense(const cpx<float>* __restrict__ prop, int V, const int2* __re
   }
 }
 
-bool dense_build_supported(int sites, int threads) { return threads == 256 && (sites == 1 || sites == 2); }
+bool dense_build_supported(int sites, int threads) {
+  return (threads == 256 || threads == 512) && (sites == 1 || sites == 2);
+}
 
 size_t dense_build_smem(const DevGroups& g, int sites) {
   return (size_t)sites * (288 + 432 * (size_t)g.n_dq + g.dense_z_slots) * sizeof(cpx<float>);
 }
 
-template <int SITES>
+template <int SITES, int THREADS>
 cudaError_t launch_dense_variant(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                  const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st) {
   const size_t sm = dense_build_smem(g, SITES);
   static int granted[64] = {0};
-  cudaError_t e = ensure_smem(k_block_build_dense<SITES>, sm, granted);
+  cudaError_t e = ensure_smem(k_block_build_dense<SITES, THREADS>, sm, granted);
   if (e != cudaSuccess) return e;
   dim3 grid(V / SITES, n_slots);
-  k_block_build_dense<SITES><<<grid, 256, sm, st>>>((const cpx<float>*)prop, V, ell_chunk, ell, tuples, g,
-                                                     (cpx<float>*)blk, n_out);
+  k_block_build_dense<SITES, THREADS><<<grid, THREADS, sm, st>>>((const cpx<float>*)prop, V, ell_chunk, ell,
+                                                                 tuples, g, (cpx<float>*)blk, n_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_block_build_dense(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                      const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st,
-                                     int sites) {
-  if (!dense_build_supported(sites, 256) || V % sites != 0 || g.n_dq < 1 || g.n_dq > kMaxDiquarks ||
+                                     int sites, int threads) {
+  if (!dense_build_supported(sites, threads) || V % sites != 0 || g.n_dq < 1 || g.n_dq > kMaxDiquarks ||
       dense_build_smem(g, sites) > kMaxSmemPerBlock)
     return cudaErrorInvalidValue;
-  if (sites == 1) return launch_dense_variant<1>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
-  return launch_dense_variant<2>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+  if (sites == 1 && threads == 256)
+    return launch_dense_variant<1, 256>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+  if (sites == 1) return launch_dense_variant<1, 512>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+  if (threads == 256)
+    return launch_dense_variant<2, 256>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
+  return launch_dense_variant<2, 512>(prop, V, n_slots, ell_chunk, ell, tuples, g, blk, n_out, st);
 }
 
 size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq) {  // fp64: 8-byte reals (FP64 or double-float)

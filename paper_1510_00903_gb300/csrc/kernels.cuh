@@ -78,12 +78,12 @@ cudaError_t launch_convert(const void* src, int dtype, long long n_complex,
 bool build_variant_supported(int sites, int threads);
 // FP32 blocks from dense entry tuples (dense_build.cpp tables): prop
 // [slots][2][V][144] complex64, blk [slots][V][n_out]; `sites` (1 or 2)
-// consecutive sites per CTA of 256 threads.
+// consecutive sites per CTA of `threads` (256 or 512) threads.
 bool dense_build_supported(int sites, int threads);
 size_t dense_build_smem(const DevGroups& g, int sites);
 cudaError_t launch_block_build_dense(const void* prop, int V, int n_slots, const int2* ell_chunk, const uint32_t* ell,
                                      const uint32_t* tuples, const DevGroups& g, void* blk, int n_out, cudaStream_t st,
-                                     int sites);
+                                     int sites, int threads);
 size_t block_build_smem(int z_slots, int sites, bool fp64, int n_dq);
 // ell_chunk[c] = (offset, length) of 32-row chunk c in ell (lane-interleaved rows).
 cudaError_t launch_block_build(const void* prop, int V, int n_slots, const int2* ell_chunk,

@@ -101,8 +101,8 @@ def test_tuning_defaults_validation_and_autotune_state():
         bbc.bbc_set_tuning(c, 2, 256, 4, 36, 2)  # no workspace yet: host schedule only
         assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 256, "fused_warps": 4, "fused_chunk": 36,
                                          "fused_steps": 2, "pair_groups": 48}
-        # the dense-tuple FP32 build runs one or two sites per CTA of 256 threads
-        for bad in [(3, 256, 8, 18), (1, 512, 8, 18), (4, 256, 8, 18), (2, 512, 8, 18), (4, 512, 8, 18),
+        # the dense-tuple FP32 build runs one or two sites per CTA of 256 or 512 threads
+        for bad in [(3, 256, 8, 18), (4, 256, 8, 18), (4, 512, 8, 18),
                     (1, 256, 10, 18), (1, 256, 8, 20), (1, 256, 8, 18, 2), (1, 256, 4, 18, 3), (1, 256, 16, 18),
                     (1, 256, 12, 18)]:
             with pytest.raises(bbc.BBCError) as e:

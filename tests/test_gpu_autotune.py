@@ -38,8 +38,8 @@ def test_autotune_then_oracle(precision):
     assert all(v > 0 for v in ms[len(BUILD):])
     assert cfg["pair_groups"] in (48, 96, 192, 384)
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
-    if precision != bbc.BBC_FP64:  # the dense-tuple FP32 build runs 1 or 2 sites per CTA of 256 threads
-        assert all(v > 0 for v in ms[:2]) and all(v == -1 for v in ms[2:len(BUILD)])
+    if precision != bbc.BBC_FP64:  # the dense-tuple FP32 build runs 1 or 2 sites per CTA of 256 or 512 threads
+        assert all((v == -1) == (BUILD[i][0] == 4) for i, v in enumerate(ms[:len(BUILD)]))
     # a later context for the same problem starts with the tuned configuration
     cor2 = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     assert cor2.tuning() == cfg
@@ -74,9 +74,8 @@ def test_every_configuration_matches(precision):
                                 "fused_chunk": chunk, "fused_steps": steps, "pair_groups": groups})
             except bbc.BBCError:
                 # FP64: four sites need 365 KB of shared memory; FP32 (dense-tuple
-                # build): one or two sites per CTA of 256 threads
-                assert (precision == bbc.BBC_FP64 and sites == 4) or \
-                    (precision != bbc.BBC_FP64 and (sites, threads) not in ((1, 256), (2, 256)))
+                # build): one or two sites per CTA
+                assert sites == 4
                 continue
             out = cor.run(Sl, Ss, [t])[0].cpu().numpy()
             assert _err(out, want) < tol, (sites, threads, warps, chunk, steps, groups)
@@ -87,5 +86,5 @@ def test_every_configuration_matches(precision):
                     ref = out
                 assert np.array_equal(out, ref)
             tried += 1
-    assert tried == {bbc.BBC_FP64: 16, bbc.BBC_MIXED_FP32: 30, bbc.BBC_MIXED_BF16: 50}[precision]
+    assert tried == {bbc.BBC_FP64: 16, bbc.BBC_MIXED_FP32: 60, bbc.BBC_MIXED_BF16: 100}[precision]
     cor.close()
