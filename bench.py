@@ -89,9 +89,12 @@ def profiled_traffic(path, kernel_src, pair_items):
 
 
 #: diquark kind read by each sink-tensor family (the families' Gamma1 and the
-#: flavours of their first two quarks): (l l) C gamma5, (l s) C gamma5,
-#: (s s) C gamma_1, C gamma_2, C gamma_3
-FAMILY_DIQUARK = [0, 0, 1, 1, 2, 3, 4]
+#: flavours of their first two quarks), in the plan's family order: the four
+#: C gamma5 families on (l l) and (l s), (s s s) with C gamma_1, C gamma_2,
+#: C gamma_3, then per flavour pattern (l l l), (l l s), (l s l), (l s s),
+#: (s s l) the three vector diquarks (l l), (l s) or (s s)
+_SS, _LL, _LS = (2, 3, 4), (5, 6, 7), (8, 9, 10)
+FAMILY_DIQUARK = [0, 0, 1, 1, *_SS, *_LL, *_LL, *_LS, *_LS, *_SS]
 
 
 def plan_counts(plan, sizes):

@@ -317,20 +317,54 @@ cudaError_t launch_build(bbc_ctx* c, int n_slots, int sites, int threads) {
 }
 
 // The tensor-core contraction of one slot: G(q) of every pair {q, -q} on
-// the tensor cores, then the CUDA-core products and the Wick sums.
+// the tensor cores, then the CUDA-core products and the Wick sums.  The
+// pairs are cut into chunks: the tensor-core kernel of chunk k + 1 runs on
+// the context stream while the CUDA-core kernel of chunk k runs on a second
+// stream (forked and joined with events, so a stream capture records the
+// same dependencies); the two kernels fill different pipes of the SMs.
 cudaError_t launch_tc(bbc_ctx* c, int slot) {
   const bbc::Plan& p = c->plan;
   const char* blk = c->d_blk + (size_t)slot * c->V * p.n_out * cplx_bytes(c->prec);
   const int n_q = (int)c->qlist.size();
-  cudaError_t e = bbc::launch_contract_tc(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist, n_q,
-                                          c->d_tc_units, (int)c->tcs.units.size(), c->d_G,
-                                          c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x, c->stream);
-  if (e != cudaSuccess) return e;
-  return bbc::launch_contract_rest(blk, c->lat.L, p.n_out, c->d_row_map, c->tcs.rest.n_out, c->n_slots, c->d_qlist,
-                                   n_q, c->d_tasks, (int)c->tcs.rest.tasks.size(), c->d_batches, c->d_wptr,
-                                   c->d_wunits, c->d_G, c->tcs.nbp * c->tcs.nbp, c->d_tc_cptr, c->d_tc_terms,
-                                   c->d_tc_coefs, (int)c->tcs.coef_values.size(), (int)p.channels.size(), c->d_ct,
-                                   c->tune.fused_warps, c->tune.fused_steps, c->stream);
+  const int g_elems = c->tcs.nbp * c->tcs.nbp;
+  const int mode = c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x;
+  auto tc = [&](int q0, int q1, cudaStream_t st) {
+    return bbc::launch_contract_tc(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist + q0,
+                                   q1 - q0, c->d_tc_units, (int)c->tcs.units.size(),
+                                   c->d_G + (size_t)q0 * g_elems * 8, mode, st);
+  };
+  auto rest = [&](int q0, int q1, cudaStream_t st) {
+    return bbc::launch_contract_rest(blk, c->lat.L, p.n_out, c->d_row_map, c->tcs.rest.n_out, c->n_slots,
+                                     c->d_qlist + q0, q1 - q0, c->d_tasks, (int)c->tcs.rest.tasks.size(),
+                                     c->d_batches, c->d_wptr, c->d_wunits, c->d_G + (size_t)q0 * g_elems * 8, g_elems,
+                                     c->d_tc_cptr, c->d_tc_terms, c->d_tc_coefs, (int)c->tcs.coef_values.size(),
+                                     (int)p.channels.size(), c->d_ct, c->tune.fused_warps, c->tune.fused_steps, st);
+  };
+  constexpr int K = bbc_ctx::kTcChunks;
+  // with fewer pairs (L = 16: 2052) a chunk is about one wave of CTAs and its
+  // tail costs more than the overlap gains (measured): one stream there
+  constexpr int kMinPairs = 4096;
+  cudaError_t e = cudaSuccess;
+  if (n_q >= kMinPairs && !c->side) {  // the second stream and its events, once
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    for (int k = 0; k < K && e == cudaSuccess; k++) e = cudaEventCreateWithFlags(&c->fork[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  if (n_q < kMinPairs) {
+    e = tc(0, n_q, c->stream);
+    return e == cudaSuccess ? rest(0, n_q, c->stream) : e;
+  }
+  for (int k = 0; k < K && e == cudaSuccess; k++) {
+    const int q0 = (int)((long long)n_q * k / K), q1 = (int)((long long)n_q * (k + 1) / K);
+    e = tc(q0, q1, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->fork[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork[k], 0);
+    if (e == cudaSuccess) e = rest(q0, q1, c->side);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->join, 0);
+  return e;
 }
 
 }  // namespace

@@ -99,10 +99,21 @@ struct bbc_ctx {
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[BBC_N_STAGES];
   std::vector<cudaEvent_t> pool;
+  // tensor-core contraction: a second stream and its fork / join events, so
+  // that the CUDA-core half of one chunk of pairs {q, -q} runs beside the
+  // tensor-core half of the next (created on first use)
+  static constexpr int kTcChunks = 4;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork[kTcChunks] = {};
+  cudaEvent_t join = nullptr;
   ~bbc_ctx() {
     for (auto& v : pending)
       for (auto& p : v) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
     for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : fork)
+      if (e) cudaEventDestroy(e);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
