@@ -48,7 +48,10 @@ struct DfRows {
   }
 };
 
-template <int NA, int NB>
+// SWAPPED: t is a 2 x 8 task with its two sides exchanged (see the kernel):
+// product (ra', rb') of the swapped task is product (rb', ra') of the
+// original, and the P pointer is at -q.
+template <int NA, int NB, bool SWAPPED = false>
 __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, long long V, int q, int nq,
                                                  const DevTask& t, cpx<dfr>* __restrict__ P, float4* ring) {
   constexpr int NR = NA + NB;
@@ -94,7 +97,8 @@ __device__ __forceinline__ void task_products_df(const float4* __restrict__ F, l
   for (int i = 0; i < NA * NB; i++) {
     df_renorm(re[i]);
     df_renorm(im[i]);
-    P[(long long)i * V] = cpx<dfr>(dfr(re[i].s, re[i].e), dfr(im[i].s, im[i].e));
+    const int o = SWAPPED ? (i % NB) * NA + i / NB : i;
+    P[(long long)o * V] = cpx<dfr>(dfr(re[i].s, re[i].e), dfr(im[i].s, im[i].e));
   }
 }
 
@@ -115,11 +119,25 @@ k_pair_products_df(const float4* __restrict__ F, int L, const DevTask* __restric
   for (int j = group_ptr[g]; j < j1; j++) {
     const int ti = group_task[j];
     const DevTask t = tasks[ti];
-    cpx<dfr>* p = P + (long long)ti * 16 * V + q;
     const int nA = t.nAnB & 0xff;
-    if (nA == 4) task_products_df<4, 4>(F, V, q, nq, t, p, ring);
-    else if (nA == 2) task_products_df<2, 8>(F, V, q, nq, t, p, ring);
-    else task_products_df<8, 2>(F, V, q, nq, t, p, ring);
+    if (nA == 4) {
+      task_products_df<4, 4>(F, V, q, nq, t, P + (long long)ti * 16 * V + q, ring);
+    } else if (nA == 8) {
+      task_products_df<8, 2>(F, V, q, nq, t, P + (long long)ti * 16 * V + q, ring);
+    } else {
+      // a 2 x 8 task runs on the 8 x 2 code (one unrolled body less): sum_k
+      // B(q; k) A(-q; k) is the task's product at -q, transposed, so the lane
+      // reads B at q and A at -q and stores at -q
+      DevTask s = t;
+      for (int r = 0; r < 8; r++) {
+        s.offA[r] = t.offB[r];
+        s.offB[r] = r < 2 ? t.offA[r] : 0;
+      }
+      s.nAnB = 8 | (2 << 8);
+      s.sA = t.sB;
+      s.sB = t.sA;
+      task_products_df<8, 2, true>(F, V, q, nq, s, P + (long long)ti * 16 * V + nq, ring);
+    }
   }
 }
 
