@@ -285,12 +285,16 @@ bbc_status bbc_set_checks(bbc_ctx* ctx, int flags);
  * of bbc_build_blocks is one persistent launch whose CTAs take (row tile,
  * z plane) and (row tile, z lines) units from a device work queue; a z-lines
  * unit waits for the planes of its row tile, at most about a second, and a
- * wait that gives up sets a sticky device word and stops the launch.
- * bbc_device_status synchronises the context stream and returns
- * BBC_ETIMEOUT if that happened since the last call (the word is cleared and
- * every slot marked unbuilt: its blocks are not valid), else BBC_OK (also
- * without a workspace).  BBC_CHECK_OUTPUT runs the same check in
- * bbc_contract.  Not inside a stream capture. */
+ * wait that gives up sets a sticky device word and stops the launch.  The
+ * tensor-core contraction of the mixed precisions (one persistent CTA per SM,
+ * tcgen05 products committed to mbarriers) bounds its mbarrier waits the
+ * same way and sets another bit of the word.  bbc_device_status synchronises
+ * the context stream and returns BBC_ETIMEOUT if either happened since the
+ * last call (the word is cleared; after an FFT timeout every slot is marked
+ * unbuilt, its blocks not being valid; after a contraction timeout the
+ * correlators of that contraction are not valid), else BBC_OK (also without a
+ * workspace).  BBC_CHECK_OUTPUT runs the same check in bbc_contract.  Not
+ * inside a stream capture. */
 bbc_status bbc_device_status(bbc_ctx* ctx);
 
 /* Self-test of those waits: one queue-driven forward FFT of slot 0's blocks

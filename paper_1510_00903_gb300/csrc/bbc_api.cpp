@@ -289,9 +289,10 @@ double time_launches(bbc_ctx* c, int reps, F launch) {
   return ok && ms >= 0.f ? ms / reps : -1.0;
 }
 
-// Sticky record of the queue-driven forward FFT's bounded waits (synchronous):
-// BBC_ETIMEOUT, the record cleared and every slot marked unbuilt, if a wait
-// gave up since the last read.
+// Sticky record of the bounded device waits (synchronous): BBC_ETIMEOUT, the
+// record cleared, if a wait gave up since the last read -- bit 0: the
+// queue-driven forward FFT (every slot is then marked unbuilt), bit 1: the
+// tensor-core contraction (its correlators are not valid).
 bbc_status wait_status(bbc_ctx* c) {
   int err = 0;
   cudaError_t e = cudaMemcpyAsync(&err, c->d_qerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -301,8 +302,13 @@ bbc_status wait_status(bbc_ctx* c) {
   e = cudaMemsetAsync(c->d_qerr, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "device status");
-  for (auto& b : c->slot_built) b = 0;
-  return fail(c, BBC_ETIMEOUT, "a bounded wait of the queue-driven forward FFT gave up: the blocks are not valid");
+  if (err & 1) {
+    for (auto& b : c->slot_built) b = 0;
+    return fail(c, BBC_ETIMEOUT, "a bounded wait of the queue-driven forward FFT gave up: the blocks are not valid");
+  }
+  return fail(c, BBC_ETIMEOUT,
+              "a bounded wait of the tensor-core contraction gave up: the correlators of the last contraction are not "
+              "valid");
 }
 
 // The block build of slots [0, n_slots): the dense-tuple FP32 kernel, or the
@@ -329,6 +335,10 @@ cudaError_t launch_tc(bbc_ctx* c, int slot) {
   const int g_elems = c->tcs.nbp * c->tcs.nbp;
   const int mode = c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x;
   auto tc = [&](int q0, int q1, cudaStream_t st) {
+    if (c->tc_umma)
+      return bbc::launch_contract_umma(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist + q0,
+                                       q1 - q0, c->d_G + (size_t)q0 * g_elems * 8, mode, c->d_qerr,
+                                       bbc::kFftSpinLimit, st);
     return bbc::launch_contract_tc(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist + q0,
                                    q1 - q0, c->d_tc_units, (int)c->tcs.units.size(),
                                    c->d_G + (size_t)q0 * g_elems * 8, mode, st);

@@ -53,6 +53,9 @@ struct bbc_ctx {
   // and the Wick sums in k_contract_rest; the fused fields above then
   // describe the rest kernel (its tasks, rows and warp units)
   bool tc = false;
+  // the trace-form products on tcgen05 (k_contract_umma, the default) or on
+  // mma.sync (k_contract_tc)
+  bool tc_umma = true;
   bbc::TcSplit tcs;
   // FP32 block build from dense entry tuples (k_block_build_dense)
   bool dense = false;

@@ -479,8 +479,8 @@ static cudaError_t fft_xy_site(void* data, int L, long long n_outer, int n_inner
 // ends: it points at smaller tickets only, all taken by running CTAs, and
 // the smallest unfinished ticket is always a running unit whose own
 // dependencies are done.  It is bounded all the same: after spin_limit polls
-// the CTA sets the sticky word *q.err (cleared only by the host), and no CTA
-// takes a ticket while it is set.
+// the CTA sets bit 0 of the sticky word *q.err (cleared only by the host),
+// and no CTA takes a ticket while that bit is set.
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -561,7 +561,7 @@ k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer
   // plane is on its way meanwhile.  Waits still point only at smaller
   // tickets, so the smallest unfinished ticket always belongs to a unit that
   // is running and whose own dependencies are complete.
-  if (tid == 0) s_next = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
+  if (tid == 0) s_next = (*(volatile int*)q.err & 1) ? -1 : atomicAdd(q.words, 1);
   __syncthreads();
   long long cur = s_next;
   int b = 0;
@@ -569,7 +569,7 @@ k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer
   cp_async_commit();
   __syncthreads();
   while (cur >= 0 && cur < total) {
-    if (tid == 0) s_next = *(volatile int*)q.err ? -1 : atomicAdd(q.words, 1);
+    if (tid == 0) s_next = (*(volatile int*)q.err & 1) ? -1 : atomicAdd(q.words, 1);
     __syncthreads();
     const long long nxt = s_next;
     fetch_plane(nxt, bufs + (b ^ 1) * PLANE);
@@ -615,7 +615,7 @@ k_fft_site_queue(cpx<float>* __restrict__ data, int n_inner, int tiles_per_outer
           long long polls = 0;
           while (ld_acquire_gpu(q.words + 1 + g) < expect) {
             if (++polls > spin_limit) {
-              atomicExch(q.err, 1);
+              atomicOr(q.err, 1);
               ok = 0;
               break;
             }

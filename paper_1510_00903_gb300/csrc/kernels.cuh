@@ -155,6 +155,15 @@ size_t contract_tc_smem(int nbp);
 cudaError_t launch_contract_tc(const void* blk, int L, int n_out, const int* base, int nb, int nbp, const int* qlist,
                                int n_q, const int* units, int n_units, void* G, int mode, cudaStream_t st,
                                int tiles = kTcTilesPerWarp);
+// The same products on the fifth-generation tensor cores (tc_umma.cu): G of
+// every pair, all nbp x nbp entries, from one tcgen05 product per pair with
+// FP32 accumulators in tensor memory; a persistent CTA per SM.  Its mbarrier
+// waits give up after spin_limit polls (about 0.1 us each), set *err = 2 and
+// free the tensor memory.
+size_t contract_umma_smem();
+cudaError_t launch_contract_umma(const void* blk, int L, int n_out, const int* base, int nb, int nbp,
+                                 const int* qlist, int n_q, void* G, int mode, int* err, long long spin_limit,
+                                 cudaStream_t st);
 // The rest of the mixed contraction (fused_contract.cu): per pair {q, -q}
 // the CUDA-core products of the other tasks on compact rows (row_map[i] =
 // block row | shared-memory slot << 16, i < n_rows) and the signed
