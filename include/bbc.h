@@ -320,14 +320,20 @@ bbc_status bbc_check_bounded_wait(bbc_ctx* ctx, long long spin_limit);
  *    (1; or 2 with 8 or 12 warps, which leave the registers for it);
  *  pair_groups (BBC_FP64, BBC_DF64 and the unfused FP32 route): warp task
  *    lists of the block-pair products per 32 q (48, 96, 192 or 384); more,
- *    shorter lists shorten the tail of the launch.
- * A new context starts with (1, 256, 16, 18, 1, 48) (pair_groups 192 for
+ *    shorter lists shorten the tail of the launch;
+ *  tc_kernel (mixed FP32 / TF32 with tensor cores): 0 = the trace-form
+ *    products on tcgen05 (one persistent CTA per SM, then the CUDA-core
+ *    kernel), 1 = on mma.sync, with the CUDA-core kernel of one quarter of
+ *    the pairs beside the tensor-core kernel of the next on a second stream
+ *    from 4096 pairs {q, -q} on.
+ * A new context starts with (1, 256, 16, 18, 1, 48, 0) (pair_groups 192 for
  * BBC_DF64), or with the configuration bbc_autotune chose earlier in the
  * process for the same L, precision and channel list. */
 typedef struct {
   int build_sites, build_threads;
   int fused_warps, fused_chunk, fused_steps;
   int pair_groups;
+  int tc_kernel;
 } bbc_tuning;
 
 bbc_status bbc_get_tuning(const bbc_ctx* ctx, bbc_tuning* out);
@@ -343,8 +349,9 @@ bbc_status bbc_set_tuning(bbc_ctx* ctx, const bbc_tuning* t);
  * propagators loaded in slot 0 -- the block-build candidates in the order
  * above, then (fused kernel) every valid (fused_warps, fused_steps,
  * fused_chunk) in row-major order (warps 8, 12, 16; steps 1, 2; chunks 0, 18,
- * 36, 72, 144), or (otherwise) pair_groups 48, 96, 192, 384 for the block-pair
- * products -- keeps the fastest of each kernel, rebuilds slot 0 with
+ * 36, 72, 144) and then, with tensor cores, tc_kernel 0 and 1, or
+ * (otherwise) pair_groups 48, 96, 192, 384 for the block-pair products --
+ * keeps the fastest of each kernel, rebuilds slot 0 with
  * it, and records it for later contexts with the same L, precision and
  * channel list.  ms[i] (i < cap) receives the average milliseconds per launch
  * of candidate i (-1 for a candidate that is not valid here); *n_tried the

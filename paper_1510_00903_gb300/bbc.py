@@ -74,7 +74,7 @@ class BBCError(RuntimeError):
 class bbc_tuning(ctypes.Structure):
     _fields_ = [("build_sites", ctypes.c_int), ("build_threads", ctypes.c_int),
                 ("fused_warps", ctypes.c_int), ("fused_chunk", ctypes.c_int), ("fused_steps", ctypes.c_int),
-                ("pair_groups", ctypes.c_int)]
+                ("pair_groups", ctypes.c_int), ("tc_kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -319,11 +319,14 @@ def bbc_get_tuning(ctx) -> dict:
 
 
 def bbc_set_tuning(ctx, build_sites: int, build_threads: int, fused_warps: int = 16, fused_chunk: int = 18,
-                   fused_steps: int = 1, pair_groups: int = 0):
-    """pair_groups 0 keeps the context's current value."""
+                   fused_steps: int = 1, pair_groups: int = 0, tc_kernel: int = -1):
+    """pair_groups 0 and tc_kernel -1 keep the context's current values."""
+    cur = bbc_get_tuning(ctx)
     if pair_groups == 0:
-        pair_groups = bbc_get_tuning(ctx)["pair_groups"]
-    t = bbc_tuning(build_sites, build_threads, fused_warps, fused_chunk, fused_steps, pair_groups)
+        pair_groups = cur["pair_groups"]
+    if tc_kernel == -1:
+        tc_kernel = cur["tc_kernel"]
+    t = bbc_tuning(build_sites, build_threads, fused_warps, fused_chunk, fused_steps, pair_groups, tc_kernel)
     _check(ctx, _lib.bbc_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -591,7 +594,7 @@ class Correlators:
 
     def set_tuning(self, cfg: dict):
         bbc_set_tuning(self.ctx, cfg["build_sites"], cfg["build_threads"], cfg["fused_warps"], cfg["fused_chunk"],
-                       cfg.get("fused_steps", 1), cfg.get("pair_groups", 0))
+                       cfg.get("fused_steps", 1), cfg.get("pair_groups", 0), cfg.get("tc_kernel", -1))
 
     def project(self, C, R=None, Ra1=None, a1: bool = True):
         """Spin states |J M> and, with ``a1``, the cubic-group A1 average of

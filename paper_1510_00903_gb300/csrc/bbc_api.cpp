@@ -208,7 +208,7 @@ bool tuning_valid(const bbc_ctx* c, const bbc_tuning& t) {
   if (!bbc::build_variant_supported(t.build_sites, t.build_threads) || c->V % t.build_sites != 0) return false;
   bool groups_ok = false;
   for (int g : kPairGroupsCand) groups_ok |= g == t.pair_groups;
-  if (!groups_ok) return false;
+  if (!groups_ok || (t.tc_kernel != 0 && t.tc_kernel != 1)) return false;
   if (c->dense) {
     if (!bbc::dense_build_supported(t.build_sites, t.build_threads) ||
         bbc::dense_build_smem(bbc::dev_groups(c->plan, &c->db), t.build_sites) > bbc::kMaxSmemPerBlock)
@@ -335,7 +335,7 @@ cudaError_t launch_tc(bbc_ctx* c, int slot) {
   const int g_elems = c->tcs.nbp * c->tcs.nbp;
   const int mode = c->prec == BBC_MIXED_TF32 ? bbc::kTc1x : bbc::kTc3x;
   auto tc = [&](int q0, int q1, cudaStream_t st) {
-    if (c->tc_umma)
+    if (c->tune.tc_kernel == 0)
       return bbc::launch_contract_umma(blk, c->lat.L, p.n_out, c->d_tc_base, c->tcs.nb, c->tcs.nbp, c->d_qlist + q0,
                                        q1 - q0, c->d_G + (size_t)q0 * g_elems * 8, mode, c->d_qerr,
                                        bbc::kFftSpinLimit, st);
@@ -352,9 +352,15 @@ cudaError_t launch_tc(bbc_ctx* c, int slot) {
   };
   constexpr int K = bbc_ctx::kTcChunks;
   // with fewer pairs (L = 16: 2052) a chunk is about one wave of CTAs and its
-  // tail costs more than the overlap gains (measured): one stream there
+  // tail costs more than the overlap gains (measured): one stream there.  The
+  // tcgen05 kernel holds every SM's shared memory, so nothing runs beside it:
+  // one stream for it too.
   constexpr int kMinPairs = 4096;
   cudaError_t e = cudaSuccess;
+  if (c->tune.tc_kernel == 0) {
+    e = tc(0, n_q, c->stream);
+    return e == cudaSuccess ? rest(0, n_q, c->stream) : e;
+  }
   if (n_q >= kMinPairs && !c->side) {  // the second stream and its events, once
     e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     for (int k = 0; k < K && e == cudaSuccess; k++) e = cudaEventCreateWithFlags(&c->fork[k], cudaEventDisableTiming);
@@ -958,6 +964,7 @@ bbc_status bbc_set_tuning(bbc_ctx* c, const bbc_tuning* t) {
   } else {  // and the fused kernel has no pair-product task lists
     want.pair_groups = c->tune.pair_groups;
   }
+  if (!c->tc) want.tc_kernel = c->tune.tc_kernel;  // no tensor-core kernel to choose
   if (!tuning_valid(c, want)) return fail(c, BBC_EINVAL, "unsupported launch configuration");
   const bbc_tuning old = c->tune;
   c->tune = want;
@@ -1033,6 +1040,17 @@ bbc_status bbc_autotune(bbc_ctx* c, int reps, bbc_tuning* best, double* ms, int 
     c->tune.fused_chunk = t.fused_chunk;
     st = apply_fused_units(c);
     if (st != BBC_OK) return st;
+    if (c->tc) {  // the trace-form products: tcgen05 or mma.sync (with its two-stream pipeline)
+      best_ms = -1.0;
+      for (int kv = 0; kv < 2; kv++) {
+        c->tune.tc_kernel = kv;
+        const double v = time_launches(c, reps, [&] { return launch_tc(c, 0); });
+        record(v);
+        if (v < 0) return cuda_fail(c, cudaGetLastError(), "autotune: tensor-core kernel");
+        if (best_ms < 0 || v < best_ms) { best_ms = v; t.tc_kernel = kv; }
+      }
+      c->tune.tc_kernel = t.tc_kernel;
+    }
   } else {  // block-pair products: task lists per 32 q
     const bool fp64 = fp64_storage(c->prec);
     const double* blks = c->d_blks;

@@ -53,9 +53,6 @@ struct bbc_ctx {
   // and the Wick sums in k_contract_rest; the fused fields above then
   // describe the rest kernel (its tasks, rows and warp units)
   bool tc = false;
-  // the trace-form products on tcgen05 (k_contract_umma, the default) or on
-  // mma.sync (k_contract_tc)
-  bool tc_umma = true;
   bbc::TcSplit tcs;
   // FP32 block build from dense entry tuples (k_block_build_dense)
   bool dense = false;
@@ -70,7 +67,7 @@ struct bbc_ctx {
   uint2* d_tc_terms = nullptr;           // [terms] (source q | source -q << 16, coefficient index)
   float2* d_tc_coefs = nullptr;          // [distinct coefficients] (hi, lo)
   char* d_G = nullptr;                   // [pairs][nbp][nbp] complex64
-  bbc_tuning tune{1, 256, 16, 18, 1, 48};
+  bbc_tuning tune{1, 256, 16, 18, 1, 48, 0};
   size_t max_units = 0;                  // warp units the workspace holds (largest chunk candidate)
   std::vector<int> row_slot;             // shared-memory slot of every block row (bank layout)
   int n_slots = 0;

@@ -28,7 +28,7 @@
 // (core matrices of 8 rows x 16 bytes) in one of two shared-memory stages,
 // and one thread issues the unit's MMAs and commits them to the stage's
 // mbarrier, so that the loads of the next unit overlap the MMAs of this one.
-// The rows of the next pair are prefetched into L2 by bulk prefetches.  Two
+// The rows of the pair after next are prefetched into L2 by bulk prefetches.  Two
 // accumulators in tensor memory let the epilogue of a pair (tensor memory to
 // registers to G, the Xi rows handed to the Xr rows through shared memory)
 // run two units after the pair's last MMA, while the next pair is
@@ -51,23 +51,17 @@ constexpr int kUmLbo = 128;                   // bytes between core matrices adj
 constexpr int kUmSbo = kUmKg * 128;           // bytes between 8-row groups
 constexpr int kUmBuf = 128 / 8 * kUmSbo;      // one operand buffer of 128 rows (24 KB)
 constexpr int kUmStage = 4 * kUmBuf;          // A hi, A lo, B hi, B lo
-constexpr int kUmWarps = 12;
-constexpr int kUmMaxTasks = 4;                // warp tasks per unit and warp: 6 nbp / 8 <= 48 over 12 warps
+constexpr int kUmWarps = 8;                   // warps 4..7 also run the epilogue (tensor-memory lanes 32 (w - 4) ..)
+constexpr int kUmMaxTasks = 6;                // warp tasks per unit and warp: 6 nbp / 8 <= 48 over 8 warps
 constexpr int kUmXld = kMaxTcBlocks + 4;      // row stride (floats) of the epilogue exchange
 constexpr int kUmXch = 2 * kMaxTcBlocks * kUmXld * 4;
 constexpr int kUmCols = 256;                  // tensor-memory columns: two accumulators of up to 128
-constexpr size_t kUmSmem = 2 * (size_t)kUmStage + kUmXch + 64;
+constexpr size_t kUmSmem = 2 * (size_t)kUmStage + kUmXch + 64 + 4 * kMaxTcBlocks;
 static_assert(kUmSmem <= kMaxSmemPerBlock, "two stages and the exchange fit one CTA");
 static_assert(6 * (kMaxTcBlocks / 8) <= kUmMaxTasks * kUmWarps, "every warp task has a warp");
 static_assert(2 * kMaxTcBlocks <= 128, "A fits the M = 128 instruction");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
 
 // Shared-memory matrix descriptor of tcgen05: start address, leading byte
 // offset (core matrices adjacent in K), stride byte offset (8-row groups),
@@ -146,11 +140,95 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[16]) {
 // byte offset of (row, 16-byte k-group) in an operand buffer
 __device__ __forceinline__ int umma_off(int row, int kg) { return (row >> 3) * kUmSbo + kg * kUmLbo + (row & 7) * 16; }
 
-// x = hi + lo: hi the nearest TF32 value, lo the FP32 rest
+// x = hi + lo: hi the nearest TF32 value (ties away from zero: the 13 low
+// mantissa bits rounded into the rest of the magnitude), lo the FP32 rest
 __device__ __forceinline__ void split4(float a, float b, float c, float d, uint4& hi, float4& lo) {
-  hi = make_uint4(tf32_rna(a), tf32_rna(b), tf32_rna(c), tf32_rna(d));
+  hi = make_uint4((__float_as_uint(a) + 0x1000u) & 0xffffe000u, (__float_as_uint(b) + 0x1000u) & 0xffffe000u,
+                  (__float_as_uint(c) + 0x1000u) & 0xffffe000u, (__float_as_uint(d) + 0x1000u) & 0xffffe000u);
   lo = make_float4(a - __uint_as_float(hi.x), b - __uint_as_float(hi.y), c - __uint_as_float(hi.z),
                    d - __uint_as_float(hi.w));
+}
+
+// A thread's warp tasks, fixed for the whole launch: task t of warp w is T
+// = w + 8 t = (side, 8-row group rg, h) and lane = (row in the group bl, u
+// offset ul), block b = 8 rg + bl.  Side X reads M_b(q)[u][4h .. 4h + 3] (32
+// bytes), side Y M_b(-q)[4h .. 4h + 3][u] (four 8-byte values 96 bytes
+// apart): both the 4 consecutive open indices k = 12 u + 4h .. 12 u + 4h + 3,
+// u = 4 c + ul in unit c.  Packed per task: the row offset of the pair's
+// first unit (bits 0..15), the stage offset / 16 of the real part (bits
+// 16..28), side (bit 29), b < nb (bit 30).
+template <int MAXT>
+struct UmRows {
+  float4 v[MAXT][2];
+};
+
+template <int MAXT>
+__device__ __forceinline__ void um_tasks(uint32_t (&tk)[MAXT], const int* s_base, int nb, int nrg, int n_tasks,
+                                         int warp, int bl, int ul) {
+#pragma unroll
+  for (int t = 0; t < MAXT; t++) {
+    const int T = warp + t * kUmWarps;
+    tk[t] = 0;
+    if (T < n_tasks) {
+      const bool side = T >= 3 * nrg;
+      const int rem = side ? T - 3 * nrg : T, rg = rem / 3, h = rem - 3 * rg, b = 8 * rg + bl;
+      const int soff = umma_off(b, 3 * ul + h) + (side ? 2 * kUmBuf : 0);
+      const int goff = b < nb ? s_base[b] + (side ? 48 * h + ul : 12 * ul + 4 * h) : 0;
+      tk[t] = (uint32_t)goff | ((uint32_t)(soff >> 4) << 16) | ((uint32_t)side << 29) | ((uint32_t)(b < nb) << 30);
+    }
+  }
+}
+
+template <int MAXT>
+__device__ __forceinline__ void um_load(UmRows<MAXT>& R, const uint32_t (&tk)[MAXT], const float2* rq,
+                                        const float2* rmq, int c, int n_tasks, int warp) {
+#pragma unroll
+  for (int t = 0; t < MAXT; t++) {
+    R.v[t][0] = R.v[t][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (warp + t * kUmWarps < n_tasks && (tk[t] >> 30)) {
+      const int goff = (int)(tk[t] & 0xffffu);
+      if (!((tk[t] >> 29) & 1u)) {
+        const float4* src = reinterpret_cast<const float4*>(rq + goff + 48 * c);
+        R.v[t][0] = __ldg(src);
+        R.v[t][1] = __ldg(src + 1);
+      } else {
+        const float2* src = rmq + goff + 4 * c;
+        const float2 y0 = __ldg(src), y1 = __ldg(src + 12), y2 = __ldg(src + 24), y3 = __ldg(src + 36);
+        R.v[t][0] = make_float4(y0.x, y0.y, y1.x, y1.y);
+        R.v[t][1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+      }
+    }
+  }
+}
+
+// the unit's rows, split, into a stage: real parts to rows b, imaginary
+// parts to rows nbp + b (nrg 8-row groups further) of A (side X) or B (side Y)
+template <int MODE, int MAXT>
+__device__ __forceinline__ void um_store(const UmRows<MAXT>& R, const uint32_t (&tk)[MAXT], unsigned char* st,
+                                         int nrg, int n_tasks, int warp) {
+#pragma unroll
+  for (int t = 0; t < MAXT; t++) {
+    if (warp + t * kUmWarps < n_tasks) {
+      unsigned char* dst = st + (((tk[t] >> 16) & 0x1fffu) << 4);
+      const float4 a = R.v[t][0], d = R.v[t][1];
+      uint4 hre, him;
+      float4 lre, lim;
+      split4(a.x, a.z, d.x, d.z, hre, lre);
+      split4(a.y, a.w, d.y, d.w, him, lim);
+      const int oim = nrg * kUmSbo;
+      *reinterpret_cast<uint4*>(dst) = hre;
+      *reinterpret_cast<uint4*>(dst + oim) = him;
+      if (MODE == kTc3x) {
+        *reinterpret_cast<float4*>(dst + kUmBuf) = lre;
+        *reinterpret_cast<float4*>(dst + kUmBuf + oim) = lim;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int neg_site(int q, int L) {
+  const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
+  return (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
 }
 
 }  // namespace
@@ -158,7 +236,7 @@ __device__ __forceinline__ void split4(float a, float b, float c, float d, uint4
 // blk: q-major blocks [V][n_out] complex64; base[nb]: first row of each block
 // (even); qlist[n_q]: q of each pair; G[n_q][nbp][nbp] complex64 (all
 // entries written); err: set to 2 when a wait gave up.  Grid <= n_q.
-template <int MODE>
+template <int MODE, int MAXT>
 __global__ void __launch_bounds__(kUmWarps * 32, 1)
 k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __restrict__ base, int nb, int nbp,
                 const int* __restrict__ qlist, int n_q, float2* __restrict__ G, int* __restrict__ err,
@@ -167,6 +245,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   float* xch = reinterpret_cast<float*>(smem + 2 * kUmStage);  // [2][nbp][kUmXld]: Xi Yr^T, Xi Yi^T
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kUmStage + kUmXch);  // stages 0, 1; accumulators 0, 1
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 4);
+  int* s_base = reinterpret_cast<int*>(bars + 8);  // [nb]: first row of each block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_mine = (n_q - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
   const int n_units = n_mine * kUmUnits;
@@ -175,6 +254,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
     for (int i = 0; i < 4; i++) mbar_init(bar0 + 8 * i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int b = tid; b < nb; b += blockDim.x) s_base[b] = base[b];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(kUmCols)
@@ -187,68 +267,55 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tslot);
   const int nrg = nbp >> 3, n_tasks = 6 * nrg, n2 = 2 * nbp;
   const uint32_t idesc = umma_idesc_tf32(128, n2);
-  const int bl = lane & 7, ul = lane >> 3;
+  uint32_t tk[MAXT];
+  um_tasks<MAXT>(tk, s_base, nb, nrg, n_tasks, warp, lane & 7, lane >> 3);
   int issued = -1;   // last unit whose MMAs thread 0 issued
   bool bad = false;  // this thread saw a wait give up
   bool aborted = false;
-  for (int u = 0; u <= n_units + 1; u++) {
-    const int i = u / kUmUnits, c = u - kUmUnits * i, s = u & 1;
-    // (1) loads of unit u: warp task T = (side, 8-row group, h), lane = (row in
-    // group, u offset); X rows of 4 consecutive k in 32 bytes, Y columns of 4
-    // consecutive k from 4 rows of M(-q)
-    float4 ld[kUmMaxTasks][2];
-    if (u < n_units) {
-      const int q = qlist[blockIdx.x + (size_t)i * gridDim.x];
-      const int qx = q % L, qy = (q / L) % L, qz = q / (L * L);
-      const int nq = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
-      const float2* rq = blk + (size_t)q * n_out;
-      const float2* rmq = blk + (size_t)nq * n_out;
-      const int uu = 4 * c + ul;
-#pragma unroll
-      for (int t = 0; t < kUmMaxTasks; t++) {
-        const int T = warp + t * kUmWarps;
-        ld[t][0] = ld[t][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (T < n_tasks) {
-          const bool side = T >= 3 * nrg;
-          const int rem = side ? T - 3 * nrg : T, rg = rem / 3, h = rem - 3 * rg, b = 8 * rg + bl;
-          if (b < nb) {
-            if (!side) {
-              const float4* src = reinterpret_cast<const float4*>(rq + base[b] + 12 * uu + 4 * h);
-              ld[t][0] = __ldg(src);
-              ld[t][1] = __ldg(src + 1);
-            } else {
-              const float2* src = rmq + base[b] + 48 * h + uu;
-              const float2 y0 = __ldg(src), y1 = __ldg(src + 12), y2 = __ldg(src + 24), y3 = __ldg(src + 36);
-              ld[t][0] = make_float4(y0.x, y0.y, y1.x, y1.y);
-              ld[t][1] = make_float4(y2.x, y2.y, y3.x, y3.y);
-            }
-          }
-        }
-      }
-      // the next pair's rows into L2 while this pair is multiplied
-      if (c == 0 && i + 1 < n_mine && tid < n2) {
-        const int q1 = qlist[blockIdx.x + (size_t)(i + 1) * gridDim.x];
-        int qs = q1;
-        if (tid >= nbp) {
-          const int qx = q1 % L, qy = (q1 / L) % L, qz = q1 / (L * L);
-          qs = (L - qx) % L + L * ((L - qy) % L + L * ((L - qz) % L));
-        }
-        const int b = tid >= nbp ? tid - nbp : tid;
-        if (b < nb)
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blk + (size_t)qs * n_out + base[b]),
-                       "r"(144 * 8)
-                       : "memory");
-      }
+  // the loader runs one unit ahead of the stores: rows of the pair being
+  // loaded, and the q of the pair after it (read a pair ahead)
+  int q_next = qlist[blockIdx.x];
+  const float2 *lrq = blk, *lrmq = blk;
+  // bulk prefetches of a pair's rows into L2, two pairs ahead of the loads:
+  // thread t < nbp the X row of block t at q, thread nbp + t the Y row at -q
+  int q_pf = -1;
+  auto prefetch_rows = [&](int qp) {
+    const int b = tid >= nbp ? tid - nbp : tid;
+    const int qs = tid >= nbp ? neg_site(qp, L) : qp;
+    if (b < nb)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(blk + (size_t)qs * n_out + s_base[b]),
+                   "r"(144 * 8)
+                   : "memory");
+  };
+  if (tid < n2 && n_mine > 1) prefetch_rows(qlist[blockIdx.x + gridDim.x]);
+  auto load_unit = [&](int w, UmRows<MAXT>& R) {
+    const int j = w / kUmUnits, cw = w - kUmUnits * j;
+    if (cw == 0) {
+      lrq = blk + (size_t)q_next * n_out;
+      lrmq = blk + (size_t)neg_site(q_next, L) * n_out;
+      if (j + 1 < n_mine) q_next = qlist[blockIdx.x + (size_t)(j + 1) * gridDim.x];
     }
-    // (2) the epilogue of pair e = (u - 4) / 3, two units after its last MMA
-    // (warps 0..3: warp w reads tensor-memory lanes 32 w .. 32 w + 31 = rows of D)
-    if (warp < 4 && u >= kUmUnits + 1 && (u - kUmUnits - 1) % kUmUnits == 0) {
+    um_load<MAXT>(R, tk, lrq, lrmq, cw, n_tasks, warp);
+  };
+  // one unit: loads of unit u + 1 issued first, then (warps 4..7) the
+  // epilogue of pair (u - 4) / 3, then unit u into stage u & 1 once the MMAs
+  // of unit u - 2 have read it, then one barrier and the MMAs of unit u
+  auto step = [&](int u, const UmRows<MAXT>& cur, UmRows<MAXT>& nxt) -> bool {
+    if (u > n_units + 1) return false;
+    const int i = u / kUmUnits, c = u - kUmUnits * i, s = u & 1;
+    if (u + 1 < n_units) load_unit(u + 1, nxt);
+    // the rows of the pair after next into L2 (its q read one unit earlier)
+    if (tid < n2 && u < n_units) {
+      if (c == 0) q_pf = i + 2 < n_mine ? qlist[blockIdx.x + (size_t)(i + 2) * gridDim.x] : -1;
+      if (c == 1 && q_pf >= 0) prefetch_rows(q_pf);
+    }
+    if (warp >= 4 && u >= kUmUnits + 1 && (u - kUmUnits - 1) % kUmUnits == 0) {
       const int e = (u - kUmUnits - 1) / kUmUnits;
       bool ok = mbar_wait(bar0 + 8 * (2 + (e & 1)), (uint32_t)((e >> 1) & 1), spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) bad = true;
       tc_fence_after();
-      const int r0 = 32 * warp, r = r0 + lane;
+      const int r0 = 32 * (warp - 4), r = r0 + lane;
       const uint32_t tw = tmem + ((uint32_t)r0 << 16) + (uint32_t)((e & 1) * 128);
       if (ok && r0 + 32 > nbp && r0 < n2) {  // this warp holds Xi rows: to the exchange
         for (int c0 = 0; c0 < n2; c0 += 16) {
@@ -287,35 +354,10 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
       }
       tc_fence_before();
     }
-    // (3) unit u into stage s, once the MMAs of unit u - 2 have read it
     if (u < n_units) {
-      bool ok = u < 2 || mbar_wait(bar0 + 8 * s, (uint32_t)(((u - 2) >> 1) & 1), spin_limit);
+      const bool ok = u < 2 || mbar_wait(bar0 + 8 * s, (uint32_t)(((u - 2) >> 1) & 1), spin_limit);
       if (!ok) bad = true;
-      if (ok) {
-        unsigned char* st = smem + (size_t)s * kUmStage;
-#pragma unroll
-        for (int t = 0; t < kUmMaxTasks; t++) {
-          const int T = warp + t * kUmWarps;
-          if (T < n_tasks) {
-            const bool side = T >= 3 * nrg;
-            const int rem = side ? T - 3 * nrg : T, rg = rem / 3, h = rem - 3 * rg, b = 8 * rg + bl;
-            const int kg = 3 * ul + h;
-            unsigned char* hi_buf = st + (side ? 2 * kUmBuf : 0);
-            const float4 a = ld[t][0], d = ld[t][1];
-            uint4 hre, him;
-            float4 lre, lim;
-            split4(a.x, a.z, d.x, d.z, hre, lre);  // real parts of 4 consecutive k
-            split4(a.y, a.w, d.y, d.w, him, lim);  // imaginary parts
-            const int ore = umma_off(b, kg), oim = umma_off(nbp + b, kg);
-            *reinterpret_cast<uint4*>(hi_buf + ore) = hre;
-            *reinterpret_cast<uint4*>(hi_buf + oim) = him;
-            if (MODE == kTc3x) {
-              *reinterpret_cast<float4*>(hi_buf + kUmBuf + ore) = lre;
-              *reinterpret_cast<float4*>(hi_buf + kUmBuf + oim) = lim;
-            }
-          }
-        }
-      }
+      if (ok) um_store<MODE, MAXT>(cur, tk, smem + (size_t)s * kUmStage, nrg, n_tasks, warp);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     tc_fence_before();
@@ -323,9 +365,9 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
     tc_fence_after();
     if (any_bad) {
       aborted = true;
-      break;
+      return false;
     }
-    // (4) the MMAs of unit u: D(pair i) += A B^T over the unit's 48 open indices
+    // D(pair i) += A B^T over the unit's 48 open indices
     if (tid == 0 && u < n_units) {
       const uint32_t sa = smem_u32(smem + (size_t)s * kUmStage);
       const uint32_t d = tmem + (uint32_t)((i & 1) * 128);
@@ -347,6 +389,13 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
       if (c == kUmUnits - 1) umma_commit(bar0 + 8 * (2 + (i & 1)));
       issued = u;
     }
+    return true;
+  };
+  UmRows<MAXT> ra, rb;
+  load_unit(0, ra);
+  for (int u = 0;; u += 2) {
+    if (!step(u, ra, rb)) break;
+    if (!step(u + 1, rb, ra)) break;
   }
   // after a wait gave up: the record, and the MMAs in flight finish before
   // the tensor memory is freed
@@ -362,16 +411,31 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
 
 size_t contract_umma_smem() { return kUmSmem; }
 
-template <int MODE>
+template <int MODE, int MAXT>
 static cudaError_t launch_umma_variant(int grid, cudaStream_t st, const void* blk, int L, int n_out, const int* base,
                                        int nb, int nbp, const int* qlist, int n_q, void* G, int* err,
                                        long long spin_limit) {
   static int granted[64] = {0};
-  cudaError_t e = ensure_smem(k_contract_umma<MODE>, kUmSmem, granted);
+  cudaError_t e = ensure_smem(k_contract_umma<MODE, MAXT>, kUmSmem, granted);
   if (e != cudaSuccess) return e;
-  k_contract_umma<MODE><<<grid, kUmWarps * 32, kUmSmem, st>>>((const float2*)blk, L, n_out, base, nb, nbp, qlist,
-                                                             n_q, (float2*)G, err, spin_limit);
+  k_contract_umma<MODE, MAXT><<<grid, kUmWarps * 32, kUmSmem, st>>>((const float2*)blk, L, n_out, base, nb, nbp,
+                                                                   qlist, n_q, (float2*)G, err, spin_limit);
   return cudaGetLastError();
+}
+
+// warp tasks per warp: 6 nbp / 8 tasks over the 8 warps
+template <int MODE>
+static cudaError_t launch_umma_mode(int grid, cudaStream_t st, const void* blk, int L, int n_out, const int* base,
+                                    int nb, int nbp, const int* qlist, int n_q, void* G, int* err, long long spin_limit) {
+  const int maxt = (6 * (nbp / 8) + kUmWarps - 1) / kUmWarps;
+  if (maxt <= 2)
+    return launch_umma_variant<MODE, 2>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
+  if (maxt <= 3)
+    return launch_umma_variant<MODE, 3>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
+  if (maxt <= 5)
+    return launch_umma_variant<MODE, 5>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
+  return launch_umma_variant<MODE, kUmMaxTasks>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err,
+                                                spin_limit);
 }
 
 cudaError_t launch_contract_umma(const void* blk, int L, int n_out, const int* base, int nb, int nbp,
@@ -391,9 +455,9 @@ cudaError_t launch_contract_umma(const void* blk, int L, int n_out, const int* b
   }
   const int grid = n_q < n_sm[dev] ? n_q : n_sm[dev];  // one CTA per SM (shared memory), each with >= 1 pair
   if (mode == kTc3x)
-    return launch_umma_variant<kTc3x>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
+    return launch_umma_mode<kTc3x>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
   if (mode == kTc1x)
-    return launch_umma_variant<kTc1x>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
+    return launch_umma_mode<kTc1x>(grid, st, blk, L, n_out, base, nb, nbp, qlist, n_q, G, err, spin_limit);
   return cudaErrorInvalidValue;
 }
 

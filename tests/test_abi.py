@@ -97,10 +97,17 @@ def test_tuning_defaults_validation_and_autotune_state():
     f = bbc.bbc_create(8, 4, 0, 0.3, 0.4, bbc.BBC_FP64, [0, 1])
     try:
         assert bbc.bbc_get_tuning(c) == {"build_sites": 1, "build_threads": 256, "fused_warps": 8, "fused_chunk": 18,
-                                         "fused_steps": 1, "pair_groups": 48}
+                                         "fused_steps": 1, "pair_groups": 48, "tc_kernel": 0}
         bbc.bbc_set_tuning(c, 2, 256, 4, 36, 2)  # no workspace yet: host schedule only
         assert bbc.bbc_get_tuning(c) == {"build_sites": 2, "build_threads": 256, "fused_warps": 4, "fused_chunk": 36,
-                                         "fused_steps": 2, "pair_groups": 48}
+                                         "fused_steps": 2, "pair_groups": 48, "tc_kernel": 0}
+        # the trace-form products on mma.sync (1) or tcgen05 (0); nothing else
+        bbc.bbc_set_tuning(c, 2, 256, 4, 36, 2, tc_kernel=1)
+        assert bbc.bbc_get_tuning(c)["tc_kernel"] == 1
+        with pytest.raises(bbc.BBCError) as e:
+            bbc.bbc_set_tuning(c, 2, 256, 4, 36, 2, tc_kernel=2)
+        assert e.value.status == bbc.BBC_EINVAL
+        bbc.bbc_set_tuning(c, 2, 256, 4, 36, 2, tc_kernel=0)
         # the dense-tuple FP32 build runs one or two sites per CTA of 256 or 512 threads
         for bad in [(3, 256, 8, 18), (4, 256, 8, 18), (4, 512, 8, 18),
                     (1, 256, 10, 18), (1, 256, 8, 20), (1, 256, 8, 18, 2), (1, 256, 4, 18, 3), (1, 256, 16, 18),
@@ -110,7 +117,9 @@ def test_tuning_defaults_validation_and_autotune_state():
             assert e.value.status == bbc.BBC_EINVAL, bad
         assert bbc.bbc_get_tuning(c)["fused_chunk"] == 36  # a rejected set leaves the configuration
         assert bbc.bbc_get_tuning(b) == {"build_sites": 1, "build_threads": 256, "fused_warps": 16, "fused_chunk": 18,
-                                         "fused_steps": 1, "pair_groups": 48}
+                                         "fused_steps": 1, "pair_groups": 48, "tc_kernel": 0}
+        bbc.bbc_set_tuning(b, 1, 256, 16, 18, 1, tc_kernel=1)  # no tensor-core kernel here: ignored
+        assert bbc.bbc_get_tuning(b)["tc_kernel"] == 0
         bbc.bbc_set_tuning(b, 2, 256, 12, 36, 2)
         for bad in [(1, 256, 16, 18, 2), (1, 256, 8, 18, 3), (1, 256, 4, 18)]:
             with pytest.raises(bbc.BBCError) as e:

@@ -32,11 +32,13 @@ def test_autotune_then_oracle(precision):
     cor = bbc.Correlators(L, T, 0, 0.3, 0.4, channels=chans, precision=precision, device=dev)
     cfg, ms = cor.autotune(Sl[0], Ss[0], t=0, reps=2)
     # FP64: four pair_groups candidates; mixed (tensor cores): the CUDA-core
-    # kernel's (warps, steps) shapes x 5 chunks
-    n_second = 4 if precision == bbc.BBC_FP64 else 15
+    # kernel's (warps, steps) shapes x 5 chunks, then the tcgen05 and the
+    # mma.sync tensor-core kernels
+    n_second = 4 if precision == bbc.BBC_FP64 else 15 + 2
     assert len(ms) == len(BUILD) + n_second
     assert all(v > 0 for v in ms[len(BUILD):])
     assert cfg["pair_groups"] in (48, 96, 192, 384)
+    assert cfg["tc_kernel"] in (0, 1)
     assert (cfg["build_sites"], cfg["build_threads"]) in BUILD
     if precision != bbc.BBC_FP64:  # the dense-tuple FP32 build runs 1 or 2 sites per CTA of 256 or 512 threads
         assert all((v == -1) == (BUILD[i][0] == 4) for i, v in enumerate(ms[:len(BUILD)]))
