@@ -350,18 +350,31 @@ k_fft3split(const cpx<S>* __restrict__ in, cpx<O>* __restrict__ out, long long n
       }
     }
     __syncthreads();
-    const long long g0 = blockIdx.x * (long long)kSplitLines;
-    for (int e = threadIdx.x; e < kSplitLines * N; e += 3 * kSplitLines) {
-      const int l = e / N, k = e - l * N;
-      const long long gl = g0 + l;
-      if (gl >= n_outer * lines * n_inner) break;  // e grows with l: the rest is past the end too
-      const int inn = (int)(gl % n_inner);
-      const long long rst = gl / n_inner;
-      const int ln = (int)(rst % lines);
-      const long long oo = rst / lines;
+    // thread t stores point k = t mod N of lines t / N, t / N + kStep, ...
+    // (the CTA's 3 x 64 threads = kStep whole lines per round); the line's
+    // (outer, row, line) decomposition is carried from one of its lines to
+    // the next by additions, not recomputed with 64-bit divisions per point
+    constexpr int kStep = 3 * kSplitLines / N;
+    static_assert(kStep * N == 3 * kSplitLines, "whole lines per round of stores");
+    const long long total = n_outer * lines * n_inner;
+    const int k = threadIdx.x % N, kj = k / M, kk = k % M;
+    int l = threadIdx.x / N;
+    long long gl = blockIdx.x * (long long)kSplitLines + l;
+    int inn = (int)(gl % n_inner), ln = (int)((gl / n_inner) % lines);
+    long long oo = gl / n_inner / lines;
+    for (; l < kSplitLines && gl < total; l += kStep) {  // lines past the end come last
       int b = 0, sd = 0;
       line_base(N, axis, ln, b, sd);
-      out[(oo * n_inner + inn) * V + b + (long long)k * sd] = cpx<O>(at(l, k / M, k % M));
+      out[(oo * n_inner + inn) * V + b + (long long)k * sd] = cpx<O>(at(l, kj, kk));
+      gl += kStep;
+      inn += kStep;
+      while (inn >= n_inner) {
+        inn -= n_inner;
+        if (++ln == lines) {
+          ln = 0;
+          ++oo;
+        }
+      }
     }
     return;
   }
