@@ -4,8 +4,10 @@ FP64 path (pinned to the oracle elsewhere): the trace-form products on tcgen05
 mma.sync (tc_kernel 1, whose CUDA-core kernel runs beside it on a second
 stream from 4096 pairs {q, -q} on).  L = 8 is one wave of pairs; L = 24
 (13824 sites) takes the two-stream pipeline in four chunks and gives the
-persistent kernel many pairs per CTA.  Both kernels compute the same G up to
-the order of FP32 accumulation.
+persistent kernel many pairs per CTA.  The channel lists give G of 12, 24,
+48 and 52 blocks (padded to 16, 32, 48 and 64: every warp-task count of the
+tcgen05 kernel, and N = 128 with no unstaged rows of A).  Both kernels compute
+the same G up to the order of FP32 accumulation.
 """
 import numpy as np
 import pytest
@@ -27,7 +29,8 @@ def _err(got, want):
     return (np.abs(got - want) / scale).max()
 
 
-@pytest.mark.parametrize("L,chans", [(8, list(range(52))), (24, [0, 10, 27, 51])])
+@pytest.mark.parametrize("L,chans", [(8, list(range(52))), (24, [0, 10, 27, 51]), (8, [0]), (8, [1]),
+                                     (8, list(range(52)) + [154])])
 def test_both_tensor_core_kernels_match_fp64(L, chans):
     dev = torch.device("cuda", torch.cuda.current_device())
     T, t = 4, 2
