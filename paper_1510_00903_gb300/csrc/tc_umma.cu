@@ -39,13 +39,15 @@
 
 #include "device_common.cuh"
 #include "kernels.cuh"
+#include "umma_schedule.hpp"
 
 namespace bbc {
 
 namespace {
 
 constexpr int kUmK = 48;                      // open indices per unit (four values of u)
-constexpr int kUmUnits = 144 / kUmK;          // units per pair
+constexpr int kUmUnits = umsched::kUnitsPerPair;  // units per pair
+static_assert(kUmUnits * kUmK == 144, "the units of a pair cover its open indices");
 constexpr int kUmKg = kUmK / 4;               // 16-byte k-groups of one operand row in a unit
 constexpr int kUmLbo = 128;                   // bytes between core matrices adjacent in K
 constexpr int kUmSbo = kUmKg * 128;           // bytes between 8-row groups
@@ -248,7 +250,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   int* s_base = reinterpret_cast<int*>(bars + 8);  // [nb]: first row of each block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n_mine = (n_q - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
-  const int n_units = n_mine * kUmUnits;
+  const int n_units = umsched::n_units(n_mine);
   const uint32_t bar0 = smem_u32(bars);
   if (tid == 0) {
     for (int i = 0; i < 4; i++) mbar_init(bar0 + 8 * i, 1);
@@ -289,7 +291,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   };
   if (tid < n2 && n_mine > 1) prefetch_rows(qlist[blockIdx.x + gridDim.x]);
   auto load_unit = [&](int w, UmRows<MAXT>& R) {
-    const int j = w / kUmUnits, cw = w - kUmUnits * j;
+    const int j = umsched::pair_of(w), cw = umsched::chunk_of(w);
     if (cw == 0) {
       lrq = blk + (size_t)q_next * n_out;
       lrmq = blk + (size_t)neg_site(q_next, L) * n_out;
@@ -301,22 +303,22 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   // epilogue of pair (u - 4) / 3, then unit u into stage u & 1 once the MMAs
   // of unit u - 2 have read it, then one barrier and the MMAs of unit u
   auto step = [&](int u, const UmRows<MAXT>& cur, UmRows<MAXT>& nxt) -> bool {
-    if (u > n_units + 1) return false;
-    const int i = u / kUmUnits, c = u - kUmUnits * i, s = u & 1;
+    if (u > umsched::last_step(n_mine)) return false;
+    const int i = umsched::pair_of(u), c = umsched::chunk_of(u), s = umsched::stage(u);
     if (u + 1 < n_units) load_unit(u + 1, nxt);
     // the rows of the pair after next into L2 (its q read one unit earlier)
     if (tid < n2 && u < n_units) {
       if (c == 0) q_pf = i + 2 < n_mine ? qlist[blockIdx.x + (size_t)(i + 2) * gridDim.x] : -1;
       if (c == 1 && q_pf >= 0) prefetch_rows(q_pf);
     }
-    if (warp >= 4 && u >= kUmUnits + 1 && (u - kUmUnits - 1) % kUmUnits == 0) {
-      const int e = (u - kUmUnits - 1) / kUmUnits;
-      bool ok = mbar_wait(bar0 + 8 * (2 + (e & 1)), (uint32_t)((e >> 1) & 1), spin_limit);
+    if (warp >= 4 && umsched::is_epilogue_step(u)) {
+      const int e = umsched::epilogue_pair(u);
+      bool ok = mbar_wait(bar0 + 8 * (2 + umsched::acc(e)), umsched::acc_parity(e), spin_limit);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) bad = true;
       tc_fence_after();
       const int r0 = 32 * (warp - 4), r = r0 + lane;
-      const uint32_t tw = tmem + ((uint32_t)r0 << 16) + (uint32_t)((e & 1) * 128);
+      const uint32_t tw = tmem + ((uint32_t)r0 << 16) + (uint32_t)(umsched::acc(e) * 128);
       if (ok && r0 + 32 > nbp && r0 < n2) {  // this warp holds Xi rows: to the exchange
         for (int c0 = 0; c0 < n2; c0 += 16) {
           uint32_t v[16];
@@ -355,7 +357,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
       tc_fence_before();
     }
     if (u < n_units) {
-      const bool ok = u < 2 || mbar_wait(bar0 + 8 * s, (uint32_t)(((u - 2) >> 1) & 1), spin_limit);
+      const bool ok = !umsched::stage_waits(u) || mbar_wait(bar0 + 8 * s, umsched::stage_parity(u), spin_limit);
       if (!ok) bad = true;
       if (ok) um_store<MODE, MAXT>(cur, tk, smem + (size_t)s * kUmStage, nrg, n_tasks, warp);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -370,7 +372,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
     // D(pair i) += A B^T over the unit's 48 open indices
     if (tid == 0 && u < n_units) {
       const uint32_t sa = smem_u32(smem + (size_t)s * kUmStage);
-      const uint32_t d = tmem + (uint32_t)((i & 1) * 128);
+      const uint32_t d = tmem + (uint32_t)(umsched::acc(i) * 128);
 #pragma unroll
       for (int kk = 0; kk < kUmK / 8; kk++) {
         const uint32_t o = 2 * kUmLbo * kk;  // 8 TF32 values = 2 core matrices along K
@@ -386,7 +388,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
         }
       }
       umma_commit(bar0 + 8 * s);
-      if (c == kUmUnits - 1) umma_commit(bar0 + 8 * (2 + (i & 1)));
+      if (c == kUmUnits - 1) umma_commit(bar0 + 8 * (2 + umsched::acc(i)));
       issued = u;
     }
     return true;
@@ -401,7 +403,7 @@ k_contract_umma(const float2* __restrict__ blk, int L, int n_out, const int* __r
   // the tensor memory is freed
   if (aborted && tid == 0) {
     atomicOr(err, 2);
-    if (issued >= 0) mbar_wait(bar0 + 8 * (issued & 1), (uint32_t)((issued >> 1) & 1), spin_limit);
+    if (issued >= 0) mbar_wait(bar0 + 8 * umsched::stage(issued), (uint32_t)((issued >> 1) & 1), spin_limit);
   }
   tc_fence_before();
   __syncthreads();
