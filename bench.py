@@ -470,7 +470,7 @@ def run_ours(args, torch, rank, world, local):
     df64 = {"value": shard.job_throughput(V * T * N_CH, world, ms_d), "ms_per_step": ms_d, "speedup_vs_fp64": ms / ms_d,
             "precision": "propagators, block build, FFTs, block-pair products and Wick sums in double-float "
                          "arithmetic (two FP32 words, 48-bit significand) on the FP32 pipes; FP64 for the input split "
-                         "and the normalisation; parity with the FP64 oracle at 1e-12 (measured <= 4e-14)",
+                         "and the normalisation; parity-tested against the FP64 oracle at 1e-12",
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in st_d.items()},
             "contract_ms_per_slice": cd_ms / max(cd_n, 1), "tuning": tune_d}
 
@@ -478,10 +478,11 @@ def run_ours(args, torch, rank, world, local):
     if not args.no_mixed:
         lower = mixed_leg(bbc.BBC_MIXED_FP32, "lower Dirac components (antibaryons backward in time), mixed FP32",
                           components=bbc.BBC_LOWER)
-        mixed = mixed_leg(bbc.BBC_MIXED_FP32, "FP32 blocks, FFTs and products; FP64 Wick sums and normalisation "
-                                              "(per-channel error vs FP64 at L=32: max 4.7e-7)")
+        mixed = mixed_leg(bbc.BBC_MIXED_FP32, "FP32 blocks, FFTs and products (tensor-core split-TF32 products "
+                                              "for the trace-form pairs); double-float Wick sums, FP64 "
+                                              "normalisation (per-channel errors: --error-report)")
         bf16 = mixed_leg(bbc.BBC_MIXED_BF16, "trial: Fourier-space blocks rounded to bfloat16 before the FP32 "
-                                             "products (per-channel error vs FP64 at L=32: max 2.9e-3)")
+                                             "products (per-channel errors: --error-report)")
 
     if rank != 0:
         return
